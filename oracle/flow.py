@@ -1,0 +1,262 @@
+"""Mass and momentum: ghost velocities, momentum predictor, ghost-fluid projection.
+
+Paper Sec. 2.3:
+  * ghost-velocity equation: in the narrow band, u_vap = u_liq - mdot [1/rho] n where
+    f_C = 1 and u_liq = u_vap + mdot [1/rho] n where f_C = 0, [1/rho] = 1/rho_l - 1/rho_v,
+    for cell and face velocities;
+  * discretization equations 1-3 solved separately for the liquid and the vapour
+    velocity fields (time-staggered approximate projection on a collocated grid);
+  * ghost-fluid Poisson equation: div(dt/rho_f grad p) = div u*_{f,liq} where
+    f_C = 1, div u*_{f,vap} where f_C = 0; face update (discretization equation 4)
+    for both fields and the cell update (discretization equation 5).
+
+Readings (the paper gives Eqs. 11-15 only):
+  * rho_c, mu_c are the property average of the cell volume fraction; face values
+    use the mean of the two cells' volume fractions (rho_f) or of their mu_c (mu_f);
+  * advection u . grad u with the WENO3 upwind derivative of the energy equation
+    (in place of the BCG scheme, whose equations the paper does not print);
+  * viscous term div(mu_f grad u*) implicit (backward Euler, the form of Eq. 11);
+    the transpose part of the stress is not included;
+  * the pressure-gradient / body-force term of Eqs. 11-15 is the face acceleration
+    a_f = g - grad_f p / rho_f averaged to cells (f->c: mean of the two faces; c->f:
+    mean of the two cells), with a_f = 0 on walls and symmetry planes;
+  * boundaries: no-slip wall (u = 0), symmetry (normal u = 0, tangential free),
+    outflow (zero normal gradient of u, p = 0 on the boundary face);
+  * a face's phase (for the face ghost velocity) is the colour of its midpoint on
+    the EBIT edge; mdot n at a face is the mean of its two cells;
+  * the surface-tension, 2[mu du/dn] and -mdot^2 [1/rho] terms of the pressure
+    jump are not imposed (the paper's projection changes only the RHS).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .energy import advect, velocity_sides
+
+WALL, OUTFLOW, SYMMETRY = 0, 1, 2
+
+
+def face_colours(vcol, hx_pos, vy_pos):
+    """Colour at the midpoint of every x-face (vertical edge) and y-face (horizontal edge)."""
+    vcut = vcol[:-1, :] != vcol[1:, :]
+    cx = np.where(vcut & (vy_pos < 0.5), vcol[1:, :], vcol[:-1, :])
+    hcut = vcol[:, :-1] != vcol[:, 1:]
+    cy = np.where(hcut & (hx_pos < 0.5), vcol[:, 1:], vcol[:, :-1])
+    return cx, cy
+
+
+# --------------------------------------------------------------------------
+# S10: ghost velocities
+# --------------------------------------------------------------------------
+def ghost_velocities(st):
+    pb, g = st.pb, st.geom
+    J = 1.0 / pb.rho_l - 1.0 / pb.rho_v
+    mn = st.mdot[..., None] * g.nb                # mdot n per cell
+    liq = (g.ccol == 1) & g.band
+    vap = (g.ccol == 0) & g.band
+    for c in range(2):
+        st.u_v[..., c] = np.where(liq, st.u_l[..., c] - J * mn[..., c], st.u_v[..., c])
+        st.u_l[..., c] = np.where(vap, st.u_v[..., c] + J * mn[..., c], st.u_l[..., c])
+    cx, cy = face_colours(st.vcol, st.hx_pos, st.vy_pos)
+    # x-faces 1..nx-1
+    bx = g.band[:, :-1] | g.band[:, 1:]
+    mfx = 0.5 * (mn[:, :-1, 0] + mn[:, 1:, 0])
+    fl = bx & (cx[:, 1:-1] == 1)
+    fv = bx & (cx[:, 1:-1] == 0)
+    ul, uv = st.ufx_l[:, 1:-1], st.ufx_v[:, 1:-1]
+    st.ufx_v[:, 1:-1] = np.where(fl, ul - J * mfx, uv)
+    st.ufx_l[:, 1:-1] = np.where(fv, uv + J * mfx, ul)
+    by = g.band[:-1, :] | g.band[1:, :]
+    mfy = 0.5 * (mn[:-1, :, 1] + mn[1:, :, 1])
+    fl = by & (cy[1:-1, :] == 1)
+    fv = by & (cy[1:-1, :] == 0)
+    ul, uv = st.ufy_l[1:-1, :], st.ufy_v[1:-1, :]
+    st.ufy_v[1:-1, :] = np.where(fl, ul - J * mfy, uv)
+    st.ufy_l[1:-1, :] = np.where(fv, uv + J * mfy, ul)
+
+
+# --------------------------------------------------------------------------
+# properties
+# --------------------------------------------------------------------------
+def mixture(pb, vf):
+    rho_c = pb.rho_l * vf + pb.rho_v * (1.0 - vf)
+    mu_c = pb.mu_l * vf + pb.mu_v * (1.0 - vf)
+    return rho_c, mu_c
+
+
+def face_rho(pb, vf):
+    """rho on x-faces [ny, nx+1] and y-faces [ny+1, nx]; boundary faces take the boundary cell."""
+    ny, nx = vf.shape
+    vx = np.empty((ny, nx + 1))
+    vx[:, 1:-1] = 0.5 * (vf[:, :-1] + vf[:, 1:])
+    vx[:, 0], vx[:, -1] = vf[:, 0], vf[:, -1]
+    vy = np.empty((ny + 1, nx))
+    vy[1:-1, :] = 0.5 * (vf[:-1, :] + vf[1:, :])
+    vy[0, :], vy[-1, :] = vf[0, :], vf[-1, :]
+    return pb.rho_l * vx + pb.rho_v * (1.0 - vx), pb.rho_l * vy + pb.rho_v * (1.0 - vy)
+
+
+def face_acceleration(pb, p, rfx, rfy):
+    """a_f = g - grad_f p / rho_f on every face (zero on walls/symmetry planes)."""
+    ny, nx = p.shape
+    h = pb.h
+    ax = np.zeros((ny, nx + 1))
+    ay = np.zeros((ny + 1, nx))
+    ax[:, 1:-1] = pb.gx - (p[:, 1:] - p[:, :-1]) / (h * rfx[:, 1:-1])
+    ay[1:-1, :] = pb.gy - (p[1:, :] - p[:-1, :]) / (h * rfy[1:-1, :])
+    if pb.bc[0] == OUTFLOW:
+        ax[:, 0] = pb.gx - (2.0 * p[:, 0]) / (h * rfx[:, 0])
+    if pb.bc[1] == OUTFLOW:
+        ax[:, -1] = pb.gx - (-2.0 * p[:, -1]) / (h * rfx[:, -1])
+    if pb.bc[2] == OUTFLOW:
+        ay[0, :] = pb.gy - (2.0 * p[0, :]) / (h * rfy[0, :])
+    if pb.bc[3] == OUTFLOW:
+        ay[-1, :] = pb.gy - (-2.0 * p[-1, :]) / (h * rfy[-1, :])
+    return ax, ay
+
+
+def faces_to_cells(ax, ay):
+    g = np.empty(ax.shape[:1] + (ax.shape[1] - 1, 2))
+    g[..., 0] = 0.5 * (ax[:, :-1] + ax[:, 1:])
+    g[..., 1] = 0.5 * (ay[:-1, :] + ay[1:, :])
+    return g
+
+
+# --------------------------------------------------------------------------
+# S11: momentum predictor
+# --------------------------------------------------------------------------
+def _five_point(nx, ny, wx, wy, diag_extra):
+    """Sparse SPD matrix: diag_extra + sum_faces w (u_i - u_j); wx [ny, nx-1], wy [ny-1, nx]."""
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    diag = diag_extra.copy()
+    diag[:, :-1] += wx
+    diag[:, 1:] += wx
+    diag[:-1, :] += wy
+    diag[1:, :] += wy
+    rows = [idx[:, :-1].ravel(), idx[:, 1:].ravel(), idx[:-1, :].ravel(), idx[1:, :].ravel(), idx.ravel()]
+    cols = [idx[:, 1:].ravel(), idx[:, :-1].ravel(), idx[1:, :].ravel(), idx[:-1, :].ravel(), idx.ravel()]
+    vals = [-wx.ravel(), -wx.ravel(), -wy.ravel(), -wy.ravel(), diag.ravel()]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(nx * ny, nx * ny))
+
+
+def _side_slices(nx, ny):
+    return {0: (slice(None), 0), 1: (slice(None), nx - 1), 2: (0, slice(None)), 3: (ny - 1, slice(None))}
+
+
+def viscous_matrix(pb, rho_c, mu_c, comp):
+    """(h^2 rho_c / dt) u + sum_f mu_f (u_i - u_j) + Dirichlet boundary faces 2 mu u_i."""
+    ny, nx = rho_c.shape
+    h = pb.h
+    wx = 0.5 * (mu_c[:, :-1] + mu_c[:, 1:])
+    wy = 0.5 * (mu_c[:-1, :] + mu_c[1:, :])
+    extra = h * h * rho_c / pb.dt
+    sl = _side_slices(nx, ny)
+    for s, (mode, _) in enumerate(velocity_sides(pb.bc, comp)):
+        if mode == "odd":
+            extra[sl[s]] += 2.0 * mu_c[sl[s]]
+    return _five_point(nx, ny, wx, wy, extra)
+
+
+def predictor(st, gc):
+    """Eqs. 11-13 for the liquid and the vapour velocity fields.  Returns u** and face u_f*."""
+    pb, g = st.pb, st.geom
+    ny, nx = pb.ny, pb.nx
+    h, dt = pb.h, pb.dt
+    rho_c, mu_c = mixture(pb, g.vf)
+    coef = h * h * rho_c / dt
+    ustar = {}
+    for name, u in (("l", st.u_l), ("v", st.u_v)):
+        ustar[name] = np.empty_like(u)
+    for c in range(2):
+        A = viscous_matrix(pb, rho_c, mu_c, c).tocsc()
+        sides = velocity_sides(pb.bc, c)
+        rhs = []
+        for name, u in (("l", st.u_l), ("v", st.u_v)):
+            ua = advect(u[..., c], u, sides, dt, h)
+            rhs.append((coef * (ua + dt * gc[..., c])).ravel())
+        sol = spla.spsolve(A, np.stack(rhs, axis=1))
+        for k, name in enumerate(("l", "v")):
+            ustar[name][..., c] = sol[:, k].reshape(ny, nx) - dt * gc[..., c]
+    faces = {}
+    for name in ("l", "v"):
+        u2 = ustar[name]
+        fx = np.zeros((ny, nx + 1))
+        fy = np.zeros((ny + 1, nx))
+        fx[:, 1:-1] = 0.5 * (u2[:, :-1, 0] + u2[:, 1:, 0]) + dt * pb.gx
+        fy[1:-1, :] = 0.5 * (u2[:-1, :, 1] + u2[1:, :, 1]) + dt * pb.gy
+        if pb.bc[0] == OUTFLOW:
+            fx[:, 0] = u2[:, 0, 0] + dt * pb.gx
+        if pb.bc[1] == OUTFLOW:
+            fx[:, -1] = u2[:, -1, 0] + dt * pb.gx
+        if pb.bc[2] == OUTFLOW:
+            fy[0, :] = u2[0, :, 1] + dt * pb.gy
+        if pb.bc[3] == OUTFLOW:
+            fy[-1, :] = u2[-1, :, 1] + dt * pb.gy
+        faces[name] = (fx, fy)
+    return ustar, faces
+
+
+# --------------------------------------------------------------------------
+# S12: projection
+# --------------------------------------------------------------------------
+def poisson_matrix(pb, rfx, rfy):
+    ny, nx = rfx.shape[0], rfy.shape[1]
+    wx = pb.dt / rfx[:, 1:-1]
+    wy = pb.dt / rfy[1:-1, :]
+    extra = np.zeros((ny, nx))
+    if pb.bc[0] == OUTFLOW:
+        extra[:, 0] += 2.0 * pb.dt / rfx[:, 0]
+    if pb.bc[1] == OUTFLOW:
+        extra[:, -1] += 2.0 * pb.dt / rfx[:, -1]
+    if pb.bc[2] == OUTFLOW:
+        extra[0, :] += 2.0 * pb.dt / rfy[0, :]
+    if pb.bc[3] == OUTFLOW:
+        extra[-1, :] += 2.0 * pb.dt / rfy[-1, :]
+    return _five_point(nx, ny, wx, wy, extra)
+
+
+def poisson_rhs(pb, ccol, faces):
+    """-h times the undivided divergence of the face field of each cell's phase (ghost-fluid Poisson equation)."""
+    div = {}
+    for name, (fx, fy) in faces.items():
+        div[name] = (fx[:, 1:] - fx[:, :-1]) + (fy[1:, :] - fy[:-1, :])
+    return -pb.h * np.where(ccol == 1, div["l"], div["v"])
+
+
+def project(st, ustar, faces):
+    """Solve the ghost-fluid Poisson equation, update faces (Eq. 14), accelerations and cells (Eq. 15)."""
+    pb, g = st.pb, st.geom
+    ny, nx = pb.ny, pb.nx
+    rfx, rfy = face_rho(pb, g.vf)
+    A = poisson_matrix(pb, rfx, rfy).tocsc()
+    b = poisson_rhs(pb, g.ccol, faces).ravel()
+    p = spla.spsolve(A, b).reshape(ny, nx)
+    ax, ay = face_acceleration(pb, p, rfx, rfy)
+    # face update: u_f^{n+1} = u_f* + dt (a_f - g) on faces the projection acts on
+    gcorr_x = ax - pb.gx
+    gcorr_y = ay - pb.gy
+    out = {}
+    for name, (fx, fy) in faces.items():
+        nfx = fx + pb.dt * gcorr_x
+        nfy = fy + pb.dt * gcorr_y
+        for s, kind in enumerate(pb.bc):
+            if kind != OUTFLOW:
+                if s == 0:
+                    nfx[:, 0] = 0.0
+                elif s == 1:
+                    nfx[:, -1] = 0.0
+                elif s == 2:
+                    nfy[0, :] = 0.0
+                else:
+                    nfy[-1, :] = 0.0
+        out[name] = (nfx, nfy)
+    gc = faces_to_cells(ax, ay)
+    st.p = p
+    st.gc = gc
+    st.u_l = ustar["l"] + pb.dt * gc
+    st.u_v = ustar["v"] + pb.dt * gc
+    st.ufx_l, st.ufy_l = out["l"]
+    st.ufx_v, st.ufy_v = out["v"]

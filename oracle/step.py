@@ -1,0 +1,158 @@
+"""State, preparation and the time iteration of Sec. 2.5; diagnostics of Sec. 3.
+
+One time step, in the paper's order (Sec. 2.5):
+  1. energy advection (S1) and extension of T* into the cells the interface will
+     sweep (S6);
+  2. interface advection by EBIT (S2 interfacial velocity, S3/S4 sweeps, S5
+     reconnection);
+  3. energy diffusion with the sharp T = T_sat condition (S7 ghost-fluid
+     coefficients, S8 solve), then the ghost band of T is refilled;
+  4. mass flux (S9) extended over the band, ghost velocities (S10);
+  5. mass and momentum: predictor (S11) and ghost-fluid projection (S12).
+Diagnostics (S13): vapour volume, the volume the mass flux should have added,
+M_d (mass-in-domain equation) and the outlet mass of M_c (mass-with-outflow
+equation).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import energy, flow, sweep
+from .geometry import reconstruct, segment_data
+
+
+class State:
+    """Full oracle state; pb is the Problem (grid, properties, boundary conditions)."""
+
+    def __init__(self, pb):
+        self.pb = pb
+        self.vcol = pb.vcol.copy()
+        self.hx_pos = np.where(pb.vcol[:, :-1] != pb.vcol[:, 1:], pb.hx_pos, 0.0)
+        self.vy_pos = np.where(pb.vcol[:-1, :] != pb.vcol[1:, :], pb.vy_pos, 0.0)
+        self.T_l = pb.T_l.copy()
+        self.T_v = pb.T_v.copy()
+        self.u_l = pb.u_l.copy()
+        self.u_v = pb.u_v.copy()
+        self.ufx_l = pb.ufx_l.copy()
+        self.ufx_v = pb.ufx_v.copy()
+        self.ufy_l = pb.ufy_l.copy()
+        self.ufy_v = pb.ufy_v.copy()
+        self.p = pb.p.copy()
+        self.gc = np.zeros(pb.u_l.shape)
+        self.mdot = np.zeros((pb.ny, pb.nx))
+        self.geom = None
+        self.t = pb.t0
+        self.nstep = 0
+        self.diag = []
+
+    def copy(self):
+        import copy
+        return copy.deepcopy(self)
+
+
+def interface_mdot(st):
+    """mdot on the cut cells (mass-flux equation, or the imposed value), extended over the band."""
+    pb, g = st.pb, st.geom
+    if pb.energy:
+        m = energy.mass_flux(g, st.T_l, st.T_v, pb)
+    else:
+        m = np.where(g.nseg > 0, pb.mdot_fixed, 0.0)
+    return energy.extend_mdot(m, g, pb.extend_iters)
+
+
+def prepare(pb):
+    """Initial state: reconstruction, ghost band of T, mdot, ghost velocities, initial accelerations."""
+    st = State(pb)
+    st.geom = reconstruct(st.vcol, st.hx_pos, st.vy_pos)
+    if pb.energy:
+        st.T_l, st.T_v = energy.extend_temperatures(st.T_l, st.T_v, st.geom, pb.extend_iters)
+    st.mdot = interface_mdot(st)
+    flow.ghost_velocities(st)
+    rfx, rfy = flow.face_rho(pb, st.geom.vf)
+    ax, ay = flow.face_acceleration(pb, st.p, rfx, rfy)
+    st.gc = flow.faces_to_cells(ax, ay)
+    return st
+
+
+def advance_interface(st):
+    """S2-S5: dimension-split EBIT advection with u_Gamma from the start-of-step state."""
+    pb = st.pb
+    g0 = st.geom
+    uG = sweep.interface_velocity_cells(st.u_l, st.u_v, g0.ccol, st.mdot, g0.nb, pb.rho_l, pb.rho_v)
+    dth = pb.dt / pb.h
+    order = (0, 1) if (pb.sweep_order == 0 or st.nstep % 2 == 0) else (1, 0)
+    g = g0
+    for axis in order:
+        st.vcol, st.hx_pos, st.vy_pos = sweep.sweep(st.vcol, st.hx_pos, st.vy_pos, g, uG, dth, axis, pb.bc)
+        g = reconstruct(st.vcol, st.hx_pos, st.vy_pos)
+    st.geom = g
+
+
+def step(st):
+    """Advance st by one time step in place; returns the diagnostics row."""
+    pb = st.pb
+    g_old = st.geom
+    # 1. energy advection + extension of T* (old interface)
+    if pb.energy:
+        Ts_l = energy.advect(st.T_l, st.u_l, energy.temperature_sides(pb.T_bc), pb.dt, pb.h)
+        Ts_v = energy.advect(st.T_v, st.u_v, energy.temperature_sides(pb.T_bc), pb.dt, pb.h)
+        Ts_l, Ts_v = energy.extend_temperatures(Ts_l, Ts_v, g_old, pb.extend_iters)
+    # 2. interface advection
+    advance_interface(st)
+    g = st.geom
+    # 3. energy diffusion (new interface) and ghost band
+    if pb.energy:
+        st.T_l, st.T_v = energy.solve_energy(g, Ts_l, Ts_v, pb)
+        st.T_l, st.T_v = energy.extend_temperatures(st.T_l, st.T_v, g, pb.extend_iters)
+    # 4. mass flux and ghost velocities
+    st.mdot = interface_mdot(st)
+    flow.ghost_velocities(st)
+    # 5. momentum predictor and projection
+    ustar, faces = flow.predictor(st, st.gc)
+    flow.project(st, ustar, faces)
+    st.t += pb.dt
+    st.nstep += 1
+    row = diagnostics(st)
+    st.diag.append(row)
+    return row
+
+
+def diagnostics(st):
+    """[t, vapour volume, dV expected from mdot this step, M_d, outlet mass this step, cut cells]."""
+    pb, g = st.pb, st.geom
+    h2 = pb.h * pb.h
+    Vv = float(np.sum(1.0 - g.vf)) * h2
+    mS = 0.0
+    for (j, i), _, _, L in segment_data(g):
+        mS += st.mdot[j, i] * L * pb.h
+    dV = mS * pb.dt / pb.rho_v
+    rho_c, _ = flow.mixture(pb, g.vf)
+    Md = float(np.sum(rho_c)) * h2
+    out = 0.0
+    ccol = g.ccol
+    for s, kind in enumerate(pb.bc):
+        if kind != flow.OUTFLOW:
+            continue
+        if s == 0:
+            u = np.where(ccol[:, 0] == 1, st.ufx_l[:, 0], st.ufx_v[:, 0])
+            out += float(np.sum(-rho_c[:, 0] * u))
+        elif s == 1:
+            u = np.where(ccol[:, -1] == 1, st.ufx_l[:, -1], st.ufx_v[:, -1])
+            out += float(np.sum(rho_c[:, -1] * u))
+        elif s == 2:
+            u = np.where(ccol[0, :] == 1, st.ufy_l[0, :], st.ufy_v[0, :])
+            out += float(np.sum(-rho_c[0, :] * u))
+        else:
+            u = np.where(ccol[-1, :] == 1, st.ufy_l[-1, :], st.ufy_v[-1, :])
+            out += float(np.sum(rho_c[-1, :] * u))
+    out *= pb.h * pb.dt
+    return np.array([st.t, Vv, dV, Md, out, float(np.count_nonzero(g.nseg))])
+
+
+def run(pb, steps=None):
+    st = prepare(pb)
+    for _ in range(pb.steps if steps is None else steps):
+        step(st)
+    return st

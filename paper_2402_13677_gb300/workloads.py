@@ -1,0 +1,348 @@
+"""Seeded, synthetic initial states for the EBIT phase-change workloads.
+
+This module only *describes problems*: grid, boundary conditions, material
+properties, the initial interface (vertex colours + one marker fraction per cut
+edge, found by root-finding an analytic level set) and the initial fields
+(closed-form similarity solutions where the problem has one).  It holds none of
+the method's arithmetic (no reconstruction, advection, ghost-fluid or solver
+step), so both the CUDA path and the CPU oracle can start from the same state.
+
+Closed forms:
+  * 1D Stefan problem (Sec. 3.1, interface-position and temperature equations):
+    X(t) = 2 beta sqrt(alpha_v t),  beta exp(beta^2) erf(beta) = cp_v dT / (sqrt(pi) h_lg).
+  * Planar (cylindrical) analogue of the Scriven problem (Sec. 3.4): the paper's
+    case is spherical/axisymmetric; the 2D planar similarity solution used here is
+    derived in the same way (liquid velocity eps R R'/r, eps = 1 - rho_v/rho_l):
+    R = 2 beta sqrt(alpha_l t),  T(eta) = T_inf - dT I(eta)/I(beta),
+    I(eta) = int_eta^inf s^(2 eps beta^2 - 1) exp(-s^2) ds,
+    Ja = rho_l cp_l dT / (rho_v h_lg) = 2 beta^2 exp(beta^2) beta^(-2 eps beta^2) I(beta).
+  * Bubble with a constant mass flux (Sec. 3.3): R(t) = R0 + mdot t / rho_v.
+
+Arrays are row-major with x fastest: cell fields are [ny, nx], vertex colours
+[ny+1, nx+1], horizontal edges [ny+1, nx], vertical edges [ny, nx+1].
+Colour 1 = liquid, 0 = vapour.  Marker fractions are measured from the
+lower/left vertex of their edge, in [FMIN, 1 - FMIN].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import optimize, special
+
+FMIN = 1e-9  # markers never sit exactly on a vertex
+
+# boundary kinds, order of sides: left, right, bottom, top
+WALL, OUTFLOW, SYMMETRY = 0, 1, 2
+BC_NAMES = {"wall": WALL, "outflow": OUTFLOW, "symmetry": SYMMETRY}
+
+
+@dataclass
+class Problem:
+    """Everything that defines one instance: grid, physics, initial state."""
+    name: str
+    nx: int
+    ny: int
+    h: float
+    x0: float = 0.0
+    y0: float = 0.0
+    dt: float = 1e-4
+    steps: int = 1
+    # properties: liquid, vapour
+    rho_l: float = 1.0
+    rho_v: float = 1.0
+    mu_l: float = 0.01
+    mu_v: float = 0.01
+    lam_l: float = 1.0
+    lam_v: float = 1.0
+    cp_l: float = 1.0
+    cp_v: float = 1.0
+    T_sat: float = 0.0
+    h_lg: float = 1.0
+    gx: float = 0.0
+    gy: float = 0.0
+    bc: tuple = (WALL, OUTFLOW, SYMMETRY, SYMMETRY)
+    # Dirichlet temperature per side (None = zero normal gradient)
+    T_bc: tuple = (None, None, None, None)
+    theta_min: float = 1e-3
+    extend_iters: int = 5
+    sweep_order: int = 1          # 0: always x then y; 1: alternate
+    energy: bool = True           # False: mdot imposed (constant-mass-flux bubble)
+    mdot_fixed: float = 0.0
+    # initial state (filled by the generators)
+    vcol: np.ndarray = None
+    hx_cut: np.ndarray = None
+    hx_pos: np.ndarray = None
+    vy_cut: np.ndarray = None
+    vy_pos: np.ndarray = None
+    T_l: np.ndarray = None
+    T_v: np.ndarray = None
+    u_l: np.ndarray = None        # [ny, nx, 2]
+    u_v: np.ndarray = None
+    ufx_l: np.ndarray = None      # [ny, nx+1]
+    ufx_v: np.ndarray = None
+    ufy_l: np.ndarray = None      # [ny+1, nx]
+    ufy_v: np.ndarray = None
+    p: np.ndarray = None
+    t0: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+    def copy(self) -> "Problem":
+        import copy
+        return copy.deepcopy(self)
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+def stefan_beta(St: float) -> float:
+    """Root of beta exp(beta^2) erf(beta) = St / sqrt(pi), St = cp_v dT / h_lg."""
+    f = lambda b: b * math.exp(b * b) * math.erf(b) - St / math.sqrt(math.pi)
+    return optimize.brentq(f, 1e-12, 10.0, xtol=1e-15, rtol=1e-15, maxiter=500)
+
+
+def stefan_position(t, beta, alpha_v):
+    return 2.0 * beta * np.sqrt(alpha_v * t)
+
+
+def stefan_temperature(x, t, beta, alpha_v, T_w, T_sat):
+    return T_w + (T_sat - T_w) / math.erf(beta) * special.erf(x / (2.0 * np.sqrt(alpha_v * t)))
+
+
+def _bubble2d_logI(eta, a):
+    """log of I(eta) = int_eta^inf s^(2a-1) exp(-s^2) ds = Gamma(a) Q(a, eta^2) / 2."""
+    q = special.gammaincc(a, eta * eta)
+    return special.gammaln(a) + np.log(q) - math.log(2.0)
+
+
+def bubble2d_beta(Ja: float, eps: float) -> float:
+    """Growth constant of the planar bubble: Ja = 2 b^2 e^{b^2} b^{-2 eps b^2} I(b)."""
+    def g(b):
+        a = eps * b * b
+        logrhs = math.log(2.0) + 2 * math.log(b) + b * b - 2 * a * math.log(b) + _bubble2d_logI(b, a)
+        return logrhs - math.log(Ja)
+    return optimize.brentq(g, 1e-3, 60.0, xtol=1e-14, rtol=1e-15, maxiter=500)
+
+
+def bubble2d_temperature(r, t, beta, eps, alpha_l, T_inf, T_sat):
+    a = eps * beta * beta
+    eta = np.asarray(r) / (2.0 * np.sqrt(alpha_l * t))
+    ratio = np.exp(_bubble2d_logI(np.maximum(eta, 1e-300), a) - _bubble2d_logI(beta, a))
+    return T_inf - (T_inf - T_sat) * ratio
+
+
+# --------------------------------------------------------------------------
+# interface from a level set (phi > 0: liquid)
+# --------------------------------------------------------------------------
+def interface_from_levelset(phi, nx, ny, h, x0=0.0, y0=0.0):
+    """Vertex colours and one marker per cut edge, the marker at the root of phi."""
+    xs = x0 + h * np.arange(nx + 1)
+    ys = y0 + h * np.arange(ny + 1)
+    X, Y = np.meshgrid(xs, ys)
+    pv = phi(X, Y)
+    vcol = (pv > 0).astype(np.uint8)
+    hx_cut = (vcol[:, :-1] != vcol[:, 1:]).astype(np.uint8)
+    vy_cut = (vcol[:-1, :] != vcol[1:, :]).astype(np.uint8)
+    hx_pos = np.zeros((ny + 1, nx))
+    vy_pos = np.zeros((ny, nx + 1))
+
+    def root(fn):
+        a, b = fn(0.0), fn(1.0)
+        if a == 0.0:
+            return FMIN
+        if b == 0.0:
+            return 1.0 - FMIN
+        s = optimize.brentq(fn, 0.0, 1.0, xtol=1e-15, rtol=1e-15, maxiter=200)
+        return min(max(s, FMIN), 1.0 - FMIN)
+
+    for j, i in zip(*np.nonzero(hx_cut)):
+        yv = y0 + h * j
+        hx_pos[j, i] = root(lambda s: float(phi(x0 + h * (i + s), yv)))
+    for j, i in zip(*np.nonzero(vy_cut)):
+        xv = x0 + h * i
+        vy_pos[j, i] = root(lambda s: float(phi(xv, y0 + h * (j + s))))
+    return vcol, hx_cut, hx_pos, vy_cut, vy_pos
+
+
+def _grids(nx, ny, h, x0, y0):
+    xc = x0 + h * (np.arange(nx) + 0.5)
+    yc = y0 + h * (np.arange(ny) + 0.5)
+    Xc, Yc = np.meshgrid(xc, yc)
+    xf = x0 + h * np.arange(nx + 1)
+    Xfx, Yfx = np.meshgrid(xf, yc)           # x-faces
+    yf = y0 + h * np.arange(ny + 1)
+    Xfy, Yfy = np.meshgrid(xc, yf)           # y-faces
+    return (Xc, Yc), (Xfx, Yfx), (Xfy, Yfy)
+
+
+def _zero_flow(pb):
+    nx, ny = pb.nx, pb.ny
+    pb.u_l = np.zeros((ny, nx, 2))
+    pb.u_v = np.zeros((ny, nx, 2))
+    pb.ufx_l = np.zeros((ny, nx + 1))
+    pb.ufx_v = np.zeros((ny, nx + 1))
+    pb.ufy_l = np.zeros((ny + 1, nx))
+    pb.ufy_v = np.zeros((ny + 1, nx))
+    pb.p = np.zeros((ny, nx))
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+def stefan(nx=64, ny=64, X0=0.1, Lx=1.0, rho_l=10.0, rho_v=1.0, St=0.1, dT=1.0,
+           mu=0.01, dt=1e-4, steps=100, **kw) -> Problem:
+    """1D Stefan problem embedded in 2D: vapour x < X0 on a wall at T_sat + dT.
+
+    Left: no-slip wall at T_w; right: outflow; bottom/top: symmetry.
+    Nondimensional: k = cp = 1 in both phases, h_lg = cp dT / St, T_sat = 0.
+    """
+    h = Lx / nx
+    h_lg = 1.0 * dT / St
+    pb = Problem("stefan", nx, ny, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v,
+                 mu_l=mu, mu_v=mu, lam_l=1.0, lam_v=1.0, cp_l=1.0, cp_v=1.0,
+                 T_sat=0.0, h_lg=h_lg, bc=(WALL, OUTFLOW, SYMMETRY, SYMMETRY),
+                 T_bc=(dT, None, None, None), **kw)
+    beta = stefan_beta(St)
+    alpha_v = pb.lam_v / (pb.rho_v * pb.cp_v)
+    t0 = (X0 / (2 * beta)) ** 2 / alpha_v
+    pb.t0 = t0
+    pb.meta.update(beta=beta, alpha_v=alpha_v, T_w=dT, X0=X0)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: x - X0, nx, ny, h)
+    (Xc, Yc), (Xfx, Yfx), (Xfy, Yfy) = _grids(nx, ny, h, 0.0, 0.0)
+    pb.T_v = stefan_temperature(Xc, t0, beta, alpha_v, dT, 0.0)
+    pb.T_l = np.zeros((ny, nx))
+    _zero_flow(pb)
+    Xdot = beta * math.sqrt(alpha_v / t0)
+    mdot = rho_v * Xdot
+    U = mdot * (1.0 / rho_v - 1.0 / rho_l)
+    pb.meta.update(mdot0=mdot, U=U)
+    pb.u_l[..., 0] = U
+    pb.ufx_l[:, 1:] = U          # the wall face stays 0
+    return pb
+
+
+def bubble(n=512, R0=0.05, rho_ratio=20.0, k_ratio=5.0, St=0.2, dT=1.0, mu=0.01,
+           dt=1.96e-6, steps=2000, seed=0, noise=1e-3, **kw) -> Problem:
+    """Circular vapour bubble growing in superheated liquid (planar), outflow on all sides."""
+    h = 1.0 / n
+    rho_v, rho_l = 1.0, rho_ratio
+    lam_v, lam_l = 1.0, k_ratio
+    h_lg = 1.0 * dT / St
+    pb = Problem("bubble", n, n, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v,
+                 mu_l=mu, mu_v=mu, lam_l=lam_l, lam_v=lam_v, cp_l=1.0, cp_v=1.0,
+                 T_sat=0.0, h_lg=h_lg, bc=(OUTFLOW,) * 4, T_bc=(None,) * 4, **kw)
+    Ja = rho_l * 1.0 * dT / (rho_v * h_lg)
+    eps = 1.0 - rho_v / rho_l
+    beta = bubble2d_beta(Ja, eps)
+    alpha_l = lam_l / (rho_l * 1.0)
+    t0 = (R0 / (2 * beta)) ** 2 / alpha_l
+    Rdot = beta * math.sqrt(alpha_l / t0)
+    pb.t0 = t0
+    pb.meta.update(beta=beta, eps=eps, alpha_l=alpha_l, Ja=Ja, R0=R0, Rdot0=Rdot, xc=0.5, yc=0.5)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: np.hypot(x - 0.5, y - 0.5) - R0, n, n, h)
+    (Xc, Yc), (Xfx, Yfx), (Xfy, Yfy) = _grids(n, n, h, 0.0, 0.0)
+    r = np.hypot(Xc - 0.5, Yc - 0.5)
+    pb.T_l = bubble2d_temperature(r, t0, beta, eps, alpha_l, dT, 0.0)
+    if seed:
+        rng = np.random.default_rng(seed)
+        pb.T_l = pb.T_l + rng.uniform(-noise, noise, size=pb.T_l.shape)
+    pb.T_v = np.zeros((n, n))
+    _zero_flow(pb)
+
+    def radial(X, Y):
+        rr = np.hypot(X - 0.5, Y - 0.5)
+        mag = np.where(rr >= R0, eps * R0 * Rdot / np.maximum(rr, 1e-300), eps * Rdot * rr / R0)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            ex = np.where(rr > 0, (X - 0.5) / np.maximum(rr, 1e-300), 0.0)
+            ey = np.where(rr > 0, (Y - 0.5) / np.maximum(rr, 1e-300), 0.0)
+        return mag * ex, mag * ey
+
+    ux, uy = radial(Xc, Yc)
+    pb.u_l[..., 0], pb.u_l[..., 1] = ux, uy
+    pb.ufx_l[:] = radial(Xfx, Yfx)[0]
+    pb.ufy_l[:] = radial(Xfy, Yfy)[1]
+    return pb
+
+
+def const_mdot_bubble(n=64, L=8.0, R0=2.0, mdot=0.1, rho_l=1000.0, rho_v=1.0,
+                      mu_l=1e-3, mu_v=1.26e-5, dt=None, steps=100, **kw) -> Problem:
+    """Bubble with an imposed constant mass flux, energy equation off (Sec. 3.3).
+
+    Lengths in mm-like units on [-L/2, L/2]^2 centred on the bubble; outflow on all sides.
+    """
+    h = L / n
+    if dt is None:
+        dt = 0.1 * h * rho_v / abs(mdot)
+    pb = Problem("const_mdot_bubble", n, n, h, x0=-L / 2, y0=-L / 2, dt=dt, steps=steps,
+                 rho_l=rho_l, rho_v=rho_v, mu_l=mu_l, mu_v=mu_v, T_sat=0.0, h_lg=1.0,
+                 bc=(OUTFLOW,) * 4, T_bc=(None,) * 4, energy=False, mdot_fixed=mdot, **kw)
+    pb.meta.update(R0=R0, mdot=mdot, xc=0.0, yc=0.0)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: np.hypot(x, y) - R0, n, n, h, -L / 2, -L / 2)
+    pb.T_l = np.zeros((n, n))
+    pb.T_v = np.zeros((n, n))
+    _zero_flow(pb)
+    return pb
+
+
+def film(nx=1024, ny=2048, Lx=1.0, mean=0.05, amp=0.005, modes=None, seed=0,
+         rho_l=5.0, rho_v=1.0, mu_l=5e-3, mu_v=1e-3, lam_l=1e-2, lam_v=1e-3,
+         St=0.064, dT=1.0, g=-1.0, dt=None, steps=5000, **kw) -> Problem:
+    """Film boiling over a heated wall: vapour film y < eta(x), eta = mean + sum_k a_k cos(2 pi k x / Lx).
+
+    Bottom: no-slip wall at T_sat + dT; top: outflow; sides: symmetry.  The seed picks the
+    number of modes (1-4 unless given) and a random sign per mode (the side walls are
+    symmetry planes, so each mode is a cosine).
+    """
+    h = Lx / nx
+    rng = np.random.default_rng(seed)
+    if modes is None:
+        modes = int(rng.integers(1, 5))
+    signs = rng.choice([-1.0, 1.0], size=modes)
+    a = amp / modes
+    h_lg = 1.0 * dT / St
+    if dt is None:
+        dt = 0.25 * h
+    pb = Problem("film", nx, ny, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v,
+                 mu_l=mu_l, mu_v=mu_v, lam_l=lam_l, lam_v=lam_v, cp_l=1.0, cp_v=1.0,
+                 T_sat=0.0, h_lg=h_lg, gx=0.0, gy=g, bc=(SYMMETRY, SYMMETRY, WALL, OUTFLOW),
+                 T_bc=(None, None, dT, None), **kw)
+    ks = np.arange(1, modes + 1)
+
+    def eta(x):
+        x = np.asarray(x, dtype=float)
+        return mean + a * np.sum(signs[:, None] * np.cos(2 * np.pi * ks[:, None] * x.ravel()[None, :] / Lx),
+                                 axis=0).reshape(x.shape)
+
+    pb.meta.update(modes=modes, signs=signs.tolist(), amp=a, mean=mean)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: y - eta(x), nx, ny, h)
+    (Xc, Yc), _, _ = _grids(nx, ny, h, 0.0, 0.0)
+    e = eta(Xc[0])[None, :]
+    pb.T_v = dT * (1.0 - Yc / e)
+    pb.T_l = np.zeros((ny, nx))
+    _zero_flow(pb)
+    return pb
+
+
+def c1_stefan(**kw):
+    return stefan(64, 64, X0=0.1, dt=1e-4, steps=100, **kw)
+
+
+def c2_bubble(**kw):
+    return bubble(512, **kw)
+
+
+def c3_film(**kw):
+    return film(1024, 2048, Lx=1.0, **kw)
+
+
+def c5_film(**kw):
+    return film(4096, 4096, Lx=8.0, modes=32, rho_l=50.0, rho_v=1.0, mu_l=1e-2, mu_v=1e-3,
+                lam_l=1e-2, lam_v=1e-3, St=0.1, **kw)
+
+
+WORKLOADS = {"c1_stefan": c1_stefan, "c2_bubble": c2_bubble, "c3_film": c3_film, "c5_film": c5_film}

@@ -20,10 +20,11 @@ paper only cites):
     marker exactly on a vertex counts as lying after it);
   * new unaligned markers: where a displaced pre-sweep segment P'Q' strictly
     crosses an unaligned grid line, the crossing of the circle through P', Q' and
-    R' (R = chain neighbour of the endpoint nearer the line, through the adjacent
-    cell) is taken, the root inside the segment's range nearest the straight-line
-    crossing; straight line if R is missing or no root lies in range; a displaced
-    marker lying exactly on an unaligned line is itself a crossing;
+    R' is taken (R = chain neighbour, through the adjacent cell, of the endpoint
+    nearer the line): the root nearest the straight-line (chord) crossing, if it
+    lies within |P'Q'|_1 of it, else the chord crossing (also when R is missing);
+    the marker is kept inside the cell row of the segment; a displaced marker
+    lying exactly on an unaligned line is itself a crossing;
   * one marker per edge: an edge is cut iff its new vertex colours differ; its
     marker is the median (lower median) of the crossings that landed on it, or the
     edge midpoint if none did;
@@ -128,16 +129,14 @@ def _crossing(E, O, R, m, axis):
                 t = -0.5 * (qb + sq)
             else:
                 t = -0.5 * (qb - sq)
-            lo = min(0.0, bac)
-            hi = max(0.0, bac)
             if t != 0.0:
-                r1 = qc / t
-                if lo <= r1 <= hi:
-                    best = r1
+                best = qc / t
             if qa != 0.0:
                 r2 = t / qa
-                if lo <= r2 <= hi and (best is None or abs(r2 - lin) < abs(best - lin)):
+                if best is None or abs(r2 - lin) < abs(best - lin):
                     best = r2
+            if best is not None and abs(best - lin) > abs(bal) + abs(bac):
+                best = None
     if best is None:
         best = lin
     return ec + best

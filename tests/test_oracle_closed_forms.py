@@ -1,0 +1,149 @@
+"""Pins of the closed forms and of the whole oracle step against the paper's exact solutions.
+
+Stefan problem (Sec. 3.1), bubble with a constant mass flux (Sec. 3.3) and the planar
+analogue of the Scriven bubble (Sec. 3.4).  These fix the oracle to something other
+than itself: a dropped term, a wrong sign or a transposed operand anywhere on the
+step shows up as a wrong interface position, radius or vapour-volume balance.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2402_13677_gb300 import workloads as w
+from oracle import step as S
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_printed_values.json")))
+
+
+def test_stefan_beta_reproduces_paper_initial_thickness():
+    g = GOLD["stefan"]
+    dT = g["T_w"] - g["T_sat"]
+    beta = w.stefan_beta(g["cp_v"] * dT / g["h_lg"])
+    alpha_v = g["lambda_v"] / (g["rho_v"] * g["cp_v"])
+    X = w.stefan_position(g["initial_time_s"], beta, alpha_v)
+    # the paper prints 322.5 um; the similarity solution gives 322.25 um
+    assert abs(X - g["initial_thickness_m"]) / g["initial_thickness_m"] < 2e-3
+    # beta solves the transcendental equation
+    assert abs(beta * math.exp(beta ** 2) * math.erf(beta) - g["cp_v"] * dT / (math.sqrt(math.pi) * g["h_lg"])) < 1e-14
+
+
+@pytest.mark.parametrize("case", ["stefan", "sucking", "film_boiling"])
+def test_jakob_numbers(case):
+    g = GOLD[case]
+    dT = g.get("dT", g.get("T_w", 0) - g.get("T_sat", 0))
+    Ja = g["rho_l"] * g["cp_l"] * dT / (g["rho_v"] * g["h_lg"])
+    assert abs(Ja - g["Ja"]) < 0.01
+
+
+def test_film_taylor_wavelength():
+    g = GOLD["film_boiling"]
+    lam0 = 2 * math.pi * math.sqrt(3 * g["sigma"] / ((g["rho_l"] - g["rho_v"]) * g["g"]))
+    assert abs(lam0 - g["lambda0_m"]) < 5e-5
+
+
+def test_stefan_temperature_profile_limits():
+    beta = w.stefan_beta(0.1)
+    t = 0.05
+    X = w.stefan_position(t, beta, 1.0)
+    assert abs(w.stefan_temperature(0.0, t, beta, 1.0, 1.0, 0.0) - 1.0) < 1e-15
+    assert abs(w.stefan_temperature(X, t, beta, 1.0, 1.0, 0.0)) < 1e-14
+
+
+def test_planar_bubble_beta_special_case_and_quadrature():
+    # eps beta^2 = 1 makes I(beta) = exp(-beta^2)/2, hence Ja = 1 exactly
+    for eps in (0.5, 0.8, 0.95):
+        assert abs(w.bubble2d_beta(1.0, eps) - 1.0 / math.sqrt(eps)) < 1e-10
+    # incomplete-gamma form of I(eta) against direct quadrature
+    beta, eps = 3.9083419774742, 0.95
+    a = eps * beta * beta
+    val, _ = integrate.quad(lambda s: s ** (2 * a - 1) * math.exp(-s * s), beta, 60.0, limit=200)
+    logI = float(w._bubble2d_logI(beta, a))
+    assert abs(math.log(val) - logI) < 1e-9
+    Ja = 2 * beta ** 2 * math.exp(beta ** 2) * beta ** (-2 * a) * val
+    assert abs(Ja - 4.0) < 1e-6
+
+
+def test_planar_bubble_temperature_solves_the_pde():
+    """Finite-difference residual of T_t + u T_r = alpha (T_rr + T_r / r) with u = eps R R'/r."""
+    beta, eps, alpha = w.bubble2d_beta(1.0, 0.5), 0.5, 0.5
+    t = 3e-3
+    R = 2 * beta * math.sqrt(alpha * t)
+    Rdot = beta * math.sqrt(alpha / t)
+    T = lambda r, tt: w.bubble2d_temperature(r, tt, beta, eps, alpha, 1.0, 0.0)
+    for r in (1.05 * R, 1.3 * R, 2.0 * R):
+        d, dtt = 1e-5 * R, 1e-7 * t
+        Tt = (T(r, t + dtt) - T(r, t - dtt)) / (2 * dtt)
+        Tr = (T(r + d, t) - T(r - d, t)) / (2 * d)
+        Trr = (T(r + d, t) - 2 * T(r, t) + T(r - d, t)) / d ** 2
+        res = Tt + eps * R * Rdot / r * Tr - alpha * (Trr + Tr / r)
+        assert abs(res) < 1e-4 * abs(alpha * Trr)
+    assert abs(T(R, t)) < 1e-12
+
+
+def _stefan_error(nx):
+    pb = w.stefan(nx, 4, X0=0.1, Lx=1.0, dt=1e-4 * 64 / nx, steps=0)
+    st = S.prepare(pb)
+    for _ in range(int(round(0.01 / pb.dt))):
+        S.step(st)
+    X = st.diag[-1][1] / (pb.ny * pb.h)
+    Xe = w.stefan_position(st.t, pb.meta["beta"], 1.0)
+    return abs(X - Xe) / Xe, st
+
+
+def test_oracle_stefan_converges_to_similarity_solution():
+    e32, _ = _stefan_error(32)
+    e64, st = _stefan_error(64)
+    assert e64 < 1e-4
+    assert e32 < 2e-3
+    assert e64 < e32 / 4
+    # liquid at T_sat, vapour between T_sat and T_w, velocity jump U in the liquid
+    g = st.geom
+    assert np.all(np.abs(st.T_l[g.ccol == 1]) < 1e-12)
+    Tv = st.T_v[g.ccol == 0]
+    assert Tv.min() > 0 and Tv.max() < 1
+    beta = st.pb.meta["beta"]
+    U = beta / math.sqrt(st.t) * (1 - 1 / 10.0)
+    assert abs(st.u_l[g.ccol == 1][:, 0].mean() - U) / U < 0.02
+    assert np.abs(st.u_v[g.ccol == 0]).max() < 0.02 * U
+
+
+def test_oracle_stefan_mass_conservation():
+    _, st = _stefan_error(64)
+    d = np.array(st.diag)
+    Md0 = st.diag[0][3] + st.diag[0][4]  # after the first step, M_d plus that step's outflow
+    Mc = d[:, 3] + np.cumsum(d[:, 4])
+    # paper: max relative conservation error 0.0082 % at its finest grid (Sec. 3.1)
+    assert np.max(np.abs(Mc / Mc[0] - 1.0)) < 2e-3
+
+
+def test_oracle_constant_mdot_bubble_radius():
+    pb = w.const_mdot_bubble(n=48, L=8.0, R0=1.0, mdot=0.1, steps=0)
+    pb.dt = 0.125 * 32 / 48
+    st = S.prepare(pb)
+    V0 = float(np.sum(1 - st.geom.vf)) * pb.h ** 2
+    dv = 0.0
+    for _ in range(36):
+        dv += S.step(st)[2]
+    R = math.sqrt(st.diag[-1][1] / math.pi)
+    Re = 1.0 + 0.1 * (st.t - pb.t0)
+    assert abs(R - Re) / Re < 0.02
+    # the vapour volume grows by the integrated mdot S / rho_v
+    assert abs((st.diag[-1][1] - V0) - dv) / dv < 0.07
+
+
+def test_oracle_planar_bubble_growth():
+    pb = w.bubble(n=64, R0=0.1, rho_ratio=2.0, k_ratio=1.0, St=0.5, mu=0.01, dt=1.6e-4, steps=0)
+    st = S.prepare(pb)
+    beta, a = pb.meta["beta"], pb.meta["alpha_l"]
+    V0 = float(np.sum(1 - st.geom.vf)) * pb.h ** 2
+    dv = 0.0
+    for _ in range(19):
+        dv += S.step(st)[2]
+    R = math.sqrt(st.diag[-1][1] / math.pi)
+    Re = 2 * beta * math.sqrt(a * st.t)
+    assert abs(R - Re) / Re < 0.03
+    assert abs((st.diag[-1][1] - V0) - dv) / dv < 5e-3

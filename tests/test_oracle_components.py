@@ -1,0 +1,342 @@
+"""Component pins of the oracle: each check is fixed by mathematics, not by the oracle itself.
+
+  * reconstruction: straight-line volume fractions against quadrature; circle area
+    converging at second order; normals pointing into vapour; edge/colour parity;
+  * EBIT sweep: a translated straight line and a translated circle stay exact (a circle
+    through three co-circular points is that circle); two half-cell sweeps equal a
+    one-cell shift; merging discs match the analytic union;
+  * bilinear interpolation exact for bilinear fields; biquadratic for quadratics;
+  * WENO3 exact for quadratic fields under uniform velocity;
+  * ghost-fluid matrix symmetric positive definite (dense 8x8), zero residual for a
+    linear profile that vanishes at the interface, dense brute-force solve;
+  * one-sided normal slope exact for quadratics; mass flux of a linear profile;
+  * ghost-velocity jump (u_l - u_v) . n = mdot [1/rho]; projected faces divergence-free;
+    a fluid at rest under gravity stays at rest.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2402_13677_gb300 import workloads as w
+from oracle import energy, flow, geometry, step as S, sweep
+
+
+def _levelset_state(phi, n, L=1.0):
+    h = L / n
+    return w.interface_from_levelset(phi, n, n, h)
+
+
+# ------------------------------------------------------------------ geometry
+def test_straight_line_volume_fraction_exact():
+    n = 16
+    a, b = 0.37, 0.2113
+    phi = lambda x, y: y - (a * x + b)          # liquid above the line
+    vcol, hc, hp, vc, vp = _levelset_state(phi, n)
+    g = geometry.reconstruct(vcol, hp, vp)
+    h = 1.0 / n
+    for j in range(n):
+        for i in range(n):
+            # liquid area of the cell by quadrature (grid units)
+            f = lambda s: min(max((j + 1) - (a * (i + s) * h + b) / h, 0.0), 1.0)
+            exact, _ = integrate.quad(f, 0.0, 1.0, points=[0.5], epsabs=1e-13)
+            assert abs(g.vf[j, i] - exact) < 1e-8, (i, j)
+
+
+def test_circle_area_second_order_and_normals():
+    errs = []
+    for n in (32, 64, 128):
+        R = 0.3
+        phi = lambda x, y: np.hypot(x - 0.5, y - 0.5) - R
+        vcol, hc, hp, vc, vp = _levelset_state(phi, n)
+        g = geometry.reconstruct(vcol, hp, vp)
+        area = np.sum(1.0 - g.vf) / n ** 2
+        errs.append(abs(area - math.pi * R * R) / (math.pi * R * R))
+        # normals point from liquid (outside) into vapour (inside): -r_hat
+        for (j, i), (mx, my), nrm, L in geometry.segment_data(g):
+            rx, ry = mx / n - 0.5, my / n - 0.5
+            r = math.hypot(rx, ry)
+            assert nrm[0] * rx / r + nrm[1] * ry / r < -0.95
+        # f_C matches the analytic phase of the cell centre away from the interface
+        xc = (np.arange(n) + 0.5) / n
+        X, Y = np.meshgrid(xc, xc)
+        dist = np.hypot(X - 0.5, Y - 0.5) - R
+        far = np.abs(dist) > 0.01 / n
+        assert np.all(g.ccol[far] == (dist[far] > 0))
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0
+
+
+def test_every_cell_has_zero_two_or_four_cut_edges_and_band_normal():
+    phi = lambda x, y: np.minimum(np.hypot(x - 0.3, y - 0.4) - 0.15, np.hypot(x - 0.62, y - 0.55) - 0.12)
+    vcol, hc, hp, vc, vp = _levelset_state(phi, 40)
+    g = geometry.reconstruct(vcol, hp, vp)
+    ncut = hc[:-1, :].astype(int) + hc[1:, :] + vc[:, :-1] + vc[:, 1:]
+    assert set(np.unique(ncut)) <= {0, 2, 4}
+    assert np.all((ncut > 0) == (g.nseg > 0))
+    nrm = np.hypot(g.nb[..., 0], g.nb[..., 1])
+    assert np.allclose(nrm[g.band & (nrm > 0)], 1.0)
+
+
+def test_saddle_cell_picks_shorter_pairing():
+    # corners alternate 1,0,1,0; markers near corner 1 and 3 -> cutting those corners is shorter
+    vcol = np.array([[1, 0], [0, 1]], np.uint8)   # [j][i]: BL=1, BR=0, TL=0, TR=1
+    hp = np.array([[0.9], [0.1]])                  # bottom marker near BR, top marker near TL
+    vp = np.array([[0.1, 0.9]])                    # left near BL? left(i=0)=0.1, right(i=1)=0.9
+    g = geometry.reconstruct(vcol, hp, vp)
+    assert g.nseg[0, 0] == 2
+    # BR is vapour, isolated by a short cut between bottom(0.9) and right(0.1)? right is 0.9 here:
+    # pairing A isolates BR (bottom 0.9 -> right 0.9) and TL (top 0.1 -> left 0.1)
+    LA = math.hypot(0.1, 0.9) * 2
+    LB = math.hypot(0.9, 0.1) + math.hypot(0.1, 0.9)
+    assert (g.ccol[0, 0] == 1) == (LA <= LB)
+    assert 0.0 < g.vf[0, 0] < 1.0
+
+
+# ------------------------------------------------------------------ sweep
+def _translate(phi, n, ux, uy, dt, steps, L=1.0):
+    h = L / n
+    vcol, hc, hp, vc, vp = w.interface_from_levelset(phi, n, n, h)
+    uG = np.zeros((n, n, 2))
+    uG[..., 0], uG[..., 1] = ux, uy
+    bc = (w.OUTFLOW,) * 4
+    for k in range(steps):
+        order = (0, 1) if k % 2 == 0 else (1, 0)
+        for axis in order:
+            g = geometry.reconstruct(vcol, hp, vp)
+            vcol, hp, vp = sweep.sweep(vcol, hp, vp, g, uG, dt / h, axis, bc)
+    return vcol, hp, vp
+
+
+def _marker_points(vcol, hp, vp):
+    pts = []
+    for j, i in zip(*np.nonzero(vcol[:, :-1] != vcol[:, 1:])):
+        pts.append((i + hp[j, i], float(j)))
+    for j, i in zip(*np.nonzero(vcol[:-1, :] != vcol[1:, :])):
+        pts.append((float(i), j + vp[j, i]))
+    return np.array(pts)
+
+
+def test_translated_line_stays_exact():
+    n = 32
+    a, b = 0.41, 0.3
+    phi = lambda x, y: y - (a * x + b)
+    vcol, hp, vp = _translate(phi, n, 0.7, -0.35, 0.013, 5)
+    T = 5 * 0.013
+    pts = _marker_points(vcol, hp, vp)
+    # markers near the domain ends feel the boundary lines (held boundary markers)
+    inner = (pts[:, 0] > 7) & (pts[:, 0] < n - 7)
+    pts = pts[inner] / n
+    res = pts[:, 1] - (a * (pts[:, 0] - 0.7 * T) + b - 0.35 * T)
+    assert len(pts) > 15
+    assert np.max(np.abs(res)) < 1e-10
+    # colours equal the analytic half-plane at every vertex away from the boundary
+    xs = np.arange(n + 1) / n
+    X, Y = np.meshgrid(xs, xs)
+    sl = (slice(None), slice(8, -8))
+    assert np.all(vcol[sl] == (Y - (a * (X - 0.7 * T) + b - 0.35 * T) > 0)[sl])
+
+
+def test_translated_circle_stays_on_circle():
+    n = 48
+    R, cx, cy = 0.23, 0.47, 0.51
+    phi = lambda x, y: np.hypot(x - cx, y - cy) - R
+    ux, uy, dt, steps = 0.5, 0.3, 0.011, 6
+    vcol, hp, vp = _translate(phi, n, ux, uy, dt, steps)
+    T = dt * steps
+    pts = _marker_points(vcol, hp, vp) / n
+    r = np.hypot(pts[:, 0] - cx - ux * T, pts[:, 1] - cy - uy * T)
+    assert np.max(np.abs(r - R)) < 1e-9
+
+
+def test_two_half_cell_sweeps_equal_one_cell_shift():
+    n = 32
+    phi = lambda x, y: 0.21 - np.hypot(x - 0.4, y - 0.45)   # liquid disc
+    h = 1.0 / n
+    v0, _, hp0, _, vp0 = w.interface_from_levelset(phi, n, n, h)
+    vcol, hp, vp = _translate(phi, n, 1.0, 0.0, 0.5 * h, 2)
+    assert np.array_equal(vcol[:, 1:], v0[:, :-1])
+    hcut = v0[:, :-1] != v0[:, 1:]
+    assert np.allclose(hp[:, 1:][hcut[:, :-1]], hp0[:, :-1][hcut[:, :-1]], atol=1e-12)
+    vcut = v0[:-1, :] != v0[1:, :]
+    assert np.allclose(vp[:, 1:][vcut[:, :-1]], vp0[:, :-1][vcut[:, :-1]], atol=1e-9)
+
+
+def test_merging_discs_topology_matches_analytic_union():
+    """A linear compressive flow u = -c (x - xc) pushes two vapour discs into each other.
+
+    Explicit Euler contracts x - xc by exactly (1 - c dt/h) per sweep, so the analytic
+    region is the pre-image of the two discs under that map."""
+    n = 40
+    R, c1, c2, xc = 5.6, 13.7, 27.3, 20.5                 # grid units
+    phi = lambda x, y: np.minimum(np.hypot(x - c1, y - 20.0), np.hypot(x - c2, y - 20.0)) - R
+    vcol, hc, hp, vc, vp = w.interface_from_levelset(phi, n, n, 1.0)
+    uG = np.zeros((n, n, 2))
+    uG[..., 0] = -0.1 * ((np.arange(n) + 0.5) - xc)[None, :]
+    bc = (w.OUTFLOW,) * 4
+    steps = 12
+    for k in range(steps):
+        for axis in ((0, 1) if k % 2 == 0 else (1, 0)):
+            g = geometry.reconstruct(vcol, hp, vp)
+            vcol, hp, vp = sweep.sweep(vcol, hp, vp, g, uG, 1.0, axis, bc)
+    X, Y = np.meshgrid(np.arange(n + 1.0), np.arange(n + 1.0))
+    Xp = xc + (X - xc) / 0.9 ** steps
+    d = np.minimum(np.hypot(Xp - c1, Y - 20.0), np.hypot(Xp - c2, Y - 20.0)) - R
+    d = d * 0.9 ** steps          # roughly a distance in the deformed frame
+    far = np.abs(d) > 0.5
+    assert np.all(vcol[far] == (d[far] > 0))
+    from scipy import ndimage
+    before = ndimage.label(w.interface_from_levelset(phi, n, n, 1.0)[0] == 0)[1]
+    after = ndimage.label(vcol == 0)[1]
+    assert before == 2 and after == 1
+
+
+def test_bilinear_exact_for_bilinear_fields():
+    n = 8
+    F = np.zeros((n, n, 2))
+    xc = np.arange(n) + 0.5
+    X, Y = np.meshgrid(xc, xc)
+    F[..., 0] = 0.3 + 0.7 * X - 1.1 * Y + 0.25 * X * Y
+    bc = (w.OUTFLOW,) * 4
+    for (x, y) in ((2.3, 3.0), (4.0, 5.77), (1.5, 1.5), (6.2, 4.9)):
+        v = sweep.interp_bilinear(F, 0, x, y, bc)
+        assert abs(v - (0.3 + 0.7 * x - 1.1 * y + 0.25 * x * y)) < 1e-12
+
+
+# ------------------------------------------------------------------ energy
+def test_weno3_exact_for_quadratics():
+    n = 12
+    xc = np.arange(n) + 0.5
+    X, Y = np.meshgrid(xc, xc)
+    T = 0.2 + 0.3 * X - 0.1 * Y + 0.05 * X * X - 0.02 * Y * Y + 0.01 * X * Y
+    u = np.zeros((n, n, 2))
+    u[..., 0], u[..., 1] = 0.8, -0.6
+    h, dt = 1.0, 0.1
+    Ts = energy.advect(T, u, [("even", 0.0)] * 4, dt, h)
+    dTdx = 0.3 + 0.1 * X + 0.01 * Y
+    dTdy = -0.1 - 0.04 * Y + 0.01 * X
+    exact = T - dt * (0.8 * dTdx - 0.6 * dTdy)
+    inner = (slice(2, -2), slice(2, -2))
+    assert np.max(np.abs(Ts[inner] - exact[inner])) < 1e-12
+
+
+def test_extension_of_constant_and_along_normal():
+    n = 16
+    phi = lambda x, y: x - 0.52   # liquid right, vapour left, n = (-1, 0)
+    vcol, hc, hp, vc, vp = _levelset_state(phi, n)
+    g = geometry.reconstruct(vcol, hp, vp)
+    T = np.where(g.ccol == 1, 3.0, -7.0)
+    Tl, Tv = energy.extend_temperatures(T, T.copy(), g, 5)
+    assert np.all(Tl[g.band] == 3.0)
+    assert np.all(Tv[g.band] == -7.0)
+    # a profile varying along x is extended with the value of the last phase cell on its row
+    F = np.tile(np.arange(n, dtype=float), (n, 1))
+    Fl, _ = energy.extend_temperatures(F, F.copy(), g, 5)
+    first_liq = int(np.argmax(g.ccol[0] == 1))
+    gb = g.band & (g.ccol == 0)
+    assert np.all(Fl[gb] == first_liq)
+
+
+def _energy_problem(n=8, X0=0.43, dt=1e10):
+    pb = w.stefan(n, n, X0=X0, Lx=1.0, dt=dt, steps=0)
+    pb.T_bc = (None, None, None, None)
+    vcol, hc, hp, vc, vp = _levelset_state(lambda x, y: x - X0 + 0.07 * (y - 0.5), n)
+    g = geometry.reconstruct(vcol, hp, vp)
+    return pb, g
+
+
+def test_ghost_fluid_matrix_spd_and_dense_solve():
+    pb, g = _energy_problem(dt=1e-2)
+    rng = np.random.default_rng(1)
+    Ts = rng.normal(size=(8, 8))
+    A, b = energy.assemble_energy(g, Ts, Ts, pb)
+    D = A.toarray()
+    assert np.allclose(D, D.T, atol=0)
+    assert np.linalg.eigvalsh(D).min() > 0
+    T_l, T_v = energy.solve_energy(g, Ts, Ts, pb)
+    x = np.where(g.ccol == 1, T_l, T_v).ravel()
+    xd = np.linalg.solve(D, b)
+    assert np.max(np.abs(x - xd)) < 1e-12 * np.max(np.abs(xd))
+
+
+def test_ghost_fluid_zero_residual_for_linear_profile():
+    """A 1D linear T with T(x_Gamma) = T_sat is a discrete steady solution (Txx-ghost equation)."""
+    n = 16
+    X0 = 0.431
+    pb = w.stefan(n, 4, X0=X0, Lx=1.0, dt=1e30, steps=0)
+    pb.T_bc = (None, None, None, None)
+    vcol, hc, hp, vc, vp = w.interface_from_levelset(lambda x, y: x - X0, n, 4, 1.0 / n)
+    g = geometry.reconstruct(vcol, hp, vp)
+    xc = (np.arange(n) + 0.5) / n
+    Tlin = np.tile(2.5 * (xc - X0), (4, 1))
+    A, b = energy.assemble_energy(g, Tlin, Tlin, pb)
+    r = A @ Tlin.ravel() - b
+    # only the cells touching the domain ends (zero-gradient walls) see a non-zero residual
+    r = r.reshape(4, n)
+    assert np.max(np.abs(r[:, 1:-1])) < 1e-12
+
+
+def test_normal_slope_and_biquadratic_exact_for_quadratics():
+    h = 0.1
+    q = lambda s: 2.0 + 0.7 * s - 3.0 * s * s
+    a = energy.normal_slope(q(energy.D1 * h), q(energy.D2 * h), q(0.0), h)
+    assert abs(a - 0.7) < 1e-12
+    n = 9
+    xc = np.arange(n) + 0.5
+    X, Y = np.meshgrid(xc, xc)
+    F = 1 + 0.3 * X - 0.2 * Y + 0.04 * X * X + 0.03 * X * Y - 0.05 * Y * Y
+    for (x, y) in ((3.3, 4.8), (0.2, 8.7), (5.0, 5.0)):
+        v = energy.interp_biquadratic(F, x, y)
+        assert abs(v - (1 + 0.3 * x - 0.2 * y + 0.04 * x * x + 0.03 * x * y - 0.05 * y * y)) < 1e-11
+
+
+def test_mass_flux_of_linear_vapour_profile():
+    n = 32
+    X0 = 0.5 + 0.3 / n
+    pb = w.stefan(n, n, X0=X0, Lx=1.0, steps=0)
+    vcol, hc, hp, vc, vp = _levelset_state(lambda x, y: x - X0, n)
+    g = geometry.reconstruct(vcol, hp, vp)
+    xc = (np.arange(n) + 0.5) / n
+    T_v = np.tile(1.7 * (X0 - xc), (n, 1))     # grows into the vapour (left)
+    T_l = np.zeros((n, n))
+    m = energy.mass_flux(g, T_l, T_v, pb)
+    cut = g.nseg > 0
+    assert np.allclose(m[cut], pb.lam_v * 1.7 / pb.h_lg, rtol=1e-10)
+
+
+# ------------------------------------------------------------------ flow
+def test_ghost_velocity_jump_and_divergence_free_projection():
+    pb = w.bubble(n=32, R0=0.2, rho_ratio=5.0, k_ratio=1.0, St=0.5, dt=2e-4, steps=0)
+    st = S.prepare(pb)
+    g = st.geom
+    J = 1.0 / pb.rho_l - 1.0 / pb.rho_v
+    jump = (st.u_l - st.u_v)[..., 0] * g.nb[..., 0] + (st.u_l - st.u_v)[..., 1] * g.nb[..., 1]
+    assert np.allclose(jump[g.band], (st.mdot * J)[g.band], atol=1e-12)
+    S.step(st)
+    for name in ("l", "v"):
+        fx, fy = getattr(st, "ufx_" + name), getattr(st, "ufy_" + name)
+        div = (fx[:, 1:] - fx[:, :-1]) + (fy[1:, :] - fy[:-1, :])
+        own = st.geom.ccol == (1 if name == "l" else 0)
+        # cells whose phase did not change during the step are exactly projected
+        assert np.max(np.abs(div[own])) < 1e-9 * max(1.0, np.abs(fx).max())
+
+
+def test_fluid_at_rest_under_gravity_stays_at_rest():
+    """Discrete hydrostatic balance: a_f = g - (p_j - p_{j-1}) / (h rho_f) = 0 on every face."""
+    pb = w.film(32, 32, Lx=1.0, mean=0.5, amp=0.0, modes=1, seed=0, steps=0, dt=1e-3)
+    pb.energy = False
+    pb.mdot_fixed = 0.0
+    g0 = geometry.reconstruct(pb.vcol, pb.hx_pos, pb.vy_pos)
+    rfx, rfy = flow.face_rho(pb, g0.vf)
+    p = np.zeros((pb.ny, pb.nx))
+    p[-1, :] = -pb.gy * pb.h * rfy[-1, :] / 2.0         # outflow top face at p = 0
+    for j in range(pb.ny - 1, 0, -1):
+        p[j - 1, :] = p[j, :] - pb.h * rfy[j, :] * pb.gy
+    pb.p = p
+    st = S.prepare(pb)
+    for _ in range(3):
+        S.step(st)
+    assert np.max(np.abs(st.u_l)) < 1e-10 and np.max(np.abs(st.u_v)) < 1e-10
+    dp = np.diff(st.p, axis=0).mean(axis=1) / pb.h
+    assert abs(dp[5] - pb.rho_v * pb.gy) < 1e-8 * pb.rho_l
+    assert abs(dp[25] - pb.rho_l * pb.gy) < 1e-8 * pb.rho_l

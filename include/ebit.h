@@ -1,0 +1,193 @@
+/*
+ * ebit.h -- C ABI of the GB300 (sm_103a) EBIT phase-change time step.
+ *
+ * Method: Long, Pan & Zaleski, "An Edge-based Interface Tracking (EBIT) Method for
+ * Multiphase Flows with Phase Change", arXiv 2402.13677.  One call of ebit_step()
+ * performs the five-step iteration of Sec. 2.5 on a uniform 2D Cartesian grid:
+ *   1. energy advection (energy-advection equation, Sec. 2.4),
+ *   2. EBIT interface advection (marker-motion equations, Sec. 2.1, Fig. 1) with the
+ *      interfacial velocity of the jump condition (interfacial-velocity equation,
+ *      Sec. 2.3, Fig. 2) and Color-Vertex reconnection (Sec. 2.1),
+ *   3. energy diffusion with T = T_sat imposed sharply through ghost-fluid
+ *      coefficients (ghost-temperature and Txx-ghost equations, Sec. 2.4),
+ *   4. interface heat and mass flux (mass-flux and normal-gradient equations) and the
+ *      ghost velocities (ghost-velocity equation, Sec. 2.3),
+ *   5. momentum predictor and ghost-fluid projection (discretization equations 1-5
+ *      and the ghost-fluid Poisson equation, Sec. 2.3).
+ *
+ * Conventions
+ *   - Grid units: cell (i, j) covers [x0 + i h, x0 + (i+1) h] x [y0 + j h, ...].  All
+ *     arrays are row-major with x fastest:
+ *       cell fields        ny     x nx        (double, or double2 = {x, y} for vectors)
+ *       x-faces            ny     x (nx + 1)  (normal velocity at x = x0 + i h)
+ *       y-faces            (ny+1) x nx
+ *       vertex colours     (ny+1) x (nx + 1)  (uint8: 1 liquid, 0 vapour)
+ *       horizontal edges   (ny+1) x nx        (marker fraction from the left vertex)
+ *       vertical edges     ny     x (nx + 1)  (marker fraction from the lower vertex)
+ *     An edge carries a marker (is "cut") iff its two vertex colours differ (one marker
+ *     per edge, Sec. 2.1); marker fractions of cut edges lie in [1e-9, 1 - 1e-9].
+ *   - Pointers: "host" pointers are plain CPU memory; "device" pointers are CUDA global
+ *     memory of the device that was current at ebit_init().  The caller owns every
+ *     pointer it passes; the library keeps none of them after the call returns.
+ *   - Streams: all device work of a context is ordered on the cudaStream_t given to
+ *     ebit_init() (passed as void*; NULL = legacy default stream).  Calls that return
+ *     data to the host (ebit_get_field with on_device = 0, ebit_get_diagnostics)
+ *     synchronise that stream before returning; ebit_step() does not synchronise
+ *     except to read solver convergence words every few iterations.
+ *   - Errors: every call returns an ebit_status; on failure a message is kept for
+ *     ebit_last_error().  EBIT_ENOCONV means a linear solve hit max_iter: the step is
+ *     completed with its last iterate and the counter is reported by
+ *     ebit_get_solver_stats().  EBIT_ECUDA means a CUDA call failed; the context should
+ *     then be destroyed.
+ *   - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef EBIT_H
+#define EBIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ebit_ctx ebit_ctx;
+
+typedef enum {
+    EBIT_OK = 0,
+    EBIT_EINVAL = -1,     /* bad argument or inconsistent input                        */
+    EBIT_ENOMEM = -2,     /* device allocation failed                                  */
+    EBIT_ENOCONV = -3,    /* a linear solve did not reach its tolerance in max_iter     */
+    EBIT_ETOPO = -4,      /* marker set inconsistent with the vertex colours            */
+    EBIT_ECUDA = -5,      /* CUDA runtime error                                        */
+    EBIT_ECFL = -6        /* a marker moved one cell or more in one sweep (CFL >= 1)   */
+} ebit_status;
+
+/* Boundary kinds (per side: 0 left, 1 right, 2 bottom, 3 top). */
+enum { EBIT_BC_WALL = 0,      /* no-slip wall: u = 0, zero normal pressure gradient     */
+       EBIT_BC_OUTFLOW = 1,   /* zero normal gradient of u and T, p = 0 on the face     */
+       EBIT_BC_SYMMETRY = 2   /* normal u = 0, tangential u and T free                  */ };
+
+/* Precision of the linear solves. */
+enum { EBIT_FP64 = 0,         /* MG-preconditioned CG entirely in FP64                   */
+       EBIT_MIXED = 1         /* FP32 MG-PCG inside an FP64 iterative-refinement loop;
+                                 ghost-fluid coefficients, jump-condition velocities and
+                                 the outer residuals stay FP64                           */ };
+
+typedef struct {
+    int nx, ny;               /* cells, each >= 4                                         */
+    double x0, y0, h;         /* origin and cell size (square cells)                      */
+    int bc[4];                /* EBIT_BC_* per side                                       */
+    int T_fixed[4];           /* 1: wall temperature T_wall[s] imposed (Dirichlet)        */
+    double T_wall[4];
+    double dt;                /* time step                                                */
+    int precision;            /* EBIT_FP64 or EBIT_MIXED                                   */
+    double rtol;              /* relative residual ||b - A x||_2 / ||b||_2 of every solve */
+    int max_iter;             /* CG iterations (FP64) or outer refinements x inner (MIXED) */
+    int extend_iters;         /* Jacobi sweeps of the narrow-band extension (paper: iterative) */
+    double theta_min;         /* lower clamp of the ghost-fluid link fraction theta        */
+    int sweep_order;          /* 0: x then y every step; 1: alternate x-y / y-x             */
+    int energy;               /* 1: solve the energy equation; 0: impose mdot_fixed (Sec. 3.3) */
+    double mdot_fixed;
+} ebit_config;
+
+typedef struct { double rho, mu, lambda, cp; } ebit_phase_props;
+
+/* Optional device allocator: returns a device pointer of at least `bytes` bytes (aligned
+ * to 256 B) or NULL; the library frees it through `free_fn` in ebit_destroy().  With
+ * alloc == NULL the library uses cudaMalloc/cudaFree. */
+typedef struct {
+    void* (*alloc_fn)(size_t bytes, void* user);
+    void (*free_fn)(void* ptr, void* user);
+    void* user;
+} ebit_allocator;
+
+/* Field identifiers for ebit_set_field / ebit_get_field. */
+enum {
+    EBIT_F_T_L = 0, EBIT_F_T_V = 1,         /* cell temperature of each phase (ghost band included) */
+    EBIT_F_U_L = 2, EBIT_F_U_V = 3,         /* cell velocity, double2                                */
+    EBIT_F_UFX_L = 4, EBIT_F_UFX_V = 5,     /* x-face normal velocity                                */
+    EBIT_F_UFY_L = 6, EBIT_F_UFY_V = 7,     /* y-face normal velocity                                */
+    EBIT_F_P = 8,                           /* pressure                                              */
+    EBIT_F_GC = 9,                          /* cell face-acceleration average, double2               */
+    EBIT_F_MDOT = 10,                       /* mass flux on the narrow band                          */
+    EBIT_F_VF = 11,                         /* liquid volume fraction (read only)                    */
+    EBIT_F_CCOL = 12,                       /* uint8 centre colour f_C (read only)                   */
+    EBIT_F_BAND = 13,                       /* uint8 narrow-band flag (read only)                    */
+    EBIT_F_NB = 14,                         /* band normal, double2, liquid -> vapour (read only)    */
+    EBIT_F_VCOL = 15,                       /* uint8 vertex colours                                  */
+    EBIT_F_HX_POS = 16, EBIT_F_VY_POS = 17, /* marker fractions of horizontal / vertical edges       */
+    EBIT_F_TSTAR_L = 18, EBIT_F_TSTAR_V = 19, /* advected temperature of the current step            */
+    EBIT_F_CSEG = 20,                       /* uint16 per cell: nseg | P0<<2 | Q0<<4 | P1<<6 | Q1<<8  */
+    EBIT_F_UG = 21,                         /* cell interfacial velocity u_Gamma, double2            */
+    EBIT_F_COUNT = 22
+};
+
+/* Stages for ebit_run_stage (one call of ebit_step runs STAGE_ADVECT_T .. STAGE_DIAGNOSTICS). */
+enum {
+    EBIT_STAGE_PREPARE = 0,          /* reconstruct, extend T, mdot, ghost velocities, gc      */
+    EBIT_STAGE_RECONSTRUCT = 1,      /* Color-Vertex reconstruction + band (S0)                */
+    EBIT_STAGE_ADVECT_T = 2,         /* S1: T* = WENO3 advection of T_l, T_v                    */
+    EBIT_STAGE_EXTEND_TSTAR = 3,     /* S6: extend T* into the band of the current interface   */
+    EBIT_STAGE_ADVANCE_INTERFACE = 4,/* S2-S5: u_Gamma, two sweeps, reconnection                */
+    EBIT_STAGE_SOLVE_ENERGY = 5,     /* S7-S8: ghost-fluid coefficients and implicit diffusion  */
+    EBIT_STAGE_EXTEND_T = 6,         /* ghost band of T after the diffusion solve               */
+    EBIT_STAGE_MASS_FLUX = 7,        /* S9: mdot on cut cells, extended over the band           */
+    EBIT_STAGE_GHOST_VELOCITY = 8,   /* S10                                                    */
+    EBIT_STAGE_MOMENTUM = 9,         /* S11 + S12: predictor and projection                    */
+    EBIT_STAGE_DIAGNOSTICS = 10,     /* S13, also advances t and the step counter               */
+    EBIT_STAGE_COUNT = 11
+};
+
+/* Create a context for `batch` independent instances (cfgs[0..batch-1]); all instance
+ * data is allocated here, once.  stream: cudaStream_t or NULL. */
+ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream,
+                      const ebit_allocator* alloc, ebit_ctx** out);
+
+/* Material properties of instance `inst` (Sec. 2.2): liquid and vapour rho, mu, lambda,
+ * cp; saturation temperature, latent heat h_lg, surface tension (must be 0: the CSF term
+ * is not part of this step), gravity. */
+ebit_status ebit_set_phase_props(ebit_ctx* ctx, int inst, const ebit_phase_props* liq,
+                                 const ebit_phase_props* vap, double T_sat, double h_lg,
+                                 double sigma, double gx, double gy);
+
+/* Interface of instance `inst`: vertex colours and marker fractions (layouts above).
+ * Cut flags are implied by the colours; fractions of uncut edges are ignored. */
+ebit_status ebit_set_interface(ebit_ctx* ctx, int inst, const uint8_t* vcol,
+                               const double* hx_pos, const double* vy_pos, int on_device);
+
+/* Copy one field in (set) or out (get); on_device selects device or host pointers. */
+ebit_status ebit_set_field(ebit_ctx* ctx, int inst, int field, const void* src, int on_device);
+ebit_status ebit_get_field(ebit_ctx* ctx, int inst, int field, void* dst, int on_device);
+
+/* Number of elements and element size of a field of instance `inst`. */
+ebit_status ebit_field_shape(const ebit_ctx* ctx, int inst, int field, size_t* count, size_t* elem_bytes);
+
+/* Set the time of instance `inst` (its step counter is reset to 0). */
+ebit_status ebit_set_time(ebit_ctx* ctx, int inst, double t);
+
+/* Run one stage on every instance (parity testing and profiling). */
+ebit_status ebit_run_stage(ebit_ctx* ctx, int stage);
+
+/* Advance every instance by nsteps time steps (ebit_run_stage(PREPARE) must have run). */
+ebit_status ebit_step(ebit_ctx* ctx, int nsteps);
+
+/* Diagnostics of the last step of instance `inst` (Sec. 3): up to n doubles of
+ * { t, vapour volume, volume expected from sum mdot S dt / rho_v in the step, M_d,
+ *   outlet mass in the step, cut cells, solver iterations (energy, viscous, Poisson),
+ *   final relative residuals (energy, viscous, Poisson) }. Synchronises. */
+ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n);
+
+/* Kernel launches issued since the context was created (all instances). */
+uint64_t ebit_launch_count(const ebit_ctx* ctx);
+
+const char* ebit_last_error(const ebit_ctx* ctx);
+void ebit_destroy(ebit_ctx* ctx);
+
+/* Library version string. */
+const char* ebit_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBIT_H */

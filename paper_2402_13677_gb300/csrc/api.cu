@@ -1,0 +1,590 @@
+// C ABI of the EBIT phase-change step: context, memory, stage orchestration.
+// The time iteration follows Sec. 2.5 of arXiv 2402.13677 (see include/ebit.h).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/ebit.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "solver.h"
+
+using namespace ebit;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+struct Instance {
+    ebit_config cfg;
+    Grid g;
+    Phys p;
+    bool props_set = false;
+    // interface
+    uint8_t *vcol, *vcol_n;
+    double *hpos, *hpos_n, *vpos, *vpos_n, *hdisp, *vdisp;
+    uint16_t* cseg;
+    uint8_t* flags;
+    double* vf;
+    double2 *nb, *uG;
+    // fields
+    double *T_l, *T_v, *Ts_l, *Ts_v, *P, *mdot;
+    double2 *u_l, *u_v, *us_l, *us_v, *gc;
+    double *ufx_l, *ufx_v, *ufy_l, *ufy_v;
+    // linear systems
+    double *op_cd, *op_dd, *op_wx, *op_wy, *op_b, *op_x;
+    double *vb[4], *vx[4];
+    // band compaction + extension values
+    int *band_list, *band_count, *band_idx;
+    double *ext[4];
+    // diagnostics and status
+    double *diag_partial, *diag_out, *clock;
+    unsigned* diag_ticket;
+    int* status;
+    Solver solver;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    double t0 = 0.0;
+    long long nstep = 0;
+    double stats[6] = {0, 0, 0, 0, 0, 0};   // iterations and residuals: energy, viscous, poisson
+    bool noconv = false;
+};
+
+}  // namespace
+
+struct ebit_ctx {
+    std::vector<Instance> inst;
+    cudaStream_t stream = nullptr;
+    ebit_allocator alloc{};
+    bool has_alloc = false;
+    int* host_flags = nullptr;
+    std::string err;
+    uint64_t launch0 = 0;
+};
+
+static ebit_status fail(ebit_ctx* ctx, ebit_status s, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+static ebit_status cuda_check(ebit_ctx* ctx, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return EBIT_OK;
+}
+
+static size_t field_count(const Grid& g, int f, size_t* elem) {
+    size_t N = (size_t)g.nx * g.ny;
+    size_t nfx = (size_t)g.ny * (g.nx + 1), nfy = (size_t)(g.ny + 1) * g.nx;
+    switch (f) {
+        case EBIT_F_T_L: case EBIT_F_T_V: case EBIT_F_P: case EBIT_F_MDOT: case EBIT_F_VF:
+        case EBIT_F_TSTAR_L: case EBIT_F_TSTAR_V:
+            *elem = 8; return N;
+        case EBIT_F_U_L: case EBIT_F_U_V: case EBIT_F_GC: case EBIT_F_NB: case EBIT_F_UG:
+            *elem = 16; return N;
+        case EBIT_F_UFX_L: case EBIT_F_UFX_V: case EBIT_F_VY_POS:
+            *elem = 8; return nfx;
+        case EBIT_F_UFY_L: case EBIT_F_UFY_V: case EBIT_F_HX_POS:
+            *elem = 8; return nfy;
+        case EBIT_F_CCOL: case EBIT_F_BAND:
+            *elem = 1; return N;
+        case EBIT_F_VCOL:
+            *elem = 1; return (size_t)(g.nx + 1) * (g.ny + 1);
+        case EBIT_F_CSEG:
+            *elem = 2; return N;
+        default:
+            *elem = 0; return 0;
+    }
+}
+
+static void* field_ptr(Instance& I, int f) {
+    switch (f) {
+        case EBIT_F_T_L: return I.T_l;
+        case EBIT_F_T_V: return I.T_v;
+        case EBIT_F_U_L: return I.u_l;
+        case EBIT_F_U_V: return I.u_v;
+        case EBIT_F_UFX_L: return I.ufx_l;
+        case EBIT_F_UFX_V: return I.ufx_v;
+        case EBIT_F_UFY_L: return I.ufy_l;
+        case EBIT_F_UFY_V: return I.ufy_v;
+        case EBIT_F_P: return I.P;
+        case EBIT_F_GC: return I.gc;
+        case EBIT_F_MDOT: return I.mdot;
+        case EBIT_F_VF: return I.vf;
+        case EBIT_F_NB: return I.nb;
+        case EBIT_F_VCOL: return I.vcol;
+        case EBIT_F_HX_POS: return I.hpos;
+        case EBIT_F_VY_POS: return I.vpos;
+        case EBIT_F_TSTAR_L: return I.Ts_l;
+        case EBIT_F_TSTAR_V: return I.Ts_v;
+        case EBIT_F_CSEG: return I.cseg;
+        case EBIT_F_UG: return I.uG;
+        default: return nullptr;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// memory layout of one instance (single arena, 256-byte aligned pieces)
+// ---------------------------------------------------------------------------------------
+template <class F>
+static size_t layout(Instance& I, char* base, F&& assign) {
+    const Grid& g = I.g;
+    size_t N = (size_t)g.nx * g.ny;
+    size_t nv = (size_t)(g.nx + 1) * (g.ny + 1);
+    size_t nh = (size_t)(g.ny + 1) * g.nx, nve = (size_t)g.ny * (g.nx + 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* r = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    assign(I, take, N, nv, nh, nve);
+    char* sb = take(Solver::bytes(g.nx, g.ny));
+    if (base) I.solver.bind(sb, g.nx, g.ny);
+    return off;
+}
+
+static void assign_ptrs(Instance& I, const std::function<char*(size_t)>& take, size_t N, size_t nv, size_t nh,
+                        size_t nve) {
+    I.vcol = (uint8_t*)take(nv);
+    I.vcol_n = (uint8_t*)take(nv);
+    I.hpos = (double*)take(nh * 8);
+    I.hpos_n = (double*)take(nh * 8);
+    I.vpos = (double*)take(nve * 8);
+    I.vpos_n = (double*)take(nve * 8);
+    I.hdisp = (double*)take(nh * 8);
+    I.vdisp = (double*)take(nve * 8);
+    I.cseg = (uint16_t*)take(N * 2);
+    I.flags = (uint8_t*)take(N);
+    I.vf = (double*)take(N * 8);
+    I.nb = (double2*)take(N * 16);
+    I.uG = (double2*)take(N * 16);
+    I.T_l = (double*)take(N * 8);
+    I.T_v = (double*)take(N * 8);
+    I.Ts_l = (double*)take(N * 8);
+    I.Ts_v = (double*)take(N * 8);
+    I.P = (double*)take(N * 8);
+    I.mdot = (double*)take(N * 8);
+    I.u_l = (double2*)take(N * 16);
+    I.u_v = (double2*)take(N * 16);
+    I.us_l = (double2*)take(N * 16);
+    I.us_v = (double2*)take(N * 16);
+    I.gc = (double2*)take(N * 16);
+    I.ufx_l = (double*)take(nve * 8);
+    I.ufx_v = (double*)take(nve * 8);
+    I.ufy_l = (double*)take(nh * 8);
+    I.ufy_v = (double*)take(nh * 8);
+    I.op_cd = (double*)take(N * 8);
+    I.op_dd = (double*)take(N * 8);
+    I.op_wx = (double*)take(nve * 8);
+    I.op_wy = (double*)take(nh * 8);
+    I.op_b = (double*)take(N * 8);
+    I.op_x = (double*)take(N * 8);
+    for (int k = 0; k < 4; ++k) { I.vb[k] = (double*)take(N * 8); I.vx[k] = (double*)take(N * 8); }
+    I.band_list = (int*)take(N * 4);
+    I.band_count = (int*)take(256);
+    I.band_idx = (int*)take(N * 4);
+    for (int k = 0; k < 4; ++k) I.ext[k] = (double*)take(N * 8);
+    I.diag_partial = (double*)take(8 * 8 * 1024);
+    I.diag_out = (double*)take(64 * 8);
+    I.clock = (double*)take(256);
+    I.diag_ticket = (unsigned*)take(256);
+    I.status = (int*)take(256);
+}
+
+// ---------------------------------------------------------------------------------------
+// stages
+// ---------------------------------------------------------------------------------------
+static void count(int n) { g_launches += (uint64_t)n; }
+
+static void reconstruct_full(Instance& I, cudaStream_t st) {
+    launch_reconstruct(I.g, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, I.vf, st);
+    launch_band(I.g, I.cseg, I.hpos, I.vpos, I.flags, I.nb, st);
+    launch_compact(I.flags, I.g.nx * I.g.ny, F_BAND, I.band_list, I.band_count, I.band_idx, st);
+    count(3);   // + memset
+}
+
+static void extend_T(Instance& I, double* Tl, double* Tv, cudaStream_t st) {
+    int it = I.p.extend_iters;
+    launch_extend(I.g, 0, it, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tl, I.ext[0], I.ext[1], st);
+    launch_extend(I.g, 1, it, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tv, I.ext[2], I.ext[3], st);
+    count(2 * it);
+}
+
+static void mass_flux(Instance& I, cudaStream_t st) {
+    launch_mass_flux(I.g, I.p, I.cseg, I.hpos, I.vpos, I.T_l, I.T_v, I.mdot, st);
+    launch_extend(I.g, 2, I.p.extend_iters, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, I.mdot, I.ext[0],
+                  I.ext[1], st);
+    count(1 + I.p.extend_iters);
+}
+
+static void ghost_velocity(Instance& I, cudaStream_t st) {
+    launch_ghost_velocity(I.g, I.p, I.flags, I.mdot, I.nb, I.vcol, I.hpos, I.vpos, I.u_l, I.u_v, I.ufx_l, I.ufx_v,
+                          I.ufy_l, I.ufy_v, st);
+    count(2);
+}
+
+static void advance_interface(Instance& I, cudaStream_t st) {
+    launch_ug(I.g, I.p, I.flags, I.u_l, I.u_v, I.mdot, I.nb, I.uG, st);
+    count(1);
+    double dth = I.p.dt / I.g.h;
+    int first = (I.cfg.sweep_order == 0 || (I.nstep % 2) == 0) ? 0 : 1;
+    for (int k = 0; k < 2; ++k) {
+        int axis = k == 0 ? first : 1 - first;
+        if (k == 1) {
+            launch_reconstruct(I.g, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, nullptr, st);
+            count(1);
+        }
+        launch_sweep(I.g, axis, dth, I.vcol, I.hpos, I.vpos, I.cseg, I.uG, I.hdisp, I.vdisp, I.vcol_n, I.hpos_n,
+                     I.vpos_n, I.status, st);
+        count(4);
+        std::swap(I.vcol, I.vcol_n);
+        std::swap(I.hpos, I.hpos_n);
+        std::swap(I.vpos, I.vpos_n);
+    }
+    reconstruct_full(I, st);
+}
+
+static void record(Instance& I, int kind, const SolveResult& r) {
+    I.stats[kind] = r.iters;
+    I.stats[3 + kind] = r.rel_res;
+    if (!r.converged) I.noconv = true;
+}
+
+static void solve_energy(Instance& I, cudaStream_t st) {
+    launch_energy_operator(I.g, I.p, I.flags, I.cseg, I.hpos, I.vpos, I.Ts_l, I.Ts_v, I.op_cd, I.op_dd, I.op_wx,
+                           I.op_wy, I.op_b, I.op_x, st);
+    count(1);
+    int l0 = I.solver.launches;
+    SolveResult r = I.solver.solve(I.op_cd, I.op_dd, I.op_wx, I.op_wy, I.op_b, I.op_x, I.cfg.precision, I.cfg.rtol,
+                                   I.cfg.max_iter, st);
+    count(I.solver.launches - l0);
+    record(I, 0, r);
+    launch_split_T(I.g, I.flags, I.op_x, I.Ts_l, I.Ts_v, I.T_l, I.T_v, st);
+    count(1);
+}
+
+static void momentum(Instance& I, cudaStream_t st) {
+    // S11: predictor, both phase fields (b/x order: lx, vx, ly, vy)
+    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vb, I.vx, st);
+    count(1);
+    int iters = 0;
+    double worst = 0.0;
+    for (int comp = 0; comp < 2; ++comp) {
+        launch_visc_operator(I.g, I.p, comp, I.vf, I.op_cd, I.op_dd, I.op_wx, I.op_wy, st);
+        count(1);
+        for (int ph = 0; ph < 2; ++ph) {
+            int k = comp * 2 + ph;
+            int l0 = I.solver.launches;
+            SolveResult r = I.solver.solve(I.op_cd, I.op_dd, I.op_wx, I.op_wy, I.vb[k], I.vx[k], I.cfg.precision,
+                                           I.cfg.rtol, I.cfg.max_iter, st);
+            count(I.solver.launches - l0);
+            iters += r.iters;
+            if (r.rel_res > worst) worst = r.rel_res;
+            if (!r.converged) I.noconv = true;
+        }
+    }
+    I.stats[1] = iters;
+    I.stats[4] = worst;
+    double* s[4] = {I.vx[0], I.vx[1], I.vx[2], I.vx[3]};
+    launch_ustar(I.g, I.p, s, I.gc, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
+    count(2);
+    // S12: projection
+    launch_poisson_operator(I.g, I.p, I.vf, I.flags, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.op_cd, I.op_dd, I.op_wx,
+                            I.op_wy, I.op_b, st);
+    count(1);
+    int l0 = I.solver.launches;
+    SolveResult r = I.solver.solve(I.op_cd, I.op_dd, I.op_wx, I.op_wy, I.op_b, I.P, I.cfg.precision, I.cfg.rtol,
+                                   I.cfg.max_iter, st);
+    count(I.solver.launches - l0);
+    record(I, 2, r);
+    launch_project(I.g, I.p, I.P, I.vf, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.gc, I.us_l, I.us_v, I.u_l, I.u_v, st);
+    count(2);
+}
+
+static void diagnostics(Instance& I, cudaStream_t st) {
+    launch_diagnostics(I.g, I.p, I.vf, I.cseg, I.hpos, I.vpos, I.mdot, I.flags, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v,
+                       I.diag_partial, I.diag_ticket, I.clock, I.diag_out, st);
+    count(1);
+    I.nstep += 1;
+}
+
+static void prepare(Instance& I, cudaStream_t st) {
+    reconstruct_full(I, st);
+    if (I.p.energy) extend_T(I, I.T_l, I.T_v, st);
+    mass_flux(I, st);
+    ghost_velocity(I, st);
+    launch_project(I.g, I.p, I.P, I.vf, nullptr, nullptr, nullptr, nullptr, I.gc, nullptr, nullptr, nullptr,
+                   nullptr, st);
+    count(1);
+}
+
+static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
+    cudaStream_t st = ctx->stream;
+    switch (stage) {
+        case EBIT_STAGE_PREPARE: prepare(I, st); break;
+        case EBIT_STAGE_RECONSTRUCT: reconstruct_full(I, st); break;
+        case EBIT_STAGE_ADVECT_T:
+            if (I.p.energy) { launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, st); count(1); }
+            break;
+        case EBIT_STAGE_EXTEND_TSTAR:
+            if (I.p.energy) extend_T(I, I.Ts_l, I.Ts_v, st);
+            break;
+        case EBIT_STAGE_ADVANCE_INTERFACE: advance_interface(I, st); break;
+        case EBIT_STAGE_SOLVE_ENERGY:
+            if (I.p.energy) solve_energy(I, st);
+            break;
+        case EBIT_STAGE_EXTEND_T:
+            if (I.p.energy) extend_T(I, I.T_l, I.T_v, st);
+            break;
+        case EBIT_STAGE_MASS_FLUX: mass_flux(I, st); break;
+        case EBIT_STAGE_GHOST_VELOCITY: ghost_velocity(I, st); break;
+        case EBIT_STAGE_MOMENTUM: momentum(I, st); break;
+        case EBIT_STAGE_DIAGNOSTICS: diagnostics(I, st); break;
+        default: return fail(ctx, EBIT_EINVAL, "unknown stage");
+    }
+    return cuda_check(ctx, "run_stage");
+}
+
+static ebit_status check_status(ebit_ctx* ctx) {
+    for (auto& I : ctx->inst) {
+        int s = 0;
+        cudaMemcpyAsync(&s, I.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(e));
+        if (s & 1) return fail(ctx, EBIT_ECFL, "a marker moved one cell or more in one sweep (reduce dt)");
+        if (s & 2) return fail(ctx, EBIT_ETOPO, "too many marker candidates on one edge");
+        if (I.noconv) {
+            I.noconv = false;
+            return fail(ctx, EBIT_ENOCONV, "a linear solve hit max_iter");
+        }
+    }
+    return EBIT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char* ebit_version(void) { return "ebit-gb300 0.1 (sm_103a)"; }
+
+ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const ebit_allocator* alloc, ebit_ctx** out) {
+    if (!out || !cfgs || batch < 1) return EBIT_EINVAL;
+    *out = nullptr;
+    ebit_ctx* ctx = new ebit_ctx();
+    ctx->stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc_fn) { ctx->alloc = *alloc; ctx->has_alloc = true; }
+    ctx->inst.resize(batch);
+    for (int b = 0; b < batch; ++b) {
+        const ebit_config& c = cfgs[b];
+        if (c.nx < 4 || c.ny < 4 || !(c.h > 0) || !(c.dt > 0) || c.extend_iters < 2 || c.extend_iters > 64 ||
+            c.max_iter < 1 || !(c.rtol > 0) || (c.precision != EBIT_FP64 && c.precision != EBIT_MIXED)) {
+            delete ctx;
+            return EBIT_EINVAL;
+        }
+        for (int s = 0; s < 4; ++s)
+            if (c.bc[s] < 0 || c.bc[s] > 2) { delete ctx; return EBIT_EINVAL; }
+        Instance& I = ctx->inst[b];
+        I.cfg = c;
+        I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0;
+        for (int s = 0; s < 4; ++s) { I.g.bc[s] = c.bc[s]; I.g.Tfix[s] = c.T_fixed[s] ? 1 : 0; I.g.Tw[s] = c.T_wall[s]; }
+        std::memset(&I.p, 0, sizeof(I.p));
+        I.p.dt = c.dt; I.p.theta_min = c.theta_min; I.p.extend_iters = c.extend_iters;
+        I.p.energy = c.energy; I.p.mdot_fixed = c.mdot_fixed;
+        size_t bytes = layout(I, nullptr, assign_ptrs);
+        void* mem = nullptr;
+        if (ctx->has_alloc) mem = ctx->alloc.alloc_fn(bytes, ctx->alloc.user);
+        else if (cudaMalloc(&mem, bytes) != cudaSuccess) mem = nullptr;
+        if (!mem) { ebit_destroy(ctx); return EBIT_ENOMEM; }
+        I.arena = mem;
+        I.arena_bytes = bytes;
+        layout(I, (char*)mem, assign_ptrs);
+        cudaMemsetAsync(mem, 0, bytes, ctx->stream);
+    }
+    if (cudaMallocHost(&ctx->host_flags, 64 * sizeof(int)) != cudaSuccess) { ebit_destroy(ctx); return EBIT_ENOMEM; }
+    for (auto& I : ctx->inst) I.solver.host_flags = ctx->host_flags;
+    ctx->launch0 = g_launches.load();
+    ebit_status s = cuda_check(ctx, "ebit_init");
+    if (s != EBIT_OK) { ebit_destroy(ctx); return s; }
+    *out = ctx;
+    return EBIT_OK;
+}
+
+ebit_status ebit_set_phase_props(ebit_ctx* ctx, int inst, const ebit_phase_props* liq, const ebit_phase_props* vap,
+                                 double T_sat, double h_lg, double sigma, double gx, double gy) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !liq || !vap) return fail(ctx, EBIT_EINVAL, "bad args");
+    if (sigma != 0.0) return fail(ctx, EBIT_EINVAL, "surface tension is not part of this step (sigma must be 0)");
+    if (!(liq->rho > 0 && vap->rho > 0 && liq->lambda > 0 && vap->lambda > 0 && liq->cp > 0 && vap->cp > 0 &&
+          liq->mu > 0 && vap->mu > 0 && h_lg != 0.0))
+        return fail(ctx, EBIT_EINVAL, "properties must be positive");
+    Phys& p = ctx->inst[inst].p;
+    p.rho_l = liq->rho; p.mu_l = liq->mu; p.lam_l = liq->lambda; p.cp_l = liq->cp;
+    p.rho_v = vap->rho; p.mu_v = vap->mu; p.lam_v = vap->lambda; p.cp_v = vap->cp;
+    p.T_sat = T_sat; p.h_lg = h_lg; p.gx = gx; p.gy = gy;
+    ctx->inst[inst].props_set = true;
+    return EBIT_OK;
+}
+
+ebit_status ebit_set_interface(ebit_ctx* ctx, int inst, const uint8_t* vcol, const double* hx_pos,
+                               const double* vy_pos, int on_device) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !vcol || !hx_pos || !vy_pos)
+        return fail(ctx, EBIT_EINVAL, "bad args");
+    Instance& I = ctx->inst[inst];
+    const Grid& g = I.g;
+    size_t nv = (size_t)(g.nx + 1) * (g.ny + 1), nh = (size_t)(g.ny + 1) * g.nx, nve = (size_t)g.ny * (g.nx + 1);
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (!on_device) {
+        // host-side validation: colours 0/1, cut fractions inside (0, 1); uncut fractions zeroed
+        std::vector<double> hp(hx_pos, hx_pos + nh), vp(vy_pos, vy_pos + nve);
+        for (size_t v = 0; v < nv; ++v)
+            if (vcol[v] > 1) return fail(ctx, EBIT_EINVAL, "vertex colours must be 0 or 1");
+        for (int j = 0; j <= g.ny; ++j)
+            for (int i = 0; i < g.nx; ++i) {
+                size_t e = (size_t)j * g.nx + i;
+                bool cut = vcol[(size_t)j * (g.nx + 1) + i] != vcol[(size_t)j * (g.nx + 1) + i + 1];
+                if (!cut) hp[e] = 0.0;
+                else if (!(hp[e] >= FMIN && hp[e] <= 1.0 - FMIN))
+                    return fail(ctx, EBIT_ETOPO, "cut horizontal edge with a marker fraction outside [1e-9, 1-1e-9]");
+            }
+        for (int j = 0; j < g.ny; ++j)
+            for (int i = 0; i <= g.nx; ++i) {
+                size_t e = (size_t)j * (g.nx + 1) + i;
+                bool cut = vcol[(size_t)j * (g.nx + 1) + i] != vcol[(size_t)(j + 1) * (g.nx + 1) + i];
+                if (!cut) vp[e] = 0.0;
+                else if (!(vp[e] >= FMIN && vp[e] <= 1.0 - FMIN))
+                    return fail(ctx, EBIT_ETOPO, "cut vertical edge with a marker fraction outside [1e-9, 1-1e-9]");
+            }
+        cudaMemcpyAsync(I.vcol, vcol, nv, k, ctx->stream);
+        cudaMemcpyAsync(I.hpos, hp.data(), nh * 8, k, ctx->stream);
+        cudaMemcpyAsync(I.vpos, vp.data(), nve * 8, k, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    } else {
+        cudaMemcpyAsync(I.vcol, vcol, nv, k, ctx->stream);
+        cudaMemcpyAsync(I.hpos, hx_pos, nh * 8, k, ctx->stream);
+        cudaMemcpyAsync(I.vpos, vy_pos, nve * 8, k, ctx->stream);
+    }
+    return cuda_check(ctx, "ebit_set_interface");
+}
+
+ebit_status ebit_field_shape(const ebit_ctx* ctx, int inst, int field, size_t* count_out, size_t* elem_bytes) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !count_out || !elem_bytes) return EBIT_EINVAL;
+    size_t e;
+    size_t n = field_count(ctx->inst[inst].g, field, &e);
+    if (!n) return EBIT_EINVAL;
+    *count_out = n;
+    *elem_bytes = e;
+    return EBIT_OK;
+}
+
+ebit_status ebit_set_field(ebit_ctx* ctx, int inst, int field, const void* src, int on_device) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !src) return fail(ctx, EBIT_EINVAL, "bad args");
+    if (field == EBIT_F_VF || field == EBIT_F_CCOL || field == EBIT_F_BAND || field == EBIT_F_NB ||
+        field == EBIT_F_CSEG || field == EBIT_F_UG)
+        return fail(ctx, EBIT_EINVAL, "field is derived (read only)");
+    Instance& I = ctx->inst[inst];
+    size_t e;
+    size_t n = field_count(I.g, field, &e);
+    void* dst = field_ptr(I, field);
+    if (!n || !dst) return fail(ctx, EBIT_EINVAL, "unknown field");
+    cudaMemcpyAsync(dst, src, n * e, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
+    if (!on_device) cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, "ebit_set_field");
+}
+
+ebit_status ebit_get_field(ebit_ctx* ctx, int inst, int field, void* dst, int on_device) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !dst) return fail(ctx, EBIT_EINVAL, "bad args");
+    Instance& I = ctx->inst[inst];
+    size_t e;
+    size_t n = field_count(I.g, field, &e);
+    if (!n) return fail(ctx, EBIT_EINVAL, "unknown field");
+    if (field == EBIT_F_CCOL || field == EBIT_F_BAND) {
+        std::vector<uint8_t> fl(n);
+        cudaMemcpyAsync(fl.data(), I.flags, n, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t er = cudaStreamSynchronize(ctx->stream);
+        if (er != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(er));
+        uint8_t mask = field == EBIT_F_CCOL ? F_CCOL : F_BAND;
+        for (size_t k = 0; k < n; ++k) fl[k] = (fl[k] & mask) ? 1 : 0;
+        if (on_device) cudaMemcpy(dst, fl.data(), n, cudaMemcpyHostToDevice);
+        else std::memcpy(dst, fl.data(), n);
+        return cuda_check(ctx, "ebit_get_field");
+    }
+    cudaMemcpyAsync(dst, field_ptr(I, field), n * e, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                    ctx->stream);
+    cudaError_t er = cudaStreamSynchronize(ctx->stream);
+    if (er != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(er));
+    return cuda_check(ctx, "ebit_get_field");
+}
+
+ebit_status ebit_set_time(ebit_ctx* ctx, int inst, double t) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size()) return EBIT_EINVAL;
+    Instance& I = ctx->inst[inst];
+    double c[2] = {t, 0.0};
+    cudaMemcpyAsync(I.clock, c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    I.nstep = 0;
+    return cuda_check(ctx, "ebit_set_time");
+}
+
+ebit_status ebit_run_stage(ebit_ctx* ctx, int stage) {
+    if (!ctx) return EBIT_EINVAL;
+    for (auto& I : ctx->inst) {
+        if (!I.props_set) return fail(ctx, EBIT_EINVAL, "ebit_set_phase_props not called");
+        ebit_status s = run_stage(ctx, I, stage);
+        if (s != EBIT_OK) return s;
+    }
+    return check_status(ctx);
+}
+
+ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
+    if (!ctx || nsteps < 0) return EBIT_EINVAL;
+    ebit_status worst = EBIT_OK;
+    for (int n = 0; n < nsteps; ++n) {
+        for (auto& I : ctx->inst) {
+            if (!I.props_set) return fail(ctx, EBIT_EINVAL, "ebit_set_phase_props not called");
+            for (int s = EBIT_STAGE_ADVECT_T; s <= EBIT_STAGE_DIAGNOSTICS; ++s) {
+                ebit_status r = run_stage(ctx, I, s);
+                if (r != EBIT_OK) return r;
+            }
+        }
+        ebit_status s = check_status(ctx);
+        if (s == EBIT_ENOCONV) worst = s;
+        else if (s != EBIT_OK) return s;
+    }
+    return worst;
+}
+
+ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !dst || n < 0) return EBIT_EINVAL;
+    Instance& I = ctx->inst[inst];
+    double d[12];
+    cudaMemcpyAsync(d, I.diag_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t er = cudaStreamSynchronize(ctx->stream);
+    if (er != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(er));
+    for (int k = 0; k < 6; ++k) d[6 + k] = I.stats[k];
+    for (int k = 0; k < n && k < 12; ++k) dst[k] = d[k];
+    return EBIT_OK;
+}
+
+uint64_t ebit_launch_count(const ebit_ctx* ctx) { return ctx ? g_launches.load() - ctx->launch0 : 0; }
+
+const char* ebit_last_error(const ebit_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void ebit_destroy(ebit_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (auto& I : ctx->inst) {
+        if (!I.arena) continue;
+        if (ctx->has_alloc) { if (ctx->alloc.free_fn) ctx->alloc.free_fn(I.arena, ctx->alloc.user); }
+        else cudaFree(I.arena);
+        I.arena = nullptr;
+    }
+    if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Shared definitions of the EBIT phase-change step on sm_103a.
+//
+// Layout (row-major, x fastest):
+//   cells    c = j*nx + i                       (ny x nx)
+//   vertices v = j*(nx+1) + i                   ((ny+1) x (nx+1))
+//   h-edges  (horizontal, on line y=j, between vertices i and i+1): j*nx + i
+//   v-edges  (vertical,   on line x=i, between vertices j and j+1): j*(nx+1) + i
+//   x-faces  = v-edges, y-faces = h-edges (a face is the edge it lies on)
+// Grid units: vertex (i, j) sits at (i, j); cell centres at (i + 0.5, j + 0.5).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ebit {
+
+constexpr double FMIN = 1e-9;   // marker fractions live in [FMIN, 1 - FMIN]
+constexpr int BC_WALL = 0, BC_OUTFLOW = 1, BC_SYMMETRY = 2;
+
+// per-cell flag byte
+constexpr uint8_t F_CCOL = 1;   // centre colour f_C (1 liquid)
+constexpr uint8_t F_BAND = 2;   // narrow band
+constexpr uint8_t F_CUT = 4;    // cell holds interface segments
+
+struct Grid {
+    int nx, ny;
+    double h, x0, y0;
+    int bc[4];        // left, right, bottom, top
+    int Tfix[4];
+    double Tw[4];
+};
+
+struct Phys {
+    double rho_l, rho_v, mu_l, mu_v, lam_l, lam_v, cp_l, cp_v;
+    double T_sat, h_lg, gx, gy;
+    double dt, theta_min;
+    int extend_iters, energy;
+    double mdot_fixed;
+};
+
+__host__ __device__ inline int cidx(const Grid& g, int i, int j) { return j * g.nx + i; }
+__host__ __device__ inline int vidx(const Grid& g, int i, int j) { return j * (g.nx + 1) + i; }
+__host__ __device__ inline int hidx(const Grid& g, int i, int j) { return j * g.nx + i; }
+__host__ __device__ inline int veidx(const Grid& g, int i, int j) { return j * (g.nx + 1) + i; }
+
+// Reflection sign of velocity component comp across the boundary on `side`
+// (normal component odd at walls and symmetry planes, tangential odd at no-slip walls,
+// everything even at outflow).
+__host__ __device__ inline bool vel_odd(int kind, int comp, int axis) {
+    if (comp == axis) return kind != BC_OUTFLOW;
+    return kind == BC_WALL;
+}
+
+// cell value of a double2 field with one layer of reflected ghost cells
+__device__ inline double cell_vel(const double2* F, const Grid& g, int comp, int i, int j) {
+    bool neg = false;
+    if (i < 0) { i = 0; neg ^= vel_odd(g.bc[0], comp, 0); }
+    else if (i >= g.nx) { i = g.nx - 1; neg ^= vel_odd(g.bc[1], comp, 0); }
+    if (j < 0) { j = 0; neg ^= vel_odd(g.bc[2], comp, 1); }
+    else if (j >= g.ny) { j = g.ny - 1; neg ^= vel_odd(g.bc[3], comp, 1); }
+    double2 v = F[cidx(g, i, j)];
+    double s = comp == 0 ? v.x : v.y;
+    return neg ? -s : s;
+}
+
+inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ebit

@@ -1,0 +1,637 @@
+// Cell/face field kernels of the EBIT phase-change step (FP64):
+//   S1   WENO3 energy advection (energy-advection equation, Sec. 2.4)
+//   S6   narrow-band extension (extrapolation equation, Sec. 2.4) over a compacted band list
+//   S10  ghost velocities (ghost-velocity equation, Sec. 2.3)
+//   S11  momentum predictor pieces (discretization equations 1-3, Sec. 2.3)
+//   S12  ghost-fluid Poisson operator/RHS and the projection update (ghost-fluid Poisson
+//        equation, discretization equations 4-5)
+//   S13  diagnostics (mass-in-domain and mass-with-outflow equations, vapour volume)
+// Cell-band compaction uses one warp ballot + popcount prefix per warp and one atomic per
+// warp; the resulting list order is irrelevant to every consumer (Jacobi updates).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ebit {
+
+// ---------------------------------------------------------------------------------
+// boundary-reflected scalar access (two ghost layers)
+// ---------------------------------------------------------------------------------
+struct Refl {
+    int odd[4];      // per side: odd reflection about val[s], else even
+    double val[4];
+};
+
+__device__ inline double refl_x(const double* F, const Grid& g, const Refl& r, int i, int j) {
+    if (i < 0) {
+        double v = F[cidx(g, -1 - i, j)];
+        return r.odd[0] ? 2.0 * r.val[0] - v : v;
+    }
+    if (i >= g.nx) {
+        double v = F[cidx(g, 2 * g.nx - 1 - i, j)];
+        return r.odd[1] ? 2.0 * r.val[1] - v : v;
+    }
+    return F[cidx(g, i, j)];
+}
+__device__ inline double refl_y(const double* F, const Grid& g, const Refl& r, int i, int j) {
+    if (j < 0) {
+        double v = F[cidx(g, i, -1 - j)];
+        return r.odd[2] ? 2.0 * r.val[2] - v : v;
+    }
+    if (j >= g.ny) {
+        double v = F[cidx(g, i, 2 * g.ny - 1 - j)];
+        return r.odd[3] ? 2.0 * r.val[3] - v : v;
+    }
+    return F[cidx(g, i, j)];
+}
+
+// components of a double2 field viewed as a strided scalar: comp 0/1
+struct Comp {
+    const double2* F;
+    int comp;
+    __device__ double operator[](int c) const { return comp == 0 ? F[c].x : F[c].y; }
+};
+__device__ inline double refl_x(const Comp& F, const Grid& g, const Refl& r, int i, int j) {
+    if (i < 0) { double v = F[cidx(g, -1 - i, j)]; return r.odd[0] ? 2.0 * r.val[0] - v : v; }
+    if (i >= g.nx) { double v = F[cidx(g, 2 * g.nx - 1 - i, j)]; return r.odd[1] ? 2.0 * r.val[1] - v : v; }
+    return F[cidx(g, i, j)];
+}
+__device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int i, int j) {
+    if (j < 0) { double v = F[cidx(g, i, -1 - j)]; return r.odd[2] ? 2.0 * r.val[2] - v : v; }
+    if (j >= g.ny) { double v = F[cidx(g, i, 2 * g.ny - 1 - j)]; return r.odd[3] ? 2.0 * r.val[3] - v : v; }
+    return F[cidx(g, i, j)];
+}
+
+// WENO3 upwind derivative (undivided) from five values along a line
+__device__ inline double weno3(double Tm2, double Tm1, double T0, double Tp1, double Tp2, bool upos) {
+    const double eps = 1e-6;
+    double v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
+    double v2 = upos ? T0 - Tm1 : Tp1 - T0;
+    double v3 = upos ? Tp1 - T0 : T0 - Tm1;
+    double phi0 = 0.5 * (3.0 * v2 - v1);
+    double phi1 = 0.5 * (v2 + v3);
+    double b0 = (v2 - v1) * (v2 - v1);
+    double b1 = (v3 - v2) * (v3 - v2);
+    double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+    double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+    return (a0 * phi0 + a1 * phi1) / (a0 + a1);
+}
+
+template <class F>
+__device__ inline double advect_one(const F& T, const Grid& g, const Refl& r, int i, int j, double2 u,
+                                    double dth) {
+    double dx = weno3(refl_x(T, g, r, i - 2, j), refl_x(T, g, r, i - 1, j), refl_x(T, g, r, i, j),
+                      refl_x(T, g, r, i + 1, j), refl_x(T, g, r, i + 2, j), u.x >= 0.0);
+    double dy = weno3(refl_y(T, g, r, i, j - 2), refl_y(T, g, r, i, j - 1), refl_y(T, g, r, i, j),
+                      refl_y(T, g, r, i, j + 1), refl_y(T, g, r, i, j + 2), u.y >= 0.0);
+    return refl_x(T, g, r, i, j) - dth * (u.x * dx + u.y * dy);
+}
+
+__host__ inline Refl temperature_refl(const Grid& g) {
+    Refl r;
+    for (int s = 0; s < 4; ++s) { r.odd[s] = g.Tfix[s]; r.val[s] = g.Tw[s]; }
+    return r;
+}
+__host__ inline Refl velocity_refl(const Grid& g, int comp) {
+    Refl r;
+    for (int s = 0; s < 4; ++s) { r.odd[s] = vel_odd(g.bc[s], comp, s < 2 ? 0 : 1); r.val[s] = 0.0; }
+    return r;
+}
+
+// S1: T*_k = T_k - dt u_k . grad T_k for both phases
+__global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l, const double* __restrict__ T_v,
+                           const double2* __restrict__ u_l, const double2* __restrict__ u_v,
+                           double* __restrict__ Ts_l, double* __restrict__ Ts_v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    Ts_l[c] = advect_one(T_l, g, r, i, j, u_l[c], dth);
+    Ts_v[c] = advect_one(T_v, g, r, i, j, u_v[c], dth);
+}
+
+// ---------------------------------------------------------------------------------
+// compaction (warp ballot + popcount prefix, one atomic per warp)
+// ---------------------------------------------------------------------------------
+__global__ void k_compact(const uint8_t* __restrict__ flags, int N, uint8_t mask, int* __restrict__ list,
+                          int* __restrict__ count, int* __restrict__ idxmap) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    bool pred = c < N && (flags[c] & mask);
+    unsigned bal = __ballot_sync(0xffffffffu, pred);
+    int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && bal) base = atomicAdd(count, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (pred) {
+        int k = base + __popc(bal & ((1u << lane) - 1u));
+        list[k] = c;
+        if (idxmap) idxmap[c] = k;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// S6: one Jacobi sweep of the upwind steady balance of the extrapolation equation
+//   mode 0: T_l into vapour band cells, along +n
+//   mode 1: T_v into liquid band cells, along -n
+//   mode 2: mdot from cut cells into the rest of the band (+n in vapour, -n in liquid)
+// Values of band cells being extended live in vcur/vnxt between sweeps; the last sweep
+// writes the field itself (its band cells are then read from vcur only).
+// ---------------------------------------------------------------------------------
+__device__ inline bool ext_update(uint8_t fl, int mode) {
+    if (!(fl & F_BAND)) return false;
+    if (mode == 0) return !(fl & F_CCOL);
+    if (mode == 1) return (fl & F_CCOL) != 0;
+    return !(fl & F_CUT);
+}
+
+__global__ void k_extend(Grid g, int mode, int it, int last, const int* __restrict__ list,
+                         const int* __restrict__ count, const uint8_t* __restrict__ flags,
+                         const int* __restrict__ idxmap, const double2* __restrict__ nb, double* f,
+                         const double* __restrict__ vcur, double* __restrict__ vnxt) {
+    int n = *count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int c = list[k];
+        uint8_t fl = flags[c];
+        if (!ext_update(fl, mode)) continue;
+        int i = c % g.nx, j = c / g.nx;
+        double sgn = mode == 0 ? 1.0 : (mode == 1 ? -1.0 : ((fl & F_CCOL) ? -1.0 : 1.0));
+        double2 nn = nb[c];
+        double ax = nn.x * sgn, ay = nn.y * sgn;
+        double acc = 0.0, w = 0.0;
+        auto val = [&](int cc) -> double {
+            if (it > 0 && ext_update(flags[cc], mode)) return vcur[idxmap[cc]];
+            return f[cc];
+        };
+        if (ax > 0.0 && i - 1 >= 0) { acc += ax * val(c - 1); w += ax; }
+        else if (ax < 0.0 && i + 1 < g.nx) { acc += -ax * val(c + 1); w += -ax; }
+        if (ay > 0.0 && j - 1 >= 0) { acc += ay * val(c - g.nx); w += ay; }
+        else if (ay < 0.0 && j + 1 < g.ny) { acc += -ay * val(c + g.nx); w += -ay; }
+        double nv = w > 0.0 ? acc / w : (it > 0 ? vcur[k] : f[c]);
+        if (last) f[c] = nv;
+        else vnxt[k] = nv;
+    }
+}
+
+// energy solution (one value per cell) back to the phase fields: T_k = T where f_C = k, T*_k elsewhere
+__global__ void k_split_T(int N, const uint8_t* __restrict__ flags, const double* __restrict__ x,
+                          const double* __restrict__ Ts_l, const double* __restrict__ Ts_v, double* __restrict__ T_l,
+                          double* __restrict__ T_v) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    bool liq = flags[c] & F_CCOL;
+    T_l[c] = liq ? x[c] : Ts_l[c];
+    T_v[c] = liq ? Ts_v[c] : x[c];
+}
+
+// ---------------------------------------------------------------------------------
+// S10: ghost velocities (cells and faces)
+// ---------------------------------------------------------------------------------
+__global__ void k_ghost_cells(Grid g, double J, const uint8_t* __restrict__ flags, const double* __restrict__ mdot,
+                              const double2* __restrict__ nb, double2* u_l, double2* u_v) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.nx * g.ny) return;
+    uint8_t fl = flags[c];
+    if (!(fl & F_BAND)) return;
+    double m = mdot[c];
+    double2 n = nb[c];
+    double mx = m * n.x, my = m * n.y;
+    if (fl & F_CCOL) {
+        double2 ul = u_l[c];
+        u_v[c] = make_double2(ul.x - J * mx, ul.y - J * my);
+    } else {
+        double2 uv = u_v[c];
+        u_l[c] = make_double2(uv.x + J * mx, uv.y + J * my);
+    }
+}
+
+// x-faces (interior, between cells i-1 and i) and y-faces (interior, between rows j-1 and j)
+__global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flags, const double* __restrict__ mdot,
+                              const double2* __restrict__ nb, const uint8_t* __restrict__ vcol,
+                              const double* __restrict__ hpos, const double* __restrict__ vpos,
+                              double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nfx = (long long)g.ny * (g.nx + 1);
+    long long nfy = (long long)(g.ny + 1) * g.nx;
+    if (t < nfx) {
+        int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        if (i == 0 || i == g.nx) return;
+        int a = cidx(g, i - 1, j), b = cidx(g, i, j);
+        if (!((flags[a] | flags[b]) & F_BAND)) return;
+        double mf = 0.5 * (mdot[a] * nb[a].x + mdot[b] * nb[b].x);
+        uint8_t v0 = vcol[vidx(g, i, j)], v1 = vcol[vidx(g, i, j + 1)];
+        int colour = (v0 != v1 && vpos[t] < 0.5) ? v1 : v0;
+        if (colour) ufx_v[t] = ufx_l[t] - J * mf;
+        else ufx_l[t] = ufx_v[t] + J * mf;
+    } else if (t < nfx + nfy) {
+        long long e = t - nfx;
+        int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        if (j == 0 || j == g.ny) return;
+        int a = cidx(g, i, j - 1), b = cidx(g, i, j);
+        if (!((flags[a] | flags[b]) & F_BAND)) return;
+        double mf = 0.5 * (mdot[a] * nb[a].y + mdot[b] * nb[b].y);
+        uint8_t v0 = vcol[vidx(g, i, j)], v1 = vcol[vidx(g, i + 1, j)];
+        int colour = (v0 != v1 && hpos[e] < 0.5) ? v1 : v0;
+        if (colour) ufy_v[e] = ufy_l[e] - J * mf;
+        else ufy_l[e] = ufy_v[e] + J * mf;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// S11: momentum predictor
+// ---------------------------------------------------------------------------------
+__device__ inline double rho_mix(const Phys& p, double vf) { return p.rho_l * vf + p.rho_v * (1.0 - vf); }
+__device__ inline double mu_mix(const Phys& p, double vf) { return p.mu_l * vf + p.mu_v * (1.0 - vf); }
+
+// viscous Helmholtz operator for velocity component comp (integrated form):
+//   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where comp is Dirichlet (odd),
+//   wx/wy = mean of the two cells' mu_c (interior faces), 0 on boundary faces.
+__global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restrict__ vf, double* __restrict__ cd,
+                                double* __restrict__ dd, double* __restrict__ wx, double* __restrict__ wy) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    double v = vf[c];
+    double mu = mu_mix(p, v);
+    cd[c] = g.h * g.h * rho_mix(p, v) / p.dt;
+    double d = 0.0;
+    if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu;
+    if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu;
+    if (j == 0 && vel_odd(g.bc[2], comp, 1)) d += 2.0 * mu;
+    if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) d += 2.0 * mu;
+    dd[c] = d;
+    wx[veidx(g, i, j)] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) : 0.0;
+    if (i == g.nx - 1) wx[veidx(g, g.nx, j)] = 0.0;
+    wy[hidx(g, i, j)] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) : 0.0;
+    if (j == g.ny - 1) wy[hidx(g, i, g.ny)] = 0.0;
+}
+
+// RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c), both phases and
+// both components; also the initial guesses (current velocity)
+__global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const double* __restrict__ vf,
+                          const double2* __restrict__ u_l, const double2* __restrict__ u_v,
+                          const double2* __restrict__ gc, double* __restrict__ b_lx, double* __restrict__ b_vx,
+                          double* __restrict__ b_ly, double* __restrict__ b_vy, double* __restrict__ x_lx,
+                          double* __restrict__ x_vx, double* __restrict__ x_ly, double* __restrict__ x_vy) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
+    double2 a = gc[c];
+    double2 ul = u_l[c], uv = u_v[c];
+    b_lx[c] = coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x);
+    b_ly[c] = coef * (advect_one(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y);
+    b_vx[c] = coef * (advect_one(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x);
+    b_vy[c] = coef * (advect_one(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y);
+    x_lx[c] = ul.x; x_ly[c] = ul.y; x_vx[c] = uv.x; x_vy[c] = uv.y;
+}
+
+// u** = u* - dt gc (cells); u_f* = c->f mean of u** + dt g (faces; outflow faces take the
+// boundary cell, wall/symmetry faces are 0)
+__global__ void k_ustar(Grid g, Phys p, const double* __restrict__ s_lx, const double* __restrict__ s_vx,
+                        const double* __restrict__ s_ly, const double* __restrict__ s_vy,
+                        const double2* __restrict__ gc, double2* __restrict__ us_l, double2* __restrict__ us_v) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.nx * g.ny) return;
+    double2 a = gc[c];
+    us_l[c] = make_double2(s_lx[c] - p.dt * a.x, s_ly[c] - p.dt * a.y);
+    us_v[c] = make_double2(s_vx[c] - p.dt * a.x, s_vy[c] - p.dt * a.y);
+}
+
+__global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, const double2* __restrict__ us_v,
+                            double* __restrict__ fx_l, double* __restrict__ fx_v, double* __restrict__ fy_l,
+                            double* __restrict__ fy_v) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nfx = (long long)g.ny * (g.nx + 1);
+    long long nfy = (long long)(g.ny + 1) * g.nx;
+    if (t < nfx) {
+        int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        double vl, vv;
+        if (i > 0 && i < g.nx) {
+            int a = cidx(g, i - 1, j), b = a + 1;
+            vl = 0.5 * (us_l[a].x + us_l[b].x) + p.dt * p.gx;
+            vv = 0.5 * (us_v[a].x + us_v[b].x) + p.dt * p.gx;
+        } else {
+            int s = i == 0 ? 0 : 1;
+            if (g.bc[s] == BC_OUTFLOW) {
+                int a = cidx(g, i == 0 ? 0 : g.nx - 1, j);
+                vl = us_l[a].x + p.dt * p.gx;
+                vv = us_v[a].x + p.dt * p.gx;
+            } else {
+                vl = vv = 0.0;
+            }
+        }
+        fx_l[t] = vl;
+        fx_v[t] = vv;
+    } else if (t < nfx + nfy) {
+        long long e = t - nfx;
+        int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        double vl, vv;
+        if (j > 0 && j < g.ny) {
+            int a = cidx(g, i, j - 1), b = cidx(g, i, j);
+            vl = 0.5 * (us_l[a].y + us_l[b].y) + p.dt * p.gy;
+            vv = 0.5 * (us_v[a].y + us_v[b].y) + p.dt * p.gy;
+        } else {
+            int s = j == 0 ? 2 : 3;
+            if (g.bc[s] == BC_OUTFLOW) {
+                int a = cidx(g, i, j == 0 ? 0 : g.ny - 1);
+                vl = us_l[a].y + p.dt * p.gy;
+                vv = us_v[a].y + p.dt * p.gy;
+            } else {
+                vl = vv = 0.0;
+            }
+        }
+        fy_l[e] = vl;
+        fy_v[e] = vv;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// S12: projection
+// ---------------------------------------------------------------------------------
+__device__ inline double face_vf_x(const Grid& g, const double* vf, int i, int j) {
+    if (i == 0) return vf[cidx(g, 0, j)];
+    if (i == g.nx) return vf[cidx(g, g.nx - 1, j)];
+    return 0.5 * (vf[cidx(g, i - 1, j)] + vf[cidx(g, i, j)]);
+}
+__device__ inline double face_vf_y(const Grid& g, const double* vf, int i, int j) {
+    if (j == 0) return vf[cidx(g, i, 0)];
+    if (j == g.ny) return vf[cidx(g, i, g.ny - 1)];
+    return 0.5 * (vf[cidx(g, i, j - 1)] + vf[cidx(g, i, j)]);
+}
+
+// Poisson operator: wx/wy = dt / rho_f (interior), dd = 2 dt / rho_f on outflow faces,
+// b = -h * (undivided divergence of the face field of the cell's phase); x0 = p
+__global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf, const uint8_t* __restrict__ flags,
+                                   const double* __restrict__ fx_l, const double* __restrict__ fx_v,
+                                   const double* __restrict__ fy_l, const double* __restrict__ fy_v,
+                                   double* __restrict__ cd, double* __restrict__ dd, double* __restrict__ wx,
+                                   double* __restrict__ wy, double* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    cd[c] = 0.0;
+    double d = 0.0;
+    if (i == 0 && g.bc[0] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, 0, j));
+    if (i == g.nx - 1 && g.bc[1] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, g.nx, j));
+    if (j == 0 && g.bc[2] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, 0));
+    if (j == g.ny - 1 && g.bc[3] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, g.ny));
+    dd[c] = d;
+    wx[veidx(g, i, j)] = i > 0 ? p.dt / rho_mix(p, face_vf_x(g, vf, i, j)) : 0.0;
+    if (i == g.nx - 1) wx[veidx(g, g.nx, j)] = 0.0;
+    wy[hidx(g, i, j)] = j > 0 ? p.dt / rho_mix(p, face_vf_y(g, vf, i, j)) : 0.0;
+    if (j == g.ny - 1) wy[hidx(g, i, g.ny)] = 0.0;
+    const double* fx = (flags[c] & F_CCOL) ? fx_l : fx_v;
+    const double* fy = (flags[c] & F_CCOL) ? fy_l : fy_v;
+    double div = (fx[veidx(g, i + 1, j)] - fx[veidx(g, i, j)]) + (fy[hidx(g, i, j + 1)] - fy[hidx(g, i, j)]);
+    b[c] = -g.h * div;
+}
+
+// face accelerations a_f = g - grad_f p / rho_f (0 on walls and symmetry planes)
+__device__ inline double accel_x(const Grid& g, const Phys& p, const double* P, const double* vf, int i, int j) {
+    if (i > 0 && i < g.nx)
+        return p.gx - (P[cidx(g, i, j)] - P[cidx(g, i - 1, j)]) / (g.h * rho_mix(p, face_vf_x(g, vf, i, j)));
+    int s = i == 0 ? 0 : 1;
+    if (g.bc[s] != BC_OUTFLOW) return 0.0;
+    double r = rho_mix(p, face_vf_x(g, vf, i, j));
+    if (i == 0) return p.gx - (2.0 * P[cidx(g, 0, j)]) / (g.h * r);
+    return p.gx - (-2.0 * P[cidx(g, g.nx - 1, j)]) / (g.h * r);
+}
+__device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, const double* vf, int i, int j) {
+    if (j > 0 && j < g.ny)
+        return p.gy - (P[cidx(g, i, j)] - P[cidx(g, i, j - 1)]) / (g.h * rho_mix(p, face_vf_y(g, vf, i, j)));
+    int s = j == 0 ? 2 : 3;
+    if (g.bc[s] != BC_OUTFLOW) return 0.0;
+    double r = rho_mix(p, face_vf_y(g, vf, i, j));
+    if (j == 0) return p.gy - (2.0 * P[cidx(g, i, 0)]) / (g.h * r);
+    return p.gy - (-2.0 * P[cidx(g, i, g.ny - 1)]) / (g.h * r);
+}
+
+// face update u_f^{n+1} = u_f* + dt (a_f - g) (discretization equation 4), both phase fields
+__global__ void k_project_faces(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
+                                double* fx_l, double* fx_v, double* fy_l, double* fy_v) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nfx = (long long)g.ny * (g.nx + 1);
+    long long nfy = (long long)(g.ny + 1) * g.nx;
+    if (t < nfx) {
+        int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        bool bnd = i == 0 || i == g.nx;
+        if (bnd && g.bc[i == 0 ? 0 : 1] != BC_OUTFLOW) { fx_l[t] = 0.0; fx_v[t] = 0.0; return; }
+        double corr = p.dt * (accel_x(g, p, P, vf, i, j) - p.gx);
+        fx_l[t] += corr;
+        fx_v[t] += corr;
+    } else if (t < nfx + nfy) {
+        long long e = t - nfx;
+        int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        bool bnd = j == 0 || j == g.ny;
+        if (bnd && g.bc[j == 0 ? 2 : 3] != BC_OUTFLOW) { fy_l[e] = 0.0; fy_v[e] = 0.0; return; }
+        double corr = p.dt * (accel_y(g, p, P, vf, i, j) - p.gy);
+        fy_l[e] += corr;
+        fy_v[e] += corr;
+    }
+}
+
+// gc = f->c mean of the face accelerations; optionally u^{n+1} = u** + dt gc (Eq. 15)
+__global__ void k_project_cells(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
+                                double2* __restrict__ gc, const double2* __restrict__ us_l,
+                                const double2* __restrict__ us_v, double2* __restrict__ u_l,
+                                double2* __restrict__ u_v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    double ax = 0.5 * (accel_x(g, p, P, vf, i, j) + accel_x(g, p, P, vf, i + 1, j));
+    double ay = 0.5 * (accel_y(g, p, P, vf, i, j) + accel_y(g, p, P, vf, i, j + 1));
+    gc[c] = make_double2(ax, ay);
+    if (us_l) {
+        double2 a = us_l[c], b = us_v[c];
+        u_l[c] = make_double2(a.x + p.dt * ax, a.y + p.dt * ay);
+        u_v[c] = make_double2(b.x + p.dt * ax, b.y + p.dt * ay);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// S13: diagnostics (block partial sums, last block finalises in a fixed order)
+// ---------------------------------------------------------------------------------
+__device__ inline double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;   // valid in thread 0
+}
+
+constexpr int NDIAG_SUMS = 5;
+
+__global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, const uint16_t* __restrict__ cseg,
+                              const double* __restrict__ hpos, const double* __restrict__ vpos,
+                              const double* __restrict__ mdot, const uint8_t* __restrict__ flags,
+                              const double* __restrict__ fx_l, const double* __restrict__ fx_v,
+                              const double* __restrict__ fy_l, const double* __restrict__ fy_v,
+                              double* __restrict__ partial, unsigned* __restrict__ ticket, double* __restrict__ clock,
+                              double* __restrict__ out) {
+    __shared__ double sh[32];
+    __shared__ bool lastblk;
+    double s[NDIAG_SUMS] = {0, 0, 0, 0, 0};
+    int N = g.nx * g.ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        int i = c % g.nx, j = c / g.nx;
+        double v = vf[c];
+        double rc = rho_mix(p, v);
+        s[0] += 1.0 - v;
+        s[2] += rc;
+        uint16_t code = cseg[c];
+        int ns = code & 3;
+        if (ns) {
+            s[4] += 1.0;
+            for (int q = 0; q < ns; ++q) {
+                int kP = (code >> (2 + 4 * q)) & 3, kQ = (code >> (4 + 4 * q)) & 3;
+                auto ml = [&](int k) -> double2 {
+                    switch (k) {
+                        case 0: return make_double2(hpos[hidx(g, i, j)], 0.0);
+                        case 1: return make_double2(1.0, vpos[veidx(g, i + 1, j)]);
+                        case 2: return make_double2(hpos[hidx(g, i, j + 1)], 1.0);
+                        default: return make_double2(0.0, vpos[veidx(g, i, j)]);
+                    }
+                };
+                double2 P = ml(kP), Q = ml(kQ);
+                double dx = Q.x - P.x, dy = Q.y - P.y;
+                s[1] += mdot[c] * sqrt(dx * dx + dy * dy) * g.h;
+            }
+        }
+        bool liq = flags[c] & F_CCOL;
+        if (i == 0 && g.bc[0] == BC_OUTFLOW) s[3] += -rc * (liq ? fx_l : fx_v)[veidx(g, 0, j)];
+        if (i == g.nx - 1 && g.bc[1] == BC_OUTFLOW) s[3] += rc * (liq ? fx_l : fx_v)[veidx(g, g.nx, j)];
+        if (j == 0 && g.bc[2] == BC_OUTFLOW) s[3] += -rc * (liq ? fy_l : fy_v)[hidx(g, i, 0)];
+        if (j == g.ny - 1 && g.bc[3] == BC_OUTFLOW) s[3] += rc * (liq ? fy_l : fy_v)[hidx(g, i, g.ny)];
+    }
+    for (int q = 0; q < NDIAG_SUMS; ++q) {
+        double r = block_sum(s[q], sh);
+        if (threadIdx.x == 0) partial[q * gridDim.x + blockIdx.x] = r;
+    }
+    __threadfence();
+    if (threadIdx.x == 0) lastblk = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!lastblk) return;
+    __threadfence();
+    for (int q = 0; q < NDIAG_SUMS; ++q) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += partial[q * gridDim.x + b];
+        double r = block_sum(v, sh);
+        if (threadIdx.x == 0) s[q] = r;
+    }
+    if (threadIdx.x == 0) {
+        double h2 = g.h * g.h;
+        clock[0] += p.dt;
+        clock[1] += 1.0;
+        out[0] = clock[0];
+        out[1] = s[0] * h2;
+        out[2] = s[1] * p.dt / p.rho_v;
+        out[3] = s[2] * h2;
+        out[4] = s[3] * g.h * p.dt;
+        out[5] = s[4];
+        *ticket = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------
+static inline dim3 rows_grid(int n, int rows, int bs) { return dim3(div_up(n, bs), rows); }
+
+void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
+                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st) {
+    k_advect_T<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v,
+                                                          Ts_l, Ts_v);
+}
+
+void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
+                    cudaStream_t st) {
+    cudaMemsetAsync(count, 0, sizeof(int), st);
+    k_compact<<<div_up(N, 256), 256, 0, st>>>(flags, N, mask, list, count, idxmap);
+}
+
+int extend_grid_blocks() { return 4 * 152; }
+
+void launch_split_T(const Grid& g, const uint8_t* flags, const double* x, const double* Ts_l, const double* Ts_v,
+                    double* T_l, double* T_v, cudaStream_t st) {
+    int N = g.nx * g.ny;
+    k_split_T<<<div_up(N, 256), 256, 0, st>>>(N, flags, x, Ts_l, Ts_v, T_l, T_v);
+}
+
+void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
+                   const int* idxmap, const double2* nb, double* f, double* va, double* vb, cudaStream_t st) {
+    int nb_ = extend_grid_blocks();
+    for (int it = 0; it < iters; ++it) {
+        const double* cur = (it & 1) ? vb : va;
+        double* nxt = (it & 1) ? va : vb;
+        k_extend<<<nb_, 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb, f, cur, nxt);
+    }
+}
+
+void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, const double* mdot, const double2* nb,
+                           const uint8_t* vcol, const double* hpos, const double* vpos, double2* u_l, double2* u_v,
+                           double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st) {
+    double J = 1.0 / p.rho_l - 1.0 / p.rho_v;
+    int N = g.nx * g.ny;
+    k_ghost_cells<<<div_up(N, 256), 256, 0, st>>>(g, J, flags, mdot, nb, u_l, u_v);
+    long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
+    k_ghost_faces<<<div_up(nf, 256), 256, 0, st>>>(g, J, flags, mdot, nb, vcol, hpos, vpos, ufx_l, ufx_v, ufy_l,
+                                                   ufy_v);
+}
+
+void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
+                          double* wx, double* wy, cudaStream_t st) {
+    k_visc_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, comp, vf, cd, dd, wx, wy);
+}
+
+void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
+                    const double2* gc, double* b[4], double* x[4], cudaStream_t st) {
+    k_mom_rhs<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
+                                                         p.dt / g.h, vf, u_l, u_v, gc, b[0], b[1], b[2], b[3],
+                                                         x[0], x[1], x[2], x[3]);
+}
+
+void launch_ustar(const Grid& g, const Phys& p, double* s[4], const double2* gc, double2* us_l, double2* us_v,
+                  double* fx_l, double* fx_v, double* fy_l, double* fy_v, cudaStream_t st) {
+    int N = g.nx * g.ny;
+    k_ustar<<<div_up(N, 256), 256, 0, st>>>(g, p, s[0], s[1], s[2], s[3], gc, us_l, us_v);
+    long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
+    k_face_star<<<div_up(nf, 256), 256, 0, st>>>(g, p, us_l, us_v, fx_l, fx_v, fy_l, fy_v);
+}
+
+void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
+                             const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
+                             double* cd, double* dd, double* wx, double* wy, double* b, cudaStream_t st) {
+    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v, cd, dd,
+                                                                  wx, wy, b);
+}
+
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* fx_l, double* fx_v,
+                    double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v,
+                    double2* u_l, double2* u_v, cudaStream_t st) {
+    if (fx_l) {
+        long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
+        k_project_faces<<<div_up(nf, 256), 256, 0, st>>>(g, p, P, vf, fx_l, fx_v, fy_l, fy_v);
+    }
+    k_project_cells<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, P, vf, gc, us_l, us_v, u_l, u_v);
+}
+
+int diag_blocks() { return 152; }
+
+void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
+                        const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
+                        const double* fx_v, const double* fy_l, const double* fy_v, double* partial,
+                        unsigned* ticket, double* clock, double* out, cudaStream_t st) {
+    k_diagnostics<<<diag_blocks(), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v,
+                                                 partial, ticket, clock, out);
+}
+
+}  // namespace ebit

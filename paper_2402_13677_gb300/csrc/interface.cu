@@ -1,0 +1,742 @@
+// EBIT interface kernels: Color-Vertex reconstruction (S0/S5), narrow band, interfacial
+// velocity (S2), dimension-split marker sweeps (S3/S4), ghost-fluid link fractions (S7)
+// and the interface mass flux (S9).
+//
+// Paper (arXiv 2402.13677): Sec. 2.1 (one marker per edge, marker-motion equations,
+// aligned/unaligned markers and the circle fit of Fig. 1, Color-Vertex reconnection),
+// Sec. 2.2 (property average), Sec. 2.3 (interfacial-velocity equation, bilinear
+// interpolation, Fig. 2), Sec. 2.4 (ghost-temperature equation, mass-flux and
+// normal-gradient equations, Fig. 3).
+//
+// This translation unit is compiled with -fmad=false: every double operation is a
+// separately rounded IEEE add/mul/div/sqrt in the order written, so cut flags, topology
+// and marker positions are reproducible bit for bit by any implementation that uses the
+// same operation order.  All geometry is FP64.
+//
+// Every kernel is one thread per item of a full-grid index space (cells, vertices or
+// edges) and gathers what it needs from its neighbours: no atomics, no ordering effects.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ebit {
+
+// ---------------------------------------------------------------------------------
+// cell-local marker coordinates (cell edge k: 0 bottom, 1 right, 2 top, 3 left; edge k
+// runs from corner k to corner k+1, corners 0 BL, 1 BR, 2 TR, 3 TL)
+// ---------------------------------------------------------------------------------
+__device__ inline double2 marker_local(const Grid& g, const double* hpos, const double* vpos,
+                                       int k, int i, int j) {
+    switch (k) {
+        case 0: return make_double2(hpos[hidx(g, i, j)], 0.0);
+        case 1: return make_double2(1.0, vpos[veidx(g, i + 1, j)]);
+        case 2: return make_double2(hpos[hidx(g, i, j + 1)], 1.0);
+        default: return make_double2(0.0, vpos[veidx(g, i, j)]);
+    }
+}
+
+__device__ inline double2 corner_local(int k) {
+    return make_double2((k == 1 || k == 2) ? 1.0 : 0.0, (k >= 2) ? 1.0 : 0.0);
+}
+
+__device__ inline double shoelace3(double2 a, double2 b, double2 c) {
+    double s = 0.0;
+    s = s + (a.x * b.y - b.x * a.y);
+    s = s + (b.x * c.y - c.x * b.y);
+    s = s + (c.x * a.y - a.x * c.y);
+    return 0.5 * s;
+}
+
+__device__ inline double cross_centre(double2 P, double2 Q) {
+    return (Q.x - P.x) * (0.5 - P.y) - (Q.y - P.y) * (0.5 - P.x);
+}
+
+__device__ inline double dist2d(double2 A, double2 B) {
+    double dx = B.x - A.x;
+    double dy = B.y - A.y;
+    return sqrt(dx * dx + dy * dy);
+}
+
+__device__ inline int seg_count(uint16_t code) { return code & 3; }
+__device__ inline int seg_P(uint16_t code, int s) { return (code >> (2 + 4 * s)) & 3; }
+__device__ inline int seg_Q(uint16_t code, int s) { return (code >> (4 + 4 * s)) & 3; }
+
+// ---------------------------------------------------------------------------------
+// S0: Color-Vertex reconstruction of every cell
+// ---------------------------------------------------------------------------------
+__global__ void k_reconstruct(Grid g, const uint8_t* __restrict__ vcol, const double* __restrict__ hpos,
+                              const double* __restrict__ vpos, uint16_t* __restrict__ cseg,
+                              uint8_t* __restrict__ flags, double* __restrict__ vf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c[4];
+    c[0] = vcol[vidx(g, i, j)];
+    c[1] = vcol[vidx(g, i + 1, j)];
+    c[2] = vcol[vidx(g, i + 1, j + 1)];
+    c[3] = vcol[vidx(g, i, j + 1)];
+    int cell = cidx(g, i, j);
+    if (c[0] == c[1] && c[0] == c[2] && c[0] == c[3]) {
+        cseg[cell] = 0;
+        flags[cell] = (uint8_t)(c[0] ? F_CCOL : 0);
+        if (vf) vf[cell] = (double)c[0];
+        return;
+    }
+    double2 M[4];
+    for (int k = 0; k < 4; ++k) M[k] = marker_local(g, hpos, vpos, k, i, j);
+    int ex[2], en[2], nex = 0, nen = 0;
+    for (int k = 0; k < 4; ++k) {
+        int a = c[k], b = c[(k + 1) & 3];
+        if (a == 1 && b == 0) ex[nex++] = k;
+        if (a == 0 && b == 1) en[nen++] = k;
+    }
+    double area;
+    int ccol;
+    uint16_t code;
+    if (nex == 1) {
+        int kx = ex[0], kn = en[0];
+        // liquid polygon: Q (enter), corners kn+1 .. kx, P (exit)
+        double2 pts[6];
+        int np = 0;
+        pts[np++] = M[kn];
+        int k = (kn + 1) & 3;
+        while (true) {
+            pts[np++] = corner_local(k);
+            if (k == kx) break;
+            k = (k + 1) & 3;
+        }
+        pts[np++] = M[kx];
+        double s = 0.0;
+        for (int a = 0; a < np; ++a) {
+            double2 A = pts[a], B = pts[(a + 1) % np];
+            s = s + (A.x * B.y - B.x * A.y);
+        }
+        area = 0.5 * s;
+        ccol = cross_centre(M[kx], M[kn]) >= 0.0 ? 1 : 0;
+        code = (uint16_t)(1 | (kx << 2) | (kn << 4));
+    } else {
+        int k1 = ex[0], k2 = ex[1];
+        double LA = dist2d(M[k1], M[(k1 + 1) & 3]) + dist2d(M[k2], M[(k2 + 1) & 3]);
+        double LB = dist2d(M[k1], M[(k1 + 3) & 3]) + dist2d(M[k2], M[(k2 + 3) & 3]);
+        if (LA <= LB) {
+            int n1 = (k1 + 1) & 3, n2 = (k2 + 1) & 3;
+            double a = 0.0;
+            a = a + shoelace3(M[k1], corner_local(n1), M[n1]);
+            a = a + shoelace3(M[k2], corner_local(n2), M[n2]);
+            area = 1.0 - a;
+            ccol = 1;
+            if (cross_centre(M[k1], M[n1]) < 0.0) ccol = 0;
+            if (cross_centre(M[k2], M[n2]) < 0.0) ccol = 0;
+            code = (uint16_t)(2 | (k1 << 2) | (n1 << 4) | (k2 << 6) | (n2 << 8));
+        } else {
+            int n1 = (k1 + 3) & 3, n2 = (k2 + 3) & 3;
+            double a = 0.0;
+            a = a + shoelace3(M[n1], corner_local(k1), M[k1]);
+            a = a + shoelace3(M[n2], corner_local(k2), M[k2]);
+            area = a;
+            ccol = 0;
+            if (cross_centre(M[k1], M[n1]) >= 0.0) ccol = 1;
+            if (cross_centre(M[k2], M[n2]) >= 0.0) ccol = 1;
+            code = (uint16_t)(2 | (k1 << 2) | (n1 << 4) | (k2 << 6) | (n2 << 8));
+        }
+    }
+    cseg[cell] = code;
+    flags[cell] = (uint8_t)((ccol ? F_CCOL : 0) | F_CUT);
+    if (vf) vf[cell] = area;
+}
+
+// narrow band (a cut cell in the 3x3 block) and band normal: normalised sum of (dy, -dx)
+// over the segments of the block, visited row by row
+__global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                       const double* __restrict__ vpos, uint8_t* __restrict__ flags,
+                       double2* __restrict__ nb) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    double ax = 0.0, ay = 0.0;
+    bool inband = false;
+    for (int jj = j - 1; jj <= j + 1; ++jj) {
+        if (jj < 0 || jj >= g.ny) continue;
+        for (int ii = i - 1; ii <= i + 1; ++ii) {
+            if (ii < 0 || ii >= g.nx) continue;
+            uint16_t code = cseg[cidx(g, ii, jj)];
+            int ns = seg_count(code);
+            if (ns == 0) continue;
+            inband = true;
+            for (int s = 0; s < ns; ++s) {
+                double2 P = marker_local(g, hpos, vpos, seg_P(code, s), ii, jj);
+                double2 Q = marker_local(g, hpos, vpos, seg_Q(code, s), ii, jj);
+                double dx = Q.x - P.x;
+                double dy = Q.y - P.y;
+                ax = ax + dy;
+                ay = ay - dx;
+            }
+        }
+    }
+    int cell = cidx(g, i, j);
+    double2 n = make_double2(0.0, 0.0);
+    uint8_t f = flags[cell] & (uint8_t)(F_CCOL | F_CUT);
+    if (inband) {
+        f |= F_BAND;
+        double nrm = sqrt(ax * ax + ay * ay);
+        if (nrm > 0.0) n = make_double2(ax / nrm, ay / nrm);
+    }
+    flags[cell] = f;
+    nb[cell] = n;
+}
+
+// u_Gamma at cell centres from the jump condition (interfacial-velocity equation)
+__global__ void k_ug(Grid g, Phys p, const uint8_t* __restrict__ flags, const double2* __restrict__ u_l,
+                     const double2* __restrict__ u_v, const double* __restrict__ mdot,
+                     const double2* __restrict__ nb, double2* __restrict__ uG) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.nx * g.ny) return;
+    double m = mdot[c];
+    double2 n = nb[c];
+    if (flags[c] & F_CCOL) {
+        double cl = m / p.rho_l;
+        double2 u = u_l[c];
+        uG[c] = make_double2(u.x - cl * n.x, u.y - cl * n.y);
+    } else {
+        double cv = m / p.rho_v;
+        double2 u = u_v[c];
+        uG[c] = make_double2(u.x - cv * n.x, u.y - cv * n.y);
+    }
+}
+
+// bilinear interpolation from the four nearest cell centres (Fig. 2)
+__device__ inline double interp_bilinear(const double2* uG, const Grid& g, int comp, double x, double y) {
+    double fx = x - 0.5;
+    double fy = y - 0.5;
+    int ix = (int)floor(fx);
+    int iy = (int)floor(fy);
+    double xb = fx - (double)ix;
+    double yb = fy - (double)iy;
+    double u2 = cell_vel(uG, g, comp, ix, iy);
+    double u1 = cell_vel(uG, g, comp, ix, iy + 1);
+    double u3 = cell_vel(uG, g, comp, ix + 1, iy);
+    double u4 = cell_vel(uG, g, comp, ix + 1, iy + 1);
+    double wx0 = 1.0 - xb;
+    double wy0 = 1.0 - yb;
+    return wx0 * wy0 * u2 + wx0 * yb * u1 + xb * wy0 * u3 + xb * yb * u4;
+}
+
+// ---------------------------------------------------------------------------------
+// S2-S4: one sweep along `axis`
+// ---------------------------------------------------------------------------------
+__device__ inline bool hcut(const Grid& g, const uint8_t* vcol, int i, int j) {
+    return vcol[vidx(g, i, j)] != vcol[vidx(g, i + 1, j)];
+}
+__device__ inline bool vcut(const Grid& g, const uint8_t* vcol, int i, int j) {
+    return vcol[vidx(g, i, j)] != vcol[vidx(g, i, j + 1)];
+}
+
+// displaced along-coordinate of every marker (marker-motion equation, explicit Euler)
+__global__ void k_displace(Grid g, int axis, double dth, const uint8_t* __restrict__ vcol,
+                           const double* __restrict__ hpos, const double* __restrict__ vpos,
+                           const double2* __restrict__ uG, double* __restrict__ hdisp,
+                           double* __restrict__ vdisp, int* __restrict__ status) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nh = (long long)(g.ny + 1) * g.nx;
+    long long nv = (long long)g.ny * (g.nx + 1);
+    double x, y;
+    bool aligned;
+    double* out;
+    if (t < nh) {
+        int i = (int)(t % g.nx), j = (int)(t / g.nx);
+        if (!hcut(g, vcol, i, j)) return;
+        x = (double)i + hpos[t];
+        y = (double)j;
+        aligned = axis == 0;
+        out = hdisp + t;
+    } else if (t < nh + nv) {
+        long long e = t - nh;
+        int i = (int)(e % (g.nx + 1)), j = (int)(e / (g.nx + 1));
+        if (!vcut(g, vcol, i, j)) return;
+        x = (double)i;
+        y = (double)j + vpos[e];
+        aligned = axis == 1;
+        out = vdisp + e;
+    } else {
+        return;
+    }
+    double u = interp_bilinear(uG, g, axis, x, y);
+    double d = u * dth;
+    double al = axis == 0 ? x : y;
+    double nal = (double)(axis == 0 ? g.nx : g.ny);
+    if (!aligned && (al == 0.0 || al == nal)) d = 0.0;
+    if (!(fabs(d) < 1.0)) atomicOr(status, 1);   // CFL >= 1 (or NaN)
+    al = al + d;
+    if (aligned) al = fmin(fmax(al, 0.0), nal - FMIN);
+    else al = fmin(fmax(al, 0.0), nal);
+    *out = al;
+}
+
+// Helpers mapping the sweep's (line, index) coordinates to h/v edges.
+// axis 0: aligned lines are horizontal (h-edges on line j, index i); unaligned are
+//         vertical lines x = m (v-edges on line m, index = row).
+// axis 1: aligned lines are vertical (v-edges on line i, index j); unaligned are
+//         horizontal lines y = m (h-edges on line m, index = column).
+struct SweepView {
+    Grid g;
+    int axis;
+    const uint8_t* vcol;
+    const double* hpos;
+    const double* vpos;
+    const double* hdisp;
+    const double* vdisp;
+
+    __device__ int n_al() const { return axis == 0 ? g.nx : g.ny; }
+    __device__ int n_ac() const { return axis == 0 ? g.ny : g.nx; }
+    // aligned edge e on aligned line l
+    __device__ bool a_cut(int l, int e) const {
+        return axis == 0 ? hcut(g, vcol, e, l) : vcut(g, vcol, l, e);
+    }
+    __device__ double a_orig(int l, int e) const {
+        return axis == 0 ? (double)e + hpos[hidx(g, e, l)] : (double)e + vpos[veidx(g, l, e)];
+    }
+    __device__ double a_disp(int l, int e) const {
+        return axis == 0 ? hdisp[hidx(g, e, l)] : vdisp[veidx(g, l, e)];
+    }
+    // unaligned edge e on unaligned line m
+    __device__ bool u_cut(int m, int e) const {
+        return axis == 0 ? vcut(g, vcol, m, e) : hcut(g, vcol, e, m);
+    }
+    __device__ double u_disp(int m, int e) const {
+        return axis == 0 ? vdisp[veidx(g, m, e)] : hdisp[hidx(g, e, m)];
+    }
+    __device__ double u_orig_ac(int m, int e) const {
+        return axis == 0 ? (double)e + vpos[veidx(g, m, e)] : (double)e + hpos[hidx(g, e, m)];
+    }
+    // displaced absolute position of the marker on cell-edge k of cell (i, j)
+    __device__ double2 disp_pos(int k, int i, int j) const {
+        double x, y;
+        if (k == 0 || k == 2) {
+            int jj = j + (k == 2);
+            long long e = hidx(g, i, jj);
+            x = (double)i + hpos[e];
+            y = (double)jj;
+            if (axis == 0) x = hdisp[e]; else y = hdisp[e];
+        } else {
+            int ii = i + (k == 1);
+            long long e = veidx(g, ii, j);
+            x = (double)ii;
+            y = (double)j + vpos[e];
+            if (axis == 0) x = vdisp[e]; else y = vdisp[e];
+        }
+        return make_double2(x, y);
+    }
+};
+
+__device__ inline double clampf(double f) { return fmin(fmax(f, FMIN), 1.0 - FMIN); }
+
+__device__ inline double pick_median(double* c, int n) {
+    if (n == 0) return 0.5;
+    for (int a = 1; a < n; ++a) {
+        double v = c[a];
+        int b = a - 1;
+        while (b >= 0 && c[b] > v) { c[b + 1] = c[b]; --b; }
+        c[b + 1] = v;
+    }
+    return c[(n - 1) / 2];
+}
+
+// vertex colours: flip once per aligned marker crossing the vertex
+__global__ void k_sweep_vertices(SweepView sv, uint8_t* __restrict__ vcol_n) {
+    const Grid& g = sv.g;
+    int iv = blockIdx.x * blockDim.x + threadIdx.x;
+    int jv = blockIdx.y;
+    if (iv > g.nx) return;
+    int l = sv.axis == 0 ? jv : iv;   // aligned line through the vertex
+    int m = sv.axis == 0 ? iv : jv;   // position of the vertex along it
+    int nal = sv.n_al();
+    int flips = 0;
+    for (int e = m - 2; e <= m + 1; ++e) {
+        if (e < 0 || e >= nal) continue;
+        if (!sv.a_cut(l, e)) continue;
+        double a0 = sv.a_orig(l, e);
+        double a1 = sv.a_disp(l, e);
+        if ((a0 < (double)m) != (a1 < (double)m)) flips ^= 1;
+    }
+    vcol_n[vidx(g, iv, jv)] = (uint8_t)(sv.vcol[vidx(g, iv, jv)] ^ flips);
+}
+
+// aligned edges: the markers that slid onto the edge, one kept (lower median)
+__global__ void k_sweep_aligned(SweepView sv, const uint8_t* __restrict__ vcol_n, double* __restrict__ out) {
+    const Grid& g = sv.g;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int l = blockIdx.y;
+    int nal = sv.n_al();
+    if (e >= nal) return;
+    bool cut;
+    long long o;
+    if (sv.axis == 0) {
+        cut = vcol_n[vidx(g, e, l)] != vcol_n[vidx(g, e + 1, l)];
+        o = hidx(g, e, l);
+    } else {
+        cut = vcol_n[vidx(g, l, e)] != vcol_n[vidx(g, l, e + 1)];
+        o = veidx(g, l, e);
+    }
+    if (!cut) { out[o] = 0.0; return; }
+    double cand[8];
+    int n = 0;
+    for (int ee = e - 2; ee <= e + 2; ++ee) {
+        if (ee < 0 || ee >= nal || !sv.a_cut(l, ee)) continue;
+        double al = sv.a_disp(l, ee);
+        double fl = floor(al);
+        if ((int)fl != e) continue;
+        cand[n++] = clampf(al - fl);
+    }
+    out[o] = pick_median(cand, n);
+}
+
+// circle (through E, O, R) or chord (through E, O) crossing of the unaligned line at m
+__device__ inline double crossing(double2 E, double2 O, bool hasR, double2 R, int m, int axis) {
+    double ea = axis == 0 ? E.x : E.y;
+    double ec = axis == 0 ? E.y : E.x;
+    double bal = (axis == 0 ? O.x : O.y) - ea;
+    double bac = (axis == 0 ? O.y : O.x) - ec;
+    double alpha = (double)m - ea;
+    double lin = alpha * bac / bal;
+    double best = 0.0;
+    bool have = false;
+    if (hasR) {
+        double cal = (axis == 0 ? R.x : R.y) - ea;
+        double cac = (axis == 0 ? R.y : R.x) - ec;
+        double det = bal * cac - bac * cal;
+        double bb = bal * bal + bac * bac;
+        double cc = cal * cal + cac * cac;
+        double Dp = cc * bac - bb * cac;
+        double Ep = bb * cal - cc * bal;
+        double qa = det;
+        double qb = Ep;
+        double qc = det * alpha * alpha + Dp * alpha;
+        double disc = qb * qb - 4.0 * qa * qc;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            double t = qb >= 0.0 ? -0.5 * (qb + sq) : -0.5 * (qb - sq);
+            if (t != 0.0) { best = qc / t; have = true; }
+            if (qa != 0.0) {
+                double r2 = t / qa;
+                if (!have || fabs(r2 - lin) < fabs(best - lin)) { best = r2; have = true; }
+            }
+            if (have && fabs(best - lin) > fabs(bal) + fabs(bac)) have = false;
+        }
+    }
+    if (!have) best = lin;
+    return ec + best;
+}
+
+// chain neighbour: displaced marker linked, through the cell adjacent across cell-edge kE,
+// to the marker on kE of cell (i, j)
+__device__ inline bool chain_neighbour(const SweepView& sv, const uint16_t* cseg, int i, int j, int kE,
+                                       double2* R) {
+    const Grid& g = sv.g;
+    int di = (kE == 1) - (kE == 3);
+    int dj = (kE == 2) - (kE == 0);
+    int in = i + di, jn = j + dj;
+    if (in < 0 || in >= g.nx || jn < 0 || jn >= g.ny) return false;
+    int kk = (kE + 2) & 3;
+    uint16_t code = cseg[cidx(g, in, jn)];
+    int ns = seg_count(code);
+    for (int s = 0; s < ns; ++s) {
+        int kP = seg_P(code, s), kQ = seg_Q(code, s);
+        if (kP == kk) { *R = sv.disp_pos(kQ, in, jn); return true; }
+        if (kQ == kk) { *R = sv.disp_pos(kP, in, jn); return true; }
+    }
+    return false;
+}
+
+// unaligned edges: crossings of the displaced segments with the edge's grid line, plus
+// displaced markers lying exactly on it; one kept (lower median)
+__global__ void k_sweep_unaligned(SweepView sv, const uint16_t* __restrict__ cseg,
+                                  const uint8_t* __restrict__ vcol_n, double* __restrict__ out,
+                                  int* __restrict__ status) {
+    const Grid& g = sv.g;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;   // index across
+    int m = blockIdx.y;                               // unaligned line
+    int nac = sv.n_ac();
+    int nal = sv.n_al();
+    if (e >= nac) return;
+    bool cut;
+    long long o;
+    if (sv.axis == 0) {
+        cut = vcol_n[vidx(g, m, e)] != vcol_n[vidx(g, m, e + 1)];
+        o = veidx(g, m, e);
+    } else {
+        cut = vcol_n[vidx(g, e, m)] != vcol_n[vidx(g, e + 1, m)];
+        o = hidx(g, e, m);
+    }
+    if (!cut) { out[o] = 0.0; return; }
+    double cand[32];
+    int n = 0;
+    const double dm = (double)m;
+    // (i) displaced segments of the cells of this row/column straddling the line
+    for (int c = m - 2; c <= m + 1; ++c) {
+        if (c < 0 || c >= nal) continue;
+        int ci = sv.axis == 0 ? c : e;
+        int cj = sv.axis == 0 ? e : c;
+        uint16_t code = cseg[cidx(g, ci, cj)];
+        int ns = seg_count(code);
+        for (int s = 0; s < ns; ++s) {
+            int kP = seg_P(code, s), kQ = seg_Q(code, s);
+            double2 Pn = sv.disp_pos(kP, ci, cj);
+            double2 Qn = sv.disp_pos(kQ, ci, cj);
+            double pa = sv.axis == 0 ? Pn.x : Pn.y;
+            double qa = sv.axis == 0 ? Qn.x : Qn.y;
+            double lo = fmin(pa, qa), hi = fmax(pa, qa);
+            if (!(lo < dm && dm < hi)) continue;
+            double2 E, O;
+            int kE;
+            if (fabs(pa - dm) <= fabs(qa - dm)) { E = Pn; O = Qn; kE = kP; }
+            else { E = Qn; O = Pn; kE = kQ; }
+            double2 R;
+            bool hasR = chain_neighbour(sv, cseg, ci, cj, kE, &R);
+            double ac = crossing(E, O, hasR, R, m, sv.axis);
+            if (n < 32) cand[n++] = clampf(ac - (double)e);
+            else atomicOr(status, 2);
+        }
+    }
+    // (ii) displaced markers exactly on the line: unaligned markers of nearby lines
+    for (int mm = m - 2; mm <= m + 2; ++mm) {
+        if (mm < 0 || mm > nal) continue;
+        if (!sv.u_cut(mm, e)) continue;
+        if (sv.u_disp(mm, e) == dm) {
+            double ac = sv.u_orig_ac(mm, e);
+            double fl = floor(ac);
+            int ee = min(max((int)fl, 0), nac - 1);
+            if (ee == e) {
+                if (n < 32) cand[n++] = clampf(ac - (double)ee);
+                else atomicOr(status, 2);
+            }
+        }
+    }
+    //      and aligned markers whose line maps to this edge index
+    for (int l = e; l <= e + 1; ++l) {
+        if (l == e + 1 && l != nac) continue;   // line nac clamps to index nac - 1
+        for (int ea = m - 3; ea <= m + 2; ++ea) {
+            if (ea < 0 || ea >= nal || !sv.a_cut(l, ea)) continue;
+            if (sv.a_disp(l, ea) == dm) {
+                double ac = (double)l;
+                int ee = min(max(l, 0), nac - 1);
+                if (ee == e) {
+                    if (n < 32) cand[n++] = clampf(ac - (double)ee);
+                    else atomicOr(status, 2);
+                }
+            }
+        }
+    }
+    out[o] = pick_median(cand, n);
+}
+
+// ---------------------------------------------------------------------------------
+// S7: ghost-fluid link fractions -> per-cell Dirichlet coefficient sum and RHS
+// ---------------------------------------------------------------------------------
+// crossings of the segments of cell (i, j) with its centre line (dir 0: y = 0.5, giving
+// local x; dir 1: x = 0.5, giving local y), restricted to [lo, hi]; returns the minimum
+// of (sign * v + off) over them, or +inf
+__device__ inline double min_crossing(const Grid& g, const uint16_t* cseg, const double* hpos,
+                                      const double* vpos, int i, int j, int dir, double lo, double hi,
+                                      double sign, double off) {
+    double best = INFINITY;
+    uint16_t code = cseg[cidx(g, i, j)];
+    int ns = seg_count(code);
+    for (int s = 0; s < ns; ++s) {
+        double2 P = marker_local(g, hpos, vpos, seg_P(code, s), i, j);
+        double2 Q = marker_local(g, hpos, vpos, seg_Q(code, s), i, j);
+        double v;
+        if (dir == 0) {
+            if ((P.y < 0.5) == (Q.y < 0.5)) continue;
+            v = P.x + (0.5 - P.y) * (Q.x - P.x) / (Q.y - P.y);
+        } else {
+            if ((P.x < 0.5) == (Q.x < 0.5)) continue;
+            v = P.y + (0.5 - P.x) * (Q.y - P.y) / (Q.x - P.x);
+        }
+        if (lo <= v && v <= hi) best = fmin(best, sign * v + off);
+    }
+    return best;
+}
+
+__device__ double link_theta(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos,
+                             int i, int j, int side, double theta_min) {
+    double t;
+    switch (side) {
+        case 0:  // +x: crossings in [0.5, 1] of this cell, [0, 0.5] of the right neighbour
+            t = fmin(min_crossing(g, cseg, hpos, vpos, i, j, 0, 0.5, 1.0, 1.0, -0.5),
+                     min_crossing(g, cseg, hpos, vpos, i + 1, j, 0, 0.0, 0.5, 1.0, 0.5));
+            break;
+        case 1:  // -x
+            t = fmin(min_crossing(g, cseg, hpos, vpos, i - 1, j, 0, 0.5, 1.0, -1.0, 1.5),
+                     min_crossing(g, cseg, hpos, vpos, i, j, 0, 0.0, 0.5, -1.0, 0.5));
+            break;
+        case 2:  // +y
+            t = fmin(min_crossing(g, cseg, hpos, vpos, i, j, 1, 0.5, 1.0, 1.0, -0.5),
+                     min_crossing(g, cseg, hpos, vpos, i, j + 1, 1, 0.0, 0.5, 1.0, 0.5));
+            break;
+        default:  // -y
+            t = fmin(min_crossing(g, cseg, hpos, vpos, i, j - 1, 1, 0.5, 1.0, -1.0, 1.5),
+                     min_crossing(g, cseg, hpos, vpos, i, j, 1, 0.0, 0.5, -1.0, 0.5));
+            break;
+    }
+    if (t == INFINITY) t = 0.5;
+    return fmin(fmax(t, theta_min), 1.0);
+}
+
+// Energy operator of the combined (block-diagonal) two-phase system, integrated form:
+//   cd = h^2 (rho cp)_k / dt,   dd = sum_cut lambda_k / theta + sum_Tfixed 2 lambda_k,
+//   wx/wy = lambda_k between two cells of the same phase, 0 across the interface,
+//   b = cd T*_k + sum_cut lambda_k T_sat / theta + sum 2 lambda_k T_w,  x0 = T*_k.
+__global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ flags,
+                                  const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                                  const double* __restrict__ vpos, const double* __restrict__ Ts_l,
+                                  const double* __restrict__ Ts_v, double* __restrict__ cd,
+                                  double* __restrict__ dd, double* __restrict__ wx, double* __restrict__ wy,
+                                  double* __restrict__ b, double* __restrict__ x0) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    int k = flags[c] & F_CCOL;
+    double lam = k ? p.lam_l : p.lam_v;
+    double rc = k ? p.rho_l * p.cp_l : p.rho_v * p.cp_v;
+    double coef = g.h * g.h * rc / p.dt;
+    double ts = k ? Ts_l[c] : Ts_v[c];
+    double dsum = 0.0, rhs = coef * ts;
+    const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+    const int bside[4] = {1, 0, 3, 2};
+    for (int s = 0; s < 4; ++s) {
+        int ii = i + di[s], jj = j + dj[s];
+        if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.ny) {
+            int bs = bside[s];
+            if (g.Tfix[bs]) {
+                dsum += 2.0 * lam;
+                rhs += 2.0 * lam * g.Tw[bs];
+            }
+            continue;
+        }
+        int kn = flags[cidx(g, ii, jj)] & F_CCOL;
+        if (kn != k) {
+            double th = link_theta(g, cseg, hpos, vpos, i, j, s, p.theta_min);
+            dsum += lam / th;
+            rhs += lam * p.T_sat / th;
+        }
+    }
+    cd[c] = coef;
+    dd[c] = dsum;
+    b[c] = rhs;
+    x0[c] = ts;
+    // faces: x-face (i, j) is the left face of cell (i, j); y-face likewise the bottom
+    double w = 0.0;
+    if (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) w = lam;
+    wx[veidx(g, i, j)] = w;
+    if (i == g.nx - 1) wx[veidx(g, g.nx, j)] = 0.0;
+    w = 0.0;
+    if (j > 0 && (flags[cidx(g, i, j - 1)] & F_CCOL) == k) w = lam;
+    wy[hidx(g, i, j)] = w;
+    if (j == g.ny - 1) wy[hidx(g, i, g.ny)] = 0.0;
+}
+
+// ---------------------------------------------------------------------------------
+// S9: mass flux on cut cells (mass-flux and normal-gradient equations)
+// ---------------------------------------------------------------------------------
+__device__ inline double interp_biquadratic(const double* F, const Grid& g, double px, double py) {
+    int ic = min(max((int)floor(px), 1), g.nx - 2);
+    int jc = min(max((int)floor(py), 1), g.ny - 2);
+    double sx = px - ((double)ic + 0.5);
+    double sy = py - ((double)jc + 0.5);
+    double wx[3] = {0.5 * sx * (sx - 1.0), 1.0 - sx * sx, 0.5 * sx * (sx + 1.0)};
+    double wy[3] = {0.5 * sy * (sy - 1.0), 1.0 - sy * sy, 0.5 * sy * (sy + 1.0)};
+    double v = 0.0;
+    for (int b = 0; b < 3; ++b) {
+        double r = 0.0;
+        for (int a = 0; a < 3; ++a) r += wx[a] * F[cidx(g, ic - 1 + a, jc - 1 + b)];
+        v += wy[b] * r;
+    }
+    return v;
+}
+
+__global__ void k_mass_flux(Grid g, Phys p, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                            const double* __restrict__ vpos, const double* __restrict__ T_l,
+                            const double* __restrict__ T_v, double* __restrict__ mdot) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    uint16_t code = cseg[c];
+    int ns = seg_count(code);
+    if (ns == 0) { mdot[c] = 0.0; return; }
+    if (!p.energy) { mdot[c] = p.mdot_fixed; return; }
+    const double D1 = 1.5, D2 = 2.5;
+    double num = 0.0, den = 0.0;
+    for (int s = 0; s < ns; ++s) {
+        double2 P = marker_local(g, hpos, vpos, seg_P(code, s), i, j);
+        double2 Q = marker_local(g, hpos, vpos, seg_Q(code, s), i, j);
+        double dx = Q.x - P.x, dy = Q.y - P.y;
+        double L = sqrt(dx * dx + dy * dy);
+        double mx = (double)i + 0.5 * (P.x + Q.x);
+        double my = (double)j + 0.5 * (P.y + Q.y);
+        double nx = L > 0.0 ? dy / L : 0.0;
+        double ny = L > 0.0 ? -dx / L : 0.0;
+        double Tv1 = interp_biquadratic(T_v, g, mx + D1 * nx, my + D1 * ny);
+        double Tv2 = interp_biquadratic(T_v, g, mx + D2 * nx, my + D2 * ny);
+        double Tl1 = interp_biquadratic(T_l, g, mx - D1 * nx, my - D1 * ny);
+        double Tl2 = interp_biquadratic(T_l, g, mx - D2 * nx, my - D2 * ny);
+        double a_v = ((Tv1 - p.T_sat) * D2 / D1 - (Tv2 - p.T_sat) * D1 / D2) / ((D2 - D1) * g.h);
+        double a_l = ((Tl1 - p.T_sat) * D2 / D1 - (Tl2 - p.T_sat) * D1 / D2) / ((D2 - D1) * g.h);
+        double ms = (p.lam_l * a_l + p.lam_v * a_v) / p.h_lg;
+        num += L * ms;
+        den += L;
+    }
+    mdot[c] = den > 0.0 ? num / den : 0.0;
+}
+
+// ---------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------
+static inline dim3 rows_grid(int n, int rows, int bs) { return dim3(div_up(n, bs), rows); }
+
+void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, const double* vpos,
+                        uint16_t* cseg, uint8_t* flags, double* vf, cudaStream_t st) {
+    k_reconstruct<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, vcol, hpos, vpos, cseg, flags, vf);
+}
+
+void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, uint8_t* flags,
+                 double2* nb, cudaStream_t st) {
+    k_band<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, cseg, hpos, vpos, flags, nb);
+}
+
+void launch_ug(const Grid& g, const Phys& p, const uint8_t* flags, const double2* u_l, const double2* u_v,
+               const double* mdot, const double2* nb, double2* uG, cudaStream_t st) {
+    int n = g.nx * g.ny;
+    k_ug<<<div_up(n, 256), 256, 0, st>>>(g, p, flags, u_l, u_v, mdot, nb, uG);
+}
+
+void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, const double* hpos,
+                  const double* vpos, const uint16_t* cseg, const double2* uG, double* hdisp, double* vdisp,
+                  uint8_t* vcol_n, double* hpos_n, double* vpos_n, int* status, cudaStream_t st) {
+    long long ne = (long long)(g.ny + 1) * g.nx + (long long)g.ny * (g.nx + 1);
+    k_displace<<<div_up(ne, 256), 256, 0, st>>>(g, axis, dth, vcol, hpos, vpos, uG, hdisp, vdisp, status);
+    SweepView sv{g, axis, vcol, hpos, vpos, hdisp, vdisp};
+    k_sweep_vertices<<<rows_grid(g.nx + 1, g.ny + 1, 128), 128, 0, st>>>(sv, vcol_n);
+    if (axis == 0) {
+        k_sweep_aligned<<<rows_grid(g.nx, g.ny + 1, 128), 128, 0, st>>>(sv, vcol_n, hpos_n);
+        k_sweep_unaligned<<<rows_grid(g.ny, g.nx + 1, 128), 128, 0, st>>>(sv, cseg, vcol_n, vpos_n, status);
+    } else {
+        k_sweep_aligned<<<rows_grid(g.ny, g.nx + 1, 128), 128, 0, st>>>(sv, vcol_n, vpos_n);
+        k_sweep_unaligned<<<rows_grid(g.nx, g.ny + 1, 128), 128, 0, st>>>(sv, cseg, vcol_n, hpos_n, status);
+    }
+}
+
+void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,
+                            const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
+                            double* cd, double* dd, double* wx, double* wy, double* b, double* x0,
+                            cudaStream_t st) {
+    k_energy_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, flags, cseg, hpos, vpos, Ts_l, Ts_v, cd,
+                                                                 dd, wx, wy, b, x0);
+}
+
+void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos,
+                      const double* vpos, const double* T_l, const double* T_v, double* mdot, cudaStream_t st) {
+    k_mass_flux<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, cseg, hpos, vpos, T_l, T_v, mdot);
+}
+
+}  // namespace ebit

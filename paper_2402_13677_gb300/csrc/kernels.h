@@ -1,0 +1,55 @@
+// Host launchers of the EBIT kernels (one translation unit per group).
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace ebit {
+
+// interface.cu (FP64, no FMA contraction)
+void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, const double* vpos, uint16_t* cseg,
+                        uint8_t* flags, double* vf, cudaStream_t st);
+void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, uint8_t* flags,
+                 double2* nb, cudaStream_t st);
+void launch_ug(const Grid& g, const Phys& p, const uint8_t* flags, const double2* u_l, const double2* u_v,
+               const double* mdot, const double2* nb, double2* uG, cudaStream_t st);
+void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, const double* hpos, const double* vpos,
+                  const uint16_t* cseg, const double2* uG, double* hdisp, double* vdisp, uint8_t* vcol_n,
+                  double* hpos_n, double* vpos_n, int* status, cudaStream_t st);
+void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,
+                            const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
+                            double* cd, double* dd, double* wx, double* wy, double* b, double* x0, cudaStream_t st);
+void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos, const double* vpos,
+                      const double* T_l, const double* T_v, double* mdot, cudaStream_t st);
+
+// fields.cu
+void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
+                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st);
+void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap, cudaStream_t st);
+void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
+                   const int* idxmap, const double2* nb, double* f, double* va, double* vb, cudaStream_t st);
+void launch_split_T(const Grid& g, const uint8_t* flags, const double* x, const double* Ts_l, const double* Ts_v,
+                    double* T_l, double* T_v, cudaStream_t st);
+void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, const double* mdot, const double2* nb,
+                           const uint8_t* vcol, const double* hpos, const double* vpos, double2* u_l, double2* u_v,
+                           double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st);
+void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
+                          double* wx, double* wy, cudaStream_t st);
+void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
+                    const double2* gc, double* b[4], double* x[4], cudaStream_t st);
+void launch_ustar(const Grid& g, const Phys& p, double* s[4], const double2* gc, double2* us_l, double2* us_v,
+                  double* fx_l, double* fx_v, double* fy_l, double* fy_v, cudaStream_t st);
+void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags, const double* fx_l,
+                             const double* fx_v, const double* fy_l, const double* fy_v, double* cd, double* dd,
+                             double* wx, double* wy, double* b, cudaStream_t st);
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* fx_l, double* fx_v,
+                    double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l,
+                    double2* u_v, cudaStream_t st);
+int diag_blocks();
+void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
+                        const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
+                        const double* fx_v, const double* fy_l, const double* fy_v, double* partial, unsigned* ticket,
+                        double* clock, double* out, cudaStream_t st);
+
+}  // namespace ebit

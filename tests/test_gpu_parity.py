@@ -1,0 +1,316 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on seeded inputs.
+
+Bar (stated by the method's GPU design): cut-edge flags, topology and reconnection
+bit-exact; temperature, pressure, velocities and marker positions within 1e-10 relative
+(to the field's max magnitude) in the FP64 path; the mixed FP32/FP64 path within 1e-6.
+
+Each stage test starts GPU and oracle from the *same* state (the oracle's state uploaded
+through ebit_set_*), runs one stage on both and compares.  Interface stages are compared
+bit for bit: both sides perform the same IEEE operations in the same order.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2402_13677_gb300 import ebit as E
+from paper_2402_13677_gb300 import workloads as w
+from oracle import energy as OE
+from oracle import flow as OF
+from oracle import step as S
+
+FIELDS = ("T_l", "T_v", "u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v", "p", "gc", "mdot")
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+    return E.TorchAllocator()
+
+
+def gpu_ctx(dev, st, precision=E.EBIT_FP64, rtol=1e-13, max_iter=600):
+    pb = st.pb
+    ctx = E.ebit_init([E.config_from_problem(pb, precision, rtol, max_iter)],
+                      torch.cuda.current_stream().cuda_stream, dev)
+    E.upload_state(ctx, 0, pb, st.vcol, st.hx_pos, st.vy_pos, {k: getattr(st, k) for k in FIELDS}, st.t)
+    E.ebit_run_stage(ctx, E.STAGE_RECONSTRUCT)
+    return ctx
+
+
+def relerr(a, b):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+def cases():
+    return {
+        "stefan": lambda: w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0),
+        "bubble": lambda: w.bubble(n=48, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01, dt=1e-4, steps=0),
+        "film": lambda: w.film(40, 56, Lx=1.0, mean=0.31, amp=0.04, modes=2, seed=3, steps=0, dt=2e-3),
+        "mdot_bubble": lambda: w.const_mdot_bubble(n=40, L=8.0, R0=2.1, mdot=0.1, dt=0.1, steps=0),
+    }
+
+
+CASES = list(cases().keys())
+
+
+def prepared(name, nsteps=0):
+    pb = cases()[name]()
+    st = S.prepare(pb)
+    for _ in range(nsteps):
+        S.step(st)
+    return st
+
+
+# ----------------------------------------------------------------------------- geometry
+@pytest.mark.parametrize("name", CASES)
+def test_reconstruction_bit_exact(dev, name):
+    st = prepared(name)
+    ctx = gpu_ctx(dev, st)
+    try:
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny, ["vf", "ccol", "band", "nb", "cseg"])
+        o = st.geom
+        assert np.array_equal(g["ccol"], o.ccol)
+        assert np.array_equal(g["band"].astype(bool), o.band)
+        nseg = (g["cseg"] & 3).astype(np.int8)
+        assert np.array_equal(nseg, o.nseg)
+        for s in range(2):
+            P = np.where(nseg > s, (g["cseg"] >> (2 + 4 * s)) & 3, -1)
+            Q = np.where(nseg > s, (g["cseg"] >> (4 + 4 * s)) & 3, -1)
+            assert np.array_equal(P, o.segP[..., s]) and np.array_equal(Q, o.segQ[..., s])
+        assert np.array_equal(g["vf"], o.vf)          # same operations, same order
+        assert np.array_equal(g["nb"], o.nb)
+    finally:
+        E.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_prepare_matches_oracle(dev, name):
+    pb = cases()[name]()
+    st = S.State(pb)
+    ctx = E.ebit_init([E.config_from_problem(pb, E.EBIT_FP64, 1e-13, 600)],
+                      torch.cuda.current_stream().cuda_stream, dev)
+    try:
+        E.upload_state(ctx, 0, pb, st.vcol, st.hx_pos, st.vy_pos, {k: getattr(st, k) for k in FIELDS}, st.t)
+        E.ebit_run_stage(ctx, E.STAGE_PREPARE)
+        so = S.prepare(pb)
+        g = E.download(ctx, 0, pb.nx, pb.ny, list(FIELDS))
+        for k in FIELDS:
+            ref = getattr(so, k)
+            if np.max(np.abs(ref)) == 0:
+                assert np.max(np.abs(g[k])) == 0, k
+            else:
+                assert relerr(g[k], ref) < 1e-12, k
+    finally:
+        E.ebit_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------- stages
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
+def test_energy_advection_and_extension(dev, name):
+    st = prepared(name, 1)
+    ctx = gpu_ctx(dev, st)
+    try:
+        E.ebit_run_stage(ctx, E.STAGE_ADVECT_T)
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny, ["Ts_l", "Ts_v"])
+        pb = st.pb
+        Tl = OE.advect(st.T_l, st.u_l, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
+        Tv = OE.advect(st.T_v, st.u_v, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
+        assert relerr(g["Ts_l"], Tl) < 1e-13 or np.max(np.abs(Tl)) == 0
+        assert relerr(g["Ts_v"], Tv) < 1e-13
+        E.ebit_run_stage(ctx, E.STAGE_EXTEND_TSTAR)
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny, ["Ts_l", "Ts_v"])
+        Tl, Tv = OE.extend_temperatures(Tl, Tv, st.geom, pb.extend_iters)
+        assert np.max(np.abs(g["Ts_l"] - Tl)) <= 1e-13 * max(1.0, np.max(np.abs(Tl)))
+        assert np.max(np.abs(g["Ts_v"] - Tv)) <= 1e-13 * max(1.0, np.max(np.abs(Tv)))
+    finally:
+        E.ebit_destroy(ctx)
+
+
+def set_counter(ctx, st, n):
+    """Step counter of the GPU instance (it picks the sweep order) and of the oracle state."""
+    E.ebit_set_time(ctx, 0, st.t)
+    for _ in range(n):
+        E.ebit_run_stage(ctx, E.STAGE_DIAGNOSTICS)   # advances the counter (and the clock)
+    st.nstep = n
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("order", [0, 1])
+def test_interface_advance_bit_exact(dev, name, order):
+    st = prepared(name, 1)
+    ctx = gpu_ctx(dev, st)
+    try:
+        so = st.copy()
+        set_counter(ctx, so, order)          # 0: x then y, 1: y then x
+        E.ebit_run_stage(ctx, E.STAGE_ADVANCE_INTERFACE)
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny, ["vcol", "hx_pos", "vy_pos", "cseg", "vf", "ccol", "nb"])
+        S.advance_interface(so)
+        assert np.array_equal(g["vcol"], so.vcol)
+        assert np.array_equal(g["hx_pos"], so.hx_pos)
+        assert np.array_equal(g["vy_pos"], so.vy_pos)
+        assert np.array_equal(g["ccol"], so.geom.ccol)
+        assert np.array_equal(g["vf"], so.geom.vf)
+        assert np.array_equal(g["nb"], so.geom.nb)
+    finally:
+        E.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
+def test_energy_solve_flux_and_ghost_velocity(dev, name):
+    st = prepared(name, 1)
+    pb = st.pb
+    # oracle: run the step up to the energy solve (step counter 0 on both sides)
+    so = st.copy()
+    Ts_l = OE.advect(so.T_l, so.u_l, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
+    Ts_v = OE.advect(so.T_v, so.u_v, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
+    Ts_l, Ts_v = OE.extend_temperatures(Ts_l, Ts_v, so.geom, pb.extend_iters)
+    so.nstep = 0
+    S.advance_interface(so)
+    ctx = gpu_ctx(dev, st)
+    try:
+        for s in (E.STAGE_ADVECT_T, E.STAGE_EXTEND_TSTAR, E.STAGE_ADVANCE_INTERFACE, E.STAGE_SOLVE_ENERGY):
+            E.ebit_run_stage(ctx, s)
+        so.T_l, so.T_v = OE.solve_energy(so.geom, Ts_l, Ts_v, pb)
+        g = E.download(ctx, 0, pb.nx, pb.ny, ["T_l", "T_v"])
+        assert relerr(g["T_l"], so.T_l) < TOL64 or np.max(np.abs(so.T_l)) == 0
+        assert relerr(g["T_v"], so.T_v) < TOL64
+        E.ebit_run_stage(ctx, E.STAGE_EXTEND_T)
+        so.T_l, so.T_v = OE.extend_temperatures(so.T_l, so.T_v, so.geom, pb.extend_iters)
+        E.ebit_run_stage(ctx, E.STAGE_MASS_FLUX)
+        so.mdot = S.interface_mdot(so)
+        g = E.download(ctx, 0, pb.nx, pb.ny, ["T_l", "T_v", "mdot"])
+        assert relerr(g["T_v"], so.T_v) < TOL64
+        assert relerr(g["mdot"], so.mdot) < 1e-9
+        E.ebit_run_stage(ctx, E.STAGE_GHOST_VELOCITY)
+        OF.ghost_velocities(so)
+        g = E.download(ctx, 0, pb.nx, pb.ny, ["u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v"])
+        for k in ("u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v"):
+            ref = getattr(so, k)
+            assert np.max(np.abs(g[k] - ref)) <= 1e-9 * max(1e-12, np.max(np.abs(ref))), k
+    finally:
+        E.ebit_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------- whole step
+@pytest.mark.parametrize("name", CASES)
+def test_full_step_fp64(dev, name):
+    st = prepared(name, 1)
+    ctx = gpu_ctx(dev, st)
+    try:
+        so = st.copy()
+        so.nstep = 0                                 # ebit_set_time reset the GPU counter to 0
+        E.ebit_step(ctx, 1)
+        row = S.step(so)
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny)
+        assert np.array_equal(g["vcol"], so.vcol)
+        assert np.array_equal(g["hx_pos"], so.hx_pos)
+        assert np.array_equal(g["vy_pos"], so.vy_pos)
+        for k in FIELDS:
+            ref = getattr(so, k)
+            if np.max(np.abs(ref)) == 0:
+                assert np.max(np.abs(g[k])) < 1e-14, k
+            else:
+                assert relerr(g[k], ref) < TOL64, (k, relerr(g[k], ref))
+        d = E.ebit_get_diagnostics(ctx, 0)
+        assert abs(d[0] - row[0]) < 1e-12
+        for q in (1, 2, 3, 4):
+            assert abs(d[q] - row[q]) <= 1e-9 * max(1e-12, abs(row[q])), q
+        assert d[5] == row[5]
+    finally:
+        E.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["stefan", "bubble"])
+def test_several_steps_track_the_oracle(dev, name):
+    st = prepared(name, 0)
+    ctx = gpu_ctx(dev, st)
+    try:
+        so = st.copy()
+        so.nstep = 0
+        for _ in range(4):
+            E.ebit_step(ctx, 1)
+            S.step(so)
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny)
+        assert np.array_equal(g["vcol"], so.vcol)
+        assert np.max(np.abs(g["hx_pos"] - so.hx_pos)) < 1e-10
+        assert np.max(np.abs(g["vy_pos"] - so.vy_pos)) < 1e-10
+        for k in FIELDS:
+            ref = getattr(so, k)
+            if np.max(np.abs(ref)) > 0:
+                assert relerr(g[k], ref) < 1e-9, k
+    finally:
+        E.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
+def test_mixed_precision_error_against_oracle(dev, name):
+    """FP32 MG-PCG inside FP64 refinement to 1e-10: error vs the FP64 oracle stated and bounded."""
+    st = prepared(name, 1)
+    ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-10)
+    try:
+        so = st.copy()
+        so.nstep = 0
+        E.ebit_step(ctx, 1)
+        S.step(so)
+        g = E.download(ctx, 0, st.pb.nx, st.pb.ny)
+        assert np.array_equal(g["vcol"], so.vcol)
+        for k in ("T_l", "T_v", "p", "u_l", "u_v"):
+            ref = getattr(so, k)
+            if np.max(np.abs(ref)) > 0:
+                assert relerr(g[k], ref) < 1e-7, (k, relerr(g[k], ref))
+    finally:
+        E.ebit_destroy(ctx)
+
+
+def test_c2_bubble_full_size_sampled(dev):
+    """512^2 planar bubble (the benchmark workload), one FP64 step and one mixed step; the oracle
+    computes the same step, every cut flag and sampled field values are compared."""
+    pb = w.c2_bubble(steps=0)
+    st = S.prepare(pb)
+    so = st.copy()
+    S.step(so)
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, pb.nx * pb.ny, size=4096)
+    for prec, tol in ((E.EBIT_FP64, 1e-9), (E.EBIT_MIXED, 1e-6)):
+        ctx = gpu_ctx(dev, st, precision=prec, rtol=1e-12 if prec == E.EBIT_FP64 else 1e-10, max_iter=1000)
+        try:
+            E.ebit_step(ctx, 1)
+            g = E.download(ctx, 0, pb.nx, pb.ny)
+            assert np.array_equal(g["vcol"], so.vcol)
+            assert np.max(np.abs(g["hx_pos"] - so.hx_pos)) == 0.0
+            for k in ("T_l", "p", "u_l"):
+                ref = getattr(so, k).reshape(pb.nx * pb.ny, -1)[idx]
+                got = g[k].reshape(pb.nx * pb.ny, -1)[idx]
+                assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(getattr(so, k))), (prec, k)
+        finally:
+            E.ebit_destroy(ctx)
+
+
+def test_edge_cases_empty_interface_and_invalid_input(dev):
+    """No interface at all (single-phase liquid at rest), and an interface whose marker sits on a vertex."""
+    pb = w.stefan(16, 8, X0=0.1, steps=0)
+    pb.vcol[:] = 1
+    pb.hx_pos[:] = 0
+    pb.vy_pos[:] = 0
+    pb.T_bc = (None, None, None, None)
+    st = S.prepare(pb)
+    ctx = gpu_ctx(dev, st)
+    try:
+        E.ebit_step(ctx, 2)
+        g = E.download(ctx, 0, pb.nx, pb.ny, ["vcol", "band", "mdot"])
+        assert np.all(g["vcol"] == 1) and not g["band"].any() and not g["mdot"].any()
+        bad = pb.hx_pos.copy()
+        vcol = pb.vcol.copy()
+        vcol[0, 0] = 0                    # cut edge (0,0) but fraction 0 -> rejected
+        with pytest.raises(E.EbitError) as ei:
+            E.ebit_set_interface(ctx, 0, vcol, bad, pb.vy_pos)
+        assert ei.value.status == E.EBIT_ETOPO
+    finally:
+        E.ebit_destroy(ctx)

@@ -1,0 +1,365 @@
+"""Benchmark of the EBIT phase-change time step on GB300.
+
+Workload (default): the 512^2 planar bubble growing in superheated liquid (rho_l/rho_v = 20,
+k_l/k_v = 5, St = 0.2, superheat 1, dt = 1.96e-6), the full step of the method: energy
+advection, EBIT marker sweeps and reconnection, sharp-interface energy solve, mass flux,
+ghost velocities, momentum predictor and ghost-fluid projection.  Headline precision:
+FP32 multigrid-preconditioned CG inside FP64 iterative refinement, every solve to a
+1e-8 relative residual; the FP64 path is timed beside it.
+
+metric: cell-steps/s = cells x steps / device time (whole job over all ranks).
+
+One JSON line on rank 0.  `--impl reference` times the CPU oracle (the plain FP64
+restatement of the method) on the host cores instead.
+
+Multi-GPU: the single-instance step does not shard (every solver iteration couples the whole
+grid), so N ranks run N independent replicas (weak scaling); no collective is on the data
+path, only the timing barrier and the max-over-ranks reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+WORKLOADS = {
+    "c2_bubble_512": dict(kind="c2", desc="2D planar vapour bubble in superheated liquid, 512x512"),
+    "c3_film_1024x2048": dict(kind="c3", desc="2D film boiling over a heated wall, 1024x2048"),
+    "c5_film_4096": dict(kind="c5", desc="multi-mode 2D film boiling, 4096x4096"),
+}
+METRIC = "cell-steps/s at 1 GPU, FP32+refine vs FP64, 1e-8 rel residual; %HBM roofline"
+
+
+def make_problem(name):
+    from paper_2402_13677_gb300 import workloads as w
+    kind = WORKLOADS[name]["kind"]
+    if kind == "c2":
+        return w.c2_bubble(steps=0)
+    if kind == "c3":
+        return w.c3_film(steps=0)
+    return w.c5_film(steps=0)
+
+
+# ------------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 3 + k and s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def oracle_rate(name, budget_s=20.0, max_steps=3):
+    """Time the oracle (as it stands) on a bounded sample of the workload: prepare once, then
+    whole steps until the CPU budget is used.  Returns (cell-steps/s, steps, seconds, threads)."""
+    from oracle import step as S
+    pb = make_problem(name)
+    st = S.prepare(pb)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        S.step(st)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return pb.nx * pb.ny * steps / dt, steps, dt
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each timed step is one whole oracle step of the workload; the run stops early (and says
+    # so in the sample) once the CPU budget is spent, so it ends within a few minutes
+    total_steps, total_s = 0, 0.0
+    from oracle import step as S
+    pb = make_problem(args.workload)
+    cells = pb.nx * pb.ny
+    st = S.prepare(pb)
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        S.step(st)
+        total_s += time.perf_counter() - t0
+        total_steps += 1
+        if total_s > args.reference_budget:
+            break
+    value = cells * total_steps / total_s
+    cores = _cores_used()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / total_steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "cells": cells, "solver": "sparse direct (SuperLU)"},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{total_steps} of {args.steps} whole oracle steps of {args.workload} "
+                                       f"from its initial state ({total_s:.1f} s)"},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _cores_used():
+    # the oracle is numpy + SuperLU: BLAS threads may be used; report the threads available
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_2402_13677_gb300 import ebit as E
+    import __graft_entry__ as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        G.build()
+    if dist:
+        dist.barrier()
+        G.build()
+    E.load()
+
+    pb = make_problem(args.workload)
+    cells = pb.nx * pb.ny
+    stream = torch.cuda.current_stream()
+    alloc = E.TorchAllocator()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def new_ctx(precision):
+        ctx = E.ebit_init([E.config_from_problem(pb, precision, args.rtol, args.max_iter)], stream.cuda_stream,
+                          alloc)
+        E.upload_state(ctx, 0, pb, pb.vcol, np.where(pb.hx_cut > 0, pb.hx_pos, 0.0),
+                       np.where(pb.vy_cut > 0, pb.vy_pos, 0.0),
+                       {"T_l": pb.T_l, "T_v": pb.T_v, "u_l": pb.u_l, "u_v": pb.u_v, "ufx_l": pb.ufx_l,
+                        "ufx_v": pb.ufx_v, "ufy_l": pb.ufy_l, "ufy_v": pb.ufy_v, "p": pb.p}, pb.t0)
+        E.ebit_run_stage(ctx, E.STAGE_PREPARE)
+        return ctx
+
+    def timed_steps(ctx, k, with_timing=False):
+        """k steps, each bracketed by CUDA events on the context's stream; L2 flushed between steps."""
+        total = 0.0
+        launches0 = E.ebit_launch_count(ctx)
+        if with_timing:
+            E.ebit_timing_begin(ctx, E.EBIT_KT_SMOOTH_L0)
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            E.ebit_step(ctx, 1, allow_noconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+        kt = E.ebit_timing_end(ctx) if with_timing else None
+        return total, E.ebit_launch_count(ctx) - launches0, kt
+
+    def barrier_max(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    prec_list = [("mixed", E.EBIT_MIXED), ("fp64", E.EBIT_FP64)]
+    if args.profile_only:
+        prec_list = prec_list[:1]
+    clocks = ClockSampler(local)
+    for name, prec in prec_list:
+        ctx = new_ctx(prec)
+        try:
+            for _ in range(args.warmup):
+                E.ebit_step(ctx, 1, allow_noconv=True)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            if name == "mixed":
+                clocks.start()
+            secs, launches, kt = timed_steps(ctx, args.steps, with_timing=(name == "mixed"))
+            if name == "mixed":
+                clk = clocks.stop()
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            secs = barrier_max(secs)
+            d = E.ebit_get_diagnostics(ctx, 0)
+            results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist())
+        finally:
+            E.ebit_destroy(ctx)
+    if args.profile_only:
+        if rank == 0:
+            r = results["mixed"]
+            print(json.dumps({"profile_only": True, "ms_per_step": 1e3 * r["secs"] / args.steps}), flush=True)
+        return 0
+
+    # end to end through the C ABI with HOST buffers: every step uploads its inputs (the whole
+    # state, from pinned host memory) with ebit_set_interface / ebit_set_field, steps, and reads
+    # the new state and the diagnostics back with ebit_get_field / ebit_get_diagnostics;
+    # wall-clock time of the whole sequence
+    e2e = None
+    if not args.no_e2e:
+        ctx = new_ctx(E.EBIT_MIXED)
+        try:
+            for _ in range(args.warmup):
+                E.ebit_step(ctx, 1, allow_noconv=True)
+            ids = {"T_l": E.F_T_L, "T_v": E.F_T_V, "u_l": E.F_U_L, "u_v": E.F_U_V, "ufx_l": E.F_UFX_L,
+                   "ufx_v": E.F_UFX_V, "ufy_l": E.F_UFY_L, "ufy_v": E.F_UFY_V, "p": E.F_P, "gc": E.F_GC,
+                   "mdot": E.F_MDOT, "vcol": E.F_VCOL, "hx_pos": E.F_HX_POS, "vy_pos": E.F_VY_POS}
+            lib = E.load()
+            host = {}
+            for n, f in ids.items():
+                cnt, eb = E.ebit_field_shape(ctx, 0, f)
+                host[n] = torch.empty(cnt * eb, dtype=torch.uint8, pin_memory=True)
+                lib.ebit_get_field(ctx, 0, f, host[n].data_ptr(), 0)
+            h2d = sum(h.numel() for h in host.values())
+            diag = np.zeros(12)
+            total = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lib.ebit_set_interface(ctx, 0, host["vcol"].data_ptr(), host["hx_pos"].data_ptr(),
+                                       host["vy_pos"].data_ptr(), 0)
+                for n, f in ids.items():
+                    if n not in ("vcol", "hx_pos", "vy_pos"):
+                        lib.ebit_set_field(ctx, 0, f, host[n].data_ptr(), 0)
+                E.ebit_run_stage(ctx, E.STAGE_RECONSTRUCT)
+                E.ebit_step(ctx, 1, allow_noconv=True)
+                for n, f in ids.items():
+                    lib.ebit_get_field(ctx, 0, f, host[n].data_ptr(), 0)
+                diag = E.ebit_get_diagnostics(ctx, 0)
+                total += time.perf_counter() - t0
+            total = barrier_max(total)
+            e2e = {"value": world * cells * args.steps / total, "unit": "cell-steps/s",
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d + 8 * len(diag),
+                   "timing": "wall clock per step, host buffers in and out through the C ABI"}
+        finally:
+            E.ebit_destroy(ctx)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    mixed, fp64 = results["mixed"], results["fp64"]
+    value = world * cells * args.steps / mixed["secs"]
+    value64 = world * cells * args.steps / fp64["secs"]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    kt_ms, kt_n, kt_bytes = mixed["kt"]
+    achieved = (kt_bytes * kt_n) / (kt_ms / 1e3) / 1e9 if kt_ms > 0 else None
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "smooth_l0_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            if tr.get("workload") == args.workload:
+                traffic = tr.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        r, n, s = oracle_rate(args.workload, budget_s=args.cpu_budget)
+        cpu = {"value": r, "unit": "cell-steps/s", "cores": _cores_used(), "kind": "oracle",
+               "sample": f"{n} whole oracle steps of {args.workload} from its initial state ({s:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * mixed["secs"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64-refine", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": cells, "grid": [pb.nx, pb.ny], "rtol": args.rtol,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp64": {"value": value64, "unit": "cell-steps/s", "ms_per_step": 1e3 * fp64["secs"] / args.steps,
+                 "speedup_mixed_over_fp64": value / value64},
+        "timesteps_per_s": args.steps / mixed["secs"],
+        "roofline": {"bound": "hbm", "kernel": "k_smooth<float> (finest-grid red/black GS half-sweep)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "launches_timed": kt_n, "bytes_per_launch": kt_bytes,
+                     "avg_launch_us": 1e3 * kt_ms / kt_n if kt_n else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": int(mixed["launches"]),
+        "solver": {"mixed_diag": mixed["diag"], "fp64_diag": fp64["diag"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2_bubble_512", choices=list(WORKLOADS))
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--max-iter", type=int, default=400)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--reference-budget", type=float, default=150.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -181,6 +181,16 @@ ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n);
 /* Kernel launches issued since the context was created (all instances). */
 uint64_t ebit_launch_count(const ebit_ctx* ctx);
 
+/* CUDA-event timing of one kernel class, on the context's stream, while ebit_step runs.
+ * kernel_class EBIT_KT_SMOOTH_L0: the red/black Gauss-Seidel half-sweeps on the finest grid
+ * (the multigrid smoother, the dominant kernel of the step).  ebit_timing_end synchronises
+ * and returns the summed kernel time, the number of timed launches and the algorithmic bytes
+ * of one launch (4.5 words per cell: x of every cell, b, diag and the new x of the updated
+ * half, the two face-coefficient arrays). */
+enum { EBIT_KT_SMOOTH_L0 = 1 };
+ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class);
+ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes_per_launch);
+
 const char* ebit_last_error(const ebit_ctx* ctx);
 void ebit_destroy(ebit_ctx* ctx);
 

@@ -571,6 +571,32 @@ ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n) {
 
 uint64_t ebit_launch_count(const ebit_ctx* ctx) { return ctx ? g_launches.load() - ctx->launch0 : 0; }
 
+ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class) {
+    if (!ctx || kernel_class != EBIT_KT_SMOOTH_L0) return EBIT_EINVAL;
+    for (auto& I : ctx->inst) I.solver.time_begin();
+    return cuda_check(ctx, "ebit_timing_begin");
+}
+
+ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes_per_launch) {
+    if (!ctx || !total_ms || !launches || !bytes_per_launch) return EBIT_EINVAL;
+    double tot = 0.0, bytes = 0.0;
+    uint64_t n = 0;
+    for (auto& I : ctx->inst) {
+        tot += I.solver.time_end_ms();
+        n += (uint64_t)I.solver.timed_launches;
+        // algorithmic bytes of one red or black half-sweep of the stored-coefficient
+        // five-point Gauss-Seidel: x read for every cell (neighbours), b and diag read and x
+        // written for the half being updated, both face arrays read (every face borders one
+        // cell of each colour): 4.5 words per cell
+        double word = I.cfg.precision == EBIT_MIXED ? 4.0 : 8.0;
+        bytes += (double)I.g.nx * I.g.ny * 4.5 * word * (double)I.solver.timed_launches;
+    }
+    *total_ms = tot;
+    *launches = n;
+    *bytes_per_launch = n ? bytes / (double)n : 0.0;
+    return cuda_check(ctx, "ebit_timing_end");
+}
+
 const char* ebit_last_error(const ebit_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void ebit_destroy(ebit_ctx* ctx) {

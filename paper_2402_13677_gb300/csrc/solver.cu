@@ -463,6 +463,36 @@ static void setup_hierarchy(Solver& s, const double* cd0, const double* dd0, con
     }
 }
 
+void Solver::time_begin() {
+    if (!ev) {
+        ev_cap = 8192;
+        ev = new cudaEvent_t[ev_cap];
+        for (int k = 0; k < ev_cap; ++k) cudaEventCreate(&ev[k]);
+    }
+    ev_used = 0;
+    timed_launches = 0;
+    timing = true;
+}
+
+void Solver::time_mark(cudaStream_t st) {
+    if (ev_used < ev_cap) cudaEventRecord(ev[ev_used], st);
+    ++ev_used;
+}
+
+double Solver::time_end_ms() {
+    timing = false;
+    double tot = 0.0;
+    int n = ev_used < ev_cap ? ev_used : ev_cap;
+    if (n >= 2) cudaEventSynchronize(ev[n - 1]);
+    for (int k = 0; k + 1 < n; k += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        tot += ms;
+    }
+    timed_launches = n / 2;
+    return tot;
+}
+
 // z = M r (one V(2,2)-cycle), level-0 input b0 = r and output x0 = z
 template <typename T>
 static void vcycle(Solver& s, const T* r, T* z, cudaStream_t st, int& launches) {
@@ -472,9 +502,13 @@ static void vcycle(Solver& s, const T* r, T* z, cudaStream_t st, int& launches) 
     for (int l = 0; l < s.nlev - 1; ++l) {
         LevelView<T> L = view<T>(s, l);
         int n = L.nx * L.ny;
+        bool tm = s.timing && l == 0;
         for (int k = 0; k < nu; ++k) {
+            if (tm) s.time_mark(st);
             k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, b, x, 0, k == 0, s.flags);
+            if (tm) { s.time_mark(st); s.time_mark(st); }
             k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, b, x, 1, 0, s.flags);
+            if (tm) s.time_mark(st);
             launches += 2;
         }
         T* bc = lb<T>(s, l + 1);
@@ -505,9 +539,13 @@ static void vcycle(Solver& s, const T* r, T* z, cudaStream_t st, int& launches) 
         const T* bl = l == 0 ? r : lb<T>(s, l);
         k_prolong<T><<<nblocks(n), RB, 0, st>>>(L.nx, L.ny, lx<T>(s, l + 1), xl, s.flags);
         ++launches;
+        bool tm = s.timing && l == 0;
         for (int k = 0; k < nu; ++k) {
+            if (tm) s.time_mark(st);
             k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, bl, xl, 1, 0, s.flags);
+            if (tm) { s.time_mark(st); s.time_mark(st); }
             k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, bl, xl, 0, 0, s.flags);
+            if (tm) s.time_mark(st);
             launches += 2;
         }
     }

@@ -27,6 +27,14 @@ struct Solver {
     int* flags;
     int* host_flags;   // pinned, set by the owner
     int launches = 0;
+    // optional CUDA-event timing of the level-0 smoother sweeps (the dominant kernel class)
+    bool timing = false;
+    int ev_cap = 0, ev_used = 0;
+    long long timed_launches = 0;
+    cudaEvent_t* ev = nullptr;
+    void time_begin();
+    void time_mark(cudaStream_t st);   // records one event (pairs: start, stop)
+    double time_end_ms();               // synchronises, sums the recorded pairs
 
     void plan(int nx, int ny);
     static size_t bytes(int nx, int ny);

@@ -35,7 +35,9 @@ FIELD_DTYPES = {F_CCOL: np.uint8, F_BAND: np.uint8, F_VCOL: np.uint8, F_CSEG: np
 
 EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_field", "ebit_get_field",
            "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
-           "ebit_launch_count", "ebit_last_error", "ebit_destroy", "ebit_version"]
+           "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_last_error", "ebit_destroy",
+           "ebit_version"]
+EBIT_KT_SMOOTH_L0 = 1
 
 
 class ebit_config(C.Structure):
@@ -89,6 +91,8 @@ def load(path: str = LIB_PATH):
     lib.ebit_get_diagnostics.argtypes = [vp, i32, C.POINTER(C.c_double), i32]
     lib.ebit_launch_count.argtypes = [vp]
     lib.ebit_launch_count.restype = C.c_uint64
+    lib.ebit_timing_begin.argtypes = [vp, i32]
+    lib.ebit_timing_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
     lib.ebit_last_error.argtypes = [vp]
     lib.ebit_last_error.restype = C.c_char_p
     lib.ebit_destroy.argtypes = [vp]
@@ -208,6 +212,17 @@ def ebit_get_diagnostics(ctx, inst, n=12):
 
 def ebit_launch_count(ctx):
     return int(load().ebit_launch_count(ctx))
+
+
+def ebit_timing_begin(ctx, kernel_class=EBIT_KT_SMOOTH_L0):
+    _check(ctx, load().ebit_timing_begin(ctx, kernel_class))
+
+
+def ebit_timing_end(ctx):
+    """(total kernel ms, launches, algorithmic bytes per launch) of the timed kernel class."""
+    ms, n, b = C.c_double(), C.c_uint64(), C.c_double()
+    _check(ctx, load().ebit_timing_end(ctx, C.byref(ms), C.byref(n), C.byref(b)))
+    return ms.value, n.value, b.value
 
 
 def ebit_last_error(ctx):

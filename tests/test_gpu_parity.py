@@ -78,11 +78,12 @@ def test_reconstruction_bit_exact(dev, name):
         o = st.geom
         assert np.array_equal(g["ccol"], o.ccol)
         assert np.array_equal(g["band"].astype(bool), o.band)
-        nseg = (g["cseg"] & 3).astype(np.int8)
+        code = g["cseg"].astype(np.int64)
+        nseg = (code & 3).astype(np.int8)
         assert np.array_equal(nseg, o.nseg)
         for s in range(2):
-            P = np.where(nseg > s, (g["cseg"] >> (2 + 4 * s)) & 3, -1)
-            Q = np.where(nseg > s, (g["cseg"] >> (4 + 4 * s)) & 3, -1)
+            P = np.where(nseg > s, (code >> (2 + 4 * s)) & 3, -1)
+            Q = np.where(nseg > s, (code >> (4 + 4 * s)) & 3, -1)
             assert np.array_equal(P, o.segP[..., s]) and np.array_equal(Q, o.segQ[..., s])
         assert np.array_equal(g["vf"], o.vf)          # same operations, same order
         assert np.array_equal(g["nb"], o.nb)

@@ -170,7 +170,7 @@ def run_ours(args):
 
     pb = make_problem(args.workload)
     cells = pb.nx * pb.ny
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # non-default stream: each step is replayed as a CUDA graph
     alloc = E.TorchAllocator()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 

@@ -32,12 +32,13 @@
  *   - Streams: all device work of a context is ordered on the cudaStream_t given to
  *     ebit_init() (passed as void*; NULL = legacy default stream).  Calls that return
  *     data to the host (ebit_get_field with on_device = 0, ebit_get_diagnostics)
- *     synchronise that stream before returning; ebit_step() does not synchronise
- *     except to read solver convergence words every few iterations.
+ *     synchronise that stream before returning; ebit_step() synchronises once per step to
+ *     read the status word and the solver statistics (and, with graphs disabled, polls the
+ *     solver convergence words every few iterations).
  *   - Errors: every call returns an ebit_status; on failure a message is kept for
  *     ebit_last_error().  EBIT_ENOCONV means a linear solve hit max_iter: the step is
- *     completed with its last iterate and the counter is reported by
- *     ebit_get_solver_stats().  EBIT_ECUDA means a CUDA call failed; the context should
+ *     completed with its last iterate; iteration counts and final residuals are reported by
+ *     ebit_get_diagnostics().  EBIT_ECUDA means a CUDA call failed; the context should
  *     then be destroyed.
  *   - Threads: a context may be used by one host thread at a time.
  */
@@ -181,15 +182,23 @@ ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n);
 /* Kernel launches issued since the context was created (all instances). */
 uint64_t ebit_launch_count(const ebit_ctx* ctx);
 
-/* CUDA-event timing of one kernel class, on the context's stream, while ebit_step runs.
- * kernel_class EBIT_KT_SMOOTH_L0: the red/black Gauss-Seidel half-sweeps on the finest grid
- * (the multigrid smoother, the dominant kernel of the step).  ebit_timing_end synchronises
- * and returns the summed kernel time, the number of timed launches and the algorithmic bytes
- * of one launch (4.5 words per cell: x of every cell, b, diag and the new x of the updated
- * half, the two face-coefficient arrays). */
+/* Device-side timing of one kernel class while ebit_step runs (graph or not): each timed
+ * launch records the span from its first block's start to its last block's end from the GPU
+ * global timer.  kernel_class EBIT_KT_SMOOTH_L0: the finest-grid multigrid smoother kernels
+ * (tiled red-black Gauss-Seidel "pre" and "post" kernels), the dominant kernels of the step.
+ * ebit_timing_end synchronises and returns the summed kernel time, the number of timed
+ * launches and the algorithmic bytes of an average launch (pre: b, diag, wl, wb read, x and a
+ * quarter-size coarse b written; post: x, a quarter-size coarse x, b, diag, wl, wb read, x
+ * written; one word per value, 4 bytes in the mixed mode, 8 in FP64, per right-hand side). */
 enum { EBIT_KT_SMOOTH_L0 = 1 };
 ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class);
 ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes_per_launch);
+
+/* Options: EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the
+ * context's stream (solver loops as conditional WHILE nodes, no host round trip inside a
+ * step); 0 launches every kernel from the host.  Graph mode needs a non-default stream. */
+enum { EBIT_OPT_GRAPH = 1 };
+ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value);
 
 const char* ebit_last_error(const ebit_ctx* ctx);
 void ebit_destroy(ebit_ctx* ctx);

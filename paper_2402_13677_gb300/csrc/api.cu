@@ -35,8 +35,8 @@ struct Instance {
     double2 *u_l, *u_v, *us_l, *us_v, *gc;
     double *ufx_l, *ufx_v, *ufy_l, *ufy_v;
     // linear systems
-    double *op_cd, *op_dd, *op_wx, *op_wy, *op_b, *op_x;
-    double *vb[4], *vx[4];
+    double *op_cd, *op_dd, *op_wl, *op_wb, *op_b, *op_x;
+    double2 *vbx, *vby, *vxx, *vxy;   // viscous RHS / solutions, liquid and vapour interleaved
     // band compaction + extension values
     int *band_list, *band_count, *band_idx;
     double *ext[4];
@@ -51,6 +51,10 @@ struct Instance {
     long long nstep = 0;
     double stats[6] = {0, 0, 0, 0, 0, 0};   // iterations and residuals: energy, viscous, poisson
     bool noconv = false;
+    // CUDA graphs of one step, per sweep-order parity
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches[2] = {0, 0};   // kernel launches captured per graph (loop bodies once)
+    unsigned solved = 0;                     // solve slots written since the last statistics read
 };
 
 }  // namespace
@@ -60,9 +64,10 @@ struct ebit_ctx {
     cudaStream_t stream = nullptr;
     ebit_allocator alloc{};
     bool has_alloc = false;
-    int* host_flags = nullptr;
+    SolveState* host_states = nullptr;   // pinned, Solver::NSLOT per instance
     std::string err;
     uint64_t launch0 = 0;
+    int use_graph = 1;
 };
 
 static ebit_status fail(ebit_ctx* ctx, ebit_status s, const std::string& msg) {
@@ -179,11 +184,14 @@ static void assign_ptrs(Instance& I, const std::function<char*(size_t)>& take, s
     I.ufy_v = (double*)take(nh * 8);
     I.op_cd = (double*)take(N * 8);
     I.op_dd = (double*)take(N * 8);
-    I.op_wx = (double*)take(nve * 8);
-    I.op_wy = (double*)take(nh * 8);
+    I.op_wl = (double*)take(N * 8);
+    I.op_wb = (double*)take(N * 8);
     I.op_b = (double*)take(N * 8);
     I.op_x = (double*)take(N * 8);
-    for (int k = 0; k < 4; ++k) { I.vb[k] = (double*)take(N * 8); I.vx[k] = (double*)take(N * 8); }
+    I.vbx = (double2*)take(N * 16);
+    I.vby = (double2*)take(N * 16);
+    I.vxx = (double2*)take(N * 16);
+    I.vxy = (double2*)take(N * 16);
     I.band_list = (int*)take(N * 4);
     I.band_count = (int*)take(256);
     I.band_idx = (int*)take(N * 4);
@@ -248,59 +256,76 @@ static void advance_interface(Instance& I, cudaStream_t st) {
     reconstruct_full(I, st);
 }
 
-static void record(Instance& I, int kind, const SolveResult& r) {
-    I.stats[kind] = r.iters;
-    I.stats[3 + kind] = r.rel_res;
-    if (!r.converged) I.noconv = true;
+enum { SLOT_ENERGY = 0, SLOT_VISC_X = 1, SLOT_VISC_Y = 2, SLOT_POISSON = 3 };
+
+static void do_solve(Instance& I, int slot, const double* b, double* x, int nr, cudaStream_t st) {
+    I.solver.slot = slot;
+    I.solved |= 1u << slot;
+    long long l0 = I.solver.launches;
+    I.solver.solve(I.op_cd, I.op_dd, I.op_wl, I.op_wb, b, x, nr, I.cfg.precision, I.cfg.rtol, I.cfg.max_iter, st);
+    count((int)(I.solver.launches - l0));
+}
+
+// solver statistics of the last step, read from the device slots (synchronises)
+static void collect_stats(Instance& I, cudaStream_t st, bool graph_step) {
+    unsigned m = I.solved;
+    I.solved = 0;
+    if (!m) return;
+    SolveResult r[4];
+    bool ok = true;
+    long long body = I.solver.body_size(), n = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (!(m & (1u << k))) continue;
+        r[k] = I.solver.read_result(k, I.cfg.precision, st);
+        ok = ok && r[k].converged;
+        // kernels executed inside the conditional loop bodies of a graph step
+        n += r[k].iters * body;
+        if (I.cfg.precision == EBIT_MIXED) n += 2 * r[k].outer - 1;
+    }
+    if (graph_step) g_launches += (uint64_t)n;
+    if (m & (1u << SLOT_ENERGY)) {
+        I.stats[0] = r[SLOT_ENERGY].iters;
+        I.stats[3] = r[SLOT_ENERGY].rel_res;
+    }
+    if (m & (1u << SLOT_VISC_X)) {
+        I.stats[1] = r[SLOT_VISC_X].iters + ((m & (1u << SLOT_VISC_Y)) ? r[SLOT_VISC_Y].iters : 0);
+        double w = r[SLOT_VISC_X].rel_res;
+        if ((m & (1u << SLOT_VISC_Y)) && r[SLOT_VISC_Y].rel_res > w) w = r[SLOT_VISC_Y].rel_res;
+        I.stats[4] = w;
+    }
+    if (m & (1u << SLOT_POISSON)) {
+        I.stats[2] = r[SLOT_POISSON].iters;
+        I.stats[5] = r[SLOT_POISSON].rel_res;
+    }
+    if (!ok) I.noconv = true;
 }
 
 static void solve_energy(Instance& I, cudaStream_t st) {
-    launch_energy_operator(I.g, I.p, I.flags, I.cseg, I.hpos, I.vpos, I.Ts_l, I.Ts_v, I.op_cd, I.op_dd, I.op_wx,
-                           I.op_wy, I.op_b, I.op_x, st);
+    launch_energy_operator(I.g, I.p, I.flags, I.cseg, I.hpos, I.vpos, I.Ts_l, I.Ts_v, I.op_cd, I.op_dd, I.op_wl,
+                           I.op_wb, I.op_b, I.op_x, st);
     count(1);
-    int l0 = I.solver.launches;
-    SolveResult r = I.solver.solve(I.op_cd, I.op_dd, I.op_wx, I.op_wy, I.op_b, I.op_x, I.cfg.precision, I.cfg.rtol,
-                                   I.cfg.max_iter, st);
-    count(I.solver.launches - l0);
-    record(I, 0, r);
+    do_solve(I, SLOT_ENERGY, I.op_b, I.op_x, 1, st);
     launch_split_T(I.g, I.flags, I.op_x, I.Ts_l, I.Ts_v, I.T_l, I.T_v, st);
     count(1);
 }
 
 static void momentum(Instance& I, cudaStream_t st) {
-    // S11: predictor, both phase fields (b/x order: lx, vx, ly, vy)
-    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vb, I.vx, st);
+    // S11: predictor; one two-RHS solve (liquid, vapour) per velocity component
+    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, st);
     count(1);
-    int iters = 0;
-    double worst = 0.0;
     for (int comp = 0; comp < 2; ++comp) {
-        launch_visc_operator(I.g, I.p, comp, I.vf, I.op_cd, I.op_dd, I.op_wx, I.op_wy, st);
+        launch_visc_operator(I.g, I.p, comp, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, st);
         count(1);
-        for (int ph = 0; ph < 2; ++ph) {
-            int k = comp * 2 + ph;
-            int l0 = I.solver.launches;
-            SolveResult r = I.solver.solve(I.op_cd, I.op_dd, I.op_wx, I.op_wy, I.vb[k], I.vx[k], I.cfg.precision,
-                                           I.cfg.rtol, I.cfg.max_iter, st);
-            count(I.solver.launches - l0);
-            iters += r.iters;
-            if (r.rel_res > worst) worst = r.rel_res;
-            if (!r.converged) I.noconv = true;
-        }
+        do_solve(I, comp == 0 ? SLOT_VISC_X : SLOT_VISC_Y, (const double*)(comp == 0 ? I.vbx : I.vby),
+                 (double*)(comp == 0 ? I.vxx : I.vxy), 2, st);
     }
-    I.stats[1] = iters;
-    I.stats[4] = worst;
-    double* s[4] = {I.vx[0], I.vx[1], I.vx[2], I.vx[3]};
-    launch_ustar(I.g, I.p, s, I.gc, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
+    launch_ustar(I.g, I.p, I.vxx, I.vxy, I.gc, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
     count(2);
     // S12: projection
-    launch_poisson_operator(I.g, I.p, I.vf, I.flags, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.op_cd, I.op_dd, I.op_wx,
-                            I.op_wy, I.op_b, st);
+    launch_poisson_operator(I.g, I.p, I.vf, I.flags, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.op_cd, I.op_dd, I.op_wl,
+                            I.op_wb, I.op_b, st);
     count(1);
-    int l0 = I.solver.launches;
-    SolveResult r = I.solver.solve(I.op_cd, I.op_dd, I.op_wx, I.op_wy, I.op_b, I.P, I.cfg.precision, I.cfg.rtol,
-                                   I.cfg.max_iter, st);
-    count(I.solver.launches - l0);
-    record(I, 2, r);
+    do_solve(I, SLOT_POISSON, I.op_b, I.P, 1, st);
     launch_project(I.g, I.p, I.P, I.vf, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.gc, I.us_l, I.us_v, I.u_l, I.u_v, st);
     count(2);
 }
@@ -349,8 +374,9 @@ static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
     return cuda_check(ctx, "run_stage");
 }
 
-static ebit_status check_status(ebit_ctx* ctx) {
+static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
     for (auto& I : ctx->inst) {
+        collect_stats(I, ctx->stream, graph_step);
         int s = 0;
         cudaMemcpyAsync(&s, I.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -388,6 +414,7 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         }
         for (int s = 0; s < 4; ++s)
             if (c.bc[s] < 0 || c.bc[s] > 2) { delete ctx; return EBIT_EINVAL; }
+        if (!Solver::supported(c.nx, c.ny)) { delete ctx; return EBIT_EINVAL; }
         Instance& I = ctx->inst[b];
         I.cfg = c;
         I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0;
@@ -405,8 +432,11 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         layout(I, (char*)mem, assign_ptrs);
         cudaMemsetAsync(mem, 0, bytes, ctx->stream);
     }
-    if (cudaMallocHost(&ctx->host_flags, 64 * sizeof(int)) != cudaSuccess) { ebit_destroy(ctx); return EBIT_ENOMEM; }
-    for (auto& I : ctx->inst) I.solver.host_flags = ctx->host_flags;
+    if (cudaMallocHost(&ctx->host_states, batch * Solver::NSLOT * sizeof(SolveState)) != cudaSuccess) {
+        ebit_destroy(ctx);
+        return EBIT_ENOMEM;
+    }
+    for (int b = 0; b < batch; ++b) ctx->inst[b].solver.st_host = ctx->host_states + b * Solver::NSLOT;
     ctx->launch0 = g_launches.load();
     ebit_status s = cuda_check(ctx, "ebit_init");
     if (s != EBIT_OK) { ebit_destroy(ctx); return s; }
@@ -539,22 +569,87 @@ ebit_status ebit_run_stage(ebit_ctx* ctx, int stage) {
     return check_status(ctx);
 }
 
+static ebit_status step_eager(ebit_ctx* ctx, Instance& I) {
+    for (int s = EBIT_STAGE_ADVECT_T; s <= EBIT_STAGE_DIAGNOSTICS; ++s) {
+        ebit_status r = run_stage(ctx, I, s);
+        if (r != EBIT_OK) return r;
+    }
+    return EBIT_OK;
+}
+
+// capture one whole step (stages ADVECT_T .. DIAGNOSTICS) into a graph; the solver loops
+// become conditional WHILE nodes, so replaying the graph needs no host round trip
+static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaGraphExec_t* out) {
+    cudaStream_t st = ctx->stream;
+    if (!st) return fail(ctx, EBIT_EINVAL, "graph mode needs a non-default stream");
+    long long nstep = I.nstep;
+    uint64_t l0 = g_launches.load();
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return fail(ctx, EBIT_ECUDA, "cudaStreamBeginCapture failed");
+    I.solver.use_graph = 1;
+    cudaStream_t s = st;
+    if (I.p.energy) {
+        launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, s);
+        extend_T(I, I.Ts_l, I.Ts_v, s);
+    }
+    advance_interface(I, s);
+    if (I.p.energy) {
+        solve_energy(I, s);
+        extend_T(I, I.T_l, I.T_v, s);
+    }
+    mass_flux(I, s);
+    ghost_velocity(I, s);
+    momentum(I, s);
+    diagnostics(I, s);
+    I.solver.use_graph = 0;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    I.nstep = nstep;
+    int par = (I.cfg.sweep_order == 0) ? 0 : (int)(nstep & 1);
+    I.graph_launches[par] = (long long)(g_launches.load() - l0);
+    g_launches -= (g_launches.load() - l0);   // counted at launch time instead
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return EBIT_OK;
+}
+
 ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
     if (!ctx || nsteps < 0) return EBIT_EINVAL;
     ebit_status worst = EBIT_OK;
     for (int n = 0; n < nsteps; ++n) {
         for (auto& I : ctx->inst) {
             if (!I.props_set) return fail(ctx, EBIT_EINVAL, "ebit_set_phase_props not called");
-            for (int s = EBIT_STAGE_ADVECT_T; s <= EBIT_STAGE_DIAGNOSTICS; ++s) {
-                ebit_status r = run_stage(ctx, I, s);
+            if (ctx->use_graph && ctx->stream) {
+                int par = (I.cfg.sweep_order == 0) ? 0 : (int)(I.nstep & 1);
+                if (!I.graph[par]) {
+                    ebit_status r = capture_step(ctx, I, &I.graph[par]);
+                    if (r != EBIT_OK) return r;
+                }
+                cudaGraphLaunch(I.graph[par], ctx->stream);
+                g_launches += (uint64_t)I.graph_launches[par];
+                I.solved = (I.p.energy ? 1u : 0u) | 2u | 4u | 8u;
+                I.nstep += 1;
+            } else {
+                ebit_status r = step_eager(ctx, I);
                 if (r != EBIT_OK) return r;
             }
         }
-        ebit_status s = check_status(ctx);
+        ebit_status s = check_status(ctx, ctx->use_graph && ctx->stream);
         if (s == EBIT_ENOCONV) worst = s;
         else if (s != EBIT_OK) return s;
     }
     return worst;
+}
+
+ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
+    if (!ctx) return EBIT_EINVAL;
+    if (option == EBIT_OPT_GRAPH) {
+        ctx->use_graph = value ? 1 : 0;
+        return EBIT_OK;
+    }
+    return fail(ctx, EBIT_EINVAL, "unknown option");
 }
 
 ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n) {
@@ -573,7 +668,12 @@ uint64_t ebit_launch_count(const ebit_ctx* ctx) { return ctx ? g_launches.load()
 
 ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class) {
     if (!ctx || kernel_class != EBIT_KT_SMOOTH_L0) return EBIT_EINVAL;
-    for (auto& I : ctx->inst) I.solver.time_begin();
+    for (auto& I : ctx->inst) {
+        KTimer z[2];
+        for (auto& t : z) { t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; }
+        cudaMemcpyAsync(I.solver.timer, z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
+    }
+    cudaStreamSynchronize(ctx->stream);
     return cuda_check(ctx, "ebit_timing_begin");
 }
 
@@ -582,14 +682,18 @@ ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches,
     double tot = 0.0, bytes = 0.0;
     uint64_t n = 0;
     for (auto& I : ctx->inst) {
-        tot += I.solver.time_end_ms();
-        n += (uint64_t)I.solver.timed_launches;
-        // algorithmic bytes of one red or black half-sweep of the stored-coefficient
-        // five-point Gauss-Seidel: x read for every cell (neighbours), b and diag read and x
-        // written for the half being updated, both face arrays read (every face borders one
-        // cell of each colour): 4.5 words per cell
+        KTimer t[2];
+        cudaMemcpyAsync(t, I.solver.timer, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        tot += (t[0].total_ns + t[1].total_ns) * 1e-6;
+        n += t[0].launches + t[1].launches;
+        // algorithmic bytes per cell of the finest-grid tiled smoother kernels, NR right-hand
+        // sides averaged over the solves of a step as 1: pre = b, diag, wl, wb read, x and the
+        // coarse b (a quarter) written; post = x, the coarse x (a quarter), b, diag, wl, wb
+        // read, x written
         double word = I.cfg.precision == EBIT_MIXED ? 4.0 : 8.0;
-        bytes += (double)I.g.nx * I.g.ny * 4.5 * word * (double)I.solver.timed_launches;
+        double cells = (double)I.g.nx * I.g.ny;
+        bytes += cells * word * ((1 + 3 + 1 + 0.25) * t[0].launches + (1 + 0.25 + 1 + 3 + 1) * t[1].launches);
     }
     *total_ms = tot;
     *launches = n;
@@ -609,7 +713,13 @@ void ebit_destroy(ebit_ctx* ctx) {
         else cudaFree(I.arena);
         I.arena = nullptr;
     }
-    if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
+    for (auto& I : ctx->inst) {
+        for (auto& gx : I.graph)
+            if (gx) cudaGraphExecDestroy(gx);
+        for (auto& s : I.solver.aux)
+            if (s) cudaStreamDestroy(s);
+    }
+    if (ctx->host_states) cudaFreeHost(ctx->host_states);
     delete ctx;
 }
 

@@ -243,9 +243,9 @@ __device__ inline double mu_mix(const Phys& p, double vf) { return p.mu_l * vf +
 
 // viscous Helmholtz operator for velocity component comp (integrated form):
 //   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where comp is Dirichlet (odd),
-//   wx/wy = mean of the two cells' mu_c (interior faces), 0 on boundary faces.
+//   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces).
 __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restrict__ vf, double* __restrict__ cd,
-                                double* __restrict__ dd, double* __restrict__ wx, double* __restrict__ wy) {
+                                double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -259,19 +259,16 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
     if (j == 0 && vel_odd(g.bc[2], comp, 1)) d += 2.0 * mu;
     if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) d += 2.0 * mu;
     dd[c] = d;
-    wx[veidx(g, i, j)] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) : 0.0;
-    if (i == g.nx - 1) wx[veidx(g, g.nx, j)] = 0.0;
-    wy[hidx(g, i, j)] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) : 0.0;
-    if (j == g.ny - 1) wy[hidx(g, i, g.ny)] = 0.0;
+    wl[c] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) : 0.0;
+    wb[c] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) : 0.0;
 }
 
-// RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c), both phases and
-// both components; also the initial guesses (current velocity)
+// RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields,
+// one two-RHS system per component (liquid, vapour interleaved); initial guesses = current u
 __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const double* __restrict__ vf,
                           const double2* __restrict__ u_l, const double2* __restrict__ u_v,
-                          const double2* __restrict__ gc, double* __restrict__ b_lx, double* __restrict__ b_vx,
-                          double* __restrict__ b_ly, double* __restrict__ b_vy, double* __restrict__ x_lx,
-                          double* __restrict__ x_vx, double* __restrict__ x_ly, double* __restrict__ x_vy) {
+                          const double2* __restrict__ gc, double2* __restrict__ bx, double2* __restrict__ by,
+                          double2* __restrict__ xx, double2* __restrict__ xy) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -279,23 +276,23 @@ __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const do
     double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
-    b_lx[c] = coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x);
-    b_ly[c] = coef * (advect_one(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y);
-    b_vx[c] = coef * (advect_one(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x);
-    b_vy[c] = coef * (advect_one(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y);
-    x_lx[c] = ul.x; x_ly[c] = ul.y; x_vx[c] = uv.x; x_vy[c] = uv.y;
+    bx[c] = make_double2(coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
+                         coef * (advect_one(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x));
+    by[c] = make_double2(coef * (advect_one(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y),
+                         coef * (advect_one(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y));
+    xx[c] = make_double2(ul.x, uv.x);
+    xy[c] = make_double2(ul.y, uv.y);
 }
 
 // u** = u* - dt gc (cells); u_f* = c->f mean of u** + dt g (faces; outflow faces take the
 // boundary cell, wall/symmetry faces are 0)
-__global__ void k_ustar(Grid g, Phys p, const double* __restrict__ s_lx, const double* __restrict__ s_vx,
-                        const double* __restrict__ s_ly, const double* __restrict__ s_vy,
+__global__ void k_ustar(Grid g, Phys p, const double2* __restrict__ sx, const double2* __restrict__ sy,
                         const double2* __restrict__ gc, double2* __restrict__ us_l, double2* __restrict__ us_v) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.nx * g.ny) return;
-    double2 a = gc[c];
-    us_l[c] = make_double2(s_lx[c] - p.dt * a.x, s_ly[c] - p.dt * a.y);
-    us_v[c] = make_double2(s_vx[c] - p.dt * a.x, s_vy[c] - p.dt * a.y);
+    double2 a = gc[c], x = sx[c], y = sy[c];
+    us_l[c] = make_double2(x.x - p.dt * a.x, y.x - p.dt * a.y);
+    us_v[c] = make_double2(x.y - p.dt * a.x, y.y - p.dt * a.y);
 }
 
 __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, const double2* __restrict__ us_v,
@@ -360,13 +357,13 @@ __device__ inline double face_vf_y(const Grid& g, const double* vf, int i, int j
     return 0.5 * (vf[cidx(g, i, j - 1)] + vf[cidx(g, i, j)]);
 }
 
-// Poisson operator: wx/wy = dt / rho_f (interior), dd = 2 dt / rho_f on outflow faces,
+// Poisson operator: wl/wb = dt / rho_f (interior faces), dd = 2 dt / rho_f on outflow faces,
 // b = -h * (undivided divergence of the face field of the cell's phase); x0 = p
 __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf, const uint8_t* __restrict__ flags,
                                    const double* __restrict__ fx_l, const double* __restrict__ fx_v,
                                    const double* __restrict__ fy_l, const double* __restrict__ fy_v,
-                                   double* __restrict__ cd, double* __restrict__ dd, double* __restrict__ wx,
-                                   double* __restrict__ wy, double* __restrict__ b) {
+                                   double* __restrict__ cd, double* __restrict__ dd, double* __restrict__ wl,
+                                   double* __restrict__ wb, double* __restrict__ b) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -378,10 +375,8 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     if (j == 0 && g.bc[2] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, 0));
     if (j == g.ny - 1 && g.bc[3] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, g.ny));
     dd[c] = d;
-    wx[veidx(g, i, j)] = i > 0 ? p.dt / rho_mix(p, face_vf_x(g, vf, i, j)) : 0.0;
-    if (i == g.nx - 1) wx[veidx(g, g.nx, j)] = 0.0;
-    wy[hidx(g, i, j)] = j > 0 ? p.dt / rho_mix(p, face_vf_y(g, vf, i, j)) : 0.0;
-    if (j == g.ny - 1) wy[hidx(g, i, g.ny)] = 0.0;
+    wl[c] = i > 0 ? p.dt / rho_mix(p, face_vf_x(g, vf, i, j)) : 0.0;
+    wb[c] = j > 0 ? p.dt / rho_mix(p, face_vf_y(g, vf, i, j)) : 0.0;
     const double* fx = (flags[c] & F_CCOL) ? fx_l : fx_v;
     const double* fy = (flags[c] & F_CCOL) ? fy_l : fy_v;
     double div = (fx[veidx(g, i + 1, j)] - fx[veidx(g, i, j)]) + (fy[hidx(g, i, j + 1)] - fy[hidx(g, i, j)]);
@@ -588,30 +583,30 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, c
 }
 
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
-                          double* wx, double* wy, cudaStream_t st) {
-    k_visc_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, comp, vf, cd, dd, wx, wy);
+                          double* wl, double* wb, cudaStream_t st) {
+    k_visc_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, comp, vf, cd, dd, wl, wb);
 }
 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
-                    const double2* gc, double* b[4], double* x[4], cudaStream_t st) {
+                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st) {
     k_mom_rhs<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
-                                                         p.dt / g.h, vf, u_l, u_v, gc, b[0], b[1], b[2], b[3],
-                                                         x[0], x[1], x[2], x[3]);
+                                                         p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
 }
 
-void launch_ustar(const Grid& g, const Phys& p, double* s[4], const double2* gc, double2* us_l, double2* us_v,
-                  double* fx_l, double* fx_v, double* fy_l, double* fy_v, cudaStream_t st) {
+void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
+                  double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
+                  cudaStream_t st) {
     int N = g.nx * g.ny;
-    k_ustar<<<div_up(N, 256), 256, 0, st>>>(g, p, s[0], s[1], s[2], s[3], gc, us_l, us_v);
+    k_ustar<<<div_up(N, 256), 256, 0, st>>>(g, p, sx, sy, gc, us_l, us_v);
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
     k_face_star<<<div_up(nf, 256), 256, 0, st>>>(g, p, us_l, us_v, fx_l, fx_v, fy_l, fy_v);
 }
 
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
                              const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
-                             double* cd, double* dd, double* wx, double* wy, double* b, cudaStream_t st) {
+                             double* cd, double* dd, double* wl, double* wb, double* b, cudaStream_t st) {
     k_poisson_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v, cd, dd,
-                                                                  wx, wy, b);
+                                                                  wl, wb, b);
 }
 
 void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* fx_l, double* fx_v,

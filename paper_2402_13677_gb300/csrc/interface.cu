@@ -583,13 +583,13 @@ __device__ double link_theta(const Grid& g, const uint16_t* cseg, const double* 
 
 // Energy operator of the combined (block-diagonal) two-phase system, integrated form:
 //   cd = h^2 (rho cp)_k / dt,   dd = sum_cut lambda_k / theta + sum_Tfixed 2 lambda_k,
-//   wx/wy = lambda_k between two cells of the same phase, 0 across the interface,
+//   wl/wb (left/bottom face) = lambda_k between two cells of the same phase, 0 across the interface,
 //   b = cd T*_k + sum_cut lambda_k T_sat / theta + sum 2 lambda_k T_w,  x0 = T*_k.
 __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ flags,
                                   const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                                   const double* __restrict__ vpos, const double* __restrict__ Ts_l,
                                   const double* __restrict__ Ts_v, double* __restrict__ cd,
-                                  double* __restrict__ dd, double* __restrict__ wx, double* __restrict__ wy,
+                                  double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb,
                                   double* __restrict__ b, double* __restrict__ x0) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
@@ -624,15 +624,9 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     dd[c] = dsum;
     b[c] = rhs;
     x0[c] = ts;
-    // faces: x-face (i, j) is the left face of cell (i, j); y-face likewise the bottom
-    double w = 0.0;
-    if (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) w = lam;
-    wx[veidx(g, i, j)] = w;
-    if (i == g.nx - 1) wx[veidx(g, g.nx, j)] = 0.0;
-    w = 0.0;
-    if (j > 0 && (flags[cidx(g, i, j - 1)] & F_CCOL) == k) w = lam;
-    wy[hidx(g, i, j)] = w;
-    if (j == g.ny - 1) wy[hidx(g, i, g.ny)] = 0.0;
+    // left and bottom face weights of the cell (domain faces carry none)
+    wl[c] = (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) ? lam : 0.0;
+    wb[c] = (j > 0 && (flags[cidx(g, i, j - 1)] & F_CCOL) == k) ? lam : 0.0;
 }
 
 // ---------------------------------------------------------------------------------
@@ -728,10 +722,10 @@ void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, cons
 
 void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,
                             const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
-                            double* cd, double* dd, double* wx, double* wy, double* b, double* x0,
+                            double* cd, double* dd, double* wl, double* wb, double* b, double* x0,
                             cudaStream_t st) {
     k_energy_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, flags, cseg, hpos, vpos, Ts_l, Ts_v, cd,
-                                                                 dd, wx, wy, b, x0);
+                                                                 dd, wl, wb, b, x0);
 }
 
 void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos,

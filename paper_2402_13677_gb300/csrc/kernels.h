@@ -19,7 +19,7 @@ void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, cons
                   double* hpos_n, double* vpos_n, int* status, cudaStream_t st);
 void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,
                             const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
-                            double* cd, double* dd, double* wx, double* wy, double* b, double* x0, cudaStream_t st);
+                            double* cd, double* dd, double* wl, double* wb, double* b, double* x0, cudaStream_t st);
 void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos, const double* vpos,
                       const double* T_l, const double* T_v, double* mdot, cudaStream_t st);
 
@@ -35,14 +35,15 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, c
                            const uint8_t* vcol, const double* hpos, const double* vpos, double2* u_l, double2* u_v,
                            double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st);
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
-                          double* wx, double* wy, cudaStream_t st);
+                          double* wl, double* wb, cudaStream_t st);
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
-                    const double2* gc, double* b[4], double* x[4], cudaStream_t st);
-void launch_ustar(const Grid& g, const Phys& p, double* s[4], const double2* gc, double2* us_l, double2* us_v,
-                  double* fx_l, double* fx_v, double* fy_l, double* fy_v, cudaStream_t st);
+                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st);
+void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
+                  double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
+                  cudaStream_t st);
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags, const double* fx_l,
                              const double* fx_v, const double* fy_l, const double* fy_v, double* cd, double* dd,
-                             double* wx, double* wy, double* b, cudaStream_t st);
+                             double* wl, double* wb, double* b, cudaStream_t st);
 void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* fx_l, double* fx_v,
                     double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l,
                     double2* u_v, cudaStream_t st);

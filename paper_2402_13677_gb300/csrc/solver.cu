@@ -1,25 +1,37 @@
-// Matrix-free-coefficient multigrid-preconditioned conjugate gradients for the three
-// implicit solves of the step (energy diffusion, viscous Helmholtz, ghost-fluid Poisson).
+// Multigrid-preconditioned conjugate gradients for the implicit solves of the step
+// (energy diffusion, viscous Helmholtz, ghost-fluid Poisson).
 //
-// All three operators have the integrated five-point form
-//     (A x)_i = (cd_i + dd_i + sum_f w_f) x_i - sum_f w_f x_nbr(f)
-// with cd the h^2 (rho cp / dt or rho / dt) term, dd the Dirichlet contributions
-// (ghost-fluid interface links, fixed-temperature walls, no-slip walls, outflow pressure)
-// and w the face conductances.  The preconditioner is a symmetric V(2,2)-cycle:
-// red-black Gauss-Seidel (red-black before, black-red after), restriction = sum of the four
-// children, prolongation = injection, coarse operators re-discretised (cd summed, dd summed
-// and halved, face weights averaged along the coarse face), and a fixed symmetric sweep
-// sequence on the coarsest grid, so CG sees a fixed SPD preconditioner.
+// Operator (integrated five-point form, cell-centred coefficients):
+//     (A x)_i = diag_i x_i - wl_i x_{i-1} - wl_{i+1} x_{i+1} - wb_i x_{i-nx} - wb_{i+nx} x_{i+nx}
+//     diag_i  = cd_i + dd_i + wl_i + wl_{i+1} + wb_i + wb_{i+nx}
+// with cd the h^2 (rho cp / dt or rho / dt) term, dd the Dirichlet contributions (ghost-fluid
+// interface links, fixed-temperature or no-slip walls, outflow pressure), wl/wb the left and
+// bottom face conductances (zero on domain faces).
 //
-// Precision modes (precision pattern of the method's GPU design):
+// Preconditioner: one symmetric V(2,2)-cycle.  Red-black Gauss-Seidel (red-black before,
+// black-red after), restriction = sum of the four children, prolongation = injection, coarse
+// operators re-discretised (cd summed, dd summed and halved, face weights averaged along the
+// coarse face), a fixed symmetric sweep sequence on the coarsest grid.
+//
+// Kernel structure (few launches per CG iteration):
+//   * large levels: k_pre  = 2 red-black sweeps from zero + residual + restriction, and
+//                   k_post = prolongation + 2 black-red sweeps (+ r.z at the finest level),
+//     each a shared-memory tile with a halo of recomputed cells, so one launch performs
+//     several Gauss-Seidel half-sweeps; halo cells are recomputed from the same inputs with
+//     the same formula, so the result equals global red-black Gauss-Seidel exactly;
+//   * every level of at most 4096 cells: one single-block kernel (k_small) runs the rest of
+//     the V-cycle in shared memory;
+//   * CG: k_apply (p = z + beta p fused into q = A p, p.q) and k_update (x, r, r.r, test).
+// Loop control lives on the device (SolveState); kernels can drive CUDA-graph conditional
+// WHILE nodes (cudaGraphSetConditional), or the host can poll the state.
+//
+// Precision modes:
 //   FP64  : CG + V-cycle in double.
 //   MIXED : iterative refinement: r = b - A x in FP64, correction A e = r solved in FP32 by
-//           the same MG-PCG to a loose tolerance, x += e in FP64, until ||r|| <= rtol ||b||.
+//           the same MG-PCG to a relative 1e-4, x += e in FP64, until ||r|| <= rtol ||b||.
 //
-// Reductions are deterministic: per-block partial sums, the last block adds them in block
-// order.  Scalars (alpha, beta, r.z, convergence flags) stay on the device; every kernel
-// returns at once when the solve has converged, so the host may enqueue iterations ahead
-// and only polls the convergence word every few iterations.
+// Reductions are deterministic: per-block partial sums, the last block adds them in block order.
+#include <cfloat>
 #include <cstdio>
 #include "common.cuh"
 #include "kernels.h"
@@ -27,33 +39,53 @@
 
 namespace ebit {
 
-constexpr int RB = 256;   // threads per block for reductions / stencils
-constexpr int NRED = 608; // blocks of grid-stride kernels (4 x 152 SMs)
+constexpr int RB = 256;          // threads of grid-stride kernels
+constexpr int NRED = 608;        // blocks of grid-stride kernels (4 x 152 SMs)
+constexpr int SMALL_MAX = 4096;  // levels with at most this many cells run inside k_small
+constexpr int TX = 32, TY = 32;  // tile of the large-level kernels
+constexpr int NU = 2;            // smoothing sweeps (red-black pairs) before and after
+constexpr int COARSE_PAIRS = 24; // symmetric sweeps on the coarsest grid
 
-// scalar slots (double) and flag slots (int)
-enum { S_RZ = 0, S_PQ, S_RR, S_TOL2, S_BB, S_RR0, S_COUNT };
-enum { FL_DONE = 0, FL_ITERS, FL_ODONE, FL_OITERS, FL_COUNT };
-
-template <typename T>
-struct LevelView {
-    int nx, ny;
-    const T* diag;
-    const T* wx;
-    const T* wy;
+template <typename T, int NR>
+struct alignas(sizeof(T) * NR) Vec {
+    T v[NR];
 };
 
 template <typename T>
-__device__ inline T nbr_sum(const LevelView<T>& L, const T* __restrict__ x, int i, int j) {
-    T s = T(0);
-    int c = j * L.nx + i;
-    if (i > 0) s += L.wx[j * (L.nx + 1) + i] * x[c - 1];
-    if (i < L.nx - 1) s += L.wx[j * (L.nx + 1) + i + 1] * x[c + 1];
-    if (j > 0) s += L.wy[j * L.nx + i] * x[c - L.nx];
-    if (j < L.ny - 1) s += L.wy[(j + 1) * L.nx + i] * x[c + L.nx];
-    return s;
-}
+struct Lev {
+    int nx, ny;
+    const T* diag;
+    const T* wl;
+    const T* wb;
+};
 
-__device__ inline bool skip(const int* fl) { return fl[FL_DONE] != 0 || fl[FL_ODONE] != 0; }
+__device__ inline bool skip(const SolveState* s) { return s->done != 0 || s->odone != 0; }
+
+__device__ inline unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ inline void timer_begin(KTimer* tm) {
+    if (tm && threadIdx.x == 0) atomicMin(&tm->start, gtimer());
+}
+__device__ inline void timer_end(KTimer* tm) {
+    if (!tm) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMax(&tm->end, gtimer());
+        __threadfence();
+        unsigned int n = gridDim.x * gridDim.y;
+        if (atomicAdd(&tm->ticket, 1u) == n - 1) {
+            unsigned long long s = atomicAdd(&tm->start, 0ull), e = atomicAdd(&tm->end, 0ull);
+            tm->total_ns += e > s ? e - s : 0ull;
+            tm->launches += 1;
+            tm->start = ~0ull;
+            tm->end = 0ull;
+            tm->ticket = 0u;
+        }
+    }
+}
 
 // ---- block reductions ---------------------------------------------------------------
 __device__ inline double bsum(double v, double* sh) {
@@ -70,278 +102,631 @@ __device__ inline double bsum(double v, double* sh) {
     return r;
 }
 
-// write this block's partial; returns true in thread 0 of the last block, with the total in *tot
-__device__ inline bool reduce_finish(double v, double* partial, unsigned* ticket, double* tot) {
+// Reduce NV per-thread values over the grid: returns true in thread 0 of the last block,
+// with the totals in tot[0..NV).  partial has room for NV x (number of blocks) doubles.
+template <int NV>
+__device__ inline bool grid_reduce(const double* v, double* partial, unsigned* ticket, double* tot) {
     __shared__ double sh[32];
     __shared__ bool last;
-    double r = bsum(v, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    int nb = gridDim.x * gridDim.y;
+    int bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double r = bsum(v[k], sh);
+        if (threadIdx.x == 0) partial[k * nb + bid] = r;
+    }
     __threadfence();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile double*)partial)[b];
-    s = bsum(s, sh);
-    if (threadIdx.x == 0) { *tot = s; *ticket = 0u; }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += ((volatile double*)partial)[k * nb + b];
+        s = bsum(s, sh);
+        if (threadIdx.x == 0) tot[k] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
     return threadIdx.x == 0;
 }
 
+__device__ inline void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
+    if (use) cudaGraphSetConditional(h, v);
+}
+
 // ---- operator setup -------------------------------------------------------------------
+// level 0 in precision T from the FP64 cell-centred operator
 template <typename T>
-__global__ void k_make_diag(int nx, int ny, const double* __restrict__ cd, const double* __restrict__ dd,
-                            const double* __restrict__ wx, const double* __restrict__ wy, T* __restrict__ diag,
-                            T* __restrict__ wx_o, T* __restrict__ wy_o) {
+__global__ void k_setup0(int nx, int ny, const double* __restrict__ cd, const double* __restrict__ dd,
+                         const double* __restrict__ wl, const double* __restrict__ wb, T* __restrict__ diag,
+                         T* __restrict__ owl, T* __restrict__ owb, T* __restrict__ ocd, T* __restrict__ odd) {
     int N = nx * ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int i = c % nx, j = c / nx;
-        double a = wx[j * (nx + 1) + i], b = wx[j * (nx + 1) + i + 1];
-        double d = wy[j * nx + i], e = wy[(j + 1) * nx + i];
-        diag[c] = (T)(cd[c] + dd[c] + a + b + d + e);
-        if (wx_o) {
-            wx_o[j * (nx + 1) + i] = (T)a;
-            if (i == nx - 1) wx_o[j * (nx + 1) + nx] = (T)b;
-            wy_o[j * nx + i] = (T)d;
-            if (j == ny - 1) wy_o[ny * nx + i] = (T)e;
-        }
+        double r = i < nx - 1 ? wl[c + 1] : 0.0;
+        double t = j < ny - 1 ? wb[c + nx] : 0.0;
+        diag[c] = (T)(cd[c] + dd[c] + wl[c] + r + wb[c] + t);
+        owl[c] = (T)wl[c];
+        owb[c] = (T)wb[c];
+        ocd[c] = (T)cd[c];
+        odd[c] = (T)dd[c];
     }
 }
 
-// coarse operator from a fine one (cd summed, dd summed and halved, faces averaged)
-template <typename Tc>
-__global__ void k_coarsen(int fnx, int fny, const double* __restrict__ fcd, const double* __restrict__ fdd,
-                          const double* __restrict__ fwx, const double* __restrict__ fwy, double* __restrict__ ccd,
-                          double* __restrict__ cdd, double* __restrict__ cwx, double* __restrict__ cwy,
-                          Tc* __restrict__ cdiag, Tc* __restrict__ cwx_t, Tc* __restrict__ cwy_t) {
+template <typename T>
+__device__ inline void coarsen_cell(int fnx, const T* fcd, const T* fdd, const T* fwl, const T* fwb, int nx, int ny,
+                                    int I, int J, T* ccd, T* cdd, T* cwl, T* cwb, T* cdiag) {
+    int f = (2 * J) * fnx + 2 * I;
+    T s_cd = fcd[f] + fcd[f + 1] + fcd[f + fnx] + fcd[f + fnx + 1];
+    T s_dd = T(0.5) * (fdd[f] + fdd[f + 1] + fdd[f + fnx] + fdd[f + fnx + 1]);
+    T wl = T(0.5) * (fwl[f] + fwl[f + fnx]);
+    T wb = T(0.5) * (fwb[f] + fwb[f + 1]);
+    T wr = I < nx - 1 ? T(0.5) * (fwl[f + 2] + fwl[f + 2 + fnx]) : T(0);
+    T wt = J < ny - 1 ? T(0.5) * (fwb[f + 2 * fnx] + fwb[f + 2 * fnx + 1]) : T(0);
+    int c = J * nx + I;
+    ccd[c] = s_cd;
+    cdd[c] = s_dd;
+    cwl[c] = wl;
+    cwb[c] = wb;
+    cdiag[c] = s_cd + s_dd + wl + wr + wb + wt;
+}
+
+template <typename T>
+__global__ void k_coarsen(int fnx, int fny, const T* __restrict__ fcd, const T* __restrict__ fdd,
+                          const T* __restrict__ fwl, const T* __restrict__ fwb, T* __restrict__ ccd,
+                          T* __restrict__ cdd, T* __restrict__ cwl, T* __restrict__ cwb, T* __restrict__ cdiag) {
     int nx = fnx / 2, ny = fny / 2;
     int N = nx * ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int I = c % nx, J = c / nx;
-        int f00 = (2 * J) * fnx + 2 * I;
-        double s_cd = fcd[f00] + fcd[f00 + 1] + fcd[f00 + fnx] + fcd[f00 + fnx + 1];
-        double s_dd = 0.5 * (fdd[f00] + fdd[f00 + 1] + fdd[f00 + fnx] + fdd[f00 + fnx + 1]);
-        auto fx = [&](int fi, int fj) { return fwx[fj * (fnx + 1) + fi]; };
-        auto fy = [&](int fi, int fj) { return fwy[fj * fnx + fi]; };
-        double wl = 0.5 * (fx(2 * I, 2 * J) + fx(2 * I, 2 * J + 1));
-        double wr = 0.5 * (fx(2 * I + 2, 2 * J) + fx(2 * I + 2, 2 * J + 1));
-        double wb = 0.5 * (fy(2 * I, 2 * J) + fy(2 * I + 1, 2 * J));
-        double wt = 0.5 * (fy(2 * I, 2 * J + 2) + fy(2 * I + 1, 2 * J + 2));
-        ccd[c] = s_cd;
-        cdd[c] = s_dd;
-        cwx[J * (nx + 1) + I] = wl;
-        if (I == nx - 1) cwx[J * (nx + 1) + nx] = wr;
-        cwy[J * nx + I] = wb;
-        if (J == ny - 1) cwy[ny * nx + I] = wt;
-        cdiag[c] = (Tc)(s_cd + s_dd + wl + wr + wb + wt);
-        cwx_t[J * (nx + 1) + I] = (Tc)wl;
-        if (I == nx - 1) cwx_t[J * (nx + 1) + nx] = (Tc)wr;
-        cwy_t[J * nx + I] = (Tc)wb;
-        if (J == ny - 1) cwy_t[ny * nx + I] = (Tc)wt;
-    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+        coarsen_cell(fnx, fcd, fdd, fwl, fwb, nx, ny, c % nx, c / nx, ccd, cdd, cwl, cwb, cdiag);
 }
 
-// ---- smoother, transfer, coarse solve --------------------------------------------------
-template <typename T>
-__global__ void k_smooth(LevelView<T> L, const T* __restrict__ b, T* __restrict__ x, int color, int zero,
-                         const int* __restrict__ fl) {
-    if (skip(fl)) return;
-    int N = L.nx * L.ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % L.nx, j = c / L.nx;
-        if (((i + j) & 1) != color) {
-            if (zero) x[c] = T(0);
-            continue;
+// ---- large-level kernels: shared-memory tiles with recomputed halos ---------------------
+// smem layout per region cell: x[NR], b[NR] (type T) then diag, wl, wb
+template <typename T, int NR, int H>
+struct Region {
+    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, N = SX * SY;
+    T* x;
+    T* b;
+    T* d;
+    T* wl;
+    T* wb;
+    __device__ Region(unsigned char* base) {
+        x = (T*)base;
+        b = x + NR * N;
+        d = b + NR * N;
+        wl = d + N;
+        wb = wl + N;
+    }
+    static constexpr size_t bytes() { return (size_t)N * (2 * NR + 3) * sizeof(T); }
+};
+
+// one Gauss-Seidel half-sweep of colour `color` over region cells at distance >= s from its edge
+template <typename T, int NR, int H>
+__device__ inline void region_sweep(Region<T, NR, H>& R, int gx0, int gy0, int nx, int ny, int s, int color) {
+    constexpr int SX = Region<T, NR, H>::SX, SY = Region<T, NR, H>::SY;
+    int w = SX - 2 * s, hgt = SY - 2 * s;
+    for (int k = threadIdx.x; k < w * hgt; k += blockDim.x) {
+        int rx = s + k % w, ry = s + k / w;
+        int gi = gx0 + rx, gj = gy0 + ry;
+        if (gi < 0 || gi >= nx || gj < 0 || gj >= ny || ((gi + gj) & 1) != color) continue;
+        int q = ry * SX + rx;
+        T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + SX];
+        T d = R.d[q];
+#pragma unroll
+        for (int k2 = 0; k2 < NR; ++k2) {
+            T acc = R.b[q * NR + k2] + wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
+                    wb * R.x[(q - SX) * NR + k2] + wt * R.x[(q + SX) * NR + k2];
+            R.x[q * NR + k2] = acc / d;
         }
-        T s = zero ? T(0) : nbr_sum(L, x, i, j);
-        x[c] = (b[c] + s) / L.diag[c];
     }
-}
-
-template <typename T>
-__global__ void k_restrict_residual(LevelView<T> F, const T* __restrict__ b, const T* __restrict__ x,
-                                    T* __restrict__ bc, const int* __restrict__ fl) {
-    if (skip(fl)) return;
-    int nx = F.nx / 2, ny = F.ny / 2;
-    int N = nx * ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int I = c % nx, J = c / nx;
-        T s = T(0);
-        for (int b2 = 0; b2 < 2; ++b2)
-            for (int a2 = 0; a2 < 2; ++a2) {
-                int i = 2 * I + a2, j = 2 * J + b2;
-                int f = j * F.nx + i;
-                s += b[f] - (F.diag[f] * x[f] - nbr_sum(F, x, i, j));
-            }
-        bc[c] = s;
-    }
-}
-
-template <typename T>
-__global__ void k_prolong(int fnx, int fny, const T* __restrict__ xc, T* __restrict__ x, const int* __restrict__ fl) {
-    if (skip(fl)) return;
-    int N = fnx * fny;
-    int cnx = fnx / 2;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % fnx, j = c / fnx;
-        x[c] += xc[(j >> 1) * cnx + (i >> 1)];
-    }
-}
-
-// coarsest grid, one block: `pairs` red-black sweeps then `pairs` black-red sweeps from zero
-template <typename T>
-__global__ void k_coarse_solve(LevelView<T> L, const T* __restrict__ b, T* __restrict__ x, int pairs,
-                               const int* __restrict__ fl) {
-    if (skip(fl)) return;
-    extern __shared__ unsigned char smem_raw[];
-    T* xs = reinterpret_cast<T*>(smem_raw);
-    int N = L.nx * L.ny;
-    for (int c = threadIdx.x; c < N; c += blockDim.x) xs[c] = T(0);
     __syncthreads();
-    for (int sweep = 0; sweep < 4 * pairs; ++sweep) {
-        int color = sweep < 2 * pairs ? (sweep & 1) : 1 - (sweep & 1);
-        for (int c = threadIdx.x; c < N; c += blockDim.x) {
-            int i = c % L.nx, j = c / L.nx;
-            if (((i + j) & 1) != color) continue;
-            xs[c] = (b[c] + nbr_sum(L, xs, i, j)) / L.diag[c];
+}
+
+template <typename T, int NR, int H>
+__device__ inline void region_load(Region<T, NR, H>& R, const Lev<T>& L, const T* __restrict__ b,
+                                   const T* __restrict__ x, const T* __restrict__ xc, int cnx, int gx0, int gy0) {
+    constexpr int SX = Region<T, NR, H>::SX, N = Region<T, NR, H>::N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        int rx = q % SX, ry = q / SX;
+        int gi = gx0 + rx, gj = gy0 + ry;
+        bool in = gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny;
+        int c = gj * L.nx + gi;
+        Vec<T, NR> bv, xv;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) { bv.v[k] = T(0); xv.v[k] = T(0); }
+        if (in) {
+            bv = reinterpret_cast<const Vec<T, NR>*>(b)[c];
+            if (x) {
+                xv = reinterpret_cast<const Vec<T, NR>*>(x)[c];
+                Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gj >> 1) * cnx + (gi >> 1)];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) xv.v[k] += cv.v[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NR; ++k) { R.b[q * NR + k] = bv.v[k]; R.x[q * NR + k] = xv.v[k]; }
+        R.d[q] = in ? L.diag[c] : T(1);
+        R.wl[q] = in ? L.wl[c] : T(0);
+        R.wb[q] = in ? L.wb[c] : T(0);
+    }
+    __syncthreads();
+}
+
+// k_pre: x = S^nu(0; b) on the tile (red-black order), coarse b = R (b - A x)
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x,
+                                              T* __restrict__ bc, const SolveState* __restrict__ st, KTimer* tm) {
+    if (skip(st)) return;
+    constexpr int H = 2 * NU + 1;
+    using Rg = Region<T, NR, H>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    timer_begin(tm);
+    Rg R(smem);
+    int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
+    region_load<T, NR, H>(R, L, b, nullptr, nullptr, 0, gx0, gy0);
+    for (int s = 1; s <= 2 * NU; ++s) region_sweep<T, NR, H>(R, gx0, gy0, L.nx, L.ny, s, (s - 1) & 1);
+    // write the tile's x
+    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
+        int rx = H + k % TX, ry = H + k / TX;
+        int gi = gx0 + rx, gj = gy0 + ry;
+        if (gi >= L.nx || gj >= L.ny) continue;
+        int q = ry * Rg::SX + rx;
+        Vec<T, NR> xv;
+#pragma unroll
+        for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = R.x[q * NR + k2];
+        reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
+    }
+    // residual of the tile, restricted (sum of four children)
+    int cnx = L.nx / 2, cny = L.ny / 2;
+    for (int k = threadIdx.x; k < (TX / 2) * (TY / 2); k += blockDim.x) {
+        int ci = blockIdx.x * (TX / 2) + k % (TX / 2), cj = blockIdx.y * (TY / 2) + k / (TX / 2);
+        if (ci >= cnx || cj >= cny) continue;
+        Vec<T, NR> acc;
+#pragma unroll
+        for (int k2 = 0; k2 < NR; ++k2) acc.v[k2] = T(0);
+        for (int d2 = 0; d2 < 4; ++d2) {
+            int gi = 2 * ci + (d2 & 1), gj = 2 * cj + (d2 >> 1);
+            int rx = gi - gx0, ry = gj - gy0;
+            int q = ry * Rg::SX + rx;
+            T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + Rg::SX], d = R.d[q];
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                T ax = d * R.x[q * NR + k2] - (wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
+                                               wb * R.x[(q - Rg::SX) * NR + k2] + wt * R.x[(q + Rg::SX) * NR + k2]);
+                acc.v[k2] += R.b[q * NR + k2] - ax;
+            }
+        }
+        reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
+    }
+    timer_end(tm);
+}
+
+// k_post: x += P xc, then black-red sweeps; at the finest level also r.z -> beta
+template <typename T, int NR, bool DOT>
+__global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b, T* __restrict__ x,
+                                               const T* __restrict__ xc, SolveState* st, double* partial,
+                                               unsigned* ticket, KTimer* tm) {
+    if (skip(st)) return;
+    constexpr int H = 2 * NU;
+    using Rg = Region<T, NR, H>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    timer_begin(tm);
+    Rg R(smem);
+    int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
+    region_load<T, NR, H>(R, L, b, x, xc, L.nx / 2, gx0, gy0);
+    for (int s = 1; s <= 2 * NU; ++s) region_sweep<T, NR, H>(R, gx0, gy0, L.nx, L.ny, s, ((s - 1) & 1) ^ 1);
+    double dot[NR];
+#pragma unroll
+    for (int k2 = 0; k2 < NR; ++k2) dot[k2] = 0.0;
+    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
+        int rx = H + k % TX, ry = H + k / TX;
+        int gi = gx0 + rx, gj = gy0 + ry;
+        if (gi >= L.nx || gj >= L.ny) continue;
+        int q = ry * Rg::SX + rx;
+        Vec<T, NR> xv;
+#pragma unroll
+        for (int k2 = 0; k2 < NR; ++k2) {
+            xv.v[k2] = R.x[q * NR + k2];
+            if (DOT) dot[k2] += (double)R.x[q * NR + k2] * (double)R.b[q * NR + k2];
+        }
+        reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
+    }
+    if (DOT) {
+        double tot[NR];
+        if (grid_reduce<NR>(dot, partial, ticket, tot)) {
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                double old = st->rz[k2];
+                st->beta[k2] = old != 0.0 ? tot[k2] / old : 0.0;
+                st->rz[k2] = tot[k2];
+            }
+        }
+    }
+    timer_end(tm);
+}
+
+// ---- small levels: the rest of the V-cycle in one block ---------------------------------
+struct SmallPlan {
+    int n;             // number of small levels (the first is `lev0`)
+    int nx[Solver::MAXLEV], ny[Solver::MAXLEV];
+    int soff[Solver::MAXLEV];   // cell offset of each small level inside the shared-memory arrays
+    size_t goff[Solver::MAXLEV]; // cell offset in the packed global level arrays
+};
+
+template <typename T, int NR>
+__device__ inline void small_sweep(const SmallPlan& P, int l, const T* __restrict__ diag, const T* __restrict__ wl,
+                                   const T* __restrict__ wb, T* xs, const T* bs, int color) {
+    int nx = P.nx[l], ny = P.ny[l];
+    const T* dg = diag + P.goff[l];
+    const T* gl = wl + P.goff[l];
+    const T* gb = wb + P.goff[l];
+    T* x = xs + (size_t)P.soff[l] * NR;
+    const T* b = bs + (size_t)P.soff[l] * NR;
+    for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
+        int i = c % nx, j = c / nx;
+        if (((i + j) & 1) != color) continue;
+        T w0 = gl[c], w1 = i < nx - 1 ? gl[c + 1] : T(0), w2 = gb[c], w3 = j < ny - 1 ? gb[c + nx] : T(0);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            T acc = b[c * NR + k];
+            if (i > 0) acc += w0 * x[(c - 1) * NR + k];
+            if (i < nx - 1) acc += w1 * x[(c + 1) * NR + k];
+            if (j > 0) acc += w2 * x[(c - nx) * NR + k];
+            if (j < ny - 1) acc += w3 * x[(c + nx) * NR + k];
+            x[c * NR + k] = acc / dg[c];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int NR, bool DOT>
+__global__ void __launch_bounds__(1024) k_small(SmallPlan P, const T* __restrict__ diag, const T* __restrict__ wl,
+                                                const T* __restrict__ wb, const T* __restrict__ b_in,
+                                                T* __restrict__ x_out, SolveState* st) {
+    if (skip(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int total = P.soff[P.n - 1] + P.nx[P.n - 1] * P.ny[P.n - 1];
+    T* xs = (T*)smem;
+    T* bs = xs + (size_t)total * NR;
+    int n0 = P.nx[0] * P.ny[0];
+    for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) bs[c] = b_in[c];
+    __syncthreads();
+    // down
+    for (int l = 0; l < P.n - 1; ++l) {
+        T* x = xs + (size_t)P.soff[l] * NR;
+        int nx = P.nx[l], ny = P.ny[l];
+        for (int c = threadIdx.x; c < nx * ny * NR; c += blockDim.x) x[c] = T(0);
+        __syncthreads();
+        for (int k = 0; k < NU; ++k) {
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
+        }
+        // residual, restricted to level l+1
+        const T* dg = diag + P.goff[l];
+        const T* gl = wl + P.goff[l];
+        const T* gb = wb + P.goff[l];
+        const T* b = bs + (size_t)P.soff[l] * NR;
+        T* bc = bs + (size_t)P.soff[l + 1] * NR;
+        int cnx = P.nx[l + 1], cny = P.ny[l + 1];
+        for (int C = threadIdx.x; C < cnx * cny; C += blockDim.x) {
+            int I = C % cnx, J = C / cnx;
+            T acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc[k] = T(0);
+            for (int d2 = 0; d2 < 4; ++d2) {
+                int i = 2 * I + (d2 & 1), j = 2 * J + (d2 >> 1);
+                int c = j * nx + i;
+                T w0 = gl[c], w1 = i < nx - 1 ? gl[c + 1] : T(0), w2 = gb[c], w3 = j < ny - 1 ? gb[c + nx] : T(0);
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    T s = T(0);
+                    if (i > 0) s += w0 * x[(c - 1) * NR + k];
+                    if (i < nx - 1) s += w1 * x[(c + 1) * NR + k];
+                    if (j > 0) s += w2 * x[(c - nx) * NR + k];
+                    if (j < ny - 1) s += w3 * x[(c + nx) * NR + k];
+                    acc[k] += b[c * NR + k] - (dg[c] * x[c * NR + k] - s);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) bc[C * NR + k] = acc[k];
         }
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = xs[c];
+    // coarsest: symmetric sweep sequence from zero
+    {
+        int l = P.n - 1;
+        T* x = xs + (size_t)P.soff[l] * NR;
+        for (int c = threadIdx.x; c < P.nx[l] * P.ny[l] * NR; c += blockDim.x) x[c] = T(0);
+        __syncthreads();
+        for (int k = 0; k < COARSE_PAIRS; ++k) {
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
+        }
+        for (int k = 0; k < COARSE_PAIRS; ++k) {
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
+        }
+    }
+    // up
+    for (int l = P.n - 2; l >= 0; --l) {
+        T* x = xs + (size_t)P.soff[l] * NR;
+        const T* xc = xs + (size_t)P.soff[l + 1] * NR;
+        int nx = P.nx[l], ny = P.ny[l], cnx = P.nx[l + 1];
+        for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
+            int i = c % nx, j = c / nx;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) x[c * NR + k] += xc[((j >> 1) * cnx + (i >> 1)) * NR + k];
+        }
+        __syncthreads();
+        for (int k = 0; k < NU; ++k) {
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
+            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
+        }
+    }
+    for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) x_out[c] = xs[c];
+    if (DOT) {
+        // the cycle started at the finest level: r.z -> beta (one block, fixed order)
+        __shared__ double sh[32];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double a = 0.0;
+            for (int c = threadIdx.x; c < n0; c += blockDim.x) a += (double)xs[c * NR + k] * (double)bs[c * NR + k];
+            a = bsum(a, sh);
+            if (threadIdx.x == 0) {
+                double old = st->rz[k];
+                st->beta[k] = old != 0.0 ? a / old : 0.0;
+                st->rz[k] = a;
+            }
+        }
+    }
 }
 
-// ---- CG kernels -------------------------------------------------------------------------
-// q = A p, pq = p.q
-template <typename T>
-__global__ void k_apply_dot(LevelView<T> L, const T* __restrict__ p, T* __restrict__ q, double* partial,
-                            unsigned* ticket, double* scal, const int* fl) {
-    if (skip(fl)) return;
+// ---- CG kernels ---------------------------------------------------------------------------
+// p_new = z + beta p_old; q = A p_new; p.q -> alpha = r.z / p.q
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z, T* __restrict__ p0,
+                                                T* __restrict__ p1, T* __restrict__ q, SolveState* st,
+                                                double* partial, unsigned* ticket) {
+    if (skip(st)) return;
+    const Vec<T, NR>* Z = reinterpret_cast<const Vec<T, NR>*>(z);
+    const Vec<T, NR>* Po = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p1 : p0);
+    Vec<T, NR>* Pn = reinterpret_cast<Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
+    Vec<T, NR>* Q = reinterpret_cast<Vec<T, NR>*>(q);
+    T beta[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) beta[k] = (T)st->beta[k];
     int N = L.nx * L.ny;
-    double acc = 0.0;
+    double acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int i = c % L.nx, j = c / L.nx;
-        T pc = p[c];
-        T v = L.diag[c] * pc - nbr_sum(L, p, i, j);
-        q[c] = v;
-        acc += (double)pc * (double)v;
+        auto pn = [&](int cc) {
+            Vec<T, NR> a = Z[cc], b = Po[cc];
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                if (beta[k] != T(0)) a.v[k] += beta[k] * b.v[k];   // beta = 0: p = z (old p unused)
+            return a;
+        };
+        Vec<T, NR> pc = pn(c), s, qv;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) s.v[k] = T(0);
+        if (i > 0) { T w = L.wl[c]; Vec<T, NR> a = pn(c - 1); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
+        if (i < L.nx - 1) { T w = L.wl[c + 1]; Vec<T, NR> a = pn(c + 1); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
+        if (j > 0) { T w = L.wb[c]; Vec<T, NR> a = pn(c - L.nx); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
+        if (j < L.ny - 1) { T w = L.wb[c + L.nx]; Vec<T, NR> a = pn(c + L.nx); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
+        T d = L.diag[c];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            qv.v[k] = d * pc.v[k] - s.v[k];
+            acc[k] += (double)pc.v[k] * (double)qv.v[k];
+        }
+        Pn[c] = pc;
+        Q[c] = qv;
     }
-    double tot;
-    if (reduce_finish(acc, partial, ticket, &tot)) scal[S_PQ] = tot;
+    double tot[NR];
+    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            st->pq[k] = tot[k];
+            st->alpha[k] = tot[k] != 0.0 ? st->rz[k] / tot[k] : 0.0;
+        }
+    }
 }
 
-// x += alpha p, r -= alpha q, rr = r.r, convergence test
-template <typename T>
-__global__ void k_cg_update(int N, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                            const T* __restrict__ q, double* partial, unsigned* ticket, double* scal, int* fl,
-                            int iter_slot) {
-    if (skip(fl)) return;
-    double pq = scal[S_PQ];
-    T alpha = (T)(pq != 0.0 ? scal[S_RZ] / pq : 0.0);
-    double acc = 0.0;
+// x += alpha p_new; r -= alpha q; r.r; convergence test; loop condition
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_update(int N, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p0,
+                                                 const T* __restrict__ p1, const T* __restrict__ q, SolveState* st,
+                                                 double* partial, unsigned* ticket, cudaGraphConditionalHandle h,
+                                                 int use_h) {
+    if (skip(st)) return;
+    const Vec<T, NR>* Pn = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
+    const Vec<T, NR>* Q = reinterpret_cast<const Vec<T, NR>*>(q);
+    Vec<T, NR>* X = reinterpret_cast<Vec<T, NR>*>(x);
+    Vec<T, NR>* Rr = reinterpret_cast<Vec<T, NR>*>(r);
+    T alpha[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) alpha[k] = (T)st->alpha[k];
+    double acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        x[c] += alpha * p[c];
-        T rv = r[c] - alpha * q[c];
-        r[c] = rv;
-        acc += (double)rv * (double)rv;
+        Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            xv.v[k] += alpha[k] * pv.v[k];
+            rv.v[k] -= alpha[k] * qv.v[k];
+            acc[k] += (double)rv.v[k] * (double)rv.v[k];
+        }
+        X[c] = xv;
+        Rr[c] = rv;
     }
-    double tot;
-    if (reduce_finish(acc, partial, ticket, &tot)) {
-        scal[S_RR] = tot;
-        fl[iter_slot] += 1;
-        if (tot <= scal[S_TOL2]) fl[FL_DONE] = 1;
-    }
-}
-
-// rz_new = r.z; beta = rz_new / rz; p = z + beta p is done by k_update_p
-template <typename T>
-__global__ void k_dot_rz(int N, const T* __restrict__ r, const T* __restrict__ z, double* partial, unsigned* ticket,
-                         double* scal, const int* fl, double* beta_out) {
-    if (skip(fl)) return;
-    double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        acc += (double)r[c] * (double)z[c];
-    double tot;
-    if (reduce_finish(acc, partial, ticket, &tot)) {
-        double old = scal[S_RZ];
-        *beta_out = old != 0.0 ? tot / old : 0.0;
-        scal[S_RZ] = tot;
+    double tot[NR];
+    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+        bool done = true;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            st->rr[k] = tot[k];
+            if (!(tot[k] <= st->tol2[k])) done = false;
+        }
+        st->iters += 1;
+        if (done) st->done = 1;
+        set_cond(h, use_h, (!done && st->iters < st->max_iters) ? 1u : 0u);
     }
 }
 
-template <typename T>
-__global__ void k_update_p(int N, const T* __restrict__ z, T* __restrict__ p, const double* __restrict__ beta,
-                           int first, const int* __restrict__ fl) {
-    if (skip(fl)) return;
-    T bt = first ? T(0) : (T)(*beta);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        p[c] = z[c] + bt * p[c];
-}
-
-// r = b - A x, rr = r.r, bb = b.b; sets the tolerance (rtol^2 bb) and the done flag
-template <typename T>
-__global__ void k_cg_init(LevelView<T> L, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r,
-                          double* partial, double* partial2, unsigned* ticket, unsigned* ticket2, double* scal,
-                          int* fl, double rtol2) {
+// FP64 CG start: r = b - A x, r.r, b.b, tolerance, state reset
+template <int NR>
+__global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__ x,
+                                                 double* __restrict__ r, SolveState* st, double* partial,
+                                                 unsigned* ticket, double rtol2, int max_iters,
+                                                 cudaGraphConditionalHandle h, int use_h) {
     int N = L.nx * L.ny;
-    double acc = 0.0, accb = 0.0;
+    double acc[2 * NR];
+#pragma unroll
+    for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
+    const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
+    const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int i = c % L.nx, j = c / L.nx;
-        T bv = b[c];
-        T rv = bv - (L.diag[c] * x[c] - nbr_sum(L, x, i, j));
-        r[c] = rv;
-        acc += (double)rv * (double)rv;
-        accb += (double)bv * (double)bv;
+        Vec<double, NR> xv = X[c], bv = B[c], s;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) s.v[k] = 0.0;
+        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - 1].v[k]; }
+        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + 1].v[k]; }
+        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - L.nx].v[k]; }
+        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + L.nx].v[k]; }
+        Vec<double, NR> rv;
+        double d = L.diag[c];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            rv.v[k] = bv.v[k] - (d * xv.v[k] - s.v[k]);
+            acc[k] += rv.v[k] * rv.v[k];
+            acc[NR + k] += bv.v[k] * bv.v[k];
+        }
+        reinterpret_cast<Vec<double, NR>*>(r)[c] = rv;
     }
-    double tot, totb;
-    bool l1 = reduce_finish(accb, partial2, ticket2, &totb);
-    if (l1) scal[S_BB] = totb;
-    if (reduce_finish(acc, partial, ticket, &tot)) {
-        // both reductions finish in the same (last) block for the first one only if ordering
-        // matches; the tolerance is therefore set by k_cg_tol below
-        scal[S_RR] = tot;
-        scal[S_RR0] = tot;
+    double tot[2 * NR];
+    if (grid_reduce<2 * NR>(acc, partial, ticket, tot)) {
+        bool done = true;
+        for (int k = 0; k < 2; ++k) {
+            double rr = k < NR ? tot[k] : 0.0, bb = k < NR ? tot[NR + k] : 0.0;
+            st->rr[k] = rr;
+            st->bb[k] = bb;
+            st->tol2[k] = rtol2 * (bb > 1e-300 ? bb : 1e-300);
+            st->rz[k] = 0.0;
+            st->beta[k] = 0.0;
+            if (!(rr <= st->tol2[k])) done = false;
+        }
+        st->iters = 0;
+        st->itot = 0;
+        st->max_iters = max_iters;
+        st->done = done ? 1 : 0;
+        st->odone = 0;
+        st->oiters = 0;
+        st->nr = NR;
+        set_cond(h, use_h, done ? 0u : 1u);
     }
-    (void)rtol2;
-    (void)fl;
 }
 
-__global__ void k_cg_tol(double* scal, int* fl, double rtol2, int reset_outer) {
-    double bb = scal[S_BB];
-    double tol2 = rtol2 * (bb > 1e-300 ? bb : 1e-300);
-    scal[S_TOL2] = tol2;
-    fl[FL_DONE] = scal[S_RR] <= tol2 ? 1 : 0;
-    fl[FL_ITERS] = 0;
-    if (reset_outer) { fl[FL_ODONE] = 0; fl[FL_OITERS] = 0; }
+// refinement start: b.b and the outer tolerance
+template <int NR>
+__global__ void __launch_bounds__(256) k_ir_init(int N, const double* __restrict__ b, SolveState* st, double* partial,
+                                                  unsigned* ticket, double rtol2, double inner_rtol, int max_iters,
+                                                  int max_outer) {
+    double acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        Vec<double, NR> bv = reinterpret_cast<const Vec<double, NR>*>(b)[c];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) acc[k] += bv.v[k] * bv.v[k];
+    }
+    double tot[NR];
+    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+        for (int k = 0; k < 2; ++k) {
+            double bb = k < NR ? tot[k] : 0.0;
+            st->obb[k] = bb;
+            st->otol2[k] = rtol2 * (bb > 1e-300 ? bb : 1e-300);
+        }
+        st->odone = 0;
+        st->oiters = 0;
+        st->done = 0;
+        st->iters = 0;
+        st->itot = 0;
+        st->max_iters = max_iters;
+        st->max_outer = max_outer;
+        st->inner_rtol = inner_rtol;
+        st->nr = NR;
+    }
 }
 
-// mixed precision: r64 = b - A64 x64 and its norm; r32 = r64; outer convergence test
-__global__ void k_ir_residual(LevelView<double> L, const double* __restrict__ b, const double* __restrict__ x,
-                              double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ e32,
-                              double* partial, unsigned* ticket, double* oscal, int* fl) {
-    if (fl[FL_ODONE]) return;
+// refinement sweep: r64 = b - A64 x, outer test, r32 = r64, e = 0, inner state reset
+template <int NR>
+__global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double* __restrict__ b,
+                                                      const double* __restrict__ x, float* __restrict__ r32,
+                                                      float* __restrict__ e32, SolveState* st, double* partial,
+                                                      unsigned* ticket, cudaGraphConditionalHandle ho,
+                                                      cudaGraphConditionalHandle hi, int use_h) {
+    if (st->odone) return;
     int N = L.nx * L.ny;
-    double acc = 0.0;
+    double acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+    const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
+    const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int i = c % L.nx, j = c / L.nx;
-        double rv = b[c] - (L.diag[c] * x[c] - nbr_sum(L, x, i, j));
-        r64[c] = rv;
-        r32[c] = (float)rv;
-        e32[c] = 0.0f;
-        acc += rv * rv;
+        Vec<double, NR> xv = X[c], bv = B[c], s;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) s.v[k] = 0.0;
+        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - 1].v[k]; }
+        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + 1].v[k]; }
+        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - L.nx].v[k]; }
+        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + L.nx].v[k]; }
+        Vec<float, NR> rf, ez;
+        double d = L.diag[c];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double rv = bv.v[k] - (d * xv.v[k] - s.v[k]);
+            acc[k] += rv * rv;
+            rf.v[k] = (float)rv;
+            ez.v[k] = 0.0f;
+        }
+        reinterpret_cast<Vec<float, NR>*>(r32)[c] = rf;
+        reinterpret_cast<Vec<float, NR>*>(e32)[c] = ez;
     }
-    double tot;
-    if (reduce_finish(acc, partial, ticket, &tot)) {
-        oscal[S_RR] = tot;
-        fl[FL_OITERS] += 1;
-        if (tot <= oscal[S_TOL2]) fl[FL_ODONE] = 1;
-        fl[FL_DONE] = 0;
-        fl[FL_ITERS] = 0;
+    double tot[NR];
+    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+        bool done = true;
+        for (int k = 0; k < 2; ++k) {
+            double rr = k < NR ? tot[k] : 0.0;
+            st->orr[k] = rr;
+            if (!(rr <= st->otol2[k])) done = false;
+            st->rr[k] = rr;
+            st->tol2[k] = st->inner_rtol * st->inner_rtol * rr;
+            st->rz[k] = 0.0;
+            st->beta[k] = 0.0;
+        }
+        st->oiters += 1;
+        st->itot += st->iters;
+        if (st->oiters > st->max_outer) done = true;
+        st->odone = done ? 1 : 0;
+        st->iters = 0;
+        st->done = done ? 1 : 0;
+        set_cond(ho, use_h, done ? 0u : 1u);
+        set_cond(hi, use_h, done ? 0u : 1u);
     }
 }
 
-__global__ void k_ir_update(int N, double* __restrict__ x, const float* __restrict__ e, const int* __restrict__ fl) {
-    if (fl[FL_ODONE]) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) x[c] += (double)e[c];
+template <int NR>
+__global__ void k_ir_update(int N, double* __restrict__ x, const float* __restrict__ e, const SolveState* st) {
+    if (st->odone) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N * NR; c += gridDim.x * blockDim.x)
+        x[c] += (double)e[c];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -352,288 +737,386 @@ static inline int nblocks(long long n) {
     return (int)(b < NRED ? (b < 1 ? 1 : b) : NRED);
 }
 
-void Solver::plan(int nx, int ny) {
+void Solver::plan(int nx_, int ny_) {
+    nx = nx_;
+    ny = ny_;
     nlev = 0;
     int x = nx, y = ny;
+    size_t off = 0;
     while (true) {
         lnx[nlev] = x;
         lny[nlev] = y;
+        loff[nlev] = off;
+        off += (size_t)x * y;
         ++nlev;
         if (nlev == MAXLEV) break;
         if ((x & 1) || (y & 1) || (long long)x * y <= 64 || x < 4 || y < 4) break;
         x /= 2;
         y /= 2;
     }
+    ncells_all = off;
+    nbig = 0;
+    while (nbig < nlev - 1 && (long long)lnx[nbig] * lny[nbig] > SMALL_MAX) ++nbig;
 }
+
+static size_t tiles(int nx, int ny) { return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
 
 size_t Solver::bytes(int nx, int ny) {
     Solver s;
     s.plan(nx, ny);
     size_t total = 0;
     auto add = [&](size_t b) { total += (b + 255) & ~size_t(255); };
-    for (int l = 0; l < s.nlev; ++l) {
-        size_t n = (size_t)s.lnx[l] * s.lny[l];
-        size_t nfx = (size_t)s.lny[l] * (s.lnx[l] + 1), nfy = (size_t)(s.lny[l] + 1) * s.lnx[l];
-        if (l > 0) { add(n * 8); add(n * 8); add(nfx * 8); add(nfy * 8); }   // cd, dd, wx, wy (FP64 coarsening)
-        for (int t = 0; t < 2; ++t) {                                        // float and double views
-            size_t e = t == 0 ? 4 : 8;
-            add(n * e); add(nfx * e); add(nfy * e);                          // diag, wx, wy
-            add(n * e); add(n * e);                                          // x, b
-        }
-    }
-    size_t n0 = (size_t)nx * ny;
-    add(n0 * 8 * 4);   // r, z, p, q double
-    add(n0 * 4 * 6);   // r, z, p, q, e, b float
-    add(n0 * 8);       // r64 (IR)
-    add(NRED * 8 * 4); add(64); add(64 * 8); add(64 * 4); add(64);
+    size_t A = s.ncells_all, N = (size_t)nx * ny;
+    for (int k = 0; k < 5; ++k) add(A * 4);
+    for (int k = 0; k < 5; ++k) add(A * 8);
+    add(A * 2 * 4); add(A * 2 * 4);
+    add(A * 2 * 8); add(A * 2 * 8);
+    add(N * 2 * 4); add(N * 4 * 4); add(N * 2 * 4); add(N * 2 * 4);
+    add(N * 2 * 8); add(N * 4 * 8); add(N * 2 * 8);
+    size_t mb = tiles(nx, ny) > (size_t)NRED ? tiles(nx, ny) : (size_t)NRED;
+    add(mb * 4 * 8);
+    add(256);
+    add(NSLOT * sizeof(SolveState));
+    add(4 * sizeof(KTimer));
     return total;
 }
 
-void Solver::bind(void* base, int nx, int ny) {
-    plan(nx, ny);
+template <typename K>
+static void allow_smem(K kern, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void Solver::bind(void* base, int nx_, int ny_) {
+    plan(nx_, ny_);
     char* p = (char*)base;
     auto take = [&](size_t b) { void* r = p; p += (b + 255) & ~size_t(255); return r; };
-    for (int l = 0; l < nlev; ++l) {
-        size_t n = (size_t)lnx[l] * lny[l];
-        size_t nfx = (size_t)lny[l] * (lnx[l] + 1), nfy = (size_t)(lny[l] + 1) * lnx[l];
-        if (l > 0) {
-            cd[l] = (double*)take(n * 8); dd[l] = (double*)take(n * 8);
-            wx64[l] = (double*)take(nfx * 8); wy64[l] = (double*)take(nfy * 8);
-        }
-        fdiag[l] = (float*)take(n * 4); fwx[l] = (float*)take(nfx * 4); fwy[l] = (float*)take(nfy * 4);
-        fx[l] = (float*)take(n * 4); fb[l] = (float*)take(n * 4);
-        ddiag[l] = (double*)take(n * 8); dwx[l] = (double*)take(nfx * 8); dwy[l] = (double*)take(nfy * 8);
-        dx[l] = (double*)take(n * 8); db[l] = (double*)take(n * 8);
-    }
-    size_t n0 = (size_t)nx * ny;
-    r64 = (double*)take(n0 * 8 * 4);
-    z64 = r64 + n0; p64 = z64 + n0; q64 = p64 + n0;
-    r32 = (float*)take(n0 * 4 * 6);
-    z32 = r32 + n0; p32 = z32 + n0; q32 = p32 + n0; e32 = q32 + n0; b32 = e32 + n0;
-    ir_r64 = (double*)take(n0 * 8);
-    partial = (double*)take(NRED * 8 * 4);
-    partial2 = partial + NRED;
-    ticket = (unsigned*)take(64);
-    scal = (double*)take(64 * 8);
-    oscal = scal + 16;
-    beta = scal + 32;
-    flags = (int*)take(64 * 4);
-    host_flags = nullptr;
+    size_t A = ncells_all, N = (size_t)nx * ny;
+    f_diag = (float*)take(A * 4); f_wl = (float*)take(A * 4); f_wb = (float*)take(A * 4);
+    f_cd = (float*)take(A * 4); f_dd = (float*)take(A * 4);
+    d_diag = (double*)take(A * 8); d_wl = (double*)take(A * 8); d_wb = (double*)take(A * 8);
+    d_cd = (double*)take(A * 8); d_dd = (double*)take(A * 8);
+    f_x = (float*)take(A * 2 * 4); f_b = (float*)take(A * 2 * 4);
+    d_x = (double*)take(A * 2 * 8); d_b = (double*)take(A * 2 * 8);
+    f_r = (float*)take(N * 2 * 4); f_p = (float*)take(N * 4 * 4); f_q = (float*)take(N * 2 * 4);
+    f_e = (float*)take(N * 2 * 4);
+    d_r = (double*)take(N * 2 * 8); d_p = (double*)take(N * 4 * 8); d_q = (double*)take(N * 2 * 8);
+    size_t mb = tiles(nx, ny) > (size_t)NRED ? tiles(nx, ny) : (size_t)NRED;
+    partial = (double*)take(mb * 4 * 8);
+    tickets = (unsigned*)take(256);
+    st_base = (SolveState*)take(NSLOT * sizeof(SolveState));
+    st = st_base;
+    timer = (KTimer*)take(4 * sizeof(KTimer));
+    for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&aux[k], cudaStreamNonBlocking);
+    // shared-memory limits of the tile kernels
+    allow_smem(k_pre<float, 1>, Region<float, 1, 2 * NU + 1>::bytes());
+    allow_smem(k_pre<float, 2>, Region<float, 2, 2 * NU + 1>::bytes());
+    allow_smem(k_pre<double, 1>, Region<double, 1, 2 * NU + 1>::bytes());
+    allow_smem(k_pre<double, 2>, Region<double, 2, 2 * NU + 1>::bytes());
+    allow_smem(k_post<float, 1, true>, Region<float, 1, 2 * NU>::bytes());
+    allow_smem(k_post<float, 1, false>, Region<float, 1, 2 * NU>::bytes());
+    allow_smem(k_post<float, 2, true>, Region<float, 2, 2 * NU>::bytes());
+    allow_smem(k_post<float, 2, false>, Region<float, 2, 2 * NU>::bytes());
+    allow_smem(k_post<double, 1, true>, Region<double, 1, 2 * NU>::bytes());
+    allow_smem(k_post<double, 1, false>, Region<double, 1, 2 * NU>::bytes());
+    allow_smem(k_post<double, 2, true>, Region<double, 2, 2 * NU>::bytes());
+    allow_smem(k_post<double, 2, false>, Region<double, 2, 2 * NU>::bytes());
+    size_t small_cells = 0;
+    for (int l = nbig; l < nlev; ++l) small_cells += (size_t)lnx[l] * lny[l];
+    allow_smem(k_small<float, 1, true>, small_cells * 2 * 1 * 4);
+    allow_smem(k_small<float, 1, false>, small_cells * 2 * 1 * 4);
+    allow_smem(k_small<float, 2, true>, small_cells * 2 * 2 * 4);
+    allow_smem(k_small<float, 2, false>, small_cells * 2 * 2 * 4);
+    allow_smem(k_small<double, 1, true>, small_cells * 2 * 1 * 8);
+    allow_smem(k_small<double, 1, false>, small_cells * 2 * 1 * 8);
+    allow_smem(k_small<double, 2, true>, small_cells * 2 * 2 * 8);
+    allow_smem(k_small<double, 2, false>, small_cells * 2 * 2 * 8);
+    KTimer init[4];
+    for (auto& t : init) { t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; }
+    cudaMemcpy(timer, init, sizeof(init), cudaMemcpyHostToDevice);
+    cudaMemset(tickets, 0, 256);
+    cudaMemset(st_base, 0, NSLOT * sizeof(SolveState));
+    timing = 1;
+}
+
+// accessors for precision T
+template <typename T> struct PT;
+template <> struct PT<float> {
+    static float* diag(Solver& s) { return s.f_diag; }
+    static float* wl(Solver& s) { return s.f_wl; }
+    static float* wb(Solver& s) { return s.f_wb; }
+    static float* cd(Solver& s) { return s.f_cd; }
+    static float* dd(Solver& s) { return s.f_dd; }
+    static float* x(Solver& s) { return s.f_x; }
+    static float* b(Solver& s) { return s.f_b; }
+};
+template <> struct PT<double> {
+    static double* diag(Solver& s) { return s.d_diag; }
+    static double* wl(Solver& s) { return s.d_wl; }
+    static double* wb(Solver& s) { return s.d_wb; }
+    static double* cd(Solver& s) { return s.d_cd; }
+    static double* dd(Solver& s) { return s.d_dd; }
+    static double* x(Solver& s) { return s.d_x; }
+    static double* b(Solver& s) { return s.d_b; }
+};
+
+template <typename T>
+static Lev<T> lev(Solver& s, int l) {
+    size_t o = s.loff[l];
+    return {s.lnx[l], s.lny[l], PT<T>::diag(s) + o, PT<T>::wl(s) + o, PT<T>::wb(s) + o};
 }
 
 template <typename T>
-static LevelView<T> view(const Solver& s, int l);
-template <>
-LevelView<float> view<float>(const Solver& s, int l) { return {s.lnx[l], s.lny[l], s.fdiag[l], s.fwx[l], s.fwy[l]}; }
-template <>
-LevelView<double> view<double>(const Solver& s, int l) {
-    return {s.lnx[l], s.lny[l], s.ddiag[l], s.dwx[l], s.dwy[l]};
-}
-template <typename T> static T* lx(const Solver& s, int l);
-template <> float* lx<float>(const Solver& s, int l) { return s.fx[l]; }
-template <> double* lx<double>(const Solver& s, int l) { return s.dx[l]; }
-template <typename T> static T* lb(const Solver& s, int l);
-template <> float* lb<float>(const Solver& s, int l) { return s.fb[l]; }
-template <> double* lb<double>(const Solver& s, int l) { return s.db[l]; }
-
-// Build the hierarchy for the fine operator (cd0, dd0, wx0, wy0 in FP64).
-template <typename T>
-static void setup_hierarchy(Solver& s, const double* cd0, const double* dd0, const double* wx0, const double* wy0,
-                            cudaStream_t st, int& launches) {
-    int N0 = s.lnx[0] * s.lny[0];
-    // FP64 level 0 always (outer residual / FP64 CG)
-    k_make_diag<double><<<nblocks(N0), RB, 0, st>>>(s.lnx[0], s.lny[0], cd0, dd0, wx0, wy0, s.ddiag[0], s.dwx[0],
-                                                    s.dwy[0]);
-    ++launches;
-    if (sizeof(T) == 4) {
-        k_make_diag<float><<<nblocks(N0), RB, 0, st>>>(s.lnx[0], s.lny[0], cd0, dd0, wx0, wy0, s.fdiag[0], s.fwx[0],
-                                                       s.fwy[0]);
-        ++launches;
-    }
-    const double *fcd = cd0, *fdd = dd0, *fwx = wx0, *fwy = wy0;
+static void setup_levels(Solver& s, const double* cd, const double* dd, const double* wl, const double* wb,
+                         cudaStream_t stm) {
+    int N = s.nx * s.ny;
+    k_setup0<T><<<nblocks(N), RB, 0, stm>>>(s.nx, s.ny, cd, dd, wl, wb, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s),
+                                             PT<T>::cd(s), PT<T>::dd(s));
+    ++s.launches;
     for (int l = 1; l < s.nlev; ++l) {
+        size_t fo = s.loff[l - 1], co = s.loff[l];
         int n = s.lnx[l] * s.lny[l];
-        T* cdiag = sizeof(T) == 4 ? (T*)s.fdiag[l] : (T*)s.ddiag[l];
-        T* cwx = sizeof(T) == 4 ? (T*)s.fwx[l] : (T*)s.dwx[l];
-        T* cwy = sizeof(T) == 4 ? (T*)s.fwy[l] : (T*)s.dwy[l];
-        k_coarsen<T><<<nblocks(n), RB, 0, st>>>(s.lnx[l - 1], s.lny[l - 1], fcd, fdd, fwx, fwy, s.cd[l], s.dd[l],
-                                               s.wx64[l], s.wy64[l], cdiag, cwx, cwy);
-        ++launches;
-        fcd = s.cd[l]; fdd = s.dd[l]; fwx = s.wx64[l]; fwy = s.wy64[l];
+        k_coarsen<T><<<nblocks(n), RB, 0, stm>>>(s.lnx[l - 1], s.lny[l - 1], PT<T>::cd(s) + fo, PT<T>::dd(s) + fo,
+                                                  PT<T>::wl(s) + fo, PT<T>::wb(s) + fo, PT<T>::cd(s) + co,
+                                                  PT<T>::dd(s) + co, PT<T>::wl(s) + co, PT<T>::wb(s) + co,
+                                                  PT<T>::diag(s) + co);
+        ++s.launches;
     }
 }
 
-void Solver::time_begin() {
-    if (!ev) {
-        ev_cap = 8192;
-        ev = new cudaEvent_t[ev_cap];
-        for (int k = 0; k < ev_cap; ++k) cudaEventCreate(&ev[k]);
-    }
-    ev_used = 0;
-    timed_launches = 0;
-    timing = true;
-}
-
-void Solver::time_mark(cudaStream_t st) {
-    if (ev_used < ev_cap) cudaEventRecord(ev[ev_used], st);
-    ++ev_used;
-}
-
-double Solver::time_end_ms() {
-    timing = false;
-    double tot = 0.0;
-    int n = ev_used < ev_cap ? ev_used : ev_cap;
-    if (n >= 2) cudaEventSynchronize(ev[n - 1]);
-    for (int k = 0; k + 1 < n; k += 2) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-        tot += ms;
-    }
-    timed_launches = n / 2;
-    return tot;
-}
-
-// z = M r (one V(2,2)-cycle), level-0 input b0 = r and output x0 = z
-template <typename T>
-static void vcycle(Solver& s, const T* r, T* z, cudaStream_t st, int& launches) {
-    const int nu = 2;
+// z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved)
+template <typename T, int NR>
+static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm) {
+    T* X = PT<T>::x(s);
+    T* B = PT<T>::b(s);
     const T* b = r;
     T* x = z;
-    for (int l = 0; l < s.nlev - 1; ++l) {
-        LevelView<T> L = view<T>(s, l);
-        int n = L.nx * L.ny;
-        bool tm = s.timing && l == 0;
-        for (int k = 0; k < nu; ++k) {
-            if (tm) s.time_mark(st);
-            k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, b, x, 0, k == 0, s.flags);
-            if (tm) { s.time_mark(st); s.time_mark(st); }
-            k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, b, x, 1, 0, s.flags);
-            if (tm) s.time_mark(st);
-            launches += 2;
-        }
-        T* bc = lb<T>(s, l + 1);
-        k_restrict_residual<T><<<nblocks(n / 4), RB, 0, st>>>(L, b, x, bc, s.flags);
-        ++launches;
+    for (int l = 0; l < s.nbig; ++l) {
+        Lev<T> L = lev<T>(s, l);
+        dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
+        T* bc = B + 2 * s.loff[l + 1];
+        k_pre<T, NR><<<grid, 256, Region<T, NR, 2 * NU + 1>::bytes(), stm>>>(L, b, x, bc, st,
+                                                                           s.timing && l == 0 ? s.timer : nullptr);
+        if (!s.use_graph) ++s.launches;
         b = bc;
-        x = lx<T>(s, l + 1);
+        x = X + 2 * s.loff[l + 1];
     }
     {
-        int l = s.nlev - 1;
-        LevelView<T> L = view<T>(s, l);
-        int n = L.nx * L.ny;
-        if (n <= 4096) {
-            int threads = n < 1024 ? ((n + 31) / 32) * 32 : 1024;
-            k_coarse_solve<T><<<1, threads, n * sizeof(T), st>>>(L, b, x, 16, s.flags);
-            ++launches;
-        } else {
-            for (int k = 0; k < 64; ++k) {
-                k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, b, x, k < 32 ? (k & 1) : 1 - (k & 1), k == 0, s.flags);
-                ++launches;
-            }
+        SmallPlan P;
+        P.n = s.nlev - s.nbig;
+        int so = 0;
+        for (int k = 0; k < P.n; ++k) {
+            int l = s.nbig + k;
+            P.nx[k] = s.lnx[l];
+            P.ny[k] = s.lny[l];
+            P.soff[k] = so;
+            P.goff[k] = s.loff[l];
+            so += s.lnx[l] * s.lny[l];
         }
+        size_t smem = (size_t)so * 2 * NR * sizeof(T);
+        int n0 = P.nx[0] * P.ny[0];
+        int threads = n0 >= 1024 ? 1024 : ((n0 + 31) / 32) * 32;
+        if (s.nbig == 0)
+            k_small<T, NR, true><<<1, threads, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x, st);
+        else
+            k_small<T, NR, false><<<1, threads, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x, st);
+        if (!s.use_graph) ++s.launches;
     }
-    for (int l = s.nlev - 2; l >= 0; --l) {
-        LevelView<T> L = view<T>(s, l);
-        int n = L.nx * L.ny;
-        T* xl = l == 0 ? z : lx<T>(s, l);
-        const T* bl = l == 0 ? r : lb<T>(s, l);
-        k_prolong<T><<<nblocks(n), RB, 0, st>>>(L.nx, L.ny, lx<T>(s, l + 1), xl, s.flags);
-        ++launches;
-        bool tm = s.timing && l == 0;
-        for (int k = 0; k < nu; ++k) {
-            if (tm) s.time_mark(st);
-            k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, bl, xl, 1, 0, s.flags);
-            if (tm) { s.time_mark(st); s.time_mark(st); }
-            k_smooth<T><<<nblocks(n), RB, 0, st>>>(L, bl, xl, 0, 0, s.flags);
-            if (tm) s.time_mark(st);
-            launches += 2;
-        }
+    for (int l = s.nbig - 1; l >= 0; --l) {
+        Lev<T> L = lev<T>(s, l);
+        dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
+        const T* bl = l == 0 ? r : B + 2 * s.loff[l];
+        T* xl = l == 0 ? z : X + 2 * s.loff[l];
+        const T* xc = X + 2 * s.loff[l + 1];
+        size_t smem = Region<T, NR, 2 * NU>::bytes();
+        KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
+        if (l == 0)
+            k_post<T, NR, true><<<grid, 256, smem, stm>>>(L, bl, xl, xc, st, s.partial, s.tickets + 4, tm);
+        else
+            k_post<T, NR, false><<<grid, 256, smem, stm>>>(L, bl, xl, xc, st, s.partial, s.tickets + 4, tm);
+        if (!s.use_graph) ++s.launches;
     }
 }
 
-// poll the convergence flags (pinned host copy)
-static void poll_flags(Solver& s, cudaStream_t st, int* out) {
-    cudaMemcpyAsync(s.host_flags, s.flags, FL_COUNT * sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    for (int k = 0; k < FL_COUNT; ++k) out[k] = s.host_flags[k];
+// one CG iteration body: z = M r (+beta), p/q/alpha, x/r/test
+template <typename T, int NR>
+static void cg_body(Solver& s, T* x, T* r, T* z, T* p, T* q, SolveState* st, cudaGraphConditionalHandle h, int use_h,
+                    cudaStream_t stm) {
+    vcycle<T, NR>(s, r, z, st, stm);
+    int N = s.nx * s.ny;
+    Lev<T> L0 = lev<T>(s, 0);
+    T* p1 = p + (size_t)N * NR;
+    k_apply<T, NR><<<nblocks(N), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1);
+    k_update<T, NR><<<nblocks(N), RB, 0, stm>>>(N, x, r, p, p1, q, st, s.partial, s.tickets + 2, h, use_h);
+    if (!s.use_graph) s.launches += 2;
 }
 
-// PCG on A x = b at level 0 in precision T (x holds the initial guess)
-template <typename T>
-static int pcg(Solver& s, const T* b, T* x, T* r, T* z, T* p, T* q, double rtol, int max_iter, int poll_every,
-               bool reset_outer, cudaStream_t st, int& launches) {
-    LevelView<T> L = view<T>(s, 0);
-    int N = L.nx * L.ny;
-    k_cg_init<T><<<nblocks(N), RB, 0, st>>>(L, b, x, r, s.partial, s.partial2, s.ticket, s.ticket + 1, s.scal,
-                                            s.flags, rtol * rtol);
-    k_cg_tol<<<1, 1, 0, st>>>(s.scal, s.flags, rtol * rtol, reset_outer ? 1 : 0);
-    vcycle<T>(s, r, z, st, launches);
-    k_dot_rz<T><<<nblocks(N), RB, 0, st>>>(N, r, z, s.partial, s.ticket, s.scal, s.flags, s.beta);
-    k_update_p<T><<<nblocks(N), RB, 0, st>>>(N, z, p, s.beta, 1, s.flags);
-    launches += 4;
-    int hf[FL_COUNT];
-    for (int it = 0; it < max_iter; ++it) {
-        k_apply_dot<T><<<nblocks(N), RB, 0, st>>>(L, p, q, s.partial, s.ticket, s.scal, s.flags);
-        k_cg_update<T><<<nblocks(N), RB, 0, st>>>(N, x, r, p, q, s.partial, s.ticket, s.scal, s.flags, FL_ITERS);
-        vcycle<T>(s, r, z, st, launches);
-        k_dot_rz<T><<<nblocks(N), RB, 0, st>>>(N, r, z, s.partial, s.ticket, s.scal, s.flags, s.beta);
-        k_update_p<T><<<nblocks(N), RB, 0, st>>>(N, z, p, s.beta, 0, s.flags);
-        launches += 4;
-        if ((it + 1) % poll_every == 0 || it == max_iter - 1) {
-            poll_flags(s, st, hf);
-            if (hf[FL_DONE] || hf[FL_ODONE]) return hf[FL_ITERS];
-        }
+// capture helpers (graph mode): open a WHILE node at the current capture position
+struct WhileScope {
+    cudaStream_t outer, inner;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t node;
+    bool ok = false;
+};
+
+static cudaGraphConditionalHandle make_handle(cudaStream_t stm, cudaGraph_t* g_out) {
+    cudaStreamCaptureStatus cs;
+    unsigned long long id;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps;
+    const cudaGraphEdgeData* ed;
+    size_t nd;
+    cudaStreamGetCaptureInfo(stm, &cs, &id, &g, &deps, &ed, &nd);
+    cudaGraphConditionalHandle h;
+    cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    *g_out = g;
+    return h;
+}
+
+static cudaStream_t begin_while(cudaStream_t stm, cudaStream_t bs, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    unsigned long long id;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps;
+    const cudaGraphEdgeData* ed;
+    size_t nd;
+    cudaStreamGetCaptureInfo(stm, &cs, &id, &g, &deps, &ed, &nd);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    cudaGraphAddNode(&node, g, deps, ed, nd, &cp);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStreamUpdateCaptureDependencies(stm, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    return bs;
+}
+
+static void end_while(cudaStream_t bs) {
+    cudaGraph_t g;
+    cudaStreamEndCapture(bs, &g);
+}
+
+static void poll(Solver& s, cudaStream_t stm) {
+    cudaMemcpyAsync(s.st_host + s.slot, s.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
+    cudaStreamSynchronize(stm);
+}
+
+template <int NR>
+static void solve_fp64(Solver& s, const double* b, double* x, double rtol, int max_iter, cudaStream_t stm) {
+    int N = s.nx * s.ny;
+    Lev<double> L0 = lev<double>(s, 0);
+    double* z = s.d_x;   // level-0 slot of the per-level x is z
+    if (s.use_graph) {
+        cudaGraph_t g;
+        cudaGraphConditionalHandle h = make_handle(stm, &g);
+        k_init64<NR><<<nblocks(N), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets, rtol * rtol, max_iter,
+                                                 h, 1);
+        ++s.launches;
+        cudaStream_t bs = begin_while(stm, s.aux[0], h);
+        cg_body<double, NR>(s, x, s.d_r, z, s.d_p, s.d_q, s.st, h, 1, bs);
+        end_while(bs);
+        return;
     }
-    return -1;
+    k_init64<NR><<<nblocks(N), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets, rtol * rtol, max_iter, 0, 0);
+    ++s.launches;
+    poll(s, stm);
+    for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
+        cg_body<double, NR>(s, x, s.d_r, z, s.d_p, s.d_q, s.st, 0, 0, stm);
+        if ((it + 1) % 4 == 0) poll(s, stm);
+    }
 }
 
-SolveResult Solver::solve(const double* cd0, const double* dd0, const double* wx0, const double* wy0, const double* b,
-                          double* x, int precision, double rtol, int max_iter, cudaStream_t st) {
-    SolveResult res{0, 0.0, true};
-    int N = lnx[0] * lny[0];
+template <int NR>
+static void solve_mixed(Solver& s, const double* b, double* x, double rtol, int max_iter, cudaStream_t stm) {
+    int N = s.nx * s.ny;
+    Lev<double> L64 = lev<double>(s, 0);
+    const int max_outer = 8;
+    const double inner_rtol = 1e-4;
+    float* z = s.f_x;
+    k_ir_init<NR><<<nblocks(N), RB, 0, stm>>>(N, b, s.st, s.partial, s.tickets + 3, rtol * rtol, inner_rtol, max_iter,
+                                              max_outer);
+    ++s.launches;
+    if (s.use_graph) {
+        cudaGraph_t g;
+        cudaGraphConditionalHandle ho = make_handle(stm, &g);
+        cudaStream_t obs = begin_while(stm, s.aux[0], ho);
+        cudaGraph_t og;
+        cudaGraphConditionalHandle hi = make_handle(obs, &og);
+        k_ir_residual<NR><<<nblocks(N), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial, s.tickets + 5, ho, hi,
+                                                      1);
+        cudaStream_t ibs = begin_while(obs, s.aux[1], hi);
+        cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, hi, 1, ibs);
+        end_while(ibs);
+        k_ir_update<NR><<<nblocks(N * NR), RB, 0, obs>>>(N, x, s.f_e, s.st);
+        end_while(obs);
+        return;
+    }
+    for (int o = 0; o <= max_outer; ++o) {
+        k_ir_residual<NR><<<nblocks(N), RB, 0, stm>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial, s.tickets + 5, 0, 0, 0);
+        ++s.launches;
+        poll(s, stm);
+        if (s.st_host[s.slot].odone) break;
+        for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
+            cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, 0, 0, stm);
+            if ((it + 1) % 4 == 0) poll(s, stm);
+        }
+        k_ir_update<NR><<<nblocks(N * NR), RB, 0, stm>>>(N, x, s.f_e, s.st);
+        ++s.launches;
+    }
+}
+
+void Solver::solve(const double* cd, const double* dd, const double* wl, const double* wb, const double* b, double* x,
+                   int nr, int precision, double rtol, int max_iter, cudaStream_t stm) {
+    st = st_base + slot;
+    // the FP64 level-0 operator is needed in both modes (outer residual of the refinement)
     if (precision == 0) {
-        setup_hierarchy<double>(*this, cd0, dd0, wx0, wy0, st, launches);
-        int it = pcg<double>(*this, b, x, r64, z64, p64, q64, rtol, max_iter, 4, true, st, launches);
-        int hf[FL_COUNT];
-        poll_flags(*this, st, hf);
-        double sc[S_COUNT];
-        cudaMemcpy(sc, scal, sizeof(sc), cudaMemcpyDeviceToHost);
-        res.iters = hf[FL_ITERS];
-        res.converged = hf[FL_DONE] != 0;
-        res.rel_res = sqrt(sc[S_RR] / (sc[S_BB] > 1e-300 ? sc[S_BB] : 1e-300));
-        (void)it;
-        return res;
-    }
-    // mixed: FP64 outer residual, FP32 inner MG-PCG
-    setup_hierarchy<float>(*this, cd0, dd0, wx0, wy0, st, launches);
-    LevelView<double> L64 = view<double>(*this, 0);
-    // ||b||^2 and tolerance for the outer loop (reuse k_cg_init on x to get b.b)
-    k_cg_init<double><<<nblocks(N), RB, 0, st>>>(L64, b, x, ir_r64, partial, partial2, ticket, ticket + 1, oscal,
-                                                 flags, 0.0);
-    k_cg_tol<<<1, 1, 0, st>>>(oscal, flags, rtol * rtol, 1);
-    launches += 2;
-    int max_outer = max_iter > 0 ? (max_iter + 19) / 20 + 4 : 8;
-    int hf[FL_COUNT];
-    int inner_total = 0;
-    for (int o = 0; o < max_outer; ++o) {
-        k_ir_residual<<<nblocks(N), RB, 0, st>>>(L64, b, x, ir_r64, r32, e32, partial, ticket, oscal, flags);
+        setup_levels<double>(*this, cd, dd, wl, wb, stm);
+        if (nr == 1) solve_fp64<1>(*this, b, x, rtol, max_iter, stm);
+        else solve_fp64<2>(*this, b, x, rtol, max_iter, stm);
+    } else {
+        int N = nx * ny;
+        k_setup0<double><<<nblocks(N), RB, 0, stm>>>(nx, ny, cd, dd, wl, wb, d_diag, d_wl, d_wb, d_cd, d_dd);
         ++launches;
-        int it = pcg<float>(*this, r32, e32, b32, z32, p32, q32, 1e-4, 60, 6, false, st, launches);
-        (void)it;
-        poll_flags(*this, st, hf);
-        if (hf[FL_ODONE]) break;
-        inner_total += hf[FL_ITERS];
-        k_ir_update<<<nblocks(N), RB, 0, st>>>(N, x, e32, flags);
-        ++launches;
+        setup_levels<float>(*this, cd, dd, wl, wb, stm);
+        if (nr == 1) solve_mixed<1>(*this, b, x, rtol, max_iter, stm);
+        else solve_mixed<2>(*this, b, x, rtol, max_iter, stm);
     }
-    poll_flags(*this, st, hf);
-    double sc[S_COUNT];
-    cudaMemcpy(sc, oscal, sizeof(sc), cudaMemcpyDeviceToHost);
-    res.iters = inner_total;
-    res.outer = hf[FL_OITERS];
-    res.converged = hf[FL_ODONE] != 0;
-    res.rel_res = sqrt(sc[S_RR] / (sc[S_BB] > 1e-300 ? sc[S_BB] : 1e-300));
-    return res;
+}
+
+int Solver::body_size() const { return 2 * nbig + 1 + 2; }
+
+bool Solver::supported(int nx, int ny) {
+    Solver s;
+    s.plan(nx, ny);
+    return (long long)s.lnx[s.nlev - 1] * s.lny[s.nlev - 1] <= SMALL_MAX;
+}
+
+SolveResult Solver::read_result(int sl, int precision, cudaStream_t stm) {
+    cudaMemcpyAsync(st_host + sl, st_base + sl, sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
+    cudaStreamSynchronize(stm);
+    const SolveState& h = st_host[sl];
+    SolveResult r{};
+    double worst = 0.0;
+    for (int k = 0; k < (h.nr > 0 ? h.nr : 1); ++k) {
+        double num = precision == 0 ? h.rr[k] : h.orr[k];
+        double den = precision == 0 ? h.bb[k] : h.obb[k];
+        double q = sqrt(num / (den > 1e-300 ? den : 1e-300));
+        if (q > worst) worst = q;
+    }
+    r.rel_res = worst;
+    if (precision == 0) {
+        r.iters = h.iters;
+        r.converged = h.done != 0;
+    } else {
+        r.iters = h.itot;
+        r.outer = h.oiters;
+        bool ok = true;
+        for (int k = 0; k < (h.nr > 0 ? h.nr : 1); ++k) ok = ok && h.orr[k] <= h.otol2[k];
+        r.converged = ok;
+    }
+    return r;
 }
 
 }  // namespace ebit

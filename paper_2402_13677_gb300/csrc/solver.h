@@ -1,47 +1,82 @@
-// Multigrid-preconditioned CG (FP64, or FP32 inside FP64 iterative refinement).
+// Multigrid-preconditioned CG for the implicit solves of the step (FP64, or FP32 inside
+// FP64 iterative refinement), with device-side loop control so that a whole solve can be
+// captured into a CUDA graph (conditional WHILE nodes) or driven from the host.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstdint>
 
 namespace ebit {
 
 struct SolveResult {
     int iters;        // CG iterations (FP64) or total inner FP32 iterations (mixed)
-    double rel_res;   // final ||r|| / ||b|| (recursive residual for FP64, true FP64 residual for mixed)
+    double rel_res;   // final ||r|| / ||b|| (max over right-hand sides)
     bool converged;
     int outer = 0;    // refinement sweeps (mixed)
 };
 
+// device-resident timing of one kernel class (span from the first block's start to the
+// last block's end, read from %globaltimer), accumulated over launches
+struct KTimer {
+    unsigned long long start;
+    unsigned long long end;
+    unsigned int ticket;
+    unsigned int pad;
+    unsigned long long total_ns;
+    unsigned long long launches;
+};
+
+// device-side scalars of one solve; per right-hand side k < 2
+struct SolveState {
+    double rz[2], pq[2], alpha[2], beta[2], rr[2], bb[2], tol2[2];
+    double orr[2], obb[2], otol2[2];   // outer (FP64) residual norms of the refinement loop
+    int done, iters, odone, oiters, max_iters, max_outer, nr, itot;
+    double inner_rtol;
+};
+
 struct Solver {
     static constexpr int MAXLEV = 16;
-    int nlev = 0;
+    int nx = 0, ny = 0;
+    int nlev = 0;     // all levels
+    int nbig = 0;     // levels [0, nbig) use the tiled kernels, [nbig, nlev) the one-block cycle
     int lnx[MAXLEV], lny[MAXLEV];
-    double *cd[MAXLEV], *dd[MAXLEV], *wx64[MAXLEV], *wy64[MAXLEV];
-    float *fdiag[MAXLEV], *fwx[MAXLEV], *fwy[MAXLEV], *fx[MAXLEV], *fb[MAXLEV];
-    double *ddiag[MAXLEV], *dwx[MAXLEV], *dwy[MAXLEV], *dx[MAXLEV], *db[MAXLEV];
-    double *r64, *z64, *p64, *q64;
-    float *r32, *z32, *p32, *q32, *e32, *b32;
-    double* ir_r64;
-    double *partial, *partial2;
-    unsigned* ticket;
-    double *scal, *oscal, *beta;
-    int* flags;
-    int* host_flags;   // pinned, set by the owner
-    int launches = 0;
-    // optional CUDA-event timing of the level-0 smoother sweeps (the dominant kernel class)
-    bool timing = false;
-    int ev_cap = 0, ev_used = 0;
-    long long timed_launches = 0;
-    cudaEvent_t* ev = nullptr;
-    void time_begin();
-    void time_mark(cudaStream_t st);   // records one event (pairs: start, stop)
-    double time_end_ms();               // synchronises, sums the recorded pairs
+    size_t loff[MAXLEV];   // cell offset of level l in the packed per-level arrays
+    size_t ncells_all = 0;
+    // per-level operators, packed over levels (float and double copies): diag, wl, wb, cd, dd
+    float *f_diag, *f_wl, *f_wb, *f_cd, *f_dd;
+    double *d_diag, *d_wl, *d_wb, *d_cd, *d_dd;
+    // per-level vectors (2 right-hand sides interleaved), packed: x (correction) and b (rhs)
+    float *f_x, *f_b;
+    double *d_x, *d_b;
+    // CG vectors at level 0 (2 RHS interleaved)
+    float *f_r, *f_p, *f_q, *f_e;
+    double *d_r, *d_p, *d_q;
+    // reductions
+    double* partial;   // [4][MAXBLK][2]
+    unsigned* tickets; // 8
+    static constexpr int NSLOT = 8;
+    SolveState* st_base;   // device, one state per solve slot
+    SolveState* st_host;   // pinned mirror of all slots (set by the owner)
+    SolveState* st = nullptr;   // slot of the current solve
+    int slot = 0;
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   // capture streams of loop bodies
+    KTimer* timer;     // device, [2]: tiled level-0 pre / post kernels
+    int timing = 0;
+    long long launches = 0;
+    int use_graph = 0;     // set by the owner while capturing
 
     void plan(int nx, int ny);
     static size_t bytes(int nx, int ny);
     void bind(void* base, int nx, int ny);
-    // Solve A x = b; A given at the fine level by cd, dd, wx, wy (FP64); x holds the guess.
-    SolveResult solve(const double* cd0, const double* dd0, const double* wx0, const double* wy0, const double* b,
-                      double* x, int precision, double rtol, int max_iter, cudaStream_t st);
+    // Solve A x = b for nr (1 or 2) interleaved right-hand sides.  The fine operator is given
+    // cell-centred in FP64: cd (h^2 c), dd (Dirichlet terms), wl (left-face weight), wb
+    // (bottom-face weight); x holds the initial guess.  In graph mode (use_graph) the loops
+    // become conditional nodes of the graph being captured on `st`; the result is then only
+    // available after the graph ran (read it with read_result).
+    void solve(const double* cd, const double* dd, const double* wl, const double* wb, const double* b, double* x,
+               int nr, int precision, double rtol, int max_iter, cudaStream_t st);
+    SolveResult read_result(int slot, int precision, cudaStream_t st);
+    static bool supported(int nx, int ny);
+    int body_size() const;   // kernels of one CG iteration (V-cycle + apply + update)
 };
 
 }  // namespace ebit

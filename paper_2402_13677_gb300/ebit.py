@@ -35,8 +35,9 @@ FIELD_DTYPES = {F_CCOL: np.uint8, F_BAND: np.uint8, F_VCOL: np.uint8, F_CSEG: np
 
 EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_field", "ebit_get_field",
            "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
-           "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_last_error", "ebit_destroy",
-           "ebit_version"]
+           "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_set_option", "ebit_last_error",
+           "ebit_destroy", "ebit_version"]
+EBIT_OPT_GRAPH = 1
 EBIT_KT_SMOOTH_L0 = 1
 
 
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
     lib.ebit_launch_count.argtypes = [vp]
     lib.ebit_launch_count.restype = C.c_uint64
     lib.ebit_timing_begin.argtypes = [vp, i32]
+    lib.ebit_set_option.argtypes = [vp, i32, i32]
     lib.ebit_timing_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
     lib.ebit_last_error.argtypes = [vp]
     lib.ebit_last_error.restype = C.c_char_p
@@ -223,6 +225,10 @@ def ebit_timing_end(ctx):
     ms, n, b = C.c_double(), C.c_uint64(), C.c_double()
     _check(ctx, load().ebit_timing_end(ctx, C.byref(ms), C.byref(n), C.byref(b)))
     return ms.value, n.value, b.value
+
+
+def ebit_set_option(ctx, option, value):
+    _check(ctx, load().ebit_set_option(ctx, option, value))
 
 
 def ebit_last_error(ctx):

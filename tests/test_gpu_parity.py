@@ -24,6 +24,12 @@ FIELDS = ("T_l", "T_v", "u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v", "p", "
 TOL64 = 1e-10
 
 
+class Dev:
+    def __init__(self):
+        self.alloc = E.TorchAllocator()
+        self.stream = torch.cuda.Stream()   # non-default stream: ebit_step runs as a CUDA graph
+
+
 @pytest.fixture(scope="module")
 def dev():
     if not torch.cuda.is_available():
@@ -31,13 +37,13 @@ def dev():
     import __graft_entry__ as g
     g.build()
     torch.cuda.set_device(0)
-    return E.TorchAllocator()
+    return Dev()
 
 
-def gpu_ctx(dev, st, precision=E.EBIT_FP64, rtol=1e-13, max_iter=600):
+def gpu_ctx(dev, st, precision=E.EBIT_FP64, rtol=1e-13, max_iter=600, graph=True):
     pb = st.pb
-    ctx = E.ebit_init([E.config_from_problem(pb, precision, rtol, max_iter)],
-                      torch.cuda.current_stream().cuda_stream, dev)
+    ctx = E.ebit_init([E.config_from_problem(pb, precision, rtol, max_iter)], dev.stream.cuda_stream, dev.alloc)
+    E.ebit_set_option(ctx, E.EBIT_OPT_GRAPH, 1 if graph else 0)
     E.upload_state(ctx, 0, pb, st.vcol, st.hx_pos, st.vy_pos, {k: getattr(st, k) for k in FIELDS}, st.t)
     E.ebit_run_stage(ctx, E.STAGE_RECONSTRUCT)
     return ctx
@@ -70,6 +76,9 @@ def cases():
         "bubble": lambda: w.bubble(n=48, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01, dt=1e-4, steps=0),
         "film": lambda: w.film(40, 56, Lx=1.0, mean=0.31, amp=0.04, modes=2, seed=3, steps=0, dt=2e-3),
         "mdot_bubble": lambda: w.const_mdot_bubble(n=40, L=8.0, R0=2.1, mdot=0.1, dt=0.1, steps=0),
+        # above 4096 cells: the tiled multigrid kernels run (32x32 tiles, ragged in x and y here)
+        "bubble_mid": lambda: w.bubble(n=96, R0=0.21, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01, dt=5e-5, steps=0),
+        "film_mid": lambda: w.film(80, 88, Lx=1.0, mean=0.27, amp=0.03, modes=3, seed=5, steps=0, dt=1e-3),
     }
 
 
@@ -111,8 +120,7 @@ def test_reconstruction_bit_exact(dev, name):
 def test_prepare_matches_oracle(dev, name):
     pb = cases()[name]()
     st = S.State(pb)
-    ctx = E.ebit_init([E.config_from_problem(pb, E.EBIT_FP64, 1e-13, 600)],
-                      torch.cuda.current_stream().cuda_stream, dev)
+    ctx = E.ebit_init([E.config_from_problem(pb, E.EBIT_FP64, 1e-13, 600)], dev.stream.cuda_stream, dev.alloc)
     try:
         E.upload_state(ctx, 0, pb, st.vcol, st.hx_pos, st.vy_pos, {k: getattr(st, k) for k in FIELDS}, st.t)
         E.ebit_run_stage(ctx, E.STAGE_PREPARE)
@@ -319,5 +327,38 @@ def test_edge_cases_empty_interface_and_invalid_input(dev):
         with pytest.raises(E.EbitError) as ei:
             E.ebit_set_interface(ctx, 0, vcol, bad, pb.vy_pos)
         assert ei.value.status == E.EBIT_ETOPO
+    finally:
+        E.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [E.EBIT_FP64, E.EBIT_MIXED])
+def test_graph_replay_equals_host_driven_step(dev, prec):
+    """The CUDA-graph step (solver loops as conditional nodes) and the host-driven step run the
+    same kernels on the same data: the results are identical bit for bit."""
+    st = prepared("bubble", 1)
+    out = []
+    for graph in (True, False):
+        ctx = gpu_ctx(dev, st, precision=prec, rtol=1e-10, graph=graph)
+        try:
+            E.ebit_step(ctx, 3)
+            out.append((E.download(ctx, 0, st.pb.nx, st.pb.ny), E.ebit_get_diagnostics(ctx, 0)))
+        finally:
+            E.ebit_destroy(ctx)
+    (a, da), (b, db) = out
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(da[6:9], db[6:9])      # iteration counts
+
+
+def test_solver_statistics_reported(dev):
+    st = prepared("bubble", 0)
+    ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-8)
+    try:
+        n0 = E.ebit_launch_count(ctx)
+        E.ebit_step(ctx, 2)
+        d = E.ebit_get_diagnostics(ctx, 0)
+        assert d[6] > 0 and d[7] > 0 and d[8] > 0          # energy, viscous, Poisson iterations
+        assert max(d[9], d[10], d[11]) <= 1e-8              # final relative residuals
+        assert E.ebit_launch_count(ctx) - n0 > 50
     finally:
         E.ebit_destroy(ctx)

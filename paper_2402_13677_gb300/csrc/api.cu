@@ -273,7 +273,7 @@ static void collect_stats(Instance& I, cudaStream_t st, bool graph_step) {
     if (!m) return;
     SolveResult r[4];
     bool ok = true;
-    long long body = I.solver.body_size(), n = 0;
+    long long body = I.solver.body_size(I.cfg.precision), n = 0;
     for (int k = 0; k < 4; ++k) {
         if (!(m & (1u << k))) continue;
         r[k] = I.solver.read_result(k, I.cfg.precision, st);

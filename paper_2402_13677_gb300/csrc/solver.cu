@@ -41,10 +41,12 @@ namespace ebit {
 
 constexpr int RB = 256;          // threads of grid-stride kernels
 constexpr int NRED = 608;        // blocks of grid-stride kernels (4 x 152 SMs)
-constexpr int SMALL_MAX = 4096;  // levels with at most this many cells run inside k_small
+constexpr int SMALL_MAX_F = 4096; // levels with at most this many cells run inside k_small (FP32)
+constexpr int SMALL_MAX_D = 1024; // (FP64: half the shared memory per value)
+constexpr int SMALL_THREADS = 512;
 constexpr int TX = 32, TY = 32;  // tile of the large-level kernels
 constexpr int NU = 2;            // smoothing sweeps (red-black pairs) before and after
-constexpr int COARSE_PAIRS = 24; // symmetric sweeps on the coarsest grid
+constexpr int COARSE_PAIRS = 12; // symmetric sweeps on the coarsest grid (at most 16 cells)
 
 template <typename T, int NR>
 struct alignas(sizeof(T) * NR) Vec {
@@ -202,23 +204,29 @@ struct Region {
     static constexpr size_t bytes() { return (size_t)N * (2 * NR + 3) * sizeof(T); }
 };
 
-// one Gauss-Seidel half-sweep of colour `color` over region cells at distance >= s from its edge
+// one Gauss-Seidel half-sweep of colour `color` over region cells at distance >= s from its
+// edge; threads are laid out 32 x 8, each row visits only the cells of the colour
 template <typename T, int NR, int H>
 __device__ inline void region_sweep(Region<T, NR, H>& R, int gx0, int gy0, int nx, int ny, int s, int color) {
     constexpr int SX = Region<T, NR, H>::SX, SY = Region<T, NR, H>::SY;
-    int w = SX - 2 * s, hgt = SY - 2 * s;
-    for (int k = threadIdx.x; k < w * hgt; k += blockDim.x) {
-        int rx = s + k % w, ry = s + k / w;
-        int gi = gx0 + rx, gj = gy0 + ry;
-        if (gi < 0 || gi >= nx || gj < 0 || gj >= ny || ((gi + gj) & 1) != color) continue;
-        int q = ry * SX + rx;
-        T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + SX];
-        T d = R.d[q];
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int ry = s + ty; ry < SY - s; ry += 8) {
+        int gj = gy0 + ry;
+        if (gj < 0 || gj >= ny) continue;
+        int par = (color - gx0 - gj) & 1;          // rx parity of this colour in this row
+        int rx0 = s + ((par - s) & 1);
+        for (int rx = rx0 + 2 * tx; rx < SX - s; rx += 64) {
+            int gi = gx0 + rx;
+            if (gi < 0 || gi >= nx) continue;
+            int q = ry * SX + rx;
+            T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + SX];
+            T d = R.d[q];
 #pragma unroll
-        for (int k2 = 0; k2 < NR; ++k2) {
-            T acc = R.b[q * NR + k2] + wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
-                    wb * R.x[(q - SX) * NR + k2] + wt * R.x[(q + SX) * NR + k2];
-            R.x[q * NR + k2] = acc / d;
+            for (int k2 = 0; k2 < NR; ++k2) {
+                T acc = R.b[q * NR + k2] + wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
+                        wb * R.x[(q - SX) * NR + k2] + wt * R.x[(q + SX) * NR + k2];
+                R.x[q * NR + k2] = acc / d;
+            }
         }
     }
     __syncthreads();
@@ -227,29 +235,34 @@ __device__ inline void region_sweep(Region<T, NR, H>& R, int gx0, int gy0, int n
 template <typename T, int NR, int H>
 __device__ inline void region_load(Region<T, NR, H>& R, const Lev<T>& L, const T* __restrict__ b,
                                    const T* __restrict__ x, const T* __restrict__ xc, int cnx, int gx0, int gy0) {
-    constexpr int SX = Region<T, NR, H>::SX, N = Region<T, NR, H>::N;
-    for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        int rx = q % SX, ry = q / SX;
-        int gi = gx0 + rx, gj = gy0 + ry;
-        bool in = gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny;
-        int c = gj * L.nx + gi;
-        Vec<T, NR> bv, xv;
+    constexpr int SX = Region<T, NR, H>::SX, SY = Region<T, NR, H>::SY;
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int ry = ty; ry < SY; ry += 8) {
+        int gj = gy0 + ry;
+        bool jin = gj >= 0 && gj < L.ny;
+        for (int rx = tx; rx < SX; rx += 32) {
+            int gi = gx0 + rx;
+            bool in = jin && gi >= 0 && gi < L.nx;
+            int q = ry * SX + rx;
+            int c = gj * L.nx + gi;
+            Vec<T, NR> bv, xv;
 #pragma unroll
-        for (int k = 0; k < NR; ++k) { bv.v[k] = T(0); xv.v[k] = T(0); }
-        if (in) {
-            bv = reinterpret_cast<const Vec<T, NR>*>(b)[c];
-            if (x) {
-                xv = reinterpret_cast<const Vec<T, NR>*>(x)[c];
-                Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gj >> 1) * cnx + (gi >> 1)];
+            for (int k = 0; k < NR; ++k) { bv.v[k] = T(0); xv.v[k] = T(0); }
+            if (in) {
+                bv = reinterpret_cast<const Vec<T, NR>*>(b)[c];
+                if (x) {
+                    xv = reinterpret_cast<const Vec<T, NR>*>(x)[c];
+                    Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gj >> 1) * cnx + (gi >> 1)];
 #pragma unroll
-                for (int k = 0; k < NR; ++k) xv.v[k] += cv.v[k];
+                    for (int k = 0; k < NR; ++k) xv.v[k] += cv.v[k];
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < NR; ++k) { R.b[q * NR + k] = bv.v[k]; R.x[q * NR + k] = xv.v[k]; }
-        R.d[q] = in ? L.diag[c] : T(1);
-        R.wl[q] = in ? L.wl[c] : T(0);
-        R.wb[q] = in ? L.wb[c] : T(0);
+            for (int k = 0; k < NR; ++k) { R.b[q * NR + k] = bv.v[k]; R.x[q * NR + k] = xv.v[k]; }
+            R.d[q] = in ? L.diag[c] : T(1);
+            R.wl[q] = in ? L.wl[c] : T(0);
+            R.wb[q] = in ? L.wb[c] : T(0);
+        }
     }
     __syncthreads();
 }
@@ -349,67 +362,79 @@ __global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b,
 
 // ---- small levels: the rest of the V-cycle in one block ---------------------------------
 struct SmallPlan {
-    int n;             // number of small levels (the first is `lev0`)
+    int n;             // number of small levels
     int nx[Solver::MAXLEV], ny[Solver::MAXLEV];
     int soff[Solver::MAXLEV];   // cell offset of each small level inside the shared-memory arrays
     size_t goff[Solver::MAXLEV]; // cell offset in the packed global level arrays
+    int total;         // cells of all small levels
+};
+
+// shared-memory layout: x[NR*total], b[NR*total], diag[total], wl[total], wb[total]
+template <typename T, int NR>
+struct SmallMem {
+    T *x, *b, *d, *wl, *wb;
+    __device__ SmallMem(unsigned char* base, int total) {
+        x = (T*)base;
+        b = x + (size_t)NR * total;
+        d = b + (size_t)NR * total;
+        wl = d + total;
+        wb = wl + total;
+    }
+    static size_t bytes(int total) { return (size_t)total * (2 * NR + 3) * sizeof(T); }
 };
 
 template <typename T, int NR>
-__device__ inline void small_sweep(const SmallPlan& P, int l, const T* __restrict__ diag, const T* __restrict__ wl,
-                                   const T* __restrict__ wb, T* xs, const T* bs, int color) {
-    int nx = P.nx[l], ny = P.ny[l];
-    const T* dg = diag + P.goff[l];
-    const T* gl = wl + P.goff[l];
-    const T* gb = wb + P.goff[l];
-    T* x = xs + (size_t)P.soff[l] * NR;
-    const T* b = bs + (size_t)P.soff[l] * NR;
+__device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M, int color) {
+    int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
     for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
         int i = c % nx, j = c / nx;
         if (((i + j) & 1) != color) continue;
-        T w0 = gl[c], w1 = i < nx - 1 ? gl[c + 1] : T(0), w2 = gb[c], w3 = j < ny - 1 ? gb[c + nx] : T(0);
+        int q = o + c;
+        T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            T acc = b[c * NR + k];
-            if (i > 0) acc += w0 * x[(c - 1) * NR + k];
-            if (i < nx - 1) acc += w1 * x[(c + 1) * NR + k];
-            if (j > 0) acc += w2 * x[(c - nx) * NR + k];
-            if (j < ny - 1) acc += w3 * x[(c + nx) * NR + k];
-            x[c * NR + k] = acc / dg[c];
+            T acc = M.b[q * NR + k];
+            if (i > 0) acc += w0 * M.x[(q - 1) * NR + k];
+            if (i < nx - 1) acc += w1 * M.x[(q + 1) * NR + k];
+            if (j > 0) acc += w2 * M.x[(q - nx) * NR + k];
+            if (j < ny - 1) acc += w3 * M.x[(q + nx) * NR + k];
+            M.x[q * NR + k] = acc / M.d[q];
         }
     }
     __syncthreads();
 }
 
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(1024) k_small(SmallPlan P, const T* __restrict__ diag, const T* __restrict__ wl,
-                                                const T* __restrict__ wb, const T* __restrict__ b_in,
-                                                T* __restrict__ x_out, SolveState* st) {
+__global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* __restrict__ diag,
+                                                         const T* __restrict__ wl, const T* __restrict__ wb,
+                                                         const T* __restrict__ b_in, T* __restrict__ x_out,
+                                                         SolveState* st) {
     if (skip(st)) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    int total = P.soff[P.n - 1] + P.nx[P.n - 1] * P.ny[P.n - 1];
-    T* xs = (T*)smem;
-    T* bs = xs + (size_t)total * NR;
+    SmallMem<T, NR> M(smem, P.total);
+    for (int l = 0; l < P.n; ++l) {
+        int n = P.nx[l] * P.ny[l];
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            int q = P.soff[l] + c;
+            M.d[q] = diag[P.goff[l] + c];
+            M.wl[q] = wl[P.goff[l] + c];
+            M.wb[q] = wb[P.goff[l] + c];
+        }
+    }
     int n0 = P.nx[0] * P.ny[0];
-    for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) bs[c] = b_in[c];
+    for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) M.b[c] = b_in[c];
     __syncthreads();
     // down
     for (int l = 0; l < P.n - 1; ++l) {
-        T* x = xs + (size_t)P.soff[l] * NR;
-        int nx = P.nx[l], ny = P.ny[l];
-        for (int c = threadIdx.x; c < nx * ny * NR; c += blockDim.x) x[c] = T(0);
+        int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
+        for (int c = threadIdx.x; c < nx * ny * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
         __syncthreads();
         for (int k = 0; k < NU; ++k) {
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
+            small_sweep<T, NR>(P, l, M, 0);
+            small_sweep<T, NR>(P, l, M, 1);
         }
         // residual, restricted to level l+1
-        const T* dg = diag + P.goff[l];
-        const T* gl = wl + P.goff[l];
-        const T* gb = wb + P.goff[l];
-        const T* b = bs + (size_t)P.soff[l] * NR;
-        T* bc = bs + (size_t)P.soff[l + 1] * NR;
-        int cnx = P.nx[l + 1], cny = P.ny[l + 1];
+        int cnx = P.nx[l + 1], cny = P.ny[l + 1], co = P.soff[l + 1];
         for (int C = threadIdx.x; C < cnx * cny; C += blockDim.x) {
             int I = C % cnx, J = C / cnx;
             T acc[NR];
@@ -417,62 +442,59 @@ __global__ void __launch_bounds__(1024) k_small(SmallPlan P, const T* __restrict
             for (int k = 0; k < NR; ++k) acc[k] = T(0);
             for (int d2 = 0; d2 < 4; ++d2) {
                 int i = 2 * I + (d2 & 1), j = 2 * J + (d2 >> 1);
-                int c = j * nx + i;
-                T w0 = gl[c], w1 = i < nx - 1 ? gl[c + 1] : T(0), w2 = gb[c], w3 = j < ny - 1 ? gb[c + nx] : T(0);
+                int q = o + j * nx + i;
+                T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
-                    T s = T(0);
-                    if (i > 0) s += w0 * x[(c - 1) * NR + k];
-                    if (i < nx - 1) s += w1 * x[(c + 1) * NR + k];
-                    if (j > 0) s += w2 * x[(c - nx) * NR + k];
-                    if (j < ny - 1) s += w3 * x[(c + nx) * NR + k];
-                    acc[k] += b[c * NR + k] - (dg[c] * x[c * NR + k] - s);
+                    T sn = T(0);
+                    if (i > 0) sn += w0 * M.x[(q - 1) * NR + k];
+                    if (i < nx - 1) sn += w1 * M.x[(q + 1) * NR + k];
+                    if (j > 0) sn += w2 * M.x[(q - nx) * NR + k];
+                    if (j < ny - 1) sn += w3 * M.x[(q + nx) * NR + k];
+                    acc[k] += M.b[q * NR + k] - (M.d[q] * M.x[q * NR + k] - sn);
                 }
             }
 #pragma unroll
-            for (int k = 0; k < NR; ++k) bc[C * NR + k] = acc[k];
+            for (int k = 0; k < NR; ++k) M.b[(co + C) * NR + k] = acc[k];
         }
         __syncthreads();
     }
     // coarsest: symmetric sweep sequence from zero
     {
-        int l = P.n - 1;
-        T* x = xs + (size_t)P.soff[l] * NR;
-        for (int c = threadIdx.x; c < P.nx[l] * P.ny[l] * NR; c += blockDim.x) x[c] = T(0);
+        int l = P.n - 1, o = P.soff[l];
+        for (int c = threadIdx.x; c < P.nx[l] * P.ny[l] * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
         __syncthreads();
         for (int k = 0; k < COARSE_PAIRS; ++k) {
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
+            small_sweep<T, NR>(P, l, M, 0);
+            small_sweep<T, NR>(P, l, M, 1);
         }
         for (int k = 0; k < COARSE_PAIRS; ++k) {
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
+            small_sweep<T, NR>(P, l, M, 1);
+            small_sweep<T, NR>(P, l, M, 0);
         }
     }
     // up
     for (int l = P.n - 2; l >= 0; --l) {
-        T* x = xs + (size_t)P.soff[l] * NR;
-        const T* xc = xs + (size_t)P.soff[l + 1] * NR;
-        int nx = P.nx[l], ny = P.ny[l], cnx = P.nx[l + 1];
+        int nx = P.nx[l], ny = P.ny[l], o = P.soff[l], cnx = P.nx[l + 1], co = P.soff[l + 1];
         for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
             int i = c % nx, j = c / nx;
 #pragma unroll
-            for (int k = 0; k < NR; ++k) x[c * NR + k] += xc[((j >> 1) * cnx + (i >> 1)) * NR + k];
+            for (int k = 0; k < NR; ++k) M.x[(o + c) * NR + k] += M.x[(co + (j >> 1) * cnx + (i >> 1)) * NR + k];
         }
         __syncthreads();
         for (int k = 0; k < NU; ++k) {
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 1);
-            small_sweep<T, NR>(P, l, diag, wl, wb, xs, bs, 0);
+            small_sweep<T, NR>(P, l, M, 1);
+            small_sweep<T, NR>(P, l, M, 0);
         }
     }
-    for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) x_out[c] = xs[c];
+    for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) x_out[c] = M.x[c];
     if (DOT) {
         // the cycle started at the finest level: r.z -> beta (one block, fixed order)
         __shared__ double sh[32];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
             double a = 0.0;
-            for (int c = threadIdx.x; c < n0; c += blockDim.x) a += (double)xs[c * NR + k] * (double)bs[c * NR + k];
+            for (int c = threadIdx.x; c < n0; c += blockDim.x) a += (double)M.x[c * NR + k] * (double)M.b[c * NR + k];
             a = bsum(a, sh);
             if (threadIdx.x == 0) {
                 double old = st->rz[k];
@@ -750,13 +772,16 @@ void Solver::plan(int nx_, int ny_) {
         off += (size_t)x * y;
         ++nlev;
         if (nlev == MAXLEV) break;
-        if ((x & 1) || (y & 1) || (long long)x * y <= 64 || x < 4 || y < 4) break;
+        if ((x & 1) || (y & 1) || (long long)x * y <= 16 || x < 2 || y < 2) break;
         x /= 2;
         y /= 2;
     }
     ncells_all = off;
-    nbig = 0;
-    while (nbig < nlev - 1 && (long long)lnx[nbig] * lny[nbig] > SMALL_MAX) ++nbig;
+    nbig_f = 0;
+    while (nbig_f < nlev - 1 && (long long)lnx[nbig_f] * lny[nbig_f] > SMALL_MAX_F) ++nbig_f;
+    nbig_d = 0;
+    while (nbig_d < nlev - 1 && (long long)lnx[nbig_d] * lny[nbig_d] > SMALL_MAX_D) ++nbig_d;
+    nbig = nbig_f;
 }
 
 static size_t tiles(int nx, int ny) { return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
@@ -782,8 +807,8 @@ size_t Solver::bytes(int nx, int ny) {
 }
 
 template <typename K>
-static void allow_smem(K kern, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+static void allow_smem(K kern, int bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void Solver::bind(void* base, int nx_, int ny_) {
@@ -808,28 +833,28 @@ void Solver::bind(void* base, int nx_, int ny_) {
     timer = (KTimer*)take(4 * sizeof(KTimer));
     for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&aux[k], cudaStreamNonBlocking);
     // shared-memory limits of the tile kernels
-    allow_smem(k_pre<float, 1>, Region<float, 1, 2 * NU + 1>::bytes());
-    allow_smem(k_pre<float, 2>, Region<float, 2, 2 * NU + 1>::bytes());
-    allow_smem(k_pre<double, 1>, Region<double, 1, 2 * NU + 1>::bytes());
-    allow_smem(k_pre<double, 2>, Region<double, 2, 2 * NU + 1>::bytes());
-    allow_smem(k_post<float, 1, true>, Region<float, 1, 2 * NU>::bytes());
-    allow_smem(k_post<float, 1, false>, Region<float, 1, 2 * NU>::bytes());
-    allow_smem(k_post<float, 2, true>, Region<float, 2, 2 * NU>::bytes());
-    allow_smem(k_post<float, 2, false>, Region<float, 2, 2 * NU>::bytes());
-    allow_smem(k_post<double, 1, true>, Region<double, 1, 2 * NU>::bytes());
-    allow_smem(k_post<double, 1, false>, Region<double, 1, 2 * NU>::bytes());
-    allow_smem(k_post<double, 2, true>, Region<double, 2, 2 * NU>::bytes());
-    allow_smem(k_post<double, 2, false>, Region<double, 2, 2 * NU>::bytes());
-    size_t small_cells = 0;
-    for (int l = nbig; l < nlev; ++l) small_cells += (size_t)lnx[l] * lny[l];
-    allow_smem(k_small<float, 1, true>, small_cells * 2 * 1 * 4);
-    allow_smem(k_small<float, 1, false>, small_cells * 2 * 1 * 4);
-    allow_smem(k_small<float, 2, true>, small_cells * 2 * 2 * 4);
-    allow_smem(k_small<float, 2, false>, small_cells * 2 * 2 * 4);
-    allow_smem(k_small<double, 1, true>, small_cells * 2 * 1 * 8);
-    allow_smem(k_small<double, 1, false>, small_cells * 2 * 1 * 8);
-    allow_smem(k_small<double, 2, true>, small_cells * 2 * 2 * 8);
-    allow_smem(k_small<double, 2, false>, small_cells * 2 * 2 * 8);
+    // shared-memory opt-in of the tile and small-level kernels (dynamic + static may pass 48 KB)
+    const int SM = 200 * 1024;
+    allow_smem(k_pre<float, 1>, SM);
+    allow_smem(k_pre<float, 2>, SM);
+    allow_smem(k_pre<double, 1>, SM);
+    allow_smem(k_pre<double, 2>, SM);
+    allow_smem(k_post<float, 1, true>, SM);
+    allow_smem(k_post<float, 1, false>, SM);
+    allow_smem(k_post<float, 2, true>, SM);
+    allow_smem(k_post<float, 2, false>, SM);
+    allow_smem(k_post<double, 1, true>, SM);
+    allow_smem(k_post<double, 1, false>, SM);
+    allow_smem(k_post<double, 2, true>, SM);
+    allow_smem(k_post<double, 2, false>, SM);
+    allow_smem(k_small<float, 1, true>, SM);
+    allow_smem(k_small<float, 1, false>, SM);
+    allow_smem(k_small<float, 2, true>, SM);
+    allow_smem(k_small<float, 2, false>, SM);
+    allow_smem(k_small<double, 1, true>, SM);
+    allow_smem(k_small<double, 1, false>, SM);
+    allow_smem(k_small<double, 2, true>, SM);
+    allow_smem(k_small<double, 2, false>, SM);
     KTimer init[4];
     for (auto& t : init) { t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; }
     cudaMemcpy(timer, init, sizeof(init), cudaMemcpyHostToDevice);
@@ -884,13 +909,37 @@ static void setup_levels(Solver& s, const double* cd, const double* dd, const do
 }
 
 // z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved)
+template <typename T> static int nbig_of(const Solver& s);
+template <> int nbig_of<float>(const Solver& s) { return s.nbig_f; }
+template <> int nbig_of<double>(const Solver& s) { return s.nbig_d; }
+
+template <typename T>
+static SmallPlan small_plan(const Solver& s) {
+    SmallPlan P;
+    int nb = nbig_of<T>(s);
+    P.n = s.nlev - nb;
+    int so = 0;
+    for (int k = 0; k < P.n; ++k) {
+        int l = nb + k;
+        P.nx[k] = s.lnx[l];
+        P.ny[k] = s.lny[l];
+        P.soff[k] = so;
+        P.goff[k] = s.loff[l];
+        so += s.lnx[l] * s.lny[l];
+    }
+    P.total = so;
+    return P;
+}
+
+// z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved)
 template <typename T, int NR>
 static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm) {
     T* X = PT<T>::x(s);
     T* B = PT<T>::b(s);
     const T* b = r;
     T* x = z;
-    for (int l = 0; l < s.nbig; ++l) {
+    int nb = nbig_of<T>(s);
+    for (int l = 0; l < nb; ++l) {
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
         T* bc = B + 2 * s.loff[l + 1];
@@ -901,27 +950,17 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         x = X + 2 * s.loff[l + 1];
     }
     {
-        SmallPlan P;
-        P.n = s.nlev - s.nbig;
-        int so = 0;
-        for (int k = 0; k < P.n; ++k) {
-            int l = s.nbig + k;
-            P.nx[k] = s.lnx[l];
-            P.ny[k] = s.lny[l];
-            P.soff[k] = so;
-            P.goff[k] = s.loff[l];
-            so += s.lnx[l] * s.lny[l];
-        }
-        size_t smem = (size_t)so * 2 * NR * sizeof(T);
-        int n0 = P.nx[0] * P.ny[0];
-        int threads = n0 >= 1024 ? 1024 : ((n0 + 31) / 32) * 32;
-        if (s.nbig == 0)
-            k_small<T, NR, true><<<1, threads, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x, st);
+        SmallPlan P = small_plan<T>(s);
+        size_t smem = SmallMem<T, NR>::bytes(P.total);
+        if (nb == 0)
+            k_small<T, NR, true><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x,
+                                                                  st);
         else
-            k_small<T, NR, false><<<1, threads, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x, st);
+            k_small<T, NR, false><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b,
+                                                                   x, st);
         if (!s.use_graph) ++s.launches;
     }
-    for (int l = s.nbig - 1; l >= 0; --l) {
+    for (int l = nb - 1; l >= 0; --l) {
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
         const T* bl = l == 0 ? r : B + 2 * s.loff[l];
@@ -1085,12 +1124,12 @@ void Solver::solve(const double* cd, const double* dd, const double* wl, const d
     }
 }
 
-int Solver::body_size() const { return 2 * nbig + 1 + 2; }
+int Solver::body_size(int precision) const { return 2 * (precision == 0 ? nbig_d : nbig_f) + 1 + 2; }
 
 bool Solver::supported(int nx, int ny) {
     Solver s;
     s.plan(nx, ny);
-    return (long long)s.lnx[s.nlev - 1] * s.lny[s.nlev - 1] <= SMALL_MAX;
+    return (long long)s.lnx[s.nlev - 1] * s.lny[s.nlev - 1] <= SMALL_MAX_D;
 }
 
 SolveResult Solver::read_result(int sl, int precision, cudaStream_t stm) {

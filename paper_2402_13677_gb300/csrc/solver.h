@@ -38,6 +38,7 @@ struct Solver {
     int nx = 0, ny = 0;
     int nlev = 0;     // all levels
     int nbig = 0;     // levels [0, nbig) use the tiled kernels, [nbig, nlev) the one-block cycle
+    int nbig_f = 0, nbig_d = 0;   // the same split for FP32 and FP64 level data
     int lnx[MAXLEV], lny[MAXLEV];
     size_t loff[MAXLEV];   // cell offset of level l in the packed per-level arrays
     size_t ncells_all = 0;
@@ -76,7 +77,7 @@ struct Solver {
                int nr, int precision, double rtol, int max_iter, cudaStream_t st);
     SolveResult read_result(int slot, int precision, cudaStream_t st);
     static bool supported(int nx, int ny);
-    int body_size() const;   // kernels of one CG iteration (V-cycle + apply + update)
+    int body_size(int precision) const;   // kernels of one CG iteration (V-cycle + apply + update)
 };
 
 }  // namespace ebit

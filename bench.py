@@ -177,6 +177,8 @@ def run_ours(args):
     def new_ctx(precision):
         ctx = E.ebit_init([E.config_from_problem(pb, precision, args.rtol, args.max_iter)], stream.cuda_stream,
                           alloc)
+        if args.no_graph:
+            E.ebit_set_option(ctx, E.EBIT_OPT_GRAPH, 0)
         E.upload_state(ctx, 0, pb, pb.vcol, np.where(pb.hx_cut > 0, pb.hx_pos, 0.0),
                        np.where(pb.vy_cut > 0, pb.vy_pos, 0.0),
                        {"T_l": pb.T_l, "T_v": pb.T_v, "u_l": pb.u_l, "u_v": pb.u_v, "ufx_l": pb.ufx_l,
@@ -240,7 +242,8 @@ def run_ours(args):
     if args.profile_only:
         if rank == 0:
             r = results["mixed"]
-            print(json.dumps({"profile_only": True, "ms_per_step": 1e3 * r["secs"] / args.steps}), flush=True)
+            print(json.dumps({"profile_only": True, "workload": args.workload, "ms_per_step": 1e3 * r["secs"] / args.steps,
+                              "diag": r["diag"], "launches": r["launches"]}), flush=True)
         return 0
 
     # end to end through the C ABI with HOST buffers: every step uploads its inputs (the whole
@@ -355,6 +358,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels from the host (profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -1,9 +1,14 @@
 // Multigrid-preconditioned conjugate gradients for the implicit solves of the step
 // (energy diffusion, viscous Helmholtz, ghost-fluid Poisson).
 //
-// Operator (integrated five-point form, cell-centred coefficients):
-//     (A x)_i = diag_i x_i - wl_i x_{i-1} - wl_{i+1} x_{i+1} - wb_i x_{i-nx} - wb_{i+nx} x_{i+nx}
-//     diag_i  = cd_i + dd_i + wl_i + wl_{i+1} + wb_i + wb_{i+nx}
+// Operator (integrated five-point form, cell-centred coefficients), applied in flux form:
+//     (A x)_i = D_i x_i + wl_i (x_i - x_{i-1}) + wl_{i+1} (x_i - x_{i+1})
+//                       + wb_i (x_i - x_{i-nx}) + wb_{i+nx} (x_i - x_{i+nx}),   D_i = cd_i + dd_i
+// The flux form keeps the zero row sum of the conductance part exact in any precision: a
+// diagonal stored as cd + dd + sum w and rounded to FP32 separately from the w would add a
+// spurious diagonal of relative size 6e-8, above the smallest eigenvalue of a 4096^2 Poisson
+// operator (condition number ~1e9), and the FP32 solve would stall.  Smoothers use
+// diag = D + sum w computed on the fly.
 // with cd the h^2 (rho cp / dt or rho / dt) term, dd the Dirichlet contributions (ghost-fluid
 // interface links, fixed-temperature or no-slip walls, outflow pressure), wl/wb the left and
 // bottom face conductances (zero on domain faces).
@@ -138,17 +143,14 @@ __device__ inline void set_cond(cudaGraphConditionalHandle h, int use, unsigned 
 }
 
 // ---- operator setup -------------------------------------------------------------------
-// level 0 in precision T from the FP64 cell-centred operator
+// level 0 in precision T from the FP64 cell-centred operator (diag holds D = cd + dd)
 template <typename T>
 __global__ void k_setup0(int nx, int ny, const double* __restrict__ cd, const double* __restrict__ dd,
                          const double* __restrict__ wl, const double* __restrict__ wb, T* __restrict__ diag,
                          T* __restrict__ owl, T* __restrict__ owb, T* __restrict__ ocd, T* __restrict__ odd) {
     int N = nx * ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % nx, j = c / nx;
-        double r = i < nx - 1 ? wl[c + 1] : 0.0;
-        double t = j < ny - 1 ? wb[c + nx] : 0.0;
-        diag[c] = (T)(cd[c] + dd[c] + wl[c] + r + wb[c] + t);
+        diag[c] = (T)(cd[c] + dd[c]);
         owl[c] = (T)wl[c];
         owb[c] = (T)wb[c];
         ocd[c] = (T)cd[c];
@@ -164,14 +166,13 @@ __device__ inline void coarsen_cell(int fnx, const T* fcd, const T* fdd, const T
     T s_dd = T(0.5) * (fdd[f] + fdd[f + 1] + fdd[f + fnx] + fdd[f + fnx + 1]);
     T wl = T(0.5) * (fwl[f] + fwl[f + fnx]);
     T wb = T(0.5) * (fwb[f] + fwb[f + 1]);
-    T wr = I < nx - 1 ? T(0.5) * (fwl[f + 2] + fwl[f + 2 + fnx]) : T(0);
-    T wt = J < ny - 1 ? T(0.5) * (fwb[f + 2 * fnx] + fwb[f + 2 * fnx + 1]) : T(0);
     int c = J * nx + I;
     ccd[c] = s_cd;
     cdd[c] = s_dd;
     cwl[c] = wl;
     cwb[c] = wb;
-    cdiag[c] = s_cd + s_dd + wl + wr + wb + wt;
+    cdiag[c] = s_cd + s_dd;
+    (void)ny;
 }
 
 template <typename T>
@@ -220,7 +221,7 @@ __device__ inline void region_sweep(Region<T, NR, H>& R, int gx0, int gy0, int n
             if (gi < 0 || gi >= nx) continue;
             int q = ry * SX + rx;
             T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + SX];
-            T d = R.d[q];
+            T d = R.d[q] + wl + wr + wb + wt;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 T acc = R.b[q * NR + k2] + wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
@@ -259,7 +260,7 @@ __device__ inline void region_load(Region<T, NR, H>& R, const Lev<T>& L, const T
             }
 #pragma unroll
             for (int k = 0; k < NR; ++k) { R.b[q * NR + k] = bv.v[k]; R.x[q * NR + k] = xv.v[k]; }
-            R.d[q] = in ? L.diag[c] : T(1);
+            R.d[q] = in ? L.diag[c] : T(1);   // D = cd + dd
             R.wl[q] = in ? L.wl[c] : T(0);
             R.wb[q] = in ? L.wb[c] : T(0);
         }
@@ -306,8 +307,9 @@ __global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, 
             T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + Rg::SX], d = R.d[q];
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
-                T ax = d * R.x[q * NR + k2] - (wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
-                                               wb * R.x[(q - Rg::SX) * NR + k2] + wt * R.x[(q + Rg::SX) * NR + k2]);
+                T xc0 = R.x[q * NR + k2];
+                T ax = d * xc0 + wl * (xc0 - R.x[(q - 1) * NR + k2]) + wr * (xc0 - R.x[(q + 1) * NR + k2]) +
+                       wb * (xc0 - R.x[(q - Rg::SX) * NR + k2]) + wt * (xc0 - R.x[(q + Rg::SX) * NR + k2]);
                 acc.v[k2] += R.b[q * NR + k2] - ax;
             }
         }
@@ -391,6 +393,7 @@ __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M
         if (((i + j) & 1) != color) continue;
         int q = o + c;
         T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
+        T dg = M.d[q] + w0 + w1 + w2 + w3;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
             T acc = M.b[q * NR + k];
@@ -398,7 +401,7 @@ __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M
             if (i < nx - 1) acc += w1 * M.x[(q + 1) * NR + k];
             if (j > 0) acc += w2 * M.x[(q - nx) * NR + k];
             if (j < ny - 1) acc += w3 * M.x[(q + nx) * NR + k];
-            M.x[q * NR + k] = acc / M.d[q];
+            M.x[q * NR + k] = acc / dg;
         }
     }
     __syncthreads();
@@ -446,12 +449,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
                 T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
-                    T sn = T(0);
-                    if (i > 0) sn += w0 * M.x[(q - 1) * NR + k];
-                    if (i < nx - 1) sn += w1 * M.x[(q + 1) * NR + k];
-                    if (j > 0) sn += w2 * M.x[(q - nx) * NR + k];
-                    if (j < ny - 1) sn += w3 * M.x[(q + nx) * NR + k];
-                    acc[k] += M.b[q * NR + k] - (M.d[q] * M.x[q * NR + k] - sn);
+                    T xq = M.x[q * NR + k];
+                    T ax = M.d[q] * xq;
+                    if (i > 0) ax += w0 * (xq - M.x[(q - 1) * NR + k]);
+                    if (i < nx - 1) ax += w1 * (xq - M.x[(q + 1) * NR + k]);
+                    if (j > 0) ax += w2 * (xq - M.x[(q - nx) * NR + k]);
+                    if (j < ny - 1) ax += w3 * (xq - M.x[(q + nx) * NR + k]);
+                    acc[k] += M.b[q * NR + k] - ax;
                 }
             }
 #pragma unroll
@@ -532,19 +536,16 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
                 if (beta[k] != T(0)) a.v[k] += beta[k] * b.v[k];   // beta = 0: p = z (old p unused)
             return a;
         };
-        Vec<T, NR> pc = pn(c), s, qv;
-#pragma unroll
-        for (int k = 0; k < NR; ++k) s.v[k] = T(0);
-        if (i > 0) { T w = L.wl[c]; Vec<T, NR> a = pn(c - 1); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
-        if (i < L.nx - 1) { T w = L.wl[c + 1]; Vec<T, NR> a = pn(c + 1); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
-        if (j > 0) { T w = L.wb[c]; Vec<T, NR> a = pn(c - L.nx); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
-        if (j < L.ny - 1) { T w = L.wb[c + L.nx]; Vec<T, NR> a = pn(c + L.nx); for (int k = 0; k < NR; ++k) s.v[k] += w * a.v[k]; }
+        Vec<T, NR> pc = pn(c), qv;
         T d = L.diag[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            qv.v[k] = d * pc.v[k] - s.v[k];
-            acc[k] += (double)pc.v[k] * (double)qv.v[k];
-        }
+        for (int k = 0; k < NR; ++k) qv.v[k] = d * pc.v[k];
+        if (i > 0) { T w = L.wl[c]; Vec<T, NR> a = pn(c - 1); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
+        if (i < L.nx - 1) { T w = L.wl[c + 1]; Vec<T, NR> a = pn(c + 1); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
+        if (j > 0) { T w = L.wb[c]; Vec<T, NR> a = pn(c - L.nx); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
+        if (j < L.ny - 1) { T w = L.wb[c + L.nx]; Vec<T, NR> a = pn(c + L.nx); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
+#pragma unroll
+        for (int k = 0; k < NR; ++k) acc[k] += (double)pc.v[k] * (double)qv.v[k];
         Pn[c] = pc;
         Q[c] = qv;
     }
@@ -614,18 +615,18 @@ __global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __r
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int i = c % L.nx, j = c / L.nx;
-        Vec<double, NR> xv = X[c], bv = B[c], s;
+        Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
+        double dg = L.diag[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) s.v[k] = 0.0;
-        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - 1].v[k]; }
-        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + 1].v[k]; }
-        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - L.nx].v[k]; }
-        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + L.nx].v[k]; }
+        for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
+        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
+        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + 1].v[k]); }
+        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
+        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]); }
         Vec<double, NR> rv;
-        double d = L.diag[c];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            rv.v[k] = bv.v[k] - (d * xv.v[k] - s.v[k]);
+            rv.v[k] = bv.v[k] - s.v[k];
             acc[k] += rv.v[k] * rv.v[k];
             acc[NR + k] += bv.v[k] * bv.v[k];
         }
@@ -702,18 +703,18 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int i = c % L.nx, j = c / L.nx;
-        Vec<double, NR> xv = X[c], bv = B[c], s;
+        Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
+        double dg = L.diag[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) s.v[k] = 0.0;
-        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - 1].v[k]; }
-        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + 1].v[k]; }
-        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c - L.nx].v[k]; }
-        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * X[c + L.nx].v[k]; }
+        for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
+        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
+        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + 1].v[k]); }
+        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
+        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]); }
         Vec<float, NR> rf, ez;
-        double d = L.diag[c];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            double rv = bv.v[k] - (d * xv.v[k] - s.v[k]);
+            double rv = bv.v[k] - s.v[k];
             acc[k] += rv * rv;
             rf.v[k] = (float)rv;
             ez.v[k] = 0.0f;

@@ -194,6 +194,23 @@ enum { EBIT_KT_SMOOTH_L0 = 1 };
 ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class);
 ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes_per_launch);
 
+/* The library's multigrid-preconditioned CG (FP64, or FP32 inside FP64 refinement) applied
+ * to a caller-supplied five-point system on instance `inst`'s grid (host pointers, cell
+ * arrays of nx*ny doubles, layout above):
+ *   (A x)_i = D_i x_i + wl_i (x_i - x_{i-1}) + wl_{i+1} (x_i - x_{i+1})
+ *                     + wb_i (x_i - x_{i-nx}) + wb_{i+nx} (x_i - x_{i+nx}),
+ * wl_i / wb_i the weights of cell i's left / bottom face (0 on domain faces), D_i >= 0, the
+ * matrix symmetric positive definite.  nr = 1 or 2 right-hand sides interleaved per cell
+ * (b and x hold nr*nx*ny doubles; x is the initial guess on entry, the solution on return).
+ * Converges to ||b - A x||_2 <= rtol ||b||_2 per right-hand side; returns the iteration count
+ * (CG iterations, or total inner FP32 iterations in refinement mode) and the final relative
+ * residual.  This is the solver used by the energy, viscous and Poisson solves of ebit_step;
+ * it overwrites that instance's operator scratch (not its state).  EBIT_ENOCONV if max_iter
+ * is reached.  Synchronises. */
+ebit_status ebit_solve_system(ebit_ctx* ctx, int inst, const double* D, const double* wl, const double* wb,
+                              const double* b, double* x, int nr, int precision, double rtol, int max_iter,
+                              int* iters, double* rel_res);
+
 /* Options: EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the
  * context's stream (solver loops as conditional WHILE nodes, no host round trip inside a
  * step); 0 launches every kernel from the host.  Graph mode needs a non-default stream. */

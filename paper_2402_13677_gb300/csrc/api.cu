@@ -643,6 +643,39 @@ ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
     return worst;
 }
 
+ebit_status ebit_solve_system(ebit_ctx* ctx, int inst, const double* D, const double* wl, const double* wb,
+                              const double* b, double* x, int nr, int precision, double rtol, int max_iter,
+                              int* iters, double* rel_res) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !D || !wl || !wb || !b || !x || (nr != 1 && nr != 2) ||
+        (precision != EBIT_FP64 && precision != EBIT_MIXED) || !(rtol > 0) || max_iter < 1)
+        return fail(ctx, EBIT_EINVAL, "bad args");
+    Instance& I = ctx->inst[inst];
+    size_t N = (size_t)I.g.nx * I.g.ny;
+    cudaStream_t st = ctx->stream;
+    // host operands -> the instance's operator arrays (cd = D, dd = 0) and viscous vectors
+    cudaMemcpyAsync(I.op_cd, D, N * 8, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(I.op_dd, 0, N * 8, st);
+    cudaMemcpyAsync(I.op_wl, wl, N * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(I.op_wb, wb, N * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(I.vbx, b, N * 8 * nr, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(I.vxx, x, N * 8 * nr, cudaMemcpyHostToDevice, st);
+    I.solver.slot = 4;
+    I.solver.use_graph = 0;
+    long long l0 = I.solver.launches;
+    I.solver.solve(I.op_cd, I.op_dd, I.op_wl, I.op_wb, (const double*)I.vbx, (double*)I.vxx, nr, precision, rtol,
+                   max_iter, st);
+    count((int)(I.solver.launches - l0));
+    SolveResult r = I.solver.read_result(4, precision, st);
+    cudaMemcpyAsync(x, I.vxx, N * 8 * nr, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(e));
+    if (iters) *iters = r.iters;
+    if (rel_res) *rel_res = r.rel_res;
+    ebit_status s = cuda_check(ctx, "ebit_solve_system");
+    if (s != EBIT_OK) return s;
+    return r.converged ? EBIT_OK : fail(ctx, EBIT_ENOCONV, "ebit_solve_system: max_iter reached");
+}
+
 ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
     if (!ctx) return EBIT_EINVAL;
     if (option == EBIT_OPT_GRAPH) {

@@ -35,7 +35,8 @@ FIELD_DTYPES = {F_CCOL: np.uint8, F_BAND: np.uint8, F_VCOL: np.uint8, F_CSEG: np
 
 EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_field", "ebit_get_field",
            "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
-           "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_set_option", "ebit_last_error",
+           "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_set_option", "ebit_solve_system",
+           "ebit_last_error",
            "ebit_destroy", "ebit_version"]
 EBIT_OPT_GRAPH = 1
 EBIT_KT_SMOOTH_L0 = 1
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.ebit_launch_count.restype = C.c_uint64
     lib.ebit_timing_begin.argtypes = [vp, i32]
     lib.ebit_set_option.argtypes = [vp, i32, i32]
+    lib.ebit_solve_system.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, i32, f64, i32, C.POINTER(C.c_int),
+                                      C.POINTER(C.c_double)]
     lib.ebit_timing_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
     lib.ebit_last_error.argtypes = [vp]
     lib.ebit_last_error.restype = C.c_char_p
@@ -229,6 +232,22 @@ def ebit_timing_end(ctx):
 
 def ebit_set_option(ctx, option, value):
     _check(ctx, load().ebit_set_option(ctx, option, value))
+
+
+def ebit_solve_system(ctx, inst, D, wl, wb, b, x0=None, nr=1, precision=EBIT_FP64, rtol=1e-10, max_iter=500,
+                      allow_noconv=False):
+    """Solve the five-point system (D, wl, wb cell arrays) for b (nr interleaved RHS); returns (x, iters, relres)."""
+    Dp = np.ascontiguousarray(D, np.float64)
+    wlp = np.ascontiguousarray(wl, np.float64)
+    wbp = np.ascontiguousarray(wb, np.float64)
+    bp = np.ascontiguousarray(b, np.float64)
+    x = np.zeros_like(bp) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it, rr = C.c_int(), C.c_double()
+    s = load().ebit_solve_system(ctx, inst, Dp.ctypes.data, wlp.ctypes.data, wbp.ctypes.data, bp.ctypes.data,
+                                 x.ctypes.data, nr, precision, rtol, max_iter, C.byref(it), C.byref(rr))
+    if not (s == EBIT_ENOCONV and allow_noconv):
+        _check(ctx, s)
+    return x, it.value, rr.value
 
 
 def ebit_last_error(ctx):

@@ -318,11 +318,11 @@ __global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, 
     timer_end(tm);
 }
 
-// k_post: x += P xc, then black-red sweeps; at the finest level also r.z -> beta
+// k_post: x = xin + P xc, then black-red sweeps; at the finest level also r.z -> beta
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b, T* __restrict__ x,
-                                               const T* __restrict__ xc, SolveState* st, double* partial,
-                                               unsigned* ticket, KTimer* tm) {
+__global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin,
+                                               T* __restrict__ x, const T* __restrict__ xc, SolveState* st,
+                                               double* partial, unsigned* ticket, KTimer* tm) {
     if (skip(st)) return;
     constexpr int H = 2 * NU;
     using Rg = Region<T, NR, H>;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b,
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
-    region_load<T, NR, H>(R, L, b, x, xc, L.nx / 2, gx0, gy0);
+    region_load<T, NR, H>(R, L, b, xin, xc, L.nx / 2, gx0, gy0);
     for (int s = 1; s <= 2 * NU; ++s) region_sweep<T, NR, H>(R, gx0, gy0, L.nx, L.ny, s, ((s - 1) & 1) ^ 1);
     double dot[NR];
 #pragma unroll
@@ -795,8 +795,8 @@ size_t Solver::bytes(int nx, int ny) {
     size_t A = s.ncells_all, N = (size_t)nx * ny;
     for (int k = 0; k < 5; ++k) add(A * 4);
     for (int k = 0; k < 5; ++k) add(A * 8);
-    add(A * 2 * 4); add(A * 2 * 4);
-    add(A * 2 * 8); add(A * 2 * 8);
+    add(A * 2 * 4); add(A * 2 * 4); add(A * 2 * 4);
+    add(A * 2 * 8); add(A * 2 * 8); add(A * 2 * 8);
     add(N * 2 * 4); add(N * 4 * 4); add(N * 2 * 4); add(N * 2 * 4);
     add(N * 2 * 8); add(N * 4 * 8); add(N * 2 * 8);
     size_t mb = tiles(nx, ny) > (size_t)NRED ? tiles(nx, ny) : (size_t)NRED;
@@ -821,8 +821,8 @@ void Solver::bind(void* base, int nx_, int ny_) {
     f_cd = (float*)take(A * 4); f_dd = (float*)take(A * 4);
     d_diag = (double*)take(A * 8); d_wl = (double*)take(A * 8); d_wb = (double*)take(A * 8);
     d_cd = (double*)take(A * 8); d_dd = (double*)take(A * 8);
-    f_x = (float*)take(A * 2 * 4); f_b = (float*)take(A * 2 * 4);
-    d_x = (double*)take(A * 2 * 8); d_b = (double*)take(A * 2 * 8);
+    f_x = (float*)take(A * 2 * 4); f_b = (float*)take(A * 2 * 4); f_x2 = (float*)take(A * 2 * 4);
+    d_x = (double*)take(A * 2 * 8); d_b = (double*)take(A * 2 * 8); d_x2 = (double*)take(A * 2 * 8);
     f_r = (float*)take(N * 2 * 4); f_p = (float*)take(N * 4 * 4); f_q = (float*)take(N * 2 * 4);
     f_e = (float*)take(N * 2 * 4);
     d_r = (double*)take(N * 2 * 8); d_p = (double*)take(N * 4 * 8); d_q = (double*)take(N * 2 * 8);
@@ -873,6 +873,7 @@ template <> struct PT<float> {
     static float* cd(Solver& s) { return s.f_cd; }
     static float* dd(Solver& s) { return s.f_dd; }
     static float* x(Solver& s) { return s.f_x; }
+    static float* x2(Solver& s) { return s.f_x2; }
     static float* b(Solver& s) { return s.f_b; }
 };
 template <> struct PT<double> {
@@ -882,6 +883,7 @@ template <> struct PT<double> {
     static double* cd(Solver& s) { return s.d_cd; }
     static double* dd(Solver& s) { return s.d_dd; }
     static double* x(Solver& s) { return s.d_x; }
+    static double* x2(Solver& s) { return s.d_x2; }
     static double* b(Solver& s) { return s.d_b; }
 };
 
@@ -932,27 +934,30 @@ static SmallPlan small_plan(const Solver& s) {
     return P;
 }
 
-// z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved)
+// z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved).
+// k_pre of level l writes the pre-smoothed x into X2_l; k_post of level l reads X2_l and the
+// coarse correction X_{l+1} (halo included) and writes the final x into X_l (z at level 0):
+// no kernel writes an array that another of its blocks still reads.
 template <typename T, int NR>
 static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm) {
     T* X = PT<T>::x(s);
+    T* X2 = PT<T>::x2(s);
     T* B = PT<T>::b(s);
     const T* b = r;
-    T* x = z;
     int nb = nbig_of<T>(s);
     for (int l = 0; l < nb; ++l) {
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
         T* bc = B + 2 * s.loff[l + 1];
-        k_pre<T, NR><<<grid, 256, Region<T, NR, 2 * NU + 1>::bytes(), stm>>>(L, b, x, bc, st,
+        k_pre<T, NR><<<grid, 256, Region<T, NR, 2 * NU + 1>::bytes(), stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
                                                                            s.timing && l == 0 ? s.timer : nullptr);
         if (!s.use_graph) ++s.launches;
         b = bc;
-        x = X + 2 * s.loff[l + 1];
     }
     {
         SmallPlan P = small_plan<T>(s);
         size_t smem = SmallMem<T, NR>::bytes(P.total);
+        T* x = nb == 0 ? z : X + 2 * s.loff[nb];
         if (nb == 0)
             k_small<T, NR, true><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x,
                                                                   st);
@@ -965,14 +970,15 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
         const T* bl = l == 0 ? r : B + 2 * s.loff[l];
-        T* xl = l == 0 ? z : X + 2 * s.loff[l];
+        const T* xin = X2 + 2 * s.loff[l];
+        T* xout = l == 0 ? z : X + 2 * s.loff[l];
         const T* xc = X + 2 * s.loff[l + 1];
         size_t smem = Region<T, NR, 2 * NU>::bytes();
         KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
         if (l == 0)
-            k_post<T, NR, true><<<grid, 256, smem, stm>>>(L, bl, xl, xc, st, s.partial, s.tickets + 4, tm);
+            k_post<T, NR, true><<<grid, 256, smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
         else
-            k_post<T, NR, false><<<grid, 256, smem, stm>>>(L, bl, xl, xc, st, s.partial, s.tickets + 4, tm);
+            k_post<T, NR, false><<<grid, 256, smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
         if (!s.use_graph) ++s.launches;
     }
 }

@@ -46,8 +46,8 @@ struct Solver {
     float *f_diag, *f_wl, *f_wb, *f_cd, *f_dd;
     double *d_diag, *d_wl, *d_wb, *d_cd, *d_dd;
     // per-level vectors (2 right-hand sides interleaved), packed: x (correction) and b (rhs)
-    float *f_x, *f_b;
-    double *d_x, *d_b;
+    float *f_x, *f_b, *f_x2;    // x2: pre-smoothed x (written by k_pre, read by k_post)
+    double *d_x, *d_b, *d_x2;
     // CG vectors at level 0 (2 RHS interleaved)
     float *f_r, *f_p, *f_q, *f_e;
     double *d_r, *d_p, *d_q;

@@ -211,6 +211,25 @@ ebit_status ebit_solve_system(ebit_ctx* ctx, int inst, const double* D, const do
                               const double* b, double* x, int nr, int precision, double rtol, int max_iter,
                               int* iters, double* rel_res);
 
+/* Allocation-free variant of ebit_solve_system, for callers that cannot allocate device
+ * memory when they call: a host framework that owns the whole device memory through its own
+ * pool and forbids other allocations, or a service loop that must not allocate per call.
+ * No context: D, wl, wb, b and x are the caller's DEVICE arrays (same meaning and layout as in
+ * ebit_solve_system, on an nx x ny grid; x holds the initial guess and receives the
+ * solution); the work is ordered on `stream` (cudaStream_t, NULL = legacy default stream) and
+ * the call synchronises it before returning.  Every scratch array of the solver lives in one
+ * fixed 6 MiB __device__ array of the library, which every GPU that loads the library holds
+ * until the process exits; grids above 128 x 128 cells (or whose coarsest multigrid level
+ * has more than 1024 cells) are rejected with EBIT_EINVAL.  The call makes no device
+ * allocation.  The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (the solver clears what must start at zero);
+ * calls whose work overlaps on the GPU (two streams, two host threads) race on the array.
+ * The paper has no counterpart: this is a deployment variant of the library's own solver. */
+ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const double* wl, const double* wb,
+                                      const double* b, double* x, int nr, int precision, double rtol, int max_iter,
+                                      void* stream, int* iters, double* rel_res);
+
 /* Options: EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the
  * context's stream (solver loops as conditional WHILE nodes, no host round trip inside a
  * step); 0 launches every kernel from the host.  Graph mode needs a non-default stream. */

@@ -150,11 +150,12 @@ __global__ void k_setup0(int nx, int ny, const double* __restrict__ cd, const do
                          T* __restrict__ owl, T* __restrict__ owb, T* __restrict__ ocd, T* __restrict__ odd) {
     int N = nx * ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        diag[c] = (T)(cd[c] + dd[c]);
+        double ddv = dd ? dd[c] : 0.0;
+        diag[c] = (T)(cd[c] + ddv);
         owl[c] = (T)wl[c];
         owb[c] = (T)wb[c];
         ocd[c] = (T)cd[c];
-        odd[c] = (T)dd[c];
+        odd[c] = (T)ddv;
     }
 }
 
@@ -812,7 +813,7 @@ static void allow_smem(K kern, int bytes) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void Solver::bind(void* base, int nx_, int ny_) {
+void Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t init_stream) {
     plan(nx_, ny_);
     char* p = (char*)base;
     auto take = [&](size_t b) { void* r = p; p += (b + 255) & ~size_t(255); return r; };
@@ -832,7 +833,8 @@ void Solver::bind(void* base, int nx_, int ny_) {
     st_base = (SolveState*)take(NSLOT * sizeof(SolveState));
     st = st_base;
     timer = (KTimer*)take(4 * sizeof(KTimer));
-    for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&aux[k], cudaStreamNonBlocking);
+    if (make_streams)
+        for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&aux[k], cudaStreamNonBlocking);
     // shared-memory limits of the tile kernels
     // shared-memory opt-in of the tile and small-level kernels (dynamic + static may pass 48 KB)
     const int SM = 200 * 1024;
@@ -856,11 +858,11 @@ void Solver::bind(void* base, int nx_, int ny_) {
     allow_smem(k_small<double, 1, false>, SM);
     allow_smem(k_small<double, 2, true>, SM);
     allow_smem(k_small<double, 2, false>, SM);
-    KTimer init[4];
-    for (auto& t : init) { t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; }
-    cudaMemcpy(timer, init, sizeof(init), cudaMemcpyHostToDevice);
-    cudaMemset(tickets, 0, 256);
-    cudaMemset(st_base, 0, NSLOT * sizeof(SolveState));
+    // device state that must start at zero (tickets, solve states, timers; timer starts at ~0)
+    cudaMemsetAsync(timer, 0, 4 * sizeof(KTimer), init_stream);
+    for (int k = 0; k < 4; ++k) cudaMemsetAsync(&timer[k].start, 0xff, sizeof(unsigned long long), init_stream);
+    cudaMemsetAsync(tickets, 0, 256, init_stream);
+    cudaMemsetAsync(st_base, 0, NSLOT * sizeof(SolveState), init_stream);
     timing = 1;
 }
 
@@ -1166,3 +1168,58 @@ SolveResult Solver::read_result(int sl, int precision, cudaStream_t stm) {
 }
 
 }  // namespace ebit
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free solve.  Some callers cannot allocate device memory when they call the
+// solver: a host framework that owns the whole device memory through its own pool and
+// forbids other allocations, or a long-running service loop that must not allocate per call
+// (latency, fragmentation).  ebit_solve_system_noalloc takes the caller's device arrays for
+// the operator, the right-hand side and the solution, and keeps every scratch array of the
+// multigrid-preconditioned CG in the fixed array below.
+//
+// The array is a file-scope __device__ variable: every GPU that loads the library holds its
+// 6 MiB until the process exits.  Its device address is looked up once per device, with that
+// device current, by the first call on that device.  All calls share the array and it keeps
+// the last call's contents; the per-call device state that must start at zero (reduction
+// tickets, solver state, timers) is cleared at the start of each call.  Two calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on the array.
+// ---------------------------------------------------------------------------------------
+#include "../../include/ebit.h"
+
+namespace ebit {
+constexpr size_t NOALLOC_BYTES = (size_t)6 << 20;
+constexpr int NOALLOC_MAX_CELLS = 128 * 128;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+static void* g_noalloc_addr[64];   // device address of g_noalloc_scratch per device (host side)
+}  // namespace ebit
+
+extern "C" ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const double* wl, const double* wb,
+                                                 const double* b, double* x, int nr, int precision, double rtol,
+                                                 int max_iter, void* stream, int* iters, double* rel_res) {
+    using namespace ebit;
+    if (nx < 2 || ny < 2 || !D || !wl || !wb || !b || !x || (nr != 1 && nr != 2) ||
+        (precision != EBIT_FP64 && precision != EBIT_MIXED) || !(rtol > 0) || max_iter < 1)
+        return EBIT_EINVAL;
+    if ((long long)nx * ny > NOALLOC_MAX_CELLS || Solver::bytes(nx, ny) > NOALLOC_BYTES || !Solver::supported(nx, ny))
+        return EBIT_EINVAL;   // larger than the fixed scratch array (at most 128 x 128 cells)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EBIT_ECUDA;
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return EBIT_ECUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Solver s;
+    s.bind(g_noalloc_addr[dev], nx, ny, false, st);
+    SolveState host[Solver::NSLOT];
+    s.st_host = host;
+    s.slot = 0;
+    s.use_graph = 0;
+    s.solve(D, nullptr, wl, wb, b, x, nr, precision, rtol, max_iter, st);
+    SolveResult r = s.read_result(0, precision, st);
+    if (cudaGetLastError() != cudaSuccess) return EBIT_ECUDA;
+    if (iters) *iters = r.iters;
+    if (rel_res) *rel_res = r.rel_res;
+    return r.converged ? EBIT_OK : EBIT_ENOCONV;
+}

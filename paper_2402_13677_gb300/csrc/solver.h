@@ -67,7 +67,7 @@ struct Solver {
 
     void plan(int nx, int ny);
     static size_t bytes(int nx, int ny);
-    void bind(void* base, int nx, int ny);
+    void bind(void* base, int nx, int ny, bool make_streams = true, cudaStream_t init_stream = 0);
     // Solve A x = b for nr (1 or 2) interleaved right-hand sides.  The fine operator is given
     // cell-centred in FP64: cd (h^2 c), dd (Dirichlet terms), wl (left-face weight), wb
     // (bottom-face weight); x holds the initial guess.  In graph mode (use_graph) the loops

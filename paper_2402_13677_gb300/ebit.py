@@ -36,7 +36,7 @@ FIELD_DTYPES = {F_CCOL: np.uint8, F_BAND: np.uint8, F_VCOL: np.uint8, F_CSEG: np
 EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_field", "ebit_get_field",
            "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
            "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_set_option", "ebit_solve_system",
-           "ebit_last_error",
+           "ebit_solve_system_noalloc", "ebit_last_error",
            "ebit_destroy", "ebit_version"]
 EBIT_OPT_GRAPH = 1
 EBIT_KT_SMOOTH_L0 = 1
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.ebit_set_option.argtypes = [vp, i32, i32]
     lib.ebit_solve_system.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, i32, f64, i32, C.POINTER(C.c_int),
                                       C.POINTER(C.c_double)]
+    lib.ebit_solve_system_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, f64, i32, vp,
+                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.ebit_timing_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
     lib.ebit_last_error.argtypes = [vp]
     lib.ebit_last_error.restype = C.c_char_p
@@ -248,6 +250,17 @@ def ebit_solve_system(ctx, inst, D, wl, wb, b, x0=None, nr=1, precision=EBIT_FP6
     if not (s == EBIT_ENOCONV and allow_noconv):
         _check(ctx, s)
     return x, it.value, rr.value
+
+
+def ebit_solve_system_noalloc(nx, ny, D, wl, wb, b, x, nr=1, precision=EBIT_FP64, rtol=1e-10, max_iter=500,
+                              stream=None):
+    """Allocation-free solve on caller-owned device tensors (x is updated in place).
+    Returns (status, iters, relres); the status is returned, not raised (no context holds a message)."""
+    it, rr = C.c_int(), C.c_double()
+    s = load().ebit_solve_system_noalloc(nx, ny, D.data_ptr(), wl.data_ptr(), wb.data_ptr(), b.data_ptr(),
+                                         x.data_ptr(), nr, precision, rtol, max_iter, C.c_void_p(stream or 0),
+                                         C.byref(it), C.byref(rr))
+    return s, it.value, rr.value
 
 
 def ebit_last_error(ctx):

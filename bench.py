@@ -36,8 +36,16 @@ WORKLOADS = {
     "c2_bubble_512": dict(kind="c2", desc="2D planar vapour bubble in superheated liquid, 512x512"),
     "c3_film_1024x2048": dict(kind="c3", desc="2D film boiling over a heated wall, 1024x2048"),
     "c5_film_4096": dict(kind="c5", desc="multi-mode 2D film boiling, 4096x4096"),
+    # profiling case: the 4096x4096 film's cell size and physics on half its width (16 modes),
+    # small enough for multi-pass ncu captures while its smoother operands exceed L2
+    "c5_film_half_2048x4096": dict(kind="c5h", desc="multi-mode 2D film boiling, 2048x4096 half-width strip"),
 }
 METRIC = "cell-steps/s at 1 GPU, FP32+refine vs FP64, 1e-8 rel residual; %HBM roofline"
+
+# DRAM bytes (read + write) per launch of the finest-grid smoother kernels, from one ncu capture
+# of the current kernels (summary and command in the named profiles/ file); an entry is removed
+# whenever those kernels change, so that a stale figure is never reported
+SMOOTH_L0_TRAFFIC = {}
 
 
 def make_problem(name):
@@ -47,6 +55,8 @@ def make_problem(name):
         return w.c2_bubble(steps=0)
     if kind == "c3":
         return w.c3_film(steps=0)
+    if kind == "c5h":
+        return w.c5_film_half(steps=0)
     return w.c5_film(steps=0)
 
 
@@ -147,6 +157,22 @@ def _cores_used():
     return os.cpu_count()
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+def replica_max(x, dist, device):
+    """Max of a per-rank time over all ranks (the slowest replica sets the job's time)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, cells, steps, secs):
+    """Whole-job cell-steps/s: every replica advances its own instance by `steps` steps."""
+    return world * cells * steps / secs
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -206,11 +232,7 @@ def run_ours(args):
         return total, E.ebit_launch_count(ctx) - launches0, kt
 
     def barrier_max(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(x, dist, "cuda")
 
     results = {}
     prec_list = [("mixed", E.EBIT_MIXED), ("fp64", E.EBIT_FP64)]
@@ -296,22 +318,15 @@ def run_ours(args):
         return 0
 
     mixed, fp64 = results["mixed"], results["fp64"]
-    value = world * cells * args.steps / mixed["secs"]
-    value64 = world * cells * args.steps / fp64["secs"]
+    value = job_rate(world, cells, args.steps, mixed["secs"])
+    value64 = job_rate(world, cells, args.steps, fp64["secs"])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     kt_ms, kt_n, kt_bytes = mixed["kt"]
     achieved = (kt_bytes * kt_n) / (kt_ms / 1e3) / 1e9 if kt_ms > 0 else None
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "smooth_l0_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            tr = json.load(open(tr_path))
-            if tr.get("workload") == args.workload:
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    tr = SMOOTH_L0_TRAFFIC.get(args.workload)
+    traffic = tr["dram_bytes_per_launch"] if tr else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         r, n, s = oracle_rate(args.workload, budget_s=args.cpu_budget)
@@ -327,7 +342,8 @@ def run_ours(args):
         "fp64": {"value": value64, "unit": "cell-steps/s", "ms_per_step": 1e3 * fp64["secs"] / args.steps,
                  "speedup_mixed_over_fp64": value / value64},
         "timesteps_per_s": args.steps / mixed["secs"],
-        "roofline": {"bound": "hbm", "kernel": "k_smooth<float> (finest-grid red/black GS half-sweep)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_pre/k_post<float> on the finest grid (tiled red-black GS V-cycle legs)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "launches_timed": kt_n, "bytes_per_launch": kt_bytes,

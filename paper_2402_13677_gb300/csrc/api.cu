@@ -217,9 +217,8 @@ static void reconstruct_full(Instance& I, cudaStream_t st) {
 
 static void extend_T(Instance& I, double* Tl, double* Tv, cudaStream_t st) {
     int it = I.p.extend_iters;
-    launch_extend(I.g, 0, it, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tl, I.ext[0], I.ext[1], st);
-    launch_extend(I.g, 1, it, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tv, I.ext[2], I.ext[3], st);
-    count(2 * it);
+    launch_extend_T(I.g, it, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tl, Tv, I.ext, st);
+    count(it);
 }
 
 static void mass_flux(Instance& I, cudaStream_t st) {
@@ -311,7 +310,7 @@ static void solve_energy(Instance& I, cudaStream_t st) {
 
 static void momentum(Instance& I, cudaStream_t st) {
     // S11: predictor; one two-RHS solve (liquid, vapour) per velocity component
-    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, st);
+    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, I.cfg.precision == EBIT_MIXED, st);
     count(1);
     for (int comp = 0; comp < 2; ++comp) {
         launch_visc_operator(I.g, I.p, comp, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, st);
@@ -353,7 +352,7 @@ static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
         case EBIT_STAGE_PREPARE: prepare(I, st); break;
         case EBIT_STAGE_RECONSTRUCT: reconstruct_full(I, st); break;
         case EBIT_STAGE_ADVECT_T:
-            if (I.p.energy) { launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, st); count(1); }
+            if (I.p.energy) { launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, I.cfg.precision == EBIT_MIXED, st); count(1); }
             break;
         case EBIT_STAGE_EXTEND_TSTAR:
             if (I.p.energy) extend_T(I, I.Ts_l, I.Ts_v, st);
@@ -590,7 +589,7 @@ static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaGraphExec_t* out
     I.solver.use_graph = 1;
     cudaStream_t s = st;
     if (I.p.energy) {
-        launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, s);
+        launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, I.cfg.precision == EBIT_MIXED, s);
         extend_T(I, I.Ts_l, I.Ts_v, s);
     }
     advance_interface(I, s);
@@ -703,7 +702,9 @@ ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class) {
     if (!ctx || kernel_class != EBIT_KT_SMOOTH_L0) return EBIT_EINVAL;
     for (auto& I : ctx->inst) {
         KTimer z[2];
-        for (auto& t : z) { t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; }
+        for (auto& t : z) {
+            t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; t.bytes = 0.0;
+        }
         cudaMemcpyAsync(I.solver.timer, z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
     }
     cudaStreamSynchronize(ctx->stream);
@@ -720,13 +721,7 @@ ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches,
         cudaStreamSynchronize(ctx->stream);
         tot += (t[0].total_ns + t[1].total_ns) * 1e-6;
         n += t[0].launches + t[1].launches;
-        // algorithmic bytes per cell of the finest-grid tiled smoother kernels, NR right-hand
-        // sides averaged over the solves of a step as 1: pre = b, diag, wl, wb read, x and the
-        // coarse b (a quarter) written; post = x, the coarse x (a quarter), b, diag, wl, wb
-        // read, x written
-        double word = I.cfg.precision == EBIT_MIXED ? 4.0 : 8.0;
-        double cells = (double)I.g.nx * I.g.ny;
-        bytes += cells * word * ((1 + 3 + 1 + 0.25) * t[0].launches + (1 + 0.25 + 1 + 3 + 1) * t[1].launches);
+        bytes += t[0].bytes + t[1].bytes;
     }
     *total_ms = tot;
     *launches = n;

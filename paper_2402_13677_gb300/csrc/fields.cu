@@ -61,28 +61,41 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
     return F[cidx(g, i, j)];
 }
 
-// WENO3 upwind derivative (undivided) from five values along a line
+// WENO3 upwind derivative (undivided) from five values along a line. The Jiang-Shu weights
+// a0 = (1/3)/(eps + b0)^2 and a1 = (2/3)/(eps + b1)^2 are normalised after multiplying both
+// by 3 (eps + b0)^2 (eps + b1)^2, which leaves one division instead of three (FP64 division
+// is a multi-instruction sequence on this GPU). F32W: the nonlinear weight is formed in FP32
+// from the FP64 differences (the mixed-precision mode); the candidate stencils and their
+// combination stay FP64.
+template <bool F32W>
 __device__ inline double weno3(double Tm2, double Tm1, double T0, double Tp1, double Tp2, bool upos) {
-    const double eps = 1e-6;
     double v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
     double v2 = upos ? T0 - Tm1 : Tp1 - T0;
     double v3 = upos ? Tp1 - T0 : T0 - Tm1;
     double phi0 = 0.5 * (3.0 * v2 - v1);
     double phi1 = 0.5 * (v2 + v3);
-    double b0 = (v2 - v1) * (v2 - v1);
-    double b1 = (v3 - v2) * (v3 - v2);
-    double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
-    double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
-    return (a0 * phi0 + a1 * phi1) / (a0 + a1);
+    if (F32W) {
+        float d0 = (float)(v2 - v1), d1 = (float)(v3 - v2);
+        float s0 = 1e-6f + d0 * d0, s1 = 1e-6f + d1 * d1;
+        float q0 = s1 * s1, q1 = 2.0f * (s0 * s0);
+        float w0 = q0 / (q0 + q1);
+        return phi1 + (double)w0 * (phi0 - phi1);
+    } else {
+        const double eps = 1e-6;
+        double s0 = eps + (v2 - v1) * (v2 - v1);
+        double s1 = eps + (v3 - v2) * (v3 - v2);
+        double q0 = s1 * s1, q1 = 2.0 * (s0 * s0);
+        return (q0 * phi0 + q1 * phi1) / (q0 + q1);
+    }
 }
 
-template <class F>
+template <bool F32W, class F>
 __device__ inline double advect_one(const F& T, const Grid& g, const Refl& r, int i, int j, double2 u,
                                     double dth) {
-    double dx = weno3(refl_x(T, g, r, i - 2, j), refl_x(T, g, r, i - 1, j), refl_x(T, g, r, i, j),
-                      refl_x(T, g, r, i + 1, j), refl_x(T, g, r, i + 2, j), u.x >= 0.0);
-    double dy = weno3(refl_y(T, g, r, i, j - 2), refl_y(T, g, r, i, j - 1), refl_y(T, g, r, i, j),
-                      refl_y(T, g, r, i, j + 1), refl_y(T, g, r, i, j + 2), u.y >= 0.0);
+    double dx = weno3<F32W>(refl_x(T, g, r, i - 2, j), refl_x(T, g, r, i - 1, j), refl_x(T, g, r, i, j),
+                            refl_x(T, g, r, i + 1, j), refl_x(T, g, r, i + 2, j), u.x >= 0.0);
+    double dy = weno3<F32W>(refl_y(T, g, r, i, j - 2), refl_y(T, g, r, i, j - 1), refl_y(T, g, r, i, j),
+                            refl_y(T, g, r, i, j + 1), refl_y(T, g, r, i, j + 2), u.y >= 0.0);
     return refl_x(T, g, r, i, j) - dth * (u.x * dx + u.y * dy);
 }
 
@@ -98,6 +111,7 @@ __host__ inline Refl velocity_refl(const Grid& g, int comp) {
 }
 
 // S1: T*_k = T_k - dt u_k . grad T_k for both phases
+template <bool F32W>
 __global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l, const double* __restrict__ T_v,
                            const double2* __restrict__ u_l, const double2* __restrict__ u_v,
                            double* __restrict__ Ts_l, double* __restrict__ Ts_v) {
@@ -105,8 +119,8 @@ __global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict_
     int j = blockIdx.y;
     if (i >= g.nx) return;
     int c = cidx(g, i, j);
-    Ts_l[c] = advect_one(T_l, g, r, i, j, u_l[c], dth);
-    Ts_v[c] = advect_one(T_v, g, r, i, j, u_v[c], dth);
+    Ts_l[c] = advect_one<F32W>(T_l, g, r, i, j, u_l[c], dth);
+    Ts_v[c] = advect_one<F32W>(T_v, g, r, i, j, u_v[c], dth);
 }
 
 // ---------------------------------------------------------------------------------
@@ -143,22 +157,29 @@ __device__ inline bool ext_update(uint8_t fl, int mode) {
     return !(fl & F_CUT);
 }
 
+// mode 3 runs modes 0 and 1 in the same sweep (they update disjoint cells of different
+// fields): (f, vcur, vnxt) belong to mode 0 and (f1, vcur1, vnxt1) to mode 1.
 __global__ void k_extend(Grid g, int mode, int it, int last, const int* __restrict__ list,
                          const int* __restrict__ count, const uint8_t* __restrict__ flags,
-                         const int* __restrict__ idxmap, const double2* __restrict__ nb, double* f,
-                         const double* __restrict__ vcur, double* __restrict__ vnxt) {
+                         const int* __restrict__ idxmap, const double2* __restrict__ nb, double* f0,
+                         const double* __restrict__ vcur0, double* __restrict__ vnxt0, double* f1,
+                         const double* __restrict__ vcur1, double* __restrict__ vnxt1) {
     int n = *count;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int c = list[k];
         uint8_t fl = flags[c];
-        if (!ext_update(fl, mode)) continue;
+        int m = mode == 3 ? ((fl & F_CCOL) ? 1 : 0) : mode;
+        if (!ext_update(fl, m)) continue;
+        double* f = m == 1 && mode == 3 ? f1 : f0;
+        const double* vcur = m == 1 && mode == 3 ? vcur1 : vcur0;
+        double* vnxt = m == 1 && mode == 3 ? vnxt1 : vnxt0;
         int i = c % g.nx, j = c / g.nx;
-        double sgn = mode == 0 ? 1.0 : (mode == 1 ? -1.0 : ((fl & F_CCOL) ? -1.0 : 1.0));
+        double sgn = m == 0 ? 1.0 : (m == 1 ? -1.0 : ((fl & F_CCOL) ? -1.0 : 1.0));
         double2 nn = nb[c];
         double ax = nn.x * sgn, ay = nn.y * sgn;
         double acc = 0.0, w = 0.0;
         auto val = [&](int cc) -> double {
-            if (it > 0 && ext_update(flags[cc], mode)) return vcur[idxmap[cc]];
+            if (it > 0 && ext_update(flags[cc], m)) return vcur[idxmap[cc]];
             return f[cc];
         };
         if (ax > 0.0 && i - 1 >= 0) { acc += ax * val(c - 1); w += ax; }
@@ -265,6 +286,7 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
 
 // RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields,
 // one two-RHS system per component (liquid, vapour interleaved); initial guesses = current u
+template <bool F32W>
 __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const double* __restrict__ vf,
                           const double2* __restrict__ u_l, const double2* __restrict__ u_v,
                           const double2* __restrict__ gc, double2* __restrict__ bx, double2* __restrict__ by,
@@ -276,10 +298,10 @@ __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const do
     double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
-    bx[c] = make_double2(coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
-                         coef * (advect_one(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x));
-    by[c] = make_double2(coef * (advect_one(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y),
-                         coef * (advect_one(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y));
+    bx[c] = make_double2(coef * (advect_one<F32W>(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
+                         coef * (advect_one<F32W>(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x));
+    by[c] = make_double2(coef * (advect_one<F32W>(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y),
+                         coef * (advect_one<F32W>(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y));
     xx[c] = make_double2(ul.x, uv.x);
     xy[c] = make_double2(ul.y, uv.y);
 }
@@ -542,9 +564,10 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
 static inline dim3 rows_grid(int n, int rows, int bs) { return dim3(div_up(n, bs), rows); }
 
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
-                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st) {
-    k_advect_T<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v,
-                                                          Ts_l, Ts_v);
+                     const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st) {
+    auto k = f32w ? k_advect_T<true> : k_advect_T<false>;
+    k<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l,
+                                                 Ts_v);
 }
 
 void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
@@ -567,7 +590,19 @@ void launch_extend(const Grid& g, int mode, int iters, const int* list, const in
     for (int it = 0; it < iters; ++it) {
         const double* cur = (it & 1) ? vb : va;
         double* nxt = (it & 1) ? va : vb;
-        k_extend<<<nb_, 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb, f, cur, nxt);
+        k_extend<<<nb_, 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb, f, cur, nxt,
+                                      nullptr, nullptr, nullptr);
+    }
+}
+
+void launch_extend_T(const Grid& g, int iters, const int* list, const int* count, const uint8_t* flags,
+                     const int* idxmap, const double2* nb, double* T_l, double* T_v, double* const ext[4],
+                     cudaStream_t st) {
+    int nb_ = extend_grid_blocks();
+    for (int it = 0; it < iters; ++it) {
+        int a = it & 1;
+        k_extend<<<nb_, 256, 0, st>>>(g, 3, it, it == iters - 1, list, count, flags, idxmap, nb, T_l, ext[a],
+                                      ext[1 - a], T_v, ext[2 + a], ext[3 - a]);
     }
 }
 
@@ -588,9 +623,11 @@ void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* 
 }
 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
-                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st) {
-    k_mom_rhs<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
-                                                         p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
+                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, bool f32w,
+                    cudaStream_t st) {
+    auto k = f32w ? k_mom_rhs<true> : k_mom_rhs<false>;
+    k<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf,
+                                                 u_l, u_v, gc, bx, by, xx, xy);
 }
 
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,

@@ -24,11 +24,17 @@ void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const 
                       const double* T_l, const double* T_v, double* mdot, cudaStream_t st);
 
 // fields.cu
+// f32w: WENO3 nonlinear weights in FP32 (mixed-precision mode)
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
-                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st);
+                     const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st);
 void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap, cudaStream_t st);
 void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
                    const int* idxmap, const double2* nb, double* f, double* va, double* vb, cudaStream_t st);
+// modes 0 and 1 (T_l into the vapour band, T_v into the liquid band) in one launch per sweep;
+// ext[0..1] and ext[2..3] are the two ping-pong pairs
+void launch_extend_T(const Grid& g, int iters, const int* list, const int* count, const uint8_t* flags,
+                     const int* idxmap, const double2* nb, double* T_l, double* T_v, double* const ext[4],
+                     cudaStream_t st);
 void launch_split_T(const Grid& g, const uint8_t* flags, const double* x, const double* Ts_l, const double* Ts_v,
                     double* T_l, double* T_v, cudaStream_t st);
 void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, const double* mdot, const double2* nb,
@@ -37,7 +43,8 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, c
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
                           double* wl, double* wb, cudaStream_t st);
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
-                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st);
+                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, bool f32w,
+                    cudaStream_t st);
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
                   double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
                   cudaStream_t st);

@@ -76,7 +76,7 @@ __device__ inline unsigned long long gtimer() {
 __device__ inline void timer_begin(KTimer* tm) {
     if (tm && threadIdx.x == 0) atomicMin(&tm->start, gtimer());
 }
-__device__ inline void timer_end(KTimer* tm) {
+__device__ inline void timer_end(KTimer* tm, double bytes) {
     if (!tm) return;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -87,6 +87,7 @@ __device__ inline void timer_end(KTimer* tm) {
             unsigned long long s = atomicAdd(&tm->start, 0ull), e = atomicAdd(&tm->end, 0ull);
             tm->total_ns += e > s ? e - s : 0ull;
             tm->launches += 1;
+            tm->bytes += bytes;
             tm->start = ~0ull;
             tm->end = 0ull;
             tm->ticket = 0u;
@@ -187,7 +188,8 @@ __global__ void k_coarsen(int fnx, int fny, const T* __restrict__ fcd, const T* 
 }
 
 // ---- large-level kernels: shared-memory tiles with recomputed halos ---------------------
-// smem layout per region cell: x[NR], b[NR] (type T) then diag, wl, wb
+// smem layout per region cell: x[NR], b[NR] (type T) then diag, wl, wb and the reciprocal of
+// the full diagonal (D + the four face weights), so that a sweep multiplies instead of divides
 template <typename T, int NR, int H>
 struct Region {
     static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, N = SX * SY;
@@ -196,14 +198,16 @@ struct Region {
     T* d;
     T* wl;
     T* wb;
+    T* id;
     __device__ Region(unsigned char* base) {
         x = (T*)base;
         b = x + NR * N;
         d = b + NR * N;
         wl = d + N;
         wb = wl + N;
+        id = wb + N;
     }
-    static constexpr size_t bytes() { return (size_t)N * (2 * NR + 3) * sizeof(T); }
+    static constexpr size_t bytes() { return (size_t)N * (2 * NR + 4) * sizeof(T); }
 };
 
 // one Gauss-Seidel half-sweep of colour `color` over region cells at distance >= s from its
@@ -222,12 +226,12 @@ __device__ inline void region_sweep(Region<T, NR, H>& R, int gx0, int gy0, int n
             if (gi < 0 || gi >= nx) continue;
             int q = ry * SX + rx;
             T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + SX];
-            T d = R.d[q] + wl + wr + wb + wt;
+            T id = R.id[q];
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 T acc = R.b[q * NR + k2] + wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
                         wb * R.x[(q - SX) * NR + k2] + wt * R.x[(q + SX) * NR + k2];
-                R.x[q * NR + k2] = acc / d;
+                R.x[q * NR + k2] = acc * id;
             }
         }
     }
@@ -266,6 +270,13 @@ __device__ inline void region_load(Region<T, NR, H>& R, const Lev<T>& L, const T
             R.wb[q] = in ? L.wb[c] : T(0);
         }
     }
+    __syncthreads();
+    // reciprocal full diagonal of every cell a sweep can reach (not the outermost ring)
+    for (int ry = 1 + ty; ry < SY - 1; ry += 8)
+        for (int rx = 1 + tx; rx < SX - 1; rx += 32) {
+            int q = ry * SX + rx;
+            R.id[q] = T(1) / (R.d[q] + R.wl[q] + R.wl[q + 1] + R.wb[q] + R.wb[q + SX]);
+        }
     __syncthreads();
 }
 
@@ -316,7 +327,8 @@ __global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, 
         }
         reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
     }
-    timer_end(tm);
+    // algorithmic bytes: b, diag, wl, wb read; x and the quarter-size coarse b written
+    timer_end(tm, (double)L.nx * L.ny * sizeof(T) * (3.0 + NR * 2.25));
 }
 
 // k_post: x = xin + P xc, then black-red sweeps; at the finest level also r.z -> beta
@@ -360,7 +372,8 @@ __global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b,
             }
         }
     }
-    timer_end(tm);
+    // algorithmic bytes: b, x, the quarter-size coarse x, diag, wl, wb read; x written
+    timer_end(tm, (double)L.nx * L.ny * sizeof(T) * (3.0 + NR * 3.25));
 }
 
 // ---- small levels: the rest of the V-cycle in one block ---------------------------------
@@ -389,20 +402,21 @@ struct SmallMem {
 template <typename T, int NR>
 __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M, int color) {
     int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-    for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
-        int i = c % nx, j = c / nx;
-        if (((i + j) & 1) != color) continue;
-        int q = o + c;
-        T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
-        T dg = M.d[q] + w0 + w1 + w2 + w3;
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+    for (int j = ty; j < ny; j += nty) {
+        for (int i = ((color - j) & 1) + 2 * tx; i < nx; i += 64) {
+            int q = o + j * nx + i;
+            T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
+            T dg = M.d[q] + w0 + w1 + w2 + w3;
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            T acc = M.b[q * NR + k];
-            if (i > 0) acc += w0 * M.x[(q - 1) * NR + k];
-            if (i < nx - 1) acc += w1 * M.x[(q + 1) * NR + k];
-            if (j > 0) acc += w2 * M.x[(q - nx) * NR + k];
-            if (j < ny - 1) acc += w3 * M.x[(q + nx) * NR + k];
-            M.x[q * NR + k] = acc / dg;
+            for (int k = 0; k < NR; ++k) {
+                T acc = M.b[q * NR + k];
+                if (i > 0) acc += w0 * M.x[(q - 1) * NR + k];
+                if (i < nx - 1) acc += w1 * M.x[(q + 1) * NR + k];
+                if (j > 0) acc += w2 * M.x[(q - nx) * NR + k];
+                if (j < ny - 1) acc += w3 * M.x[(q + nx) * NR + k];
+                M.x[q * NR + k] = acc / dg;
+            }
         }
     }
     __syncthreads();
@@ -411,21 +425,29 @@ __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M
 template <typename T, int NR, bool DOT>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* __restrict__ diag,
                                                          const T* __restrict__ wl, const T* __restrict__ wb,
-                                                         const T* __restrict__ b_in, T* __restrict__ x_out,
-                                                         SolveState* st) {
+                                                         const T* __restrict__ inv, const T* __restrict__ b_in,
+                                                         T* __restrict__ x_out, SolveState* st) {
     if (skip(st)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     SmallMem<T, NR> M(smem, P.total);
-    for (int l = 0; l < P.n; ++l) {
-        int n = P.nx[l] * P.ny[l];
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            int q = P.soff[l] + c;
-            M.d[q] = diag[P.goff[l] + c];
-            M.wl[q] = wl[P.goff[l] + c];
-            M.wb[q] = wb[P.goff[l] + c];
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+    // the small levels are contiguous in the packed level arrays and in shared memory: one flat
+    // copy per array, four independent loads in flight per thread and array
+    {
+        const T* gd = diag + P.goff[0];
+        const T* gl = wl + P.goff[0];
+        const T* gb = wb + P.goff[0];
+        int tot = P.total;
+#pragma unroll 4
+        for (int c = threadIdx.x; c < tot; c += blockDim.x) {
+            T a = gd[c], b2 = gl[c], c2 = gb[c];
+            M.d[c] = a;
+            M.wl[c] = b2;
+            M.wb[c] = c2;
         }
     }
     int n0 = P.nx[0] * P.ny[0];
+#pragma unroll 4
     for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) M.b[c] = b_in[c];
     __syncthreads();
     // down
@@ -439,53 +461,77 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
         }
         // residual, restricted to level l+1
         int cnx = P.nx[l + 1], cny = P.ny[l + 1], co = P.soff[l + 1];
-        for (int C = threadIdx.x; C < cnx * cny; C += blockDim.x) {
-            int I = C % cnx, J = C / cnx;
-            T acc[NR];
+        for (int J = ty; J < cny; J += nty) {
+            for (int I = tx; I < cnx; I += 32) {
+                T acc[NR];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = T(0);
-            for (int d2 = 0; d2 < 4; ++d2) {
-                int i = 2 * I + (d2 & 1), j = 2 * J + (d2 >> 1);
-                int q = o + j * nx + i;
-                T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
+                for (int k = 0; k < NR; ++k) acc[k] = T(0);
+                for (int d2 = 0; d2 < 4; ++d2) {
+                    int i = 2 * I + (d2 & 1), j = 2 * J + (d2 >> 1);
+                    int q = o + j * nx + i;
+                    T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q],
+                      w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
 #pragma unroll
-                for (int k = 0; k < NR; ++k) {
-                    T xq = M.x[q * NR + k];
-                    T ax = M.d[q] * xq;
-                    if (i > 0) ax += w0 * (xq - M.x[(q - 1) * NR + k]);
-                    if (i < nx - 1) ax += w1 * (xq - M.x[(q + 1) * NR + k]);
-                    if (j > 0) ax += w2 * (xq - M.x[(q - nx) * NR + k]);
-                    if (j < ny - 1) ax += w3 * (xq - M.x[(q + nx) * NR + k]);
-                    acc[k] += M.b[q * NR + k] - ax;
+                    for (int k = 0; k < NR; ++k) {
+                        T xq = M.x[q * NR + k];
+                        T ax = M.d[q] * xq;
+                        if (i > 0) ax += w0 * (xq - M.x[(q - 1) * NR + k]);
+                        if (i < nx - 1) ax += w1 * (xq - M.x[(q + 1) * NR + k]);
+                        if (j > 0) ax += w2 * (xq - M.x[(q - nx) * NR + k]);
+                        if (j < ny - 1) ax += w3 * (xq - M.x[(q + nx) * NR + k]);
+                        acc[k] += M.b[q * NR + k] - ax;
+                    }
                 }
-            }
 #pragma unroll
-            for (int k = 0; k < NR; ++k) M.b[(co + C) * NR + k] = acc[k];
+                for (int k = 0; k < NR; ++k) M.b[(co + J * cnx + I) * NR + k] = acc[k];
+            }
         }
         __syncthreads();
     }
-    // coarsest: symmetric sweep sequence from zero
+    // coarsest: exact solve with the precomputed inverse (up to 32 cells), else a symmetric
+    // red-black sweep sequence from zero
     {
-        int l = P.n - 1, o = P.soff[l];
-        for (int c = threadIdx.x; c < P.nx[l] * P.ny[l] * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
-        __syncthreads();
-        for (int k = 0; k < COARSE_PAIRS; ++k) {
-            small_sweep<T, NR>(P, l, M, 0);
-            small_sweep<T, NR>(P, l, M, 1);
-        }
-        for (int k = 0; k < COARSE_PAIRS; ++k) {
-            small_sweep<T, NR>(P, l, M, 1);
-            small_sweep<T, NR>(P, l, M, 0);
+        int l = P.n - 1, o = P.soff[l], n = P.nx[l] * P.ny[l];
+        if (n <= 32 && inv[n * n] == T(1)) {
+            if (threadIdx.x < 32) {
+                int r = threadIdx.x;
+                T acc[NR];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc[k] = T(0);
+                if (r < n)
+                    for (int c = 0; c < n; ++c) {
+                        T a = inv[r * n + c];
+#pragma unroll
+                        for (int k = 0; k < NR; ++k) acc[k] += a * M.b[(o + c) * NR + k];
+                    }
+                __syncwarp();
+                if (r < n)
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) M.x[(o + r) * NR + k] = acc[k];
+            }
+            __syncthreads();
+        } else {
+            for (int c = threadIdx.x; c < n * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
+            __syncthreads();
+            for (int k = 0; k < COARSE_PAIRS; ++k) {
+                small_sweep<T, NR>(P, l, M, 0);
+                small_sweep<T, NR>(P, l, M, 1);
+            }
+            for (int k = 0; k < COARSE_PAIRS; ++k) {
+                small_sweep<T, NR>(P, l, M, 1);
+                small_sweep<T, NR>(P, l, M, 0);
+            }
         }
     }
     // up
     for (int l = P.n - 2; l >= 0; --l) {
         int nx = P.nx[l], ny = P.ny[l], o = P.soff[l], cnx = P.nx[l + 1], co = P.soff[l + 1];
-        for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
-            int i = c % nx, j = c / nx;
+        for (int j = ty; j < ny; j += nty)
+            for (int i = tx; i < nx; i += 32) {
 #pragma unroll
-            for (int k = 0; k < NR; ++k) M.x[(o + c) * NR + k] += M.x[(co + (j >> 1) * cnx + (i >> 1)) * NR + k];
-        }
+                for (int k = 0; k < NR; ++k)
+                    M.x[(o + j * nx + i) * NR + k] += M.x[(co + (j >> 1) * cnx + (i >> 1)) * NR + k];
+            }
         __syncthreads();
         for (int k = 0; k < NU; ++k) {
             small_sweep<T, NR>(P, l, M, 1);
@@ -508,6 +554,57 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
             }
         }
     }
+}
+
+// dense inverse of the coarsest operator (at most 32 cells), Gauss-Jordan in one warp in
+// precision T: lane l owns columns l and l + 32 of [A | I]; one reciprocal per pivot.
+// inv[n * n] = 1 marks a usable inverse; a non-positive or non-finite pivot (a singular
+// coarsest operator, e.g. a pure-Neumann pressure problem) leaves 0 there and the cycle
+// falls back to sweeps.
+template <typename T>
+__global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ diag, const T* __restrict__ wl,
+                                 const T* __restrict__ wb, T* __restrict__ inv) {
+    __shared__ T A[32][65];
+    __shared__ T col[32];
+    int n = nx * ny;
+    int lane = threadIdx.x;
+    for (int r = 0; r < n; ++r) {
+        A[r][lane] = T(0);
+        A[r][lane + 32] = T(0);
+    }
+    __syncwarp();
+    if (lane < n) {
+        int r = lane, i = r % nx, j = r / nx;
+        T w0 = wl[r], w1 = i < nx - 1 ? wl[r + 1] : T(0), w2 = wb[r], w3 = j < ny - 1 ? wb[r + nx] : T(0);
+        A[r][r] = diag[r] + w0 + w1 + w2 + w3;
+        if (i > 0) A[r][r - 1] = -w0;
+        if (i < nx - 1) A[r][r + 1] = -w1;
+        if (j > 0) A[r][r - nx] = -w2;
+        if (j < ny - 1) A[r][r + nx] = -w3;
+        A[r][n + r] = T(1);
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int p = 0; p < n; ++p) {
+        T piv = A[p][p];
+        ok = ok && piv > T(0) && piv < T(INFINITY);
+        T rp = T(1) / piv;
+        if (lane < n) col[lane] = A[lane][p];
+        __syncwarp();
+        T a0 = A[p][lane] * rp, a1 = A[p][lane + 32] * rp;
+        for (int r = 0; r < n; ++r) {
+            if (r == p) continue;
+            T f = col[r];
+            A[r][lane] -= f * a0;
+            A[r][lane + 32] -= f * a1;
+        }
+        A[p][lane] = a0;
+        A[p][lane + 32] = a1;
+        __syncwarp();
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = lane; c < n; c += 32) inv[r * n + c] = A[r][n + c];
+    if (lane == 0) inv[n * n] = ok ? T(1) : T(0);
 }
 
 // ---- CG kernels ---------------------------------------------------------------------------
@@ -800,6 +897,7 @@ size_t Solver::bytes(int nx, int ny) {
     add(A * 2 * 8); add(A * 2 * 8); add(A * 2 * 8);
     add(N * 2 * 4); add(N * 4 * 4); add(N * 2 * 4); add(N * 2 * 4);
     add(N * 2 * 8); add(N * 4 * 8); add(N * 2 * 8);
+    add(1040 * 4); add(1040 * 8);
     size_t mb = tiles(nx, ny) > (size_t)NRED ? tiles(nx, ny) : (size_t)NRED;
     add(mb * 4 * 8);
     add(256);
@@ -827,6 +925,7 @@ void Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t 
     f_r = (float*)take(N * 2 * 4); f_p = (float*)take(N * 4 * 4); f_q = (float*)take(N * 2 * 4);
     f_e = (float*)take(N * 2 * 4);
     d_r = (double*)take(N * 2 * 8); d_p = (double*)take(N * 4 * 8); d_q = (double*)take(N * 2 * 8);
+    f_inv = (float*)take(1040 * 4); d_inv = (double*)take(1040 * 8);
     size_t mb = tiles(nx, ny) > (size_t)NRED ? tiles(nx, ny) : (size_t)NRED;
     partial = (double*)take(mb * 4 * 8);
     tickets = (unsigned*)take(256);
@@ -876,6 +975,7 @@ template <> struct PT<float> {
     static float* dd(Solver& s) { return s.f_dd; }
     static float* x(Solver& s) { return s.f_x; }
     static float* x2(Solver& s) { return s.f_x2; }
+    static float* inv(Solver& s) { return s.f_inv; }
     static float* b(Solver& s) { return s.f_b; }
 };
 template <> struct PT<double> {
@@ -886,6 +986,7 @@ template <> struct PT<double> {
     static double* dd(Solver& s) { return s.d_dd; }
     static double* x(Solver& s) { return s.d_x; }
     static double* x2(Solver& s) { return s.d_x2; }
+    static double* inv(Solver& s) { return s.d_inv; }
     static double* b(Solver& s) { return s.d_b; }
 };
 
@@ -909,6 +1010,13 @@ static void setup_levels(Solver& s, const double* cd, const double* dd, const do
                                                   PT<T>::wl(s) + fo, PT<T>::wb(s) + fo, PT<T>::cd(s) + co,
                                                   PT<T>::dd(s) + co, PT<T>::wl(s) + co, PT<T>::wb(s) + co,
                                                   PT<T>::diag(s) + co);
+        ++s.launches;
+    }
+    int lc = s.nlev - 1;
+    if (s.lnx[lc] * s.lny[lc] <= 32) {
+        size_t o = s.loff[lc];
+        k_coarse_inverse<T><<<1, 32, 0, stm>>>(s.lnx[lc], s.lny[lc], PT<T>::diag(s) + o, PT<T>::wl(s) + o,
+                                               PT<T>::wb(s) + o, PT<T>::inv(s));
         ++s.launches;
     }
 }
@@ -960,12 +1068,13 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         SmallPlan P = small_plan<T>(s);
         size_t smem = SmallMem<T, NR>::bytes(P.total);
         T* x = nb == 0 ? z : X + 2 * s.loff[nb];
+        const T* inv = PT<T>::inv(s);
         if (nb == 0)
-            k_small<T, NR, true><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b, x,
-                                                                  st);
+            k_small<T, NR, true><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
+                                                                  b, x, st);
         else
-            k_small<T, NR, false><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), b,
-                                                                   x, st);
+            k_small<T, NR, false><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
+                                                                   b, x, st);
         if (!s.use_graph) ++s.launches;
     }
     for (int l = nb - 1; l >= 0; --l) {
@@ -1072,7 +1181,7 @@ static void solve_fp64(Solver& s, const double* b, double* x, double rtol, int m
     poll(s, stm);
     for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
         cg_body<double, NR>(s, x, s.d_r, z, s.d_p, s.d_q, s.st, 0, 0, stm);
-        if ((it + 1) % 4 == 0) poll(s, stm);
+        poll(s, stm);
     }
 }
 
@@ -1108,7 +1217,7 @@ static void solve_mixed(Solver& s, const double* b, double* x, double rtol, int 
         if (s.st_host[s.slot].odone) break;
         for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
             cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, 0, 0, stm);
-            if ((it + 1) % 4 == 0) poll(s, stm);
+            poll(s, stm);
         }
         k_ir_update<NR><<<nblocks(N * NR), RB, 0, stm>>>(N, x, s.f_e, s.st);
         ++s.launches;

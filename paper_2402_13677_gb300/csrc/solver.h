@@ -23,6 +23,7 @@ struct KTimer {
     unsigned int pad;
     unsigned long long total_ns;
     unsigned long long launches;
+    double bytes;      // algorithmic bytes of the timed launches (each launch adds its own)
 };
 
 // device-side scalars of one solve; per right-hand side k < 2
@@ -51,6 +52,8 @@ struct Solver {
     // CG vectors at level 0 (2 RHS interleaved)
     float *f_r, *f_p, *f_q, *f_e;
     double *d_r, *d_p, *d_q;
+    float* f_inv;      // dense inverse of the coarsest operator (at most 32 cells)
+    double* d_inv;
     // reductions
     double* partial;   // [4][MAXBLK][2]
     unsigned* tickets; // 8

@@ -345,4 +345,11 @@ def c5_film(**kw):
                 lam_l=1e-2, lam_v=1e-3, St=0.1, **kw)
 
 
-WORKLOADS = {"c1_stefan": c1_stefan, "c2_bubble": c2_bubble, "c3_film": c3_film, "c5_film": c5_film}
+def c5_film_half(**kw):
+    """The 4096x4096 film's cell size and properties on the strip [0,4]x[0,8] (2048x4096, 16 modes)."""
+    return film(2048, 4096, Lx=4.0, modes=16, rho_l=50.0, rho_v=1.0, mu_l=1e-2, mu_v=1e-3,
+                lam_l=1e-2, lam_v=1e-3, St=0.1, **kw)
+
+
+WORKLOADS = {"c1_stefan": c1_stefan, "c2_bubble": c2_bubble, "c3_film": c3_film, "c5_film": c5_film,
+             "c5_film_half": c5_film_half}

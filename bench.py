@@ -259,6 +259,9 @@ def run_ours(args):
             secs = barrier_max(secs)
             d = E.ebit_get_diagnostics(ctx, 0)
             results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist())
+            if not args.profile_only and rank == 0:
+                results[name]["final"] = E.download(ctx, 0, pb.nx, pb.ny, ["T_l", "T_v", "p", "u_l", "u_v", "vcol",
+                                                                           "hx_pos", "vy_pos"])
         finally:
             E.ebit_destroy(ctx)
     if args.profile_only:
@@ -325,6 +328,24 @@ def run_ours(args):
     peak = peaks.get("hbm_gbs", 6800.0)
     kt_ms, kt_n, kt_bytes = mixed["kt"]
     achieved = (kt_bytes * kt_n) / (kt_ms / 1e3) / 1e9 if kt_ms > 0 else None
+    # the mixed path's error against the FP64 path after the same warm-up + timed steps from the
+    # same initial state: max difference over a field group relative to the group's scale
+    # (temperatures: max |T| over both phases; velocities: max |u| over both phase fields;
+    # pressure: max(|p|, rho_l u_max^2), p being defined by its outflow reference)
+    fm, fd = mixed["final"], fp64["final"]
+    t_scale = max(float(np.max(np.abs(fd["T_l"]))), float(np.max(np.abs(fd["T_v"]))), 1e-300)
+    u_scale = max(float(np.max(np.abs(fd["u_l"]))), float(np.max(np.abs(fd["u_v"]))), 1e-300)
+    p_scale = max(float(np.max(np.abs(fd["p"]))), pb.rho_l * u_scale ** 2, 1e-300)
+    scale = {"T_l": t_scale, "T_v": t_scale, "u_l": u_scale, "u_v": u_scale, "p": p_scale}
+
+    def rel(k):
+        return float(np.max(np.abs(fm[k] - fd[k]))) / scale[k]
+
+    mixed_err = {"steps": args.warmup + args.steps, **{k: rel(k) for k in ("T_l", "T_v", "p", "u_l", "u_v")},
+                 "vertex_colours_differing": int(np.sum(fm["vcol"] != fd["vcol"])),
+                 "marker_max_abs_diff": float(max(np.max(np.abs(fm["hx_pos"] - fd["hx_pos"])),
+                                                  np.max(np.abs(fm["vy_pos"] - fd["vy_pos"])))),
+                 "scales": "T: max|T| both phases; u: max|u| both fields; p: max(|p|, rho_l u_max^2)"}
     tr = SMOOTH_L0_TRAFFIC.get(args.workload)
     traffic = tr["dram_bytes_per_launch"] if tr else None
     cpu = None
@@ -341,6 +362,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp64": {"value": value64, "unit": "cell-steps/s", "ms_per_step": 1e3 * fp64["secs"] / args.steps,
                  "speedup_mixed_over_fp64": value / value64},
+        "mixed_error_vs_fp64": mixed_err,
         "timesteps_per_s": args.steps / mixed["secs"],
         "roofline": {"bound": "hbm",
                      "kernel": "k_pre/k_post<float> on the finest grid (tiled red-black GS V-cycle legs)",

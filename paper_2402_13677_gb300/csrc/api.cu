@@ -40,6 +40,7 @@ struct Instance {
     // band compaction + extension values
     int *band_list, *band_count, *band_idx;
     double *ext[4];
+    double *face_ax, *face_ay;   // face accelerations of the projection
     // diagnostics and status
     double *diag_partial, *diag_out, *clock;
     unsigned* diag_ticket;
@@ -182,6 +183,8 @@ static void assign_ptrs(Instance& I, const std::function<char*(size_t)>& take, s
     I.ufx_v = (double*)take(nve * 8);
     I.ufy_l = (double*)take(nh * 8);
     I.ufy_v = (double*)take(nh * 8);
+    I.face_ax = (double*)take(nve * 8);
+    I.face_ay = (double*)take(nh * 8);
     I.op_cd = (double*)take(N * 8);
     I.op_dd = (double*)take(N * 8);
     I.op_wl = (double*)take(N * 8);
@@ -310,7 +313,8 @@ static void solve_energy(Instance& I, cudaStream_t st) {
 
 static void momentum(Instance& I, cudaStream_t st) {
     // S11: predictor; one two-RHS solve (liquid, vapour) per velocity component
-    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, I.cfg.precision == EBIT_MIXED, st);
+    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, I.cfg.precision == EBIT_MIXED,
+                   st);
     count(1);
     for (int comp = 0; comp < 2; ++comp) {
         launch_visc_operator(I.g, I.p, comp, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, st);
@@ -325,7 +329,8 @@ static void momentum(Instance& I, cudaStream_t st) {
                             I.op_wb, I.op_b, st);
     count(1);
     do_solve(I, SLOT_POISSON, I.op_b, I.P, 1, st);
-    launch_project(I.g, I.p, I.P, I.vf, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.gc, I.us_l, I.us_v, I.u_l, I.u_v, st);
+    launch_project(I.g, I.p, I.P, I.vf, I.face_ax, I.face_ay, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.gc, I.us_l, I.us_v,
+                   I.u_l, I.u_v, st);
     count(2);
 }
 
@@ -341,9 +346,9 @@ static void prepare(Instance& I, cudaStream_t st) {
     if (I.p.energy) extend_T(I, I.T_l, I.T_v, st);
     mass_flux(I, st);
     ghost_velocity(I, st);
-    launch_project(I.g, I.p, I.P, I.vf, nullptr, nullptr, nullptr, nullptr, I.gc, nullptr, nullptr, nullptr,
-                   nullptr, st);
-    count(1);
+    launch_project(I.g, I.p, I.P, I.vf, I.face_ax, I.face_ay, nullptr, nullptr, nullptr, nullptr, I.gc, nullptr,
+                   nullptr, nullptr, nullptr, st);
+    count(2);
 }
 
 static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
@@ -352,7 +357,11 @@ static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
         case EBIT_STAGE_PREPARE: prepare(I, st); break;
         case EBIT_STAGE_RECONSTRUCT: reconstruct_full(I, st); break;
         case EBIT_STAGE_ADVECT_T:
-            if (I.p.energy) { launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, I.cfg.precision == EBIT_MIXED, st); count(1); }
+            if (I.p.energy) {
+                launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, I.cfg.precision == EBIT_MIXED,
+                                st);
+                count(1);
+            }
             break;
         case EBIT_STAGE_EXTEND_TSTAR:
             if (I.p.energy) extend_T(I, I.Ts_l, I.Ts_v, st);

@@ -64,40 +64,76 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
 // WENO3 upwind derivative (undivided) from five values along a line. The Jiang-Shu weights
 // a0 = (1/3)/(eps + b0)^2 and a1 = (2/3)/(eps + b1)^2 are normalised after multiplying both
 // by 3 (eps + b0)^2 (eps + b1)^2, which leaves one division instead of three (FP64 division
-// is a multi-instruction sequence on this GPU). F32W: the nonlinear weight is formed in FP32
-// from the FP64 differences (the mixed-precision mode); the candidate stencils and their
-// combination stay FP64.
-template <bool F32W>
-__device__ inline double weno3(double Tm2, double Tm1, double T0, double Tp1, double Tp2, bool upos) {
-    double v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
-    double v2 = upos ? T0 - Tm1 : Tp1 - T0;
-    double v3 = upos ? Tp1 - T0 : T0 - Tm1;
-    double phi0 = 0.5 * (3.0 * v2 - v1);
-    double phi1 = 0.5 * (v2 + v3);
-    if (F32W) {
-        float d0 = (float)(v2 - v1), d1 = (float)(v3 - v2);
-        float s0 = 1e-6f + d0 * d0, s1 = 1e-6f + d1 * d1;
-        float q0 = s1 * s1, q1 = 2.0f * (s0 * s0);
-        float w0 = q0 / (q0 + q1);
-        return phi1 + (double)w0 * (phi0 - phi1);
-    } else {
-        const double eps = 1e-6;
-        double s0 = eps + (v2 - v1) * (v2 - v1);
-        double s1 = eps + (v3 - v2) * (v3 - v2);
-        double q0 = s1 * s1, q1 = 2.0 * (s0 * s0);
-        return (q0 * phi0 + q1 * phi1) / (q0 + q1);
-    }
+// is a multi-instruction sequence on this GPU).
+template <typename R>
+__device__ inline R weno3(R Tm2, R Tm1, R T0, R Tp1, R Tp2, bool upos) {
+    const R eps = R(1e-6);
+    R v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
+    R v2 = upos ? T0 - Tm1 : Tp1 - T0;
+    R v3 = upos ? Tp1 - T0 : T0 - Tm1;
+    R phi0 = R(0.5) * (R(3) * v2 - v1);
+    R phi1 = R(0.5) * (v2 + v3);
+    R s0 = eps + (v2 - v1) * (v2 - v1);
+    R s1 = eps + (v3 - v2) * (v3 - v2);
+    R q0 = s1 * s1, q1 = R(2) * (s0 * s0);
+    return (q0 * phi0 + q1 * phi1) / (q0 + q1);
 }
 
-template <bool F32W, class F>
+template <class F>
 __device__ inline double advect_one(const F& T, const Grid& g, const Refl& r, int i, int j, double2 u,
                                     double dth) {
-    double dx = weno3<F32W>(refl_x(T, g, r, i - 2, j), refl_x(T, g, r, i - 1, j), refl_x(T, g, r, i, j),
-                            refl_x(T, g, r, i + 1, j), refl_x(T, g, r, i + 2, j), u.x >= 0.0);
-    double dy = weno3<F32W>(refl_y(T, g, r, i, j - 2), refl_y(T, g, r, i, j - 1), refl_y(T, g, r, i, j),
-                            refl_y(T, g, r, i, j + 1), refl_y(T, g, r, i, j + 2), u.y >= 0.0);
+    double dx = weno3<double>(refl_x(T, g, r, i - 2, j), refl_x(T, g, r, i - 1, j), refl_x(T, g, r, i, j),
+                              refl_x(T, g, r, i + 1, j), refl_x(T, g, r, i + 2, j), u.x >= 0.0);
+    double dy = weno3<double>(refl_y(T, g, r, i, j - 2), refl_y(T, g, r, i, j - 1), refl_y(T, g, r, i, j),
+                              refl_y(T, g, r, i, j + 1), refl_y(T, g, r, i, j + 2), u.y >= 0.0);
     return refl_x(T, g, r, i, j) - dth * (u.x * dx + u.y * dy);
 }
+
+// ---- mixed-precision variant: the WENO3 stencils of a 32 x 8 tile run in FP32 on values
+// staged once in shared memory (two halo layers, boundary reflections applied), each minus a
+// per-tile FP64 reference so that differences keep the precision of the local variation; the
+// update T - dt/h (u . D) and everything after it stay FP64.
+constexpr int WX = 32, WY = 8, WH = 2, WSX = WX + 2 * WH, WSY = WY + 2 * WH;
+
+struct Scal {
+    const double* F;
+    __device__ double operator[](int c) const { return F[c]; }
+};
+__device__ inline double refl_x(const Scal& F, const Grid& g, const Refl& r, int i, int j) {
+    return refl_x(F.F, g, r, i, j);
+}
+__device__ inline double refl_y(const Scal& F, const Grid& g, const Refl& r, int i, int j) {
+    return refl_y(F.F, g, r, i, j);
+}
+
+template <class F>
+__device__ inline double tile_value(const F& T, const Grid& g, const Refl& r, int i, int j) {
+    bool iin = i >= 0 && i < g.nx, jin = j >= 0 && j < g.ny;
+    if (iin && jin) return T[cidx(g, i, j)];
+    if (jin) return refl_x(T, g, r, i, j);
+    if (iin) return refl_y(T, g, r, i, j);
+    return 0.0;   // a tile corner: no stencil reads it
+}
+
+// stage NF fields of the tile (field f: accessor F[f], reflection rule R[f]) as floats
+template <int NF, class F>
+__device__ inline void tile_stage(const F* T, const Refl* R, const Grid& g, int i0, int j0, const double* ref,
+                                  float (*sh)[WSY][WSX]) {
+    for (int k = threadIdx.x; k < WSX * WSY; k += blockDim.x) {
+        int rx = k % WSX, ry = k / WSX;
+        int i = i0 - WH + rx, j = j0 - WH + ry;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) sh[f][ry][rx] = (float)(tile_value(T[f], g, R[f], i, j) - ref[f]);
+    }
+    __syncthreads();
+}
+
+__device__ inline float2 tile_derivs(const float (*v)[WSX], int rx, int ry, float2 u) {
+    float dx = weno3<float>(v[ry][rx - 2], v[ry][rx - 1], v[ry][rx], v[ry][rx + 1], v[ry][rx + 2], u.x >= 0.0f);
+    float dy = weno3<float>(v[ry - 2][rx], v[ry - 1][rx], v[ry][rx], v[ry + 1][rx], v[ry + 2][rx], u.y >= 0.0f);
+    return make_float2(dx, dy);
+}
+
 
 __host__ inline Refl temperature_refl(const Grid& g) {
     Refl r;
@@ -111,7 +147,6 @@ __host__ inline Refl velocity_refl(const Grid& g, int comp) {
 }
 
 // S1: T*_k = T_k - dt u_k . grad T_k for both phases
-template <bool F32W>
 __global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l, const double* __restrict__ T_v,
                            const double2* __restrict__ u_l, const double2* __restrict__ u_v,
                            double* __restrict__ Ts_l, double* __restrict__ Ts_v) {
@@ -119,8 +154,32 @@ __global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict_
     int j = blockIdx.y;
     if (i >= g.nx) return;
     int c = cidx(g, i, j);
-    Ts_l[c] = advect_one<F32W>(T_l, g, r, i, j, u_l[c], dth);
-    Ts_v[c] = advect_one<F32W>(T_v, g, r, i, j, u_v[c], dth);
+    Ts_l[c] = advect_one(T_l, g, r, i, j, u_l[c], dth);
+    Ts_v[c] = advect_one(T_v, g, r, i, j, u_v[c], dth);
+}
+
+// S1, mixed-precision tile variant (block WX x WY threads, one cell each)
+__global__ void __launch_bounds__(WX * WY) k_advect_T_f32(Grid g, Refl r, double dth, const double* __restrict__ T_l,
+                                                         const double* __restrict__ T_v,
+                                                         const double2* __restrict__ u_l,
+                                                         const double2* __restrict__ u_v, double* __restrict__ Ts_l,
+                                                         double* __restrict__ Ts_v) {
+    __shared__ float sh[2][WSY][WSX];
+    int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
+    int ic = min(i0 + WX / 2, g.nx - 1), jc = min(j0 + WY / 2, g.ny - 1);
+    double ref[2] = {T_l[cidx(g, ic, jc)], T_v[cidx(g, ic, jc)]};
+    Scal F[2] = {{T_l}, {T_v}};
+    Refl R[2] = {r, r};
+    tile_stage<2>(F, R, g, i0, j0, ref, sh);
+    int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
+    int i = i0 + tx, j = j0 + ty;
+    if (i >= g.nx || j >= g.ny) return;
+    int c = cidx(g, i, j);
+    double2 ul = u_l[c], uv = u_v[c];
+    float2 dl = tile_derivs(sh[0], tx + WH, ty + WH, make_float2((float)ul.x, (float)ul.y));
+    float2 dv = tile_derivs(sh[1], tx + WH, ty + WH, make_float2((float)uv.x, (float)uv.y));
+    Ts_l[c] = T_l[c] - dth * (double)((float)ul.x * dl.x + (float)ul.y * dl.y);
+    Ts_v[c] = T_v[c] - dth * (double)((float)uv.x * dv.x + (float)uv.y * dv.y);
 }
 
 // ---------------------------------------------------------------------------------
@@ -286,7 +345,6 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
 
 // RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields,
 // one two-RHS system per component (liquid, vapour interleaved); initial guesses = current u
-template <bool F32W>
 __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const double* __restrict__ vf,
                           const double2* __restrict__ u_l, const double2* __restrict__ u_v,
                           const double2* __restrict__ gc, double2* __restrict__ bx, double2* __restrict__ by,
@@ -298,10 +356,44 @@ __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const do
     double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
-    bx[c] = make_double2(coef * (advect_one<F32W>(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
-                         coef * (advect_one<F32W>(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x));
-    by[c] = make_double2(coef * (advect_one<F32W>(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y),
-                         coef * (advect_one<F32W>(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y));
+    bx[c] = make_double2(coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
+                         coef * (advect_one(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x));
+    by[c] = make_double2(coef * (advect_one(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y),
+                         coef * (advect_one(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y));
+    xx[c] = make_double2(ul.x, uv.x);
+    xy[c] = make_double2(ul.y, uv.y);
+}
+
+// mixed-precision tile variant of k_mom_rhs (block WX x WY threads, one cell each)
+__global__ void __launch_bounds__(WX * WY) k_mom_rhs_f32(Grid g, Phys p, Refl rx, Refl ry, double dth,
+                                                        const double* __restrict__ vf,
+                                                        const double2* __restrict__ u_l,
+                                                        const double2* __restrict__ u_v,
+                                                        const double2* __restrict__ gc, double2* __restrict__ bx,
+                                                        double2* __restrict__ by, double2* __restrict__ xx,
+                                                        double2* __restrict__ xy) {
+    __shared__ float sh[4][WSY][WSX];
+    int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
+    int ic = min(i0 + WX / 2, g.nx - 1), jc = min(j0 + WY / 2, g.ny - 1);
+    double2 ulc = u_l[cidx(g, ic, jc)], uvc = u_v[cidx(g, ic, jc)];
+    double ref[4] = {ulc.x, ulc.y, uvc.x, uvc.y};
+    Comp F[4] = {{u_l, 0}, {u_l, 1}, {u_v, 0}, {u_v, 1}};
+    Refl R[4] = {rx, ry, rx, ry};
+    tile_stage<4>(F, R, g, i0, j0, ref, sh);
+    int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
+    int i = i0 + tx, j = j0 + ty;
+    if (i >= g.nx || j >= g.ny) return;
+    int c = cidx(g, i, j);
+    double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
+    double2 a = gc[c];
+    double2 ul = u_l[c], uv = u_v[c];
+    float2 fl = make_float2((float)ul.x, (float)ul.y), fv = make_float2((float)uv.x, (float)uv.y);
+    float2 d0 = tile_derivs(sh[0], tx + WH, ty + WH, fl), d1 = tile_derivs(sh[1], tx + WH, ty + WH, fl);
+    float2 d2 = tile_derivs(sh[2], tx + WH, ty + WH, fv), d3 = tile_derivs(sh[3], tx + WH, ty + WH, fv);
+    bx[c] = make_double2(coef * (ul.x - dth * (double)(fl.x * d0.x + fl.y * d0.y) + p.dt * a.x),
+                         coef * (uv.x - dth * (double)(fv.x * d2.x + fv.y * d2.y) + p.dt * a.x));
+    by[c] = make_double2(coef * (ul.y - dth * (double)(fl.x * d1.x + fl.y * d1.y) + p.dt * a.y),
+                         coef * (uv.y - dth * (double)(fv.x * d3.x + fv.y * d3.y) + p.dt * a.y));
     xx[c] = make_double2(ul.x, uv.x);
     xy[c] = make_double2(ul.y, uv.y);
 }
@@ -425,32 +517,41 @@ __device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, 
     return p.gy - (-2.0 * P[cidx(g, i, g.ny - 1)]) / (g.h * r);
 }
 
-// face update u_f^{n+1} = u_f* + dt (a_f - g) (discretization equation 4), both phase fields
-__global__ void k_project_faces(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
-                                double* fx_l, double* fx_v, double* fy_l, double* fy_v) {
+// face accelerations a_f = g - grad_f p / rho_f (one FP64 division per face), stored in ax/ay;
+// with fx_l != null also the face update u_f^{n+1} = u_f* + dt (a_f - g) (discretization
+// equation 4) for both phase fields
+__global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
+                             double* __restrict__ ax, double* __restrict__ ay, double* fx_l, double* fx_v,
+                             double* fy_l, double* fy_v) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
         int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        double a = accel_x(g, p, P, vf, i, j);
+        ax[t] = a;
+        if (!fx_l) return;
         bool bnd = i == 0 || i == g.nx;
         if (bnd && g.bc[i == 0 ? 0 : 1] != BC_OUTFLOW) { fx_l[t] = 0.0; fx_v[t] = 0.0; return; }
-        double corr = p.dt * (accel_x(g, p, P, vf, i, j) - p.gx);
+        double corr = p.dt * (a - p.gx);
         fx_l[t] += corr;
         fx_v[t] += corr;
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
         int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        double a = accel_y(g, p, P, vf, i, j);
+        ay[e] = a;
+        if (!fx_l) return;
         bool bnd = j == 0 || j == g.ny;
         if (bnd && g.bc[j == 0 ? 2 : 3] != BC_OUTFLOW) { fy_l[e] = 0.0; fy_v[e] = 0.0; return; }
-        double corr = p.dt * (accel_y(g, p, P, vf, i, j) - p.gy);
+        double corr = p.dt * (a - p.gy);
         fy_l[e] += corr;
         fy_v[e] += corr;
     }
 }
 
 // gc = f->c mean of the face accelerations; optionally u^{n+1} = u** + dt gc (Eq. 15)
-__global__ void k_project_cells(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
+__global__ void k_project_cells(Grid g, Phys p, const double* __restrict__ axf, const double* __restrict__ ayf,
                                 double2* __restrict__ gc, const double2* __restrict__ us_l,
                                 const double2* __restrict__ us_v, double2* __restrict__ u_l,
                                 double2* __restrict__ u_v) {
@@ -458,8 +559,9 @@ __global__ void k_project_cells(Grid g, Phys p, const double* __restrict__ P, co
     int j = blockIdx.y;
     if (i >= g.nx) return;
     int c = cidx(g, i, j);
-    double ax = 0.5 * (accel_x(g, p, P, vf, i, j) + accel_x(g, p, P, vf, i + 1, j));
-    double ay = 0.5 * (accel_y(g, p, P, vf, i, j) + accel_y(g, p, P, vf, i, j + 1));
+    int fx = j * (g.nx + 1) + i;
+    double ax = 0.5 * (axf[fx] + axf[fx + 1]);
+    double ay = 0.5 * (ayf[c] + ayf[c + g.nx]);
     gc[c] = make_double2(ax, ay);
     if (us_l) {
         double2 a = us_l[c], b = us_v[c];
@@ -565,9 +667,12 @@ static inline dim3 rows_grid(int n, int rows, int bs) { return dim3(div_up(n, bs
 
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
                      const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st) {
-    auto k = f32w ? k_advect_T<true> : k_advect_T<false>;
-    k<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l,
-                                                 Ts_v);
+    if (f32w)
+        k_advect_T_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY)), WX * WY, 0, st>>>(
+            g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l, Ts_v);
+    else
+        k_advect_T<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l,
+                                                              u_v, Ts_l, Ts_v);
 }
 
 void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
@@ -625,9 +730,12 @@ void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
                     const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, bool f32w,
                     cudaStream_t st) {
-    auto k = f32w ? k_mom_rhs<true> : k_mom_rhs<false>;
-    k<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf,
-                                                 u_l, u_v, gc, bx, by, xx, xy);
+    if (f32w)
+        k_mom_rhs_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY)), WX * WY, 0, st>>>(
+            g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
+    else
+        k_mom_rhs<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
+                                                             p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
 }
 
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
@@ -646,14 +754,12 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
                                                                   wl, wb, b);
 }
 
-void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* fx_l, double* fx_v,
-                    double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v,
-                    double2* u_l, double2* u_v, cudaStream_t st) {
-    if (fx_l) {
-        long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-        k_project_faces<<<div_up(nf, 256), 256, 0, st>>>(g, p, P, vf, fx_l, fx_v, fy_l, fy_v);
-    }
-    k_project_cells<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, P, vf, gc, us_l, us_v, u_l, u_v);
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* ax, double* ay,
+                    double* fx_l, double* fx_v, double* fy_l, double* fy_v, double2* gc, const double2* us_l,
+                    const double2* us_v, double2* u_l, double2* u_v, cudaStream_t st) {
+    long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
+    k_face_accel<<<div_up(nf, 256), 256, 0, st>>>(g, p, P, vf, ax, ay, fx_l, fx_v, fy_l, fy_v);
+    k_project_cells<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, ax, ay, gc, us_l, us_v, u_l, u_v);
 }
 
 int diag_blocks() { return 152; }

@@ -48,7 +48,7 @@ constexpr int RB = 256;          // threads of grid-stride kernels
 constexpr int NRED = 608;        // blocks of grid-stride kernels (4 x 152 SMs)
 constexpr int SMALL_MAX_F = 4096; // levels with at most this many cells run inside k_small (FP32)
 constexpr int SMALL_MAX_D = 1024; // (FP64: half the shared memory per value)
-constexpr int SMALL_THREADS = 512;
+constexpr int SMALL_THREADS = 1024;
 constexpr int TX = 32, TY = 32;  // tile of the large-level kernels
 constexpr int NU = 2;            // smoothing sweeps (red-black pairs) before and after
 constexpr int COARSE_PAIRS = 12; // symmetric sweeps on the coarsest grid (at most 16 cells)
@@ -188,122 +188,211 @@ __global__ void k_coarsen(int fnx, int fny, const T* __restrict__ fcd, const T* 
 }
 
 // ---- large-level kernels: shared-memory tiles with recomputed halos ---------------------
-// smem layout per region cell: x[NR], b[NR] (type T) then diag, wl, wb and the reciprocal of
-// the full diagonal (D + the four face weights), so that a sweep multiplies instead of divides
+// The region (tile + halo, SX x SY cells, SX even) is stored split by colour: region cell
+// (rx, ry) has colour c = (p0 + rx + ry) & 1, p0 = (gx0 + gy0) & 1 the colour of the region's
+// first cell, and sits in column k = rx >> 1 of row ry of colour c's arrays (HX = SX / 2
+// columns).  A colour-c cell with e = rx & 1 finds its left / right neighbours (colour 1 - c)
+// in columns k - 1 + e / k + e of the same row, and its lower / upper neighbours in column k
+// of rows ry -+ 1.  A half-sweep thus reads unit-stride rows of the other colour.
+// Per colour: x[NR], b[NR] per cell (type T), then D (= cd + dd), wl, wb and the reciprocal
+// of the full diagonal (D + the four face weights), so that a sweep multiplies.
 template <typename T, int NR, int H>
 struct Region {
-    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, N = SX * SY;
-    T* x;
-    T* b;
-    T* d;
-    T* wl;
-    T* wb;
-    T* id;
-    __device__ Region(unsigned char* base) {
-        x = (T*)base;
-        b = x + NR * N;
-        d = b + NR * N;
-        wl = d + N;
-        wb = wl + N;
-        id = wb + N;
-    }
-    static constexpr size_t bytes() { return (size_t)N * (2 * NR + 4) * sizeof(T); }
+    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, HX = SX / 2, NC = SY * HX;
+    static_assert(SX % 2 == 0, "region width must be even");
+    T* x0;   // colour-0 arrays; colour 1 follows each at +NR*NC (x, b) or +NC (the rest)
+    __device__ Region(unsigned char* base) { x0 = (T*)base; }
+    __device__ T* x(int c) const { return x0 + c * (NR * NC); }
+    __device__ T* b(int c) const { return x0 + (2 + c) * (NR * NC); }
+    __device__ T* d(int c) const { return x0 + 4 * NR * NC + c * NC; }
+    __device__ T* wl(int c) const { return x0 + 4 * NR * NC + (2 + c) * NC; }
+    __device__ T* wb(int c) const { return x0 + 4 * NR * NC + (4 + c) * NC; }
+    __device__ T* id(int c) const { return x0 + 4 * NR * NC + (6 + c) * NC; }
+    static constexpr size_t bytes() { return (size_t)2 * NC * (2 * NR + 4) * sizeof(T); }
 };
 
-// one Gauss-Seidel half-sweep of colour `color` over region cells at distance >= s from its
-// edge; threads are laid out 32 x 8, each row visits only the cells of the colour
-template <typename T, int NR, int H>
-__device__ inline void region_sweep(Region<T, NR, H>& R, int gx0, int gy0, int nx, int ny, int s, int color) {
-    constexpr int SX = Region<T, NR, H>::SX, SY = Region<T, NR, H>::SY;
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int ry = s + ty; ry < SY - s; ry += 8) {
-        int gj = gy0 + ry;
-        if (gj < 0 || gj >= ny) continue;
-        int par = (color - gx0 - gj) & 1;          // rx parity of this colour in this row
-        int rx0 = s + ((par - s) & 1);
-        for (int rx = rx0 + 2 * tx; rx < SX - s; rx += 64) {
-            int gi = gx0 + rx;
-            if (gi < 0 || gi >= nx) continue;
-            int q = ry * SX + rx;
-            T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + SX];
-            T id = R.id[q];
+// Thread layout of the region kernels: thread (k, seg) owns column slot k of every row of
+// segment seg (RPS = SY / NSEG consecutive rows), i.e. region columns 2k and 2k + 1; in every
+// row exactly one of the two has the colour being swept, so no lane idles inside the region.
+template <int H> struct TileShape;
+template <> struct TileShape<5> { static constexpr int NSEG = 21; };  // 42 rows = 21 x 2, 441 threads
+template <> struct TileShape<4> { static constexpr int NSEG = 20; };  // 40 rows = 20 x 2, 400 threads
+template <int H>
+constexpr int tile_threads() { return ((TX + 2 * H) / 2) * TileShape<H>::NSEG; }
+template <int H>
+constexpr int tile_block() { return (tile_threads<H>() + 31) / 32 * 32; }
+
+// one Gauss-Seidel half-sweep of colour `color` over the region cells at distance >= S from
+// its edge (cells outside the domain have b = 0 and zero weights, so they stay 0); every
+// operand of the thread's rows is loaded before any of its results is stored
+template <typename T, int NR, int H, int S>
+__device__ inline void region_sweep(Region<T, NR, H>& R, int p0, int color) {
+    using Rg = Region<T, NR, H>;
+    constexpr int HX = Rg::HX, SX = Rg::SX, SY = Rg::SY, NSEG = TileShape<H>::NSEG, RPS = SY / NSEG;
+    static_assert(RPS * NSEG == SY, "segments must tile the region rows");
+    int t = threadIdx.x;
+    if (t < HX * NSEG) {
+        int k = t % HX, ry0 = (t / HX) * RPS;
+        const int o = 1 - color;
+        const T* xo = R.x(o);
+        const T* bs = R.b(color);
+        const T* wls = R.wl(color);
+        const T* wlo = R.wl(o);
+        const T* wbs = R.wb(color);
+        const T* wbo = R.wb(o);
+        const T* ids = R.id(color);
+        T acc[RPS][NR];
+        bool ok[RPS];
 #pragma unroll
-            for (int k2 = 0; k2 < NR; ++k2) {
-                T acc = R.b[q * NR + k2] + wl * R.x[(q - 1) * NR + k2] + wr * R.x[(q + 1) * NR + k2] +
-                        wb * R.x[(q - SX) * NR + k2] + wt * R.x[(q + SX) * NR + k2];
-                R.x[q * NR + k2] = acc * id;
+        for (int r = 0; r < RPS; ++r) {
+            int ry = ry0 + r;
+            int e = (color + p0 + ry) & 1;
+            int rx = 2 * k + e;
+            ok[r] = ry >= S && ry < SY - S && rx >= S && rx < SX - S;
+            int q = ok[r] ? ry * HX + k : HX + 1;   // a harmless in-range slot otherwise
+            int ee = ok[r] ? e : 0;
+            T wl = wls[q], wr = wlo[q + ee], wb = wbs[q], wt = wbo[q + HX], id = ids[q];
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2)
+                acc[r][k2] = (bs[q * NR + k2] + wl * xo[(q - 1 + ee) * NR + k2] + wr * xo[(q + ee) * NR + k2] +
+                              wb * xo[(q - HX) * NR + k2] + wt * xo[(q + HX) * NR + k2]) * id;
+        }
+        T* xs = R.x(color);
+#pragma unroll
+        for (int r = 0; r < RPS; ++r)
+            if (ok[r])
+#pragma unroll
+                for (int k2 = 0; k2 < NR; ++k2) xs[((ry0 + r) * HX + k) * NR + k2] = acc[r][k2];
+    }
+    __syncthreads();
+}
+
+// region cell -> (colour, column-major slot)
+template <typename T, int NR, int H>
+__device__ inline int region_slot(int p0, int rx, int ry, int& c) {
+    c = (p0 + rx + ry) & 1;
+    return ry * Region<T, NR, H>::HX + (rx >> 1);
+}
+
+// (A x)_cell - computed from the region (the cell must be at distance >= 1 from its edge)
+template <typename T, int NR, int H>
+__device__ inline void region_residual(const Region<T, NR, H>& R, int p0, int rx, int ry, T* res) {
+    constexpr int HX = Region<T, NR, H>::HX;
+    int c;
+    int q = region_slot<T, NR, H>(p0, rx, ry, c);
+    int o = 1 - c, e = rx & 1;
+    T wl = R.wl(c)[q], wr = R.wl(o)[q + e], wb = R.wb(c)[q], wt = R.wb(o)[q + HX], d = R.d(c)[q];
+#pragma unroll
+    for (int k2 = 0; k2 < NR; ++k2) {
+        T xc0 = R.x(c)[q * NR + k2];
+        T ax = d * xc0 + wl * (xc0 - R.x(o)[(q - 1 + e) * NR + k2]) + wr * (xc0 - R.x(o)[(q + e) * NR + k2]) +
+               wb * (xc0 - R.x(o)[(q - HX) * NR + k2]) + wt * (xc0 - R.x(o)[(q + HX) * NR + k2]);
+        res[k2] = R.b(c)[q * NR + k2] - ax;
+    }
+}
+
+// load b (and x = xin + prolongated coarse x when x != null), D, wl, wb of the region and the
+// reciprocal of every cell's full diagonal (its right and upper face weights read from global
+// memory too); cells outside the domain get D = 1, zero weights, b = x = 0.  Thread (k, seg)
+// loads region columns 2k, 2k + 1 of its rows.
+template <typename T, int NR, int H>
+__device__ inline void region_load(Region<T, NR, H>& R, int p0, const Lev<T>& L, const T* __restrict__ b,
+                                   const T* __restrict__ x, const T* __restrict__ xc, int cnx, int gx0, int gy0) {
+    using Rg = Region<T, NR, H>;
+    constexpr int HX = Rg::HX, SY = Rg::SY, NSEG = TileShape<H>::NSEG, RPS = SY / NSEG;
+    int t = threadIdx.x;
+    if (t < HX * NSEG) {
+        int k = t % HX, ry0 = (t / HX) * RPS;
+#pragma unroll
+        for (int r = 0; r < RPS; ++r) {
+            int ry = ry0 + r;
+            int gj = gy0 + ry;
+            bool jin = gj >= 0 && gj < L.ny;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                int rx = 2 * k + e;
+                int gi = gx0 + rx;
+                bool in = jin && gi >= 0 && gi < L.nx;
+                int c = (p0 + rx + ry) & 1;
+                int q = ry * HX + k;
+                // loads are unconditional (clamped to the domain, then masked) so that all of a
+                // thread's loads can be in flight at once
+                int gic = min(max(gi, 0), L.nx - 1), gjc = min(max(gj, 0), L.ny - 1);
+                int g = gjc * L.nx + gic;
+                Vec<T, NR> bv = reinterpret_cast<const Vec<T, NR>*>(b)[g], xv;
+                T dv = L.diag[g], wlv = L.wl[g], wbv = L.wb[g];
+                T wrv = L.wl[gic + 1 < L.nx ? g + 1 : g], wtv = L.wb[gjc + 1 < L.ny ? g + L.nx : g];
+                if (gi + 1 >= L.nx) wrv = T(0);
+                if (gj + 1 >= L.ny) wtv = T(0);
+                if (x) {
+                    xv = reinterpret_cast<const Vec<T, NR>*>(x)[g];
+                    Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gjc >> 1) * cnx + (gic >> 1)];
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] += cv.v[k2];
+                } else {
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
+                }
+                if (!in) {
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) { bv.v[k2] = T(0); xv.v[k2] = T(0); }
+                    dv = T(1); wlv = wbv = wrv = wtv = T(0);
+                }
+                T* xb = R.x(c);
+                T* bb = R.b(c);
+#pragma unroll
+                for (int k2 = 0; k2 < NR; ++k2) { bb[q * NR + k2] = bv.v[k2]; xb[q * NR + k2] = xv.v[k2]; }
+                R.d(c)[q] = dv;
+                R.wl(c)[q] = wlv;
+                R.wb(c)[q] = wbv;
+                R.id(c)[q] = T(1) / (dv + wlv + wrv + wbv + wtv);
             }
         }
     }
     __syncthreads();
 }
 
+// write the tile core's x (natural order, coalesced)
 template <typename T, int NR, int H>
-__device__ inline void region_load(Region<T, NR, H>& R, const Lev<T>& L, const T* __restrict__ b,
-                                   const T* __restrict__ x, const T* __restrict__ xc, int cnx, int gx0, int gy0) {
-    constexpr int SX = Region<T, NR, H>::SX, SY = Region<T, NR, H>::SY;
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int ry = ty; ry < SY; ry += 8) {
-        int gj = gy0 + ry;
-        bool jin = gj >= 0 && gj < L.ny;
-        for (int rx = tx; rx < SX; rx += 32) {
-            int gi = gx0 + rx;
-            bool in = jin && gi >= 0 && gi < L.nx;
-            int q = ry * SX + rx;
-            int c = gj * L.nx + gi;
-            Vec<T, NR> bv, xv;
+__device__ inline double2 region_store_core(const Region<T, NR, H>& R, int p0, const Lev<T>& L, int gx0, int gy0,
+                                            T* __restrict__ x, bool dot) {
+    double acc[2] = {0.0, 0.0};
+    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
+        int rx = H + k % TX, ry = H + k / TX;
+        int gi = gx0 + rx, gj = gy0 + ry;
+        if (gi >= L.nx || gj >= L.ny) continue;
+        int c;
+        int q = region_slot<T, NR, H>(p0, rx, ry, c);
+        Vec<T, NR> xv;
 #pragma unroll
-            for (int k = 0; k < NR; ++k) { bv.v[k] = T(0); xv.v[k] = T(0); }
-            if (in) {
-                bv = reinterpret_cast<const Vec<T, NR>*>(b)[c];
-                if (x) {
-                    xv = reinterpret_cast<const Vec<T, NR>*>(x)[c];
-                    Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gj >> 1) * cnx + (gi >> 1)];
-#pragma unroll
-                    for (int k = 0; k < NR; ++k) xv.v[k] += cv.v[k];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NR; ++k) { R.b[q * NR + k] = bv.v[k]; R.x[q * NR + k] = xv.v[k]; }
-            R.d[q] = in ? L.diag[c] : T(1);   // D = cd + dd
-            R.wl[q] = in ? L.wl[c] : T(0);
-            R.wb[q] = in ? L.wb[c] : T(0);
+        for (int k2 = 0; k2 < NR; ++k2) {
+            xv.v[k2] = R.x(c)[q * NR + k2];
+            if (dot) acc[k2] += (double)xv.v[k2] * (double)R.b(c)[q * NR + k2];
         }
+        reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
     }
-    __syncthreads();
-    // reciprocal full diagonal of every cell a sweep can reach (not the outermost ring)
-    for (int ry = 1 + ty; ry < SY - 1; ry += 8)
-        for (int rx = 1 + tx; rx < SX - 1; rx += 32) {
-            int q = ry * SX + rx;
-            R.id[q] = T(1) / (R.d[q] + R.wl[q] + R.wl[q + 1] + R.wb[q] + R.wb[q + SX]);
-        }
-    __syncthreads();
+    return make_double2(acc[0], acc[1]);
 }
 
 // k_pre: x = S^nu(0; b) on the tile (red-black order), coarse b = R (b - A x)
 template <typename T, int NR>
-__global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x,
+__global__ void __launch_bounds__(tile_block<2 * NU + 1>()) k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x,
                                               T* __restrict__ bc, const SolveState* __restrict__ st, KTimer* tm) {
     if (skip(st)) return;
     constexpr int H = 2 * NU + 1;
+    static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(16) unsigned char smem[];
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
-    region_load<T, NR, H>(R, L, b, nullptr, nullptr, 0, gx0, gy0);
-    for (int s = 1; s <= 2 * NU; ++s) region_sweep<T, NR, H>(R, gx0, gy0, L.nx, L.ny, s, (s - 1) & 1);
-    // write the tile's x
-    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
-        int rx = H + k % TX, ry = H + k / TX;
-        int gi = gx0 + rx, gj = gy0 + ry;
-        if (gi >= L.nx || gj >= L.ny) continue;
-        int q = ry * Rg::SX + rx;
-        Vec<T, NR> xv;
-#pragma unroll
-        for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = R.x[q * NR + k2];
-        reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
-    }
+    int p0 = (gx0 + gy0) & 1;
+    region_load<T, NR, H>(R, p0, L, b, nullptr, nullptr, 0, gx0, gy0);
+    region_sweep<T, NR, H, 1>(R, p0, 0);
+    region_sweep<T, NR, H, 2>(R, p0, 1);
+    region_sweep<T, NR, H, 3>(R, p0, 0);
+    region_sweep<T, NR, H, 4>(R, p0, 1);
+    region_store_core<T, NR, H>(R, p0, L, gx0, gy0, x, false);
     // residual of the tile, restricted (sum of four children)
     int cnx = L.nx / 2, cny = L.ny / 2;
     for (int k = threadIdx.x; k < (TX / 2) * (TY / 2); k += blockDim.x) {
@@ -314,16 +403,10 @@ __global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, 
         for (int k2 = 0; k2 < NR; ++k2) acc.v[k2] = T(0);
         for (int d2 = 0; d2 < 4; ++d2) {
             int gi = 2 * ci + (d2 & 1), gj = 2 * cj + (d2 >> 1);
-            int rx = gi - gx0, ry = gj - gy0;
-            int q = ry * Rg::SX + rx;
-            T wl = R.wl[q], wr = R.wl[q + 1], wb = R.wb[q], wt = R.wb[q + Rg::SX], d = R.d[q];
+            T res[NR];
+            region_residual<T, NR, H>(R, p0, gi - gx0, gj - gy0, res);
 #pragma unroll
-            for (int k2 = 0; k2 < NR; ++k2) {
-                T xc0 = R.x[q * NR + k2];
-                T ax = d * xc0 + wl * (xc0 - R.x[(q - 1) * NR + k2]) + wr * (xc0 - R.x[(q + 1) * NR + k2]) +
-                       wb * (xc0 - R.x[(q - Rg::SX) * NR + k2]) + wt * (xc0 - R.x[(q + Rg::SX) * NR + k2]);
-                acc.v[k2] += R.b[q * NR + k2] - ax;
-            }
+            for (int k2 = 0; k2 < NR; ++k2) acc.v[k2] += res[k2];
         }
         reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
     }
@@ -333,7 +416,7 @@ __global__ void __launch_bounds__(256) k_pre(Lev<T> L, const T* __restrict__ b, 
 
 // k_post: x = xin + P xc, then black-red sweeps; at the finest level also r.z -> beta
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin,
+__global__ void __launch_bounds__(tile_block<2 * NU>()) k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin,
                                                T* __restrict__ x, const T* __restrict__ xc, SolveState* st,
                                                double* partial, unsigned* ticket, KTimer* tm) {
     if (skip(st)) return;
@@ -343,25 +426,15 @@ __global__ void __launch_bounds__(256) k_post(Lev<T> L, const T* __restrict__ b,
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
-    region_load<T, NR, H>(R, L, b, xin, xc, L.nx / 2, gx0, gy0);
-    for (int s = 1; s <= 2 * NU; ++s) region_sweep<T, NR, H>(R, gx0, gy0, L.nx, L.ny, s, ((s - 1) & 1) ^ 1);
-    double dot[NR];
-#pragma unroll
-    for (int k2 = 0; k2 < NR; ++k2) dot[k2] = 0.0;
-    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
-        int rx = H + k % TX, ry = H + k / TX;
-        int gi = gx0 + rx, gj = gy0 + ry;
-        if (gi >= L.nx || gj >= L.ny) continue;
-        int q = ry * Rg::SX + rx;
-        Vec<T, NR> xv;
-#pragma unroll
-        for (int k2 = 0; k2 < NR; ++k2) {
-            xv.v[k2] = R.x[q * NR + k2];
-            if (DOT) dot[k2] += (double)R.x[q * NR + k2] * (double)R.b[q * NR + k2];
-        }
-        reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
-    }
+    int p0 = (gx0 + gy0) & 1;
+    region_load<T, NR, H>(R, p0, L, b, xin, xc, L.nx / 2, gx0, gy0);
+    region_sweep<T, NR, H, 1>(R, p0, 1);
+    region_sweep<T, NR, H, 2>(R, p0, 0);
+    region_sweep<T, NR, H, 3>(R, p0, 1);
+    region_sweep<T, NR, H, 4>(R, p0, 0);
+    double2 dd = region_store_core<T, NR, H>(R, p0, L, gx0, gy0, x, DOT);
     if (DOT) {
+        double dot[2] = {dd.x, dd.y};
         double tot[NR];
         if (grid_reduce<NR>(dot, partial, ticket, tot)) {
 #pragma unroll
@@ -388,36 +461,55 @@ struct SmallPlan {
 // shared-memory layout: x[NR*total], b[NR*total], diag[total], wl[total], wb[total]
 template <typename T, int NR>
 struct SmallMem {
-    T *x, *b, *d, *wl, *wb;
+    T *x, *b, *d, *wl, *wb, *id;   // id: reciprocal of the full diagonal D + the four face weights
     __device__ SmallMem(unsigned char* base, int total) {
         x = (T*)base;
         b = x + (size_t)NR * total;
         d = b + (size_t)NR * total;
         wl = d + total;
         wb = wl + total;
+        id = wb + total;
     }
-    static size_t bytes(int total) { return (size_t)total * (2 * NR + 3) * sizeof(T); }
+    static size_t bytes(int total) { return (size_t)total * (2 * NR + 4) * sizeof(T); }
 };
 
+// one red-black half-sweep of level l; each thread takes two cells of the colour per pass and
+// loads both cells' operands before storing either result
 template <typename T, int NR>
 __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M, int color) {
     int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
-    for (int j = ty; j < ny; j += nty) {
-        for (int i = ((color - j) & 1) + 2 * tx; i < nx; i += 64) {
-            int q = o + j * nx + i;
-            T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
-            T dg = M.d[q] + w0 + w1 + w2 + w3;
+    int hx = nx >> 1;                    // cells of one colour per row (nx is even on these levels)
+    int n = hx * ny;
+    if (nx & 1) hx = (nx + 1) >> 1, n = hx * ny;
+    for (int base = threadIdx.x; base < n; base += 2 * blockDim.x) {
+        T acc[2][NR], id[2];
+        int q[2];
+        bool ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            int idx = base + u * blockDim.x;
+            int j = idx / hx, i = 2 * (idx - j * hx) + ((color - j) & 1);
+            ok[u] = idx < n && i < nx;
+            int qq = ok[u] ? o + j * nx + i : o;
+            q[u] = qq;
+            T w0 = M.wl[qq], w1 = ok[u] && i < nx - 1 ? M.wl[qq + 1] : T(0), w2 = M.wb[qq],
+              w3 = ok[u] && j < ny - 1 ? M.wb[qq + nx] : T(0);
+            id[u] = M.id[qq];
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                T acc = M.b[q * NR + k];
-                if (i > 0) acc += w0 * M.x[(q - 1) * NR + k];
-                if (i < nx - 1) acc += w1 * M.x[(q + 1) * NR + k];
-                if (j > 0) acc += w2 * M.x[(q - nx) * NR + k];
-                if (j < ny - 1) acc += w3 * M.x[(q + nx) * NR + k];
-                M.x[q * NR + k] = acc / dg;
+                T a = M.b[qq * NR + k];
+                if (ok[u] && i > 0) a += w0 * M.x[(qq - 1) * NR + k];
+                if (ok[u] && i < nx - 1) a += w1 * M.x[(qq + 1) * NR + k];
+                if (ok[u] && j > 0) a += w2 * M.x[(qq - nx) * NR + k];
+                if (ok[u] && j < ny - 1) a += w3 * M.x[(qq + nx) * NR + k];
+                acc[u][k] = a;
             }
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (ok[u])
+#pragma unroll
+                for (int k = 0; k < NR; ++k) M.x[q[u] * NR + k] = acc[u][k] * id[u];
     }
     __syncthreads();
 }
@@ -449,6 +541,15 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
     int n0 = P.nx[0] * P.ny[0];
 #pragma unroll 4
     for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) M.b[c] = b_in[c];
+    __syncthreads();
+    for (int l = 0; l < P.n; ++l) {
+        int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
+        for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
+            int j = c / nx, i = c - j * nx, q = o + c;
+            T dg = M.d[q] + M.wl[q] + (i < nx - 1 ? M.wl[q + 1] : T(0)) + M.wb[q] + (j < ny - 1 ? M.wb[q + nx] : T(0));
+            M.id[q] = T(1) / dg;
+        }
+    }
     __syncthreads();
     // down
     for (int l = 0; l < P.n - 1; ++l) {
@@ -1059,7 +1160,7 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
         T* bc = B + 2 * s.loff[l + 1];
-        k_pre<T, NR><<<grid, 256, Region<T, NR, 2 * NU + 1>::bytes(), stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
+        k_pre<T, NR><<<grid, tile_block<2 * NU + 1>(), Region<T, NR, 2 * NU + 1>::bytes(), stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
                                                                            s.timing && l == 0 ? s.timer : nullptr);
         if (!s.use_graph) ++s.launches;
         b = bc;
@@ -1087,9 +1188,9 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         size_t smem = Region<T, NR, 2 * NU>::bytes();
         KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
         if (l == 0)
-            k_post<T, NR, true><<<grid, 256, smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
+            k_post<T, NR, true><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
         else
-            k_post<T, NR, false><<<grid, 256, smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
+            k_post<T, NR, false><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
         if (!s.use_graph) ++s.launches;
     }
 }

@@ -271,9 +271,17 @@ def test_several_steps_track_the_oracle(dev, name):
         E.ebit_destroy(ctx)
 
 
+# Mixed mode: the solves are FP32 MG-PCG inside FP64 refinement (here to 1e-10) and the WENO3
+# advection stencils run in FP32, whose rounding is of order the FP32 epsilon (6e-8) relative to
+# the advected increment; the projection turns a velocity error d into a pressure error of
+# about d / CFL relative to rho_l u^2.  Bar: 16 FP32 epsilons, 1e-6.
+TOL_MIXED = 1e-6
+
+
 @pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
 def test_mixed_precision_error_against_oracle(dev, name):
-    """FP32 MG-PCG inside FP64 refinement to 1e-10: error vs the FP64 oracle stated and bounded."""
+    """FP32 MG-PCG inside FP64 refinement to 1e-10, FP32 WENO3 stencils: error vs the FP64 oracle
+    stated and bounded."""
     st = prepared(name, 1)
     ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-10)
     try:
@@ -285,7 +293,8 @@ def test_mixed_precision_error_against_oracle(dev, name):
         assert np.array_equal(g["vcol"], so.vcol)
         for k in ("T_l", "T_v", "p", "u_l", "u_v"):
             e = relerr(g[k], getattr(so, k), group_scale(so, k))
-            assert e < 1e-7, (k, e)
+            print(f"mixed {name} {k}: {e:.2e}")
+            assert e < TOL_MIXED, (k, e)
     finally:
         E.ebit_destroy(ctx)
 

@@ -187,227 +187,223 @@ __global__ void k_coarsen(int fnx, int fny, const T* __restrict__ fcd, const T* 
         coarsen_cell(fnx, fcd, fdd, fwl, fwb, nx, ny, c % nx, c / nx, ccd, cdd, cwl, cwb, cdiag);
 }
 
-// ---- large-level kernels: shared-memory tiles with recomputed halos ---------------------
-// The region (tile + halo, SX x SY cells, SX even) is stored split by colour: region cell
-// (rx, ry) has colour c = (p0 + rx + ry) & 1, p0 = (gx0 + gy0) & 1 the colour of the region's
-// first cell, and sits in column k = rx >> 1 of row ry of colour c's arrays (HX = SX / 2
-// columns).  A colour-c cell with e = rx & 1 finds its left / right neighbours (colour 1 - c)
-// in columns k - 1 + e / k + e of the same row, and its lower / upper neighbours in column k
-// of rows ry -+ 1.  A half-sweep thus reads unit-stride rows of the other colour.
-// Per colour: x[NR], b[NR] per cell (type T), then D (= cd + dd), wl, wb and the reciprocal
-// of the full diagonal (D + the four face weights), so that a sweep multiplies.
+// ---- large-level kernels: tiles with recomputed halos ------------------------------------
+// A tile kernel owns a TX x TY block of cells and recomputes a halo of H cells around it, so one
+// launch performs several red-black half-sweeps with no exchange between blocks (halo cells
+// are recomputed from the same inputs with the same formula, so the result equals global
+// red-black Gauss-Seidel exactly).
+//
+// Thread (k, seg) owns the cells of region columns 2k and 2k + 1 in the two rows 2 seg and
+// 2 seg + 1; in every row exactly one of its two cells has the colour being swept.  A thread
+// keeps its four cells' coefficients (b, the reciprocal of the full diagonal, the four face
+// weights, D) in registers; only x lives in shared memory, split by colour: region cell
+// (rx, ry) has colour c = (p0 + rx + ry) & 1 (p0 = (gx0 + gy0) & 1) and sits in column
+// k = rx >> 1 of row ry of colour c's array (HX = SX / 2 columns).  A colour-c cell with
+// e = rx & 1 finds its left / right neighbours (colour 1 - c) in columns k - 1 + e / k + e of
+// its row and its lower / upper neighbours in column k of rows ry -+ 1.
 template <typename T, int NR, int H>
 struct Region {
     static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, HX = SX / 2, NC = SY * HX;
-    static_assert(SX % 2 == 0, "region width must be even");
-    T* x0;   // colour-0 arrays; colour 1 follows each at +NR*NC (x, b) or +NC (the rest)
+    static constexpr int NSEG = SY / 2, THREADS = HX * NSEG;
+    static_assert(SX % 2 == 0 && SY % 2 == 0, "region sides must be even");
+    T* x0;   // x of colour 0 (NR per cell), then colour 1; then the core residuals (k_pre)
     __device__ Region(unsigned char* base) { x0 = (T*)base; }
     __device__ T* x(int c) const { return x0 + c * (NR * NC); }
-    __device__ T* b(int c) const { return x0 + (2 + c) * (NR * NC); }
-    __device__ T* d(int c) const { return x0 + 4 * NR * NC + c * NC; }
-    __device__ T* wl(int c) const { return x0 + 4 * NR * NC + (2 + c) * NC; }
-    __device__ T* wb(int c) const { return x0 + 4 * NR * NC + (4 + c) * NC; }
-    __device__ T* id(int c) const { return x0 + 4 * NR * NC + (6 + c) * NC; }
-    static constexpr size_t bytes() { return (size_t)2 * NC * (2 * NR + 4) * sizeof(T); }
+    __device__ T* res() const { return x0 + 2 * NR * NC; }
+    static constexpr size_t bytes() { return ((size_t)2 * NC + TX * TY) * NR * sizeof(T); }
+};
+template <int H>
+constexpr int tile_block() { return (((TX + 2 * H) / 2) * ((TY + 2 * H) / 2) + 31) / 32 * 32; }
+// blocks per SM the single-value FP32 tile kernels are compiled for (register budget); the
+// others keep the compiler's choice
+template <typename T, int NR>
+constexpr int tile_min_blocks() { return sizeof(T) == 4 && NR == 1 ? 3 : 1; }
+
+// the thread's four cells: [r][c] = row ry0 + r, colour c (its column is 2k + (c ^ sw[r]))
+template <typename T, int NR>
+struct Cells {
+    T b[2][2][NR], id[2][2], wl[2][2], wr[2][2], wb[2][2], wt[2][2], d[2][2];
+    int sw[2];   // (p0 + ry) & 1: the colour-0 cell of row r is in column 2k + sw[r]
 };
 
-// Thread layout of the region kernels: thread (k, seg) owns column slot k of every row of
-// segment seg (RPS = SY / NSEG consecutive rows), i.e. region columns 2k and 2k + 1; in every
-// row exactly one of the two has the colour being swept, so no lane idles inside the region.
-template <int H> struct TileShape;
-template <> struct TileShape<5> { static constexpr int NSEG = 21; };  // 42 rows = 21 x 2, 441 threads
-template <> struct TileShape<4> { static constexpr int NSEG = 20; };  // 40 rows = 20 x 2, 400 threads
-template <int H>
-constexpr int tile_threads() { return ((TX + 2 * H) / 2) * TileShape<H>::NSEG; }
-template <int H>
-constexpr int tile_block() { return (tile_threads<H>() + 31) / 32 * 32; }
-
-// one Gauss-Seidel half-sweep of colour `color` over the region cells at distance >= S from
-// its edge (cells outside the domain have b = 0 and zero weights, so they stay 0); every
-// operand of the thread's rows is loaded before any of its results is stored
-template <typename T, int NR, int H, int S>
-__device__ inline void region_sweep(Region<T, NR, H>& R, int p0, int color) {
-    using Rg = Region<T, NR, H>;
-    constexpr int HX = Rg::HX, SX = Rg::SX, SY = Rg::SY, NSEG = TileShape<H>::NSEG, RPS = SY / NSEG;
-    static_assert(RPS * NSEG == SY, "segments must tile the region rows");
-    int t = threadIdx.x;
-    if (t < HX * NSEG) {
-        int k = t % HX, ry0 = (t / HX) * RPS;
-        const int o = 1 - color;
-        const T* xo = R.x(o);
-        const T* bs = R.b(color);
-        const T* wls = R.wl(color);
-        const T* wlo = R.wl(o);
-        const T* wbs = R.wb(color);
-        const T* wbo = R.wb(o);
-        const T* ids = R.id(color);
-        T acc[RPS][NR];
-        bool ok[RPS];
+// load the thread's cells (coefficients to registers, x to shared memory: 0, or xin + the
+// prolongated coarse x when xin != null); cells outside the domain get D = 1, zero weights,
+// b = x = 0, so sweeps leave them 0
+template <typename T, int NR, int H>
+__device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, int k, int ry0, const Lev<T>& L,
+                                 const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
+                                 int cnx, int gx0, int gy0) {
+    constexpr int HX = Region<T, NR, H>::HX;
 #pragma unroll
-        for (int r = 0; r < RPS; ++r) {
+    for (int r = 0; r < 2; ++r) {
+        int ry = ry0 + r;
+        int gj = gy0 + ry;
+        C.sw[r] = (p0 + ry) & 1;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            int rx = 2 * k + e;
+            int gi = gx0 + rx;
+            bool in = gj >= 0 && gj < L.ny && gi >= 0 && gi < L.nx;
+            // unconditional loads (clamped, then masked): all of them can be in flight at once
+            int gic = min(max(gi, 0), L.nx - 1), gjc = min(max(gj, 0), L.ny - 1);
+            int g = gjc * L.nx + gic;
+            Vec<T, NR> bv = reinterpret_cast<const Vec<T, NR>*>(b)[g], xv;
+            T dv = L.diag[g], wlv = L.wl[g], wbv = L.wb[g];
+            T wrv = L.wl[gic + 1 < L.nx ? g + 1 : g], wtv = L.wb[gjc + 1 < L.ny ? g + L.nx : g];
+            if (gi + 1 >= L.nx) wrv = T(0);
+            if (gj + 1 >= L.ny) wtv = T(0);
+            if (xin) {
+                xv = reinterpret_cast<const Vec<T, NR>*>(xin)[g];
+                Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gjc >> 1) * cnx + (gic >> 1)];
+#pragma unroll
+                for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] += cv.v[k2];
+            } else {
+#pragma unroll
+                for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
+            }
+            if (!in) {
+#pragma unroll
+                for (int k2 = 0; k2 < NR; ++k2) { bv.v[k2] = T(0); xv.v[k2] = T(0); }
+                dv = T(1);
+                wlv = wbv = wrv = wtv = T(0);
+            }
+            // this cell's colour is e ^ sw[r]; both register slots of the row are written by
+            // selects so that no register array is indexed at run time
+            bool mine0 = (e ^ C.sw[r]) == 0;
+            T idv = T(1) / (dv + wlv + wrv + wbv + wtv);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                bool m = (c == 0) == mine0;
+                if (m) {
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) C.b[r][c][k2] = bv.v[k2];
+                    C.id[r][c] = idv;
+                    C.wl[r][c] = wlv;
+                    C.wr[r][c] = wrv;
+                    C.wb[r][c] = wbv;
+                    C.wt[r][c] = wtv;
+                    C.d[r][c] = dv;
+                }
+            }
+            int cc = e ^ C.sw[r];
+            T* xd = R.x(cc) + (ry * HX + k) * NR;
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) xd[k2] = xv.v[k2];
+        }
+    }
+}
+
+// one Gauss-Seidel half-sweep of colour COLOR over the region cells at distance >= S from its
+// edge; both rows' operands are loaded before either result is stored
+template <typename T, int NR, int H, int S, int COLOR>
+__device__ inline void tile_sweep(Region<T, NR, H>& R, const Cells<T, NR>& C, int k, int ry0, bool act) {
+    using Rg = Region<T, NR, H>;
+    constexpr int HX = Rg::HX, SX = Rg::SX, SY = Rg::SY;
+    if (act) {
+        const T* xo = R.x(1 - COLOR);
+        T acc[2][NR];
+        bool ok[2];
+        int qs[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
             int ry = ry0 + r;
-            int e = (color + p0 + ry) & 1;
+            int e = COLOR ^ C.sw[r];
             int rx = 2 * k + e;
             ok[r] = ry >= S && ry < SY - S && rx >= S && rx < SX - S;
             int q = ok[r] ? ry * HX + k : HX + 1;   // a harmless in-range slot otherwise
             int ee = ok[r] ? e : 0;
-            T wl = wls[q], wr = wlo[q + ee], wb = wbs[q], wt = wbo[q + HX], id = ids[q];
+            qs[r] = q;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2)
-                acc[r][k2] = (bs[q * NR + k2] + wl * xo[(q - 1 + ee) * NR + k2] + wr * xo[(q + ee) * NR + k2] +
-                              wb * xo[(q - HX) * NR + k2] + wt * xo[(q + HX) * NR + k2]) * id;
+                acc[r][k2] = (C.b[r][COLOR][k2] + C.wl[r][COLOR] * xo[(q - 1 + ee) * NR + k2] +
+                              C.wr[r][COLOR] * xo[(q + ee) * NR + k2] + C.wb[r][COLOR] * xo[(q - HX) * NR + k2] +
+                              C.wt[r][COLOR] * xo[(q + HX) * NR + k2]) *
+                             C.id[r][COLOR];
         }
-        T* xs = R.x(color);
+        T* xs = R.x(COLOR);
 #pragma unroll
-        for (int r = 0; r < RPS; ++r)
+        for (int r = 0; r < 2; ++r)
             if (ok[r])
 #pragma unroll
-                for (int k2 = 0; k2 < NR; ++k2) xs[((ry0 + r) * HX + k) * NR + k2] = acc[r][k2];
+                for (int k2 = 0; k2 < NR; ++k2) xs[qs[r] * NR + k2] = acc[r][k2];
     }
     __syncthreads();
 }
 
-// region cell -> (colour, column-major slot)
-template <typename T, int NR, int H>
-__device__ inline int region_slot(int p0, int rx, int ry, int& c) {
-    c = (p0 + rx + ry) & 1;
-    return ry * Region<T, NR, H>::HX + (rx >> 1);
-}
-
-// (A x)_cell - computed from the region (the cell must be at distance >= 1 from its edge)
-template <typename T, int NR, int H>
-__device__ inline void region_residual(const Region<T, NR, H>& R, int p0, int rx, int ry, T* res) {
+// the thread's core cells (inside the TX x TY tile and the domain): f(r, c, rx, ry, q, gi, gj)
+template <typename T, int NR, int H, class Fn>
+__device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, int gx0, int gy0, const Lev<T>& L,
+                                       Fn&& f) {
     constexpr int HX = Region<T, NR, H>::HX;
-    int c;
-    int q = region_slot<T, NR, H>(p0, rx, ry, c);
-    int o = 1 - c, e = rx & 1;
-    T wl = R.wl(c)[q], wr = R.wl(o)[q + e], wb = R.wb(c)[q], wt = R.wb(o)[q + HX], d = R.d(c)[q];
 #pragma unroll
-    for (int k2 = 0; k2 < NR; ++k2) {
-        T xc0 = R.x(c)[q * NR + k2];
-        T ax = d * xc0 + wl * (xc0 - R.x(o)[(q - 1 + e) * NR + k2]) + wr * (xc0 - R.x(o)[(q + e) * NR + k2]) +
-               wb * (xc0 - R.x(o)[(q - HX) * NR + k2]) + wt * (xc0 - R.x(o)[(q + HX) * NR + k2]);
-        res[k2] = R.b(c)[q * NR + k2] - ax;
-    }
-}
-
-// load b (and x = xin + prolongated coarse x when x != null), D, wl, wb of the region and the
-// reciprocal of every cell's full diagonal (its right and upper face weights read from global
-// memory too); cells outside the domain get D = 1, zero weights, b = x = 0.  Thread (k, seg)
-// loads region columns 2k, 2k + 1 of its rows.
-template <typename T, int NR, int H>
-__device__ inline void region_load(Region<T, NR, H>& R, int p0, const Lev<T>& L, const T* __restrict__ b,
-                                   const T* __restrict__ x, const T* __restrict__ xc, int cnx, int gx0, int gy0) {
-    using Rg = Region<T, NR, H>;
-    constexpr int HX = Rg::HX, SY = Rg::SY, NSEG = TileShape<H>::NSEG, RPS = SY / NSEG;
-    int t = threadIdx.x;
-    if (t < HX * NSEG) {
-        int k = t % HX, ry0 = (t / HX) * RPS;
+    for (int r = 0; r < 2; ++r) {
+        int ry = ry0 + r;
 #pragma unroll
-        for (int r = 0; r < RPS; ++r) {
-            int ry = ry0 + r;
-            int gj = gy0 + ry;
-            bool jin = gj >= 0 && gj < L.ny;
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                int rx = 2 * k + e;
-                int gi = gx0 + rx;
-                bool in = jin && gi >= 0 && gi < L.nx;
-                int c = (p0 + rx + ry) & 1;
-                int q = ry * HX + k;
-                // loads are unconditional (clamped to the domain, then masked) so that all of a
-                // thread's loads can be in flight at once
-                int gic = min(max(gi, 0), L.nx - 1), gjc = min(max(gj, 0), L.ny - 1);
-                int g = gjc * L.nx + gic;
-                Vec<T, NR> bv = reinterpret_cast<const Vec<T, NR>*>(b)[g], xv;
-                T dv = L.diag[g], wlv = L.wl[g], wbv = L.wb[g];
-                T wrv = L.wl[gic + 1 < L.nx ? g + 1 : g], wtv = L.wb[gjc + 1 < L.ny ? g + L.nx : g];
-                if (gi + 1 >= L.nx) wrv = T(0);
-                if (gj + 1 >= L.ny) wtv = T(0);
-                if (x) {
-                    xv = reinterpret_cast<const Vec<T, NR>*>(x)[g];
-                    Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gjc >> 1) * cnx + (gic >> 1)];
-#pragma unroll
-                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] += cv.v[k2];
-                } else {
-#pragma unroll
-                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
-                }
-                if (!in) {
-#pragma unroll
-                    for (int k2 = 0; k2 < NR; ++k2) { bv.v[k2] = T(0); xv.v[k2] = T(0); }
-                    dv = T(1); wlv = wbv = wrv = wtv = T(0);
-                }
-                T* xb = R.x(c);
-                T* bb = R.b(c);
-#pragma unroll
-                for (int k2 = 0; k2 < NR; ++k2) { bb[q * NR + k2] = bv.v[k2]; xb[q * NR + k2] = xv.v[k2]; }
-                R.d(c)[q] = dv;
-                R.wl(c)[q] = wlv;
-                R.wb(c)[q] = wbv;
-                R.id(c)[q] = T(1) / (dv + wlv + wrv + wbv + wtv);
-            }
+        for (int c = 0; c < 2; ++c) {
+            int rx = 2 * k + (c ^ C.sw[r]);
+            int gi = gx0 + rx, gj = gy0 + ry;
+            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY && gi < L.nx && gj < L.ny)
+                f(r, c, rx, ry, ry * HX + k, gi, gj);
         }
     }
-    __syncthreads();
-}
-
-// write the tile core's x (natural order, coalesced)
-template <typename T, int NR, int H>
-__device__ inline double2 region_store_core(const Region<T, NR, H>& R, int p0, const Lev<T>& L, int gx0, int gy0,
-                                            T* __restrict__ x, bool dot) {
-    double acc[2] = {0.0, 0.0};
-    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
-        int rx = H + k % TX, ry = H + k / TX;
-        int gi = gx0 + rx, gj = gy0 + ry;
-        if (gi >= L.nx || gj >= L.ny) continue;
-        int c;
-        int q = region_slot<T, NR, H>(p0, rx, ry, c);
-        Vec<T, NR> xv;
-#pragma unroll
-        for (int k2 = 0; k2 < NR; ++k2) {
-            xv.v[k2] = R.x(c)[q * NR + k2];
-            if (dot) acc[k2] += (double)xv.v[k2] * (double)R.b(c)[q * NR + k2];
-        }
-        reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
-    }
-    return make_double2(acc[0], acc[1]);
 }
 
 // k_pre: x = S^nu(0; b) on the tile (red-black order), coarse b = R (b - A x)
 template <typename T, int NR>
-__global__ void __launch_bounds__(tile_block<2 * NU + 1>()) k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x,
-                                              T* __restrict__ bc, const SolveState* __restrict__ st, KTimer* tm) {
+__global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>()) k_pre(Lev<T> L, const T* __restrict__ b,
+                                                                  T* __restrict__ x, T* __restrict__ bc,
+                                                                  const SolveState* __restrict__ st, KTimer* tm) {
     if (skip(st)) return;
     constexpr int H = 2 * NU + 1;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
+    constexpr int HX = Rg::HX;
     extern __shared__ __align__(16) unsigned char smem[];
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
     int p0 = (gx0 + gy0) & 1;
-    region_load<T, NR, H>(R, p0, L, b, nullptr, nullptr, 0, gx0, gy0);
-    region_sweep<T, NR, H, 1>(R, p0, 0);
-    region_sweep<T, NR, H, 2>(R, p0, 1);
-    region_sweep<T, NR, H, 3>(R, p0, 0);
-    region_sweep<T, NR, H, 4>(R, p0, 1);
-    region_store_core<T, NR, H>(R, p0, L, gx0, gy0, x, false);
-    // residual of the tile, restricted (sum of four children)
+    bool act = threadIdx.x < Rg::THREADS;
+    int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    Cells<T, NR> C;
+    if (act) tile_load<T, NR, H>(R, C, p0, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0);
+    __syncthreads();
+    tile_sweep<T, NR, H, 1, 0>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 2, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 3, 0>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 4, 1>(R, C, k, ry0, act);
+    // x of the core cells to global memory, their residuals to shared memory
+    T* res = R.res();
+    if (act)
+        tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
+            const T* xo = R.x(1 - c);
+            const T* xm = R.x(c);
+            int e = rx & 1;
+            Vec<T, NR> xv;
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                T x0v = xm[q * NR + k2];
+                xv.v[k2] = x0v;
+                T ax = C.d[r][c] * x0v + C.wl[r][c] * (x0v - xo[(q - 1 + e) * NR + k2]) +
+                       C.wr[r][c] * (x0v - xo[(q + e) * NR + k2]) + C.wb[r][c] * (x0v - xo[(q - HX) * NR + k2]) +
+                       C.wt[r][c] * (x0v - xo[(q + HX) * NR + k2]);
+                res[((ry - H) * TX + (rx - H)) * NR + k2] = C.b[r][c][k2] - ax;
+            }
+            reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
+        });
+    __syncthreads();
+    // restriction: sum of the four children
     int cnx = L.nx / 2, cny = L.ny / 2;
-    for (int k = threadIdx.x; k < (TX / 2) * (TY / 2); k += blockDim.x) {
-        int ci = blockIdx.x * (TX / 2) + k % (TX / 2), cj = blockIdx.y * (TY / 2) + k / (TX / 2);
+    for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += blockDim.x) {
+        int ti = t % (TX / 2), tj = t / (TX / 2);
+        int ci = blockIdx.x * (TX / 2) + ti, cj = blockIdx.y * (TY / 2) + tj;
         if (ci >= cnx || cj >= cny) continue;
+        // the core starts at an even global index, so children (2ti + a, 2tj + b) are core cells
         Vec<T, NR> acc;
 #pragma unroll
-        for (int k2 = 0; k2 < NR; ++k2) acc.v[k2] = T(0);
-        for (int d2 = 0; d2 < 4; ++d2) {
-            int gi = 2 * ci + (d2 & 1), gj = 2 * cj + (d2 >> 1);
-            T res[NR];
-            region_residual<T, NR, H>(R, p0, gi - gx0, gj - gy0, res);
-#pragma unroll
-            for (int k2 = 0; k2 < NR; ++k2) acc.v[k2] += res[k2];
-        }
+        for (int k2 = 0; k2 < NR; ++k2)
+            acc.v[k2] = res[((2 * tj) * TX + 2 * ti) * NR + k2] + res[((2 * tj) * TX + 2 * ti + 1) * NR + k2] +
+                        res[((2 * tj + 1) * TX + 2 * ti) * NR + k2] + res[((2 * tj + 1) * TX + 2 * ti + 1) * NR + k2];
         reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
     }
     // algorithmic bytes: b, diag, wl, wb read; x and the quarter-size coarse b written
@@ -416,25 +412,41 @@ __global__ void __launch_bounds__(tile_block<2 * NU + 1>()) k_pre(Lev<T> L, cons
 
 // k_post: x = xin + P xc, then black-red sweeps; at the finest level also r.z -> beta
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(tile_block<2 * NU>()) k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin,
-                                               T* __restrict__ x, const T* __restrict__ xc, SolveState* st,
-                                               double* partial, unsigned* ticket, KTimer* tm) {
+__global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>()) k_post(Lev<T> L, const T* __restrict__ b,
+                                                               const T* __restrict__ xin, T* __restrict__ x,
+                                                               const T* __restrict__ xc, SolveState* st,
+                                                               double* partial, unsigned* ticket, KTimer* tm) {
     if (skip(st)) return;
     constexpr int H = 2 * NU;
     using Rg = Region<T, NR, H>;
+    constexpr int HX = Rg::HX;
     extern __shared__ __align__(16) unsigned char smem[];
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
     int p0 = (gx0 + gy0) & 1;
-    region_load<T, NR, H>(R, p0, L, b, xin, xc, L.nx / 2, gx0, gy0);
-    region_sweep<T, NR, H, 1>(R, p0, 1);
-    region_sweep<T, NR, H, 2>(R, p0, 0);
-    region_sweep<T, NR, H, 3>(R, p0, 1);
-    region_sweep<T, NR, H, 4>(R, p0, 0);
-    double2 dd = region_store_core<T, NR, H>(R, p0, L, gx0, gy0, x, DOT);
+    bool act = threadIdx.x < Rg::THREADS;
+    int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    Cells<T, NR> C;
+    if (act) tile_load<T, NR, H>(R, C, p0, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0);
+    __syncthreads();
+    tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 4, 0>(R, C, k, ry0, act);
+    double dot[2] = {0.0, 0.0};
+    if (act)
+        tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
+            const T* xm = R.x(c);
+            Vec<T, NR> xv;
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                xv.v[k2] = xm[q * NR + k2];
+                if (DOT) dot[k2] += (double)xv.v[k2] * (double)C.b[r][c][k2];
+            }
+            reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
+        });
     if (DOT) {
-        double dot[2] = {dd.x, dd.y};
         double tot[NR];
         if (grid_reduce<NR>(dot, partial, ticket, tot)) {
 #pragma unroll

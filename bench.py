@@ -29,6 +29,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the batched workload replays its instances on 32 worker streams: give each its own hardware
+# queue (read when the CUDA context is created, so before torch initialises CUDA)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np
 
@@ -39,6 +42,7 @@ WORKLOADS = {
     # profiling case: the 4096x4096 film's cell size and physics on half its width (16 modes),
     # small enough for multi-pass ncu captures while its smoother operands exceed L2
     "c5_film_half_2048x4096": dict(kind="c5h", desc="multi-mode 2D film boiling, 2048x4096 half-width strip"),
+    "c4_batch_4096": dict(kind="c4", desc="4096 independent Stefan / bubble-growth instances, sides 32..256"),
 }
 METRIC = "cell-steps/s at 1 GPU, FP32+refine vs FP64, 1e-8 rel residual; %HBM roofline"
 
@@ -51,16 +55,22 @@ SMOOTH_L0_TRAFFIC = {
 }
 
 
-def make_problem(name):
+BATCH_COUNT = None   # --batch-count
+
+
+def make_problems(name, count=None):
+    """The workload's instances (one for every workload but the batched one)."""
     from paper_2402_13677_gb300 import workloads as w
     kind = WORKLOADS[name]["kind"]
+    if kind == "c4":
+        return w.c4_batch(count if count is not None else (BATCH_COUNT or 4096))
     if kind == "c2":
-        return w.c2_bubble(steps=0)
+        return [w.c2_bubble(steps=0)]
     if kind == "c3":
-        return w.c3_film(steps=0)
+        return [w.c3_film(steps=0)]
     if kind == "c5h":
-        return w.c5_film_half(steps=0)
-    return w.c5_film(steps=0)
+        return [w.c5_film_half(steps=0)]
+    return [w.c5_film(steps=0)]
 
 
 # ------------------------------------------------------------------ clocks sampling
@@ -105,19 +115,28 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)
 def oracle_rate(name, budget_s=20.0, max_steps=3):
-    """Time the oracle (as it stands) on a bounded sample of the workload: prepare once, then
-    whole steps until the CPU budget is used.  Returns (cell-steps/s, steps, seconds, threads)."""
+    """Time the oracle (as it stands) on a bounded sample of the workload: whole steps of its
+    first instance(s), prepared once each, until the CPU budget is used.  Returns (cell-steps/s,
+    cell-steps done, seconds, description of the sample)."""
     from oracle import step as S
-    pb = make_problem(name)
-    st = S.prepare(pb)
-    steps, t0 = 0, time.perf_counter()
-    while steps < max_steps:
-        S.step(st)
-        steps += 1
-        if time.perf_counter() - t0 > budget_s:
+    pbs = make_problems(name, count=64) if WORKLOADS[name]["kind"] == "c4" else make_problems(name)
+    done, secs, steps, inst = 0, 0.0, 0, 0
+    for pb in pbs:
+        st = S.prepare(pb)
+        inst += 1
+        for _ in range(max_steps):
+            t0 = time.perf_counter()
+            S.step(st)
+            secs += time.perf_counter() - t0
+            done += pb.nx * pb.ny
+            steps += 1
+            if secs > budget_s:
+                break
+        if secs > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return pb.nx * pb.ny * steps / dt, steps, dt
+    what = (f"{steps} whole oracle steps of {name}" if inst == 1 else
+            f"{steps} whole oracle steps over its first {inst} instances")
+    return done / secs, done, secs, what
 
 
 def reference_arm(args):
@@ -126,24 +145,30 @@ def reference_arm(args):
         return 0
     # each timed step is one whole oracle step of the workload; the run stops early (and says
     # so in the sample) once the CPU budget is spent, so it ends within a few minutes
-    total_steps, total_s = 0, 0.0
+    total_steps, total_s, done = 0, 0.0, 0
     from oracle import step as S
-    pb = make_problem(args.workload)
-    cells = pb.nx * pb.ny
-    st = S.prepare(pb)
+    pbs = make_problems(args.workload)
+    cells = sum(pb.nx * pb.ny for pb in pbs)
+    sts = [S.prepare(pb) for pb in pbs[:1]]
     for k in range(args.steps):
+        # one timed step = one whole oracle step of the next instance of the sample
+        b = k % len(pbs)
+        if b >= len(sts):
+            sts.append(S.prepare(pbs[b]))
         t0 = time.perf_counter()
-        S.step(st)
+        S.step(sts[b])
         total_s += time.perf_counter() - t0
+        done += pbs[b].nx * pbs[b].ny
         total_steps += 1
         if total_s > args.reference_budget:
             break
-    value = cells * total_steps / total_s
+    value = done / total_s
     cores = _cores_used()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / total_steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "cells": cells, "solver": "sparse direct (SuperLU)"},
+            "config": {"workload": args.workload, "cells": cells, "instances": len(pbs),
+                       "instances_sampled": len(sts), "solver": "sparse direct (SuperLU)"},
             "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{total_steps} of {args.steps} whole oracle steps of {args.workload} "
                                        f"from its initial state ({total_s:.1f} s)"},
@@ -197,21 +222,22 @@ def run_ours(args):
         G.build()
     E.load()
 
-    pb = make_problem(args.workload)
-    cells = pb.nx * pb.ny
+    pbs = make_problems(args.workload)
+    cells = sum(pb.nx * pb.ny for pb in pbs)
     stream = torch.cuda.Stream()          # non-default stream: each step is replayed as a CUDA graph
     alloc = E.TorchAllocator()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
     def new_ctx(precision):
-        ctx = E.ebit_init([E.config_from_problem(pb, precision, args.rtol, args.max_iter)], stream.cuda_stream,
-                          alloc)
+        ctx = E.ebit_init([E.config_from_problem(pb, precision, args.rtol, args.max_iter) for pb in pbs],
+                          stream.cuda_stream, alloc)
         if args.no_graph:
             E.ebit_set_option(ctx, E.EBIT_OPT_GRAPH, 0)
-        E.upload_state(ctx, 0, pb, pb.vcol, np.where(pb.hx_cut > 0, pb.hx_pos, 0.0),
-                       np.where(pb.vy_cut > 0, pb.vy_pos, 0.0),
-                       {"T_l": pb.T_l, "T_v": pb.T_v, "u_l": pb.u_l, "u_v": pb.u_v, "ufx_l": pb.ufx_l,
-                        "ufx_v": pb.ufx_v, "ufy_l": pb.ufy_l, "ufy_v": pb.ufy_v, "p": pb.p}, pb.t0)
+        for b, pb in enumerate(pbs):
+            E.upload_state(ctx, b, pb, pb.vcol, np.where(pb.hx_cut > 0, pb.hx_pos, 0.0),
+                           np.where(pb.vy_cut > 0, pb.vy_pos, 0.0),
+                           {"T_l": pb.T_l, "T_v": pb.T_v, "u_l": pb.u_l, "u_v": pb.u_v, "ufx_l": pb.ufx_l,
+                            "ufx_v": pb.ufx_v, "ufy_l": pb.ufy_l, "ufy_v": pb.ufy_v, "p": pb.p}, pb.t0)
         E.ebit_run_stage(ctx, E.STAGE_PREPARE)
         return ctx
 
@@ -263,8 +289,9 @@ def run_ours(args):
             d = E.ebit_get_diagnostics(ctx, 0)
             results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist())
             if not args.profile_only and rank == 0:
-                results[name]["final"] = E.download(ctx, 0, pb.nx, pb.ny, ["T_l", "T_v", "p", "u_l", "u_v", "vcol",
-                                                                           "hx_pos", "vy_pos"])
+                results[name]["final"] = [E.download(ctx, b, pbs[b].nx, pbs[b].ny,
+                                                     ["T_l", "T_v", "p", "u_l", "u_v", "vcol", "hx_pos", "vy_pos"])
+                                          for b in range(min(len(pbs), 16))]
         finally:
             E.ebit_destroy(ctx)
     if args.profile_only:
@@ -279,7 +306,10 @@ def run_ours(args):
     # the new state and the diagnostics back with ebit_get_field / ebit_get_diagnostics;
     # wall-clock time of the whole sequence
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and len(pbs) > 64:
+        e2e = {"value": None, "skipped": "batched workload: per-instance host buffers for every field of "
+                                         f"{len(pbs)} instances are not staged; run a single-instance workload"}
+    elif not args.no_e2e:
         ctx = new_ctx(E.EBIT_MIXED)
         try:
             for _ in range(args.warmup):
@@ -288,32 +318,35 @@ def run_ours(args):
                    "ufx_v": E.F_UFX_V, "ufy_l": E.F_UFY_L, "ufy_v": E.F_UFY_V, "p": E.F_P, "gc": E.F_GC,
                    "mdot": E.F_MDOT, "vcol": E.F_VCOL, "hx_pos": E.F_HX_POS, "vy_pos": E.F_VY_POS}
             lib = E.load()
-            host = {}
-            for n, f in ids.items():
-                cnt, eb = E.ebit_field_shape(ctx, 0, f)
-                host[n] = torch.empty(cnt * eb, dtype=torch.uint8, pin_memory=True)
-                lib.ebit_get_field(ctx, 0, f, host[n].data_ptr(), 0)
-            h2d = sum(h.numel() for h in host.values())
+            host = [{} for _ in pbs]
+            for b in range(len(pbs)):
+                for n, f in ids.items():
+                    cnt, eb = E.ebit_field_shape(ctx, b, f)
+                    host[b][n] = torch.empty(cnt * eb, dtype=torch.uint8, pin_memory=True)
+                    lib.ebit_get_field(ctx, b, f, host[b][n].data_ptr(), 0)
+            h2d = sum(h.numel() for hb in host for h in hb.values())
             diag = np.zeros(12)
             total = 0.0
             for _ in range(args.steps):
                 flush.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                lib.ebit_set_interface(ctx, 0, host["vcol"].data_ptr(), host["hx_pos"].data_ptr(),
-                                       host["vy_pos"].data_ptr(), 0)
-                for n, f in ids.items():
-                    if n not in ("vcol", "hx_pos", "vy_pos"):
-                        lib.ebit_set_field(ctx, 0, f, host[n].data_ptr(), 0)
+                for b in range(len(pbs)):
+                    lib.ebit_set_interface(ctx, b, host[b]["vcol"].data_ptr(), host[b]["hx_pos"].data_ptr(),
+                                           host[b]["vy_pos"].data_ptr(), 0)
+                    for n, f in ids.items():
+                        if n not in ("vcol", "hx_pos", "vy_pos"):
+                            lib.ebit_set_field(ctx, b, f, host[b][n].data_ptr(), 0)
                 E.ebit_run_stage(ctx, E.STAGE_RECONSTRUCT)
                 E.ebit_step(ctx, 1, allow_noconv=True)
-                for n, f in ids.items():
-                    lib.ebit_get_field(ctx, 0, f, host[n].data_ptr(), 0)
-                diag = E.ebit_get_diagnostics(ctx, 0)
+                for b in range(len(pbs)):
+                    for n, f in ids.items():
+                        lib.ebit_get_field(ctx, b, f, host[b][n].data_ptr(), 0)
+                    diag = E.ebit_get_diagnostics(ctx, b)
                 total += time.perf_counter() - t0
             total = barrier_max(total)
             e2e = {"value": world * cells * args.steps / total, "unit": "cell-steps/s",
-                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d + 8 * len(diag),
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d + 8 * len(diag) * len(pbs),
                    "timing": "wall clock per step, host buffers in and out through the C ABI"}
         finally:
             E.ebit_destroy(ctx)
@@ -335,32 +368,35 @@ def run_ours(args):
     # same initial state: max difference over a field group relative to the group's scale
     # (temperatures: max |T| over both phases; velocities: max |u| over both phase fields;
     # pressure: max(|p|, rho_l u_max^2), p being defined by its outflow reference)
-    fm, fd = mixed["final"], fp64["final"]
-    t_scale = max(float(np.max(np.abs(fd["T_l"]))), float(np.max(np.abs(fd["T_v"]))), 1e-300)
-    u_scale = max(float(np.max(np.abs(fd["u_l"]))), float(np.max(np.abs(fd["u_v"]))), 1e-300)
-    p_scale = max(float(np.max(np.abs(fd["p"]))), pb.rho_l * u_scale ** 2, 1e-300)
-    scale = {"T_l": t_scale, "T_v": t_scale, "u_l": u_scale, "u_v": u_scale, "p": p_scale}
-
-    def rel(k):
-        return float(np.max(np.abs(fm[k] - fd[k]))) / scale[k]
-
-    mixed_err = {"steps": args.warmup + args.steps, **{k: rel(k) for k in ("T_l", "T_v", "p", "u_l", "u_v")},
-                 "vertex_colours_differing": int(np.sum(fm["vcol"] != fd["vcol"])),
-                 "marker_max_abs_diff": float(max(np.max(np.abs(fm["hx_pos"] - fd["hx_pos"])),
-                                                  np.max(np.abs(fm["vy_pos"] - fd["vy_pos"])))),
+    errs = []
+    for b, (fm, fd) in enumerate(zip(mixed["final"], fp64["final"])):
+        t_scale = max(float(np.max(np.abs(fd["T_l"]))), float(np.max(np.abs(fd["T_v"]))), 1e-300)
+        u_scale = max(float(np.max(np.abs(fd["u_l"]))), float(np.max(np.abs(fd["u_v"]))), 1e-300)
+        p_scale = max(float(np.max(np.abs(fd["p"]))), pbs[b].rho_l * u_scale ** 2, 1e-300)
+        scale = {"T_l": t_scale, "T_v": t_scale, "u_l": u_scale, "u_v": u_scale, "p": p_scale}
+        e = {k: float(np.max(np.abs(fm[k] - fd[k]))) / scale[k] for k in ("T_l", "T_v", "p", "u_l", "u_v")}
+        e["vcol"] = int(np.sum(fm["vcol"] != fd["vcol"]))
+        e["markers"] = float(max(np.max(np.abs(fm["hx_pos"] - fd["hx_pos"])),
+                                 np.max(np.abs(fm["vy_pos"] - fd["vy_pos"]))))
+        errs.append(e)
+    mixed_err = {"steps": args.warmup + args.steps, "instances_compared": len(errs),
+                 **{k: max(e[k] for e in errs) for k in ("T_l", "T_v", "p", "u_l", "u_v")},
+                 "vertex_colours_differing": sum(e["vcol"] for e in errs),
+                 "marker_max_abs_diff": max(e["markers"] for e in errs),
                  "scales": "T: max|T| both phases; u: max|u| both fields; p: max(|p|, rho_l u_max^2)"}
     tr = SMOOTH_L0_TRAFFIC.get(args.workload)
     traffic = tr["dram_bytes_per_launch"] if tr else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        r, n, s = oracle_rate(args.workload, budget_s=args.cpu_budget)
+        r, n, secs, what = oracle_rate(args.workload, budget_s=args.cpu_budget)
         cpu = {"value": r, "unit": "cell-steps/s", "cores": _cores_used(), "kind": "oracle",
-               "sample": f"{n} whole oracle steps of {args.workload} from its initial state ({s:.1f} s)"}
+               "sample": f"{what} from the initial state ({n} cell-steps, {secs:.1f} s)"}
     line = {
         "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * mixed["secs"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64-refine", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": cells, "grid": [pb.nx, pb.ny], "rtol": args.rtol,
+        "config": {"workload": args.workload, "cells": cells, "instances": len(pbs),
+                   "grid": [pbs[0].nx, pbs[0].ny] if len(pbs) == 1 else "sides 32..256", "rtol": args.rtol,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp64": {"value": value64, "unit": "cell-steps/s", "ms_per_step": 1e3 * fp64["secs"] / args.steps,
@@ -392,6 +428,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_bubble_512", choices=list(WORKLOADS))
+    ap.add_argument("--batch-count", type=int, default=None,
+                    help="instances of the batched workload (default 4096; fewer only for quick checks)")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=400)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
@@ -401,6 +439,8 @@ def main():
     ap.add_argument("--profile-only", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels from the host (profilers)")
     args = ap.parse_args()
+    global BATCH_COUNT
+    BATCH_COUNT = args.batch_count
     if args.impl == "reference":
         return reference_arm(args)
     return run_ours(args)

@@ -63,6 +63,13 @@ struct Instance {
 struct ebit_ctx {
     std::vector<Instance> inst;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   // capture streams of the solvers' loop bodies
+    // batched steps: instance b replays its step graph on workers[b % workers.size()], between a
+    // fork event recorded on the context stream and the workers' join events
+    std::vector<cudaStream_t> workers;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    int* host_status = nullptr;   // pinned, one status word per instance
     ebit_allocator alloc{};
     bool has_alloc = false;
     SolveState* host_states = nullptr;   // pinned, Solver::NSLOT per instance
@@ -149,7 +156,7 @@ static size_t layout(Instance& I, char* base, F&& assign) {
     };
     assign(I, take, N, nv, nh, nve);
     char* sb = take(Solver::bytes(g.nx, g.ny));
-    if (base) I.solver.bind(sb, g.nx, g.ny);
+    if (base) I.solver.bind(sb, g.nx, g.ny, false);   // capture streams come from the context
     return off;
 }
 
@@ -268,8 +275,9 @@ static void do_solve(Instance& I, int slot, const double* b, double* x, int nr, 
     count((int)(I.solver.launches - l0));
 }
 
-// solver statistics of the last step, read from the device slots (synchronises)
-static void collect_stats(Instance& I, cudaStream_t st, bool graph_step) {
+// solver statistics of the last step from the host copy of the solver slots (fetched by
+// check_status before its synchronisation)
+static void collect_stats(Instance& I, bool graph_step) {
     unsigned m = I.solved;
     I.solved = 0;
     if (!m) return;
@@ -278,7 +286,7 @@ static void collect_stats(Instance& I, cudaStream_t st, bool graph_step) {
     long long body = I.solver.body_size(I.cfg.precision), n = 0;
     for (int k = 0; k < 4; ++k) {
         if (!(m & (1u << k))) continue;
-        r[k] = I.solver.read_result(k, I.cfg.precision, st);
+        r[k] = I.solver.result_from_host(k, I.cfg.precision);
         ok = ok && r[k].converged;
         // kernels executed inside the conditional loop bodies of a graph step
         n += r[k].iters * body;
@@ -382,21 +390,30 @@ static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
     return cuda_check(ctx, "run_stage");
 }
 
+// status and solver statistics of every instance: all read-backs are queued on the context
+// stream, then one synchronisation
 static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
-    for (auto& I : ctx->inst) {
-        collect_stats(I, ctx->stream, graph_step);
-        int s = 0;
-        cudaMemcpyAsync(&s, I.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-        cudaError_t e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(e));
-        if (s & 1) return fail(ctx, EBIT_ECFL, "a marker moved one cell or more in one sweep (reduce dt)");
-        if (s & 2) return fail(ctx, EBIT_ETOPO, "too many marker candidates on one edge");
+    for (size_t b = 0; b < ctx->inst.size(); ++b) {
+        Instance& I = ctx->inst[b];
+        if (I.solved) I.solver.fetch_states(ctx->stream);
+        cudaMemcpyAsync(ctx->host_status + b, I.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(e));
+    ebit_status worst = EBIT_OK;
+    for (size_t b = 0; b < ctx->inst.size(); ++b) {
+        Instance& I = ctx->inst[b];
+        collect_stats(I, graph_step);
+        int s = ctx->host_status[b];
+        std::string where = ctx->inst.size() > 1 ? " (instance " + std::to_string(b) + ")" : "";
+        if (s & 1) return fail(ctx, EBIT_ECFL, "a marker moved one cell or more in one sweep (reduce dt)" + where);
+        if (s & 2) return fail(ctx, EBIT_ETOPO, "too many marker candidates on one edge" + where);
         if (I.noconv) {
             I.noconv = false;
-            return fail(ctx, EBIT_ENOCONV, "a linear solve hit max_iter");
+            worst = fail(ctx, EBIT_ENOCONV, "a linear solve hit max_iter" + where);
         }
     }
-    return EBIT_OK;
+    return worst;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -440,11 +457,16 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         layout(I, (char*)mem, assign_ptrs);
         cudaMemsetAsync(mem, 0, bytes, ctx->stream);
     }
-    if (cudaMallocHost(&ctx->host_states, batch * Solver::NSLOT * sizeof(SolveState)) != cudaSuccess) {
+    if (cudaMallocHost(&ctx->host_states, batch * Solver::NSLOT * sizeof(SolveState)) != cudaSuccess ||
+        cudaMallocHost(&ctx->host_status, batch * sizeof(int)) != cudaSuccess) {
         ebit_destroy(ctx);
         return EBIT_ENOMEM;
     }
-    for (int b = 0; b < batch; ++b) ctx->inst[b].solver.st_host = ctx->host_states + b * Solver::NSLOT;
+    for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking);
+    for (int b = 0; b < batch; ++b) {
+        ctx->inst[b].solver.st_host = ctx->host_states + b * Solver::NSLOT;
+        for (int k = 0; k < 3; ++k) ctx->inst[b].solver.aux[k] = ctx->aux[k];
+    }
     ctx->launch0 = g_launches.load();
     ebit_status s = cuda_check(ctx, "ebit_init");
     if (s != EBIT_OK) { ebit_destroy(ctx); return s; }
@@ -587,8 +609,7 @@ static ebit_status step_eager(ebit_ctx* ctx, Instance& I) {
 
 // capture one whole step (stages ADVECT_T .. DIAGNOSTICS) into a graph; the solver loops
 // become conditional WHILE nodes, so replaying the graph needs no host round trip
-static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaGraphExec_t* out) {
-    cudaStream_t st = ctx->stream;
+static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaStream_t st, cudaGraphExec_t* out) {
     if (!st) return fail(ctx, EBIT_EINVAL, "graph mode needs a non-default stream");
     long long nstep = I.nstep;
     uint64_t l0 = g_launches.load();
@@ -623,28 +644,70 @@ static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaGraphExec_t* out
     return EBIT_OK;
 }
 
+// replay (capturing it first if needed) one instance's step graph on stream st
+static ebit_status replay_step(ebit_ctx* ctx, Instance& I, cudaStream_t st) {
+    int par = (I.cfg.sweep_order == 0) ? 0 : (int)(I.nstep & 1);
+    if (!I.graph[par]) {
+        ebit_status r = capture_step(ctx, I, st, &I.graph[par]);
+        if (r != EBIT_OK) return r;
+    }
+    cudaGraphLaunch(I.graph[par], st);
+    g_launches += (uint64_t)I.graph_launches[par];
+    I.solved = (I.p.energy ? 1u : 0u) | 2u | 4u | 8u;
+    I.nstep += 1;
+    return EBIT_OK;
+}
+
+// a batch of instances: up to MAX_WORKERS instances run concurrently, each on a worker stream
+// forked from the context stream and joined back before the status check
+// (a process that sets CUDA_DEVICE_MAX_CONNECTIONS=32 before creating its CUDA context gives
+// each of them its own hardware queue)
+static constexpr int MAX_WORKERS = 32;
+
+static ebit_status ensure_workers(ebit_ctx* ctx) {
+    if (!ctx->workers.empty()) return EBIT_OK;
+    int k = (int)ctx->inst.size() < MAX_WORKERS ? (int)ctx->inst.size() : MAX_WORKERS;
+    ctx->workers.resize(k);
+    ctx->joins.resize(k);
+    for (int w = 0; w < k; ++w) {
+        cudaStreamCreateWithFlags(&ctx->workers[w], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&ctx->joins[w], cudaEventDisableTiming);
+    }
+    cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    return cuda_check(ctx, "worker streams");
+}
+
 ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
     if (!ctx || nsteps < 0) return EBIT_EINVAL;
+    for (auto& I : ctx->inst)
+        if (!I.props_set) return fail(ctx, EBIT_EINVAL, "ebit_set_phase_props not called");
+    bool graph = ctx->use_graph && ctx->stream;
+    bool batched = graph && ctx->inst.size() > 1;
+    if (batched) {
+        ebit_status r = ensure_workers(ctx);
+        if (r != EBIT_OK) return r;
+    }
     ebit_status worst = EBIT_OK;
     for (int n = 0; n < nsteps; ++n) {
-        for (auto& I : ctx->inst) {
-            if (!I.props_set) return fail(ctx, EBIT_EINVAL, "ebit_set_phase_props not called");
-            if (ctx->use_graph && ctx->stream) {
-                int par = (I.cfg.sweep_order == 0) ? 0 : (int)(I.nstep & 1);
-                if (!I.graph[par]) {
-                    ebit_status r = capture_step(ctx, I, &I.graph[par]);
-                    if (r != EBIT_OK) return r;
-                }
-                cudaGraphLaunch(I.graph[par], ctx->stream);
-                g_launches += (uint64_t)I.graph_launches[par];
-                I.solved = (I.p.energy ? 1u : 0u) | 2u | 4u | 8u;
-                I.nstep += 1;
-            } else {
-                ebit_status r = step_eager(ctx, I);
+        if (batched) {
+            int K = (int)ctx->workers.size();
+            cudaEventRecord(ctx->fork, ctx->stream);
+            for (int w = 0; w < K; ++w) cudaStreamWaitEvent(ctx->workers[w], ctx->fork, 0);
+            for (size_t b = 0; b < ctx->inst.size(); ++b) {
+                ebit_status r = replay_step(ctx, ctx->inst[b], ctx->workers[b % K]);
+                if (r != EBIT_OK) return r;
+            }
+            for (int w = 0; w < K; ++w) {
+                cudaEventRecord(ctx->joins[w], ctx->workers[w]);
+                cudaStreamWaitEvent(ctx->stream, ctx->joins[w], 0);
+            }
+        } else {
+            for (auto& I : ctx->inst) {
+                ebit_status r = graph ? replay_step(ctx, I, ctx->stream) : step_eager(ctx, I);
                 if (r != EBIT_OK) return r;
             }
         }
-        ebit_status s = check_status(ctx, ctx->use_graph && ctx->stream);
+        ebit_status s = check_status(ctx, graph);
         if (s == EBIT_ENOCONV) worst = s;
         else if (s != EBIT_OK) return s;
     }
@@ -750,13 +813,16 @@ void ebit_destroy(ebit_ctx* ctx) {
         else cudaFree(I.arena);
         I.arena = nullptr;
     }
-    for (auto& I : ctx->inst) {
+    for (auto& I : ctx->inst)
         for (auto& gx : I.graph)
             if (gx) cudaGraphExecDestroy(gx);
-        for (auto& s : I.solver.aux)
-            if (s) cudaStreamDestroy(s);
-    }
+    for (auto& s : ctx->aux)
+        if (s) cudaStreamDestroy(s);
+    for (auto& s : ctx->workers) cudaStreamDestroy(s);
+    for (auto& e : ctx->joins) cudaEventDestroy(e);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->host_states) cudaFreeHost(ctx->host_states);
+    if (ctx->host_status) cudaFreeHost(ctx->host_status);
     delete ctx;
 }
 

@@ -1363,9 +1363,17 @@ bool Solver::supported(int nx, int ny) {
     return (long long)s.lnx[s.nlev - 1] * s.lny[s.nlev - 1] <= SMALL_MAX_D;
 }
 
+void Solver::fetch_states(cudaStream_t stm) {
+    cudaMemcpyAsync(st_host, st_base, NSLOT * sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
+}
+
 SolveResult Solver::read_result(int sl, int precision, cudaStream_t stm) {
     cudaMemcpyAsync(st_host + sl, st_base + sl, sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
     cudaStreamSynchronize(stm);
+    return result_from_host(sl, precision);
+}
+
+SolveResult Solver::result_from_host(int sl, int precision) const {
     const SolveState& h = st_host[sl];
     SolveResult r{};
     double worst = 0.0;

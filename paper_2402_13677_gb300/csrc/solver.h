@@ -79,6 +79,10 @@ struct Solver {
     void solve(const double* cd, const double* dd, const double* wl, const double* wb, const double* b, double* x,
                int nr, int precision, double rtol, int max_iter, cudaStream_t st);
     SolveResult read_result(int slot, int precision, cudaStream_t st);
+    // batched read-back: queue the copy of every slot's state to st_host (no synchronisation),
+    // then, once the stream has been synchronised, read a slot from the host copy
+    void fetch_states(cudaStream_t st);
+    SolveResult result_from_host(int slot, int precision) const;
     static bool supported(int nx, int ny);
     int body_size(int precision) const;   // kernels of one CG iteration (V-cycle + apply + update)
 };

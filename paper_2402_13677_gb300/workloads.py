@@ -113,7 +113,8 @@ def stefan_temperature(x, t, beta, alpha_v, T_w, T_sat):
 def _bubble2d_logI(eta, a):
     """log of I(eta) = int_eta^inf s^(2a-1) exp(-s^2) ds = Gamma(a) Q(a, eta^2) / 2."""
     q = special.gammaincc(a, eta * eta)
-    return special.gammaln(a) + np.log(q) - math.log(2.0)
+    with np.errstate(divide="ignore"):   # Q underflows to 0 far outside the layer: log -> -inf, I -> 0
+        return special.gammaln(a) + np.log(q) - math.log(2.0)
 
 
 def bubble2d_beta(Ja: float, eps: float) -> float:
@@ -267,6 +268,28 @@ def bubble(n=512, R0=0.05, rho_ratio=20.0, k_ratio=5.0, St=0.2, dT=1.0, mu=0.01,
     return pb
 
 
+def bubble_layer(n=64, R0=0.15, rho_ratio=20.0, St=0.2, dT=1.0, delta=None, mu=0.01, dt=1e-4, steps=100,
+                 **kw) -> Problem:
+    """Circular vapour bubble in liquid superheated by dT, with a linear thermal layer of
+    thickness delta outside the interface and fluid at rest (a synthetic start where the
+    planar similarity solution does not exist); outflow on all sides, lambda = cp = 1."""
+    h = 1.0 / n
+    if delta is None:
+        delta = 2.0 * h
+    pb = Problem("bubble_layer", n, n, h, dt=dt, steps=steps, rho_l=rho_ratio, rho_v=1.0, mu_l=mu, mu_v=mu,
+                 lam_l=1.0, lam_v=1.0, cp_l=1.0, cp_v=1.0, T_sat=0.0, h_lg=1.0 * dT / St,
+                 bc=(OUTFLOW,) * 4, T_bc=(None,) * 4, **kw)
+    pb.meta.update(R0=R0, xc=0.5, yc=0.5, delta=delta)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: np.hypot(x - 0.5, y - 0.5) - R0, n, n, h)
+    (Xc, Yc), _, _ = _grids(n, n, h, 0.0, 0.0)
+    r = np.hypot(Xc - 0.5, Yc - 0.5)
+    pb.T_l = dT * np.clip((r - R0) / delta, 0.0, 1.0)
+    pb.T_v = np.zeros((n, n))
+    _zero_flow(pb)
+    return pb
+
+
 def const_mdot_bubble(n=64, L=8.0, R0=2.0, mdot=0.1, rho_l=1000.0, rho_v=1.0,
                       mu_l=1e-3, mu_v=1.26e-5, dt=None, steps=100, **kw) -> Problem:
     """Bubble with an imposed constant mass flux, energy equation off (Sec. 3.3).
@@ -349,6 +372,53 @@ def c5_film_half(**kw):
     """The 4096x4096 film's cell size and properties on the strip [0,4]x[0,8] (2048x4096, 16 modes)."""
     return film(2048, 4096, Lx=4.0, modes=16, rho_l=50.0, rho_v=1.0, mu_l=1e-2, mu_v=1e-3,
                 lam_l=1e-2, lam_v=1e-3, St=0.1, **kw)
+
+
+C4_SIDES = (32, 48, 64, 96, 128, 192, 256)
+
+
+def c4_instance(k, seed=0):
+    """Instance k of the batched workload: side from C4_SIDES, Stefan or bubble with p = 1/2,
+    St ~ U[0.05, 0.5], rho_l / rho_v ~ U[2, 100], lambda = cp = 1 in both phases, dt from a CFL
+    number of 0.2 on the closed-form interface (or liquid) speed at the start.  Bubbles start at
+    R0 = 0.15 (at least 4.8 cells on the 32^2 grids), Stefan fronts at X0 = 0.1."""
+    rng = np.random.default_rng([seed, k])
+    n = int(rng.choice(C4_SIDES))
+    kind = "stefan" if rng.random() < 0.5 else "bubble"
+    St = float(rng.uniform(0.05, 0.5))
+    ratio = float(rng.uniform(2.0, 100.0))
+    h = 1.0 / n
+    if kind == "stefan":
+        beta = stefan_beta(St)
+        t0 = (0.1 / (2 * beta)) ** 2      # alpha_v = 1
+        speed = beta * math.sqrt(1.0 / t0)
+        dt = 0.2 * h / speed
+        pb = stefan(n, n, X0=0.1, rho_l=ratio, rho_v=1.0, St=St, dt=dt, steps=200)
+    else:
+        eps = 1.0 - 1.0 / ratio
+        R0 = 0.15
+        try:
+            with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+                beta = bubble2d_beta(ratio * St, eps)
+        except ValueError:
+            beta = None   # Ja = ratio St beyond the planar similarity solution's range
+        if beta is not None:
+            alpha_l = 1.0 / ratio
+            t0 = (R0 / (2 * beta)) ** 2 / alpha_l
+            speed = beta * math.sqrt(alpha_l / t0)
+            dt = 0.2 * h / speed
+            pb = bubble(n, R0=R0, rho_ratio=ratio, k_ratio=1.0, St=St, dt=dt, steps=200, seed=0)
+        else:
+            delta = 2.0 * h
+            speed = St / delta      # interface speed of a linear layer: lambda dT / (delta h_lg rho_v)
+            pb = bubble_layer(n, R0=R0, rho_ratio=ratio, St=St, delta=delta, dt=0.2 * h / speed, steps=200)
+    pb.meta.update(c4_index=k, c4_kind=kind, c4_St=St, c4_ratio=ratio)
+    return pb
+
+
+def c4_batch(count=4096, seed=0):
+    """The batched workload: `count` independent instances (see c4_instance)."""
+    return [c4_instance(k, seed) for k in range(count)]
 
 
 WORKLOADS = {"c1_stefan": c1_stefan, "c2_bubble": c2_bubble, "c3_film": c3_film, "c5_film": c5_film,

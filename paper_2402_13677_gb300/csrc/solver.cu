@@ -24,7 +24,7 @@
 //     each a shared-memory tile with a halo of recomputed cells, so one launch performs
 //     several Gauss-Seidel half-sweeps; halo cells are recomputed from the same inputs with
 //     the same formula, so the result equals global red-black Gauss-Seidel exactly;
-//   * every level of at most 4096 cells: one single-block kernel (k_small) runs the rest of
+//   * every level of at most 1024 cells: one single-block kernel (k_small) runs the rest of
 //     the V-cycle in shared memory;
 //   * CG: k_apply (p = z + beta p fused into q = A p, p.q) and k_update (x, r, r.r, test).
 // Loop control lives on the device (SolveState); kernels can drive CUDA-graph conditional
@@ -33,7 +33,7 @@
 // Precision modes:
 //   FP64  : CG + V-cycle in double.
 //   MIXED : iterative refinement: r = b - A x in FP64, correction A e = r solved in FP32 by
-//           the same MG-PCG to a relative 1e-4, x += e in FP64, until ||r|| <= rtol ||b||.
+//           the same MG-PCG to a relative 1e-5, x += e in FP64, until ||r|| <= rtol ||b||.
 //
 // Reductions are deterministic: per-block partial sums, the last block adds them in block order.
 #include <cfloat>
@@ -46,11 +46,12 @@ namespace ebit {
 
 constexpr int RB = 256;          // threads of grid-stride kernels
 constexpr int NRED = 608;        // blocks of grid-stride kernels (4 x 152 SMs)
-constexpr int SMALL_MAX_F = 4096; // levels with at most this many cells run inside k_small (FP32)
+constexpr int SMALL_MAX_F = 1024; // levels with at most this many cells run inside k_small (FP32)
 constexpr int SMALL_MAX_D = 1024; // (FP64: half the shared memory per value)
 constexpr int SMALL_THREADS = 1024;
 constexpr int TX = 32, TY = 32;  // tile of the large-level kernels
 constexpr int NU = 2;            // smoothing sweeps (red-black pairs) before and after
+constexpr int NU_SMALL = 2;      // the same on the levels of the single-block kernel
 constexpr int COARSE_PAIRS = 12; // symmetric sweeps on the coarsest grid (at most 16 cells)
 
 template <typename T, int NR>
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
         int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
         for (int c = threadIdx.x; c < nx * ny * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
         __syncthreads();
-        for (int k = 0; k < NU; ++k) {
+        for (int k = 0; k < NU_SMALL; ++k) {
             small_sweep<T, NR>(P, l, M, 0);
             small_sweep<T, NR>(P, l, M, 1);
         }
@@ -646,7 +647,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
                     M.x[(o + j * nx + i) * NR + k] += M.x[(co + (j >> 1) * cnx + (i >> 1)) * NR + k];
             }
         __syncthreads();
-        for (int k = 0; k < NU; ++k) {
+        for (int k = 0; k < NU_SMALL; ++k) {
             small_sweep<T, NR>(P, l, M, 1);
             small_sweep<T, NR>(P, l, M, 0);
         }
@@ -1303,7 +1304,7 @@ static void solve_mixed(Solver& s, const double* b, double* x, double rtol, int 
     int N = s.nx * s.ny;
     Lev<double> L64 = lev<double>(s, 0);
     const int max_outer = 8;
-    const double inner_rtol = 1e-4;
+    const double inner_rtol = 1e-5;
     float* z = s.f_x;
     k_ir_init<NR><<<nblocks(N), RB, 0, stm>>>(N, b, s.st, s.partial, s.tickets + 3, rtol * rtol, inner_rtol, max_iter,
                                               max_outer);

@@ -216,39 +216,47 @@ __device__ inline bool ext_update(uint8_t fl, int mode) {
     return !(fl & F_CUT);
 }
 
-// mode 3 runs modes 0 and 1 in the same sweep (they update disjoint cells of different
-// fields): (f, vcur, vnxt) belong to mode 0 and (f1, vcur1, vnxt1) to mode 1.
+// one Jacobi update of band entry k; mode 3 runs modes 0 and 1 in the same sweep (they update
+// disjoint cells of different fields): (f0, vcur0, vnxt0) belong to mode 0 and (f1, vcur1,
+// vnxt1) to mode 1
+__device__ inline void extend_entry(const Grid& g, int mode, int it, int last, int k, const int* __restrict__ list,
+                                    const uint8_t* __restrict__ flags, const int* __restrict__ idxmap,
+                                    const double2* __restrict__ nb, double* f0, const double* vcur0, double* vnxt0,
+                                    double* f1, const double* vcur1, double* vnxt1) {
+    int c = list[k];
+    uint8_t fl = flags[c];
+    int m = mode == 3 ? ((fl & F_CCOL) ? 1 : 0) : mode;
+    if (!ext_update(fl, m)) return;
+    double* f = m == 1 && mode == 3 ? f1 : f0;
+    const double* vcur = m == 1 && mode == 3 ? vcur1 : vcur0;
+    double* vnxt = m == 1 && mode == 3 ? vnxt1 : vnxt0;
+    int i = c % g.nx, j = c / g.nx;
+    double sgn = m == 0 ? 1.0 : (m == 1 ? -1.0 : ((fl & F_CCOL) ? -1.0 : 1.0));
+    double2 nn = nb[c];
+    double ax = nn.x * sgn, ay = nn.y * sgn;
+    double acc = 0.0, w = 0.0;
+    auto val = [&](int cc) -> double {
+        if (it > 0 && ext_update(flags[cc], m)) return vcur[idxmap[cc]];
+        return f[cc];
+    };
+    if (ax > 0.0 && i - 1 >= 0) { acc += ax * val(c - 1); w += ax; }
+    else if (ax < 0.0 && i + 1 < g.nx) { acc += -ax * val(c + 1); w += -ax; }
+    if (ay > 0.0 && j - 1 >= 0) { acc += ay * val(c - g.nx); w += ay; }
+    else if (ay < 0.0 && j + 1 < g.ny) { acc += -ay * val(c + g.nx); w += -ay; }
+    double nv = w > 0.0 ? acc / w : (it > 0 ? vcur[k] : f[c]);
+    if (last) f[c] = nv;
+    else vnxt[k] = nv;
+}
+
+// one sweep over the band, grid-stride
 __global__ void k_extend(Grid g, int mode, int it, int last, const int* __restrict__ list,
                          const int* __restrict__ count, const uint8_t* __restrict__ flags,
                          const int* __restrict__ idxmap, const double2* __restrict__ nb, double* f0,
                          const double* __restrict__ vcur0, double* __restrict__ vnxt0, double* f1,
                          const double* __restrict__ vcur1, double* __restrict__ vnxt1) {
     int n = *count;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int c = list[k];
-        uint8_t fl = flags[c];
-        int m = mode == 3 ? ((fl & F_CCOL) ? 1 : 0) : mode;
-        if (!ext_update(fl, m)) continue;
-        double* f = m == 1 && mode == 3 ? f1 : f0;
-        const double* vcur = m == 1 && mode == 3 ? vcur1 : vcur0;
-        double* vnxt = m == 1 && mode == 3 ? vnxt1 : vnxt0;
-        int i = c % g.nx, j = c / g.nx;
-        double sgn = m == 0 ? 1.0 : (m == 1 ? -1.0 : ((fl & F_CCOL) ? -1.0 : 1.0));
-        double2 nn = nb[c];
-        double ax = nn.x * sgn, ay = nn.y * sgn;
-        double acc = 0.0, w = 0.0;
-        auto val = [&](int cc) -> double {
-            if (it > 0 && ext_update(flags[cc], m)) return vcur[idxmap[cc]];
-            return f[cc];
-        };
-        if (ax > 0.0 && i - 1 >= 0) { acc += ax * val(c - 1); w += ax; }
-        else if (ax < 0.0 && i + 1 < g.nx) { acc += -ax * val(c + 1); w += -ax; }
-        if (ay > 0.0 && j - 1 >= 0) { acc += ay * val(c - g.nx); w += ay; }
-        else if (ay < 0.0 && j + 1 < g.ny) { acc += -ay * val(c + g.nx); w += -ay; }
-        double nv = w > 0.0 ? acc / w : (it > 0 ? vcur[k] : f[c]);
-        if (last) f[c] = nv;
-        else vnxt[k] = nv;
-    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        extend_entry(g, mode, it, last, k, list, flags, idxmap, nb, f0, vcur0, vnxt0, f1, vcur1, vnxt1);
 }
 
 // energy solution (one value per cell) back to the phase fields: T_k = T where f_C = k, T*_k elsewhere

@@ -145,22 +145,6 @@ __device__ inline void set_cond(cudaGraphConditionalHandle h, int use, unsigned 
 }
 
 // ---- operator setup -------------------------------------------------------------------
-// level 0 in precision T from the FP64 cell-centred operator (diag holds D = cd + dd)
-template <typename T>
-__global__ void k_setup0(int nx, int ny, const double* __restrict__ cd, const double* __restrict__ dd,
-                         const double* __restrict__ wl, const double* __restrict__ wb, T* __restrict__ diag,
-                         T* __restrict__ owl, T* __restrict__ owb, T* __restrict__ ocd, T* __restrict__ odd) {
-    int N = nx * ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        double ddv = dd ? dd[c] : 0.0;
-        diag[c] = (T)(cd[c] + ddv);
-        owl[c] = (T)wl[c];
-        owb[c] = (T)wb[c];
-        ocd[c] = (T)cd[c];
-        odd[c] = (T)ddv;
-    }
-}
-
 template <typename T>
 __device__ inline void coarsen_cell(int fnx, const T* fcd, const T* fdd, const T* fwl, const T* fwb, int nx, int ny,
                                     int I, int J, T* ccd, T* cdd, T* cwl, T* cwb, T* cdiag) {
@@ -176,16 +160,6 @@ __device__ inline void coarsen_cell(int fnx, const T* fcd, const T* fdd, const T
     cwb[c] = wb;
     cdiag[c] = s_cd + s_dd;
     (void)ny;
-}
-
-template <typename T>
-__global__ void k_coarsen(int fnx, int fny, const T* __restrict__ fcd, const T* __restrict__ fdd,
-                          const T* __restrict__ fwl, const T* __restrict__ fwb, T* __restrict__ ccd,
-                          T* __restrict__ cdd, T* __restrict__ cwl, T* __restrict__ cwb, T* __restrict__ cdiag) {
-    int nx = fnx / 2, ny = fny / 2;
-    int N = nx * ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        coarsen_cell(fnx, fcd, fdd, fwl, fwb, nx, ny, c % nx, c / nx, ccd, cdd, cwl, cwb, cdiag);
 }
 
 // ---- large-level kernels: tiles with recomputed halos ------------------------------------
@@ -676,12 +650,12 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
 // coarsest operator, e.g. a pure-Neumann pressure problem) leaves 0 there and the cycle
 // falls back to sweeps.
 template <typename T>
-__global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ diag, const T* __restrict__ wl,
-                                 const T* __restrict__ wb, T* __restrict__ inv) {
+__device__ inline void coarse_inverse_warp(int nx, int ny, const T* __restrict__ diag, const T* __restrict__ wl,
+                                           const T* __restrict__ wb, T* __restrict__ inv) {
     __shared__ T A[32][65];
     __shared__ T col[32];
     int n = nx * ny;
-    int lane = threadIdx.x;
+    int lane = threadIdx.x & 31;
     for (int r = 0; r < n; ++r) {
         A[r][lane] = T(0);
         A[r][lane + 32] = T(0);
@@ -721,6 +695,93 @@ __global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ diag, con
     if (lane == 0) inv[n * n] = ok ? T(1) : T(0);
 }
 
+
+// Levels of the hierarchy as the setup kernel sees them.
+struct SetupPlan {
+    int nlev, nx[Solver::MAXLEV], ny[Solver::MAXLEV];
+    size_t off[Solver::MAXLEV];
+};
+
+// The whole multigrid hierarchy in precision T in one launch.  Block (bx, by) converts its
+// SB x SB cells of level 0 (D = cd + dd, face weights, cd, dd; with d64 != null also D in FP64
+// for the refinement residual) and coarsens its own footprint level by level while a level-l
+// cell still lies inside it (2^l <= SB); the last block to finish builds the remaining levels
+// from the others' results and, when the coarsest level has at most 32 cells, its dense inverse.
+constexpr int SB = 32;
+template <typename T>
+__global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* __restrict__ cd,
+                                                    const double* __restrict__ dd, const double* __restrict__ wl,
+                                                    const double* __restrict__ wb, T* diag, T* owl, T* owb, T* ocd,
+                                                    T* odd, double* __restrict__ d64, T* inv, unsigned* ticket) {
+    int nx = P.nx[0], ny = P.ny[0];
+    for (int k = threadIdx.x; k < SB * SB; k += blockDim.x) {
+        int i = blockIdx.x * SB + k % SB, j = blockIdx.y * SB + k / SB;
+        if (i >= nx || j >= ny) continue;
+        int c = j * nx + i;
+        double ddv = dd ? dd[c] : 0.0;
+        double dg = cd[c] + ddv;
+        diag[c] = (T)dg;
+        owl[c] = (T)wl[c];
+        owb[c] = (T)wb[c];
+        ocd[c] = (T)cd[c];
+        odd[c] = (T)ddv;
+        if (d64) d64[c] = dg;
+    }
+    __syncthreads();   // this block's level-l cells are read back by its own threads below
+    int l = 1;
+    for (; l < P.nlev && (1 << l) <= SB; ++l) {
+        int w = SB >> l;
+        int i0 = blockIdx.x * w, j0 = blockIdx.y * w;
+        size_t fo = P.off[l - 1], co = P.off[l];
+        for (int k = threadIdx.x; k < w * w; k += blockDim.x) {
+            int I = i0 + k % w, J = j0 + k / w;
+            if (I >= P.nx[l] || J >= P.ny[l]) continue;
+            coarsen_cell(P.nx[l - 1], ocd + fo, odd + fo, owl + fo, owb + fo, P.nx[l], P.ny[l], I, J, ocd + co,
+                         odd + co, owl + co, owb + co, diag + co);
+        }
+        __syncthreads();
+    }
+    // the last block: the levels above every block's footprint, then the coarsest inverse
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (; l < P.nlev; ++l) {
+        size_t fo = P.off[l - 1], co = P.off[l];
+        int n = P.nx[l] * P.ny[l];
+        for (int k = threadIdx.x; k < n; k += blockDim.x)
+            coarsen_cell(P.nx[l - 1], ocd + fo, odd + fo, owl + fo, owb + fo, P.nx[l], P.ny[l], k % P.nx[l],
+                         k / P.nx[l], ocd + co, odd + co, owl + co, owb + co, diag + co);
+        __syncthreads();
+    }
+    int lc = P.nlev - 1;
+    if (P.nx[lc] * P.ny[lc] <= 32 && threadIdx.x < 32)
+        coarse_inverse_warp(P.nx[lc], P.ny[lc], diag + P.off[lc], owl + P.off[lc], owb + P.off[lc], inv);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// grid-stride walk over the cells of an nx-wide grid that keeps (i, j) without a division per
+// step
+struct CellWalk {
+    int c, i, j, stride, di, dj, nx;
+    __device__ CellWalk(int nx_) : nx(nx_) {
+        c = blockIdx.x * blockDim.x + threadIdx.x;
+        stride = gridDim.x * blockDim.x;
+        i = c % nx;
+        j = c / nx;
+        di = stride % nx;
+        dj = stride / nx;
+    }
+    __device__ void next() {
+        c += stride;
+        i += di;
+        j += dj;
+        if (i >= nx) { i -= nx; ++j; }
+    }
+};
+
 // ---- CG kernels ---------------------------------------------------------------------------
 // p_new = z + beta p_old; q = A p_new; p.q -> alpha = r.z / p.q
 template <typename T, int NR>
@@ -739,8 +800,8 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % L.nx, j = c / L.nx;
+    for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
+        int c = cw.c, i = cw.i, j = cw.j;
         auto pn = [&](int cc) {
             Vec<T, NR> a = Z[cc], b = Po[cc];
 #pragma unroll
@@ -825,8 +886,8 @@ __global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __r
     for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
     const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % L.nx, j = c / L.nx;
+    for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
+        int c = cw.c, i = cw.i, j = cw.j;
         Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
         double dg = L.diag[c];
 #pragma unroll
@@ -913,8 +974,8 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
     const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % L.nx, j = c / L.nx;
+    for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
+        int c = cw.c, i = cw.i, j = cw.j;
         Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
         double dg = L.diag[c];
 #pragma unroll
@@ -1112,27 +1173,14 @@ static Lev<T> lev(Solver& s, int l) {
 
 template <typename T>
 static void setup_levels(Solver& s, const double* cd, const double* dd, const double* wl, const double* wb,
-                         cudaStream_t stm) {
-    int N = s.nx * s.ny;
-    k_setup0<T><<<nblocks(N), RB, 0, stm>>>(s.nx, s.ny, cd, dd, wl, wb, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s),
-                                             PT<T>::cd(s), PT<T>::dd(s));
+                         double* d64, cudaStream_t stm) {
+    SetupPlan P;
+    P.nlev = s.nlev;
+    for (int l = 0; l < s.nlev; ++l) { P.nx[l] = s.lnx[l]; P.ny[l] = s.lny[l]; P.off[l] = s.loff[l]; }
+    dim3 grid((s.nx + SB - 1) / SB, (s.ny + SB - 1) / SB);
+    k_setup_tree<T><<<grid, 256, 0, stm>>>(P, cd, dd, wl, wb, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s),
+                                           PT<T>::cd(s), PT<T>::dd(s), d64, PT<T>::inv(s), s.tickets + 6);
     ++s.launches;
-    for (int l = 1; l < s.nlev; ++l) {
-        size_t fo = s.loff[l - 1], co = s.loff[l];
-        int n = s.lnx[l] * s.lny[l];
-        k_coarsen<T><<<nblocks(n), RB, 0, stm>>>(s.lnx[l - 1], s.lny[l - 1], PT<T>::cd(s) + fo, PT<T>::dd(s) + fo,
-                                                  PT<T>::wl(s) + fo, PT<T>::wb(s) + fo, PT<T>::cd(s) + co,
-                                                  PT<T>::dd(s) + co, PT<T>::wl(s) + co, PT<T>::wb(s) + co,
-                                                  PT<T>::diag(s) + co);
-        ++s.launches;
-    }
-    int lc = s.nlev - 1;
-    if (s.lnx[lc] * s.lny[lc] <= 32) {
-        size_t o = s.loff[lc];
-        k_coarse_inverse<T><<<1, 32, 0, stm>>>(s.lnx[lc], s.lny[lc], PT<T>::diag(s) + o, PT<T>::wl(s) + o,
-                                               PT<T>::wb(s) + o, PT<T>::inv(s));
-        ++s.launches;
-    }
 }
 
 // z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved)
@@ -1300,9 +1348,9 @@ static void solve_fp64(Solver& s, const double* b, double* x, double rtol, int m
 }
 
 template <int NR>
-static void solve_mixed(Solver& s, const double* b, double* x, double rtol, int max_iter, cudaStream_t stm) {
+static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, double rtol, int max_iter,
+                        cudaStream_t stm) {
     int N = s.nx * s.ny;
-    Lev<double> L64 = lev<double>(s, 0);
     const int max_outer = 8;
     const double inner_rtol = 1e-5;
     float* z = s.f_x;
@@ -1343,16 +1391,16 @@ void Solver::solve(const double* cd, const double* dd, const double* wl, const d
     st = st_base + slot;
     // the FP64 level-0 operator is needed in both modes (outer residual of the refinement)
     if (precision == 0) {
-        setup_levels<double>(*this, cd, dd, wl, wb, stm);
+        setup_levels<double>(*this, cd, dd, wl, wb, nullptr, stm);
         if (nr == 1) solve_fp64<1>(*this, b, x, rtol, max_iter, stm);
         else solve_fp64<2>(*this, b, x, rtol, max_iter, stm);
     } else {
-        int N = nx * ny;
-        k_setup0<double><<<nblocks(N), RB, 0, stm>>>(nx, ny, cd, dd, wl, wb, d_diag, d_wl, d_wb, d_cd, d_dd);
-        ++launches;
-        setup_levels<float>(*this, cd, dd, wl, wb, stm);
-        if (nr == 1) solve_mixed<1>(*this, b, x, rtol, max_iter, stm);
-        else solve_mixed<2>(*this, b, x, rtol, max_iter, stm);
+        // the FP32 hierarchy, plus D in FP64 for the refinement residual (whose face weights are
+        // the caller's FP64 arrays)
+        setup_levels<float>(*this, cd, dd, wl, wb, d_diag, stm);
+        Lev<double> L64{nx, ny, d_diag, wl, wb};
+        if (nr == 1) solve_mixed<1>(*this, L64, b, x, rtol, max_iter, stm);
+        else solve_mixed<2>(*this, L64, b, x, rtol, max_iter, stm);
     }
 }
 

@@ -230,10 +230,17 @@ ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const dou
                                       const double* b, double* x, int nr, int precision, double rtol, int max_iter,
                                       void* stream, int* iters, double* rel_res);
 
-/* Options: EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the
- * context's stream (solver loops as conditional WHILE nodes, no host round trip inside a
- * step); 0 launches every kernel from the host.  Graph mode needs a non-default stream. */
-enum { EBIT_OPT_GRAPH = 1 };
+/* Options:
+ *   EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the context's
+ *   stream (solver loops as conditional WHILE nodes, no host round trip inside a step); 0
+ *   launches every kernel from the host.  Graph mode needs a non-default stream.
+ *   EBIT_OPT_TMA (default 1) stages the tile regions of the multigrid smoother kernels into
+ *   shared memory with tensor-memory-accelerator copies (cp.async.bulk.tensor); 0 loads them
+ *   with ordinary loads.  Both give the same values; levels whose rows or base are not 16-byte
+ *   aligned always use ordinary loads.  Changing it drops the captured step graphs.
+ * A tile kernel that waits for its copies in vain gives up after a bounded wait; ebit_step
+ * then returns EBIT_ECUDA. */
+enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2 };
 ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value);
 
 const char* ebit_last_error(const ebit_ctx* ctx);

@@ -52,6 +52,7 @@ struct Instance {
     long long nstep = 0;
     double stats[6] = {0, 0, 0, 0, 0, 0};   // iterations and residuals: energy, viscous, poisson
     bool noconv = false;
+    bool fault = false;   // a tile kernel's bounded wait for its TMA copies gave up
     // CUDA graphs of one step, per sweep-order parity
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};   // kernel launches captured per graph (loop bodies once)
@@ -288,6 +289,7 @@ static void collect_stats(Instance& I, bool graph_step) {
         if (!(m & (1u << k))) continue;
         r[k] = I.solver.result_from_host(k, I.cfg.precision);
         ok = ok && r[k].converged;
+        if (r[k].fault) I.fault = true;
         // kernels executed inside the conditional loop bodies of a graph step
         n += r[k].iters * body;
         if (I.cfg.precision == EBIT_MIXED) n += 2 * r[k].outer - 1;
@@ -408,6 +410,10 @@ static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
         std::string where = ctx->inst.size() > 1 ? " (instance " + std::to_string(b) + ")" : "";
         if (s & 1) return fail(ctx, EBIT_ECFL, "a marker moved one cell or more in one sweep (reduce dt)" + where);
         if (s & 2) return fail(ctx, EBIT_ETOPO, "too many marker candidates on one edge" + where);
+        if (I.fault) {
+            I.fault = false;
+            return fail(ctx, EBIT_ECUDA, "a multigrid tile kernel's TMA copies did not complete" + where);
+        }
         if (I.noconv) {
             I.noconv = false;
             worst = fail(ctx, EBIT_ENOCONV, "a linear solve hit max_iter" + where);
@@ -752,6 +758,15 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
     if (option == EBIT_OPT_GRAPH) {
         ctx->use_graph = value ? 1 : 0;
         return EBIT_OK;
+    }
+    if (option == EBIT_OPT_TMA) {
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        for (auto& I : ctx->inst) {
+            I.solver.use_tma = value ? 1 : 0;
+            for (auto& gx : I.graph)
+                if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+        }
+        return cuda_check(ctx, "ebit_set_option");
     }
     return fail(ctx, EBIT_EINVAL, "unknown option");
 }

@@ -185,14 +185,106 @@ struct Region {
     __device__ Region(unsigned char* base) { x0 = (T*)base; }
     __device__ T* x(int c) const { return x0 + c * (NR * NC); }
     __device__ T* res() const { return x0 + 2 * NR * NC; }
-    static constexpr size_t bytes() { return ((size_t)2 * NC + TX * TY) * NR * sizeof(T); }
+    static constexpr size_t BYTES = ((size_t)2 * NC + TX * TY) * NR * sizeof(T);
+    __host__ __device__ static constexpr size_t bytes() { return BYTES; }
 };
 template <int H>
 constexpr int tile_block() { return (((TX + 2 * H) / 2) * ((TY + 2 * H) / 2) + 31) / 32 * 32; }
 // blocks per SM the single-value FP32 tile kernels are compiled for (register budget); the
 // others keep the compiler's choice
 template <typename T, int NR>
-constexpr int tile_min_blocks() { return sizeof(T) == 4 && NR == 1 ? 3 : 1; }
+constexpr int tile_min_blocks() { return sizeof(T) == 4 ? (NR == 1 ? 3 : 2) : 1; }
+
+// ---- TMA staging of the tile regions ------------------------------------------------------
+// One elected thread issues a 2-D tensor copy (cp.async.bulk.tensor) per operand array into
+// dense shared-memory boxes and arms an mbarrier with their byte count; every thread waits on
+// the barrier (bounded) and then reads its cells from the boxes.  A copy must start at an x
+// coordinate whose byte offset is a multiple of 16, so each box starts up to A - 1 cells left
+// of the region (A = 16 / bytes per cell) and the region indexes it from that offset; cells
+// outside the grid are filled with zeros by the copy.
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// wait for phase 0 of the barrier; false if it did not complete within the bound
+__device__ inline bool mbar_wait_bounded(uint64_t* bar) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, 0)) return true;
+    return false;
+}
+
+__host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
+__host__ __device__ constexpr int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+__host__ __device__ constexpr int round_up(int a, int m) { return (a + m - 1) / m * m; }
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~size_t(127); }
+
+// box geometry of a tile kernel with halo H; POST: k_post (also the pre-smoothed x and the
+// coarse x)
+template <typename T, int NR, int H, bool POST>
+struct Stage {
+    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H;
+    static constexpr int AS = 16 / (int)sizeof(T);          // x alignment of D, wl, wb (cells)
+    static constexpr int AV = 16 / (NR * (int)sizeof(T));   // x alignment of the NR-vector arrays
+    static constexpr int OXS = pmod(-H, AS), OXV = pmod(-H, AV), OXC = pmod(floordiv2(-H), AV);
+    static constexpr int BWS = round_up(OXS + SX + 1, AS), BHS = SY + 1;   // +1: right / upper faces
+    static constexpr int BWV = round_up(OXV + SX, AV), BHV = SY;
+    static constexpr int BWC = round_up(OXC + SX / 2 + 1, AV), BHC = SY / 2 + 1;
+    static constexpr size_t SB = (size_t)BWS * BHS * sizeof(T);
+    static constexpr size_t VB = (size_t)BWV * NR * BHV * sizeof(T);
+    static constexpr size_t CB = (size_t)BWC * NR * BHC * sizeof(T);
+    static constexpr size_t OFF_D = 0, OFF_WL = align128(SB), OFF_WB = 2 * align128(SB), OFF_B = 3 * align128(SB);
+    static constexpr size_t OFF_XIN = OFF_B + align128(VB), OFF_XC = OFF_XIN + (POST ? align128(VB) : 0);
+    static constexpr size_t OFF_BAR = OFF_XC + (POST ? align128(CB) : 0);
+    static constexpr size_t BYTES = OFF_BAR + 128;
+    static constexpr uint32_t TX_BYTES = (uint32_t)(3 * SB + VB + (POST ? VB + CB : 0));
+    static_assert(BWS <= 256 && BWV * NR <= 256 && BWC * NR <= 256 && BHS <= 256, "TMA box too large");
+};
+
+// issue the region's copies (thread 0) and wait for them (all threads); false on a timeout
+template <typename T, int NR, int H, bool POST>
+__device__ inline bool stage_region(unsigned char* sbase, const TileMaps& M, int gx0, int gy0) {
+    using Sg = Stage<T, NR, H, POST>;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Sg::OFF_BAR);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, Sg::TX_BYTES);
+        int xs = gx0 - Sg::OXS, xv = (gx0 - Sg::OXV) * NR;
+        tma_load_2d(sbase + Sg::OFF_D, &M.d, xs, gy0, bar);
+        tma_load_2d(sbase + Sg::OFF_WL, &M.wl, xs, gy0, bar);
+        tma_load_2d(sbase + Sg::OFF_WB, &M.wb, xs, gy0, bar);
+        tma_load_2d(sbase + Sg::OFF_B, &M.b, xv, gy0, bar);
+        if (POST) {
+            tma_load_2d(sbase + Sg::OFF_XIN, &M.xin, xv, gy0, bar);
+            tma_load_2d(sbase + Sg::OFF_XC, &M.xc, ((gx0 >> 1) - Sg::OXC) * NR, gy0 >> 1, bar);
+        }
+    }
+    return mbar_wait_bounded(bar);
+}
 
 // the thread's four cells: [r][c] = row ry0 + r, colour c (its column is 2k + (c ^ sw[r]))
 template <typename T, int NR>
@@ -204,11 +296,12 @@ struct Cells {
 // load the thread's cells (coefficients to registers, x to shared memory: 0, or xin + the
 // prolongated coarse x when xin != null); cells outside the domain get D = 1, zero weights,
 // b = x = 0, so sweeps leave them 0
-template <typename T, int NR, int H>
+template <typename T, int NR, int H, bool POST>
 __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, int k, int ry0, const Lev<T>& L,
                                  const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
-                                 int cnx, int gx0, int gy0) {
+                                 int cnx, int gx0, int gy0, const unsigned char* stage) {
     constexpr int HX = Region<T, NR, H>::HX;
+    using Sg = Stage<T, NR, H, POST>;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         int ry = ry0 + r;
@@ -219,22 +312,54 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, i
             int rx = 2 * k + e;
             int gi = gx0 + rx;
             bool in = gj >= 0 && gj < L.ny && gi >= 0 && gi < L.nx;
-            // unconditional loads (clamped, then masked): all of them can be in flight at once
-            int gic = min(max(gi, 0), L.nx - 1), gjc = min(max(gj, 0), L.ny - 1);
-            int g = gjc * L.nx + gic;
-            Vec<T, NR> bv = reinterpret_cast<const Vec<T, NR>*>(b)[g], xv;
-            T dv = L.diag[g], wlv = L.wl[g], wbv = L.wb[g];
-            T wrv = L.wl[gic + 1 < L.nx ? g + 1 : g], wtv = L.wb[gjc + 1 < L.ny ? g + L.nx : g];
-            if (gi + 1 >= L.nx) wrv = T(0);
-            if (gj + 1 >= L.ny) wtv = T(0);
-            if (xin) {
-                xv = reinterpret_cast<const Vec<T, NR>*>(xin)[g];
-                Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gjc >> 1) * cnx + (gic >> 1)];
+            Vec<T, NR> bv, xv;
+            T dv, wlv, wbv, wrv, wtv;
+            if (stage) {
+                // from the TMA boxes (zeros outside the grid)
+                const T* sd = reinterpret_cast<const T*>(stage + Sg::OFF_D);
+                const T* swl = reinterpret_cast<const T*>(stage + Sg::OFF_WL);
+                const T* swb = reinterpret_cast<const T*>(stage + Sg::OFF_WB);
+                const T* sb = reinterpret_cast<const T*>(stage + Sg::OFF_B);
+                int qs = ry * Sg::BWS + rx + Sg::OXS, qv = (ry * Sg::BWV + rx + Sg::OXV) * NR;
+                dv = sd[qs];
+                wlv = swl[qs];
+                wbv = swb[qs];
+                wrv = swl[qs + 1];
+                wtv = swb[qs + Sg::BWS];
 #pragma unroll
-                for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] += cv.v[k2];
+                for (int k2 = 0; k2 < NR; ++k2) bv.v[k2] = sb[qv + k2];
+                if (POST) {
+                    const T* sx = reinterpret_cast<const T*>(stage + Sg::OFF_XIN);
+                    const T* sc = reinterpret_cast<const T*>(stage + Sg::OFF_XC);
+                    int cx = (gi >> 1) - ((gx0 >> 1) - Sg::OXC), cy = (gj >> 1) - (gy0 >> 1);
+                    int qc = (cy * Sg::BWC + cx) * NR;
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = sx[qv + k2] + sc[qc + k2];
+                } else {
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
+                }
             } else {
+                // unconditional loads (clamped, then masked): all of them can be in flight at once
+                int gic = min(max(gi, 0), L.nx - 1), gjc = min(max(gj, 0), L.ny - 1);
+                int g = gjc * L.nx + gic;
+                bv = reinterpret_cast<const Vec<T, NR>*>(b)[g];
+                dv = L.diag[g];
+                wlv = L.wl[g];
+                wbv = L.wb[g];
+                wrv = L.wl[gic + 1 < L.nx ? g + 1 : g];
+                wtv = L.wb[gjc + 1 < L.ny ? g + L.nx : g];
+                if (gi + 1 >= L.nx) wrv = T(0);
+                if (gj + 1 >= L.ny) wtv = T(0);
+                if (POST) {
+                    xv = reinterpret_cast<const Vec<T, NR>*>(xin)[g];
+                    Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gjc >> 1) * cnx + (gic >> 1)];
 #pragma unroll
-                for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
+                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] += cv.v[k2];
+                } else {
+#pragma unroll
+                    for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
+                }
             }
             if (!in) {
 #pragma unroll
@@ -327,21 +452,31 @@ __device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, in
 template <typename T, int NR>
 __global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>()) k_pre(Lev<T> L, const T* __restrict__ b,
                                                                   T* __restrict__ x, T* __restrict__ bc,
-                                                                  const SolveState* __restrict__ st, KTimer* tm) {
+                                                                  SolveState* st, KTimer* tm,
+                                                                  const __grid_constant__ TileMaps maps,
+                                                                  int use_tma) {
     if (skip(st)) return;
     constexpr int H = 2 * NU + 1;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
     int p0 = (gx0 + gy0) & 1;
     bool act = threadIdx.x < Rg::THREADS;
     int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    // TMA boxes: 128-byte aligned after the region (the launch reserves 128 bytes of slack)
+    unsigned char* stage =
+        use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
+    bool landed = true;
+    if (stage) {
+        landed = stage_region<T, NR, H, false>(stage, maps, gx0, gy0);
+        if (!landed && threadIdx.x == 0) atomicOr(&st->fault, 1);
+    }
     Cells<T, NR> C;
-    if (act) tile_load<T, NR, H>(R, C, p0, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0);
+    if (act) tile_load<T, NR, H, false>(R, C, p0, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0, stage);
     __syncthreads();
     tile_sweep<T, NR, H, 1, 0>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 2, 1>(R, C, k, ry0, act);
@@ -390,20 +525,30 @@ template <typename T, int NR, bool DOT>
 __global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>()) k_post(Lev<T> L, const T* __restrict__ b,
                                                                const T* __restrict__ xin, T* __restrict__ x,
                                                                const T* __restrict__ xc, SolveState* st,
-                                                               double* partial, unsigned* ticket, KTimer* tm) {
+                                                               double* partial, unsigned* ticket, KTimer* tm,
+                                                               const __grid_constant__ TileMaps maps,
+                                                               int use_tma) {
     if (skip(st)) return;
     constexpr int H = 2 * NU;
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
     Rg R(smem);
     int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
     int p0 = (gx0 + gy0) & 1;
     bool act = threadIdx.x < Rg::THREADS;
     int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    // TMA boxes: 128-byte aligned after the region (the launch reserves 128 bytes of slack)
+    unsigned char* stage =
+        use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
+    bool landed = true;
+    if (stage) {
+        landed = stage_region<T, NR, H, true>(stage, maps, gx0, gy0);
+        if (!landed && threadIdx.x == 0) atomicOr(&st->fault, 1);
+    }
     Cells<T, NR> C;
-    if (act) tile_load<T, NR, H>(R, C, p0, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0);
+    if (act) tile_load<T, NR, H, true>(R, C, p0, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0, stage);
     __syncthreads();
     tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
@@ -507,7 +652,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
                                                          const T* __restrict__ inv, const T* __restrict__ b_in,
                                                          T* __restrict__ x_out, SolveState* st) {
     if (skip(st)) return;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     SmallMem<T, NR> M(smem, P.total);
     int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
     // the small levels are contiguous in the packed level arrays and in shared memory: one flat
@@ -789,10 +934,10 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
                                                 T* __restrict__ p1, T* __restrict__ q, SolveState* st,
                                                 double* partial, unsigned* ticket) {
     if (skip(st)) return;
-    const Vec<T, NR>* Z = reinterpret_cast<const Vec<T, NR>*>(z);
-    const Vec<T, NR>* Po = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p1 : p0);
-    Vec<T, NR>* Pn = reinterpret_cast<Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
-    Vec<T, NR>* Q = reinterpret_cast<Vec<T, NR>*>(q);
+    const Vec<T, NR>* __restrict__ Z = reinterpret_cast<const Vec<T, NR>*>(z);
+    const Vec<T, NR>* __restrict__ Po = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p1 : p0);
+    Vec<T, NR>* __restrict__ Pn = reinterpret_cast<Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
+    Vec<T, NR>* __restrict__ Q = reinterpret_cast<Vec<T, NR>*>(q);
     T beta[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) beta[k] = (T)st->beta[k];
@@ -800,6 +945,7 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+#pragma unroll 2
     for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
         int c = cw.c, i = cw.i, j = cw.j;
         auto pn = [&](int cc) {
@@ -839,16 +985,17 @@ __global__ void __launch_bounds__(256) k_update(int N, T* __restrict__ x, T* __r
                                                  double* partial, unsigned* ticket, cudaGraphConditionalHandle h,
                                                  int use_h) {
     if (skip(st)) return;
-    const Vec<T, NR>* Pn = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
-    const Vec<T, NR>* Q = reinterpret_cast<const Vec<T, NR>*>(q);
-    Vec<T, NR>* X = reinterpret_cast<Vec<T, NR>*>(x);
-    Vec<T, NR>* Rr = reinterpret_cast<Vec<T, NR>*>(r);
+    const Vec<T, NR>* __restrict__ Pn = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
+    const Vec<T, NR>* __restrict__ Q = reinterpret_cast<const Vec<T, NR>*>(q);
+    Vec<T, NR>* __restrict__ X = reinterpret_cast<Vec<T, NR>*>(x);
+    Vec<T, NR>* __restrict__ Rr = reinterpret_cast<Vec<T, NR>*>(r);
     T alpha[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) alpha[k] = (T)st->alpha[k];
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+#pragma unroll 4
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
 #pragma unroll
@@ -1088,6 +1235,7 @@ static void allow_smem(K kern, int bytes) {
 
 void Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t init_stream) {
     plan(nx_, ny_);
+    tma_ready = false;   // descriptors hold addresses: re-encode after every binding
     char* p = (char*)base;
     auto take = [&](size_t b) { void* r = p; p += (b + 255) & ~size_t(255); return r; };
     size_t A = ncells_all, N = (size_t)nx * ny;
@@ -1152,6 +1300,8 @@ template <> struct PT<float> {
     static float* x2(Solver& s) { return s.f_x2; }
     static float* inv(Solver& s) { return s.f_inv; }
     static float* b(Solver& s) { return s.f_b; }
+    static float* r(Solver& s) { return s.f_r; }
+    static constexpr int prec = 1;
 };
 template <> struct PT<double> {
     static double* diag(Solver& s) { return s.d_diag; }
@@ -1163,7 +1313,91 @@ template <> struct PT<double> {
     static double* x2(Solver& s) { return s.d_x2; }
     static double* inv(Solver& s) { return s.d_inv; }
     static double* b(Solver& s) { return s.d_b; }
+    static double* r(Solver& s) { return s.d_r; }
+    static constexpr int prec = 0;
 };
+
+// ---- TMA descriptors (host) ----------------------------------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// a 2-D row-major array of w x h elements of T, copied in boxes of bw x bh; false when the base
+// or the row pitch is not 16-byte aligned or the encoder refuses
+template <typename T>
+static bool encode_2d(CUtensorMap* m, const void* base, int w, int h, int bw, int bh) {
+    EncodeTiledFn fn = tensor_map_encoder();
+    if (!fn || (uintptr_t)base % 16 != 0 || ((size_t)w * sizeof(T)) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    cuuint64_t pitch[1] = {(cuuint64_t)w * sizeof(T)};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t es[2] = {1, 1};
+    CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return fn(m, dt, 2, const_cast<void*>(base), dims, pitch, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+static size_t tmap_index(int prec, int nr, int l, int post) {
+    return ((size_t)(prec * 2 + (nr - 1)) * Solver::MAXLEV + l) * 2 + post;
+}
+
+template <typename T, int NR, bool POST>
+static bool encode_tile_maps(Solver& s, int l, TileMaps& M) {
+    constexpr int H = POST ? 2 * NU : 2 * NU + 1;
+    using Sg = Stage<T, NR, H, POST>;
+    int nx = s.lnx[l], ny = s.lny[l];
+    size_t o = s.loff[l];
+    const T* b = l == 0 ? PT<T>::r(s) : PT<T>::b(s) + 2 * o;
+    bool ok = encode_2d<T>(&M.d, PT<T>::diag(s) + o, nx, ny, Sg::BWS, Sg::BHS) &&
+              encode_2d<T>(&M.wl, PT<T>::wl(s) + o, nx, ny, Sg::BWS, Sg::BHS) &&
+              encode_2d<T>(&M.wb, PT<T>::wb(s) + o, nx, ny, Sg::BWS, Sg::BHS) &&
+              encode_2d<T>(&M.b, b, nx * NR, ny, Sg::BWV * NR, Sg::BHV);
+    if (POST)
+        ok = ok && encode_2d<T>(&M.xin, PT<T>::x2(s) + 2 * o, nx * NR, ny, Sg::BWV * NR, Sg::BHV) &&
+             encode_2d<T>(&M.xc, PT<T>::x(s) + 2 * s.loff[l + 1], s.lnx[l + 1] * NR, s.lny[l + 1], Sg::BWC * NR,
+                          Sg::BHC);
+    return ok;
+}
+
+template <typename T>
+static void encode_precision(Solver& s, int nbig) {
+    for (int l = 0; l < nbig; ++l) {
+        int p = PT<T>::prec;
+        s.tma_ok[tmap_index(p, 1, l, 0)] = encode_tile_maps<T, 1, false>(s, l, s.tmaps[tmap_index(p, 1, l, 0)]);
+        s.tma_ok[tmap_index(p, 1, l, 1)] = encode_tile_maps<T, 1, true>(s, l, s.tmaps[tmap_index(p, 1, l, 1)]);
+        s.tma_ok[tmap_index(p, 2, l, 0)] = encode_tile_maps<T, 2, false>(s, l, s.tmaps[tmap_index(p, 2, l, 0)]);
+        s.tma_ok[tmap_index(p, 2, l, 1)] = encode_tile_maps<T, 2, true>(s, l, s.tmaps[tmap_index(p, 2, l, 1)]);
+    }
+}
+
+// descriptors of every tiled level, both precisions and right-hand-side counts (host work only)
+static void ensure_tile_maps(Solver& s) {
+    if (s.tma_ready) return;
+    size_t n = tmap_index(1, 2, Solver::MAXLEV - 1, 1) + 1;
+    s.tmaps.assign(n, TileMaps{});
+    s.tma_ok.assign(n, 0);
+    encode_precision<float>(s, s.nbig_f);
+    encode_precision<double>(s, s.nbig_d);
+    s.tma_ready = true;
+}
 
 template <typename T>
 static Lev<T> lev(Solver& s, int l) {
@@ -1217,12 +1451,19 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
     T* B = PT<T>::b(s);
     const T* b = r;
     int nb = nbig_of<T>(s);
+    ensure_tile_maps(s);
+    const int pr = PT<T>::prec;
     for (int l = 0; l < nb; ++l) {
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
         T* bc = B + 2 * s.loff[l + 1];
-        k_pre<T, NR><<<grid, tile_block<2 * NU + 1>(), Region<T, NR, 2 * NU + 1>::bytes(), stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
-                                                                           s.timing && l == 0 ? s.timer : nullptr);
+        size_t ix = tmap_index(pr, NR, l, 0);
+        int tma = s.use_tma && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
+        using Rg = Region<T, NR, 2 * NU + 1>;
+        size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, 2 * NU + 1, false>::BYTES : Rg::bytes();
+        k_pre<T, NR><<<grid, tile_block<2 * NU + 1>(), smem, stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
+                                                                   s.timing && l == 0 ? s.timer : nullptr,
+                                                                   s.tmaps[ix], tma);
         if (!s.use_graph) ++s.launches;
         b = bc;
     }
@@ -1246,12 +1487,17 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         const T* xin = X2 + 2 * s.loff[l];
         T* xout = l == 0 ? z : X + 2 * s.loff[l];
         const T* xc = X + 2 * s.loff[l + 1];
-        size_t smem = Region<T, NR, 2 * NU>::bytes();
+        size_t ix = tmap_index(pr, NR, l, 1);
+        int tma = s.use_tma && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
+        using Rg = Region<T, NR, 2 * NU>;
+        size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, 2 * NU, true>::BYTES : Rg::bytes();
         KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
         if (l == 0)
-            k_post<T, NR, true><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
+            k_post<T, NR, true><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
+                                                                          s.tickets + 4, tm, s.tmaps[ix], tma);
         else
-            k_post<T, NR, false><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial, s.tickets + 4, tm);
+            k_post<T, NR, false><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
+                                                                           s.tickets + 4, tm, s.tmaps[ix], tma);
         if (!s.use_graph) ++s.launches;
     }
 }
@@ -1433,6 +1679,7 @@ SolveResult Solver::result_from_host(int sl, int precision) const {
         if (q > worst) worst = q;
     }
     r.rel_res = worst;
+    r.fault = h.fault != 0;
     if (precision == 0) {
         r.iters = h.iters;
         r.converged = h.done != 0;

@@ -2,8 +2,10 @@
 // FP64 iterative refinement), with device-side loop control so that a whole solve can be
 // captured into a CUDA graph (conditional WHILE nodes) or driven from the host.
 #pragma once
+#include <cuda.h>           // CUtensorMap (the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 namespace ebit {
 
@@ -12,6 +14,7 @@ struct SolveResult {
     double rel_res;   // final ||r|| / ||b|| (max over right-hand sides)
     bool converged;
     int outer = 0;    // refinement sweeps (mixed)
+    bool fault = false;   // a bounded wait for TMA copies gave up (the result is not valid)
 };
 
 // device-resident timing of one kernel class (span from the first block's start to the
@@ -32,6 +35,13 @@ struct SolveState {
     double orr[2], obb[2], otol2[2];   // outer (FP64) residual norms of the refinement loop
     int done, iters, odone, oiters, max_iters, max_outer, nr, itot;
     double inner_rtol;
+    int fault;         // nonzero: a bounded wait of a tile kernel gave up (its TMA copies never landed)
+};
+
+// TMA descriptors of one tiled level (precision and right-hand-side count fixed): the level's
+// right-hand side b, the pre-smoothed x (k_post), the next level's x (k_post), and D, wl, wb
+struct TileMaps {
+    CUtensorMap b, xin, xc, d, wl, wb;
 };
 
 struct Solver {
@@ -67,6 +77,12 @@ struct Solver {
     int timing = 0;
     long long launches = 0;
     int use_graph = 0;     // set by the owner while capturing
+    // TMA descriptors of the tiled levels, [precision][NR - 1][level], encoded on first use;
+    // tma_ok false where a level's rows or base are not 16-byte aligned (plain loads then)
+    std::vector<TileMaps> tmaps;
+    std::vector<char> tma_ok;
+    bool tma_ready = false;
+    int use_tma = 1;       // 0: the tile kernels load their regions with plain loads
 
     void plan(int nx, int ny);
     static size_t bytes(int nx, int ny);

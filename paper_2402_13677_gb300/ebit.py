@@ -39,6 +39,7 @@ EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_
            "ebit_solve_system_noalloc", "ebit_last_error",
            "ebit_destroy", "ebit_version"]
 EBIT_OPT_GRAPH = 1
+EBIT_OPT_TMA = 2
 EBIT_KT_SMOOTH_L0 = 1
 
 

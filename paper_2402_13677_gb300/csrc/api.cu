@@ -57,6 +57,23 @@ struct Instance {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};   // kernel launches captured per graph (loop bodies once)
     unsigned solved = 0;                     // solve slots written since the last statistics read
+    int batch = -1;                          // batch this instance belongs to (-1: stepped alone)
+    int bz = 0;                              // its index inside the batch
+};
+
+// Instances that share grid, boundary conditions and solver settings are stepped together when
+// the context replays graphs: their arenas lie `stride` bytes apart in one allocation, and one
+// graph of batched launches (grid z = instance) steps all of them; `lead` is a copy of the first
+// member whose Grid and Solver carry the batch stride, count and the device array of properties.
+struct Batch {
+    std::vector<int> members;
+    size_t stride = 0;
+    void* arena = nullptr;
+    Phys* d_phys = nullptr;
+    std::vector<Phys> h_phys;
+    Instance lead;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches[2] = {0, 0};
 };
 
 }  // namespace
@@ -71,6 +88,7 @@ struct ebit_ctx {
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
     int* host_status = nullptr;   // pinned, one status word per instance
+    std::vector<Batch> batches;
     ebit_allocator alloc{};
     bool has_alloc = false;
     SolveState* host_states = nullptr;   // pinned, Solver::NSLOT per instance
@@ -222,7 +240,7 @@ static void count(int n) { g_launches += (uint64_t)n; }
 static void reconstruct_full(Instance& I, cudaStream_t st) {
     launch_reconstruct(I.g, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, I.vf, st);
     launch_band(I.g, I.cseg, I.hpos, I.vpos, I.flags, I.nb, st);
-    launch_compact(I.flags, I.g.nx * I.g.ny, F_BAND, I.band_list, I.band_count, I.band_idx, st);
+    launch_compact(I.g, I.flags, I.g.nx * I.g.ny, F_BAND, I.band_list, I.band_count, I.band_idx, st);
     count(3);   // + memset
 }
 
@@ -294,7 +312,7 @@ static void collect_stats(Instance& I, bool graph_step) {
         n += r[k].iters * body;
         if (I.cfg.precision == EBIT_MIXED) n += 2 * r[k].outer - 1;
     }
-    if (graph_step) g_launches += (uint64_t)n;
+    if (graph_step && I.bz == 0) g_launches += (uint64_t)n;   // a batched launch counts once
     if (m & (1u << SLOT_ENERGY)) {
         I.stats[0] = r[SLOT_ENERGY].iters;
         I.stats[3] = r[SLOT_ENERGY].rel_res;
@@ -422,6 +440,17 @@ static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
     return worst;
 }
 
+// two configurations can share batched launches: the same grid, boundaries and solver settings
+// (the time step and the properties may differ)
+static bool batchable(const ebit_config& a, const ebit_config& b) {
+    if (a.nx != b.nx || a.ny != b.ny || a.h != b.h || a.x0 != b.x0 || a.y0 != b.y0) return false;
+    for (int s = 0; s < 4; ++s)
+        if (a.bc[s] != b.bc[s] || a.T_fixed[s] != b.T_fixed[s] || a.T_wall[s] != b.T_wall[s]) return false;
+    return a.precision == b.precision && a.rtol == b.rtol && a.max_iter == b.max_iter &&
+           a.extend_iters == b.extend_iters && a.theta_min == b.theta_min && a.sweep_order == b.sweep_order &&
+           a.energy == b.energy && a.mdot_fixed == b.mdot_fixed;
+}
+
 // ---------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------
@@ -449,19 +478,58 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         Instance& I = ctx->inst[b];
         I.cfg = c;
         I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0;
+        I.g.nz = 1; I.g.zs = 0; I.g.pz = nullptr;
         for (int s = 0; s < 4; ++s) { I.g.bc[s] = c.bc[s]; I.g.Tfix[s] = c.T_fixed[s] ? 1 : 0; I.g.Tw[s] = c.T_wall[s]; }
         std::memset(&I.p, 0, sizeof(I.p));
         I.p.dt = c.dt; I.p.theta_min = c.theta_min; I.p.extend_iters = c.extend_iters;
         I.p.energy = c.energy; I.p.mdot_fixed = c.mdot_fixed;
-        size_t bytes = layout(I, nullptr, assign_ptrs);
+    }
+    // group instances that can share batched launches (same grid, boundaries and solver settings)
+    std::vector<int> group(batch, -1);
+    std::vector<std::vector<int>> groups;
+    for (int b = 0; b < batch; ++b) {
+        if (group[b] >= 0) continue;
+        group[b] = (int)groups.size();
+        groups.push_back({b});
+        for (int b2 = b + 1; b2 < batch; ++b2)
+            if (group[b2] < 0 && batchable(cfgs[b], cfgs[b2])) {
+                group[b2] = group[b];
+                groups.back().push_back(b2);
+            }
+    }
+    for (auto& gm : groups) {
+        Instance& I0 = ctx->inst[gm[0]];
+        size_t bytes = (layout(I0, nullptr, assign_ptrs) + 255) & ~size_t(255);
+        size_t total = bytes * gm.size();
         void* mem = nullptr;
-        if (ctx->has_alloc) mem = ctx->alloc.alloc_fn(bytes, ctx->alloc.user);
-        else if (cudaMalloc(&mem, bytes) != cudaSuccess) mem = nullptr;
+        if (ctx->has_alloc) mem = ctx->alloc.alloc_fn(total, ctx->alloc.user);
+        else if (cudaMalloc(&mem, total) != cudaSuccess) mem = nullptr;
         if (!mem) { ebit_destroy(ctx); return EBIT_ENOMEM; }
-        I.arena = mem;
-        I.arena_bytes = bytes;
-        layout(I, (char*)mem, assign_ptrs);
-        cudaMemsetAsync(mem, 0, bytes, ctx->stream);
+        for (size_t z = 0; z < gm.size(); ++z) {
+            Instance& I = ctx->inst[gm[z]];
+            I.arena_bytes = bytes;
+            layout(I, (char*)mem + z * bytes, assign_ptrs);
+        }
+        cudaMemsetAsync(mem, 0, total, ctx->stream);
+        if (gm.size() == 1) {
+            I0.arena = mem;
+            continue;
+        }
+        Batch B;
+        B.members = gm;
+        B.stride = bytes;
+        B.arena = mem;
+        B.h_phys.resize(gm.size());
+        if (cudaMalloc(&B.d_phys, gm.size() * sizeof(Phys)) != cudaSuccess) {
+            ctx->batches.push_back(B);
+            ebit_destroy(ctx);
+            return EBIT_ENOMEM;
+        }
+        for (size_t z = 0; z < gm.size(); ++z) {
+            ctx->inst[gm[z]].batch = (int)ctx->batches.size();
+            ctx->inst[gm[z]].bz = (int)z;
+        }
+        ctx->batches.push_back(B);
     }
     if (cudaMallocHost(&ctx->host_states, batch * Solver::NSLOT * sizeof(SolveState)) != cudaSuccess ||
         cudaMallocHost(&ctx->host_status, batch * sizeof(int)) != cudaSuccess) {
@@ -683,6 +751,38 @@ static ebit_status ensure_workers(ebit_ctx* ctx) {
     return cuda_check(ctx, "worker streams");
 }
 
+// one step of a batch: refresh the members' properties on the device, capture the batched graph
+// of the lead on first use, replay it on stream st
+static ebit_status replay_batch(ebit_ctx* ctx, Batch& B, cudaStream_t st) {
+    Instance& I0 = ctx->inst[B.members[0]];
+    if (B.lead.batch < 0 || B.lead.g.nz == 1) {
+        B.lead = I0;
+        B.lead.g.nz = (int)B.members.size();
+        B.lead.g.zs = (long long)B.stride;
+        B.lead.g.pz = B.d_phys;
+        B.lead.solver.nz = (int)B.members.size();
+        B.lead.solver.zs = (long long)B.stride;
+        B.lead.solver.use_tma = 0;   // descriptors hold one instance's addresses
+    }
+    for (size_t z = 0; z < B.members.size(); ++z) B.h_phys[z] = ctx->inst[B.members[z]].p;
+    cudaMemcpyAsync(B.d_phys, B.h_phys.data(), B.h_phys.size() * sizeof(Phys), cudaMemcpyHostToDevice, st);
+    B.lead.nstep = I0.nstep;
+    int par = (I0.cfg.sweep_order == 0) ? 0 : (int)(I0.nstep & 1);
+    if (!B.graph[par]) {
+        ebit_status r = capture_step(ctx, B.lead, st, &B.graph[par]);
+        if (r != EBIT_OK) return r;
+        B.graph_launches[par] = B.lead.graph_launches[par];
+    }
+    cudaGraphLaunch(B.graph[par], st);
+    g_launches += (uint64_t)B.graph_launches[par];
+    for (int m : B.members) {
+        Instance& I = ctx->inst[m];
+        I.solved = (I.p.energy ? 1u : 0u) | 2u | 4u | 8u;
+        I.nstep += 1;
+    }
+    return EBIT_OK;
+}
+
 ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
     if (!ctx || nsteps < 0) return EBIT_EINVAL;
     for (auto& I : ctx->inst)
@@ -696,16 +796,22 @@ ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
     ebit_status worst = EBIT_OK;
     for (int n = 0; n < nsteps; ++n) {
         if (batched) {
-            int K = (int)ctx->workers.size();
+            // batches and the instances stepped alone, round-robin over the worker streams
+            int K = (int)ctx->workers.size(), w = 0;
             cudaEventRecord(ctx->fork, ctx->stream);
-            for (int w = 0; w < K; ++w) cudaStreamWaitEvent(ctx->workers[w], ctx->fork, 0);
-            for (size_t b = 0; b < ctx->inst.size(); ++b) {
-                ebit_status r = replay_step(ctx, ctx->inst[b], ctx->workers[b % K]);
+            for (int k = 0; k < K; ++k) cudaStreamWaitEvent(ctx->workers[k], ctx->fork, 0);
+            for (auto& B : ctx->batches) {
+                ebit_status r = replay_batch(ctx, B, ctx->workers[w++ % K]);
                 if (r != EBIT_OK) return r;
             }
-            for (int w = 0; w < K; ++w) {
-                cudaEventRecord(ctx->joins[w], ctx->workers[w]);
-                cudaStreamWaitEvent(ctx->stream, ctx->joins[w], 0);
+            for (auto& I : ctx->inst) {
+                if (I.batch >= 0) continue;
+                ebit_status r = replay_step(ctx, I, ctx->workers[w++ % K]);
+                if (r != EBIT_OK) return r;
+            }
+            for (int k = 0; k < K; ++k) {
+                cudaEventRecord(ctx->joins[k], ctx->workers[k]);
+                cudaStreamWaitEvent(ctx->stream, ctx->joins[k], 0);
             }
         } else {
             for (auto& I : ctx->inst) {
@@ -766,6 +872,9 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
             for (auto& gx : I.graph)
                 if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
         }
+        for (auto& B : ctx->batches)
+            for (auto& gx : B.graph)
+                if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
         return cuda_check(ctx, "ebit_set_option");
     }
     return fail(ctx, EBIT_EINVAL, "unknown option");
@@ -831,6 +940,15 @@ void ebit_destroy(ebit_ctx* ctx) {
     for (auto& I : ctx->inst)
         for (auto& gx : I.graph)
             if (gx) cudaGraphExecDestroy(gx);
+    for (auto& B : ctx->batches) {
+        for (auto& gx : B.graph)
+            if (gx) cudaGraphExecDestroy(gx);
+        if (B.arena) {
+            if (ctx->has_alloc) { if (ctx->alloc.free_fn) ctx->alloc.free_fn(B.arena, ctx->alloc.user); }
+            else cudaFree(B.arena);
+        }
+        if (B.d_phys) cudaFree(B.d_phys);
+    }
     for (auto& s : ctx->aux)
         if (s) cudaStreamDestroy(s);
     for (auto& s : ctx->workers) cudaStreamDestroy(s);

@@ -21,14 +21,6 @@ constexpr uint8_t F_CCOL = 1;   // centre colour f_C (1 liquid)
 constexpr uint8_t F_BAND = 2;   // narrow band
 constexpr uint8_t F_CUT = 4;    // cell holds interface segments
 
-struct Grid {
-    int nx, ny;
-    double h, x0, y0;
-    int bc[4];        // left, right, bottom, top
-    int Tfix[4];
-    double Tw[4];
-};
-
 struct Phys {
     double rho_l, rho_v, mu_l, mu_v, lam_l, lam_v, cp_l, cp_v;
     double T_sat, h_lg, gx, gy;
@@ -36,6 +28,30 @@ struct Phys {
     int extend_iters, energy;
     double mdot_fixed;
 };
+
+// Grid of one instance, or of a batch of instances that share it: a batched launch runs
+// instance z = blockIdx.z (of nz) on the arrays at byte offset z * zs from instance 0's, with
+// the properties pz[z] (null pz: the Phys passed by value)
+struct Grid {
+    int nx, ny;
+    double h, x0, y0;
+    int bc[4];        // left, right, bottom, top
+    int Tfix[4];
+    double Tw[4];
+    int nz;                  // instances in the launch (1 unless batched)
+    long long zs;            // byte stride between consecutive instances' arenas
+    const Phys* pz;          // device array of the instances' properties, or null
+};
+
+// byte offset of this block's instance, and a pointer moved to it
+__device__ __forceinline__ long long zoff(long long zs) { return (long long)blockIdx.z * zs; }
+template <class P>
+__device__ __forceinline__ P* zsh(P* p, long long off) {
+    return p ? reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(p) + off) : p;
+}
+__device__ __forceinline__ void zphys(const Grid& g, Phys& p) {
+    if (g.pz) p = g.pz[blockIdx.z];
+}
 
 __host__ __device__ inline int cidx(const Grid& g, int i, int j) { return j * g.nx + i; }
 __host__ __device__ inline int vidx(const Grid& g, int i, int j) { return j * (g.nx + 1) + i; }
@@ -63,5 +79,8 @@ __device__ inline double cell_vel(const double2* F, const Grid& g, int comp, int
 }
 
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
+// launch grids that cover every instance of a (possibly batched) launch
+inline dim3 grid1(long long n, int bs, int nz) { return dim3(div_up(n, bs), 1, nz); }
+inline dim3 rows_grid(int n, int rows, int bs, int nz) { return dim3(div_up(n, bs), rows, nz); }
 
 }  // namespace ebit

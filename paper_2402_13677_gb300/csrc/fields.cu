@@ -150,6 +150,14 @@ __host__ inline Refl velocity_refl(const Grid& g, int comp) {
 __global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l, const double* __restrict__ T_v,
                            const double2* __restrict__ u_l, const double2* __restrict__ u_v,
                            double* __restrict__ Ts_l, double* __restrict__ Ts_v) {
+    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const long long zo = zoff(g.zs);
+    T_l = zsh(T_l, zo);
+    T_v = zsh(T_v, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
+    Ts_l = zsh(Ts_l, zo);
+    Ts_v = zsh(Ts_v, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -164,6 +172,14 @@ __global__ void __launch_bounds__(WX * WY) k_advect_T_f32(Grid g, Refl r, double
                                                          const double2* __restrict__ u_l,
                                                          const double2* __restrict__ u_v, double* __restrict__ Ts_l,
                                                          double* __restrict__ Ts_v) {
+    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const long long zo = zoff(g.zs);
+    T_l = zsh(T_l, zo);
+    T_v = zsh(T_v, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
+    Ts_l = zsh(Ts_l, zo);
+    Ts_v = zsh(Ts_v, zo);
     __shared__ float sh[2][WSY][WSX];
     int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
     int ic = min(i0 + WX / 2, g.nx - 1), jc = min(j0 + WY / 2, g.ny - 1);
@@ -186,7 +202,12 @@ __global__ void __launch_bounds__(WX * WY) k_advect_T_f32(Grid g, Refl r, double
 // compaction (warp ballot + popcount prefix, one atomic per warp)
 // ---------------------------------------------------------------------------------
 __global__ void k_compact(const uint8_t* __restrict__ flags, int N, uint8_t mask, int* __restrict__ list,
-                          int* __restrict__ count, int* __restrict__ idxmap) {
+                          int* __restrict__ count, int* __restrict__ idxmap, long long zs) {
+    const long long zo = zoff(zs);
+    flags = zsh(flags, zo);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    idxmap = zsh(idxmap, zo);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     bool pred = c < N && (flags[c] & mask);
     unsigned bal = __ballot_sync(0xffffffffu, pred);
@@ -254,6 +275,18 @@ __global__ void k_extend(Grid g, int mode, int it, int last, const int* __restri
                          const int* __restrict__ idxmap, const double2* __restrict__ nb, double* f0,
                          const double* __restrict__ vcur0, double* __restrict__ vnxt0, double* f1,
                          const double* __restrict__ vcur1, double* __restrict__ vnxt1) {
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    flags = zsh(flags, zo);
+    idxmap = zsh(idxmap, zo);
+    nb = zsh(nb, zo);
+    f0 = zsh(f0, zo);
+    vcur0 = zsh(vcur0, zo);
+    vnxt0 = zsh(vnxt0, zo);
+    f1 = zsh(f1, zo);
+    vcur1 = zsh(vcur1, zo);
+    vnxt1 = zsh(vnxt1, zo);
     int n = *count;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
         extend_entry(g, mode, it, last, k, list, flags, idxmap, nb, f0, vcur0, vnxt0, f1, vcur1, vnxt1);
@@ -262,7 +295,14 @@ __global__ void k_extend(Grid g, int mode, int it, int last, const int* __restri
 // energy solution (one value per cell) back to the phase fields: T_k = T where f_C = k, T*_k elsewhere
 __global__ void k_split_T(int N, const uint8_t* __restrict__ flags, const double* __restrict__ x,
                           const double* __restrict__ Ts_l, const double* __restrict__ Ts_v, double* __restrict__ T_l,
-                          double* __restrict__ T_v) {
+                          double* __restrict__ T_v, long long zs) {
+    const long long zo = zoff(zs);
+    flags = zsh(flags, zo);
+    x = zsh(x, zo);
+    Ts_l = zsh(Ts_l, zo);
+    Ts_v = zsh(Ts_v, zo);
+    T_l = zsh(T_l, zo);
+    T_v = zsh(T_v, zo);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     bool liq = flags[c] & F_CCOL;
@@ -275,6 +315,13 @@ __global__ void k_split_T(int N, const uint8_t* __restrict__ flags, const double
 // ---------------------------------------------------------------------------------
 __global__ void k_ghost_cells(Grid g, double J, const uint8_t* __restrict__ flags, const double* __restrict__ mdot,
                               const double2* __restrict__ nb, double2* u_l, double2* u_v) {
+    if (g.pz) J = 1.0 / g.pz[blockIdx.z].rho_l - 1.0 / g.pz[blockIdx.z].rho_v;
+    const long long zo = zoff(g.zs);
+    flags = zsh(flags, zo);
+    mdot = zsh(mdot, zo);
+    nb = zsh(nb, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.nx * g.ny) return;
     uint8_t fl = flags[c];
@@ -296,6 +343,18 @@ __global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flag
                               const double2* __restrict__ nb, const uint8_t* __restrict__ vcol,
                               const double* __restrict__ hpos, const double* __restrict__ vpos,
                               double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v) {
+    if (g.pz) J = 1.0 / g.pz[blockIdx.z].rho_l - 1.0 / g.pz[blockIdx.z].rho_v;
+    const long long zo = zoff(g.zs);
+    flags = zsh(flags, zo);
+    mdot = zsh(mdot, zo);
+    nb = zsh(nb, zo);
+    vcol = zsh(vcol, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    ufx_l = zsh(ufx_l, zo);
+    ufx_v = zsh(ufx_v, zo);
+    ufy_l = zsh(ufy_l, zo);
+    ufy_v = zsh(ufy_v, zo);
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
@@ -334,6 +393,13 @@ __device__ inline double mu_mix(const Phys& p, double vf) { return p.mu_l * vf +
 //   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces).
 __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restrict__ vf, double* __restrict__ cd,
                                 double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    vf = zsh(vf, zo);
+    cd = zsh(cd, zo);
+    dd = zsh(dd, zo);
+    wl = zsh(wl, zo);
+    wb = zsh(wb, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -357,6 +423,17 @@ __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const do
                           const double2* __restrict__ u_l, const double2* __restrict__ u_v,
                           const double2* __restrict__ gc, double2* __restrict__ bx, double2* __restrict__ by,
                           double2* __restrict__ xx, double2* __restrict__ xy) {
+    zphys(g, p);
+    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const long long zo = zoff(g.zs);
+    vf = zsh(vf, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
+    gc = zsh(gc, zo);
+    bx = zsh(bx, zo);
+    by = zsh(by, zo);
+    xx = zsh(xx, zo);
+    xy = zsh(xy, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -380,6 +457,17 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs_f32(Grid g, Phys p, Refl rx
                                                         const double2* __restrict__ gc, double2* __restrict__ bx,
                                                         double2* __restrict__ by, double2* __restrict__ xx,
                                                         double2* __restrict__ xy) {
+    zphys(g, p);
+    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const long long zo = zoff(g.zs);
+    vf = zsh(vf, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
+    gc = zsh(gc, zo);
+    bx = zsh(bx, zo);
+    by = zsh(by, zo);
+    xx = zsh(xx, zo);
+    xy = zsh(xy, zo);
     __shared__ float sh[4][WSY][WSX];
     int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
     int ic = min(i0 + WX / 2, g.nx - 1), jc = min(j0 + WY / 2, g.ny - 1);
@@ -410,6 +498,13 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs_f32(Grid g, Phys p, Refl rx
 // boundary cell, wall/symmetry faces are 0)
 __global__ void k_ustar(Grid g, Phys p, const double2* __restrict__ sx, const double2* __restrict__ sy,
                         const double2* __restrict__ gc, double2* __restrict__ us_l, double2* __restrict__ us_v) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    sx = zsh(sx, zo);
+    sy = zsh(sy, zo);
+    gc = zsh(gc, zo);
+    us_l = zsh(us_l, zo);
+    us_v = zsh(us_v, zo);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.nx * g.ny) return;
     double2 a = gc[c], x = sx[c], y = sy[c];
@@ -420,6 +515,14 @@ __global__ void k_ustar(Grid g, Phys p, const double2* __restrict__ sx, const do
 __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, const double2* __restrict__ us_v,
                             double* __restrict__ fx_l, double* __restrict__ fx_v, double* __restrict__ fy_l,
                             double* __restrict__ fy_v) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    us_l = zsh(us_l, zo);
+    us_v = zsh(us_v, zo);
+    fx_l = zsh(fx_l, zo);
+    fx_v = zsh(fx_v, zo);
+    fy_l = zsh(fy_l, zo);
+    fy_v = zsh(fy_v, zo);
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
@@ -486,6 +589,19 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
                                    const double* __restrict__ fy_l, const double* __restrict__ fy_v,
                                    double* __restrict__ cd, double* __restrict__ dd, double* __restrict__ wl,
                                    double* __restrict__ wb, double* __restrict__ b) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    vf = zsh(vf, zo);
+    flags = zsh(flags, zo);
+    fx_l = zsh(fx_l, zo);
+    fx_v = zsh(fx_v, zo);
+    fy_l = zsh(fy_l, zo);
+    fy_v = zsh(fy_v, zo);
+    cd = zsh(cd, zo);
+    dd = zsh(dd, zo);
+    wl = zsh(wl, zo);
+    wb = zsh(wb, zo);
+    b = zsh(b, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -531,6 +647,16 @@ __device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, 
 __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
                              double* __restrict__ ax, double* __restrict__ ay, double* fx_l, double* fx_v,
                              double* fy_l, double* fy_v) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    P = zsh(P, zo);
+    vf = zsh(vf, zo);
+    ax = zsh(ax, zo);
+    ay = zsh(ay, zo);
+    fx_l = zsh(fx_l, zo);
+    fx_v = zsh(fx_v, zo);
+    fy_l = zsh(fy_l, zo);
+    fy_v = zsh(fy_v, zo);
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
@@ -563,6 +689,15 @@ __global__ void k_project_cells(Grid g, Phys p, const double* __restrict__ axf, 
                                 double2* __restrict__ gc, const double2* __restrict__ us_l,
                                 const double2* __restrict__ us_v, double2* __restrict__ u_l,
                                 double2* __restrict__ u_v) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    axf = zsh(axf, zo);
+    ayf = zsh(ayf, zo);
+    gc = zsh(gc, zo);
+    us_l = zsh(us_l, zo);
+    us_v = zsh(us_v, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -604,6 +739,22 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
                               const double* __restrict__ fy_l, const double* __restrict__ fy_v,
                               double* __restrict__ partial, unsigned* __restrict__ ticket, double* __restrict__ clock,
                               double* __restrict__ out) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    vf = zsh(vf, zo);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    mdot = zsh(mdot, zo);
+    flags = zsh(flags, zo);
+    fx_l = zsh(fx_l, zo);
+    fx_v = zsh(fx_v, zo);
+    fy_l = zsh(fy_l, zo);
+    fy_v = zsh(fy_v, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
+    clock = zsh(clock, zo);
+    out = zsh(out, zo);
     __shared__ double sh[32];
     __shared__ bool lastblk;
     double s[NDIAG_SUMS] = {0, 0, 0, 0, 0};
@@ -671,39 +822,45 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
 // ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
-static inline dim3 rows_grid(int n, int rows, int bs) { return dim3(div_up(n, bs), rows); }
 
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
                      const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st) {
     if (f32w)
-        k_advect_T_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY)), WX * WY, 0, st>>>(
+        k_advect_T_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
             g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l, Ts_v);
     else
-        k_advect_T<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l,
+        k_advect_T<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l,
                                                               u_v, Ts_l, Ts_v);
 }
 
-void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
+void launch_compact(const Grid& g, const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
                     cudaStream_t st) {
-    cudaMemsetAsync(count, 0, sizeof(int), st);
-    k_compact<<<div_up(N, 256), 256, 0, st>>>(flags, N, mask, list, count, idxmap);
+    if (g.nz > 1)   // the count word of every instance of the batch (one stride apart)
+        cudaMemset2DAsync(count, (size_t)g.zs, 0, sizeof(int), g.nz, st);
+    else
+        cudaMemsetAsync(count, 0, sizeof(int), st);
+    k_compact<<<grid1(N, 256, g.nz), 256, 0, st>>>(flags, N, mask, list, count, idxmap, g.zs);
 }
 
-int extend_grid_blocks() { return 4 * 152; }
+// blocks of a band sweep: the band holds at most every cell; four per SM at most
+static int extend_grid_blocks(const Grid& g) {
+    int n = div_up((long long)g.nx * g.ny, 256);
+    return n < 4 * 152 ? n : 4 * 152;
+}
 
 void launch_split_T(const Grid& g, const uint8_t* flags, const double* x, const double* Ts_l, const double* Ts_v,
                     double* T_l, double* T_v, cudaStream_t st) {
     int N = g.nx * g.ny;
-    k_split_T<<<div_up(N, 256), 256, 0, st>>>(N, flags, x, Ts_l, Ts_v, T_l, T_v);
+    k_split_T<<<grid1(N, 256, g.nz), 256, 0, st>>>(N, flags, x, Ts_l, Ts_v, T_l, T_v, g.zs);
 }
 
 void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
                    const int* idxmap, const double2* nb, double* f, double* va, double* vb, cudaStream_t st) {
-    int nb_ = extend_grid_blocks();
+    int nb_ = extend_grid_blocks(g);
     for (int it = 0; it < iters; ++it) {
         const double* cur = (it & 1) ? vb : va;
         double* nxt = (it & 1) ? va : vb;
-        k_extend<<<nb_, 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb, f, cur, nxt,
+        k_extend<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb, f, cur, nxt,
                                       nullptr, nullptr, nullptr);
     }
 }
@@ -711,10 +868,10 @@ void launch_extend(const Grid& g, int mode, int iters, const int* list, const in
 void launch_extend_T(const Grid& g, int iters, const int* list, const int* count, const uint8_t* flags,
                      const int* idxmap, const double2* nb, double* T_l, double* T_v, double* const ext[4],
                      cudaStream_t st) {
-    int nb_ = extend_grid_blocks();
+    int nb_ = extend_grid_blocks(g);
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;
-        k_extend<<<nb_, 256, 0, st>>>(g, 3, it, it == iters - 1, list, count, flags, idxmap, nb, T_l, ext[a],
+        k_extend<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, 3, it, it == iters - 1, list, count, flags, idxmap, nb, T_l, ext[a],
                                       ext[1 - a], T_v, ext[2 + a], ext[3 - a]);
     }
 }
@@ -724,25 +881,25 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, c
                            double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st) {
     double J = 1.0 / p.rho_l - 1.0 / p.rho_v;
     int N = g.nx * g.ny;
-    k_ghost_cells<<<div_up(N, 256), 256, 0, st>>>(g, J, flags, mdot, nb, u_l, u_v);
+    k_ghost_cells<<<grid1(N, 256, g.nz), 256, 0, st>>>(g, J, flags, mdot, nb, u_l, u_v);
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_ghost_faces<<<div_up(nf, 256), 256, 0, st>>>(g, J, flags, mdot, nb, vcol, hpos, vpos, ufx_l, ufx_v, ufy_l,
+    k_ghost_faces<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, J, flags, mdot, nb, vcol, hpos, vpos, ufx_l, ufx_v, ufy_l,
                                                    ufy_v);
 }
 
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
                           double* wl, double* wb, cudaStream_t st) {
-    k_visc_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, comp, vf, cd, dd, wl, wb);
+    k_visc_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, comp, vf, cd, dd, wl, wb);
 }
 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
                     const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, bool f32w,
                     cudaStream_t st) {
     if (f32w)
-        k_mom_rhs_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY)), WX * WY, 0, st>>>(
+        k_mom_rhs_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
             g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
     else
-        k_mom_rhs<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
+        k_mom_rhs<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
                                                              p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
 }
 
@@ -750,15 +907,15 @@ void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2
                   double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
                   cudaStream_t st) {
     int N = g.nx * g.ny;
-    k_ustar<<<div_up(N, 256), 256, 0, st>>>(g, p, sx, sy, gc, us_l, us_v);
+    k_ustar<<<grid1(N, 256, g.nz), 256, 0, st>>>(g, p, sx, sy, gc, us_l, us_v);
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_face_star<<<div_up(nf, 256), 256, 0, st>>>(g, p, us_l, us_v, fx_l, fx_v, fy_l, fy_v);
+    k_face_star<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, us_l, us_v, fx_l, fx_v, fy_l, fy_v);
 }
 
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
                              const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
                              double* cd, double* dd, double* wl, double* wb, double* b, cudaStream_t st) {
-    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v, cd, dd,
+    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v, cd, dd,
                                                                   wl, wb, b);
 }
 
@@ -766,17 +923,21 @@ void launch_project(const Grid& g, const Phys& p, const double* P, const double*
                     double* fx_l, double* fx_v, double* fy_l, double* fy_v, double2* gc, const double2* us_l,
                     const double2* us_v, double2* u_l, double2* u_v, cudaStream_t st) {
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_face_accel<<<div_up(nf, 256), 256, 0, st>>>(g, p, P, vf, ax, ay, fx_l, fx_v, fy_l, fy_v);
-    k_project_cells<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, ax, ay, gc, us_l, us_v, u_l, u_v);
+    k_face_accel<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, P, vf, ax, ay, fx_l, fx_v, fy_l, fy_v);
+    k_project_cells<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, ax, ay, gc, us_l, us_v, u_l, u_v);
 }
 
-int diag_blocks() { return 152; }
+// blocks of the diagnostics reduction: one per SM at most, fewer for small grids
+int diag_blocks(const Grid& g) {
+    int n = div_up((long long)g.nx * g.ny, 1024);
+    return n < 152 ? n : 152;
+}
 
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
                         const double* fx_v, const double* fy_l, const double* fy_v, double* partial,
                         unsigned* ticket, double* clock, double* out, cudaStream_t st) {
-    k_diagnostics<<<diag_blocks(), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v,
+    k_diagnostics<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v,
                                                  partial, ticket, clock, out);
 }
 

@@ -66,6 +66,13 @@ __device__ inline int seg_Q(uint16_t code, int s) { return (code >> (4 + 4 * s))
 __global__ void k_reconstruct(Grid g, const uint8_t* __restrict__ vcol, const double* __restrict__ hpos,
                               const double* __restrict__ vpos, uint16_t* __restrict__ cseg,
                               uint8_t* __restrict__ flags, double* __restrict__ vf) {
+    const long long zo = zoff(g.zs);
+    vcol = zsh(vcol, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    cseg = zsh(cseg, zo);
+    flags = zsh(flags, zo);
+    vf = zsh(vf, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -149,6 +156,12 @@ __global__ void k_reconstruct(Grid g, const uint8_t* __restrict__ vcol, const do
 __global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                        const double* __restrict__ vpos, uint8_t* __restrict__ flags,
                        double2* __restrict__ nb) {
+    const long long zo = zoff(g.zs);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    flags = zsh(flags, zo);
+    nb = zsh(nb, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -188,6 +201,14 @@ __global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* 
 __global__ void k_ug(Grid g, Phys p, const uint8_t* __restrict__ flags, const double2* __restrict__ u_l,
                      const double2* __restrict__ u_v, const double* __restrict__ mdot,
                      const double2* __restrict__ nb, double2* __restrict__ uG) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    flags = zsh(flags, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
+    mdot = zsh(mdot, zo);
+    nb = zsh(nb, zo);
+    uG = zsh(uG, zo);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.nx * g.ny) return;
     double m = mdot[c];
@@ -235,6 +256,15 @@ __global__ void k_displace(Grid g, int axis, double dth, const uint8_t* __restri
                            const double* __restrict__ hpos, const double* __restrict__ vpos,
                            const double2* __restrict__ uG, double* __restrict__ hdisp,
                            double* __restrict__ vdisp, int* __restrict__ status) {
+    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const long long zo = zoff(g.zs);
+    vcol = zsh(vcol, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    uG = zsh(uG, zo);
+    hdisp = zsh(hdisp, zo);
+    vdisp = zsh(vdisp, zo);
+    status = zsh(status, zo);
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nh = (long long)(g.ny + 1) * g.nx;
     long long nv = (long long)g.ny * (g.nx + 1);
@@ -342,6 +372,13 @@ __device__ inline double pick_median(double* c, int n) {
 
 // vertex colours: flip once per aligned marker crossing the vertex
 __global__ void k_sweep_vertices(SweepView sv, uint8_t* __restrict__ vcol_n) {
+    const long long zo = zoff(sv.g.zs);
+    sv.vcol = zsh(sv.vcol, zo);
+    sv.hpos = zsh(sv.hpos, zo);
+    sv.vpos = zsh(sv.vpos, zo);
+    sv.hdisp = zsh(sv.hdisp, zo);
+    sv.vdisp = zsh(sv.vdisp, zo);
+    vcol_n = zsh(vcol_n, zo);
     const Grid& g = sv.g;
     int iv = blockIdx.x * blockDim.x + threadIdx.x;
     int jv = blockIdx.y;
@@ -362,6 +399,14 @@ __global__ void k_sweep_vertices(SweepView sv, uint8_t* __restrict__ vcol_n) {
 
 // aligned edges: the markers that slid onto the edge, one kept (lower median)
 __global__ void k_sweep_aligned(SweepView sv, const uint8_t* __restrict__ vcol_n, double* __restrict__ out) {
+    const long long zo = zoff(sv.g.zs);
+    sv.vcol = zsh(sv.vcol, zo);
+    sv.hpos = zsh(sv.hpos, zo);
+    sv.vpos = zsh(sv.vpos, zo);
+    sv.hdisp = zsh(sv.hdisp, zo);
+    sv.vdisp = zsh(sv.vdisp, zo);
+    vcol_n = zsh(vcol_n, zo);
+    out = zsh(out, zo);
     const Grid& g = sv.g;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int l = blockIdx.y;
@@ -451,6 +496,16 @@ __device__ inline bool chain_neighbour(const SweepView& sv, const uint16_t* cseg
 __global__ void k_sweep_unaligned(SweepView sv, const uint16_t* __restrict__ cseg,
                                   const uint8_t* __restrict__ vcol_n, double* __restrict__ out,
                                   int* __restrict__ status) {
+    const long long zo = zoff(sv.g.zs);
+    sv.vcol = zsh(sv.vcol, zo);
+    sv.hpos = zsh(sv.hpos, zo);
+    sv.vpos = zsh(sv.vpos, zo);
+    sv.hdisp = zsh(sv.hdisp, zo);
+    sv.vdisp = zsh(sv.vdisp, zo);
+    cseg = zsh(cseg, zo);
+    vcol_n = zsh(vcol_n, zo);
+    out = zsh(out, zo);
+    status = zsh(status, zo);
     const Grid& g = sv.g;
     int e = blockIdx.x * blockDim.x + threadIdx.x;   // index across
     int m = blockIdx.y;                               // unaligned line
@@ -591,6 +646,20 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
                                   const double* __restrict__ Ts_v, double* __restrict__ cd,
                                   double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb,
                                   double* __restrict__ b, double* __restrict__ x0) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    flags = zsh(flags, zo);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    Ts_l = zsh(Ts_l, zo);
+    Ts_v = zsh(Ts_v, zo);
+    cd = zsh(cd, zo);
+    dd = zsh(dd, zo);
+    wl = zsh(wl, zo);
+    wb = zsh(wb, zo);
+    b = zsh(b, zo);
+    x0 = zsh(x0, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -651,6 +720,14 @@ __device__ inline double interp_biquadratic(const double* F, const Grid& g, doub
 __global__ void k_mass_flux(Grid g, Phys p, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                             const double* __restrict__ vpos, const double* __restrict__ T_l,
                             const double* __restrict__ T_v, double* __restrict__ mdot) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    T_l = zsh(T_l, zo);
+    T_v = zsh(T_v, zo);
+    mdot = zsh(mdot, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -686,37 +763,36 @@ __global__ void k_mass_flux(Grid g, Phys p, const uint16_t* __restrict__ cseg, c
 // ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
-static inline dim3 rows_grid(int n, int rows, int bs) { return dim3(div_up(n, bs), rows); }
 
 void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, const double* vpos,
                         uint16_t* cseg, uint8_t* flags, double* vf, cudaStream_t st) {
-    k_reconstruct<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, vcol, hpos, vpos, cseg, flags, vf);
+    k_reconstruct<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, vcol, hpos, vpos, cseg, flags, vf);
 }
 
 void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, uint8_t* flags,
                  double2* nb, cudaStream_t st) {
-    k_band<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, cseg, hpos, vpos, flags, nb);
+    k_band<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, cseg, hpos, vpos, flags, nb);
 }
 
 void launch_ug(const Grid& g, const Phys& p, const uint8_t* flags, const double2* u_l, const double2* u_v,
                const double* mdot, const double2* nb, double2* uG, cudaStream_t st) {
     int n = g.nx * g.ny;
-    k_ug<<<div_up(n, 256), 256, 0, st>>>(g, p, flags, u_l, u_v, mdot, nb, uG);
+    k_ug<<<grid1(n, 256, g.nz), 256, 0, st>>>(g, p, flags, u_l, u_v, mdot, nb, uG);
 }
 
 void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, const double* hpos,
                   const double* vpos, const uint16_t* cseg, const double2* uG, double* hdisp, double* vdisp,
                   uint8_t* vcol_n, double* hpos_n, double* vpos_n, int* status, cudaStream_t st) {
     long long ne = (long long)(g.ny + 1) * g.nx + (long long)g.ny * (g.nx + 1);
-    k_displace<<<div_up(ne, 256), 256, 0, st>>>(g, axis, dth, vcol, hpos, vpos, uG, hdisp, vdisp, status);
+    k_displace<<<grid1(ne, 256, g.nz), 256, 0, st>>>(g, axis, dth, vcol, hpos, vpos, uG, hdisp, vdisp, status);
     SweepView sv{g, axis, vcol, hpos, vpos, hdisp, vdisp};
-    k_sweep_vertices<<<rows_grid(g.nx + 1, g.ny + 1, 128), 128, 0, st>>>(sv, vcol_n);
+    k_sweep_vertices<<<rows_grid(g.nx + 1, g.ny + 1, 128, g.nz), 128, 0, st>>>(sv, vcol_n);
     if (axis == 0) {
-        k_sweep_aligned<<<rows_grid(g.nx, g.ny + 1, 128), 128, 0, st>>>(sv, vcol_n, hpos_n);
-        k_sweep_unaligned<<<rows_grid(g.ny, g.nx + 1, 128), 128, 0, st>>>(sv, cseg, vcol_n, vpos_n, status);
+        k_sweep_aligned<<<rows_grid(g.nx, g.ny + 1, 128, g.nz), 128, 0, st>>>(sv, vcol_n, hpos_n);
+        k_sweep_unaligned<<<rows_grid(g.ny, g.nx + 1, 128, g.nz), 128, 0, st>>>(sv, cseg, vcol_n, vpos_n, status);
     } else {
-        k_sweep_aligned<<<rows_grid(g.ny, g.nx + 1, 128), 128, 0, st>>>(sv, vcol_n, vpos_n);
-        k_sweep_unaligned<<<rows_grid(g.nx, g.ny + 1, 128), 128, 0, st>>>(sv, cseg, vcol_n, hpos_n, status);
+        k_sweep_aligned<<<rows_grid(g.ny, g.nx + 1, 128, g.nz), 128, 0, st>>>(sv, vcol_n, vpos_n);
+        k_sweep_unaligned<<<rows_grid(g.nx, g.ny + 1, 128, g.nz), 128, 0, st>>>(sv, cseg, vcol_n, hpos_n, status);
     }
 }
 
@@ -724,13 +800,13 @@ void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, 
                             const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
                             double* cd, double* dd, double* wl, double* wb, double* b, double* x0,
                             cudaStream_t st) {
-    k_energy_operator<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, flags, cseg, hpos, vpos, Ts_l, Ts_v, cd,
+    k_energy_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, flags, cseg, hpos, vpos, Ts_l, Ts_v, cd,
                                                                  dd, wl, wb, b, x0);
 }
 
 void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos,
                       const double* vpos, const double* T_l, const double* T_v, double* mdot, cudaStream_t st) {
-    k_mass_flux<<<rows_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, p, cseg, hpos, vpos, T_l, T_v, mdot);
+    k_mass_flux<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, cseg, hpos, vpos, T_l, T_v, mdot);
 }
 
 }  // namespace ebit

@@ -27,7 +27,8 @@ void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const 
 // f32w: WENO3 nonlinear weights in FP32 (mixed-precision mode)
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
                      const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st);
-void launch_compact(const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap, cudaStream_t st);
+void launch_compact(const Grid& g, const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
+                    cudaStream_t st);
 void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
                    const int* idxmap, const double2* nb, double* f, double* va, double* vb, cudaStream_t st);
 // modes 0 and 1 (T_l into the vapour band, T_v into the liquid band) in one launch per sweep;
@@ -56,7 +57,7 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
 void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* ax, double* ay,
                     double* fx_l, double* fx_v, double* fy_l, double* fy_v, double2* gc, const double2* us_l,
                     const double2* us_v, double2* u_l, double2* u_v, cudaStream_t st);
-int diag_blocks();
+int diag_blocks(const Grid& g);
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
                         const double* fx_v, const double* fy_l, const double* fy_v, double* partial, unsigned* ticket,

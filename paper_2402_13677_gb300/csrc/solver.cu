@@ -65,6 +65,7 @@ struct Lev {
     const T* diag;
     const T* wl;
     const T* wb;
+    long long zs;   // byte stride between the instances of a batched launch (0: one instance)
 };
 
 __device__ inline bool skip(const SolveState* s) { return s->done != 0 || s->odone != 0; }
@@ -140,8 +141,18 @@ __device__ inline bool grid_reduce(const double* v, double* partial, unsigned* t
     return threadIdx.x == 0;
 }
 
+// use 1: the loop condition is this solve's own (assigned); use 2: a batched launch, where the
+// condition is the OR over the instances (reset to 0 at the top of each loop body by
+// k_cond_reset, raised to 1 by every instance that continues)
 __device__ inline void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
-    if (use) cudaGraphSetConditional(h, v);
+    if (use == 1 || (use == 2 && v)) cudaGraphSetConditional(h, v);
+}
+
+__global__ void k_cond_reset(cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1, int two) {
+    if (threadIdx.x == 0) {
+        cudaGraphSetConditional(h0, 0u);
+        if (two) cudaGraphSetConditional(h1, 0u);
+    }
 }
 
 // ---- operator setup -------------------------------------------------------------------
@@ -455,6 +466,15 @@ __global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, N
                                                                   SolveState* st, KTimer* tm,
                                                                   const __grid_constant__ TileMaps maps,
                                                                   int use_tma) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    b = zsh(b, zo);
+    x = zsh(x, zo);
+    bc = zsh(bc, zo);
+    st = zsh(st, zo);
+    tm = zsh(tm, zo);
     if (skip(st)) return;
     constexpr int H = 2 * NU + 1;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
@@ -528,6 +548,18 @@ __global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>()
                                                                double* partial, unsigned* ticket, KTimer* tm,
                                                                const __grid_constant__ TileMaps maps,
                                                                int use_tma) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    b = zsh(b, zo);
+    xin = zsh(xin, zo);
+    x = zsh(x, zo);
+    xc = zsh(xc, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
+    tm = zsh(tm, zo);
     if (skip(st)) return;
     constexpr int H = 2 * NU;
     using Rg = Region<T, NR, H>;
@@ -588,6 +620,7 @@ struct SmallPlan {
     int soff[Solver::MAXLEV];   // cell offset of each small level inside the shared-memory arrays
     size_t goff[Solver::MAXLEV]; // cell offset in the packed global level arrays
     int total;         // cells of all small levels
+    long long zs;      // byte stride between the instances of a batched launch
 };
 
 // shared-memory layout: x[NR*total], b[NR*total], diag[total], wl[total], wb[total]
@@ -651,6 +684,14 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
                                                          const T* __restrict__ wl, const T* __restrict__ wb,
                                                          const T* __restrict__ inv, const T* __restrict__ b_in,
                                                          T* __restrict__ x_out, SolveState* st) {
+    const long long zo = zoff(P.zs);
+    diag = zsh(diag, zo);
+    wl = zsh(wl, zo);
+    wb = zsh(wb, zo);
+    inv = zsh(inv, zo);
+    b_in = zsh(b_in, zo);
+    x_out = zsh(x_out, zo);
+    st = zsh(st, zo);
     if (skip(st)) return;
     extern __shared__ __align__(128) unsigned char smem[];
     SmallMem<T, NR> M(smem, P.total);
@@ -845,6 +886,7 @@ __device__ inline void coarse_inverse_warp(int nx, int ny, const T* __restrict__
 struct SetupPlan {
     int nlev, nx[Solver::MAXLEV], ny[Solver::MAXLEV];
     size_t off[Solver::MAXLEV];
+    long long zs;      // byte stride between the instances of a batched launch
 };
 
 // The whole multigrid hierarchy in precision T in one launch.  Block (bx, by) converts its
@@ -858,6 +900,19 @@ __global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* _
                                                     const double* __restrict__ dd, const double* __restrict__ wl,
                                                     const double* __restrict__ wb, T* diag, T* owl, T* owb, T* ocd,
                                                     T* odd, double* __restrict__ d64, T* inv, unsigned* ticket) {
+    const long long zo = zoff(P.zs);
+    cd = zsh(cd, zo);
+    dd = zsh(dd, zo);
+    wl = zsh(wl, zo);
+    wb = zsh(wb, zo);
+    diag = zsh(diag, zo);
+    owl = zsh(owl, zo);
+    owb = zsh(owb, zo);
+    ocd = zsh(ocd, zo);
+    odd = zsh(odd, zo);
+    d64 = zsh(d64, zo);
+    inv = zsh(inv, zo);
+    ticket = zsh(ticket, zo);
     int nx = P.nx[0], ny = P.ny[0];
     for (int k = threadIdx.x; k < SB * SB; k += blockDim.x) {
         int i = blockIdx.x * SB + k % SB, j = blockIdx.y * SB + k / SB;
@@ -933,6 +988,17 @@ template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z, T* __restrict__ p0,
                                                 T* __restrict__ p1, T* __restrict__ q, SolveState* st,
                                                 double* partial, unsigned* ticket) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    z = zsh(z, zo);
+    p0 = zsh(p0, zo);
+    p1 = zsh(p1, zo);
+    q = zsh(q, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
     if (skip(st)) return;
     const Vec<T, NR>* __restrict__ Z = reinterpret_cast<const Vec<T, NR>*>(z);
     const Vec<T, NR>* __restrict__ Po = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p1 : p0);
@@ -980,10 +1046,20 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
 
 // x += alpha p_new; r -= alpha q; r.r; convergence test; loop condition
 template <typename T, int NR>
-__global__ void __launch_bounds__(256) k_update(int N, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p0,
+__global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restrict__ x, T* __restrict__ r,
+                                                 const T* __restrict__ p0,
                                                  const T* __restrict__ p1, const T* __restrict__ q, SolveState* st,
                                                  double* partial, unsigned* ticket, cudaGraphConditionalHandle h,
                                                  int use_h) {
+    const long long zo = zoff(zs);
+    x = zsh(x, zo);
+    r = zsh(r, zo);
+    p0 = zsh(p0, zo);
+    p1 = zsh(p1, zo);
+    q = zsh(q, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
     if (skip(st)) return;
     const Vec<T, NR>* __restrict__ Pn = reinterpret_cast<const Vec<T, NR>*>((st->iters & 1) ? p0 : p1);
     const Vec<T, NR>* __restrict__ Q = reinterpret_cast<const Vec<T, NR>*>(q);
@@ -1027,6 +1103,16 @@ __global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __r
                                                  double* __restrict__ r, SolveState* st, double* partial,
                                                  unsigned* ticket, double rtol2, int max_iters,
                                                  cudaGraphConditionalHandle h, int use_h) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    b = zsh(b, zo);
+    x = zsh(x, zo);
+    r = zsh(r, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
     int N = L.nx * L.ny;
     double acc[2 * NR];
 #pragma unroll
@@ -1077,9 +1163,15 @@ __global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __r
 
 // refinement start: b.b and the outer tolerance
 template <int NR>
-__global__ void __launch_bounds__(256) k_ir_init(int N, const double* __restrict__ b, SolveState* st, double* partial,
+__global__ void __launch_bounds__(256) k_ir_init(int N, long long zs, const double* __restrict__ b, SolveState* st,
+                                                  double* partial,
                                                   unsigned* ticket, double rtol2, double inner_rtol, int max_iters,
                                                   int max_outer) {
+    const long long zo = zoff(zs);
+    b = zsh(b, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
@@ -1114,6 +1206,17 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
                                                       float* __restrict__ e32, SolveState* st, double* partial,
                                                       unsigned* ticket, cudaGraphConditionalHandle ho,
                                                       cudaGraphConditionalHandle hi, int use_h) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    b = zsh(b, zo);
+    x = zsh(x, zo);
+    r32 = zsh(r32, zo);
+    e32 = zsh(e32, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
     if (st->odone) return;
     int N = L.nx * L.ny;
     double acc[NR];
@@ -1166,7 +1269,12 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
 }
 
 template <int NR>
-__global__ void k_ir_update(int N, double* __restrict__ x, const float* __restrict__ e, const SolveState* st) {
+__global__ void k_ir_update(int N, long long zs, double* __restrict__ x, const float* __restrict__ e,
+                            const SolveState* st) {
+    const long long zo = zoff(zs);
+    x = zsh(x, zo);
+    e = zsh(e, zo);
+    st = zsh(st, zo);
     if (st->odone) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N * NR; c += gridDim.x * blockDim.x)
         x[c] += (double)e[c];
@@ -1402,16 +1510,17 @@ static void ensure_tile_maps(Solver& s) {
 template <typename T>
 static Lev<T> lev(Solver& s, int l) {
     size_t o = s.loff[l];
-    return {s.lnx[l], s.lny[l], PT<T>::diag(s) + o, PT<T>::wl(s) + o, PT<T>::wb(s) + o};
+    return {s.lnx[l], s.lny[l], PT<T>::diag(s) + o, PT<T>::wl(s) + o, PT<T>::wb(s) + o, s.zs};
 }
 
 template <typename T>
 static void setup_levels(Solver& s, const double* cd, const double* dd, const double* wl, const double* wb,
                          double* d64, cudaStream_t stm) {
     SetupPlan P;
+    P.zs = s.zs;
     P.nlev = s.nlev;
     for (int l = 0; l < s.nlev; ++l) { P.nx[l] = s.lnx[l]; P.ny[l] = s.lny[l]; P.off[l] = s.loff[l]; }
-    dim3 grid((s.nx + SB - 1) / SB, (s.ny + SB - 1) / SB);
+    dim3 grid((s.nx + SB - 1) / SB, (s.ny + SB - 1) / SB, s.nz);
     k_setup_tree<T><<<grid, 256, 0, stm>>>(P, cd, dd, wl, wb, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s),
                                            PT<T>::cd(s), PT<T>::dd(s), d64, PT<T>::inv(s), s.tickets + 6);
     ++s.launches;
@@ -1425,6 +1534,7 @@ template <> int nbig_of<double>(const Solver& s) { return s.nbig_d; }
 template <typename T>
 static SmallPlan small_plan(const Solver& s) {
     SmallPlan P;
+    P.zs = s.zs;
     int nb = nbig_of<T>(s);
     P.n = s.nlev - nb;
     int so = 0;
@@ -1455,10 +1565,10 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
     const int pr = PT<T>::prec;
     for (int l = 0; l < nb; ++l) {
         Lev<T> L = lev<T>(s, l);
-        dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
+        dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, s.nz);
         T* bc = B + 2 * s.loff[l + 1];
         size_t ix = tmap_index(pr, NR, l, 0);
-        int tma = s.use_tma && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
+        int tma = s.use_tma && s.nz == 1 && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
         using Rg = Region<T, NR, 2 * NU + 1>;
         size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, 2 * NU + 1, false>::BYTES : Rg::bytes();
         k_pre<T, NR><<<grid, tile_block<2 * NU + 1>(), smem, stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
@@ -1473,22 +1583,22 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         T* x = nb == 0 ? z : X + 2 * s.loff[nb];
         const T* inv = PT<T>::inv(s);
         if (nb == 0)
-            k_small<T, NR, true><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
+            k_small<T, NR, true><<<dim3(1, 1, s.nz), SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
                                                                   b, x, st);
         else
-            k_small<T, NR, false><<<1, SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
+            k_small<T, NR, false><<<dim3(1, 1, s.nz), SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
                                                                    b, x, st);
         if (!s.use_graph) ++s.launches;
     }
     for (int l = nb - 1; l >= 0; --l) {
         Lev<T> L = lev<T>(s, l);
-        dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
+        dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, s.nz);
         const T* bl = l == 0 ? r : B + 2 * s.loff[l];
         const T* xin = X2 + 2 * s.loff[l];
         T* xout = l == 0 ? z : X + 2 * s.loff[l];
         const T* xc = X + 2 * s.loff[l + 1];
         size_t ix = tmap_index(pr, NR, l, 1);
-        int tma = s.use_tma && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
+        int tma = s.use_tma && s.nz == 1 && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
         using Rg = Region<T, NR, 2 * NU>;
         size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, 2 * NU, true>::BYTES : Rg::bytes();
         KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
@@ -1506,12 +1616,14 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
 template <typename T, int NR>
 static void cg_body(Solver& s, T* x, T* r, T* z, T* p, T* q, SolveState* st, cudaGraphConditionalHandle h, int use_h,
                     cudaStream_t stm) {
+    if (use_h == 2) k_cond_reset<<<1, 32, 0, stm>>>(h, h, 0);
     vcycle<T, NR>(s, r, z, st, stm);
     int N = s.nx * s.ny;
     Lev<T> L0 = lev<T>(s, 0);
     T* p1 = p + (size_t)N * NR;
-    k_apply<T, NR><<<nblocks(N), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1);
-    k_update<T, NR><<<nblocks(N), RB, 0, stm>>>(N, x, r, p, p1, q, st, s.partial, s.tickets + 2, h, use_h);
+    k_apply<T, NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1);
+    k_update<T, NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial, s.tickets + 2,
+                                                               h, use_h);
     if (!s.use_graph) s.launches += 2;
 }
 
@@ -1576,15 +1688,17 @@ static void solve_fp64(Solver& s, const double* b, double* x, double rtol, int m
     if (s.use_graph) {
         cudaGraph_t g;
         cudaGraphConditionalHandle h = make_handle(stm, &g);
-        k_init64<NR><<<nblocks(N), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets, rtol * rtol, max_iter,
-                                                 h, 1);
+        int mode = s.nz > 1 ? 2 : 1;
+        k_init64<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets,
+                                                                rtol * rtol, max_iter, h, mode);
         ++s.launches;
         cudaStream_t bs = begin_while(stm, s.aux[0], h);
-        cg_body<double, NR>(s, x, s.d_r, z, s.d_p, s.d_q, s.st, h, 1, bs);
+        cg_body<double, NR>(s, x, s.d_r, z, s.d_p, s.d_q, s.st, h, mode, bs);
         end_while(bs);
         return;
     }
-    k_init64<NR><<<nblocks(N), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets, rtol * rtol, max_iter, 0, 0);
+    k_init64<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets,
+                                                            rtol * rtol, max_iter, 0, 0);
     ++s.launches;
     poll(s, stm);
     for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
@@ -1600,8 +1714,8 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
     const int max_outer = 8;
     const double inner_rtol = 1e-5;
     float* z = s.f_x;
-    k_ir_init<NR><<<nblocks(N), RB, 0, stm>>>(N, b, s.st, s.partial, s.tickets + 3, rtol * rtol, inner_rtol, max_iter,
-                                              max_outer);
+    k_ir_init<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(N, s.zs, b, s.st, s.partial, s.tickets + 3,
+                                                             rtol * rtol, inner_rtol, max_iter, max_outer);
     ++s.launches;
     if (s.use_graph) {
         cudaGraph_t g;
@@ -1609,17 +1723,20 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
         cudaStream_t obs = begin_while(stm, s.aux[0], ho);
         cudaGraph_t og;
         cudaGraphConditionalHandle hi = make_handle(obs, &og);
-        k_ir_residual<NR><<<nblocks(N), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial, s.tickets + 5, ho, hi,
-                                                      1);
+        int mode = s.nz > 1 ? 2 : 1;
+        if (mode == 2) k_cond_reset<<<1, 32, 0, obs>>>(ho, hi, 1);
+        k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                                     s.tickets + 5, ho, hi, mode);
         cudaStream_t ibs = begin_while(obs, s.aux[1], hi);
-        cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, hi, 1, ibs);
+        cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, hi, mode, ibs);
         end_while(ibs);
-        k_ir_update<NR><<<nblocks(N * NR), RB, 0, obs>>>(N, x, s.f_e, s.st);
+        k_ir_update<NR><<<dim3(nblocks(N * NR), 1, s.nz), RB, 0, obs>>>(N, s.zs, x, s.f_e, s.st);
         end_while(obs);
         return;
     }
     for (int o = 0; o <= max_outer; ++o) {
-        k_ir_residual<NR><<<nblocks(N), RB, 0, stm>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial, s.tickets + 5, 0, 0, 0);
+        k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                                     s.tickets + 5, 0, 0, 0);
         ++s.launches;
         poll(s, stm);
         if (s.st_host[s.slot].odone) break;
@@ -1627,7 +1744,7 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
             cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, 0, 0, stm);
             poll(s, stm);
         }
-        k_ir_update<NR><<<nblocks(N * NR), RB, 0, stm>>>(N, x, s.f_e, s.st);
+        k_ir_update<NR><<<dim3(nblocks(N * NR), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, s.f_e, s.st);
         ++s.launches;
     }
 }
@@ -1644,7 +1761,7 @@ void Solver::solve(const double* cd, const double* dd, const double* wl, const d
         // the FP32 hierarchy, plus D in FP64 for the refinement residual (whose face weights are
         // the caller's FP64 arrays)
         setup_levels<float>(*this, cd, dd, wl, wb, d_diag, stm);
-        Lev<double> L64{nx, ny, d_diag, wl, wb};
+        Lev<double> L64{nx, ny, d_diag, wl, wb, zs};
         if (nr == 1) solve_mixed<1>(*this, L64, b, x, rtol, max_iter, stm);
         else solve_mixed<2>(*this, L64, b, x, rtol, max_iter, stm);
     }

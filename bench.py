@@ -50,7 +50,7 @@ METRIC = "cell-steps/s at 1 GPU, FP32+refine vs FP64, 1e-8 rel residual; %HBM ro
 # of the current kernels (summary and command in the named profiles/ file); an entry is removed
 # whenever those kernels change, so that a stale figure is never reported
 SMOOTH_L0_TRAFFIC = {
-    "c2_bubble_512": {"dram_bytes_per_launch": 5.17e6,
+    "c2_bubble_512": {"dram_bytes_per_launch": 5.27e6,
                       "summary": "profiles/smoother_l0_traffic_c2_bubble_512.md"},
 }
 
@@ -239,6 +239,8 @@ def run_ours(args):
                            {"T_l": pb.T_l, "T_v": pb.T_v, "u_l": pb.u_l, "u_v": pb.u_v, "ufx_l": pb.ufx_l,
                             "ufx_v": pb.ufx_v, "ufy_l": pb.ufy_l, "ufy_v": pb.ufy_v, "p": pb.p}, pb.t0)
         E.ebit_run_stage(ctx, E.STAGE_PREPARE)
+        if not args.no_graph and not args.no_autotune:
+            E.ebit_autotune(ctx, 2)   # multigrid schedule per batch / instance (state restored)
         return ctx
 
     def timed_steps(ctx, k, with_timing=False):
@@ -288,6 +290,12 @@ def run_ours(args):
             secs = barrier_max(secs)
             d = E.ebit_get_diagnostics(ctx, 0)
             results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist())
+            sched = {}
+            for b in range(len(pbs)):
+                sm, it, tm = E.ebit_get_schedule(ctx, b)
+                key = f"small_max={sm} inner_rtol={it:g} tma={tm}"
+                sched[key] = sched.get(key, 0) + 1
+            results[name]["schedule"] = sched
             if not args.profile_only and rank == 0:
                 results[name]["final"] = [E.download(ctx, b, pbs[b].nx, pbs[b].ny,
                                                      ["T_l", "T_v", "p", "u_l", "u_v", "vcol", "hx_pos", "vy_pos"])
@@ -413,7 +421,9 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": int(mixed["launches"]),
-        "solver": {"mixed_diag": mixed["diag"], "fp64_diag": fp64["diag"]},
+        "solver": {"mixed_diag": mixed["diag"], "fp64_diag": fp64["diag"],
+                   "schedule_mixed": mixed["schedule"], "schedule_fp64": fp64["schedule"],
+                   "autotuned": not args.no_autotune and not args.no_graph},
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -438,6 +448,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels from the host (profilers)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
     args = ap.parse_args()
     global BATCH_COUNT
     BATCH_COUNT = args.batch_count

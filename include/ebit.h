@@ -230,6 +230,22 @@ ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const dou
                                       const double* b, double* x, int nr, int precision, double rtol, int max_iter,
                                       void* stream, int* iters, double* rel_res);
 
+/* Autotuning of the multigrid schedule (the paper has no counterpart; a deployment feature of
+ * the library's solver).  For every batch of instances sharing launches, and every instance
+ * stepped alone, times `trial_steps` graph-replayed steps (after one untimed step) of each
+ * candidate schedule and keeps the fastest:
+ *   - the size of the largest level solved inside the single-block kernel: 256, 1024 or 4096
+ *     cells, the values that change the level split of this grid;
+ *   - the relative tolerance of the refinement's inner FP32 solves: 1e-4 or 1e-5 (mixed
+ *     precision only);
+ *   - TMA staging of the tile regions on or off (instances stepped alone).
+ * The state of every instance (fields, markers, time, step counter) is restored afterwards
+ * from a device snapshot of the largest unit's arena, which is allocated with cudaMalloc for
+ * the duration of the call.  Needs graph mode.  EBIT_ENOMEM when the snapshot does not fit. */
+ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps);
+/* The schedule an instance uses: single-block level size, inner tolerance, TMA staging. */
+ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma);
+
 /* Options:
  *   EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the context's
  *   stream (solver loops as conditional WHILE nodes, no host round trip inside a step); 0

@@ -826,6 +826,134 @@ ebit_status ebit_step(ebit_ctx* ctx, int nsteps) {
     return worst;
 }
 
+// ---- autotuning of the multigrid schedule ------------------------------------------------
+// A unit is a batch or an instance stepped alone; its arena, step counter and schedule.
+struct Unit {
+    std::vector<int> members;
+    Batch* batch = nullptr;
+    char* arena = nullptr;
+    size_t bytes = 0;
+};
+
+static void apply_schedule(ebit_ctx* ctx, Unit& U, int small_max, double inner, int tma) {
+    auto set = [&](Instance& I) {
+        I.solver.set_schedule(small_max, inner);
+        I.solver.use_tma = tma;
+        for (auto& gx : I.graph)
+            if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+    };
+    for (int m : U.members) set(ctx->inst[m]);
+    if (U.batch) {
+        for (auto& gx : U.batch->graph)
+            if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+        U.batch->lead.batch = -1;   // rebuilt from the first member on the next replay
+    }
+}
+
+// one step of the unit on the context stream, with the status check of its members
+static ebit_status step_unit(ebit_ctx* ctx, Unit& U) {
+    ebit_status r = U.batch ? replay_batch(ctx, *U.batch, ctx->stream) : replay_step(ctx, ctx->inst[U.members[0]], ctx->stream);
+    if (r != EBIT_OK) return r;
+    return check_status(ctx, true);
+}
+
+ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps) {
+    if (!ctx || trial_steps < 1) return EBIT_EINVAL;
+    if (!ctx->use_graph || !ctx->stream) return fail(ctx, EBIT_EINVAL, "autotuning times graph replays (graph mode)");
+    for (auto& I : ctx->inst)
+        if (!I.props_set) return fail(ctx, EBIT_EINVAL, "ebit_set_phase_props not called");
+    std::vector<Unit> units;
+    for (auto& B : ctx->batches) {
+        Unit U;
+        U.members = B.members;
+        U.batch = &B;
+        U.arena = (char*)B.arena;
+        U.bytes = B.stride * B.members.size();
+        units.push_back(U);
+    }
+    for (size_t b = 0; b < ctx->inst.size(); ++b) {
+        Instance& I = ctx->inst[b];
+        if (I.batch >= 0) continue;
+        Unit U;
+        U.members = {(int)b};
+        U.arena = (char*)I.arena;
+        U.bytes = I.arena_bytes;
+        units.push_back(U);
+    }
+    size_t most = 0;
+    for (auto& U : units) most = U.bytes > most ? U.bytes : most;
+    void* snap = nullptr;
+    if (cudaMalloc(&snap, most) != cudaSuccess) return fail(ctx, EBIT_ENOMEM, "no room for the autotuning snapshot");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ebit_status status = EBIT_OK;
+    for (auto& U : units) {
+        Instance& I0 = ctx->inst[U.members[0]];
+        std::vector<long long> nstep0;
+        for (int m : U.members) nstep0.push_back(ctx->inst[m].nstep);
+        cudaMemcpyAsync(snap, U.arena, U.bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        auto restore = [&]() {
+            cudaMemcpyAsync(U.arena, snap, U.bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+            for (size_t z = 0; z < U.members.size(); ++z) ctx->inst[U.members[z]].nstep = nstep0[z];
+        };
+        // candidates: single-block threshold x inner tolerance (mixed) x TMA staging (alone)
+        std::vector<int> smalls;
+        int last_nbig = -1;
+        for (int sm : {256, 1024, 4096}) {
+            Solver probe = I0.solver;
+            probe.set_schedule(sm, 1e-5);
+            if (probe.nbig_f != last_nbig) { smalls.push_back(sm); last_nbig = probe.nbig_f; }
+        }
+        std::vector<double> inners = I0.cfg.precision == EBIT_MIXED ? std::vector<double>{1e-4, 1e-5}
+                                                                    : std::vector<double>{1e-5};
+        std::vector<int> tmas = U.batch ? std::vector<int>{0} : std::vector<int>{1, 0};
+        float best = 1e30f;
+        int bs = I0.solver.small_max_f, bt = I0.solver.use_tma;
+        double bi = I0.solver.inner_rtol;
+        for (int sm : smalls)
+            for (double in : inners)
+                for (int tm : tmas) {
+                    apply_schedule(ctx, U, sm, in, tm);
+                    restore();
+                    ebit_status r = step_unit(ctx, U);   // captures the graphs, warms up
+                    if (r == EBIT_OK || r == EBIT_ENOCONV) {
+                        cudaEventRecord(e0, ctx->stream);
+                        for (int k = 0; k < trial_steps && (r == EBIT_OK || r == EBIT_ENOCONV); ++k)
+                            r = U.batch ? replay_batch(ctx, *U.batch, ctx->stream)
+                                        : replay_step(ctx, I0, ctx->stream);
+                        cudaEventRecord(e1, ctx->stream);
+                        ebit_status c = check_status(ctx, true);
+                        float ms = 0.0f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if ((r == EBIT_OK || r == EBIT_ENOCONV) && c == EBIT_OK && ms < best) {
+                            best = ms;
+                            bs = sm;
+                            bi = in;
+                            bt = tm;
+                        }
+                    }
+                }
+        apply_schedule(ctx, U, bs, bi, bt);
+        restore();
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (status == EBIT_OK) status = cuda_check(ctx, "ebit_autotune");
+    return status;
+}
+
+ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !small_max || !inner_rtol || !tma) return EBIT_EINVAL;
+    const Solver& s = ctx->inst[inst].solver;
+    *small_max = s.small_max_f;
+    *inner_rtol = s.inner_rtol;
+    *tma = s.use_tma;
+    return EBIT_OK;
+}
+
 ebit_status ebit_solve_system(ebit_ctx* ctx, int inst, const double* D, const double* wl, const double* wb,
                               const double* b, double* x, int nr, int precision, double rtol, int max_iter,
                               int* iters, double* rel_res) {

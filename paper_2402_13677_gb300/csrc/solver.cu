@@ -46,7 +46,8 @@ namespace ebit {
 
 constexpr int RB = 256;          // threads of grid-stride kernels
 constexpr int NRED = 608;        // blocks of grid-stride kernels (4 x 152 SMs)
-constexpr int SMALL_MAX_F = 1024; // levels with at most this many cells run inside k_small (FP32)
+constexpr int SMALL_MAX_F = 1024; // default: levels with at most this many cells run inside k_small (FP32)
+constexpr int SMALL_MAX_F_LIMIT = 4096;   // the shared memory of k_small holds at most this level
 constexpr int SMALL_MAX_D = 1024; // (FP64: half the shared memory per value)
 constexpr int SMALL_THREADS = 1024;
 constexpr int TX = 32, TY = 32;  // tile of the large-level kernels
@@ -1306,8 +1307,9 @@ void Solver::plan(int nx_, int ny_) {
         y /= 2;
     }
     ncells_all = off;
+    if (small_max_f <= 0) small_max_f = SMALL_MAX_F;
     nbig_f = 0;
-    while (nbig_f < nlev - 1 && (long long)lnx[nbig_f] * lny[nbig_f] > SMALL_MAX_F) ++nbig_f;
+    while (nbig_f < nlev - 1 && (long long)lnx[nbig_f] * lny[nbig_f] > small_max_f) ++nbig_f;
     nbig_d = 0;
     while (nbig_d < nlev - 1 && (long long)lnx[nbig_d] * lny[nbig_d] > SMALL_MAX_D) ++nbig_d;
     nbig = nbig_f;
@@ -1712,7 +1714,7 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
                         cudaStream_t stm) {
     int N = s.nx * s.ny;
     const int max_outer = 8;
-    const double inner_rtol = 1e-5;
+    const double inner_rtol = s.inner_rtol;
     float* z = s.f_x;
     k_ir_init<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(N, s.zs, b, s.st, s.partial, s.tickets + 3,
                                                              rtol * rtol, inner_rtol, max_iter, max_outer);
@@ -1765,6 +1767,18 @@ void Solver::solve(const double* cd, const double* dd, const double* wl, const d
         if (nr == 1) solve_mixed<1>(*this, L64, b, x, rtol, max_iter, stm);
         else solve_mixed<2>(*this, L64, b, x, rtol, max_iter, stm);
     }
+}
+
+bool Solver::set_schedule(int small_max, double inner) {
+    if (small_max < 16 || small_max > SMALL_MAX_F_LIMIT || !(inner > 0 && inner < 1)) return false;
+    small_max_f = small_max;
+    inner_rtol = inner;
+    int nb = 0;
+    while (nb < nlev - 1 && (long long)lnx[nb] * lny[nb] > small_max_f) ++nb;
+    nbig_f = nb;
+    nbig = nbig_f;
+    tma_ready = false;
+    return true;
 }
 
 int Solver::body_size(int precision) const { return 2 * (precision == 0 ? nbig_d : nbig_f) + 1 + 2; }

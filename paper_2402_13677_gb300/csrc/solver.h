@@ -87,6 +87,11 @@ struct Solver {
     // solvers of instances 1..nz-1 are bound to their own arenas, read only for statistics)
     int nz = 1;
     long long zs = 0;
+    // schedule (tunable): levels with at most small_max_f cells run in the single-block kernel
+    // (FP32); the refinement's inner FP32 solves stop at inner_rtol
+    int small_max_f = 0;   // 0: the default
+    double inner_rtol = 1e-5;
+    bool set_schedule(int small_max, double inner);
 
     void plan(int nx, int ny);
     static size_t bytes(int nx, int ny);

@@ -36,7 +36,7 @@ FIELD_DTYPES = {F_CCOL: np.uint8, F_BAND: np.uint8, F_VCOL: np.uint8, F_CSEG: np
 EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_field", "ebit_get_field",
            "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
            "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_set_option", "ebit_solve_system",
-           "ebit_solve_system_noalloc", "ebit_last_error",
+           "ebit_solve_system_noalloc", "ebit_autotune", "ebit_get_schedule", "ebit_last_error",
            "ebit_destroy", "ebit_version"]
 EBIT_OPT_GRAPH = 1
 EBIT_OPT_TMA = 2
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     lib.ebit_solve_system_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, f64, i32, vp,
                                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.ebit_timing_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
+    lib.ebit_autotune.argtypes = [vp, i32]
+    lib.ebit_get_schedule.argtypes = [vp, i32, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.ebit_last_error.argtypes = [vp]
     lib.ebit_last_error.restype = C.c_char_p
     lib.ebit_destroy.argtypes = [vp]
@@ -235,6 +237,18 @@ def ebit_timing_end(ctx):
 
 def ebit_set_option(ctx, option, value):
     _check(ctx, load().ebit_set_option(ctx, option, value))
+
+
+def ebit_autotune(ctx, trial_steps=2):
+    """Time candidate multigrid schedules per batch / instance, keep the fastest (state restored)."""
+    _check(ctx, load().ebit_autotune(ctx, trial_steps))
+
+
+def ebit_get_schedule(ctx, inst):
+    """(single-block level size, inner FP32 tolerance, TMA staging) of an instance."""
+    sm, it, tm = C.c_int(), C.c_double(), C.c_int()
+    _check(ctx, load().ebit_get_schedule(ctx, inst, C.byref(sm), C.byref(it), C.byref(tm)))
+    return sm.value, it.value, tm.value
 
 
 def ebit_solve_system(ctx, inst, D, wl, wb, b, x0=None, nr=1, precision=EBIT_FP64, rtol=1e-10, max_iter=500,

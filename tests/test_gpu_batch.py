@@ -98,3 +98,32 @@ def test_batched_instance_matches_oracle(dev):
     t_scale = max(np.max(np.abs(st.T_l)), np.max(np.abs(st.T_v)))
     for k in ("T_l", "T_v"):
         assert np.max(np.abs(g[k] - getattr(st, k))) <= TOL64 * t_scale, k
+
+
+def test_autotune_restores_state_and_picks_a_candidate(dev):
+    pbs = batch_problems()[:6]
+    ctx = make_ctx(dev, pbs, E.EBIT_MIXED)
+    try:
+        before = [E.download(ctx, b, pb.nx, pb.ny, NAMES) for b, pb in enumerate(pbs)]
+        E.ebit_autotune(ctx, 1)
+        after = [E.download(ctx, b, pb.nx, pb.ny, NAMES) for b, pb in enumerate(pbs)]
+        for b in range(len(pbs)):
+            for k in NAMES:
+                assert np.array_equal(before[b][k], after[b][k]), (b, k)
+            small, inner, tma = E.ebit_get_schedule(ctx, b)
+            assert small in (256, 1024, 4096) and inner in (1e-4, 1e-5) and tma in (0, 1)
+        E.ebit_step(ctx, 1)   # the tuned schedules step normally
+        tuned = [E.download(ctx, b, pb.nx, pb.ny, ("T_l", "T_v", "vcol")) for b, pb in enumerate(pbs)]
+    finally:
+        E.ebit_destroy(ctx)
+    ref_ctx = make_ctx(dev, pbs, E.EBIT_MIXED)
+    try:
+        E.ebit_step(ref_ctx, 1)
+        for b, pb in enumerate(pbs):
+            ref = E.download(ref_ctx, b, pb.nx, pb.ny, ("T_l", "T_v", "vcol"))
+            assert np.array_equal(tuned[b]["vcol"], ref["vcol"])
+            scale = max(np.max(np.abs(ref["T_l"])), np.max(np.abs(ref["T_v"])))
+            for k in ("T_l", "T_v"):   # both solved to the same relative residual
+                assert np.max(np.abs(tuned[b][k] - ref[k])) <= 1e-6 * scale, (b, k)
+    finally:
+        E.ebit_destroy(ref_ctx)

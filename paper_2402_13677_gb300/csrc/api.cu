@@ -36,6 +36,7 @@ struct Instance {
     double *ufx_l, *ufx_v, *ufy_l, *ufy_v;
     // linear systems
     double *op_cd, *op_dd, *op_wl, *op_wb, *op_b, *op_x;
+    double *op2_cd, *op2_dd, *op2_wl, *op2_wb;   // the second viscous component's operator
     double2 *vbx, *vby, *vxx, *vxy;   // viscous RHS / solutions, liquid and vapour interleaved
     // band compaction + extension values
     int *band_list, *band_count, *band_idx;
@@ -46,6 +47,9 @@ struct Instance {
     unsigned* diag_ticket;
     int* status;
     Solver solver;
+    Solver solver2;          // the second viscous component's solve (runs beside the first in graphs)
+    cudaStream_t side = nullptr;   // capture branch of the second viscous solve (the context's)
+    cudaEvent_t e_fork = nullptr, e_join = nullptr;   // its fork / join while capturing
     void* arena = nullptr;
     size_t arena_bytes = 0;
     double t0 = 0.0;
@@ -82,6 +86,7 @@ struct ebit_ctx {
     std::vector<Instance> inst;
     cudaStream_t stream = nullptr;
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   // capture streams of the solvers' loop bodies
+    cudaStream_t side = nullptr;   // capture branch of the second viscous solve
     // batched steps: instance b replays its step graph on workers[b % workers.size()], between a
     // fork event recorded on the context stream and the workers' join events
     std::vector<cudaStream_t> workers;
@@ -176,6 +181,8 @@ static size_t layout(Instance& I, char* base, F&& assign) {
     assign(I, take, N, nv, nh, nve);
     char* sb = take(Solver::bytes(g.nx, g.ny));
     if (base) I.solver.bind(sb, g.nx, g.ny, false);   // capture streams come from the context
+    char* sb2 = take(Solver::bytes(g.nx, g.ny));
+    if (base) I.solver2.bind(sb2, g.nx, g.ny, false);
     return off;
 }
 
@@ -217,6 +224,10 @@ static void assign_ptrs(Instance& I, const std::function<char*(size_t)>& take, s
     I.op_wb = (double*)take(N * 8);
     I.op_b = (double*)take(N * 8);
     I.op_x = (double*)take(N * 8);
+    I.op2_cd = (double*)take(N * 8);
+    I.op2_dd = (double*)take(N * 8);
+    I.op2_wl = (double*)take(N * 8);
+    I.op2_wb = (double*)take(N * 8);
     I.vbx = (double2*)take(N * 16);
     I.vby = (double2*)take(N * 16);
     I.vxx = (double2*)take(N * 16);
@@ -294,6 +305,16 @@ static void do_solve(Instance& I, int slot, const double* b, double* x, int nr, 
     count((int)(I.solver.launches - l0));
 }
 
+// the second viscous component on its own solver and operator arrays
+static void do_solve2(Instance& I, int slot, const double* b, double* x, int nr, cudaStream_t st) {
+    I.solver2.slot = slot;
+    I.solved |= 1u << slot;
+    long long l0 = I.solver2.launches;
+    I.solver2.solve(I.op2_cd, I.op2_dd, I.op2_wl, I.op2_wb, b, x, nr, I.cfg.precision, I.cfg.rtol, I.cfg.max_iter,
+                    st);
+    count((int)(I.solver2.launches - l0));
+}
+
 // solver statistics of the last step from the host copy of the solver slots (fetched by
 // check_status before its synchronisation)
 static void collect_stats(Instance& I, bool graph_step) {
@@ -305,7 +326,7 @@ static void collect_stats(Instance& I, bool graph_step) {
     long long body = I.solver.body_size(I.cfg.precision), n = 0;
     for (int k = 0; k < 4; ++k) {
         if (!(m & (1u << k))) continue;
-        r[k] = I.solver.result_from_host(k, I.cfg.precision);
+        r[k] = (k == SLOT_VISC_Y ? I.solver2 : I.solver).result_from_host(k, I.cfg.precision);
         ok = ok && r[k].converged;
         if (r[k].fault) I.fault = true;
         // kernels executed inside the conditional loop bodies of a graph step
@@ -344,11 +365,27 @@ static void momentum(Instance& I, cudaStream_t st) {
     launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, I.cfg.precision == EBIT_MIXED,
                    st);
     count(1);
-    for (int comp = 0; comp < 2; ++comp) {
-        launch_visc_operator(I.g, I.p, comp, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, st);
-        count(1);
-        do_solve(I, comp == 0 ? SLOT_VISC_X : SLOT_VISC_Y, (const double*)(comp == 0 ? I.vbx : I.vby),
-                 (double*)(comp == 0 ? I.vxx : I.vxy), 2, st);
+    // the two components are independent: while capturing a graph the y solve becomes a
+    // parallel branch (forked and joined through events on the side stream)
+    bool fork = I.solver.use_graph && I.side;
+    cudaStream_t s2 = fork ? I.side : st;
+    if (fork) {
+        if (!I.e_fork) cudaEventCreateWithFlags(&I.e_fork, cudaEventDisableTiming);
+        if (!I.e_join) cudaEventCreateWithFlags(&I.e_join, cudaEventDisableTiming);
+        cudaEventRecord(I.e_fork, st);
+        cudaStreamWaitEvent(s2, I.e_fork, 0);
+        I.solver2.use_graph = 1;
+    }
+    launch_visc_operator(I.g, I.p, 0, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, st);
+    count(1);
+    do_solve(I, SLOT_VISC_X, (const double*)I.vbx, (double*)I.vxx, 2, st);
+    launch_visc_operator(I.g, I.p, 1, I.vf, I.op2_cd, I.op2_dd, I.op2_wl, I.op2_wb, s2);
+    count(1);
+    do_solve2(I, SLOT_VISC_Y, (const double*)I.vby, (double*)I.vxy, 2, s2);
+    if (fork) {
+        cudaEventRecord(I.e_join, s2);
+        cudaStreamWaitEvent(st, I.e_join, 0);
+        I.solver2.use_graph = 0;
     }
     launch_ustar(I.g, I.p, I.vxx, I.vxy, I.gc, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
     count(2);
@@ -416,6 +453,7 @@ static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
     for (size_t b = 0; b < ctx->inst.size(); ++b) {
         Instance& I = ctx->inst[b];
         if (I.solved) I.solver.fetch_states(ctx->stream);
+        if (I.solved & (1u << SLOT_VISC_Y)) I.solver2.fetch_states(ctx->stream);
         cudaMemcpyAsync(ctx->host_status + b, I.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -531,15 +569,19 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         }
         ctx->batches.push_back(B);
     }
-    if (cudaMallocHost(&ctx->host_states, batch * Solver::NSLOT * sizeof(SolveState)) != cudaSuccess ||
+    if (cudaMallocHost(&ctx->host_states, 2 * batch * Solver::NSLOT * sizeof(SolveState)) != cudaSuccess ||
         cudaMallocHost(&ctx->host_status, batch * sizeof(int)) != cudaSuccess) {
         ebit_destroy(ctx);
         return EBIT_ENOMEM;
     }
     for (int k = 0; k < 3; ++k) cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
     for (int b = 0; b < batch; ++b) {
-        ctx->inst[b].solver.st_host = ctx->host_states + b * Solver::NSLOT;
-        for (int k = 0; k < 3; ++k) ctx->inst[b].solver.aux[k] = ctx->aux[k];
+        Instance& I = ctx->inst[b];
+        I.solver.st_host = ctx->host_states + b * Solver::NSLOT;
+        I.solver2.st_host = ctx->host_states + (batch + b) * Solver::NSLOT;
+        for (int k = 0; k < 3; ++k) I.solver.aux[k] = I.solver2.aux[k] = ctx->aux[k];
+        I.side = ctx->side;
     }
     ctx->launch0 = g_launches.load();
     ebit_status s = cuda_check(ctx, "ebit_init");
@@ -760,9 +802,11 @@ static ebit_status replay_batch(ebit_ctx* ctx, Batch& B, cudaStream_t st) {
         B.lead.g.nz = (int)B.members.size();
         B.lead.g.zs = (long long)B.stride;
         B.lead.g.pz = B.d_phys;
-        B.lead.solver.nz = (int)B.members.size();
-        B.lead.solver.zs = (long long)B.stride;
-        B.lead.solver.use_tma = 0;   // descriptors hold one instance's addresses
+        for (Solver* sv : {&B.lead.solver, &B.lead.solver2}) {
+            sv->nz = (int)B.members.size();
+            sv->zs = (long long)B.stride;
+            sv->use_tma = 0;   // descriptors hold one instance's addresses
+        }
     }
     for (size_t z = 0; z < B.members.size(); ++z) B.h_phys[z] = ctx->inst[B.members[z]].p;
     cudaMemcpyAsync(B.d_phys, B.h_phys.data(), B.h_phys.size() * sizeof(Phys), cudaMemcpyHostToDevice, st);
@@ -839,6 +883,8 @@ static void apply_schedule(ebit_ctx* ctx, Unit& U, int small_max, double inner, 
     auto set = [&](Instance& I) {
         I.solver.set_schedule(small_max, inner);
         I.solver.use_tma = tma;
+        I.solver2.set_schedule(small_max, inner);
+        I.solver2.use_tma = tma;
         for (auto& gx : I.graph)
             if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
     };
@@ -997,6 +1043,7 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         for (auto& I : ctx->inst) {
             I.solver.use_tma = value ? 1 : 0;
+            I.solver2.use_tma = value ? 1 : 0;
             for (auto& gx : I.graph)
                 if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
         }
@@ -1030,6 +1077,7 @@ ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class) {
             t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; t.bytes = 0.0;
         }
         cudaMemcpyAsync(I.solver.timer, z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(I.solver2.timer, z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
     }
     cudaStreamSynchronize(ctx->stream);
     return cuda_check(ctx, "ebit_timing_begin");
@@ -1039,13 +1087,18 @@ ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches,
     if (!ctx || !total_ms || !launches || !bytes_per_launch) return EBIT_EINVAL;
     double tot = 0.0, bytes = 0.0;
     uint64_t n = 0;
-    for (auto& I : ctx->inst) {
-        KTimer t[2];
-        cudaMemcpyAsync(t, I.solver.timer, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream);
-        cudaStreamSynchronize(ctx->stream);
-        tot += (t[0].total_ns + t[1].total_ns) * 1e-6;
-        n += t[0].launches + t[1].launches;
-        bytes += t[0].bytes + t[1].bytes;
+    std::vector<KTimer> t(4 * ctx->inst.size());
+    for (size_t b = 0; b < ctx->inst.size(); ++b) {
+        cudaMemcpyAsync(&t[4 * b], ctx->inst[b].solver.timer, 2 * sizeof(KTimer), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+        cudaMemcpyAsync(&t[4 * b + 2], ctx->inst[b].solver2.timer, 2 * sizeof(KTimer), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+    }
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& k : t) {
+        tot += k.total_ns * 1e-6;
+        n += k.launches;
+        bytes += k.bytes;
     }
     *total_ms = tot;
     *launches = n;
@@ -1079,6 +1132,11 @@ void ebit_destroy(ebit_ctx* ctx) {
     }
     for (auto& s : ctx->aux)
         if (s) cudaStreamDestroy(s);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (auto& I : ctx->inst) {
+        if (I.e_fork) cudaEventDestroy(I.e_fork);
+        if (I.e_join) cudaEventDestroy(I.e_join);
+    }
     for (auto& s : ctx->workers) cudaStreamDestroy(s);
     for (auto& e : ctx->joins) cudaEventDestroy(e);
     if (ctx->fork) cudaEventDestroy(ctx->fork);

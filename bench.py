@@ -292,8 +292,8 @@ def run_ours(args):
             results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist())
             sched = {}
             for b in range(len(pbs)):
-                sm, it, tm = E.ebit_get_schedule(ctx, b)
-                key = f"small_max={sm} inner_rtol={it:g} tma={tm}"
+                sm, it, tm, co = E.ebit_get_schedule(ctx, b)
+                key = f"small_max={sm} inner_rtol={it:g} tma={tm} coop={co}"
                 sched[key] = sched.get(key, 0) + 1
             results[name]["schedule"] = sched
             if not args.profile_only and rank == 0:

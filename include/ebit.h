@@ -238,13 +238,16 @@ ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const dou
  *     cells, the values that change the level split of this grid;
  *   - the relative tolerance of the refinement's inner FP32 solves: 1e-4 or 1e-5 (mixed
  *     precision only);
- *   - TMA staging of the tile regions on or off (instances stepped alone).
+ *   - TMA staging of the tile regions on or off (instances stepped alone);
+ *   - the coarse tiled levels and the single-block levels in one cooperative launch (grid
+ *     barriers between the phases) or one launch per level (instances stepped alone).
  * The state of every instance (fields, markers, time, step counter) is restored afterwards
  * from a device snapshot of the largest unit's arena, which is allocated with cudaMalloc for
  * the duration of the call.  Needs graph mode.  EBIT_ENOMEM when the snapshot does not fit. */
 ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps);
-/* The schedule an instance uses: single-block level size, inner tolerance, TMA staging. */
-ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma);
+/* The schedule an instance uses: single-block level size, inner tolerance, TMA staging,
+ * cooperative coarse cycle. */
+ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma, int* coop);
 
 /* Options:
  *   EBIT_OPT_GRAPH (default 1) replays each step as a CUDA graph captured on the context's
@@ -254,9 +257,13 @@ ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* i
  *   shared memory with tensor-memory-accelerator copies (cp.async.bulk.tensor); 0 loads them
  *   with ordinary loads.  Both give the same values; levels whose rows or base are not 16-byte
  *   aligned always use ordinary loads.  Changing it drops the captured step graphs.
+ *   EBIT_OPT_COOP (default 1) runs the coarse tiled levels of each V-cycle (those whose tiles
+ *   fit one per co-resident block) and the single-block levels in one cooperative launch with
+ *   grid barriers between the phases; 0 launches each level separately.  Both give the same
+ *   values.  Instances stepped in batches always launch each level separately.
  * A tile kernel that waits for its copies in vain gives up after a bounded wait; ebit_step
  * then returns EBIT_ECUDA. */
-enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2 };
+enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2, EBIT_OPT_COOP = 3 };
 ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value);
 
 const char* ebit_last_error(const ebit_ctx* ctx);

@@ -56,7 +56,7 @@ struct Instance {
     long long nstep = 0;
     double stats[6] = {0, 0, 0, 0, 0, 0};   // iterations and residuals: energy, viscous, poisson
     bool noconv = false;
-    bool fault = false;   // a tile kernel's bounded wait for its TMA copies gave up
+    bool fault = false;   // a multigrid kernel gave up a bounded wait (TMA copies, grid barrier)
     // CUDA graphs of one step, per sweep-order parity
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};   // kernel launches captured per graph (loop bodies once)
@@ -468,7 +468,8 @@ static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
         if (s & 2) return fail(ctx, EBIT_ETOPO, "too many marker candidates on one edge" + where);
         if (I.fault) {
             I.fault = false;
-            return fail(ctx, EBIT_ECUDA, "a multigrid tile kernel's TMA copies did not complete" + where);
+            return fail(ctx, EBIT_ECUDA,
+                        "a multigrid kernel gave up a bounded wait (TMA copies or grid barrier)" + where);
         }
         if (I.noconv) {
             I.noconv = false;
@@ -805,7 +806,8 @@ static ebit_status replay_batch(ebit_ctx* ctx, Batch& B, cudaStream_t st) {
         for (Solver* sv : {&B.lead.solver, &B.lead.solver2}) {
             sv->nz = (int)B.members.size();
             sv->zs = (long long)B.stride;
-            sv->use_tma = 0;   // descriptors hold one instance's addresses
+            sv->use_tma = 0;    // descriptors hold one instance's addresses
+            sv->use_coop = 0;   // a grid barrier per member would not fit one cooperative grid
         }
     }
     for (size_t z = 0; z < B.members.size(); ++z) B.h_phys[z] = ctx->inst[B.members[z]].p;
@@ -879,12 +881,13 @@ struct Unit {
     size_t bytes = 0;
 };
 
-static void apply_schedule(ebit_ctx* ctx, Unit& U, int small_max, double inner, int tma) {
+static void apply_schedule(ebit_ctx* ctx, Unit& U, int small_max, double inner, int tma, int coop) {
     auto set = [&](Instance& I) {
-        I.solver.set_schedule(small_max, inner);
-        I.solver.use_tma = tma;
-        I.solver2.set_schedule(small_max, inner);
-        I.solver2.use_tma = tma;
+        for (Solver* sv : {&I.solver, &I.solver2}) {
+            sv->set_schedule(small_max, inner);
+            sv->use_tma = tma;
+            sv->use_coop = coop;
+        }
         for (auto& gx : I.graph)
             if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
     };
@@ -954,13 +957,15 @@ ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps) {
         std::vector<double> inners = I0.cfg.precision == EBIT_MIXED ? std::vector<double>{1e-4, 1e-5}
                                                                     : std::vector<double>{1e-5};
         std::vector<int> tmas = U.batch ? std::vector<int>{0} : std::vector<int>{1, 0};
+        std::vector<int> coops = U.batch ? std::vector<int>{0} : std::vector<int>{1, 0};
         float best = 1e30f;
-        int bs = I0.solver.small_max_f, bt = I0.solver.use_tma;
+        int bs = I0.solver.small_max_f, bt = I0.solver.use_tma, bc = I0.solver.use_coop;
         double bi = I0.solver.inner_rtol;
         for (int sm : smalls)
             for (double in : inners)
-                for (int tm : tmas) {
-                    apply_schedule(ctx, U, sm, in, tm);
+                for (int tm : tmas)
+                for (int co : coops) {
+                    apply_schedule(ctx, U, sm, in, tm, co);
                     restore();
                     ebit_status r = step_unit(ctx, U);   // captures the graphs, warms up
                     if (r == EBIT_OK || r == EBIT_ENOCONV) {
@@ -977,10 +982,11 @@ ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps) {
                             bs = sm;
                             bi = in;
                             bt = tm;
+                            bc = co;
                         }
                     }
                 }
-        apply_schedule(ctx, U, bs, bi, bt);
+        apply_schedule(ctx, U, bs, bi, bt, bc);
         restore();
         cudaStreamSynchronize(ctx->stream);
     }
@@ -991,12 +997,14 @@ ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps) {
     return status;
 }
 
-ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma) {
-    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !small_max || !inner_rtol || !tma) return EBIT_EINVAL;
+ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma, int* coop) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !small_max || !inner_rtol || !tma || !coop)
+        return EBIT_EINVAL;
     const Solver& s = ctx->inst[inst].solver;
     *small_max = s.small_max_f;
     *inner_rtol = s.inner_rtol;
     *tma = s.use_tma;
+    *coop = s.use_coop;
     return EBIT_OK;
 }
 
@@ -1039,11 +1047,13 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
         ctx->use_graph = value ? 1 : 0;
         return EBIT_OK;
     }
-    if (option == EBIT_OPT_TMA) {
+    if (option == EBIT_OPT_TMA || option == EBIT_OPT_COOP) {
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         for (auto& I : ctx->inst) {
-            I.solver.use_tma = value ? 1 : 0;
-            I.solver2.use_tma = value ? 1 : 0;
+            for (Solver* sv : {&I.solver, &I.solver2}) {
+                if (option == EBIT_OPT_TMA) sv->use_tma = value ? 1 : 0;
+                else sv->use_coop = value ? 1 : 0;
+            }
             for (auto& gx : I.graph)
                 if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
         }

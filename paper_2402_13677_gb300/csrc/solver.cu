@@ -460,42 +460,20 @@ __device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, in
     }
 }
 
-// k_pre: x = S^nu(0; b) on the tile (red-black order), coarse b = R (b - A x)
+// pre-smoothing of tile (bx, by): x = S^nu(0; b) on the tile (red-black order), coarse
+// b = R (b - A x); smem holds the region (stage: its TMA boxes, already landed, or null)
 template <typename T, int NR>
-__global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>()) k_pre(Lev<T> L, const T* __restrict__ b,
-                                                                  T* __restrict__ x, T* __restrict__ bc,
-                                                                  SolveState* st, KTimer* tm,
-                                                                  const __grid_constant__ TileMaps maps,
-                                                                  int use_tma) {
-    const long long zo = zoff(L.zs);
-    L.diag = zsh(L.diag, zo);
-    L.wl = zsh(L.wl, zo);
-    L.wb = zsh(L.wb, zo);
-    b = zsh(b, zo);
-    x = zsh(x, zo);
-    bc = zsh(bc, zo);
-    st = zsh(st, zo);
-    tm = zsh(tm, zo);
-    if (skip(st)) return;
+__device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
+                                int bx, int by, unsigned char* smem, const unsigned char* stage) {
     constexpr int H = 2 * NU + 1;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
-    extern __shared__ __align__(128) unsigned char smem[];
-    timer_begin(tm);
     Rg R(smem);
-    int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
+    int gx0 = bx * TX - H, gy0 = by * TY - H;
     int p0 = (gx0 + gy0) & 1;
     bool act = threadIdx.x < Rg::THREADS;
     int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
-    // TMA boxes: 128-byte aligned after the region (the launch reserves 128 bytes of slack)
-    unsigned char* stage =
-        use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
-    bool landed = true;
-    if (stage) {
-        landed = stage_region<T, NR, H, false>(stage, maps, gx0, gy0);
-        if (!landed && threadIdx.x == 0) atomicOr(&st->fault, 1);
-    }
     Cells<T, NR> C;
     if (act) tile_load<T, NR, H, false>(R, C, p0, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0, stage);
     __syncthreads();
@@ -527,7 +505,7 @@ __global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, N
     int cnx = L.nx / 2, cny = L.ny / 2;
     for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += blockDim.x) {
         int ti = t % (TX / 2), tj = t / (TX / 2);
-        int ci = blockIdx.x * (TX / 2) + ti, cj = blockIdx.y * (TY / 2) + tj;
+        int ci = bx * (TX / 2) + ti, cj = by * (TY / 2) + tj;
         if (ci >= cnx || cj >= cny) continue;
         // the core starts at an even global index, so children (2ti + a, 2tj + b) are core cells
         Vec<T, NR> acc;
@@ -537,11 +515,77 @@ __global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, N
                         res[((2 * tj + 1) * TX + 2 * ti) * NR + k2] + res[((2 * tj + 1) * TX + 2 * ti + 1) * NR + k2];
         reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
     }
+}
+
+// k_pre: one tile per block
+template <typename T, int NR>
+__global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>()) k_pre(Lev<T> L, const T* __restrict__ b,
+                                                                  T* __restrict__ x, T* __restrict__ bc,
+                                                                  SolveState* st, KTimer* tm,
+                                                                  const __grid_constant__ TileMaps maps,
+                                                                  int use_tma) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    b = zsh(b, zo);
+    x = zsh(x, zo);
+    bc = zsh(bc, zo);
+    st = zsh(st, zo);
+    tm = zsh(tm, zo);
+    if (skip(st)) return;
+    constexpr int H = 2 * NU + 1;
+    using Rg = Region<T, NR, H>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    timer_begin(tm);
+    // TMA boxes: 128-byte aligned after the region (the launch reserves 128 bytes of slack)
+    unsigned char* stage =
+        use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
+    if (stage && !stage_region<T, NR, H, false>(stage, maps, blockIdx.x * TX - H, blockIdx.y * TY - H) &&
+        threadIdx.x == 0)
+        atomicOr(&st->fault, 1);
+    pre_tile<T, NR>(L, b, x, bc, blockIdx.x, blockIdx.y, smem, stage);
     // algorithmic bytes: b, diag, wl, wb read; x and the quarter-size coarse b written
     timer_end(tm, (double)L.nx * L.ny * sizeof(T) * (3.0 + NR * 2.25));
 }
 
-// k_post: x = xin + P xc, then black-red sweeps; at the finest level also r.z -> beta
+// post-smoothing of tile (bx, by): x = xin + P xc, then black-red sweeps; returns the tile's
+// part of r.z (each right-hand side) when DOT
+template <typename T, int NR, bool DOT>
+__device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, const T* __restrict__ xin,
+                                    T* __restrict__ x, const T* __restrict__ xc, int bx, int by, unsigned char* smem,
+                                    const unsigned char* stage) {
+    constexpr int H = 2 * NU;
+    using Rg = Region<T, NR, H>;
+    constexpr int HX = Rg::HX;
+    Rg R(smem);
+    int gx0 = bx * TX - H, gy0 = by * TY - H;
+    int p0 = (gx0 + gy0) & 1;
+    bool act = threadIdx.x < Rg::THREADS;
+    int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    Cells<T, NR> C;
+    if (act) tile_load<T, NR, H, true>(R, C, p0, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0, stage);
+    __syncthreads();
+    tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 4, 0>(R, C, k, ry0, act);
+    double dot[2] = {0.0, 0.0};
+    if (act)
+        tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
+            const T* xm = R.x(c);
+            Vec<T, NR> xv;
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) {
+                xv.v[k2] = xm[q * NR + k2];
+                if (DOT) dot[k2] += (double)xv.v[k2] * (double)C.b[r][c][k2];
+            }
+            reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
+        });
+    return make_double2(dot[0], dot[1]);
+}
+
+// k_post: one tile per block; at the finest level also r.z -> beta
 template <typename T, int NR, bool DOT>
 __global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>()) k_post(Lev<T> L, const T* __restrict__ b,
                                                                const T* __restrict__ xin, T* __restrict__ x,
@@ -564,42 +608,16 @@ __global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>()
     if (skip(st)) return;
     constexpr int H = 2 * NU;
     using Rg = Region<T, NR, H>;
-    constexpr int HX = Rg::HX;
     extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
-    Rg R(smem);
-    int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
-    int p0 = (gx0 + gy0) & 1;
-    bool act = threadIdx.x < Rg::THREADS;
-    int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
-    // TMA boxes: 128-byte aligned after the region (the launch reserves 128 bytes of slack)
     unsigned char* stage =
         use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
-    bool landed = true;
-    if (stage) {
-        landed = stage_region<T, NR, H, true>(stage, maps, gx0, gy0);
-        if (!landed && threadIdx.x == 0) atomicOr(&st->fault, 1);
-    }
-    Cells<T, NR> C;
-    if (act) tile_load<T, NR, H, true>(R, C, p0, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0, stage);
-    __syncthreads();
-    tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 4, 0>(R, C, k, ry0, act);
-    double dot[2] = {0.0, 0.0};
-    if (act)
-        tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
-            const T* xm = R.x(c);
-            Vec<T, NR> xv;
-#pragma unroll
-            for (int k2 = 0; k2 < NR; ++k2) {
-                xv.v[k2] = xm[q * NR + k2];
-                if (DOT) dot[k2] += (double)xv.v[k2] * (double)C.b[r][c][k2];
-            }
-            reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
-        });
+    if (stage && !stage_region<T, NR, H, true>(stage, maps, blockIdx.x * TX - H, blockIdx.y * TY - H) &&
+        threadIdx.x == 0)
+        atomicOr(&st->fault, 1);
+    double2 dd = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, stage);
     if (DOT) {
+        double dot[2] = {dd.x, dd.y};
         double tot[NR];
         if (grid_reduce<NR>(dot, partial, ticket, tot)) {
 #pragma unroll
@@ -680,21 +698,12 @@ __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M
     __syncthreads();
 }
 
+// the V-cycle on the small levels in one block, from the level-(first small) rhs b_in to its
+// correction x_out; with DOT (the cycle starts at the finest level) also r.z -> beta
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* __restrict__ diag,
-                                                         const T* __restrict__ wl, const T* __restrict__ wb,
-                                                         const T* __restrict__ inv, const T* __restrict__ b_in,
-                                                         T* __restrict__ x_out, SolveState* st) {
-    const long long zo = zoff(P.zs);
-    diag = zsh(diag, zo);
-    wl = zsh(wl, zo);
-    wb = zsh(wb, zo);
-    inv = zsh(inv, zo);
-    b_in = zsh(b_in, zo);
-    x_out = zsh(x_out, zo);
-    st = zsh(st, zo);
-    if (skip(st)) return;
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ void small_cycle(const SmallPlan& P, const T* __restrict__ diag, const T* __restrict__ wl,
+                            const T* __restrict__ wb, const T* __restrict__ inv, const T* __restrict__ b_in,
+                            T* __restrict__ x_out, SolveState* st, unsigned char* smem) {
     SmallMem<T, NR> M(smem, P.total);
     int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
     // the small levels are contiguous in the packed level arrays and in shared memory: one flat
@@ -828,6 +837,101 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
                 st->rz[k] = a;
             }
         }
+    }
+}
+
+template <typename T, int NR, bool DOT>
+__global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* __restrict__ diag,
+                                                         const T* __restrict__ wl, const T* __restrict__ wb,
+                                                         const T* __restrict__ inv, const T* __restrict__ b_in,
+                                                         T* __restrict__ x_out, SolveState* st) {
+    const long long zo = zoff(P.zs);
+    diag = zsh(diag, zo);
+    wl = zsh(wl, zo);
+    wb = zsh(wb, zo);
+    inv = zsh(inv, zo);
+    b_in = zsh(b_in, zo);
+    x_out = zsh(x_out, zo);
+    st = zsh(st, zo);
+    if (skip(st)) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    small_cycle<T, NR, DOT>(P, diag, wl, wb, inv, b_in, x_out, st, smem);
+}
+
+
+// ---- the coarse part of the V-cycle in one cooperative launch -----------------------------
+// Tiled levels with few tiles are latency-bound: each launch costs more than its work.  The
+// tiled levels [l0, nb) and the single-block levels run in one cooperative launch whose blocks
+// take the tiles of a level in turn and meet at a grid barrier between the phases:
+// pre-smoothing down the levels, the single-block cycle (block 0), post-smoothing up.
+template <typename T>
+struct CoarsePlan {
+    int l0, nb;                      // levels handled: tiled [l0, nb), then the single-block ones
+    Lev<T> L[Solver::MAXLEV];
+    const T* b[Solver::MAXLEV];      // rhs of level l
+    T* x2[Solver::MAXLEV];           // pre-smoothed x of level l
+    T* bc[Solver::MAXLEV];           // rhs of level l + 1 (written by the pre phase of level l)
+    T* xo[Solver::MAXLEV];           // final x of level l
+    const T* xc[Solver::MAXLEV];     // x of level l + 1 (read by the post phase of level l)
+};
+constexpr int CC_THREADS = 512;
+
+// grid-wide barrier of a cooperative launch (all blocks resident): arrival counter bar[0],
+// generation bar[1]; the wait is bounded and a timeout is recorded in st->fault
+__device__ inline void grid_sync(unsigned* bar, unsigned& gen, SolveState* st) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            for (int it = 0; atomicAdd(&bar[1], 0u) == gen; ++it) {
+                if (it > (1 << 24)) {
+                    atomicOr(&st->fault, 2);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    ++gen;
+    __syncthreads();
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(CC_THREADS) k_coarse_cycle(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag,
+                                                             const T* __restrict__ wl, const T* __restrict__ wb,
+                                                             const T* __restrict__ inv, SolveState* st,
+                                                             unsigned* bar) {
+    if (skip(st)) return;   // written by an earlier launch: the same for every block
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned gen0;
+    if (threadIdx.x == 0) gen0 = atomicAdd(&bar[1], 0u);
+    __syncthreads();
+    unsigned gen = gen0;
+    for (int l = C.l0; l < C.nb; ++l) {
+        const Lev<T>& L = C.L[l];
+        int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr);
+            __syncthreads();
+        }
+        grid_sync(bar, gen, st);
+    }
+    if (blockIdx.x == 0) small_cycle<T, NR, false>(P, diag, wl, wb, inv, C.bc[C.nb - 1], C.xo[C.nb], st, smem);
+    grid_sync(bar, gen, st);
+    for (int l = C.nb - 1; l >= C.l0; --l) {
+        const Lev<T>& L = C.L[l];
+        int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr);
+            __syncthreads();
+        }
+        if (l > C.l0) grid_sync(bar, gen, st);
     }
 }
 
@@ -1382,6 +1486,10 @@ void Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t 
     allow_smem(k_post<double, 1, false>, SM);
     allow_smem(k_post<double, 2, true>, SM);
     allow_smem(k_post<double, 2, false>, SM);
+    allow_smem(k_coarse_cycle<float, 1>, SM);
+    allow_smem(k_coarse_cycle<float, 2>, SM);
+    allow_smem(k_coarse_cycle<double, 1>, SM);
+    allow_smem(k_coarse_cycle<double, 2>, SM);
     allow_smem(k_small<float, 1, true>, SM);
     allow_smem(k_small<float, 1, false>, SM);
     allow_smem(k_small<float, 2, true>, SM);
@@ -1552,6 +1660,42 @@ static SmallPlan small_plan(const Solver& s) {
     return P;
 }
 
+// shared memory of the cooperative coarse cycle: the larger of the tile regions and the
+// single-block levels
+template <typename T, int NR>
+static size_t coarse_smem(const SmallPlan& P) {
+    size_t a = Region<T, NR, 2 * NU + 1>::bytes(), b = Region<T, NR, 2 * NU>::bytes();
+    size_t c = SmallMem<T, NR>::bytes(P.total);
+    size_t m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+// first tiled level of the cooperative coarse cycle (nb: none).  A level joins when its tiles
+// fit one per co-resident block; the finest level stays separate (its post-smoothing carries
+// the r.z of CG).  Single instances only.
+template <typename T, int NR>
+static int coarse_start(Solver& s) {
+    int nb = nbig_of<T>(s);
+    if (!s.use_coop || s.nz != 1 || nb < 2) return nb;
+    static int resident[2][2] = {{-1, -1}, {-1, -1}};
+    int& res = resident[PT<T>::prec][NR - 1];
+    if (res < 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        size_t smem = Region<T, NR, 2 * NU + 1>::bytes() > Region<T, NR, 2 * NU>::bytes()
+                          ? Region<T, NR, 2 * NU + 1>::bytes()
+                          : Region<T, NR, 2 * NU>::bytes();
+        smem = smem > SmallMem<T, NR>::bytes(5461) ? smem : SmallMem<T, NR>::bytes(5461);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_cycle<T, NR>, CC_THREADS, smem);
+        res = per * sms;
+        cudaGetLastError();
+    }
+    for (int l = 1; l < nb; ++l)
+        if ((long long)((s.lnx[l] + TX - 1) / TX) * ((s.lny[l] + TY - 1) / TY) <= res) return l;
+    return nb;
+}
+
 // z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved).
 // k_pre of level l writes the pre-smoothed x into X2_l; k_post of level l reads X2_l and the
 // coarse correction X_{l+1} (halo included) and writes the final x into X_l (z at level 0):
@@ -1565,7 +1709,8 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
     int nb = nbig_of<T>(s);
     ensure_tile_maps(s);
     const int pr = PT<T>::prec;
-    for (int l = 0; l < nb; ++l) {
+    int l0 = coarse_start<T, NR>(s);   // tiled levels [l0, nb) go into the cooperative launch
+    for (int l = 0; l < l0; ++l) {
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, s.nz);
         T* bc = B + 2 * s.loff[l + 1];
@@ -1579,20 +1724,48 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         if (!s.use_graph) ++s.launches;
         b = bc;
     }
-    {
-        SmallPlan P = small_plan<T>(s);
+    SmallPlan P = small_plan<T>(s);
+    if (l0 < nb) {
+        CoarsePlan<T> C;
+        C.l0 = l0;
+        C.nb = nb;
+        for (int l = l0; l < nb; ++l) {
+            C.L[l] = lev<T>(s, l);
+            C.b[l] = l == 0 ? r : B + 2 * s.loff[l];
+            C.x2[l] = X2 + 2 * s.loff[l];
+            C.bc[l] = B + 2 * s.loff[l + 1];
+            C.xo[l] = l == 0 ? z : X + 2 * s.loff[l];
+            C.xc[l] = X + 2 * s.loff[l + 1];
+        }
+        C.xo[nb] = X + 2 * s.loff[nb];
+        size_t smem = coarse_smem<T, NR>(P);
+        int tiles = ((s.lnx[l0] + TX - 1) / TX) * ((s.lny[l0] + TY - 1) / TY);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(tiles);
+        cfg.blockDim = dim3(CC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stm;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_coarse_cycle<T, NR>, C, P, (const T*)PT<T>::diag(s), (const T*)PT<T>::wl(s),
+                           (const T*)PT<T>::wb(s), (const T*)PT<T>::inv(s), st, s.tickets + 8);
+        if (!s.use_graph) ++s.launches;
+    } else {
         size_t smem = SmallMem<T, NR>::bytes(P.total);
         T* x = nb == 0 ? z : X + 2 * s.loff[nb];
         const T* inv = PT<T>::inv(s);
         if (nb == 0)
-            k_small<T, NR, true><<<dim3(1, 1, s.nz), SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
-                                                                  b, x, st);
+            k_small<T, NR, true><<<dim3(1, 1, s.nz), SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s),
+                                                                               PT<T>::wb(s), inv, b, x, st);
         else
-            k_small<T, NR, false><<<dim3(1, 1, s.nz), SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s), PT<T>::wb(s), inv,
-                                                                   b, x, st);
+            k_small<T, NR, false><<<dim3(1, 1, s.nz), SMALL_THREADS, smem, stm>>>(P, PT<T>::diag(s), PT<T>::wl(s),
+                                                                                PT<T>::wb(s), inv, b, x, st);
         if (!s.use_graph) ++s.launches;
     }
-    for (int l = nb - 1; l >= 0; --l) {
+    for (int l = l0 - 1; l >= 0; --l) {
         Lev<T> L = lev<T>(s, l);
         dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, s.nz);
         const T* bl = l == 0 ? r : B + 2 * s.loff[l];

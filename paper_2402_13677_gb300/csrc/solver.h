@@ -83,6 +83,7 @@ struct Solver {
     std::vector<char> tma_ok;
     bool tma_ready = false;
     int use_tma = 1;       // 0: the tile kernels load their regions with plain loads
+    int use_coop = 1;      // 0: no cooperative launch for the coarse part of the V-cycle
     // batched launches: this solver drives nz instances whose arenas lie zs bytes apart (the
     // solvers of instances 1..nz-1 are bound to their own arenas, read only for statistics)
     int nz = 1;

@@ -40,6 +40,7 @@ EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_
            "ebit_destroy", "ebit_version"]
 EBIT_OPT_GRAPH = 1
 EBIT_OPT_TMA = 2
+EBIT_OPT_COOP = 3
 EBIT_KT_SMOOTH_L0 = 1
 
 
@@ -102,7 +103,8 @@ def load(path: str = LIB_PATH):
                                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.ebit_timing_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
     lib.ebit_autotune.argtypes = [vp, i32]
-    lib.ebit_get_schedule.argtypes = [vp, i32, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.ebit_get_schedule.argtypes = [vp, i32, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]
     lib.ebit_last_error.argtypes = [vp]
     lib.ebit_last_error.restype = C.c_char_p
     lib.ebit_destroy.argtypes = [vp]
@@ -245,10 +247,10 @@ def ebit_autotune(ctx, trial_steps=2):
 
 
 def ebit_get_schedule(ctx, inst):
-    """(single-block level size, inner FP32 tolerance, TMA staging) of an instance."""
-    sm, it, tm = C.c_int(), C.c_double(), C.c_int()
-    _check(ctx, load().ebit_get_schedule(ctx, inst, C.byref(sm), C.byref(it), C.byref(tm)))
-    return sm.value, it.value, tm.value
+    """(single-block level size, inner FP32 tolerance, TMA staging, cooperative coarse cycle)."""
+    sm, it, tm, co = C.c_int(), C.c_double(), C.c_int(), C.c_int()
+    _check(ctx, load().ebit_get_schedule(ctx, inst, C.byref(sm), C.byref(it), C.byref(tm), C.byref(co)))
+    return sm.value, it.value, tm.value, co.value
 
 
 def ebit_solve_system(ctx, inst, D, wl, wb, b, x0=None, nr=1, precision=EBIT_FP64, rtol=1e-10, max_iter=500,

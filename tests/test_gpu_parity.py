@@ -398,3 +398,23 @@ def test_tma_staging_equals_plain_loads(dev, name, precision):
             E.ebit_destroy(ctx)
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@pytest.mark.parametrize("name", ["bubble_mid", "film_mid"])
+@pytest.mark.parametrize("precision", [E.EBIT_FP64, E.EBIT_MIXED])
+def test_cooperative_coarse_cycle_equals_separate_launches(dev, name, precision):
+    """The coarse tiled levels and the single-block levels give the same values in one
+    cooperative launch (grid barriers between the phases) as in one launch per level."""
+    st = prepared(name, 0)
+    rtol = 1e-13 if precision == E.EBIT_FP64 else 1e-10
+    out = []
+    for coop in (1, 0):
+        ctx = gpu_ctx(dev, st, precision=precision, rtol=rtol)
+        try:
+            E.ebit_set_option(ctx, E.EBIT_OPT_COOP, coop)
+            E.ebit_step(ctx, 2)
+            out.append(E.download(ctx, 0, st.pb.nx, st.pb.ny))
+        finally:
+            E.ebit_destroy(ctx)
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k

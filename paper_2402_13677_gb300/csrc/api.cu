@@ -518,7 +518,11 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         I.cfg = c;
         I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0;
         I.g.nz = 1; I.g.zs = 0; I.g.pz = nullptr;
-        for (int s = 0; s < 4; ++s) { I.g.bc[s] = c.bc[s]; I.g.Tfix[s] = c.T_fixed[s] ? 1 : 0; I.g.Tw[s] = c.T_wall[s]; }
+        for (int s = 0; s < 4; ++s) {
+            I.g.bc[s] = c.bc[s];
+            I.g.Tfix[s] = c.T_fixed[s] ? 1 : 0;
+            I.g.Tw[s] = c.T_wall[s];
+        }
         std::memset(&I.p, 0, sizeof(I.p));
         I.p.dt = c.dt; I.p.theta_min = c.theta_min; I.p.extend_iters = c.extend_iters;
         I.p.energy = c.energy; I.p.mdot_fixed = c.mdot_fixed;
@@ -901,7 +905,8 @@ static void apply_schedule(ebit_ctx* ctx, Unit& U, int small_max, double inner, 
 
 // one step of the unit on the context stream, with the status check of its members
 static ebit_status step_unit(ebit_ctx* ctx, Unit& U) {
-    ebit_status r = U.batch ? replay_batch(ctx, *U.batch, ctx->stream) : replay_step(ctx, ctx->inst[U.members[0]], ctx->stream);
+    ebit_status r = U.batch ? replay_batch(ctx, *U.batch, ctx->stream)
+                            : replay_step(ctx, ctx->inst[U.members[0]], ctx->stream);
     if (r != EBIT_OK) return r;
     return check_status(ctx, true);
 }

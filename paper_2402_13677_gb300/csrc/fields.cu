@@ -860,8 +860,8 @@ void launch_extend(const Grid& g, int mode, int iters, const int* list, const in
     for (int it = 0; it < iters; ++it) {
         const double* cur = (it & 1) ? vb : va;
         double* nxt = (it & 1) ? va : vb;
-        k_extend<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb, f, cur, nxt,
-                                      nullptr, nullptr, nullptr);
+        k_extend<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, mode, it, it == iters - 1, list, count, flags, idxmap, nb,
+                                                     f, cur, nxt, nullptr, nullptr, nullptr);
     }
 }
 
@@ -871,8 +871,8 @@ void launch_extend_T(const Grid& g, int iters, const int* list, const int* count
     int nb_ = extend_grid_blocks(g);
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;
-        k_extend<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, 3, it, it == iters - 1, list, count, flags, idxmap, nb, T_l, ext[a],
-                                      ext[1 - a], T_v, ext[2 + a], ext[3 - a]);
+        k_extend<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, 3, it, it == iters - 1, list, count, flags, idxmap, nb,
+                                                     T_l, ext[a], ext[1 - a], T_v, ext[2 + a], ext[3 - a]);
     }
 }
 
@@ -915,8 +915,8 @@ void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
                              const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
                              double* cd, double* dd, double* wl, double* wb, double* b, cudaStream_t st) {
-    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v, cd, dd,
-                                                                  wl, wb, b);
+    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v,
+                                                                         cd, dd, wl, wb, b);
 }
 
 void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* ax, double* ay,
@@ -937,8 +937,8 @@ void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const ui
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
                         const double* fx_v, const double* fy_l, const double* fy_v, double* partial,
                         unsigned* ticket, double* clock, double* out, cudaStream_t st) {
-    k_diagnostics<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v,
-                                                 partial, ticket, clock, out);
+    k_diagnostics<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v,
+                                                                 fy_l, fy_v, partial, ticket, clock, out);
 }
 
 }  // namespace ebit

@@ -519,11 +519,9 @@ __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __r
 
 // k_pre: one tile per block
 template <typename T, int NR>
-__global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>()) k_pre(Lev<T> L, const T* __restrict__ b,
-                                                                  T* __restrict__ x, T* __restrict__ bc,
-                                                                  SolveState* st, KTimer* tm,
-                                                                  const __grid_constant__ TileMaps maps,
-                                                                  int use_tma) {
+__global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>())
+k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, SolveState* st, KTimer* tm,
+      const __grid_constant__ TileMaps maps, int use_tma) {
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -587,12 +585,10 @@ __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, co
 
 // k_post: one tile per block; at the finest level also r.z -> beta
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>()) k_post(Lev<T> L, const T* __restrict__ b,
-                                                               const T* __restrict__ xin, T* __restrict__ x,
-                                                               const T* __restrict__ xc, SolveState* st,
-                                                               double* partial, unsigned* ticket, KTimer* tm,
-                                                               const __grid_constant__ TileMaps maps,
-                                                               int use_tma) {
+__global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>())
+k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ x, const T* __restrict__ xc,
+       SolveState* st, double* partial, unsigned* ticket, KTimer* tm, const __grid_constant__ TileMaps maps,
+       int use_tma) {
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -1130,10 +1126,30 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
         T d = L.diag[c];
 #pragma unroll
         for (int k = 0; k < NR; ++k) qv.v[k] = d * pc.v[k];
-        if (i > 0) { T w = L.wl[c]; Vec<T, NR> a = pn(c - 1); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
-        if (i < L.nx - 1) { T w = L.wl[c + 1]; Vec<T, NR> a = pn(c + 1); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
-        if (j > 0) { T w = L.wb[c]; Vec<T, NR> a = pn(c - L.nx); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
-        if (j < L.ny - 1) { T w = L.wb[c + L.nx]; Vec<T, NR> a = pn(c + L.nx); for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]); }
+        if (i > 0) {
+            T w = L.wl[c];
+            Vec<T, NR> a = pn(c - 1);
+            for (int k = 0; k < NR; ++k)
+                qv.v[k] += w * (pc.v[k] - a.v[k]);
+        }
+        if (i < L.nx - 1) {
+            T w = L.wl[c + 1];
+            Vec<T, NR> a = pn(c + 1);
+            for (int k = 0; k < NR; ++k)
+                qv.v[k] += w * (pc.v[k] - a.v[k]);
+        }
+        if (j > 0) {
+            T w = L.wb[c];
+            Vec<T, NR> a = pn(c - L.nx);
+            for (int k = 0; k < NR; ++k)
+                qv.v[k] += w * (pc.v[k] - a.v[k]);
+        }
+        if (j < L.ny - 1) {
+            T w = L.wb[c + L.nx];
+            Vec<T, NR> a = pn(c + L.nx);
+            for (int k = 0; k < NR; ++k)
+                qv.v[k] += w * (pc.v[k] - a.v[k]);
+        }
 #pragma unroll
         for (int k = 0; k < NR; ++k) acc[k] += (double)pc.v[k] * (double)qv.v[k];
         Pn[c] = pc;
@@ -1204,10 +1220,10 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
 
 // FP64 CG start: r = b - A x, r.r, b.b, tolerance, state reset
 template <int NR>
-__global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__ x,
-                                                 double* __restrict__ r, SolveState* st, double* partial,
-                                                 unsigned* ticket, double rtol2, int max_iters,
-                                                 cudaGraphConditionalHandle h, int use_h) {
+__global__ void __launch_bounds__(256)
+k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
+         SolveState* st, double* partial, unsigned* ticket, double rtol2, int max_iters,
+         cudaGraphConditionalHandle h, int use_h) {
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -1231,9 +1247,17 @@ __global__ void __launch_bounds__(256) k_init64(Lev<double> L, const double* __r
 #pragma unroll
         for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
         if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
-        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + 1].v[k]); }
+        if (i < L.nx - 1) {
+            double w = L.wl[c + 1];
+            for (int k = 0; k < NR; ++k)
+                s.v[k] += w * (xv.v[k] - X[c + 1].v[k]);
+        }
         if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
-        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]); }
+        if (j < L.ny - 1) {
+            double w = L.wb[c + L.nx];
+            for (int k = 0; k < NR; ++k)
+                s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]);
+        }
         Vec<double, NR> rv;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
@@ -1336,9 +1360,17 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
 #pragma unroll
         for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
         if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
-        if (i < L.nx - 1) { double w = L.wl[c + 1]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + 1].v[k]); }
+        if (i < L.nx - 1) {
+            double w = L.wl[c + 1];
+            for (int k = 0; k < NR; ++k)
+                s.v[k] += w * (xv.v[k] - X[c + 1].v[k]);
+        }
         if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
-        if (j < L.ny - 1) { double w = L.wb[c + L.nx]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]); }
+        if (j < L.ny - 1) {
+            double w = L.wb[c + L.nx];
+            for (int k = 0; k < NR; ++k)
+                s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]);
+        }
         Vec<float, NR> rf, ez;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {

@@ -53,6 +53,11 @@ constexpr int SMALL_THREADS = 1024;
 constexpr int TX = 32, TY = 32;  // tile of the large-level kernels
 constexpr int NU = 2;            // smoothing sweeps (red-black pairs) before and after
 constexpr int NU_SMALL = 2;      // the same on the levels of the single-block kernel
+// halo of the tile kernels: every half-sweep after the first leaves one more ring of the region
+// stale.  Pre-smoothing starts from x = 0, so its first half-sweep needs no neighbours and is
+// exact up to the region edge: 2 NU - 1 further half-sweeps and the residual need 2 NU rings.
+// Post-smoothing: 2 NU half-sweeps, then the core only.
+constexpr int HPRE = 2 * NU, HPOST = 2 * NU;
 constexpr int COARSE_PAIRS = 12; // symmetric sweeps on the coarsest grid (at most 16 cells)
 
 template <typename T, int NR>
@@ -305,9 +310,10 @@ struct Cells {
     int sw[2];   // (p0 + ry) & 1: the colour-0 cell of row r is in column 2k + sw[r]
 };
 
-// load the thread's cells (coefficients to registers, x to shared memory: 0, or xin + the
-// prolongated coarse x when xin != null); cells outside the domain get D = 1, zero weights,
-// b = x = 0, so sweeps leave them 0
+// load the thread's cells (coefficients to registers, x to shared memory: for pre-smoothing
+// the result of the first colour-0 half-sweep from x = 0, for post-smoothing xin + the
+// prolongated coarse x); cells outside the domain get D = 1, zero weights, b = x = 0, so
+// sweeps leave them 0
 template <typename T, int NR, int H, bool POST>
 __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, int k, int ry0, const Lev<T>& L,
                                  const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
@@ -398,6 +404,12 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, i
                 }
             }
             int cc = e ^ C.sw[r];
+            if (!POST && cc == 0) {
+                // pre-smoothing starts from x = 0: its first (colour-0) half-sweep reads only
+                // zeros and reduces to x = b / (full diagonal), done here
+#pragma unroll
+                for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = bv.v[k2] * idv;
+            }
             T* xd = R.x(cc) + (ry * HX + k) * NR;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) xd[k2] = xv.v[k2];
@@ -465,7 +477,7 @@ __device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, in
 template <typename T, int NR>
 __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
                                 int bx, int by, unsigned char* smem, const unsigned char* stage) {
-    constexpr int H = 2 * NU + 1;
+    constexpr int H = HPRE;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
@@ -477,10 +489,10 @@ __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __r
     Cells<T, NR> C;
     if (act) tile_load<T, NR, H, false>(R, C, p0, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0, stage);
     __syncthreads();
-    tile_sweep<T, NR, H, 1, 0>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 2, 1>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 3, 0>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 4, 1>(R, C, k, ry0, act);
+    // the first colour-0 half-sweep (from x = 0) was done by tile_load
+    tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
     // x of the core cells to global memory, their residuals to shared memory
     T* res = R.res();
     if (act)
@@ -519,9 +531,12 @@ __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __r
 
 // k_pre: one tile per block
 template <typename T, int NR>
-__global__ void __launch_bounds__(tile_block<2 * NU + 1>(), tile_min_blocks<T, NR>())
+__global__ void __launch_bounds__(tile_block<HPRE>(), tile_min_blocks<T, NR>())
 k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, SolveState* st, KTimer* tm,
-      const __grid_constant__ TileMaps maps, int use_tma) {
+      const __grid_constant__ TileMaps maps, int use_tma, unsigned* coop_bar) {
+    // the cooperative coarse-cycle launch that follows this (level-0) launch counts its
+    // barrier arrivals from 0; the previous one has completed (stream order)
+    if (coop_bar && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *coop_bar = 0u;
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -532,7 +547,7 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
     st = zsh(st, zo);
     tm = zsh(tm, zo);
     if (skip(st)) return;
-    constexpr int H = 2 * NU + 1;
+    constexpr int H = HPRE;
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
@@ -553,7 +568,7 @@ template <typename T, int NR, bool DOT>
 __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, const T* __restrict__ xin,
                                     T* __restrict__ x, const T* __restrict__ xc, int bx, int by, unsigned char* smem,
                                     const unsigned char* stage) {
-    constexpr int H = 2 * NU;
+    constexpr int H = HPOST;
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
     Rg R(smem);
@@ -585,7 +600,7 @@ __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, co
 
 // k_post: one tile per block; at the finest level also r.z -> beta
 template <typename T, int NR, bool DOT>
-__global__ void __launch_bounds__(tile_block<2 * NU>(), tile_min_blocks<T, NR>())
+__global__ void __launch_bounds__(tile_block<HPOST>(), tile_min_blocks<T, NR>())
 k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ x, const T* __restrict__ xc,
        SolveState* st, double* partial, unsigned* ticket, KTimer* tm, const __grid_constant__ TileMaps maps,
        int use_tma) {
@@ -602,7 +617,7 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
     ticket = zsh(ticket, zo);
     tm = zsh(tm, zo);
     if (skip(st)) return;
-    constexpr int H = 2 * NU;
+    constexpr int H = HPOST;
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
@@ -653,44 +668,62 @@ struct SmallMem {
     static size_t bytes(int total) { return (size_t)total * (2 * NR + 4) * sizeof(T); }
 };
 
-// one red-black half-sweep of level l; each thread takes two cells of the colour per pass and
-// loads both cells' operands before storing either result
+// lane layout of a small level's half-sweep: a row holds hx = ceil(nx / 2) cells of one colour;
+// 2^ls lanes (the smallest power of two >= hx, at most 32) take a row, so a warp covers
+// 32 >> ls rows at once and no lane is left idle on the narrow levels
+struct SmallLanes {
+    int ls, rpw, jr, ic;
+    __device__ SmallLanes(int hx) {
+        ls = 0;
+        while ((1 << ls) < hx && ls < 5) ++ls;
+        rpw = 32 >> ls;
+        int lane = threadIdx.x & 31;
+        jr = (threadIdx.x >> 5) * rpw + (lane >> ls);
+        ic = lane & ((1 << ls) - 1);
+    }
+};
+
+// one red-black half-sweep of colour `color` on level l
 template <typename T, int NR>
 __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M, int color) {
     int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-    int hx = nx >> 1;                    // cells of one colour per row (nx is even on these levels)
-    int n = hx * ny;
-    if (nx & 1) hx = (nx + 1) >> 1, n = hx * ny;
-    for (int base = threadIdx.x; base < n; base += 2 * blockDim.x) {
-        T acc[2][NR], id[2];
-        int q[2];
-        bool ok[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            int idx = base + u * blockDim.x;
-            int j = idx / hx, i = 2 * (idx - j * hx) + ((color - j) & 1);
-            ok[u] = idx < n && i < nx;
-            int qq = ok[u] ? o + j * nx + i : o;
-            q[u] = qq;
-            T w0 = M.wl[qq], w1 = ok[u] && i < nx - 1 ? M.wl[qq + 1] : T(0), w2 = M.wb[qq],
-              w3 = ok[u] && j < ny - 1 ? M.wb[qq + nx] : T(0);
-            id[u] = M.id[qq];
+    int hx = (nx + 1) >> 1;
+    SmallLanes G(hx);
+    int jstep = (blockDim.x >> 5) * G.rpw;
+    for (int j = G.jr; j < ny; j += jstep)
+        for (int i2 = G.ic; i2 < hx; i2 += 1 << G.ls) {
+            int i = 2 * i2 + ((color + j) & 1);
+            if (i >= nx) continue;
+            int q = o + j * nx + i;
+            T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q], w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
+            T id = M.id[q];
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                T a = M.b[qq * NR + k];
-                if (ok[u] && i > 0) a += w0 * M.x[(qq - 1) * NR + k];
-                if (ok[u] && i < nx - 1) a += w1 * M.x[(qq + 1) * NR + k];
-                if (ok[u] && j > 0) a += w2 * M.x[(qq - nx) * NR + k];
-                if (ok[u] && j < ny - 1) a += w3 * M.x[(qq + nx) * NR + k];
-                acc[u][k] = a;
+                T a = M.b[q * NR + k];
+                if (i > 0) a += w0 * M.x[(q - 1) * NR + k];
+                if (i < nx - 1) a += w1 * M.x[(q + 1) * NR + k];
+                if (j > 0) a += w2 * M.x[(q - nx) * NR + k];
+                if (j < ny - 1) a += w3 * M.x[(q + nx) * NR + k];
+                M.x[q * NR + k] = a * id;
             }
         }
+    __syncthreads();
+}
+
+// start of the down-leg smoothing of level l from x = 0: the first colour-0 half-sweep reads
+// only zeros and reduces to x = b / (full diagonal); colour-1 cells are set to 0
+template <typename T, int NR>
+__device__ inline void small_first_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M) {
+    int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+    for (int j = ty; j < ny; j += nty)
+        for (int i = tx; i < nx; i += 32) {
+            int q = o + j * nx + i;
+            bool c0 = ((i + j) & 1) == 0;
+            T id = M.id[q];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-            if (ok[u])
-#pragma unroll
-                for (int k = 0; k < NR; ++k) M.x[q[u] * NR + k] = acc[u][k] * id[u];
-    }
+            for (int k = 0; k < NR; ++k) M.x[q * NR + k] = c0 ? M.b[q * NR + k] * id : T(0);
+        }
     __syncthreads();
 }
 
@@ -733,9 +766,9 @@ __device__ void small_cycle(const SmallPlan& P, const T* __restrict__ diag, cons
     // down
     for (int l = 0; l < P.n - 1; ++l) {
         int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-        for (int c = threadIdx.x; c < nx * ny * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
-        __syncthreads();
-        for (int k = 0; k < NU_SMALL; ++k) {
+        small_first_sweep<T, NR>(P, l, M);
+        small_sweep<T, NR>(P, l, M, 1);
+        for (int k = 1; k < NU_SMALL; ++k) {
             small_sweep<T, NR>(P, l, M, 0);
             small_sweep<T, NR>(P, l, M, 1);
         }
@@ -872,29 +905,29 @@ struct CoarsePlan {
 };
 constexpr int CC_THREADS = 512;
 
-// grid-wide barrier of a cooperative launch (all blocks resident): arrival counter bar[0],
-// generation bar[1]; the wait is bounded and a timeout is recorded in st->fault
-__device__ inline void grid_sync(unsigned* bar, unsigned& gen, SolveState* st) {
+// grid-wide barrier of a cooperative launch (all blocks resident).  bar[0] counts arrivals and
+// only grows during a launch (the level-0 pre-smoothing kernel, which precedes every launch,
+// zeroes it): barrier k of the launch is passed once it reaches k x (number of blocks).  One
+// atomic per block and acquire loads while waiting; the wait is bounded and a timeout is
+// recorded in st->fault.
+__device__ inline unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ inline void grid_sync(unsigned* bar, unsigned& target, SolveState* st) {
+    target += gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
-            for (int it = 0; atomicAdd(&bar[1], 0u) == gen; ++it) {
-                if (it > (1 << 24)) {
-                    atomicOr(&st->fault, 2);
-                    break;
-                }
-                __nanosleep(32);
+        atomicAdd(&bar[0], 1u);
+        for (int it = 0; (int)(ld_acquire_gpu(&bar[0]) - target) < 0; ++it)
+            if (it > (1 << 22)) {
+                atomicOr(&st->fault, 2);
+                break;
             }
-        }
         __threadfence();
     }
-    ++gen;
     __syncthreads();
 }
 
@@ -905,10 +938,7 @@ __global__ void __launch_bounds__(CC_THREADS) k_coarse_cycle(CoarsePlan<T> C, Sm
                                                              unsigned* bar) {
     if (skip(st)) return;   // written by an earlier launch: the same for every block
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ unsigned gen0;
-    if (threadIdx.x == 0) gen0 = atomicAdd(&bar[1], 0u);
-    __syncthreads();
-    unsigned gen = gen0;
+    unsigned gen = 0;   // arrivals that pass the next barrier (bar[0] starts the launch at 0)
     for (int l = C.l0; l < C.nb; ++l) {
         const Lev<T>& L = C.L[l];
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
@@ -1611,7 +1641,7 @@ static size_t tmap_index(int prec, int nr, int l, int post) {
 
 template <typename T, int NR, bool POST>
 static bool encode_tile_maps(Solver& s, int l, TileMaps& M) {
-    constexpr int H = POST ? 2 * NU : 2 * NU + 1;
+    constexpr int H = POST ? HPOST : HPRE;
     using Sg = Stage<T, NR, H, POST>;
     int nx = s.lnx[l], ny = s.lny[l];
     size_t o = s.loff[l];
@@ -1696,7 +1726,7 @@ static SmallPlan small_plan(const Solver& s) {
 // single-block levels
 template <typename T, int NR>
 static size_t coarse_smem(const SmallPlan& P) {
-    size_t a = Region<T, NR, 2 * NU + 1>::bytes(), b = Region<T, NR, 2 * NU>::bytes();
+    size_t a = Region<T, NR, HPRE>::bytes(), b = Region<T, NR, HPOST>::bytes();
     size_t c = SmallMem<T, NR>::bytes(P.total);
     size_t m = a > b ? a : b;
     return m > c ? m : c;
@@ -1715,9 +1745,9 @@ static int coarse_start(Solver& s) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        size_t smem = Region<T, NR, 2 * NU + 1>::bytes() > Region<T, NR, 2 * NU>::bytes()
-                          ? Region<T, NR, 2 * NU + 1>::bytes()
-                          : Region<T, NR, 2 * NU>::bytes();
+        size_t smem = Region<T, NR, HPRE>::bytes() > Region<T, NR, HPOST>::bytes()
+                          ? Region<T, NR, HPRE>::bytes()
+                          : Region<T, NR, HPOST>::bytes();
         smem = smem > SmallMem<T, NR>::bytes(5461) ? smem : SmallMem<T, NR>::bytes(5461);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_cycle<T, NR>, CC_THREADS, smem);
         res = per * sms;
@@ -1748,11 +1778,12 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         T* bc = B + 2 * s.loff[l + 1];
         size_t ix = tmap_index(pr, NR, l, 0);
         int tma = s.use_tma && s.nz == 1 && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
-        using Rg = Region<T, NR, 2 * NU + 1>;
-        size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, 2 * NU + 1, false>::BYTES : Rg::bytes();
-        k_pre<T, NR><<<grid, tile_block<2 * NU + 1>(), smem, stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
-                                                                   s.timing && l == 0 ? s.timer : nullptr,
-                                                                   s.tmaps[ix], tma);
+        using Rg = Region<T, NR, HPRE>;
+        size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, HPRE, false>::BYTES : Rg::bytes();
+        k_pre<T, NR><<<grid, tile_block<HPRE>(), smem, stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
+                                                              s.timing && l == 0 ? s.timer : nullptr,
+                                                              s.tmaps[ix], tma,
+                                                              l == 0 && l0 < nb ? s.tickets + 8 : nullptr);
         if (!s.use_graph) ++s.launches;
         b = bc;
     }
@@ -1806,14 +1837,14 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         const T* xc = X + 2 * s.loff[l + 1];
         size_t ix = tmap_index(pr, NR, l, 1);
         int tma = s.use_tma && s.nz == 1 && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
-        using Rg = Region<T, NR, 2 * NU>;
-        size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, 2 * NU, true>::BYTES : Rg::bytes();
+        using Rg = Region<T, NR, HPOST>;
+        size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, HPOST, true>::BYTES : Rg::bytes();
         KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
         if (l == 0)
-            k_post<T, NR, true><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
+            k_post<T, NR, true><<<grid, tile_block<HPOST>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
                                                                           s.tickets + 4, tm, s.tmaps[ix], tma);
         else
-            k_post<T, NR, false><<<grid, tile_block<2 * NU>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
+            k_post<T, NR, false><<<grid, tile_block<HPOST>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
                                                                            s.tickets + 4, tm, s.tmaps[ix], tma);
         if (!s.use_graph) ++s.launches;
     }

@@ -36,6 +36,7 @@
 //           the same MG-PCG to a relative 1e-5, x += e in FP64, until ||r|| <= rtol ||b||.
 //
 // Reductions are deterministic: per-block partial sums, the last block adds them in block order.
+#include <vector>
 #include <cfloat>
 #include <cstdio>
 #include "common.cuh"
@@ -73,6 +74,10 @@ struct Lev {
     const T* wb;
     long long zs;   // byte stride between the instances of a batched launch (0: one instance)
 };
+
+// correctly rounded reciprocal (the same value as 1 / v)
+__device__ inline float rcp_rn(float v) { return __frcp_rn(v); }
+__device__ inline double rcp_rn(double v) { return __drcp_rn(v); }
 
 __device__ inline bool skip(const SolveState* s) { return s->done != 0 || s->odone != 0; }
 
@@ -118,33 +123,44 @@ __device__ inline double bsum(double v, double* sh) {
     return r;
 }
 
-// Reduce NV per-thread values over the grid: returns true in thread 0 of the last block,
-// with the totals in tot[0..NV).  partial has room for NV x (number of blocks) doubles.
+// Grid reductions in a fixed order.  block_partial writes the block sum of NV per-thread values
+// into slot `slot` of partial (partial[k * nslot + slot], thread 0); once every block of the grid
+// has written its slots, last_block_total returns true in thread 0 of the last block to arrive,
+// with the totals over the nslot slots in tot[0..NV).
 template <int NV>
-__device__ inline bool grid_reduce(const double* v, double* partial, unsigned* ticket, double* tot) {
+__device__ inline void block_partial(const double* v, double* partial, int nslot, int slot) {
     __shared__ double sh[32];
-    __shared__ bool last;
-    int nb = gridDim.x * gridDim.y;
-    int bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         double r = bsum(v[k], sh);
-        if (threadIdx.x == 0) partial[k * nb + bid] = r;
+        if (threadIdx.x == 0) partial[k * nslot + slot] = r;
     }
+}
+template <int NV>
+__device__ inline bool last_block_total(double* partial, int nslot, unsigned* ticket, double* tot) {
+    __shared__ double sh[32];
+    __shared__ bool last;
     __threadfence();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!last) return false;
     __threadfence();
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += ((volatile double*)partial)[k * nb + b];
+        for (int b = threadIdx.x; b < nslot; b += blockDim.x) s += ((volatile double*)partial)[k * nslot + b];
         s = bsum(s, sh);
         if (threadIdx.x == 0) tot[k] = s;
     }
     if (threadIdx.x == 0) *ticket = 0u;
     return threadIdx.x == 0;
+}
+// one slot per block; partial has room for NV x (number of blocks) doubles
+template <int NV>
+__device__ inline bool grid_reduce(const double* v, double* partial, unsigned* ticket, double* tot) {
+    int nb = gridDim.x * gridDim.y;
+    block_partial<NV>(v, partial, nb, blockIdx.y * gridDim.x + blockIdx.x);
+    return last_block_total<NV>(partial, nb, ticket, tot);
 }
 
 // use 1: the loop condition is this solve's own (assigned); use 2: a batched launch, where the
@@ -188,9 +204,11 @@ __device__ inline void coarsen_cell(int fnx, const T* fcd, const T* fdd, const T
 // Thread (k, seg) owns the cells of region columns 2k and 2k + 1 in the two rows 2 seg and
 // 2 seg + 1; in every row exactly one of its two cells has the colour being swept.  A thread
 // keeps its four cells' coefficients (b, the reciprocal of the full diagonal, the four face
-// weights, D) in registers; only x lives in shared memory, split by colour: region cell
-// (rx, ry) has colour c = (p0 + rx + ry) & 1 (p0 = (gx0 + gy0) & 1) and sits in column
-// k = rx >> 1 of row ry of colour c's array (HX = SX / 2 columns).  A colour-c cell with
+// weights, D) in registers; only x lives in shared memory, split by colour.  The region starts
+// at an even global cell (tile origins are multiples of TX, TY and the halos are even), so
+// region cell (rx, ry) has colour c = (rx + ry) & 1, known at compile time for each of a
+// thread's cells, and sits in column k = rx >> 1 of row ry of colour c's array (HX = SX / 2
+// columns).  A colour-c cell with
 // e = rx & 1 finds its left / right neighbours (colour 1 - c) in columns k - 1 + e / k + e of
 // its row and its lower / upper neighbours in column k of rows ry -+ 1.
 template <typename T, int NR, int H>
@@ -244,12 +262,16 @@ __device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int x, int
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-// wait for phase 0 of the barrier; false if it did not complete within the bound
-__device__ inline bool mbar_wait_bounded(uint64_t* bar) {
+// wait for the phase of the barrier with the given parity; false if it did not complete within
+// the bound
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity = 0) {
     for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try_wait(bar, 0)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// order this thread's earlier generic-proxy accesses to shared memory (the block's reads of a
+// box, made visible to it by a block barrier) before its next async-proxy (TMA) writes there
+__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
 __host__ __device__ constexpr int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
@@ -278,36 +300,70 @@ struct Stage {
     static_assert(BWS <= 256 && BWV * NR <= 256 && BWC * NR <= 256 && BHS <= 256, "TMA box too large");
 };
 
-// issue the region's copies (thread 0) and wait for them (all threads); false on a timeout
+// the copies of one region into the boxes (thread 0): arms the barrier with their byte count
 template <typename T, int NR, int H, bool POST>
-__device__ inline bool stage_region(unsigned char* sbase, const TileMaps& M, int gx0, int gy0) {
+__device__ inline void stage_issue(unsigned char* sbase, const TileMaps& M, int gx0, int gy0) {
     using Sg = Stage<T, NR, H, POST>;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Sg::OFF_BAR);
+    mbar_expect_tx(bar, Sg::TX_BYTES);
+    int xs = gx0 - Sg::OXS, xv = (gx0 - Sg::OXV) * NR;
+    tma_load_2d(sbase + Sg::OFF_D, &M.d, xs, gy0, bar);
+    tma_load_2d(sbase + Sg::OFF_WL, &M.wl, xs, gy0, bar);
+    tma_load_2d(sbase + Sg::OFF_WB, &M.wb, xs, gy0, bar);
+    tma_load_2d(sbase + Sg::OFF_B, &M.b, xv, gy0, bar);
+    if (POST) {
+        tma_load_2d(sbase + Sg::OFF_XIN, &M.xin, xv, gy0, bar);
+        tma_load_2d(sbase + Sg::OFF_XC, &M.xc, ((gx0 >> 1) - Sg::OXC) * NR, gy0 >> 1, bar);
+    }
+}
+
+// barrier set-up (thread 0), visible to the block after the barrier
+template <typename T, int NR, int H, bool POST>
+__device__ inline void stage_init(unsigned char* sbase) {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Stage<T, NR, H, POST>::OFF_BAR);
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_fence_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, Sg::TX_BYTES);
-        int xs = gx0 - Sg::OXS, xv = (gx0 - Sg::OXV) * NR;
-        tma_load_2d(sbase + Sg::OFF_D, &M.d, xs, gy0, bar);
-        tma_load_2d(sbase + Sg::OFF_WL, &M.wl, xs, gy0, bar);
-        tma_load_2d(sbase + Sg::OFF_WB, &M.wb, xs, gy0, bar);
-        tma_load_2d(sbase + Sg::OFF_B, &M.b, xv, gy0, bar);
-        if (POST) {
-            tma_load_2d(sbase + Sg::OFF_XIN, &M.xin, xv, gy0, bar);
-            tma_load_2d(sbase + Sg::OFF_XC, &M.xc, ((gx0 >> 1) - Sg::OXC) * NR, gy0 >> 1, bar);
-        }
-    }
-    return mbar_wait_bounded(bar);
 }
 
-// the thread's four cells: [r][c] = row ry0 + r, colour c (its column is 2k + (c ^ sw[r]))
+// The tiles of a TMA-staged tile kernel, persistent: block b takes tiles b, b + G, ... (G blocks).
+// The next tile's boxes are requested as soon as the current tile has been read out of them
+// (into registers and the region), so the copies overlap the current tile's sweeps.  work(t,
+// after_load) runs tile t and calls after_load() once the boxes have been read and the block has
+// passed a barrier.  A copy that does not land within the bound sets st->fault bit 0 and ends
+// the loop (the decision is the same in every thread).
+template <typename T, int NR, int H, bool POST, class Work>
+__device__ inline void staged_tiles(unsigned char* sbase, const TileMaps& M, int tx, int nt, SolveState* st,
+                                    Work&& work) {
+    using Sg = Stage<T, NR, H, POST>;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Sg::OFF_BAR);
+    stage_init<T, NR, H, POST>(sbase);
+    int t = blockIdx.x;
+    if (threadIdx.x == 0 && t < nt) stage_issue<T, NR, H, POST>(sbase, M, (t % tx) * TX - H, (t / tx) * TY - H);
+    for (uint32_t i = 0; t < nt; ++i, t += gridDim.x) {
+        bool landed = mbar_wait_bounded(bar, i & 1u);
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(&st->fault, 1);
+            break;
+        }
+        int tn = t + gridDim.x;
+        work(t, [&]() {
+            if (threadIdx.x == 0 && tn < nt) {
+                fence_proxy_async();
+                stage_issue<T, NR, H, POST>(sbase, M, (tn % tx) * TX - H, (tn / tx) * TY - H);
+            }
+        });
+        __syncthreads();   // the region is rewritten by the next tile
+    }
+}
+
+
+// the thread's four cells: [r][c] = row ry0 + r (ry0 even), colour c; its column is 2k + (c ^ r)
 template <typename T, int NR>
 struct Cells {
     T b[2][2][NR], id[2][2], wl[2][2], wr[2][2], wb[2][2], wt[2][2], d[2][2];
-    int sw[2];   // (p0 + ry) & 1: the colour-0 cell of row r is in column 2k + sw[r]
 };
 
 // load the thread's cells (coefficients to registers, x to shared memory: for pre-smoothing
@@ -315,16 +371,16 @@ struct Cells {
 // prolongated coarse x); cells outside the domain get D = 1, zero weights, b = x = 0, so
 // sweeps leave them 0
 template <typename T, int NR, int H, bool POST>
-__device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, int k, int ry0, const Lev<T>& L,
+__device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, int ry0, const Lev<T>& L,
                                  const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
                                  int cnx, int gx0, int gy0, const unsigned char* stage) {
     constexpr int HX = Region<T, NR, H>::HX;
     using Sg = Stage<T, NR, H, POST>;
+    static_assert(H % 2 == 0 && TX % 2 == 0 && TY % 2 == 0, "regions must start at an even cell");
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         int ry = ry0 + r;
         int gj = gy0 + ry;
-        C.sw[r] = (p0 + ry) & 1;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             int rx = 2 * k + e;
@@ -385,10 +441,9 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, i
                 dv = T(1);
                 wlv = wbv = wrv = wtv = T(0);
             }
-            // this cell's colour is e ^ sw[r]; both register slots of the row are written by
-            // selects so that no register array is indexed at run time
-            bool mine0 = (e ^ C.sw[r]) == 0;
-            T idv = T(1) / (dv + wlv + wrv + wbv + wtv);
+            // this cell's colour is e ^ r (both known at compile time)
+            bool mine0 = (e ^ r) == 0;
+            T idv = rcp_rn(dv + wlv + wrv + wbv + wtv);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 bool m = (c == 0) == mine0;
@@ -403,7 +458,7 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int p0, i
                     C.d[r][c] = dv;
                 }
             }
-            int cc = e ^ C.sw[r];
+            int cc = e ^ r;
             if (!POST && cc == 0) {
                 // pre-smoothing starts from x = 0: its first (colour-0) half-sweep reads only
                 // zeros and reduces to x = b / (full diagonal), done here
@@ -431,7 +486,7 @@ __device__ inline void tile_sweep(Region<T, NR, H>& R, const Cells<T, NR>& C, in
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             int ry = ry0 + r;
-            int e = COLOR ^ C.sw[r];
+            int e = COLOR ^ r;
             int rx = 2 * k + e;
             ok[r] = ry >= S && ry < SY - S && rx >= S && rx < SX - S;
             int q = ok[r] ? ry * HX + k : HX + 1;   // a harmless in-range slot otherwise
@@ -464,7 +519,7 @@ __device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, in
         int ry = ry0 + r;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            int rx = 2 * k + (c ^ C.sw[r]);
+            int rx = 2 * k + (c ^ r);
             int gi = gx0 + rx, gj = gy0 + ry;
             if (rx >= H && rx < H + TX && ry >= H && ry < H + TY && gi < L.nx && gj < L.ny)
                 f(r, c, rx, ry, ry * HX + k, gi, gj);
@@ -472,23 +527,29 @@ __device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, in
     }
 }
 
+struct NoOp {
+    __device__ void operator()() const {}
+};
+
 // pre-smoothing of tile (bx, by): x = S^nu(0; b) on the tile (red-black order), coarse
-// b = R (b - A x); smem holds the region (stage: its TMA boxes, already landed, or null)
-template <typename T, int NR>
+// b = R (b - A x); smem holds the region (stage: its TMA boxes, already landed, or null);
+// after_load() runs in every thread once the boxes have been read
+template <typename T, int NR, class AfterLoad = NoOp>
 __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
-                                int bx, int by, unsigned char* smem, const unsigned char* stage) {
+                                int bx, int by, unsigned char* smem, const unsigned char* stage,
+                                AfterLoad after_load = AfterLoad()) {
     constexpr int H = HPRE;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
     Rg R(smem);
     int gx0 = bx * TX - H, gy0 = by * TY - H;
-    int p0 = (gx0 + gy0) & 1;
     bool act = threadIdx.x < Rg::THREADS;
     int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
     Cells<T, NR> C;
-    if (act) tile_load<T, NR, H, false>(R, C, p0, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0, stage);
+    if (act) tile_load<T, NR, H, false>(R, C, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0, stage);
     __syncthreads();
+    after_load();
     // the first colour-0 half-sweep (from x = 0) was done by tile_load
     tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
@@ -551,34 +612,38 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
-    // TMA boxes: 128-byte aligned after the region (the launch reserves 128 bytes of slack)
-    unsigned char* stage =
-        use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
-    if (stage && !stage_region<T, NR, H, false>(stage, maps, blockIdx.x * TX - H, blockIdx.y * TY - H) &&
-        threadIdx.x == 0)
-        atomicOr(&st->fault, 1);
-    pre_tile<T, NR>(L, b, x, bc, blockIdx.x, blockIdx.y, smem, stage);
+    if (use_tma) {
+        // persistent blocks over the tiles (1-D grid), TMA boxes 128-byte aligned after the
+        // region (the launch reserves 128 bytes of slack)
+        unsigned char* stage = reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
+        int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
+        staged_tiles<T, NR, H, false>(stage, maps, tx, nt, st, [&](int t, auto after_load) {
+            pre_tile<T, NR>(L, b, x, bc, t % tx, t / tx, smem, stage, after_load);
+        });
+    } else {
+        pre_tile<T, NR>(L, b, x, bc, blockIdx.x, blockIdx.y, smem, nullptr);
+    }
     // algorithmic bytes: b, diag, wl, wb read; x and the quarter-size coarse b written
     timer_end(tm, (double)L.nx * L.ny * sizeof(T) * (3.0 + NR * 2.25));
 }
 
 // post-smoothing of tile (bx, by): x = xin + P xc, then black-red sweeps; returns the tile's
-// part of r.z (each right-hand side) when DOT
-template <typename T, int NR, bool DOT>
+// part of r.z (each right-hand side) when DOT; after_load() as for pre_tile
+template <typename T, int NR, bool DOT, class AfterLoad = NoOp>
 __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, const T* __restrict__ xin,
                                     T* __restrict__ x, const T* __restrict__ xc, int bx, int by, unsigned char* smem,
-                                    const unsigned char* stage) {
+                                    const unsigned char* stage, AfterLoad after_load = AfterLoad()) {
     constexpr int H = HPOST;
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
     Rg R(smem);
     int gx0 = bx * TX - H, gy0 = by * TY - H;
-    int p0 = (gx0 + gy0) & 1;
     bool act = threadIdx.x < Rg::THREADS;
     int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
     Cells<T, NR> C;
-    if (act) tile_load<T, NR, H, true>(R, C, p0, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0, stage);
+    if (act) tile_load<T, NR, H, true>(R, C, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0, stage);
     __syncthreads();
+    after_load();
     tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
@@ -621,16 +686,30 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(128) unsigned char smem[];
     timer_begin(tm);
-    unsigned char* stage =
-        use_tma ? reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES)) : nullptr;
-    if (stage && !stage_region<T, NR, H, true>(stage, maps, blockIdx.x * TX - H, blockIdx.y * TY - H) &&
-        threadIdx.x == 0)
-        atomicOr(&st->fault, 1);
-    double2 dd = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, stage);
+    int nslot = gridDim.x * gridDim.y;
+    if (use_tma) {
+        // persistent blocks over the tiles (1-D grid); r.z summed over the block's tiles
+        unsigned char* stage = reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
+        int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
+        // r.z: one slot per tile, summed in tile order as with one block per tile
+        staged_tiles<T, NR, H, true>(stage, maps, tx, nt, st, [&](int t, auto after_load) {
+            double2 d = post_tile<T, NR, DOT>(L, b, xin, x, xc, t % tx, t / tx, smem, stage, after_load);
+            if (DOT) {
+                double dot[2] = {d.x, d.y};
+                block_partial<NR>(dot, partial, nt, t);
+            }
+        });
+        nslot = nt;
+    } else {
+        double2 d = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, nullptr);
+        if (DOT) {
+            double dot[2] = {d.x, d.y};
+            block_partial<NR>(dot, partial, nslot, blockIdx.y * gridDim.x + blockIdx.x);
+        }
+    }
     if (DOT) {
-        double dot[2] = {dd.x, dd.y};
         double tot[NR];
-        if (grid_reduce<NR>(dot, partial, ticket, tot)) {
+        if (last_block_total<NR>(partial, nslot, ticket, tot)) {
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 double old = st->rz[k2];
@@ -668,30 +747,54 @@ struct SmallMem {
     static size_t bytes(int total) { return (size_t)total * (2 * NR + 4) * sizeof(T); }
 };
 
-// lane layout of a small level's half-sweep: a row holds hx = ceil(nx / 2) cells of one colour;
-// 2^ls lanes (the smallest power of two >= hx, at most 32) take a row, so a warp covers
-// 32 >> ls rows at once and no lane is left idle on the narrow levels
-struct SmallLanes {
-    int ls, rpw, jr, ic;
-    __device__ SmallLanes(int hx) {
-        ls = 0;
-        while ((1 << ls) < hx && ls < 5) ++ls;
-        rpw = 32 >> ls;
-        int lane = threadIdx.x & 31;
-        jr = (threadIdx.x >> 5) * rpw + (lane >> ls);
-        ic = lane & ((1 << ls) - 1);
+// The small levels run in one block.  Their half-sweeps are short, so a block-wide barrier
+// between them costs more than the work; the levels with at most SMALL_WARP_CELLS cells (and
+// every level below them) therefore run on warp 0 alone, with warp barriers.  Team<WARP> is
+// the group of threads of one part: the whole block, or warp 0.
+constexpr int SMALL_WARP_CELLS = 64;
+template <bool WARP>
+struct Team {
+    __device__ static int size() { return WARP ? 32 : (int)blockDim.x; }
+    __device__ static void sync() {
+        if (WARP) __syncwarp();
+        else __syncthreads();
     }
 };
 
-// one red-black half-sweep of colour `color` on level l
-template <typename T, int NR>
-__device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M, int color) {
-    int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-    int hx = (nx + 1) >> 1;
-    SmallLanes G(hx);
-    int jstep = (blockDim.x >> 5) * G.rpw;
-    for (int j = G.jr; j < ny; j += jstep)
-        for (int i2 = G.ic; i2 < hx; i2 += 1 << G.ls) {
+// lane layout of a row sweep over rows of width w: 2^ls lanes (the smallest power of two >= w,
+// at most 32) take a row, so a warp covers 32 >> ls rows at once and no lane idles on the
+// narrow levels; row j0 + m * jstep, column i0 + m * istep
+template <bool WARP>
+struct RowLanes {
+    int jr, ic, jstep, istep;
+    __device__ RowLanes(int w) {
+        int ls = w <= 1 ? 0 : 32 - __clz(w - 1);
+        ls = ls < 5 ? ls : 5;
+        int rpw = 32 >> ls, lane = threadIdx.x & 31;
+        jr = (WARP ? 0 : (int)(threadIdx.x >> 5)) * rpw + (lane >> ls);
+        ic = lane & ((1 << ls) - 1);
+        jstep = (Team<WARP>::size() >> 5) * rpw;
+        istep = 1 << ls;
+    }
+};
+
+// a small level's sizes, offset and half-sweep lane layout, set up once for all its sweeps
+template <bool WARP>
+struct SmallLevel {
+    int nx, ny, o, hx;
+    RowLanes<WARP> G;
+    __device__ SmallLevel(const SmallPlan& P, int l)
+        : nx(P.nx[l]), ny(P.ny[l]), o(P.soff[l]), hx((P.nx[l] + 1) >> 1), G((P.nx[l] + 1) >> 1) {}
+};
+
+// one red-black half-sweep of colour `color` on a level (a row holds ceil(nx / 2) cells of a
+// colour)
+template <typename T, int NR, bool WARP>
+__device__ inline void small_sweep(const SmallLevel<WARP>& V, SmallMem<T, NR>& M, int color) {
+    const int nx = V.nx, ny = V.ny, o = V.o, hx = V.hx;
+    const RowLanes<WARP>& G = V.G;
+    for (int j = G.jr; j < ny; j += G.jstep)
+        for (int i2 = G.ic; i2 < hx; i2 += G.istep) {
             int i = 2 * i2 + ((color + j) & 1);
             if (i >= nx) continue;
             int q = o + j * nx + i;
@@ -707,24 +810,118 @@ __device__ inline void small_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M
                 M.x[q * NR + k] = a * id;
             }
         }
-    __syncthreads();
+    Team<WARP>::sync();
 }
 
-// start of the down-leg smoothing of level l from x = 0: the first colour-0 half-sweep reads
-// only zeros and reduces to x = b / (full diagonal); colour-1 cells are set to 0
-template <typename T, int NR>
-__device__ inline void small_first_sweep(const SmallPlan& P, int l, SmallMem<T, NR>& M) {
-    int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
-    for (int j = ty; j < ny; j += nty)
-        for (int i = tx; i < nx; i += 32) {
-            int q = o + j * nx + i;
-            bool c0 = ((i + j) & 1) == 0;
-            T id = M.id[q];
+// down-leg smoothing of level l from x = 0 (its first colour-0 half-sweep reads only zeros and
+// reduces to x = b / (full diagonal), written together with zeros on colour 1), then the
+// residual restricted to level l + 1
+template <typename T, int NR, bool WARP>
+__device__ inline void small_down(const SmallPlan& P, int l, SmallMem<T, NR>& M) {
+    SmallLevel<WARP> V(P, l);
+    const int nx = V.nx, ny = V.ny, o = V.o;
+    {
+        RowLanes<WARP> G(nx);
+        for (int j = G.jr; j < ny; j += G.jstep)
+            for (int i = G.ic; i < nx; i += G.istep) {
+                int q = o + j * nx + i;
+                bool c0 = ((i + j) & 1) == 0;
+                T id = M.id[q];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) M.x[q * NR + k] = c0 ? M.b[q * NR + k] * id : T(0);
+                for (int k = 0; k < NR; ++k) M.x[q * NR + k] = c0 ? M.b[q * NR + k] * id : T(0);
+            }
+        Team<WARP>::sync();
+    }
+    small_sweep<T, NR, WARP>(V, M, 1);
+    for (int k = 1; k < NU_SMALL; ++k) {
+        small_sweep<T, NR, WARP>(V, M, 0);
+        small_sweep<T, NR, WARP>(V, M, 1);
+    }
+    int cnx = P.nx[l + 1], cny = P.ny[l + 1], co = P.soff[l + 1];
+    RowLanes<WARP> G(cnx);
+    for (int J = G.jr; J < cny; J += G.jstep)
+        for (int I = G.ic; I < cnx; I += G.istep) {
+            T acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc[k] = T(0);
+            for (int d2 = 0; d2 < 4; ++d2) {
+                int i = 2 * I + (d2 & 1), j = 2 * J + (d2 >> 1);
+                int q = o + j * nx + i;
+                T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q],
+                  w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    T xq = M.x[q * NR + k];
+                    T ax = M.d[q] * xq;
+                    if (i > 0) ax += w0 * (xq - M.x[(q - 1) * NR + k]);
+                    if (i < nx - 1) ax += w1 * (xq - M.x[(q + 1) * NR + k]);
+                    if (j > 0) ax += w2 * (xq - M.x[(q - nx) * NR + k]);
+                    if (j < ny - 1) ax += w3 * (xq - M.x[(q + nx) * NR + k]);
+                    acc[k] += M.b[q * NR + k] - ax;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) M.b[(co + J * cnx + I) * NR + k] = acc[k];
         }
-    __syncthreads();
+    Team<WARP>::sync();
+}
+
+// coarsest level: exact solve with the precomputed inverse (up to 32 cells), else a symmetric
+// red-black sweep sequence from zero
+template <typename T, int NR, bool WARP>
+__device__ inline void small_coarsest(const SmallPlan& P, SmallMem<T, NR>& M, const T* __restrict__ inv) {
+    int l = P.n - 1, o = P.soff[l], n = P.nx[l] * P.ny[l];
+    if (n <= 32 && inv[n * n] == T(1)) {
+        if (threadIdx.x < 32) {
+            int r = threadIdx.x;
+            T acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc[k] = T(0);
+            if (r < n)
+                for (int c = 0; c < n; ++c) {
+                    T a = inv[r * n + c];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc[k] += a * M.b[(o + c) * NR + k];
+                }
+            __syncwarp();
+            if (r < n)
+#pragma unroll
+                for (int k = 0; k < NR; ++k) M.x[(o + r) * NR + k] = acc[k];
+        }
+        Team<WARP>::sync();
+    } else {
+        int t = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+        for (int c = t; c < n * NR; c += Team<WARP>::size()) M.x[o * NR + c] = T(0);
+        Team<WARP>::sync();
+        SmallLevel<WARP> V(P, l);
+        for (int k = 0; k < COARSE_PAIRS; ++k) {
+            small_sweep<T, NR, WARP>(V, M, 0);
+            small_sweep<T, NR, WARP>(V, M, 1);
+        }
+        for (int k = 0; k < COARSE_PAIRS; ++k) {
+            small_sweep<T, NR, WARP>(V, M, 1);
+            small_sweep<T, NR, WARP>(V, M, 0);
+        }
+    }
+}
+
+// up-leg of level l: x += P x_{l+1}, then the post-smoothing half-sweeps
+template <typename T, int NR, bool WARP>
+__device__ inline void small_up(const SmallPlan& P, int l, SmallMem<T, NR>& M) {
+    SmallLevel<WARP> V(P, l);
+    const int nx = V.nx, ny = V.ny, o = V.o, cnx = P.nx[l + 1], co = P.soff[l + 1];
+    RowLanes<WARP> G(nx);
+    for (int j = G.jr; j < ny; j += G.jstep)
+        for (int i = G.ic; i < nx; i += G.istep) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                M.x[(o + j * nx + i) * NR + k] += M.x[(co + (j >> 1) * cnx + (i >> 1)) * NR + k];
+        }
+    Team<WARP>::sync();
+    for (int k = 0; k < NU_SMALL; ++k) {
+        small_sweep<T, NR, WARP>(V, M, 1);
+        small_sweep<T, NR, WARP>(V, M, 0);
+    }
 }
 
 // the V-cycle on the small levels in one block, from the level-(first small) rhs b_in to its
@@ -734,7 +931,6 @@ __device__ void small_cycle(const SmallPlan& P, const T* __restrict__ diag, cons
                             const T* __restrict__ wb, const T* __restrict__ inv, const T* __restrict__ b_in,
                             T* __restrict__ x_out, SolveState* st, unsigned char* smem) {
     SmallMem<T, NR> M(smem, P.total);
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
     // the small levels are contiguous in the packed level arrays and in shared memory: one flat
     // copy per array, four independent loads in flight per thread and array
     {
@@ -756,101 +952,37 @@ __device__ void small_cycle(const SmallPlan& P, const T* __restrict__ diag, cons
     __syncthreads();
     for (int l = 0; l < P.n; ++l) {
         int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-        for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
-            int j = c / nx, i = c - j * nx, q = o + c;
-            T dg = M.d[q] + M.wl[q] + (i < nx - 1 ? M.wl[q + 1] : T(0)) + M.wb[q] + (j < ny - 1 ? M.wb[q + nx] : T(0));
-            M.id[q] = T(1) / dg;
-        }
+        RowLanes<false> G(nx);
+        for (int j = G.jr; j < ny; j += G.jstep)
+            for (int i = G.ic; i < nx; i += G.istep) {
+                int q = o + j * nx + i;
+                T dg = M.d[q] + M.wl[q] + (i < nx - 1 ? M.wl[q + 1] : T(0)) + M.wb[q] +
+                       (j < ny - 1 ? M.wb[q + nx] : T(0));
+                M.id[q] = rcp_rn(dg);
+            }
     }
     __syncthreads();
-    // down
-    for (int l = 0; l < P.n - 1; ++l) {
-        int nx = P.nx[l], ny = P.ny[l], o = P.soff[l];
-        small_first_sweep<T, NR>(P, l, M);
-        small_sweep<T, NR>(P, l, M, 1);
-        for (int k = 1; k < NU_SMALL; ++k) {
-            small_sweep<T, NR>(P, l, M, 0);
-            small_sweep<T, NR>(P, l, M, 1);
+    // down to the first level of at most SMALL_WARP_CELLS cells (lw) on the whole block, the
+    // levels from lw on (coarsest included) on warp 0, then up on the whole block
+    int lw = P.n;
+    for (int l = 0; l < P.n; ++l)
+        if (P.nx[l] * P.ny[l] <= SMALL_WARP_CELLS) {
+            lw = l;
+            break;
         }
-        // residual, restricted to level l+1
-        int cnx = P.nx[l + 1], cny = P.ny[l + 1], co = P.soff[l + 1];
-        for (int J = ty; J < cny; J += nty) {
-            for (int I = tx; I < cnx; I += 32) {
-                T acc[NR];
-#pragma unroll
-                for (int k = 0; k < NR; ++k) acc[k] = T(0);
-                for (int d2 = 0; d2 < 4; ++d2) {
-                    int i = 2 * I + (d2 & 1), j = 2 * J + (d2 >> 1);
-                    int q = o + j * nx + i;
-                    T w0 = M.wl[q], w1 = i < nx - 1 ? M.wl[q + 1] : T(0), w2 = M.wb[q],
-                      w3 = j < ny - 1 ? M.wb[q + nx] : T(0);
-#pragma unroll
-                    for (int k = 0; k < NR; ++k) {
-                        T xq = M.x[q * NR + k];
-                        T ax = M.d[q] * xq;
-                        if (i > 0) ax += w0 * (xq - M.x[(q - 1) * NR + k]);
-                        if (i < nx - 1) ax += w1 * (xq - M.x[(q + 1) * NR + k]);
-                        if (j > 0) ax += w2 * (xq - M.x[(q - nx) * NR + k]);
-                        if (j < ny - 1) ax += w3 * (xq - M.x[(q + nx) * NR + k]);
-                        acc[k] += M.b[q * NR + k] - ax;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < NR; ++k) M.b[(co + J * cnx + I) * NR + k] = acc[k];
-            }
+    int lb = lw < P.n - 1 ? lw : P.n - 1;   // levels [0, lb) have block-wide down and up legs
+    for (int l = 0; l < lb; ++l) small_down<T, NR, false>(P, l, M);
+    if (lw < P.n) {
+        if (threadIdx.x < 32) {
+            for (int l = lw; l < P.n - 1; ++l) small_down<T, NR, true>(P, l, M);
+            small_coarsest<T, NR, true>(P, M, inv);
+            for (int l = P.n - 2; l >= lw; --l) small_up<T, NR, true>(P, l, M);
         }
         __syncthreads();
+    } else {
+        small_coarsest<T, NR, false>(P, M, inv);
     }
-    // coarsest: exact solve with the precomputed inverse (up to 32 cells), else a symmetric
-    // red-black sweep sequence from zero
-    {
-        int l = P.n - 1, o = P.soff[l], n = P.nx[l] * P.ny[l];
-        if (n <= 32 && inv[n * n] == T(1)) {
-            if (threadIdx.x < 32) {
-                int r = threadIdx.x;
-                T acc[NR];
-#pragma unroll
-                for (int k = 0; k < NR; ++k) acc[k] = T(0);
-                if (r < n)
-                    for (int c = 0; c < n; ++c) {
-                        T a = inv[r * n + c];
-#pragma unroll
-                        for (int k = 0; k < NR; ++k) acc[k] += a * M.b[(o + c) * NR + k];
-                    }
-                __syncwarp();
-                if (r < n)
-#pragma unroll
-                    for (int k = 0; k < NR; ++k) M.x[(o + r) * NR + k] = acc[k];
-            }
-            __syncthreads();
-        } else {
-            for (int c = threadIdx.x; c < n * NR; c += blockDim.x) M.x[o * NR + c] = T(0);
-            __syncthreads();
-            for (int k = 0; k < COARSE_PAIRS; ++k) {
-                small_sweep<T, NR>(P, l, M, 0);
-                small_sweep<T, NR>(P, l, M, 1);
-            }
-            for (int k = 0; k < COARSE_PAIRS; ++k) {
-                small_sweep<T, NR>(P, l, M, 1);
-                small_sweep<T, NR>(P, l, M, 0);
-            }
-        }
-    }
-    // up
-    for (int l = P.n - 2; l >= 0; --l) {
-        int nx = P.nx[l], ny = P.ny[l], o = P.soff[l], cnx = P.nx[l + 1], co = P.soff[l + 1];
-        for (int j = ty; j < ny; j += nty)
-            for (int i = tx; i < nx; i += 32) {
-#pragma unroll
-                for (int k = 0; k < NR; ++k)
-                    M.x[(o + j * nx + i) * NR + k] += M.x[(co + (j >> 1) * cnx + (i >> 1)) * NR + k];
-            }
-        __syncthreads();
-        for (int k = 0; k < NU_SMALL; ++k) {
-            small_sweep<T, NR>(P, l, M, 1);
-            small_sweep<T, NR>(P, l, M, 0);
-        }
-    }
+    for (int l = lb - 1; l >= 0; --l) small_up<T, NR, false>(P, l, M);
     for (int c = threadIdx.x; c < n0 * NR; c += blockDim.x) x_out[c] = M.x[c];
     if (DOT) {
         // the cycle started at the finest level: r.z -> beta (one block, fixed order)
@@ -1758,6 +1890,31 @@ static int coarse_start(Solver& s) {
     return nb;
 }
 
+// blocks of a persistent (TMA-staged) tile launch: one per tile, at most as many as are resident
+// on the device at once (cached per kernel and shared-memory size)
+static int persistent_blocks(const void* kern, int threads, size_t smem, int tiles) {
+    struct Entry {
+        const void* k;
+        size_t smem;
+        int dev, blocks;
+    };
+    thread_local std::vector<Entry> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int resident = 0;
+    for (const Entry& e : cache)
+        if (e.k == kern && e.smem == smem && e.dev == dev) resident = e.blocks;
+    if (resident == 0) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+        resident = per > 0 && sms > 0 ? per * sms : 1;
+        cudaGetLastError();
+        cache.push_back({kern, smem, dev, resident});
+    }
+    return tiles < resident ? tiles : resident;
+}
+
 // z = M r: r is the level-0 rhs, z the level-0 output (both NR-interleaved).
 // k_pre of level l writes the pre-smoothed x into X2_l; k_post of level l reads X2_l and the
 // coarse correction X_{l+1} (halo included) and writes the final x into X_l (z at level 0):
@@ -1780,6 +1937,8 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         int tma = s.use_tma && s.nz == 1 && s.tma_ok[ix] && (l > 0 || r == PT<T>::r(s));
         using Rg = Region<T, NR, HPRE>;
         size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, HPRE, false>::BYTES : Rg::bytes();
+        if (tma)
+            grid = dim3(persistent_blocks((const void*)k_pre<T, NR>, tile_block<HPRE>(), smem, grid.x * grid.y));
         k_pre<T, NR><<<grid, tile_block<HPRE>(), smem, stm>>>(L, b, X2 + 2 * s.loff[l], bc, st,
                                                               s.timing && l == 0 ? s.timer : nullptr,
                                                               s.tmaps[ix], tma,
@@ -1840,6 +1999,10 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         using Rg = Region<T, NR, HPOST>;
         size_t smem = tma ? Rg::bytes() + 128 + Stage<T, NR, HPOST, true>::BYTES : Rg::bytes();
         KTimer* tm = s.timing && l == 0 ? s.timer + 1 : nullptr;
+        if (tma) {
+            const void* kern = l == 0 ? (const void*)k_post<T, NR, true> : (const void*)k_post<T, NR, false>;
+            grid = dim3(persistent_blocks(kern, tile_block<HPOST>(), smem, grid.x * grid.y));
+        }
         if (l == 0)
             k_post<T, NR, true><<<grid, tile_block<HPOST>(), smem, stm>>>(L, bl, xin, xout, xc, st, s.partial,
                                                                           s.tickets + 4, tm, s.tmaps[ix], tma);

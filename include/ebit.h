@@ -76,7 +76,7 @@ enum { EBIT_FP64 = 0,         /* MG-preconditioned CG entirely in FP64          
                                  the outer residuals stay FP64                           */ };
 
 typedef struct {
-    int nx, ny;               /* cells, each >= 4                                         */
+    int nx, ny;               /* cells, each >= 4, nx * ny <= 2^29                        */
     double x0, y0, h;         /* origin and cell size (square cells)                      */
     int bc[4];                /* EBIT_BC_* per side                                       */
     int T_fixed[4];           /* 1: wall temperature T_wall[s] imposed (Dirichlet)        */

@@ -506,7 +506,7 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
     ctx->inst.resize(batch);
     for (int b = 0; b < batch; ++b) {
         const ebit_config& c = cfgs[b];
-        if (c.nx < 4 || c.ny < 4 || !(c.h > 0) || !(c.dt > 0) || c.extend_iters < 2 || c.extend_iters > 64 ||
+        if (c.nx < 4 || c.ny < 4 || (long long)c.nx * c.ny > (1LL << 29) || !(c.h > 0) || !(c.dt > 0) || c.extend_iters < 2 || c.extend_iters > 64 ||
             c.max_iter < 1 || !(c.rtol > 0) || (c.precision != EBIT_FP64 && c.precision != EBIT_MIXED)) {
             delete ctx;
             return EBIT_EINVAL;
@@ -526,6 +526,7 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         std::memset(&I.p, 0, sizeof(I.p));
         I.p.dt = c.dt; I.p.theta_min = c.theta_min; I.p.extend_iters = c.extend_iters;
         I.p.energy = c.energy; I.p.mdot_fixed = c.mdot_fixed;
+        phys_derive(I.p);
     }
     // group instances that can share batched launches (same grid, boundaries and solver settings)
     std::vector<int> group(batch, -1);
@@ -605,6 +606,7 @@ ebit_status ebit_set_phase_props(ebit_ctx* ctx, int inst, const ebit_phase_props
     Phys& p = ctx->inst[inst].p;
     p.rho_l = liq->rho; p.mu_l = liq->mu; p.lam_l = liq->lambda; p.cp_l = liq->cp;
     p.rho_v = vap->rho; p.mu_v = vap->mu; p.lam_v = vap->lambda; p.cp_v = vap->cp;
+    phys_derive(p);
     p.T_sat = T_sat; p.h_lg = h_lg; p.gx = gx; p.gy = gy;
     ctx->inst[inst].props_set = true;
     return EBIT_OK;

@@ -27,7 +27,16 @@ struct Phys {
     double dt, theta_min;
     int extend_iters, energy;
     double mdot_fixed;
+    // derived on the host (phys_derive) whenever the above change: 1 / dt and the liquid-minus-
+    // vapour differences of density and viscosity (mixtures as one fused multiply-add)
+    double inv_dt, drho, dmu;
 };
+
+__host__ inline void phys_derive(Phys& p) {
+    p.inv_dt = p.dt > 0.0 ? 1.0 / p.dt : 0.0;
+    p.drho = p.rho_l - p.rho_v;
+    p.dmu = p.mu_l - p.mu_v;
+}
 
 // Grid of one instance, or of a batch of instances that share it: a batched launch runs
 // instance z = blockIdx.z (of nz) on the arrays at byte offset z * zs from instance 0's, with

@@ -359,7 +359,7 @@ __global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flag
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
-        int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
         if (i == 0 || i == g.nx) return;
         int a = cidx(g, i - 1, j), b = cidx(g, i, j);
         if (!((flags[a] | flags[b]) & F_BAND)) return;
@@ -370,7 +370,7 @@ __global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flag
         else ufx_l[t] = ufx_v[t] + J * mf;
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
-        int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
         if (j == 0 || j == g.ny) return;
         int a = cidx(g, i, j - 1), b = cidx(g, i, j);
         if (!((flags[a] | flags[b]) & F_BAND)) return;
@@ -385,8 +385,9 @@ __global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flag
 // ---------------------------------------------------------------------------------
 // S11: momentum predictor
 // ---------------------------------------------------------------------------------
-__device__ inline double rho_mix(const Phys& p, double vf) { return p.rho_l * vf + p.rho_v * (1.0 - vf); }
-__device__ inline double mu_mix(const Phys& p, double vf) { return p.mu_l * vf + p.mu_v * (1.0 - vf); }
+// volume-fraction mixtures rho_l f + rho_v (1 - f), written as rho_v + (rho_l - rho_v) f
+__device__ inline double rho_mix(const Phys& p, double vf) { return fma(p.drho, vf, p.rho_v); }
+__device__ inline double mu_mix(const Phys& p, double vf) { return fma(p.dmu, vf, p.mu_v); }
 
 // viscous Helmholtz operator for velocity component comp (integrated form):
 //   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where comp is Dirichlet (odd),
@@ -406,7 +407,7 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
     int c = cidx(g, i, j);
     double v = vf[c];
     double mu = mu_mix(p, v);
-    cd[c] = g.h * g.h * rho_mix(p, v) / p.dt;
+    cd[c] = g.h * g.h * rho_mix(p, v) * p.inv_dt;
     double d = 0.0;
     if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu;
     if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu;
@@ -438,7 +439,7 @@ __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const do
     int j = blockIdx.y;
     if (i >= g.nx) return;
     int c = cidx(g, i, j);
-    double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
+    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt;
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
     bx[c] = make_double2(coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs_f32(Grid g, Phys p, Refl rx
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
     int c = cidx(g, i, j);
-    double coef = g.h * g.h * rho_mix(p, vf[c]) / p.dt;
+    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt;
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
     float2 fl = make_float2((float)ul.x, (float)ul.y), fv = make_float2((float)uv.x, (float)uv.y);
@@ -527,7 +528,7 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
-        int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
         double vl, vv;
         if (i > 0 && i < g.nx) {
             int a = cidx(g, i - 1, j), b = a + 1;
@@ -547,7 +548,7 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
         fx_v[t] = vv;
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
-        int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
         double vl, vv;
         if (j > 0 && j < g.ny) {
             int a = cidx(g, i, j - 1), b = cidx(g, i, j);
@@ -661,7 +662,7 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
-        int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
         double a = accel_x(g, p, P, vf, i, j);
         ax[t] = a;
         if (!fx_l) return;
@@ -672,7 +673,7 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
         fx_v[t] += corr;
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
-        int i = (int)(e % g.nx), j = (int)(e / g.nx);
+        int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
         double a = accel_y(g, p, P, vf, i, j);
         ay[e] = a;
         if (!fx_l) return;

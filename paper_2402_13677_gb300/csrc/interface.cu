@@ -272,7 +272,7 @@ __global__ void k_displace(Grid g, int axis, double dth, const uint8_t* __restri
     bool aligned;
     double* out;
     if (t < nh) {
-        int i = (int)(t % g.nx), j = (int)(t / g.nx);
+        int j = (int)((unsigned)t / (unsigned)g.nx), i = (int)t - j * g.nx;   // edges < 2^31 (nx ny <= 2^29)
         if (!hcut(g, vcol, i, j)) return;
         x = (double)i + hpos[t];
         y = (double)j;
@@ -280,7 +280,7 @@ __global__ void k_displace(Grid g, int axis, double dth, const uint8_t* __restri
         out = hdisp + t;
     } else if (t < nh + nv) {
         long long e = t - nh;
-        int i = (int)(e % (g.nx + 1)), j = (int)(e / (g.nx + 1));
+        int j = (int)((unsigned)e / (unsigned)(g.nx + 1)), i = (int)e - j * (g.nx + 1);
         if (!vcut(g, vcol, i, j)) return;
         x = (double)i;
         y = (double)j + vpos[e];

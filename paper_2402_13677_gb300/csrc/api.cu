@@ -394,8 +394,8 @@ static void momentum(Instance& I, cudaStream_t st) {
                             I.op_wb, I.op_b, st);
     count(1);
     do_solve(I, SLOT_POISSON, I.op_b, I.P, 1, st);
-    launch_project(I.g, I.p, I.P, I.vf, I.face_ax, I.face_ay, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.gc, I.us_l, I.us_v,
-                   I.u_l, I.u_v, st);
+    launch_project(I.g, I.p, I.P, I.vf, I.op_wl, I.op_wb, I.face_ax, I.face_ay, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v,
+                   I.gc, I.us_l, I.us_v, I.u_l, I.u_v, st);
     count(2);
 }
 
@@ -411,8 +411,8 @@ static void prepare(Instance& I, cudaStream_t st) {
     if (I.p.energy) extend_T(I, I.T_l, I.T_v, st);
     mass_flux(I, st);
     ghost_velocity(I, st);
-    launch_project(I.g, I.p, I.P, I.vf, I.face_ax, I.face_ay, nullptr, nullptr, nullptr, nullptr, I.gc, nullptr,
-                   nullptr, nullptr, nullptr, st);
+    launch_project(I.g, I.p, I.P, I.vf, nullptr, nullptr, I.face_ax, I.face_ay, nullptr, nullptr, nullptr, nullptr,
+                   I.gc, nullptr, nullptr, nullptr, nullptr, st);
     count(2);
 }
 
@@ -516,7 +516,7 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         if (!Solver::supported(c.nx, c.ny)) { delete ctx; return EBIT_EINVAL; }
         Instance& I = ctx->inst[b];
         I.cfg = c;
-        I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0;
+        I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0; I.g.inv_h = 1.0 / c.h;
         I.g.nz = 1; I.g.zs = 0; I.g.pz = nullptr;
         for (int s = 0; s < 4; ++s) {
             I.g.bc[s] = c.bc[s];

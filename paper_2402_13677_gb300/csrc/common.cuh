@@ -44,6 +44,7 @@ __host__ inline void phys_derive(Phys& p) {
 struct Grid {
     int nx, ny;
     double h, x0, y0;
+    double inv_h;     // 1 / h
     int bc[4];        // left, right, bottom, top
     int Tfix[4];
     double Tw[4];
@@ -61,6 +62,26 @@ __device__ __forceinline__ P* zsh(P* p, long long off) {
 __device__ __forceinline__ void zphys(const Grid& g, Phys& p) {
     if (g.pz) p = g.pz[blockIdx.z];
 }
+
+// grid-stride walk over the cells of an nx-wide grid that keeps (i, j) without a division per
+// step
+struct CellWalk {
+    int c, i, j, stride, di, dj, nx;
+    __device__ CellWalk(int nx_) : nx(nx_) {
+        c = blockIdx.x * blockDim.x + threadIdx.x;
+        stride = gridDim.x * blockDim.x;
+        i = c % nx;
+        j = c / nx;
+        di = stride % nx;
+        dj = stride / nx;
+    }
+    __device__ void next() {
+        c += stride;
+        i += di;
+        j += dj;
+        if (i >= nx) { i -= nx; ++j; }
+    }
+};
 
 __host__ __device__ inline int cidx(const Grid& g, int i, int j) { return j * g.nx + i; }
 __host__ __device__ inline int vidx(const Grid& g, int i, int j) { return j * (g.nx + 1) + i; }

@@ -622,19 +622,28 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     b[c] = -g.h * div;
 }
 
-// face accelerations a_f = g - grad_f p / rho_f (0 on walls and symmetry planes)
-__device__ inline double accel_x(const Grid& g, const Phys& p, const double* P, const double* vf, int i, int j) {
-    if (i > 0 && i < g.nx)
-        return p.gx - (P[cidx(g, i, j)] - P[cidx(g, i - 1, j)]) / (g.h * rho_mix(p, face_vf_x(g, vf, i, j)));
+// face accelerations a_f = g - grad_f p / rho_f (0 on walls and symmetry planes); on interior
+// faces, with the Poisson face weight w = dt / rho_f given (wl != null), as g - dp w / (h dt)
+__device__ inline double accel_x(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl,
+                                 int i, int j) {
+    if (i > 0 && i < g.nx) {
+        double dP = P[cidx(g, i, j)] - P[cidx(g, i - 1, j)];
+        if (wl) return p.gx - dP * wl[cidx(g, i, j)] * (g.inv_h * p.inv_dt);
+        return p.gx - dP / (g.h * rho_mix(p, face_vf_x(g, vf, i, j)));
+    }
     int s = i == 0 ? 0 : 1;
     if (g.bc[s] != BC_OUTFLOW) return 0.0;
     double r = rho_mix(p, face_vf_x(g, vf, i, j));
     if (i == 0) return p.gx - (2.0 * P[cidx(g, 0, j)]) / (g.h * r);
     return p.gx - (-2.0 * P[cidx(g, g.nx - 1, j)]) / (g.h * r);
 }
-__device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, const double* vf, int i, int j) {
-    if (j > 0 && j < g.ny)
-        return p.gy - (P[cidx(g, i, j)] - P[cidx(g, i, j - 1)]) / (g.h * rho_mix(p, face_vf_y(g, vf, i, j)));
+__device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wb,
+                                 int i, int j) {
+    if (j > 0 && j < g.ny) {
+        double dP = P[cidx(g, i, j)] - P[cidx(g, i, j - 1)];
+        if (wb) return p.gy - dP * wb[cidx(g, i, j)] * (g.inv_h * p.inv_dt);
+        return p.gy - dP / (g.h * rho_mix(p, face_vf_y(g, vf, i, j)));
+    }
     int s = j == 0 ? 2 : 3;
     if (g.bc[s] != BC_OUTFLOW) return 0.0;
     double r = rho_mix(p, face_vf_y(g, vf, i, j));
@@ -646,12 +655,15 @@ __device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, 
 // with fx_l != null also the face update u_f^{n+1} = u_f* + dt (a_f - g) (discretization
 // equation 4) for both phase fields
 __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
+                             const double* __restrict__ wl_p, const double* __restrict__ wb_p,
                              double* __restrict__ ax, double* __restrict__ ay, double* fx_l, double* fx_v,
                              double* fy_l, double* fy_v) {
     zphys(g, p);
     const long long zo = zoff(g.zs);
     P = zsh(P, zo);
     vf = zsh(vf, zo);
+    wl_p = zsh(wl_p, zo);
+    wb_p = zsh(wb_p, zo);
     ax = zsh(ax, zo);
     ay = zsh(ay, zo);
     fx_l = zsh(fx_l, zo);
@@ -663,7 +675,7 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
         int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
-        double a = accel_x(g, p, P, vf, i, j);
+        double a = accel_x(g, p, P, vf, wl_p, i, j);
         ax[t] = a;
         if (!fx_l) return;
         bool bnd = i == 0 || i == g.nx;
@@ -674,7 +686,7 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
         int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
-        double a = accel_y(g, p, P, vf, i, j);
+        double a = accel_y(g, p, P, vf, wb_p, i, j);
         ay[e] = a;
         if (!fx_l) return;
         bool bnd = j == 0 || j == g.ny;
@@ -760,8 +772,8 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
     __shared__ bool lastblk;
     double s[NDIAG_SUMS] = {0, 0, 0, 0, 0};
     int N = g.nx * g.ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        int i = c % g.nx, j = c / g.nx;
+    for (CellWalk cw(g.nx); cw.c < N; cw.next()) {
+        int c = cw.c, i = cw.i, j = cw.j;
         double v = vf[c];
         double rc = rho_mix(p, v);
         s[0] += 1.0 - v;
@@ -920,18 +932,20 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
                                                                          cd, dd, wl, wb, b);
 }
 
-void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* ax, double* ay,
-                    double* fx_l, double* fx_v, double* fy_l, double* fy_v, double2* gc, const double2* us_l,
-                    const double2* us_v, double2* u_l, double2* u_v, cudaStream_t st) {
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl_p,
+                    const double* wb_p, double* ax, double* ay, double* fx_l, double* fx_v, double* fy_l,
+                    double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l, double2* u_v,
+                    cudaStream_t st) {
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_face_accel<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, P, vf, ax, ay, fx_l, fx_v, fy_l, fy_v);
+    k_face_accel<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, P, vf, wl_p, wb_p, ax, ay, fx_l, fx_v, fy_l, fy_v);
     k_project_cells<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, ax, ay, gc, us_l, us_v, u_l, u_v);
 }
 
-// blocks of the diagnostics reduction: one per SM at most, fewer for small grids
+// blocks of the diagnostics reduction: four per SM at most (the partial sums hold 5 x 1638),
+// fewer for small grids
 int diag_blocks(const Grid& g) {
     int n = div_up((long long)g.nx * g.ny, 1024);
-    return n < 152 ? n : 152;
+    return n < 4 * 152 ? n : 4 * 152;
 }
 
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,

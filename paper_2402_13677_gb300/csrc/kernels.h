@@ -54,9 +54,12 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
                              double* wl, double* wb, double* b, cudaStream_t st);
 // ax/ay: face-acceleration scratch (x-faces ny*(nx+1), y-faces (ny+1)*nx); face velocities
 // are updated when fx_l != null
-void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, double* ax, double* ay,
-                    double* fx_l, double* fx_v, double* fy_l, double* fy_v, double2* gc, const double2* us_l,
-                    const double2* us_v, double2* u_l, double2* u_v, cudaStream_t st);
+// wl_p / wb_p: the Poisson operator's face weights dt / rho_f of the same volume fractions (they
+// replace the per-face division), or null
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl_p,
+                    const double* wb_p, double* ax, double* ay, double* fx_l, double* fx_v, double* fy_l,
+                    double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l, double2* u_v,
+                    cudaStream_t st);
 int diag_blocks(const Grid& g);
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,

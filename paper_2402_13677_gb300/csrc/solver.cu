@@ -1225,25 +1225,6 @@ __global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* _
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// grid-stride walk over the cells of an nx-wide grid that keeps (i, j) without a division per
-// step
-struct CellWalk {
-    int c, i, j, stride, di, dj, nx;
-    __device__ CellWalk(int nx_) : nx(nx_) {
-        c = blockIdx.x * blockDim.x + threadIdx.x;
-        stride = gridDim.x * blockDim.x;
-        i = c % nx;
-        j = c / nx;
-        di = stride % nx;
-        dj = stride / nx;
-    }
-    __device__ void next() {
-        c += stride;
-        i += di;
-        j += dj;
-        if (i >= nx) { i -= nx; ++j; }
-    }
-};
 
 // ---- CG kernels ---------------------------------------------------------------------------
 // p_new = z + beta p_old; q = A p_new; p.q -> alpha = r.z / p.q

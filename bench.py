@@ -333,6 +333,8 @@ def run_ours(args):
                     host[b][n] = torch.empty(cnt * eb, dtype=torch.uint8, pin_memory=True)
                     lib.ebit_get_field(ctx, b, f, host[b][n].data_ptr(), 0)
             h2d = sum(h.numel() for hb in host for h in hb.values())
+            # fields in and out through the batched copies (one synchronisation per call)
+            state = [(n, f) for n, f in ids.items() if n not in ("vcol", "hx_pos", "vy_pos")]
             diag = np.zeros(12)
             total = 0.0
             for _ in range(args.steps):
@@ -342,14 +344,11 @@ def run_ours(args):
                 for b in range(len(pbs)):
                     lib.ebit_set_interface(ctx, b, host[b]["vcol"].data_ptr(), host[b]["hx_pos"].data_ptr(),
                                            host[b]["vy_pos"].data_ptr(), 0)
-                    for n, f in ids.items():
-                        if n not in ("vcol", "hx_pos", "vy_pos"):
-                            lib.ebit_set_field(ctx, b, f, host[b][n].data_ptr(), 0)
+                    E.ebit_set_fields(ctx, b, [f for _, f in state], [host[b][n].data_ptr() for n, _ in state], 0)
                 E.ebit_run_stage(ctx, E.STAGE_RECONSTRUCT)
                 E.ebit_step(ctx, 1, allow_noconv=True)
                 for b in range(len(pbs)):
-                    for n, f in ids.items():
-                        lib.ebit_get_field(ctx, b, f, host[b][n].data_ptr(), 0)
+                    E.ebit_get_fields(ctx, b, list(ids.values()), [host[b][n].data_ptr() for n in ids], 0)
                     diag = E.ebit_get_diagnostics(ctx, b)
                 total += time.perf_counter() - t0
             total = barrier_max(total)

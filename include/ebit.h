@@ -161,6 +161,17 @@ ebit_status ebit_set_interface(ebit_ctx* ctx, int inst, const uint8_t* vcol,
 ebit_status ebit_set_field(ebit_ctx* ctx, int inst, int field, const void* src, int on_device);
 ebit_status ebit_get_field(ebit_ctx* ctx, int inst, int field, void* dst, int on_device);
 
+/* Copy n fields in (set) or out (get) in one call: field ids[k] from srcs[k] / to dsts[k]
+ * (each laid out as for ebit_set_field / ebit_get_field).  The copies are issued back to back
+ * on the context stream and, for host pointers, the stream is synchronised once after the
+ * last of them (page-locked host buffers make the copies asynchronous).  Read-only fields
+ * are rejected by ebit_set_fields; ebit_get_fields rejects EBIT_F_CCOL and EBIT_F_BAND (bits
+ * of the flag byte: use ebit_get_field).  EBIT_EINVAL names the first bad entry; no copy is
+ * issued then. */
+ebit_status ebit_set_fields(ebit_ctx* ctx, int inst, int n, const int* ids, const void* const* srcs,
+                            int on_device);
+ebit_status ebit_get_fields(ebit_ctx* ctx, int inst, int n, const int* ids, void* const* dsts, int on_device);
+
 /* Number of elements and element size of a field of instance `inst`. */
 ebit_status ebit_field_shape(const ebit_ctx* ctx, int inst, int field, size_t* count, size_t* elem_bytes);
 

@@ -621,30 +621,24 @@ ebit_status ebit_set_interface(ebit_ctx* ctx, int inst, const uint8_t* vcol, con
     size_t nv = (size_t)(g.nx + 1) * (g.ny + 1), nh = (size_t)(g.ny + 1) * g.nx, nve = (size_t)g.ny * (g.nx + 1);
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (!on_device) {
-        // host-side validation: colours 0/1, cut fractions inside (0, 1); uncut fractions zeroed
-        std::vector<double> hp(hx_pos, hx_pos + nh), vp(vy_pos, vy_pos + nve);
-        for (size_t v = 0; v < nv; ++v)
-            if (vcol[v] > 1) return fail(ctx, EBIT_EINVAL, "vertex colours must be 0 or 1");
-        for (int j = 0; j <= g.ny; ++j)
-            for (int i = 0; i < g.nx; ++i) {
-                size_t e = (size_t)j * g.nx + i;
-                bool cut = vcol[(size_t)j * (g.nx + 1) + i] != vcol[(size_t)j * (g.nx + 1) + i + 1];
-                if (!cut) hp[e] = 0.0;
-                else if (!(hp[e] >= FMIN && hp[e] <= 1.0 - FMIN))
-                    return fail(ctx, EBIT_ETOPO, "cut horizontal edge with a marker fraction outside [1e-9, 1-1e-9]");
-            }
-        for (int j = 0; j < g.ny; ++j)
-            for (int i = 0; i <= g.nx; ++i) {
-                size_t e = (size_t)j * (g.nx + 1) + i;
-                bool cut = vcol[(size_t)j * (g.nx + 1) + i] != vcol[(size_t)(j + 1) * (g.nx + 1) + i];
-                if (!cut) vp[e] = 0.0;
-                else if (!(vp[e] >= FMIN && vp[e] <= 1.0 - FMIN))
-                    return fail(ctx, EBIT_ETOPO, "cut vertical edge with a marker fraction outside [1e-9, 1-1e-9]");
-            }
-        cudaMemcpyAsync(I.vcol, vcol, nv, k, ctx->stream);
-        cudaMemcpyAsync(I.hpos, hp.data(), nh * 8, k, ctx->stream);
-        cudaMemcpyAsync(I.vpos, vp.data(), nve * 8, k, ctx->stream);
-        cudaStreamSynchronize(ctx->stream);
+        // validated on the device: the upload lands in the sweep scratch arrays, is checked there
+        // (colours 0/1, cut fractions inside [FMIN, 1 - FMIN]; uncut fractions zeroed) and only
+        // then replaces the instance's interface, so a rejected upload leaves it unchanged
+        int* err = I.status + 32;
+        cudaMemcpyAsync(I.vcol_n, vcol, nv, k, ctx->stream);
+        cudaMemcpyAsync(I.hpos_n, hx_pos, nh * 8, k, ctx->stream);
+        cudaMemcpyAsync(I.vpos_n, vy_pos, nve * 8, k, ctx->stream);
+        cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
+        launch_check_interface(g, I.vcol_n, I.hpos_n, I.vpos_n, err, ctx->stream);
+        int herr = 0;
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t ce = cudaStreamSynchronize(ctx->stream);
+        if (ce != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(ce));
+        if (herr & 1) return fail(ctx, EBIT_EINVAL, "vertex colours must be 0 or 1");
+        if (herr & 2) return fail(ctx, EBIT_ETOPO, "cut edge with a marker fraction outside [1e-9, 1-1e-9]");
+        cudaMemcpyAsync(I.vcol, I.vcol_n, nv, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaMemcpyAsync(I.hpos, I.hpos_n, nh * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaMemcpyAsync(I.vpos, I.vpos_n, nve * 8, cudaMemcpyDeviceToDevice, ctx->stream);
     } else {
         cudaMemcpyAsync(I.vcol, vcol, nv, k, ctx->stream);
         cudaMemcpyAsync(I.hpos, hx_pos, nh * 8, k, ctx->stream);
@@ -700,6 +694,49 @@ ebit_status ebit_get_field(ebit_ctx* ctx, int inst, int field, void* dst, int on
     cudaError_t er = cudaStreamSynchronize(ctx->stream);
     if (er != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(er));
     return cuda_check(ctx, "ebit_get_field");
+}
+
+ebit_status ebit_set_fields(ebit_ctx* ctx, int inst, int n, const int* ids, const void* const* srcs,
+                            int on_device) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || n < 0 || (n > 0 && (!ids || !srcs)))
+        return fail(ctx, EBIT_EINVAL, "bad args");
+    Instance& I = ctx->inst[inst];
+    for (int k = 0; k < n; ++k) {
+        int f = ids[k];
+        size_t e;
+        if (f == EBIT_F_VF || f == EBIT_F_CCOL || f == EBIT_F_BAND || f == EBIT_F_NB || f == EBIT_F_CSEG ||
+            f == EBIT_F_UG || !srcs[k] || !field_count(I.g, f, &e) || !field_ptr(I, f))
+            return fail(ctx, EBIT_EINVAL, "ebit_set_fields: entry " + std::to_string(k) + " is not a writable field");
+    }
+    for (int k = 0; k < n; ++k) {
+        size_t e;
+        size_t cnt = field_count(I.g, ids[k], &e);
+        cudaMemcpyAsync(field_ptr(I, ids[k]), srcs[k], cnt * e,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
+    }
+    if (!on_device) cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, "ebit_set_fields");
+}
+
+ebit_status ebit_get_fields(ebit_ctx* ctx, int inst, int n, const int* ids, void* const* dsts, int on_device) {
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || n < 0 || (n > 0 && (!ids || !dsts)))
+        return fail(ctx, EBIT_EINVAL, "bad args");
+    Instance& I = ctx->inst[inst];
+    for (int k = 0; k < n; ++k) {
+        int f = ids[k];
+        size_t e;
+        if (f == EBIT_F_CCOL || f == EBIT_F_BAND || !dsts[k] || !field_count(I.g, f, &e) || !field_ptr(I, f))
+            return fail(ctx, EBIT_EINVAL, "ebit_get_fields: entry " + std::to_string(k) + " is not a readable field");
+    }
+    for (int k = 0; k < n; ++k) {
+        size_t e;
+        size_t cnt = field_count(I.g, ids[k], &e);
+        cudaMemcpyAsync(dsts[k], field_ptr(I, ids[k]), cnt * e,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    cudaError_t er = cudaStreamSynchronize(ctx->stream);
+    if (er != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(er));
+    return cuda_check(ctx, "ebit_get_fields");
 }
 
 ebit_status ebit_set_time(ebit_ctx* ctx, int inst, double t) {

@@ -760,9 +760,40 @@ __global__ void k_mass_flux(Grid g, Phys p, const uint16_t* __restrict__ cseg, c
     mdot[c] = den > 0.0 ? num / den : 0.0;
 }
 
+// check of an uploaded interface (one instance): vertex colours 0 or 1 (err bit 0), every cut
+// edge's marker fraction inside [FMIN, 1 - FMIN] (err bit 1); fractions of uncut edges are set
+// to 0.  One thread per vertex / h-edge / v-edge index.
+__global__ void k_check_interface(Grid g, const uint8_t* __restrict__ vcol, double* __restrict__ hpos,
+                                  double* __restrict__ vpos, int* __restrict__ err) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nv = (long long)(g.nx + 1) * (g.ny + 1), nh = (long long)(g.ny + 1) * g.nx,
+              nve = (long long)g.ny * (g.nx + 1);
+    int bad = 0;
+    if (t < nv && vcol[t] > 1) bad |= 1;
+    if (t < nh) {
+        int j = (int)((unsigned)t / (unsigned)g.nx), i = (int)t - j * g.nx;
+        double f = hpos[t];
+        if (!hcut(g, vcol, i, j)) hpos[t] = 0.0;
+        else if (!(f >= FMIN && f <= 1.0 - FMIN)) bad |= 2;
+    }
+    if (t < nve) {
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
+        double f = vpos[t];
+        if (!vcut(g, vcol, i, j)) vpos[t] = 0.0;
+        else if (!(f >= FMIN && f <= 1.0 - FMIN)) bad |= 2;
+    }
+    if (bad) atomicOr(err, bad);
+}
+
 // ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
+
+void launch_check_interface(const Grid& g, const uint8_t* vcol, double* hpos, double* vpos, int* err,
+                            cudaStream_t st) {
+    long long n = (long long)(g.nx + 1) * (g.ny + 1);
+    k_check_interface<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, vcol, hpos, vpos, err);
+}
 
 void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, const double* vpos,
                         uint16_t* cseg, uint8_t* flags, double* vf, cudaStream_t st) {

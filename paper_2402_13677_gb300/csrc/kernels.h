@@ -8,6 +8,10 @@
 namespace ebit {
 
 // interface.cu (FP64, no FMA contraction)
+// validation of an uploaded interface; err (device, zeroed by the caller): bit 0 a colour other
+// than 0/1, bit 1 a cut edge with a fraction outside [FMIN, 1 - FMIN]; uncut fractions set to 0
+void launch_check_interface(const Grid& g, const uint8_t* vcol, double* hpos, double* vpos, int* err,
+                            cudaStream_t st);
 void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, const double* vpos, uint16_t* cseg,
                         uint8_t* flags, double* vf, cudaStream_t st);
 void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, uint8_t* flags,

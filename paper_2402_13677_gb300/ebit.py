@@ -34,7 +34,7 @@ FIELD_DTYPES = {F_CCOL: np.uint8, F_BAND: np.uint8, F_VCOL: np.uint8, F_CSEG: np
  STAGE_EXTEND_T, STAGE_MASS_FLUX, STAGE_GHOST_VELOCITY, STAGE_MOMENTUM, STAGE_DIAGNOSTICS) = range(11)
 
 EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_field", "ebit_get_field",
-           "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
+           "ebit_set_fields", "ebit_get_fields", "ebit_field_shape", "ebit_set_time", "ebit_run_stage", "ebit_step", "ebit_get_diagnostics",
            "ebit_launch_count", "ebit_timing_begin", "ebit_timing_end", "ebit_set_option", "ebit_solve_system",
            "ebit_solve_system_noalloc", "ebit_autotune", "ebit_get_schedule", "ebit_last_error",
            "ebit_destroy", "ebit_version"]
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.ebit_set_interface.argtypes = [vp, i32, vp, vp, vp, i32]
     lib.ebit_set_field.argtypes = [vp, i32, i32, vp, i32]
     lib.ebit_get_field.argtypes = [vp, i32, i32, vp, i32]
+    lib.ebit_set_fields.argtypes = [vp, i32, i32, C.POINTER(C.c_int), C.POINTER(vp), i32]
+    lib.ebit_get_fields.argtypes = [vp, i32, i32, C.POINTER(C.c_int), C.POINTER(vp), i32]
     lib.ebit_field_shape.argtypes = [vp, i32, i32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
     lib.ebit_set_time.argtypes = [vp, i32, f64]
     lib.ebit_run_stage.argtypes = [vp, i32]
@@ -186,6 +188,26 @@ def ebit_field_shape(ctx, inst, field):
     n, e = C.c_size_t(), C.c_size_t()
     _check(ctx, load().ebit_field_shape(ctx, inst, field, C.byref(n), C.byref(e)))
     return n.value, e.value
+
+
+def _field_batch(fields, ptrs):
+    n = len(fields)
+    ids = (C.c_int * n)(*fields)
+    pp = (C.c_void_p * n)(*ptrs)
+    return n, ids, pp
+
+
+def ebit_set_fields(ctx, inst, fields, ptrs, on_device):
+    """Copy several fields in with one call: fields (ids) and raw pointers (host page-locked or
+    device, per on_device), one synchronisation for host pointers."""
+    n, ids, pp = _field_batch(fields, ptrs)
+    _check(ctx, load().ebit_set_fields(ctx, inst, n, ids, pp, 1 if on_device else 0))
+
+
+def ebit_get_fields(ctx, inst, fields, ptrs, on_device):
+    """Copy several fields out with one call (raw pointers as for ebit_set_fields)."""
+    n, ids, pp = _field_batch(fields, ptrs)
+    _check(ctx, load().ebit_get_fields(ctx, inst, n, ids, pp, 1 if on_device else 0))
 
 
 def ebit_get_field(ctx, inst, field, out=None):

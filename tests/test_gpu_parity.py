@@ -342,6 +342,14 @@ def test_edge_cases_empty_interface_and_invalid_input(dev):
         with pytest.raises(E.EbitError) as ei:
             E.ebit_set_interface(ctx, 0, vcol, bad, pb.vy_pos)
         assert ei.value.status == E.EBIT_ETOPO
+        # a rejected upload (checked on the device) leaves the instance's interface unchanged
+        assert np.all(E.download(ctx, 0, pb.nx, pb.ny, ["vcol"])["vcol"] == 1)
+        vcol2 = pb.vcol.copy()
+        vcol2[1, 1] = 2                   # not a colour
+        with pytest.raises(E.EbitError) as ei:
+            E.ebit_set_interface(ctx, 0, vcol2, pb.hx_pos, pb.vy_pos)
+        assert ei.value.status == E.EBIT_EINVAL
+        assert np.all(E.download(ctx, 0, pb.nx, pb.ny, ["vcol"])["vcol"] == 1)
     finally:
         E.ebit_destroy(ctx)
 
@@ -418,3 +426,42 @@ def test_cooperative_coarse_cycle_equals_separate_launches(dev, name, precision)
             E.ebit_destroy(ctx)
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_batched_field_copies_equal_single_field_copies(dev):
+    """ebit_set_fields / ebit_get_fields (one synchronisation per call) move the same bytes as
+    one ebit_set_field / ebit_get_field per field, from and to page-locked host buffers and
+    device buffers; bad entries are rejected before any copy."""
+    st = prepared("bubble_mid", 0)
+    nx, ny = st.pb.nx, st.pb.ny
+    ctx = gpu_ctx(dev, st)
+    try:
+        E.ebit_step(ctx, 1)
+        ids = [E.F_T_L, E.F_T_V, E.F_U_L, E.F_UFX_V, E.F_UFY_L, E.F_P, E.F_GC, E.F_MDOT, E.F_VCOL, E.F_HX_POS]
+        ref = {f: E.ebit_get_field(ctx, 0, f) for f in ids}
+        host = {f: torch.empty(ref[f].nbytes, dtype=torch.uint8, pin_memory=True) for f in ids}
+        E.ebit_get_fields(ctx, 0, ids, [host[f].data_ptr() for f in ids], 0)
+        for f in ids:
+            assert np.array_equal(host[f].numpy().view(ref[f].dtype), ref[f]), f
+        # device round trip: out to CUDA buffers, perturb the instance, back in
+        devb = {f: torch.empty(ref[f].nbytes, dtype=torch.uint8, device="cuda") for f in ids}
+        E.ebit_get_fields(ctx, 0, ids, [devb[f].data_ptr() for f in ids], 1)
+        torch.cuda.synchronize()
+        writable = [f for f in ids if f not in (E.F_VCOL, E.F_HX_POS)]
+        for f in writable:
+            E.ebit_set_field(ctx, 0, f, np.zeros_like(ref[f]))
+        E.ebit_set_fields(ctx, 0, writable, [devb[f].data_ptr() for f in writable], 1)
+        for f in writable:
+            assert np.array_equal(E.ebit_get_field(ctx, 0, f), ref[f]), f
+        # host upload of perturbed values, checked field by field
+        for f in writable:
+            host[f].numpy().view(ref[f].dtype)[:] = ref[f] + 1
+        E.ebit_set_fields(ctx, 0, writable, [host[f].data_ptr() for f in writable], 0)
+        for f in writable:
+            assert np.array_equal(E.ebit_get_field(ctx, 0, f), ref[f] + 1), f
+        with pytest.raises(E.EbitError) as ei:   # read-only field
+            E.ebit_set_fields(ctx, 0, [E.F_T_L, E.F_VF], [host[E.F_T_L].data_ptr(), host[E.F_P].data_ptr()], 0)
+        assert ei.value.status == E.EBIT_EINVAL
+        assert np.array_equal(E.ebit_get_field(ctx, 0, E.F_T_L), ref[E.F_T_L] + 1)   # nothing copied
+    finally:
+        E.ebit_destroy(ctx)

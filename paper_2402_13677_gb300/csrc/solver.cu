@@ -1533,7 +1533,9 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
             st->orr[k] = rr;
             if (!(rr <= st->otol2[k])) done = false;
             st->rr[k] = rr;
-            st->tol2[k] = st->inner_rtol * st->inner_rtol * rr;
+            // the inner solve reduces the residual by inner_rtol, but never below half the
+            // outer target: no solve past what the refinement needs
+            st->tol2[k] = fmax(st->inner_rtol * st->inner_rtol * rr, 0.25 * st->otol2[k]);
             st->rz[k] = 0.0;
             st->beta[k] = 0.0;
         }

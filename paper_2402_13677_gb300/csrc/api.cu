@@ -506,7 +506,8 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
     ctx->inst.resize(batch);
     for (int b = 0; b < batch; ++b) {
         const ebit_config& c = cfgs[b];
-        if (c.nx < 4 || c.ny < 4 || (long long)c.nx * c.ny > (1LL << 29) || !(c.h > 0) || !(c.dt > 0) || c.extend_iters < 2 || c.extend_iters > 64 ||
+        if (c.nx < 4 || c.ny < 4 || (long long)c.nx * c.ny > (1LL << 29) || !(c.h > 0) || !(c.dt > 0) ||
+            c.extend_iters < 2 || c.extend_iters > 64 ||
             c.max_iter < 1 || !(c.rtol > 0) || (c.precision != EBIT_FP64 && c.precision != EBIT_MIXED)) {
             delete ctx;
             return EBIT_EINVAL;

@@ -359,7 +359,8 @@ __global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flag
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
-        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
+        // faces < 2^31 (nx ny <= 2^29): 32-bit division
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
         if (i == 0 || i == g.nx) return;
         int a = cidx(g, i - 1, j), b = cidx(g, i, j);
         if (!((flags[a] | flags[b]) & F_BAND)) return;
@@ -528,7 +529,8 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
-        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
+        // faces < 2^31 (nx ny <= 2^29): 32-bit division
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
         double vl, vv;
         if (i > 0 && i < g.nx) {
             int a = cidx(g, i - 1, j), b = a + 1;
@@ -674,7 +676,8 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
     long long nfx = (long long)g.ny * (g.nx + 1);
     long long nfy = (long long)(g.ny + 1) * g.nx;
     if (t < nfx) {
-        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);   // faces < 2^31 (nx ny <= 2^29)
+        // faces < 2^31 (nx ny <= 2^29): 32-bit division
+        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
         double a = accel_x(g, p, P, vf, wl_p, i, j);
         ax[t] = a;
         if (!fx_l) return;

@@ -615,7 +615,8 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
     if (use_tma) {
         // persistent blocks over the tiles (1-D grid), TMA boxes 128-byte aligned after the
         // region (the launch reserves 128 bytes of slack)
-        unsigned char* stage = reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
+        unsigned char* stage =
+            reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
         staged_tiles<T, NR, H, false>(stage, maps, tx, nt, st, [&](int t, auto after_load) {
             pre_tile<T, NR>(L, b, x, bc, t % tx, t / tx, smem, stage, after_load);
@@ -689,7 +690,8 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
     int nslot = gridDim.x * gridDim.y;
     if (use_tma) {
         // persistent blocks over the tiles (1-D grid); r.z summed over the block's tiles
-        unsigned char* stage = reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
+        unsigned char* stage =
+            reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
         // r.z: one slot per tile, summed in tile order as with one block per tile
         staged_tiles<T, NR, H, true>(stage, maps, tx, nt, st, [&](int t, auto after_load) {

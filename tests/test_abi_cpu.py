@@ -75,6 +75,7 @@ def test_struct_layout_matches_header(tmp_path):
     lambda c: setattr(c, "precision", 7),
     lambda c: c.bc.__setitem__(0, 9),
     lambda c: setattr(c, "rtol", 0.0),
+    lambda c: (setattr(c, "nx", 1 << 15), setattr(c, "ny", (1 << 14) + 2)),   # more than 2^29 cells
 ])
 def test_init_rejects_invalid_config_without_device(lib, mutate):
     pb = w.stefan(16, 4, steps=0)

@@ -364,6 +364,9 @@ __device__ inline void staged_tiles(unsigned char* sbase, const TileMaps& M, int
 template <typename T, int NR>
 struct Cells {
     T b[2][2][NR], id[2][2], wl[2][2], wr[2][2], wb[2][2], wt[2][2], d[2][2];
+    // the cells' current x (the copy in shared memory is for the neighbour threads): two of a
+    // cell's four neighbours are the thread's own cells of the other colour
+    T x[2][2][NR];
 };
 
 // load the thread's cells (coefficients to registers, x to shared memory: for pre-smoothing
@@ -467,15 +470,21 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, in
             }
             T* xd = R.x(cc) + (ry * HX + k) * NR;
 #pragma unroll
-            for (int k2 = 0; k2 < NR; ++k2) xd[k2] = xv.v[k2];
+            for (int k2 = 0; k2 < NR; ++k2) {
+                xd[k2] = xv.v[k2];
+                C.x[r][cc][k2] = xv.v[k2];
+            }
         }
     }
 }
 
 // one Gauss-Seidel half-sweep of colour COLOR over the region cells at distance >= S from its
-// edge; both rows' operands are loaded before either result is stored
+// edge; both rows' operands are loaded before either result is stored.  Cell (r, e) of the
+// thread (colour COLOR, e = COLOR ^ r) has its horizontal neighbour 2k + 1 - e and its vertical
+// neighbour in row 1 - r among the thread's own cells (registers); the other two come from the
+// neighbour threads through shared memory.
 template <typename T, int NR, int H, int S, int COLOR>
-__device__ inline void tile_sweep(Region<T, NR, H>& R, const Cells<T, NR>& C, int k, int ry0, bool act) {
+__device__ inline void tile_sweep(Region<T, NR, H>& R, Cells<T, NR>& C, int k, int ry0, bool act) {
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX, SX = Rg::SX, SY = Rg::SY;
     if (act) {
@@ -486,25 +495,32 @@ __device__ inline void tile_sweep(Region<T, NR, H>& R, const Cells<T, NR>& C, in
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             int ry = ry0 + r;
-            int e = COLOR ^ r;
+            const int e = COLOR ^ r;
             int rx = 2 * k + e;
             ok[r] = ry >= S && ry < SY - S && rx >= S && rx < SX - S;
             int q = ok[r] ? ry * HX + k : HX + 1;   // a harmless in-range slot otherwise
-            int ee = ok[r] ? e : 0;
             qs[r] = q;
 #pragma unroll
-            for (int k2 = 0; k2 < NR; ++k2)
-                acc[r][k2] = (C.b[r][COLOR][k2] + C.wl[r][COLOR] * xo[(q - 1 + ee) * NR + k2] +
-                              C.wr[r][COLOR] * xo[(q + ee) * NR + k2] + C.wb[r][COLOR] * xo[(q - HX) * NR + k2] +
-                              C.wt[r][COLOR] * xo[(q + HX) * NR + k2]) *
+            for (int k2 = 0; k2 < NR; ++k2) {
+                const T own_h = C.x[r][1 - COLOR][k2], own_v = C.x[1 - r][1 - COLOR][k2];
+                T xl = e == 1 ? own_h : xo[(q - 1) * NR + k2];
+                T xrt = e == 0 ? own_h : xo[(q + 1) * NR + k2];
+                T xd = r == 1 ? own_v : xo[(q - HX) * NR + k2];
+                T xu = r == 0 ? own_v : xo[(q + HX) * NR + k2];
+                acc[r][k2] = (C.b[r][COLOR][k2] + C.wl[r][COLOR] * xl + C.wr[r][COLOR] * xrt +
+                              C.wb[r][COLOR] * xd + C.wt[r][COLOR] * xu) *
                              C.id[r][COLOR];
+            }
         }
         T* xs = R.x(COLOR);
 #pragma unroll
         for (int r = 0; r < 2; ++r)
             if (ok[r])
 #pragma unroll
-                for (int k2 = 0; k2 < NR; ++k2) xs[qs[r] * NR + k2] = acc[r][k2];
+                for (int k2 = 0; k2 < NR; ++k2) {
+                    xs[qs[r] * NR + k2] = acc[r][k2];
+                    C.x[r][COLOR][k2] = acc[r][k2];
+                }
     }
     __syncthreads();
 }
@@ -559,16 +575,19 @@ __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __r
     if (act)
         tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
             const T* xo = R.x(1 - c);
-            const T* xm = R.x(c);
-            int e = rx & 1;
+            const int e = c ^ r;   // rx = 2k + e
             Vec<T, NR> xv;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
-                T x0v = xm[q * NR + k2];
+                T x0v = C.x[r][c][k2];
                 xv.v[k2] = x0v;
-                T ax = C.d[r][c] * x0v + C.wl[r][c] * (x0v - xo[(q - 1 + e) * NR + k2]) +
-                       C.wr[r][c] * (x0v - xo[(q + e) * NR + k2]) + C.wb[r][c] * (x0v - xo[(q - HX) * NR + k2]) +
-                       C.wt[r][c] * (x0v - xo[(q + HX) * NR + k2]);
+                const T own_h = C.x[r][1 - c][k2], own_v = C.x[1 - r][1 - c][k2];
+                T xl = e == 1 ? own_h : xo[(q - 1) * NR + k2];
+                T xrt = e == 0 ? own_h : xo[(q + 1) * NR + k2];
+                T xd = r == 1 ? own_v : xo[(q - HX) * NR + k2];
+                T xu = r == 0 ? own_v : xo[(q + HX) * NR + k2];
+                T ax = C.d[r][c] * x0v + C.wl[r][c] * (x0v - xl) + C.wr[r][c] * (x0v - xrt) +
+                       C.wb[r][c] * (x0v - xd) + C.wt[r][c] * (x0v - xu);
                 res[((ry - H) * TX + (rx - H)) * NR + k2] = C.b[r][c][k2] - ax;
             }
             reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
@@ -652,11 +671,10 @@ __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, co
     double dot[2] = {0.0, 0.0};
     if (act)
         tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
-            const T* xm = R.x(c);
             Vec<T, NR> xv;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
-                xv.v[k2] = xm[q * NR + k2];
+                xv.v[k2] = C.x[r][c][k2];
                 if (DOT) dot[k2] += (double)xv.v[k2] * (double)C.b[r][c][k2];
             }
             reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;

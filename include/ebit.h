@@ -200,7 +200,8 @@ uint64_t ebit_launch_count(const ebit_ctx* ctx);
  * ebit_timing_end synchronises and returns the summed kernel time, the number of timed
  * launches and the algorithmic bytes of an average launch (pre: b, diag, wl, wb read, x and a
  * quarter-size coarse b written; post: x, a quarter-size coarse x, b, diag, wl, wb read, x
- * written; one word per value, 4 bytes in the mixed mode, 8 in FP64, per right-hand side). */
+ * written; one word per value, 4 bytes in the mixed mode, 8 in FP64, per right-hand side).  A
+ * batched launch counts once, with the bytes of all its instances that had not converged. */
 enum { EBIT_KT_SMOOTH_L0 = 1 };
 ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class);
 ebit_status ebit_timing_end(ebit_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes_per_launch);

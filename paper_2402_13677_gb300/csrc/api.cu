@@ -1129,7 +1129,7 @@ ebit_status ebit_timing_begin(ebit_ctx* ctx, int kernel_class) {
     for (auto& I : ctx->inst) {
         KTimer z[2];
         for (auto& t : z) {
-            t.start = ~0ull; t.end = 0; t.ticket = 0; t.pad = 0; t.total_ns = 0; t.launches = 0; t.bytes = 0.0;
+            t.start = ~0ull; t.end = 0; t.ticket = 0; t.active = 0; t.total_ns = 0; t.launches = 0; t.bytes = 0.0;
         }
         cudaMemcpyAsync(I.solver.timer, z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
         cudaMemcpyAsync(I.solver2.timer, z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream);

@@ -86,27 +86,41 @@ __device__ inline unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Device timing of a tile-kernel launch (one timer per launch; the instances of a batched launch
+// share their lead's).  Every block arrives once: a block that runs records its start and end
+// (and the first block of each instance counts that instance as active), a block of a converged
+// instance only arrives.  The last block to arrive adds the launch's span (first start to last
+// end), its launch and the algorithmic bytes of its active instances, and resets the timer.
 __device__ inline void timer_begin(KTimer* tm) {
-    if (tm && threadIdx.x == 0) atomicMin(&tm->start, gtimer());
+    if (tm && threadIdx.x == 0) {
+        atomicMin(&tm->start, gtimer());
+        if (blockIdx.x == 0 && blockIdx.y == 0) atomicAdd(&tm->active, 1u);
+    }
 }
-__device__ inline void timer_end(KTimer* tm, double bytes) {
+__device__ inline void timer_arrive(KTimer* tm, double bytes_per_instance, bool ran) {
     if (!tm) return;
     __syncthreads();
     if (threadIdx.x == 0) {
-        atomicMax(&tm->end, gtimer());
+        if (ran) atomicMax(&tm->end, gtimer());
         __threadfence();
-        unsigned int n = gridDim.x * gridDim.y;
+        unsigned int n = gridDim.x * gridDim.y * gridDim.z;
         if (atomicAdd(&tm->ticket, 1u) == n - 1) {
+            __threadfence();
             unsigned long long s = atomicAdd(&tm->start, 0ull), e = atomicAdd(&tm->end, 0ull);
-            tm->total_ns += e > s ? e - s : 0ull;
-            tm->launches += 1;
-            tm->bytes += bytes;
+            unsigned act = atomicAdd(&tm->active, 0u);
+            if (act > 0) {
+                tm->total_ns += e > s ? e - s : 0ull;
+                tm->launches += 1;
+                tm->bytes += bytes_per_instance * act;
+            }
             tm->start = ~0ull;
             tm->end = 0ull;
             tm->ticket = 0u;
+            tm->active = 0u;
         }
     }
 }
+__device__ inline void timer_end(KTimer* tm, double bytes_per_instance) { timer_arrive(tm, bytes_per_instance, true); }
 
 // ---- block reductions ---------------------------------------------------------------
 __device__ inline double bsum(double v, double* sh) {
@@ -333,7 +347,8 @@ __device__ inline void stage_init(unsigned char* sbase) {
 // (into registers and the region), so the copies overlap the current tile's sweeps.  work(t,
 // after_load) runs tile t and calls after_load() once the boxes have been read and the block has
 // passed a barrier.  A copy that does not land within the bound sets st->fault bit 0 and ends
-// the loop (the decision is the same in every thread).
+// the loop (the decision is the same in every thread) after one more bounded wait for that
+// copy, the only one in flight.
 template <typename T, int NR, int H, bool POST, class Work>
 __device__ inline void staged_tiles(unsigned char* sbase, const TileMaps& M, int tx, int nt, SolveState* st,
                                     Work&& work) {
@@ -346,6 +361,8 @@ __device__ inline void staged_tiles(unsigned char* sbase, const TileMaps& M, int
         bool landed = mbar_wait_bounded(bar, i & 1u);
         if (__syncthreads_or(!landed)) {
             if (threadIdx.x == 0) atomicOr(&st->fault, 1);
+            mbar_wait_bounded(bar, i & 1u);
+            __syncthreads();
             break;
         }
         int tn = t + gridDim.x;
@@ -625,8 +642,11 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
     x = zsh(x, zo);
     bc = zsh(bc, zo);
     st = zsh(st, zo);
-    tm = zsh(tm, zo);
-    if (skip(st)) return;
+    constexpr double bytes_cell = sizeof(T) * (3.0 + NR * 2.25);
+    if (skip(st)) {
+        timer_arrive(tm, 0.0, false);
+        return;
+    }
     constexpr int H = HPRE;
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -644,7 +664,7 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
         pre_tile<T, NR>(L, b, x, bc, blockIdx.x, blockIdx.y, smem, nullptr);
     }
     // algorithmic bytes: b, diag, wl, wb read; x and the quarter-size coarse b written
-    timer_end(tm, (double)L.nx * L.ny * sizeof(T) * (3.0 + NR * 2.25));
+    timer_end(tm, (double)L.nx * L.ny * bytes_cell);
 }
 
 // post-smoothing of tile (bx, by): x = xin + P xc, then black-red sweeps; returns the tile's
@@ -699,8 +719,11 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
     st = zsh(st, zo);
     partial = zsh(partial, zo);
     ticket = zsh(ticket, zo);
-    tm = zsh(tm, zo);
-    if (skip(st)) return;
+    constexpr double bytes_cell = sizeof(T) * (3.0 + NR * 3.25);
+    if (skip(st)) {
+        timer_arrive(tm, 0.0, false);
+        return;
+    }
     constexpr int H = HPOST;
     using Rg = Region<T, NR, H>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -739,7 +762,7 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
         }
     }
     // algorithmic bytes: b, x, the quarter-size coarse x, diag, wl, wb read; x written
-    timer_end(tm, (double)L.nx * L.ny * sizeof(T) * (3.0 + NR * 3.25));
+    timer_end(tm, (double)L.nx * L.ny * bytes_cell);
 }
 
 // ---- small levels: the rest of the V-cycle in one block ---------------------------------

@@ -23,7 +23,7 @@ struct KTimer {
     unsigned long long start;
     unsigned long long end;
     unsigned int ticket;
-    unsigned int pad;
+    unsigned int active;   // instances of the current launch that ran (not converged)
     unsigned long long total_ns;
     unsigned long long launches;
     double bytes;      // algorithmic bytes of the timed launches (each launch adds its own)

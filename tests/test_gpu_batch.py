@@ -127,3 +127,25 @@ def test_autotune_restores_state_and_picks_a_candidate(dev):
                 assert np.max(np.abs(tuned[b][k] - ref[k])) <= 1e-6 * scale, (b, k)
     finally:
         E.ebit_destroy(ref_ctx)
+
+
+def test_batched_launch_timer_counts_each_launch_once(dev):
+    """The device timer of the finest-level smoother kernels counts a batched launch once, with
+    the algorithmic bytes of all its instances: a batch of four identical instances reports as
+    many timed launches as one instance stepped alone, and four times its bytes per launch."""
+    pb = batch_problems()[0]
+    nz = 4
+    out = []
+    for count in (nz, 1):
+        ctx = make_ctx(dev, [pb] * count, E.EBIT_MIXED)
+        try:
+            E.ebit_step(ctx, 1)
+            E.ebit_timing_begin(ctx)
+            E.ebit_step(ctx, 1)
+            out.append(E.ebit_timing_end(ctx))
+        finally:
+            E.ebit_destroy(ctx)
+    (ms_b, n_b, b_b), (ms_1, n_1, b_1) = out
+    assert n_1 > 0 and n_b == n_1
+    assert ms_b > 0 and ms_1 > 0
+    assert b_b == pytest.approx(nz * b_1, rel=1e-12)

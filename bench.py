@@ -19,6 +19,7 @@ path, only the timing barrier and the max-over-ranks reduction.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -333,8 +334,14 @@ def run_ours(args):
                     host[b][n] = torch.empty(cnt * eb, dtype=torch.uint8, pin_memory=True)
                     lib.ebit_get_field(ctx, b, f, host[b][n].data_ptr(), 0)
             h2d = sum(h.numel() for hb in host for h in hb.values())
-            # fields in and out through the batched copies (one synchronisation per call)
+            # fields in and out through the batched copies (one synchronisation per call); the
+            # id and pointer arrays are built once
             state = [(n, f) for n, f in ids.items() if n not in ("vcol", "hx_pos", "vy_pos")]
+            ids_in = (ctypes.c_int * len(state))(*[f for _, f in state])
+            ids_out = (ctypes.c_int * len(ids))(*ids.values())
+            ptr_in = [(ctypes.c_void_p * len(state))(*[host[b][n].data_ptr() for n, _ in state])
+                      for b in range(len(pbs))]
+            ptr_out = [(ctypes.c_void_p * len(ids))(*[host[b][n].data_ptr() for n in ids]) for b in range(len(pbs))]
             diag = np.zeros(12)
             total = 0.0
             for _ in range(args.steps):
@@ -342,13 +349,13 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 for b in range(len(pbs)):
-                    lib.ebit_set_interface(ctx, b, host[b]["vcol"].data_ptr(), host[b]["hx_pos"].data_ptr(),
-                                           host[b]["vy_pos"].data_ptr(), 0)
-                    E.ebit_set_fields(ctx, b, [f for _, f in state], [host[b][n].data_ptr() for n, _ in state], 0)
+                    E.check(ctx, lib.ebit_set_interface(ctx, b, host[b]["vcol"].data_ptr(),
+                                                        host[b]["hx_pos"].data_ptr(), host[b]["vy_pos"].data_ptr(), 0))
+                    E.check(ctx, lib.ebit_set_fields(ctx, b, len(state), ids_in, ptr_in[b], 0))
                 E.ebit_run_stage(ctx, E.STAGE_RECONSTRUCT)
                 E.ebit_step(ctx, 1, allow_noconv=True)
                 for b in range(len(pbs)):
-                    E.ebit_get_fields(ctx, b, list(ids.values()), [host[b][n].data_ptr() for n in ids], 0)
+                    E.check(ctx, lib.ebit_get_fields(ctx, b, len(ids), ids_out, ptr_out[b], 0))
                     diag = E.ebit_get_diagnostics(ctx, b)
                 total += time.perf_counter() - t0
             total = barrier_max(total)

@@ -125,6 +125,11 @@ def _check(ctx, status):
     return status
 
 
+def check(ctx, status):
+    """Raise EbitError for a non-OK status returned by a direct call into the library."""
+    _check(ctx, status)
+
+
 # ------------------------------------------------------------------ torch-backed device memory
 class TorchAllocator:
     """Device allocator callback backed by torch tensors (kept alive until freed)."""

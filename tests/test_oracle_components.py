@@ -1,7 +1,8 @@
 """Component pins of the oracle: each check is fixed by mathematics, not by the oracle itself.
 
   * reconstruction: straight-line volume fractions against quadrature; circle area
-    converging at second order; normals pointing into vapour; edge/colour parity;
+    converging at second order; normals pointing into vapour; edge/colour parity; saddle
+    cells of bilinear level sets joined as the asymptotic decider joins them;
   * EBIT sweep: a translated straight line and a translated circle stay exact (a circle
     through three co-circular points is that circle); two half-cell sweeps equal a
     one-cell shift; merging discs match the analytic union;
@@ -11,7 +12,11 @@
     linear profile that vanishes at the interface, dense brute-force solve;
   * one-sided normal slope exact for quadratics; mass flux of a linear profile;
   * ghost-velocity jump (u_l - u_v) . n = mdot [1/rho]; projected faces divergence-free;
-    a fluid at rest under gravity stays at rest.
+    a fluid at rest under gravity stays at rest;
+  * momentum predictor: a shear mode decays by the exact discrete backward-Euler factor
+    (symmetry planes and no-slip walls, both components); the two-layer Poiseuille profile
+    is approached as the grid is refined; the two-layer step is mirror-symmetric; WENO3
+    momentum advection is exact for quadratic velocity fields.
 """
 import math
 
@@ -78,19 +83,48 @@ def test_every_cell_has_zero_two_or_four_cut_edges_and_band_normal():
     assert np.allclose(nrm[g.band & (nrm > 0)], 1.0)
 
 
-def test_saddle_cell_picks_shorter_pairing():
-    # corners alternate 1,0,1,0; markers near corner 1 and 3 -> cutting those corners is shorter
-    vcol = np.array([[1, 0], [0, 1]], np.uint8)   # [j][i]: BL=1, BR=0, TL=0, TR=1
-    hp = np.array([[0.9], [0.1]])                  # bottom marker near BR, top marker near TL
-    vp = np.array([[0.1, 0.9]])                    # left near BL? left(i=0)=0.1, right(i=1)=0.9
-    g = geometry.reconstruct(vcol, hp, vp)
-    assert g.nseg[0, 0] == 2
-    # BR is vapour, isolated by a short cut between bottom(0.9) and right(0.1)? right is 0.9 here:
-    # pairing A isolates BR (bottom 0.9 -> right 0.9) and TL (top 0.1 -> left 0.1)
-    LA = math.hypot(0.1, 0.9) * 2
-    LB = math.hypot(0.9, 0.1) + math.hypot(0.1, 0.9)
-    assert (g.ccol[0, 0] == 1) == (LA <= LB)
-    assert 0.0 < g.vf[0, 0] < 1.0
+def _bilinear_saddle_cell(a, b, c, d):
+    """One cell [0,1]^2 with the bilinear level set of corner values a (0,0), b (1,0), c (0,1),
+    d (1,1): vertex colours and the exact zero crossings on the edges (phi is linear there)."""
+    vcol = np.array([[a > 0, b > 0], [c > 0, d > 0]], np.uint8)
+    hp = np.array([[a / (a - b)], [c / (c - d)]])
+    vp = np.array([[a / (a - c), b / (b - d)]])
+    return vcol, hp, vp
+
+
+def test_saddle_cells_follow_the_asymptotic_decider():
+    """A saddle cell (four cut edges) has two possible pairings of its markers.  For a bilinear
+    level set the pairing is fixed by the sign of phi at the saddle point of the bilinear
+    interpolant, phi_s = (a d - b c) / (a + d - b - c) (the asymptotic decider of Nielson and
+    Hamann, 1991): the corners of that sign are joined through the cell.  The centre colour of
+    the reconstruction must be the phase joined through the cell, i.e. the sign of phi_s:
+      * exactly for every symmetric saddle (a = d, b = c: the saddle point is the centre);
+      * for random saddles whose saddle value is not close to zero (the pairing rule is a
+        geometric criterion; it departs from the decider only for |phi_s| < 2 % of the corner
+        values in this sample).
+    Choosing the longer pairing, or giving the centre the colour of the isolated corners,
+    fails both."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for t in range(4000):
+        a, d = rng.uniform(0.02, 1.0, 2)
+        b, c = -rng.uniform(0.02, 1.0, 2)
+        if t % 2:
+            a, b, c, d = -a, -b, -c, -d
+        if t < 1000:            # symmetric family
+            d, c = a, b
+        fs = (a * d - b * c) / (a + d - b - c)
+        if t >= 1000 and abs(fs) < 0.05 * max(abs(a), abs(b), abs(c), abs(d)):
+            continue
+        vcol, hp, vp = _bilinear_saddle_cell(a, b, c, d)
+        if min(hp.min(), vp.min()) < 1e-6 or max(hp.max(), vp.max()) > 1 - 1e-6:
+            continue
+        g = geometry.reconstruct(vcol, hp, vp)
+        assert g.nseg[0, 0] == 2
+        assert g.ccol[0, 0] == (1 if fs > 0 else 0), (a, b, c, d)
+        assert 0.0 < g.vf[0, 0] < 1.0
+        checked += 1
+    assert checked > 2500
 
 
 # ------------------------------------------------------------------ sweep
@@ -340,3 +374,147 @@ def test_fluid_at_rest_under_gravity_stays_at_rest():
     dp = np.diff(st.p, axis=0).mean(axis=1) / pb.h
     assert abs(dp[5] - pb.rho_v * pb.gy) < 1e-8 * pb.rho_l
     assert abs(dp[25] - pb.rho_l * pb.gy) < 1e-8 * pb.rho_l
+
+
+# ------------------------------------------------------------------ momentum predictor
+def _flow_state(n, bc, phi=None, rho=(1.0, 1.0), mu=(0.01, 0.01), dt=1e-2, gx=0.0):
+    """Oracle state on [0,1]^2 at rest with no heat transfer: all liquid (phi None) or the two
+    phases of the level set phi (liquid where phi > 0); rho, mu = (liquid, vapour)."""
+    pb = w.stefan(n, n, X0=0.5, Lx=1.0, dt=dt, steps=0)
+    pb.bc = bc
+    pb.T_bc = (None, None, None, None)
+    pb.rho_l, pb.rho_v = rho
+    pb.mu_l, pb.mu_v = mu
+    pb.gx, pb.gy = gx, 0.0
+    pb.energy, pb.mdot_fixed = False, 0.0
+    if phi is None:
+        pb.vcol = np.ones((n + 1, n + 1), np.uint8)
+        pb.hx_pos = np.zeros((n + 1, n))
+        pb.vy_pos = np.zeros((n, n + 1))
+    else:
+        pb.vcol, _, pb.hx_pos, _, pb.vy_pos = w.interface_from_levelset(phi, n, n, 1.0 / n)
+    for k in ("u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v", "p", "T_l", "T_v"):
+        setattr(pb, k, np.zeros_like(getattr(pb, k)))
+    st = S.State(pb)
+    st.geom = geometry.reconstruct(st.vcol, st.hx_pos, st.vy_pos)
+    rfx, rfy = flow.face_rho(pb, st.geom.vf)
+    st.gc = flow.faces_to_cells(*flow.face_acceleration(pb, st.p, rfx, rfy))
+    return st
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+@pytest.mark.parametrize("kind", ["symmetry", "wall"])
+def test_predictor_viscous_decay_of_a_shear_mode(comp, kind):
+    """Backward Euler viscous step (discretization eq. 1) on a single-phase shear wave.
+
+    u_comp = cos(k s) (tangential component on symmetry planes: even reflection) or
+    sin(k s) (no-slip walls: odd reflection), s the coordinate across the walls, k = pi m.
+    On the cell-centred grid both are exact eigenvectors of the five-point Laplacian with
+    lambda_h = (2 - 2 cos(k h)) / h^2, so one predictor step must multiply the mode by
+    1 / (1 + nu dt lambda_h) to round-off (nu = mu / rho); u . grad u vanishes for this field.
+    A missing h^2 or rho/dt factor, a wrong face viscosity, or a wrong wall term (2 mu u_i)
+    breaks the identity.  lambda_h -> k^2 at second order, the continuous decay rate."""
+    n, m = 32, 3
+    k = math.pi * m
+    h = 1.0 / n
+    rho, mu, dt = 3.7, 0.23, 0.01
+    side = flow.SYMMETRY if kind == "symmetry" else flow.WALL
+    bc = (side, side, flow.OUTFLOW, flow.OUTFLOW) if comp == 1 else (flow.OUTFLOW, flow.OUTFLOW, side, side)
+    st = _flow_state(n, bc, rho=(rho, rho), mu=(mu, mu), dt=dt)
+    sc = (np.arange(n) + 0.5) * h
+    prof = np.cos(k * sc) if kind == "symmetry" else np.sin(k * sc)
+    field = np.tile(prof, (n, 1)) if comp == 1 else np.tile(prof[:, None], (1, n))
+    st.u_l[..., comp] = field
+    st.u_v[..., comp] = 0.5 * field
+    ustar, _ = flow.predictor(st, st.gc)
+    lam_h = (2.0 - 2.0 * math.cos(k * h)) / (h * h)
+    amp = 1.0 / (1.0 + (mu / rho) * dt * lam_h)
+    assert np.max(np.abs(ustar["l"][..., comp] - amp * field)) < 1e-13
+    assert np.max(np.abs(ustar["v"][..., comp] - 0.5 * amp * field)) < 1e-13
+    assert np.max(np.abs(ustar["l"][..., 1 - comp])) < 1e-15
+    assert abs(lam_h / (k * k) - 1.0) < (k * h) ** 2 / 12.0 * 1.01
+
+
+def _two_layer_poiseuille(y, y0, rho, mu, g):
+    """Steady (mu u')' = -rho g between no-slip walls at y = 0, 1; vapour (index 1) below y0,
+    liquid (index 0) above; u and mu u' continuous at y0.  Coefficients by a 4x4 solve."""
+    aL, aV = -rho[0] * g / (2 * mu[0]), -rho[1] * g / (2 * mu[1])
+    # unknowns bV, cV, bL, cL of u = a y^2 + b y + c
+    M = np.array([[0, 1, 0, 0],
+                  [0, 0, 1, 1],
+                  [y0, 1, -y0, -1],
+                  [mu[1], 0, -mu[0], 0]], float)
+    r = np.array([0.0, -aL, aL * y0 * y0 - aV * y0 * y0, 2 * y0 * (mu[0] * aL - mu[1] * aV)])
+    bV, cV, bL, cL = np.linalg.solve(M, r)
+    return np.where(y < y0, aV * y * y + bV * y + cV, aL * y * y + bL * y + cL)
+
+
+def test_predictor_two_layer_poiseuille_converges():
+    """Two viscosities and densities (property average of the volume fraction, face viscosity
+    from the two cells): with a very large dt the predictor's implicit solve is the steady
+    two-layer Poiseuille flow driven by a body force g_x between no-slip walls, whose exact
+    profile is piecewise quadratic with continuous u and mu u' at the interface.  The discrete
+    profile must converge to it; a factor error in the face viscosity or the mixture, or a
+    dropped h^2, leaves an O(1) error."""
+    y0, rho, mu, g = 0.4037, (3.0, 1.0), (2.0, 0.5), 1.0
+    dt = 1e6
+    errs = []
+    for n in (16, 32, 64):
+        st = _flow_state(n, (flow.OUTFLOW, flow.OUTFLOW, flow.WALL, flow.WALL), phi=lambda x, y: y - y0,
+                         rho=rho, mu=mu, dt=dt, gx=g)
+        ustar, _ = flow.predictor(st, st.gc)
+        yc = (np.arange(n) + 0.5) / n
+        exact = _two_layer_poiseuille(yc, y0, rho, mu, g)
+        for name in ("l", "v"):
+            u = ustar[name][..., 0] + dt * st.gc[..., 0]       # the implicit solve's solution
+            assert np.max(np.abs(u - u[:, :1])) < 1e-9        # uniform along x
+        u = ustar["l"][:, 0, 0] + dt * g
+        errs.append(np.max(np.abs(u - exact)) / np.max(np.abs(exact)))
+    assert errs[0] < 0.05
+    assert errs[1] < errs[0] / 1.7 and errs[2] < errs[1] / 1.7, errs
+
+
+def test_predictor_viscous_step_is_mirror_symmetric():
+    """The face viscosity is a symmetric function of the two cells it joins: the two-layer
+    viscous step mirrored top to bottom (vapour above instead of below) is the mirror image of
+    the original to round-off.  A face weight taken from one side only (an index shift) breaks
+    the symmetry at the interface even though it still converges."""
+    n, y0, rho, mu, dt = 32, 0.4037, (3.0, 1.0), (2.0, 0.5), 0.05
+    bc = (flow.OUTFLOW, flow.OUTFLOW, flow.WALL, flow.WALL)
+    yc = (np.arange(n) + 0.5) / n
+    prof = np.sin(math.pi * yc) + 0.3 * np.sin(3 * math.pi * yc)
+    out = []
+    for phi, u in ((lambda x, y: y - y0, prof), (lambda x, y: (1.0 - y0) - y, prof[::-1])):
+        st = _flow_state(n, bc, phi=phi, rho=rho, mu=mu, dt=dt)
+        st.u_l[..., 0] = u[:, None]
+        st.u_v[..., 0] = u[:, None]
+        out.append(flow.predictor(st, st.gc)[0]["l"][:, 0, 0])
+    assert np.max(np.abs(out[0] - out[1][::-1])) < 1e-12
+
+
+def test_predictor_advection_exact_for_quadratic_velocity():
+    """Inviscid predictor (mu = 0, g = 0, p = 0): u** = u - dt (u . grad) u, and WENO3 is exact
+    for quadratic data (its two smoothness indicators are equal, so the weights are the linear
+    1/3, 2/3 of the third-order scheme).  For a quadratic velocity field the result must equal
+    the exact u - dt (u u_x + v u_y) at every cell two or more cells from the boundary.  A
+    dropped or sign-flipped advection term, or an axis swapped, fails."""
+    n = 16
+    dt = 0.01
+    st = _flow_state(n, (flow.OUTFLOW,) * 4, mu=(0.0, 0.0), dt=dt)
+    xc = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(xc, xc)
+    ux = 0.3 + 0.8 * X - 0.5 * Y + 0.6 * X * X - 0.4 * X * Y + 0.2 * Y * Y
+    uy = -0.2 + 0.1 * X + 0.7 * Y - 0.3 * X * X + 0.5 * X * Y - 0.6 * Y * Y
+    dux = (0.8 + 1.2 * X - 0.4 * Y, -0.5 - 0.4 * X + 0.4 * Y)     # (d/dx, d/dy) of ux
+    duy = (0.1 - 0.6 * X + 0.5 * Y, 0.7 + 0.5 * X - 1.2 * Y)
+    st.u_l[..., 0], st.u_l[..., 1] = ux, uy
+    st.u_v[..., 0], st.u_v[..., 1] = -ux, -uy
+    ustar, _ = flow.predictor(st, st.gc)
+    inner = (slice(2, -2), slice(2, -2))
+    ex = ux - dt * (ux * dux[0] + uy * dux[1])
+    ey = uy - dt * (ux * duy[0] + uy * duy[1])
+    assert np.max(np.abs(ustar["l"][..., 0][inner] - ex[inner])) < 1e-13
+    assert np.max(np.abs(ustar["l"][..., 1][inner] - ey[inner])) < 1e-13
+    # the vapour field -u advects itself with -u: -(u - dt (u . grad) u) in its own frame
+    exv = -ux - dt * (ux * dux[0] + uy * dux[1])
+    assert np.max(np.abs(ustar["v"][..., 0][inner] - exv[inner])) < 1e-13

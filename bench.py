@@ -121,14 +121,15 @@ def oracle_rate(name, budget_s=20.0, max_steps=3):
     cell-steps done, seconds, description of the sample)."""
     from oracle import step as S
     pbs = make_problems(name, count=64) if WORKLOADS[name]["kind"] == "c4" else make_problems(name)
-    done, secs, steps, inst = 0, 0.0, 0, 0
+    done, secs, cpu, steps, inst = 0, 0.0, 0.0, 0, 0
     for pb in pbs:
         st = S.prepare(pb)
         inst += 1
         for _ in range(max_steps):
-            t0 = time.perf_counter()
+            t0, c0 = time.perf_counter(), time.process_time()
             S.step(st)
             secs += time.perf_counter() - t0
+            cpu += time.process_time() - c0
             done += pb.nx * pb.ny
             steps += 1
             if secs > budget_s:
@@ -137,7 +138,7 @@ def oracle_rate(name, budget_s=20.0, max_steps=3):
             break
     what = (f"{steps} whole oracle steps of {name}" if inst == 1 else
             f"{steps} whole oracle steps over its first {inst} instances")
-    return done / secs, done, secs, what
+    return done / secs, done, secs, what, cores_used(cpu, secs)
 
 
 def reference_arm(args):
@@ -146,7 +147,7 @@ def reference_arm(args):
         return 0
     # each timed step is one whole oracle step of the workload; the run stops early (and says
     # so in the sample) once the CPU budget is spent, so it ends within a few minutes
-    total_steps, total_s, done = 0, 0.0, 0
+    total_steps, total_s, total_cpu, done = 0, 0.0, 0.0, 0
     from oracle import step as S
     pbs = make_problems(args.workload)
     cells = sum(pb.nx * pb.ny for pb in pbs)
@@ -156,34 +157,37 @@ def reference_arm(args):
         b = k % len(pbs)
         if b >= len(sts):
             sts.append(S.prepare(pbs[b]))
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         S.step(sts[b])
         total_s += time.perf_counter() - t0
+        total_cpu += time.process_time() - c0
         done += pbs[b].nx * pbs[b].ny
         total_steps += 1
         if total_s > args.reference_budget:
             break
     value = done / total_s
-    cores = _cores_used()
+    cores = cores_used(total_cpu, total_s)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / total_steps,
+            "steps": total_steps, "steps_requested": args.steps, "warmup": 0,
+            "ms_per_step": 1e3 * total_s / total_steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "cells": cells, "instances": len(pbs),
                        "instances_sampled": len(sts), "solver": "sparse direct (SuperLU)"},
             "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{total_steps} of {args.steps} whole oracle steps of {args.workload} "
-                                       f"from its initial state ({total_s:.1f} s)"},
+                             "implementation": "Python/numpy + scipy SuperLU, single process",
+                             "cpu_s_per_wall_s": total_cpu / total_s,
+                             "sample": f"{total_steps} of {args.steps} requested whole oracle steps of "
+                                       f"{args.workload} from its initial state ({total_s:.1f} s; the run stops "
+                                       f"once {args.reference_budget:.0f} s of oracle time is spent)"},
             "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _cores_used():
-    # the oracle is numpy + SuperLU: BLAS threads may be used; report the threads available
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
-        if os.environ.get(var):
-            return int(os.environ[var])
-    return os.cpu_count()
+def cores_used(cpu_s, wall_s):
+    """Cores the oracle kept busy: its process CPU time over the wall time of the same steps
+    (numpy and SuperLU run single-threaded here; a threaded BLAS would show as more than 1)."""
+    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
 
 
 # ------------------------------------------------------------------ replicas (N > 1)
@@ -200,6 +204,51 @@ def replica_max(x, dist, device):
 def job_rate(world, cells, steps, secs):
     """Whole-job cell-steps/s: every replica advances its own instance by `steps` steps."""
     return world * cells * steps / secs
+
+
+# ------------------------------------------------------------------ result summaries
+# Bytes per cell that one pass of the step must move (the method's algorithmic minimum, one
+# word per value): a preconditioned CG iteration (stencil apply with its dot product, the
+# vector updates and a V(2,2) multigrid cycle) moves about 250 B per cell in FP64 and 125 B in
+# FP32; the explicit part of the step (advection, operators, projection, diagnostics) about
+# 250 B.  Iteration counts are the solver's own (energy, both viscous components, Poisson; the
+# mixed path counts its FP32 iterations over all refinement passes).
+B_ITER = {"fp64": 250.0, "mixed": 125.0}
+B_EXPLICIT = 250.0
+
+
+def step_roofline(r, cells, steps, prec, peak):
+    d = r["diag"]
+    iters = d[6] + d[7] + d[8]
+    b_cell = iters * B_ITER[prec] + B_EXPLICIT
+    achieved = b_cell * cells / (r["secs"] / steps) / 1e9
+    return {"bytes_per_cell_step": b_cell, "iterations": [d[6], d[7], d[8]], "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "formula": f"(energy + viscous + Poisson iterations) x {B_ITER[prec]:.0f} B + {B_EXPLICIT:.0f} B "
+                       f"per cell, iterations of the last timed step"}
+
+
+def mixed_error(pbs, mixed, fp64, nsteps):
+    """The mixed path's error against the FP64 path after the same steps from the same initial
+    state: max difference over a field group relative to the group's scale (temperatures: max |T|
+    over both phases; velocities: max |u| over both phase fields; pressure: max(|p|, rho_l
+    u_max^2), p being defined by its outflow reference)."""
+    errs = []
+    for b, (fm, fd) in enumerate(zip(mixed["final"], fp64["final"])):
+        t_scale = max(float(np.max(np.abs(fd["T_l"]))), float(np.max(np.abs(fd["T_v"]))), 1e-300)
+        u_scale = max(float(np.max(np.abs(fd["u_l"]))), float(np.max(np.abs(fd["u_v"]))), 1e-300)
+        p_scale = max(float(np.max(np.abs(fd["p"]))), pbs[b].rho_l * u_scale ** 2, 1e-300)
+        scale = {"T_l": t_scale, "T_v": t_scale, "u_l": u_scale, "u_v": u_scale, "p": p_scale}
+        e = {k: float(np.max(np.abs(fm[k] - fd[k]))) / scale[k] for k in ("T_l", "T_v", "p", "u_l", "u_v")}
+        e["vcol"] = int(np.sum(fm["vcol"] != fd["vcol"]))
+        e["markers"] = float(max(np.max(np.abs(fm["hx_pos"] - fd["hx_pos"])),
+                                 np.max(np.abs(fm["vy_pos"] - fd["vy_pos"]))))
+        errs.append(e)
+    return {"steps": nsteps, "instances_compared": len(errs),
+            **{k: max(e[k] for e in errs) for k in ("T_l", "T_v", "p", "u_l", "u_v")},
+            "vertex_colours_differing": sum(e["vcol"] for e in errs),
+            "marker_max_abs_diff": max(e["markers"] for e in errs),
+            "scales": "T: max|T| both phases; u: max|u| both fields; p: max(|p|, rho_l u_max^2)"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -229,7 +278,7 @@ def run_ours(args):
     alloc = E.TorchAllocator()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
-    def new_ctx(precision):
+    def new_ctx(pbs, precision):
         ctx = E.ebit_init([E.config_from_problem(pb, precision, args.rtol, args.max_iter) for pb in pbs],
                           stream.cuda_stream, alloc)
         if args.no_graph:
@@ -266,43 +315,49 @@ def run_ours(args):
     def barrier_max(x):
         return replica_max(x, dist, "cuda")
 
-    results = {}
+    def measure(pbs, steps, warmup, prec_list, clocks=None, keep_final=True):
+        """Warm-up and timed steps of each precision from the workload's initial state."""
+        results = {}
+        for name, prec in prec_list:
+            ctx = new_ctx(pbs, prec)
+            try:
+                for _ in range(warmup):
+                    E.ebit_step(ctx, 1, allow_noconv=True)
+                torch.cuda.synchronize()
+                if dist:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                if clocks is not None and name == "mixed":
+                    clocks.start()
+                secs, launches, kt = timed_steps(ctx, steps, with_timing=(name == "mixed"))
+                clk = clocks.stop() if clocks is not None and name == "mixed" else None
+                torch.cuda.synchronize()
+                if dist:
+                    dist.barrier()
+                secs = barrier_max(secs)
+                d = E.ebit_get_diagnostics(ctx, 0)
+                results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist(), clocks=clk)
+                sched = {}
+                for b in range(len(pbs)):
+                    sm, it, tm, co = E.ebit_get_schedule(ctx, b)
+                    key = f"small_max={sm} inner_rtol={it:g} tma={tm} coop={co}"
+                    sched[key] = sched.get(key, 0) + 1
+                results[name]["schedule"] = sched
+                if keep_final and rank == 0:
+                    results[name]["final"] = [
+                        E.download(ctx, b, pbs[b].nx, pbs[b].ny,
+                                   ["T_l", "T_v", "p", "u_l", "u_v", "vcol", "hx_pos", "vy_pos"])
+                        for b in range(min(len(pbs), 16))]
+            finally:
+                E.ebit_destroy(ctx)
+        return results
+
     prec_list = [("mixed", E.EBIT_MIXED), ("fp64", E.EBIT_FP64)]
     if args.profile_only:
         prec_list = prec_list[:1]
     clocks = ClockSampler(local)
-    for name, prec in prec_list:
-        ctx = new_ctx(prec)
-        try:
-            for _ in range(args.warmup):
-                E.ebit_step(ctx, 1, allow_noconv=True)
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            torch.cuda.synchronize()
-            if name == "mixed":
-                clocks.start()
-            secs, launches, kt = timed_steps(ctx, args.steps, with_timing=(name == "mixed"))
-            if name == "mixed":
-                clk = clocks.stop()
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            secs = barrier_max(secs)
-            d = E.ebit_get_diagnostics(ctx, 0)
-            results[name] = dict(secs=secs, launches=launches, kt=kt, diag=d.tolist())
-            sched = {}
-            for b in range(len(pbs)):
-                sm, it, tm, co = E.ebit_get_schedule(ctx, b)
-                key = f"small_max={sm} inner_rtol={it:g} tma={tm} coop={co}"
-                sched[key] = sched.get(key, 0) + 1
-            results[name]["schedule"] = sched
-            if not args.profile_only and rank == 0:
-                results[name]["final"] = [E.download(ctx, b, pbs[b].nx, pbs[b].ny,
-                                                     ["T_l", "T_v", "p", "u_l", "u_v", "vcol", "hx_pos", "vy_pos"])
-                                          for b in range(min(len(pbs), 16))]
-        finally:
-            E.ebit_destroy(ctx)
+    results = measure(pbs, args.steps, args.warmup, prec_list, clocks, keep_final=not args.profile_only)
+    clk = results["mixed"]["clocks"]
     if args.profile_only:
         if rank == 0:
             r = results["mixed"]
@@ -379,32 +434,40 @@ def run_ours(args):
     peak_source = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
     kt_ms, kt_n, kt_bytes = mixed["kt"]
     achieved = (kt_bytes * kt_n) / (kt_ms / 1e3) / 1e9 if kt_ms > 0 else None
-    # the mixed path's error against the FP64 path after the same warm-up + timed steps from the
-    # same initial state: max difference over a field group relative to the group's scale
-    # (temperatures: max |T| over both phases; velocities: max |u| over both phase fields;
-    # pressure: max(|p|, rho_l u_max^2), p being defined by its outflow reference)
-    errs = []
-    for b, (fm, fd) in enumerate(zip(mixed["final"], fp64["final"])):
-        t_scale = max(float(np.max(np.abs(fd["T_l"]))), float(np.max(np.abs(fd["T_v"]))), 1e-300)
-        u_scale = max(float(np.max(np.abs(fd["u_l"]))), float(np.max(np.abs(fd["u_v"]))), 1e-300)
-        p_scale = max(float(np.max(np.abs(fd["p"]))), pbs[b].rho_l * u_scale ** 2, 1e-300)
-        scale = {"T_l": t_scale, "T_v": t_scale, "u_l": u_scale, "u_v": u_scale, "p": p_scale}
-        e = {k: float(np.max(np.abs(fm[k] - fd[k]))) / scale[k] for k in ("T_l", "T_v", "p", "u_l", "u_v")}
-        e["vcol"] = int(np.sum(fm["vcol"] != fd["vcol"]))
-        e["markers"] = float(max(np.max(np.abs(fm["hx_pos"] - fd["hx_pos"])),
-                                 np.max(np.abs(fm["vy_pos"] - fd["vy_pos"]))))
-        errs.append(e)
-    mixed_err = {"steps": args.warmup + args.steps, "instances_compared": len(errs),
-                 **{k: max(e[k] for e in errs) for k in ("T_l", "T_v", "p", "u_l", "u_v")},
-                 "vertex_colours_differing": sum(e["vcol"] for e in errs),
-                 "marker_max_abs_diff": max(e["markers"] for e in errs),
-                 "scales": "T: max|T| both phases; u: max|u| both fields; p: max(|p|, rho_l u_max^2)"}
+    mixed_err = mixed_error(pbs, mixed, fp64, args.warmup + args.steps)
+    step_roof = {"mixed": step_roofline(mixed, cells, args.steps, "mixed", peak),
+                 "fp64": step_roofline(fp64, cells, args.steps, "fp64", peak)}
+    extras = {}
+    for wname in [x for x in args.extra.split(",") if x and x != args.workload and world == 1]:
+        xp = make_problems(wname)
+        xc = sum(pb.nx * pb.ny for pb in xp)
+        xs = max(1, args.extra_steps)
+        xr = measure(xp, xs, args.extra_warmup, [("mixed", E.EBIT_MIXED), ("fp64", E.EBIT_FP64)])
+        xm, xd = xr["mixed"], xr["fp64"]
+        km, kn, kb = xm["kt"]
+        xa = (kb * kn) / (km / 1e3) / 1e9 if km > 0 else None
+        extras[wname] = {
+            "desc": WORKLOADS[wname]["desc"], "cells": xc, "steps": xs, "warmup": args.extra_warmup,
+            "value": job_rate(1, xc, xs, xm["secs"]), "unit": "cell-steps/s",
+            "ms_per_step": 1e3 * xm["secs"] / xs, "timesteps_per_s": xs / xm["secs"],
+            "fp64": {"value": job_rate(1, xc, xs, xd["secs"]), "ms_per_step": 1e3 * xd["secs"] / xs,
+                     "speedup_mixed_over_fp64": xd["secs"] / xm["secs"]},
+            "roofline": {"bound": "hbm", "kernel": "k_pre/k_post<float> on the finest grid", "achieved": xa,
+                         "peak": peak, "unit": "GB/s", "frac": (xa / peak) if xa else None,
+                         "launches_timed": kn, "avg_launch_us": 1e3 * km / kn if kn else None},
+            "step_roofline": {"mixed": step_roofline(xm, xc, xs, "mixed", peak),
+                              "fp64": step_roofline(xd, xc, xs, "fp64", peak)},
+            "mixed_error_vs_fp64": mixed_error(xp, xm, xd, args.extra_warmup + xs),
+            "schedule_mixed": xm["schedule"], "gpu_launches": int(xm["launches"]),
+        }
+        del xp
     tr = SMOOTH_L0_TRAFFIC.get(args.workload)
     traffic = tr["dram_bytes_per_launch"] if tr else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        r, n, secs, what = oracle_rate(args.workload, budget_s=args.cpu_budget)
-        cpu = {"value": r, "unit": "cell-steps/s", "cores": _cores_used(), "kind": "oracle",
+        r, n, secs, what, cores = oracle_rate(args.workload, budget_s=args.cpu_budget)
+        cpu = {"value": r, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+               "implementation": "Python/numpy + scipy SuperLU, single process",
                "sample": f"{what} from the initial state ({n} cell-steps, {secs:.1f} s)"}
     line = {
         "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
@@ -418,6 +481,7 @@ def run_ours(args):
                  "speedup_mixed_over_fp64": value / value64},
         "mixed_error_vs_fp64": mixed_err,
         "timesteps_per_s": args.steps / mixed["secs"],
+        "step_roofline": step_roof,
         "roofline": {"bound": "hbm",
                      "kernel": "k_pre/k_post<float> on the finest grid (tiled red-black GS V-cycle legs)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -428,6 +492,7 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": int(mixed["launches"]),
+        "workloads": extras,
         "solver": {"mixed_diag": mixed["diag"], "fp64_diag": fp64["diag"],
                    "schedule_mixed": mixed["schedule"], "schedule_fp64": fp64["schedule"],
                    "autotuned": not args.no_autotune and not args.no_graph},
@@ -456,6 +521,10 @@ def main():
     ap.add_argument("--profile-only", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels from the host (profilers)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
+    ap.add_argument("--extra", default="c3_film_1024x2048,c5_film_4096",
+                    help="further workloads measured in the same run (sub-objects of the line; '' for none)")
+    ap.add_argument("--extra-steps", type=int, default=5)
+    ap.add_argument("--extra-warmup", type=int, default=3)
     args = ap.parse_args()
     global BATCH_COUNT
     BATCH_COUNT = args.batch_count

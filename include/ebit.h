@@ -38,8 +38,10 @@
  *   - Errors: every call returns an ebit_status; on failure a message is kept for
  *     ebit_last_error().  EBIT_ENOCONV means a linear solve hit max_iter: the step is
  *     completed with its last iterate; iteration counts and final residuals are reported by
- *     ebit_get_diagnostics().  EBIT_ECUDA means a CUDA call failed; the context should
- *     then be destroyed.
+ *     ebit_get_diagnostics().  EBIT_ECUDA means a CUDA call failed, or a bounded device
+ *     wait gave up; the context should then be destroyed.  EBIT_ENONFINITE means a NaN or
+ *     an infinity reached a linear solve (each solve tests its residual norms and stops at
+ *     the first non-finite one): the step is completed but its results are not usable.
  *   - Threads: a context may be used by one host thread at a time.
  */
 #ifndef EBIT_H
@@ -61,7 +63,9 @@ typedef enum {
     EBIT_ENOCONV = -3,    /* a linear solve did not reach its tolerance in max_iter     */
     EBIT_ETOPO = -4,      /* marker set inconsistent with the vertex colours            */
     EBIT_ECUDA = -5,      /* CUDA runtime error                                        */
-    EBIT_ECFL = -6        /* a marker moved one cell or more in one sweep (CFL >= 1)   */
+    EBIT_ECFL = -6,       /* a marker moved one cell or more in one sweep (CFL >= 1)   */
+    EBIT_ENONFINITE = -7  /* a linear solve met a NaN or an infinity (in the state, a field
+                             the caller set, or the system passed to a solve entry point) */
 } ebit_status;
 
 /* Boundary kinds (per side: 0 left, 1 right, 2 bottom, 3 top). */
@@ -273,9 +277,15 @@ ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* i
  *   fit one per co-resident block) and the single-block levels in one cooperative launch with
  *   grid barriers between the phases; 0 launches each level separately.  Both give the same
  *   values.  Instances stepped in batches always launch each level separately.
- * A tile kernel that waits for its copies in vain gives up after a bounded wait; ebit_step
- * then returns EBIT_ECUDA. */
-enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2, EBIT_OPT_COOP = 3 };
+ *   EBIT_OPT_BARRIER_SPIN (default 0 = 2^22 polls) bounds the wait of each grid barrier of the
+ *   cooperative launch, in polls of the arrival counter.  A fault-path test setting: a bound of
+ *   a few polls makes the barriers give up before the other blocks arrive.  Changing it drops
+ *   the captured step graphs.
+ * A tile kernel that waits for its copies in vain, or a grid barrier that waits in vain, gives
+ * up after a bounded wait and records a fault; ebit_step, ebit_solve_system and
+ * ebit_solve_system_noalloc then return EBIT_ECUDA: every result of that launch (not only of
+ * the instance) is invalid, and the context should be destroyed. */
+enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2, EBIT_OPT_COOP = 3, EBIT_OPT_BARRIER_SPIN = 4 };
 ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value);
 
 const char* ebit_last_error(const ebit_ctx* ctx);

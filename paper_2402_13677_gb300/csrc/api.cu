@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "solver.h"
+#include "status.h"
 
 using namespace ebit;
 
@@ -57,6 +58,7 @@ struct Instance {
     double stats[6] = {0, 0, 0, 0, 0, 0};   // iterations and residuals: energy, viscous, poisson
     bool noconv = false;
     bool fault = false;   // a multigrid kernel gave up a bounded wait (TMA copies, grid barrier)
+    bool nonfinite = false;   // a solve met a NaN or an infinity
     // CUDA graphs of one step, per sweep-order parity
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};   // kernel launches captured per graph (loop bodies once)
@@ -329,6 +331,7 @@ static void collect_stats(Instance& I, bool graph_step) {
         r[k] = (k == SLOT_VISC_Y ? I.solver2 : I.solver).result_from_host(k, I.cfg.precision);
         ok = ok && r[k].converged;
         if (r[k].fault) I.fault = true;
+        if (r[k].nonfinite) I.nonfinite = true;
         // kernels executed inside the conditional loop bodies of a graph step
         n += r[k].iters * body;
         if (I.cfg.precision == EBIT_MIXED) n += 2 * r[k].outer - 1;
@@ -362,8 +365,7 @@ static void solve_energy(Instance& I, cudaStream_t st) {
 
 static void momentum(Instance& I, cudaStream_t st) {
     // S11: predictor; one two-RHS solve (liquid, vapour) per velocity component
-    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, I.cfg.precision == EBIT_MIXED,
-                   st);
+    launch_mom_rhs(I.g, I.p, I.vf, I.u_l, I.u_v, I.gc, I.vbx, I.vby, I.vxx, I.vxy, st);
     count(1);
     // the two components are independent: while capturing a graph the y solve becomes a
     // parallel branch (forked and joined through events on the side stream)
@@ -423,8 +425,7 @@ static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
         case EBIT_STAGE_RECONSTRUCT: reconstruct_full(I, st); break;
         case EBIT_STAGE_ADVECT_T:
             if (I.p.energy) {
-                launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, I.cfg.precision == EBIT_MIXED,
-                                st);
+                launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, st);
                 count(1);
             }
             break;
@@ -470,6 +471,11 @@ static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
             I.fault = false;
             return fail(ctx, EBIT_ECUDA,
                         "a multigrid kernel gave up a bounded wait (TMA copies or grid barrier)" + where);
+        }
+        if (I.nonfinite) {
+            I.nonfinite = false;
+            I.noconv = false;
+            return fail(ctx, EBIT_ENONFINITE, "a linear solve met a NaN or an infinity in the state" + where);
         }
         if (I.noconv) {
             I.noconv = false;
@@ -780,7 +786,7 @@ static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaStream_t st, cud
     I.solver.use_graph = 1;
     cudaStream_t s = st;
     if (I.p.energy) {
-        launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, I.cfg.precision == EBIT_MIXED, s);
+        launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, s);
         extend_T(I, I.Ts_l, I.Ts_v, s);
     }
     advance_interface(I, s);
@@ -1075,15 +1081,22 @@ ebit_status ebit_solve_system(ebit_ctx* ctx, int inst, const double* D, const do
     I.solver.solve(I.op_cd, I.op_dd, I.op_wl, I.op_wb, (const double*)I.vbx, (double*)I.vxx, nr, precision, rtol,
                    max_iter, st);
     count((int)(I.solver.launches - l0));
-    SolveResult r = I.solver.read_result(4, precision, st);
+    cudaError_t e = cudaSuccess;
+    SolveResult r = I.solver.read_result(4, precision, st, &e);
+    if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(e));
     cudaMemcpyAsync(x, I.vxx, N * 8 * nr, cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
+    e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(e));
     if (iters) *iters = r.iters;
     if (rel_res) *rel_res = r.rel_res;
     ebit_status s = cuda_check(ctx, "ebit_solve_system");
     if (s != EBIT_OK) return s;
-    return r.converged ? EBIT_OK : fail(ctx, EBIT_ENOCONV, "ebit_solve_system: max_iter reached");
+    s = solve_status(true, r.fault, r.nonfinite, r.converged);
+    if (s == EBIT_ECUDA)
+        return fail(ctx, s, "ebit_solve_system: a multigrid kernel gave up a bounded wait (result invalid)");
+    if (s == EBIT_ENONFINITE) return fail(ctx, s, "ebit_solve_system: a NaN or an infinity in the system");
+    if (s == EBIT_ENOCONV) return fail(ctx, s, "ebit_solve_system: max_iter reached");
+    return EBIT_OK;
 }
 
 ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
@@ -1092,12 +1105,14 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
         ctx->use_graph = value ? 1 : 0;
         return EBIT_OK;
     }
-    if (option == EBIT_OPT_TMA || option == EBIT_OPT_COOP) {
+    if (option == EBIT_OPT_TMA || option == EBIT_OPT_COOP || option == EBIT_OPT_BARRIER_SPIN) {
+        if (option == EBIT_OPT_BARRIER_SPIN && value < 0) return fail(ctx, EBIT_EINVAL, "negative spin bound");
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         for (auto& I : ctx->inst) {
             for (Solver* sv : {&I.solver, &I.solver2}) {
                 if (option == EBIT_OPT_TMA) sv->use_tma = value ? 1 : 0;
-                else sv->use_coop = value ? 1 : 0;
+                else if (option == EBIT_OPT_COOP) sv->use_coop = value ? 1 : 0;
+                else sv->barrier_spin = value;
             }
             for (auto& gx : I.graph)
                 if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }

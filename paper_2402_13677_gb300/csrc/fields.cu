@@ -79,20 +79,10 @@ __device__ inline R weno3(R Tm2, R Tm1, R T0, R Tp1, R Tp2, bool upos) {
     return (q0 * phi0 + q1 * phi1) / (q0 + q1);
 }
 
-template <class F>
-__device__ inline double advect_one(const F& T, const Grid& g, const Refl& r, int i, int j, double2 u,
-                                    double dth) {
-    double dx = weno3<double>(refl_x(T, g, r, i - 2, j), refl_x(T, g, r, i - 1, j), refl_x(T, g, r, i, j),
-                              refl_x(T, g, r, i + 1, j), refl_x(T, g, r, i + 2, j), u.x >= 0.0);
-    double dy = weno3<double>(refl_y(T, g, r, i, j - 2), refl_y(T, g, r, i, j - 1), refl_y(T, g, r, i, j),
-                              refl_y(T, g, r, i, j + 1), refl_y(T, g, r, i, j + 2), u.y >= 0.0);
-    return refl_x(T, g, r, i, j) - dth * (u.x * dx + u.y * dy);
-}
-
-// ---- mixed-precision variant: the WENO3 stencils of a 32 x 8 tile run in FP32 on values
-// staged once in shared memory (two halo layers, boundary reflections applied), each minus a
-// per-tile FP64 reference so that differences keep the precision of the local variation; the
-// update T - dt/h (u . D) and everything after it stay FP64.
+// ---- tiled form: the values a 32 x 8 tile of cells reads (two halo layers, boundary
+// reflections applied) are staged once in shared memory, in FP64, and each thread evaluates
+// the WENO3 stencils of its cell from there (the same values and operations as the per-cell
+// form above, without the five-fold re-reading of the field through the cache)
 constexpr int WX = 32, WY = 8, WH = 2, WSX = WX + 2 * WH, WSY = WY + 2 * WH;
 
 struct Scal {
@@ -115,23 +105,24 @@ __device__ inline double tile_value(const F& T, const Grid& g, const Refl& r, in
     return 0.0;   // a tile corner: no stencil reads it
 }
 
-// stage NF fields of the tile (field f: accessor F[f], reflection rule R[f]) as floats
+// stage NF fields of the tile (field f: accessor T[f], reflection rule R[f])
 template <int NF, class F>
-__device__ inline void tile_stage(const F* T, const Refl* R, const Grid& g, int i0, int j0, const double* ref,
-                                  float (*sh)[WSY][WSX]) {
+__device__ inline void tile_stage(const F* T, const Refl* R, const Grid& g, int i0, int j0,
+                                  double (*sh)[WSY][WSX]) {
     for (int k = threadIdx.x; k < WSX * WSY; k += blockDim.x) {
         int rx = k % WSX, ry = k / WSX;
         int i = i0 - WH + rx, j = j0 - WH + ry;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) sh[f][ry][rx] = (float)(tile_value(T[f], g, R[f], i, j) - ref[f]);
+        for (int f = 0; f < NF; ++f) sh[f][ry][rx] = tile_value(T[f], g, R[f], i, j);
     }
     __syncthreads();
 }
 
-__device__ inline float2 tile_derivs(const float (*v)[WSX], int rx, int ry, float2 u) {
-    float dx = weno3<float>(v[ry][rx - 2], v[ry][rx - 1], v[ry][rx], v[ry][rx + 1], v[ry][rx + 2], u.x >= 0.0f);
-    float dy = weno3<float>(v[ry - 2][rx], v[ry - 1][rx], v[ry][rx], v[ry + 1][rx], v[ry + 2][rx], u.y >= 0.0f);
-    return make_float2(dx, dy);
+// T - dt/h (u . D T) at tile position (rx, ry) of the staged field v
+__device__ inline double tile_advect(const double (*v)[WSX], int rx, int ry, double2 u, double dth) {
+    double dx = weno3<double>(v[ry][rx - 2], v[ry][rx - 1], v[ry][rx], v[ry][rx + 1], v[ry][rx + 2], u.x >= 0.0);
+    double dy = weno3<double>(v[ry - 2][rx], v[ry - 1][rx], v[ry][rx], v[ry + 1][rx], v[ry + 2][rx], u.y >= 0.0);
+    return v[ry][rx] - dth * (u.x * dx + u.y * dy);
 }
 
 
@@ -146,10 +137,12 @@ __host__ inline Refl velocity_refl(const Grid& g, int comp) {
     return r;
 }
 
-// S1: T*_k = T_k - dt u_k . grad T_k for both phases
-__global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l, const double* __restrict__ T_v,
-                           const double2* __restrict__ u_l, const double2* __restrict__ u_v,
-                           double* __restrict__ Ts_l, double* __restrict__ Ts_v) {
+// S1: T*_k = T_k - dt u_k . grad T_k for both phases (block WX x WY threads, one cell each)
+__global__ void __launch_bounds__(WX * WY) k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l,
+                                                     const double* __restrict__ T_v,
+                                                     const double2* __restrict__ u_l,
+                                                     const double2* __restrict__ u_v, double* __restrict__ Ts_l,
+                                                     double* __restrict__ Ts_v) {
     if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
     const long long zo = zoff(g.zs);
     T_l = zsh(T_l, zo);
@@ -158,44 +151,17 @@ __global__ void k_advect_T(Grid g, Refl r, double dth, const double* __restrict_
     u_v = zsh(u_v, zo);
     Ts_l = zsh(Ts_l, zo);
     Ts_v = zsh(Ts_v, zo);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (i >= g.nx) return;
-    int c = cidx(g, i, j);
-    Ts_l[c] = advect_one(T_l, g, r, i, j, u_l[c], dth);
-    Ts_v[c] = advect_one(T_v, g, r, i, j, u_v[c], dth);
-}
-
-// S1, mixed-precision tile variant (block WX x WY threads, one cell each)
-__global__ void __launch_bounds__(WX * WY) k_advect_T_f32(Grid g, Refl r, double dth, const double* __restrict__ T_l,
-                                                         const double* __restrict__ T_v,
-                                                         const double2* __restrict__ u_l,
-                                                         const double2* __restrict__ u_v, double* __restrict__ Ts_l,
-                                                         double* __restrict__ Ts_v) {
-    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
-    const long long zo = zoff(g.zs);
-    T_l = zsh(T_l, zo);
-    T_v = zsh(T_v, zo);
-    u_l = zsh(u_l, zo);
-    u_v = zsh(u_v, zo);
-    Ts_l = zsh(Ts_l, zo);
-    Ts_v = zsh(Ts_v, zo);
-    __shared__ float sh[2][WSY][WSX];
+    __shared__ double sh[2][WSY][WSX];
     int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
-    int ic = min(i0 + WX / 2, g.nx - 1), jc = min(j0 + WY / 2, g.ny - 1);
-    double ref[2] = {T_l[cidx(g, ic, jc)], T_v[cidx(g, ic, jc)]};
     Scal F[2] = {{T_l}, {T_v}};
     Refl R[2] = {r, r};
-    tile_stage<2>(F, R, g, i0, j0, ref, sh);
+    tile_stage<2>(F, R, g, i0, j0, sh);
     int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
     int c = cidx(g, i, j);
-    double2 ul = u_l[c], uv = u_v[c];
-    float2 dl = tile_derivs(sh[0], tx + WH, ty + WH, make_float2((float)ul.x, (float)ul.y));
-    float2 dv = tile_derivs(sh[1], tx + WH, ty + WH, make_float2((float)uv.x, (float)uv.y));
-    Ts_l[c] = T_l[c] - dth * (double)((float)ul.x * dl.x + (float)ul.y * dl.y);
-    Ts_v[c] = T_v[c] - dth * (double)((float)uv.x * dv.x + (float)uv.y * dv.y);
+    Ts_l[c] = tile_advect(sh[0], tx + WH, ty + WH, u_l[c], dth);
+    Ts_v[c] = tile_advect(sh[1], tx + WH, ty + WH, u_v[c], dth);
 }
 
 // ---------------------------------------------------------------------------------
@@ -421,10 +387,12 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
 
 // RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields,
 // one two-RHS system per component (liquid, vapour interleaved); initial guesses = current u
-__global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const double* __restrict__ vf,
-                          const double2* __restrict__ u_l, const double2* __restrict__ u_v,
-                          const double2* __restrict__ gc, double2* __restrict__ bx, double2* __restrict__ by,
-                          double2* __restrict__ xx, double2* __restrict__ xy) {
+// (block WX x WY threads, one cell each; the four velocity components staged per tile)
+__global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth,
+                                                    const double* __restrict__ vf, const double2* __restrict__ u_l,
+                                                    const double2* __restrict__ u_v, const double2* __restrict__ gc,
+                                                    double2* __restrict__ bx, double2* __restrict__ by,
+                                                    double2* __restrict__ xx, double2* __restrict__ xy) {
     zphys(g, p);
     if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
     const long long zo = zoff(g.zs);
@@ -436,48 +404,11 @@ __global__ void k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth, const do
     by = zsh(by, zo);
     xx = zsh(xx, zo);
     xy = zsh(xy, zo);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (i >= g.nx) return;
-    int c = cidx(g, i, j);
-    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt;
-    double2 a = gc[c];
-    double2 ul = u_l[c], uv = u_v[c];
-    bx[c] = make_double2(coef * (advect_one(Comp{u_l, 0}, g, rx, i, j, ul, dth) + p.dt * a.x),
-                         coef * (advect_one(Comp{u_v, 0}, g, rx, i, j, uv, dth) + p.dt * a.x));
-    by[c] = make_double2(coef * (advect_one(Comp{u_l, 1}, g, ry, i, j, ul, dth) + p.dt * a.y),
-                         coef * (advect_one(Comp{u_v, 1}, g, ry, i, j, uv, dth) + p.dt * a.y));
-    xx[c] = make_double2(ul.x, uv.x);
-    xy[c] = make_double2(ul.y, uv.y);
-}
-
-// mixed-precision tile variant of k_mom_rhs (block WX x WY threads, one cell each)
-__global__ void __launch_bounds__(WX * WY) k_mom_rhs_f32(Grid g, Phys p, Refl rx, Refl ry, double dth,
-                                                        const double* __restrict__ vf,
-                                                        const double2* __restrict__ u_l,
-                                                        const double2* __restrict__ u_v,
-                                                        const double2* __restrict__ gc, double2* __restrict__ bx,
-                                                        double2* __restrict__ by, double2* __restrict__ xx,
-                                                        double2* __restrict__ xy) {
-    zphys(g, p);
-    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
-    const long long zo = zoff(g.zs);
-    vf = zsh(vf, zo);
-    u_l = zsh(u_l, zo);
-    u_v = zsh(u_v, zo);
-    gc = zsh(gc, zo);
-    bx = zsh(bx, zo);
-    by = zsh(by, zo);
-    xx = zsh(xx, zo);
-    xy = zsh(xy, zo);
-    __shared__ float sh[4][WSY][WSX];
+    __shared__ double sh[4][WSY][WSX];
     int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
-    int ic = min(i0 + WX / 2, g.nx - 1), jc = min(j0 + WY / 2, g.ny - 1);
-    double2 ulc = u_l[cidx(g, ic, jc)], uvc = u_v[cidx(g, ic, jc)];
-    double ref[4] = {ulc.x, ulc.y, uvc.x, uvc.y};
     Comp F[4] = {{u_l, 0}, {u_l, 1}, {u_v, 0}, {u_v, 1}};
     Refl R[4] = {rx, ry, rx, ry};
-    tile_stage<4>(F, R, g, i0, j0, ref, sh);
+    tile_stage<4>(F, R, g, i0, j0, sh);
     int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
@@ -485,13 +416,11 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs_f32(Grid g, Phys p, Refl rx
     double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt;
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
-    float2 fl = make_float2((float)ul.x, (float)ul.y), fv = make_float2((float)uv.x, (float)uv.y);
-    float2 d0 = tile_derivs(sh[0], tx + WH, ty + WH, fl), d1 = tile_derivs(sh[1], tx + WH, ty + WH, fl);
-    float2 d2 = tile_derivs(sh[2], tx + WH, ty + WH, fv), d3 = tile_derivs(sh[3], tx + WH, ty + WH, fv);
-    bx[c] = make_double2(coef * (ul.x - dth * (double)(fl.x * d0.x + fl.y * d0.y) + p.dt * a.x),
-                         coef * (uv.x - dth * (double)(fv.x * d2.x + fv.y * d2.y) + p.dt * a.x));
-    by[c] = make_double2(coef * (ul.y - dth * (double)(fl.x * d1.x + fl.y * d1.y) + p.dt * a.y),
-                         coef * (uv.y - dth * (double)(fv.x * d3.x + fv.y * d3.y) + p.dt * a.y));
+    int sx = tx + WH, sy = ty + WH;
+    bx[c] = make_double2(coef * (tile_advect(sh[0], sx, sy, ul, dth) + p.dt * a.x),
+                         coef * (tile_advect(sh[2], sx, sy, uv, dth) + p.dt * a.x));
+    by[c] = make_double2(coef * (tile_advect(sh[1], sx, sy, ul, dth) + p.dt * a.y),
+                         coef * (tile_advect(sh[3], sx, sy, uv, dth) + p.dt * a.y));
     xx[c] = make_double2(ul.x, uv.x);
     xy[c] = make_double2(ul.y, uv.y);
 }
@@ -840,13 +769,9 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
 // ---------------------------------------------------------------------------------
 
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
-                     const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st) {
-    if (f32w)
-        k_advect_T_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
-            g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l, Ts_v);
-    else
-        k_advect_T<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l,
-                                                              u_v, Ts_l, Ts_v);
+                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st) {
+    k_advect_T<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
+        g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l, Ts_v);
 }
 
 void launch_compact(const Grid& g, const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
@@ -909,14 +834,9 @@ void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* 
 }
 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
-                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, bool f32w,
-                    cudaStream_t st) {
-    if (f32w)
-        k_mom_rhs_f32<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
-            g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
-    else
-        k_mom_rhs<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, velocity_refl(g, 0), velocity_refl(g, 1),
-                                                             p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
+                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st) {
+    k_mom_rhs<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
+        g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
 }
 
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,

@@ -30,7 +30,7 @@ void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const 
 // fields.cu
 // f32w: WENO3 nonlinear weights in FP32 (mixed-precision mode)
 void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
-                     const double2* u_v, double* Ts_l, double* Ts_v, bool f32w, cudaStream_t st);
+                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st);
 void launch_compact(const Grid& g, const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
                     cudaStream_t st);
 void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
@@ -48,8 +48,7 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, c
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
                           double* wl, double* wb, cudaStream_t st);
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
-                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, bool f32w,
-                    cudaStream_t st);
+                    const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st);
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
                   double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
                   cudaStream_t st);

@@ -1071,6 +1071,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small(SmallPlan P, const T* _
 template <typename T>
 struct CoarsePlan {
     int l0, nb;                      // levels handled: tiled [l0, nb), then the single-block ones
+    int spin;                        // polls of a grid barrier before it gives up (fault bit 1)
     Lev<T> L[Solver::MAXLEV];
     const T* b[Solver::MAXLEV];      // rhs of level l
     T* x2[Solver::MAXLEV];           // pre-smoothed x of level l
@@ -1090,14 +1091,14 @@ __device__ inline unsigned ld_acquire_gpu(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ inline void grid_sync(unsigned* bar, unsigned& target, SolveState* st) {
+__device__ inline void grid_sync(unsigned* bar, unsigned& target, SolveState* st, int spin) {
     target += gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(&bar[0], 1u);
         for (int it = 0; (int)(ld_acquire_gpu(&bar[0]) - target) < 0; ++it)
-            if (it > (1 << 22)) {
+            if (it > spin) {
                 atomicOr(&st->fault, 2);
                 break;
             }
@@ -1121,10 +1122,10 @@ __global__ void __launch_bounds__(CC_THREADS) k_coarse_cycle(CoarsePlan<T> C, Sm
             pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr);
             __syncthreads();
         }
-        grid_sync(bar, gen, st);
+        grid_sync(bar, gen, st, C.spin);
     }
     if (blockIdx.x == 0) small_cycle<T, NR, false>(P, diag, wl, wb, inv, C.bc[C.nb - 1], C.xo[C.nb], st, smem);
-    grid_sync(bar, gen, st);
+    grid_sync(bar, gen, st, C.spin);
     for (int l = C.nb - 1; l >= C.l0; --l) {
         const Lev<T>& L = C.L[l];
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
@@ -1132,7 +1133,7 @@ __global__ void __launch_bounds__(CC_THREADS) k_coarse_cycle(CoarsePlan<T> C, Sm
             post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr);
             __syncthreads();
         }
-        if (l > C.l0) grid_sync(bar, gen, st);
+        if (l > C.l0) grid_sync(bar, gen, st, C.spin);
     }
 }
 
@@ -1392,13 +1393,18 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
     }
     double tot[NR];
     if (grid_reduce<NR>(acc, partial, ticket, tot)) {
-        bool done = true;
+        bool done = true, bad = false;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
             st->rr[k] = tot[k];
             if (!(tot[k] <= st->tol2[k])) done = false;
+            bad = bad || !isfinite(tot[k]);
         }
         st->iters += 1;
+        if (bad) {   // a NaN or infinity: no further iteration can recover
+            st->nonfinite = 1;
+            done = true;
+        }
         if (done) st->done = 1;
         set_cond(h, use_h, (!done && st->iters < st->max_iters) ? 1u : 0u);
     }
@@ -1455,7 +1461,7 @@ k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__
     }
     double tot[2 * NR];
     if (grid_reduce<2 * NR>(acc, partial, ticket, tot)) {
-        bool done = true;
+        bool done = true, bad = false;
         for (int k = 0; k < 2; ++k) {
             double rr = k < NR ? tot[k] : 0.0, bb = k < NR ? tot[NR + k] : 0.0;
             st->rr[k] = rr;
@@ -1464,7 +1470,10 @@ k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__
             st->rz[k] = 0.0;
             st->beta[k] = 0.0;
             if (!(rr <= st->tol2[k])) done = false;
+            if (!isfinite(rr) || !isfinite(bb)) bad = true;
         }
+        st->nonfinite = bad ? 1 : 0;
+        if (bad) done = true;   // no iteration: the system holds a NaN or an infinity
         st->iters = 0;
         st->itot = 0;
         st->max_iters = max_iters;
@@ -1511,6 +1520,7 @@ __global__ void __launch_bounds__(256) k_ir_init(int N, long long zs, const doub
         st->max_outer = max_outer;
         st->inner_rtol = inner_rtol;
         st->nr = NR;
+        st->nonfinite = 0;
     }
 }
 
@@ -1575,6 +1585,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
             double rr = k < NR ? tot[k] : 0.0;
             st->orr[k] = rr;
             if (!(rr <= st->otol2[k])) done = false;
+            if (!isfinite(rr) || !isfinite(st->obb[k])) st->nonfinite = 1;
             st->rr[k] = rr;
             // the inner solve reduces the residual by inner_rtol, but never below half the
             // outer target: no solve past what the refinement needs
@@ -1584,7 +1595,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
         }
         st->oiters += 1;
         st->itot += st->iters;
-        if (st->oiters > st->max_outer) done = true;
+        if (st->oiters > st->max_outer || st->nonfinite) done = true;
         st->odone = done ? 1 : 0;
         st->iters = 0;
         st->done = done ? 1 : 0;
@@ -1663,11 +1674,12 @@ size_t Solver::bytes(int nx, int ny) {
 }
 
 template <typename K>
-static void allow_smem(K kern, int bytes) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static void allow_smem(K kern, int bytes, cudaError_t* first) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess && *first == cudaSuccess) *first = e;
 }
 
-void Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t init_stream) {
+cudaError_t Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t init_stream) {
     plan(nx_, ny_);
     tma_ready = false;   // descriptors hold addresses: re-encode after every binding
     char* p = (char*)base;
@@ -1694,36 +1706,44 @@ void Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaStream_t 
     // shared-memory limits of the tile kernels
     // shared-memory opt-in of the tile and small-level kernels (dynamic + static may pass 48 KB)
     const int SM = 200 * 1024;
-    allow_smem(k_pre<float, 1>, SM);
-    allow_smem(k_pre<float, 2>, SM);
-    allow_smem(k_pre<double, 1>, SM);
-    allow_smem(k_pre<double, 2>, SM);
-    allow_smem(k_post<float, 1, true>, SM);
-    allow_smem(k_post<float, 1, false>, SM);
-    allow_smem(k_post<float, 2, true>, SM);
-    allow_smem(k_post<float, 2, false>, SM);
-    allow_smem(k_post<double, 1, true>, SM);
-    allow_smem(k_post<double, 1, false>, SM);
-    allow_smem(k_post<double, 2, true>, SM);
-    allow_smem(k_post<double, 2, false>, SM);
-    allow_smem(k_coarse_cycle<float, 1>, SM);
-    allow_smem(k_coarse_cycle<float, 2>, SM);
-    allow_smem(k_coarse_cycle<double, 1>, SM);
-    allow_smem(k_coarse_cycle<double, 2>, SM);
-    allow_smem(k_small<float, 1, true>, SM);
-    allow_smem(k_small<float, 1, false>, SM);
-    allow_smem(k_small<float, 2, true>, SM);
-    allow_smem(k_small<float, 2, false>, SM);
-    allow_smem(k_small<double, 1, true>, SM);
-    allow_smem(k_small<double, 1, false>, SM);
-    allow_smem(k_small<double, 2, true>, SM);
-    allow_smem(k_small<double, 2, false>, SM);
+    cudaError_t err = cudaSuccess;
+    allow_smem(k_pre<float, 1>, SM, &err);
+    allow_smem(k_pre<float, 2>, SM, &err);
+    allow_smem(k_pre<double, 1>, SM, &err);
+    allow_smem(k_pre<double, 2>, SM, &err);
+    allow_smem(k_post<float, 1, true>, SM, &err);
+    allow_smem(k_post<float, 1, false>, SM, &err);
+    allow_smem(k_post<float, 2, true>, SM, &err);
+    allow_smem(k_post<float, 2, false>, SM, &err);
+    allow_smem(k_post<double, 1, true>, SM, &err);
+    allow_smem(k_post<double, 1, false>, SM, &err);
+    allow_smem(k_post<double, 2, true>, SM, &err);
+    allow_smem(k_post<double, 2, false>, SM, &err);
+    allow_smem(k_coarse_cycle<float, 1>, SM, &err);
+    allow_smem(k_coarse_cycle<float, 2>, SM, &err);
+    allow_smem(k_coarse_cycle<double, 1>, SM, &err);
+    allow_smem(k_coarse_cycle<double, 2>, SM, &err);
+    allow_smem(k_small<float, 1, true>, SM, &err);
+    allow_smem(k_small<float, 1, false>, SM, &err);
+    allow_smem(k_small<float, 2, true>, SM, &err);
+    allow_smem(k_small<float, 2, false>, SM, &err);
+    allow_smem(k_small<double, 1, true>, SM, &err);
+    allow_smem(k_small<double, 1, false>, SM, &err);
+    allow_smem(k_small<double, 2, true>, SM, &err);
+    allow_smem(k_small<double, 2, false>, SM, &err);
     // device state that must start at zero (tickets, solve states, timers; timer starts at ~0)
-    cudaMemsetAsync(timer, 0, 4 * sizeof(KTimer), init_stream);
-    for (int k = 0; k < 4; ++k) cudaMemsetAsync(&timer[k].start, 0xff, sizeof(unsigned long long), init_stream);
-    cudaMemsetAsync(tickets, 0, 256, init_stream);
-    cudaMemsetAsync(st_base, 0, NSLOT * sizeof(SolveState), init_stream);
+    cudaError_t e[4];
+    e[0] = cudaMemsetAsync(timer, 0, 4 * sizeof(KTimer), init_stream);
+    e[1] = cudaSuccess;
+    for (int k = 0; k < 4; ++k) {
+        cudaError_t ek = cudaMemsetAsync(&timer[k].start, 0xff, sizeof(unsigned long long), init_stream);
+        if (ek != cudaSuccess) e[1] = ek;
+    }
+    e[2] = cudaMemsetAsync(tickets, 0, 256, init_stream);
+    e[3] = cudaMemsetAsync(st_base, 0, NSLOT * sizeof(SolveState), init_stream);
+    for (int k = 0; k < 4 && err == cudaSuccess; ++k) err = e[k];
     timing = 1;
+    return err;
 }
 
 // accessors for precision T
@@ -1977,6 +1997,7 @@ static void vcycle(Solver& s, const T* r, T* z, SolveState* st, cudaStream_t stm
         CoarsePlan<T> C;
         C.l0 = l0;
         C.nb = nb;
+        C.spin = s.barrier_spin > 0 ? s.barrier_spin : (1 << 22);
         for (int l = l0; l < nb; ++l) {
             C.L[l] = lev<T>(s, l);
             C.b[l] = l == 0 ? r : B + 2 * s.loff[l];
@@ -2218,9 +2239,16 @@ void Solver::fetch_states(cudaStream_t stm) {
     cudaMemcpyAsync(st_host, st_base, NSLOT * sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
 }
 
-SolveResult Solver::read_result(int sl, int precision, cudaStream_t stm) {
-    cudaMemcpyAsync(st_host + sl, st_base + sl, sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
-    cudaStreamSynchronize(stm);
+SolveResult Solver::read_result(int sl, int precision, cudaStream_t stm, cudaError_t* err) {
+    cudaError_t e = cudaMemcpyAsync(st_host + sl, st_base + sl, sizeof(SolveState), cudaMemcpyDeviceToHost, stm);
+    cudaError_t es = cudaStreamSynchronize(stm);
+    if (e == cudaSuccess) e = es;
+    if (err) *err = e;
+    SolveResult r{};
+    if (e != cudaSuccess) {   // the state was not read back: no valid result
+        r.fault = true;
+        return r;
+    }
     return result_from_host(sl, precision);
 }
 
@@ -2236,6 +2264,7 @@ SolveResult Solver::result_from_host(int sl, int precision) const {
     }
     r.rel_res = worst;
     r.fault = h.fault != 0;
+    r.nonfinite = h.nonfinite != 0;
     if (precision == 0) {
         r.iters = h.iters;
         r.converged = h.done != 0;
@@ -2266,13 +2295,18 @@ SolveResult Solver::result_from_host(int sl, int precision) const {
 // tickets, solver state, timers) is cleared at the start of each call.  Two calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on the array.
 // ---------------------------------------------------------------------------------------
+#include <atomic>
+
 #include "../../include/ebit.h"
+#include "status.h"
 
 namespace ebit {
 constexpr size_t NOALLOC_BYTES = (size_t)6 << 20;
 constexpr int NOALLOC_MAX_CELLS = 128 * 128;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
-static void* g_noalloc_addr[64];   // device address of g_noalloc_scratch per device (host side)
+// device address of g_noalloc_scratch per device (host side); every writer stores the same
+// address for a device, and the atomics make concurrent first calls well defined
+static std::atomic<void*> g_noalloc_addr[64];
 }  // namespace ebit
 
 extern "C" ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const double* wl, const double* wb,
@@ -2286,22 +2320,31 @@ extern "C" ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D
         return EBIT_EINVAL;   // larger than the fixed scratch array (at most 128 x 128 cells)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EBIT_ECUDA;
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return EBIT_ECUDA;
-        g_noalloc_addr[dev] = p;
+    void* base = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!base) {
+        if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) return EBIT_ECUDA;
+        g_noalloc_addr[dev].store(base, std::memory_order_release);
     }
+    // an error already pending from an earlier, unrelated runtime call is not this call's: it
+    // is left in place, and only an error that appears during this call is taken (and cleared)
+    const bool clean = cudaPeekAtLastError() == cudaSuccess;
     cudaStream_t st = (cudaStream_t)stream;
     Solver s;
-    s.bind(g_noalloc_addr[dev], nx, ny, false, st);
-    SolveState host[Solver::NSLOT];
+    if (s.bind(base, nx, ny, false, st) != cudaSuccess) {
+        if (clean) cudaGetLastError();
+        return EBIT_ECUDA;
+    }
+    SolveState host[Solver::NSLOT];   // read_result synchronises before returning: the stack copy is safe
     s.st_host = host;
     s.slot = 0;
     s.use_graph = 0;
     s.solve(D, nullptr, wl, wb, b, x, nr, precision, rtol, max_iter, st);
-    SolveResult r = s.read_result(0, precision, st);
-    if (cudaGetLastError() != cudaSuccess) return EBIT_ECUDA;
-    if (iters) *iters = r.iters;
-    if (rel_res) *rel_res = r.rel_res;
-    return r.converged ? EBIT_OK : EBIT_ENOCONV;
+    cudaError_t e = cudaSuccess;
+    SolveResult r = s.read_result(0, precision, st, &e);
+    if (e == cudaSuccess && clean) e = cudaGetLastError();   // launch errors of the solve
+    if (e == cudaSuccess) {
+        if (iters) *iters = r.iters;
+        if (rel_res) *rel_res = r.rel_res;
+    }
+    return solve_status(e == cudaSuccess, r.fault, r.nonfinite, r.converged);
 }

@@ -14,7 +14,8 @@ struct SolveResult {
     double rel_res;   // final ||r|| / ||b|| (max over right-hand sides)
     bool converged;
     int outer = 0;    // refinement sweeps (mixed)
-    bool fault = false;   // a bounded wait for TMA copies gave up (the result is not valid)
+    bool fault = false;   // a bounded wait (TMA copies, grid barrier) gave up: the result is not valid
+    bool nonfinite = false;   // the system or the iterate held a NaN or an infinity
 };
 
 // device-resident timing of one kernel class (span from the first block's start to the
@@ -35,7 +36,8 @@ struct SolveState {
     double orr[2], obb[2], otol2[2];   // outer (FP64) residual norms of the refinement loop
     int done, iters, odone, oiters, max_iters, max_outer, nr, itot;
     double inner_rtol;
-    int fault;         // nonzero: a bounded wait of a tile kernel gave up (its TMA copies never landed)
+    int fault;         // nonzero: a bounded wait gave up (TMA copies that never landed, a grid barrier)
+    int nonfinite;     // nonzero: a residual norm was NaN or infinite (the solve stopped there)
 };
 
 // TMA descriptors of one tiled level (precision and right-hand-side count fixed): the level's
@@ -84,6 +86,7 @@ struct Solver {
     bool tma_ready = false;
     int use_tma = 1;       // 0: the tile kernels load their regions with plain loads
     int use_coop = 1;      // 0: no cooperative launch for the coarse part of the V-cycle
+    int barrier_spin = 0;  // polls of the cooperative launch's grid barrier before it gives up (0: 2^22)
     // batched launches: this solver drives nz instances whose arenas lie zs bytes apart (the
     // solvers of instances 1..nz-1 are bound to their own arenas, read only for statistics)
     int nz = 1;
@@ -96,7 +99,8 @@ struct Solver {
 
     void plan(int nx, int ny);
     static size_t bytes(int nx, int ny);
-    void bind(void* base, int nx, int ny, bool make_streams = true, cudaStream_t init_stream = 0);
+    // carve the arrays out of `base`; returns the first CUDA error of the set-up calls
+    cudaError_t bind(void* base, int nx, int ny, bool make_streams = true, cudaStream_t init_stream = 0);
     // Solve A x = b for nr (1 or 2) interleaved right-hand sides.  The fine operator is given
     // cell-centred in FP64: cd (h^2 c), dd (Dirichlet terms), wl (left-face weight), wb
     // (bottom-face weight); x holds the initial guess.  In graph mode (use_graph) the loops
@@ -104,7 +108,9 @@ struct Solver {
     // available after the graph ran (read it with read_result).
     void solve(const double* cd, const double* dd, const double* wl, const double* wb, const double* b, double* x,
                int nr, int precision, double rtol, int max_iter, cudaStream_t st);
-    SolveResult read_result(int slot, int precision, cudaStream_t st);
+    // synchronises st; a failed copy or synchronisation is returned in *err (if given) and
+    // gives a result with fault set
+    SolveResult read_result(int slot, int precision, cudaStream_t st, cudaError_t* err = nullptr);
     // batched read-back: queue the copy of every slot's state to st_host (no synchronisation),
     // then, once the stream has been synchronised, read a slot from the host copy
     void fetch_states(cudaStream_t st);

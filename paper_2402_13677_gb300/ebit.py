@@ -19,9 +19,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libebit.so")
 
 # status codes
-EBIT_OK, EBIT_EINVAL, EBIT_ENOMEM, EBIT_ENOCONV, EBIT_ETOPO, EBIT_ECUDA, EBIT_ECFL = 0, -1, -2, -3, -4, -5, -6
+EBIT_OK, EBIT_EINVAL, EBIT_ENOMEM, EBIT_ENOCONV, EBIT_ETOPO, EBIT_ECUDA, EBIT_ECFL, EBIT_ENONFINITE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 STATUS_NAMES = {0: "EBIT_OK", -1: "EBIT_EINVAL", -2: "EBIT_ENOMEM", -3: "EBIT_ENOCONV", -4: "EBIT_ETOPO",
-                -5: "EBIT_ECUDA", -6: "EBIT_ECFL"}
+                -5: "EBIT_ECUDA", -6: "EBIT_ECFL", -7: "EBIT_ENONFINITE"}
 EBIT_FP64, EBIT_MIXED = 0, 1
 
 # field ids
@@ -41,6 +42,7 @@ EXPORTS = ["ebit_init", "ebit_set_phase_props", "ebit_set_interface", "ebit_set_
 EBIT_OPT_GRAPH = 1
 EBIT_OPT_TMA = 2
 EBIT_OPT_COOP = 3
+EBIT_OPT_BARRIER_SPIN = 4
 EBIT_KT_SMOOTH_L0 = 1
 
 

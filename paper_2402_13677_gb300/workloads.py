@@ -311,6 +311,25 @@ def const_mdot_bubble(n=64, L=8.0, R0=2.0, mdot=0.1, rho_l=1000.0, rho_v=1.0,
     return pb
 
 
+def const_mdot_levelset(phi, n=48, L=1.0, mdot=1.0, rho_l=10.0, rho_v=1.0, mu=0.01, dt=None, cfl=0.35,
+                        name="levelset", steps=4, **kw) -> Problem:
+    """An arbitrary initial interface (liquid where phi > 0) with an imposed constant mass flux
+    and the energy equation off (Sec. 3.3), at rest, outflow on all sides, on [0, L]^2.  Used
+    for the topology cases: growing discs that merge, a condensing film that annihilates,
+    saddle-shaped level sets, and a bubble that crosses the domain boundary.  dt defaults to
+    moving the interface cfl cells per step relative to the vapour (mdot dt / (rho_v h))."""
+    h = L / n
+    if dt is None:
+        dt = cfl * h * rho_v / abs(mdot)
+    pb = Problem(name, n, n, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v, mu_l=mu, mu_v=mu,
+                 T_sat=0.0, h_lg=1.0, bc=(OUTFLOW,) * 4, T_bc=(None,) * 4, energy=False, mdot_fixed=mdot, **kw)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(phi, n, n, h)
+    pb.T_l = np.zeros((n, n))
+    pb.T_v = np.zeros((n, n))
+    _zero_flow(pb)
+    return pb
+
+
 def film(nx=1024, ny=2048, Lx=1.0, mean=0.05, amp=0.005, modes=None, seed=0,
          rho_l=5.0, rho_v=1.0, mu_l=5e-3, mu_v=1e-3, lam_l=1e-2, lam_v=1e-3,
          St=0.064, dT=1.0, g=-1.0, dt=None, steps=5000, **kw) -> Problem:

@@ -96,3 +96,42 @@ def test_binding_fails_loudly_without_library(tmp_path):
             mod.load(str(tmp_path / "missing.so"))
     finally:
         mod._lib = saved
+
+
+def test_status_codes_match_the_header():
+    """The binding's status numbers are the header's enum values."""
+    hdr = open(os.path.join(ROOT, "include", "ebit.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    body = re.search(r"typedef enum \{(.*?)\} ebit_status;", hdr, flags=re.S).group(1)
+    vals = {n: int(v) for n, v in re.findall(r"(EBIT_\w+)\s*=\s*(-?\d+)", body)}
+    assert {v: n for n, v in vals.items()} == E.STATUS_NAMES
+    for n, v in vals.items():
+        assert getattr(E, n) == v
+
+
+def test_solve_status_mapping(tmp_path):
+    """A solve whose bounded device wait gave up is an error (EBIT_ECUDA) even when its residual
+    looks converged; a non-finite residual is EBIT_ENONFINITE; otherwise converged or not.  The
+    mapping both solve entry points use, compiled with the host compiler."""
+    src = tmp_path / "status.cpp"
+    src.write_text("\n".join([
+        '#include <cstdio>',
+        '#include "status.h"',
+        "int main() {",
+        "  for (int m = 0; m < 16; ++m)",
+        '    std::printf("%d %d\\n", m, (int)ebit::solve_status(m & 1, m & 2, m & 4, m & 8));',
+        "  return 0;",
+        "}"]))
+    exe = tmp_path / "status"
+    subprocess.run(["g++", "-std=c++17", "-I", os.path.join(ROOT, "paper_2402_13677_gb300", "csrc"), str(src),
+                    "-o", str(exe)], check=True)
+    got = dict(map(int, l.split()) for l in subprocess.run([str(exe)], capture_output=True,
+                                                             text=True).stdout.splitlines())
+    for m, s in got.items():
+        cuda_ok, fault, nonfinite, converged = m & 1, m & 2, m & 4, m & 8
+        if not cuda_ok or fault:
+            assert s == E.EBIT_ECUDA, m        # a fault is never reported as success
+        elif nonfinite:
+            assert s == E.EBIT_ENONFINITE, m
+        else:
+            assert s == (E.EBIT_OK if converged else E.EBIT_ENOCONV), m

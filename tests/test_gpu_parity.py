@@ -2,7 +2,8 @@
 
 Bar (stated by the method's GPU design): cut-edge flags, topology and reconnection
 bit-exact; temperature, pressure, velocities and marker positions within 1e-10 relative
-(to the field group's magnitude) in the FP64 path; the mixed FP32/FP64 path within 1e-6.
+(to the field group's magnitude) in the FP64 path; the mixed path (FP32 inside the FP64
+refinement of the solves, everything else FP64) within 1e-7.
 The FP64 solves run to a 1e-15 relative residual here: the error of a solve is bounded by
 its relative residual times the condition number (1e3-1e5 for these Poisson operators), so
 1e-10 on the solution needs a residual below ~1e-14.
@@ -76,6 +77,30 @@ def group_scale(st, k):
     return max(np.max(np.abs(getattr(st, k))), 1e-300)
 
 
+def _translating_film(n=48):
+    """A liquid film 0.6 cells thick around a row of vertices, carried up half a cell per step
+    by a uniform flow (no phase change): its lower marker crosses the vertex row, which flips,
+    and the film's edges become uncut (EBIT annihilation of a sub-cell film)."""
+    h = 1.0 / n
+    pb = w.const_mdot_levelset(lambda x, y: np.abs(y - 25.05 * h) - 0.3 * h, n=n, mdot=0.0, dt=0.5 * h,
+                               name="annihilate")
+    for k in ("u_l", "u_v"):
+        getattr(pb, k)[..., 1] = 1.0
+    pb.ufy_l[:] = 1.0
+    pb.ufy_v[:] = 1.0
+    return pb
+
+
+def _merging_discs(n=48, gap=0.3):
+    """Two vapour discs 0.3 cells apart growing at an imposed mass flux: they merge, split and
+    merge again at their contact within four steps."""
+    h, R = 1.0 / n, 0.15
+    d = R + gap * h / 2
+    return w.const_mdot_levelset(lambda x, y: np.minimum(np.hypot(x - 0.4969 + d, y - 0.5013) - R,
+                                                         np.hypot(x - 0.4969 - d, y - 0.5013) - R),
+                                 n=n, mdot=1.0, name="merge")
+
+
 def cases():
     return {
         "stefan": lambda: w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0),
@@ -85,7 +110,19 @@ def cases():
         # above 4096 cells: the tiled multigrid kernels run (32x32 tiles, ragged in x and y here)
         "bubble_mid": lambda: w.bubble(n=96, R0=0.21, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01, dt=5e-5, steps=0),
         "film_mid": lambda: w.film(80, 88, Lx=1.0, mean=0.27, amp=0.03, modes=3, seed=5, steps=0, dt=1e-3),
+        # topology: merging and splitting discs, an annihilated film, 36 saddle cells whose
+        # liquid components pinch off, a bubble cut by the outflow boundary (markers held on it)
+        "merge": _merging_discs,
+        "annihilate": _translating_film,
+        "saddle": lambda: w.const_mdot_levelset(
+            lambda x, y: np.cos(6 * np.pi * (x + 0.0104)) * np.cos(6 * np.pi * (y + 0.009)) + 0.01, n=48,
+            mdot=0.5, cfl=0.1, name="saddle"),
+        "outflow": lambda: w.const_mdot_levelset(lambda x, y: np.hypot(x - 0.9, y - 0.47) - 0.17, n=48, mdot=1.0,
+                                                 cfl=0.2, name="outflow"),
     }
+
+
+TOPOLOGY = ["merge", "annihilate", "saddle", "outflow"]
 
 
 CASES = list(cases().keys())
@@ -215,12 +252,12 @@ def test_energy_solve_flux_and_ghost_velocity(dev, name):
         g = E.download(ctx, 0, pb.nx, pb.ny, ["T_l", "T_v", "mdot"])
         assert relerr(g["T_l"], so.T_l, group_scale(so, "T_l")) < TOL64
         assert relerr(g["T_v"], so.T_v, group_scale(so, "T_v")) < TOL64
-        assert relerr(g["mdot"], so.mdot) < 1e-9
+        assert relerr(g["mdot"], so.mdot) < TOL64
         E.ebit_run_stage(ctx, E.STAGE_GHOST_VELOCITY)
         OF.ghost_velocities(so)
         g = E.download(ctx, 0, pb.nx, pb.ny, ["u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v"])
         for k in ("u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v"):
-            assert relerr(g[k], getattr(so, k), group_scale(so, k)) < 1e-9, k
+            assert relerr(g[k], getattr(so, k), group_scale(so, k)) < TOL64, k
     finally:
         E.ebit_destroy(ctx)
 
@@ -266,22 +303,52 @@ def test_several_steps_track_the_oracle(dev, name):
         assert np.max(np.abs(g["hx_pos"] - so.hx_pos)) < 1e-10
         assert np.max(np.abs(g["vy_pos"] - so.vy_pos)) < 1e-10
         for k in FIELDS:
-            assert relerr(g[k], getattr(so, k), group_scale(so, k)) < 1e-9, k
+            assert relerr(g[k], getattr(so, k), group_scale(so, k)) < TOL64, k
     finally:
         E.ebit_destroy(ctx)
 
 
-# Mixed mode: the solves are FP32 MG-PCG inside FP64 refinement (here to 1e-10) and the WENO3
-# advection stencils run in FP32, whose rounding is of order the FP32 epsilon (6e-8) relative to
-# the advected increment; the projection turns a velocity error d into a pressure error of
-# about d / CFL relative to rho_l u^2.  Bar: 16 FP32 epsilons, 1e-6.
-TOL_MIXED = 1e-6
+@pytest.mark.parametrize("name", TOPOLOGY)
+def test_topology_changes_track_the_oracle(dev, name):
+    """Four whole steps through merging, splitting, annihilation, saddle cells and a boundary-
+    cut bubble: the first step's markers bit for bit, vertex colours (the topology) identical
+    after every step, markers and fields within 1e-10."""
+    from scipy import ndimage
+    st = prepared(name, 0)
+    ctx = gpu_ctx(dev, st)
+    try:
+        so = st.copy()
+        so.nstep = 0
+        seen = {(ndimage.label(so.vcol == 0)[1], ndimage.label(so.vcol == 1)[1])}
+        for k in range(4):
+            E.ebit_step(ctx, 1)
+            S.step(so)
+            g = E.download(ctx, 0, st.pb.nx, st.pb.ny)
+            assert np.array_equal(g["vcol"], so.vcol), k
+            if k == 0:
+                assert np.array_equal(g["hx_pos"], so.hx_pos) and np.array_equal(g["vy_pos"], so.vy_pos)
+            assert np.max(np.abs(g["hx_pos"] - so.hx_pos)) < TOL64
+            assert np.max(np.abs(g["vy_pos"] - so.vy_pos)) < TOL64
+            for f in FIELDS:
+                e = relerr(g[f], getattr(so, f), group_scale(so, f))
+                assert e < TOL64, (k, f, e)
+            seen.add((ndimage.label(so.vcol == 0)[1], ndimage.label(so.vcol == 1)[1]))
+        assert len(seen) > 1 or name == "outflow"   # the topology did change
+    finally:
+        E.ebit_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
+# Mixed mode: the solves are FP32 MG-PCG inside FP64 refinement (here to a 1e-10 relative
+# residual); every explicit stencil (WENO3 advection, operators, fluxes) is FP64.  The error of
+# a solve is bounded by its residual times the condition number of the operator (1e2-1e3 for
+# these cases), so 1e-10 residuals keep the fields within 1e-7.
+TOL_MIXED = 1e-7
+
+
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "bubble_mid"])
 def test_mixed_precision_error_against_oracle(dev, name):
-    """FP32 MG-PCG inside FP64 refinement to 1e-10, FP32 WENO3 stencils: error vs the FP64 oracle
-    stated and bounded."""
+    """FP32 MG-PCG inside FP64 refinement to 1e-10, FP64 explicit stencils: error vs the FP64
+    oracle stated and bounded."""
     st = prepared(name, 1)
     ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-10)
     try:
@@ -299,26 +366,27 @@ def test_mixed_precision_error_against_oracle(dev, name):
         E.ebit_destroy(ctx)
 
 
-def test_c2_bubble_full_size_sampled(dev):
-    """512^2 planar bubble (the benchmark workload), one FP64 step and one mixed step; the oracle
-    computes the same step, every cut flag and sampled field values are compared."""
+def test_c2_bubble_full_size_every_cell(dev):
+    """512^2 planar bubble (the benchmark workload), one FP64 step and one mixed step, against the
+    oracle's step from the same state: markers and vertex colours bit for bit, every cell and
+    face of every field (temperatures, velocities, pressure, accelerations, mass flux) within
+    1e-10 (FP64, solves to a 1e-15 relative residual) and 1e-7 (mixed, solves to 1e-10)."""
     pb = w.c2_bubble(steps=0)
     st = S.prepare(pb)
     so = st.copy()
     S.step(so)
-    rng = np.random.default_rng(7)
-    idx = rng.integers(0, pb.nx * pb.ny, size=4096)
-    for prec, tol in ((E.EBIT_FP64, 1e-9), (E.EBIT_MIXED, 1e-6)):
-        ctx = gpu_ctx(dev, st, precision=prec, rtol=1e-12 if prec == E.EBIT_FP64 else 1e-10, max_iter=1000)
+    for prec, tol, rtol in ((E.EBIT_FP64, TOL64, 1e-15), (E.EBIT_MIXED, TOL_MIXED, 1e-10)):
+        ctx = gpu_ctx(dev, st, precision=prec, rtol=rtol, max_iter=2000)
         try:
             E.ebit_step(ctx, 1)
             g = E.download(ctx, 0, pb.nx, pb.ny)
             assert np.array_equal(g["vcol"], so.vcol)
-            assert np.max(np.abs(g["hx_pos"] - so.hx_pos)) == 0.0
-            for k in ("T_l", "p", "u_l"):
-                ref = getattr(so, k).reshape(pb.nx * pb.ny, -1)[idx]
-                got = g[k].reshape(pb.nx * pb.ny, -1)[idx]
-                assert relerr(got, ref, group_scale(so, k)) <= tol, (prec, k)
+            assert np.array_equal(g["hx_pos"], so.hx_pos)
+            assert np.array_equal(g["vy_pos"], so.vy_pos)
+            for k in FIELDS:
+                e = relerr(g[k], getattr(so, k), group_scale(so, k))
+                print(f"c2 512^2 {'fp64' if prec == E.EBIT_FP64 else 'mixed'} {k}: {e:.2e}")
+                assert e <= tol, (prec, k, e)
         finally:
             E.ebit_destroy(ctx)
 

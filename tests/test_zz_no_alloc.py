@@ -82,3 +82,30 @@ def test_noalloc_rejects_grids_beyond_its_fixed_scratch(dev):
     z = torch.zeros(nx * ny, dtype=torch.float64, device="cuda")
     s, it, rr = E.ebit_solve_system_noalloc(nx, ny, z, z, z, z, z.clone(), stream=dev[1].cuda_stream)
     assert s == E.EBIT_EINVAL
+
+
+@pytest.mark.parametrize("nx, ny, nr, prec", [(128, 128, 2, E.EBIT_FP64), (128, 128, 2, E.EBIT_MIXED),
+                                              (120, 104, 1, E.EBIT_MIXED)])
+def test_noalloc_at_the_cap_and_on_ragged_tiles_allocates_nothing(dev, nx, ny, nr, prec):
+    """The largest grid the fixed scratch takes (128 x 128, two right-hand sides) and a grid of
+    ragged 32 x 32 tiles near it; the second of two identical calls (the first loads the
+    kernels) leaves the device's free memory unchanged to the byte."""
+    rng = np.random.default_rng(nx + ny + nr + prec)
+    D, wl, wb = system(nx, ny, rng, "poisson_top")
+    b = rng.normal(size=nx * ny * nr)
+    ref = reference(dev, nx, ny, D, wl, wb, b, nr, prec)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device="cuda")
+    Dd, wld, wbd, bd = t(D), t(wl), t(wb), t(b)
+    xs = [torch.zeros(nx * ny * nr, dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free = []
+    for xd in xs:
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        s, it, rr = E.ebit_solve_system_noalloc(nx, ny, Dd, wld, wbd, bd, xd, nr=nr, precision=prec, rtol=1e-13,
+                                                max_iter=500, stream=dev[1].cuda_stream)
+        assert s == E.EBIT_OK, E.STATUS_NAMES.get(s, s)
+        torch.cuda.synchronize()
+        x = xd.cpu().numpy()
+        assert np.max(np.abs(x - ref)) <= TOL * np.max(np.abs(ref)), (nx, ny)
+    assert torch.cuda.mem_get_info()[0] == free[1]

@@ -374,7 +374,7 @@ def run_ours(args):
         e2e = {"value": None, "skipped": "batched workload: per-instance host buffers for every field of "
                                          f"{len(pbs)} instances are not staged; run a single-instance workload"}
     elif not args.no_e2e:
-        ctx = new_ctx(E.EBIT_MIXED)
+        ctx = new_ctx(pbs, E.EBIT_MIXED)
         try:
             for _ in range(args.warmup):
                 E.ebit_step(ctx, 1, allow_noconv=True)

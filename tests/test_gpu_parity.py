@@ -68,9 +68,13 @@ def group_scale(st, k):
     """Magnitude a field is judged against: its group's max over the oracle state (velocities
     together, temperatures together); fields that are identically zero in a case (vapour at
     T_sat, the y-velocity of the 1D Stefan problem) are thereby compared absolutely."""
+    umax = max(np.max(np.abs(getattr(st, n))) for n in GROUPS["U"])
     if k == "p":   # pressure: at least the dynamic pressure rho_l |u|^2 of the state
-        umax = max(np.max(np.abs(getattr(st, n))) for n in GROUPS["U"])
         return max(np.max(np.abs(st.p)), st.pb.rho_l * umax * umax, 1e-300)
+    if k == "gc":  # acceleration: at least |g| and u^2 over the domain size (a flow at rest or in
+        # uniform motion has gc at round-off, which is not a scale)
+        L = min(st.pb.nx, st.pb.ny) * st.pb.h
+        return max(np.max(np.abs(st.gc)), abs(st.pb.gx), abs(st.pb.gy), umax * umax / L, 1e-300)
     for names in GROUPS.values():
         if k in names:
             return max(max(np.max(np.abs(getattr(st, n))) for n in names), 1e-300)
@@ -281,8 +285,14 @@ def test_full_step_fp64(dev, name):
             assert e < TOL64, (k, e)
         d = E.ebit_get_diagnostics(ctx, 0)
         assert abs(d[0] - row[0]) < 1e-12
+        pb = st.pb
+        umax = max(np.max(np.abs(getattr(so, n))) for n in GROUPS["U"])
+        L = min(pb.nx, pb.ny) * pb.h
+        # scales: vapour volume and its expected change ~ the domain area; mass ~ rho_l area;
+        # outlet mass per step ~ rho_l u_max L dt (sums whose terms cancel end at round-off of it)
+        scale = {1: L * L, 2: L * L, 3: pb.rho_l * L * L, 4: pb.rho_l * umax * L * pb.dt}
         for q in (1, 2, 3, 4):
-            assert abs(d[q] - row[q]) <= 1e-9 * max(1e-12, abs(row[q])), q
+            assert abs(d[q] - row[q]) <= 1e-9 * max(abs(row[q]), 1e-6 * scale[q]), q
         assert d[5] == row[5]
     finally:
         E.ebit_destroy(ctx)
@@ -338,19 +348,21 @@ def test_topology_changes_track_the_oracle(dev, name):
         E.ebit_destroy(ctx)
 
 
-# Mixed mode: the solves are FP32 MG-PCG inside FP64 refinement (here to a 1e-10 relative
-# residual); every explicit stencil (WENO3 advection, operators, fluxes) is FP64.  The error of
-# a solve is bounded by its residual times the condition number of the operator (1e2-1e3 for
-# these cases), so 1e-10 residuals keep the fields within 1e-7.
+# Mixed mode: the solves are FP32 MG-PCG inside FP64 refinement; every explicit stencil (WENO3
+# advection, operators, fluxes) is FP64.  The error of a solve is bounded by its residual times
+# the condition number of the operator (up to ~1e5 for the projection with a density ratio of 20
+# on 512^2), so the refinement runs to a 1e-12 relative residual here: what remains is the
+# precision of the path, not the tolerance of the solve.
 TOL_MIXED = 1e-7
+RTOL_MIXED = 1e-12
 
 
 @pytest.mark.parametrize("name", ["stefan", "bubble", "film", "bubble_mid"])
 def test_mixed_precision_error_against_oracle(dev, name):
-    """FP32 MG-PCG inside FP64 refinement to 1e-10, FP64 explicit stencils: error vs the FP64
+    """FP32 MG-PCG inside FP64 refinement to 1e-12, FP64 explicit stencils: error vs the FP64
     oracle stated and bounded."""
     st = prepared(name, 1)
-    ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-10)
+    ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=RTOL_MIXED)
     try:
         so = st.copy()
         so.nstep = 0
@@ -370,12 +382,12 @@ def test_c2_bubble_full_size_every_cell(dev):
     """512^2 planar bubble (the benchmark workload), one FP64 step and one mixed step, against the
     oracle's step from the same state: markers and vertex colours bit for bit, every cell and
     face of every field (temperatures, velocities, pressure, accelerations, mass flux) within
-    1e-10 (FP64, solves to a 1e-15 relative residual) and 1e-7 (mixed, solves to 1e-10)."""
+    1e-10 (FP64, solves to a 1e-15 relative residual) and 1e-7 (mixed, refinement to 1e-12)."""
     pb = w.c2_bubble(steps=0)
     st = S.prepare(pb)
     so = st.copy()
     S.step(so)
-    for prec, tol, rtol in ((E.EBIT_FP64, TOL64, 1e-15), (E.EBIT_MIXED, TOL_MIXED, 1e-10)):
+    for prec, tol, rtol in ((E.EBIT_FP64, TOL64, 1e-15), (E.EBIT_MIXED, TOL_MIXED, RTOL_MIXED)):
         ctx = gpu_ctx(dev, st, precision=prec, rtol=rtol, max_iter=2000)
         try:
             E.ebit_step(ctx, 1)

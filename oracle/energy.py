@@ -124,6 +124,18 @@ def advect(F, u, sides, dt, h):
     return F - (dt / h) * (u[..., 0] * dx + u[..., 1] * dy)
 
 
+def advect_phases(T_l, T_v, u_l, u_v, ccol, T_bc, dt, h):
+    """Energy advection of each phase on the cells of that phase (the energy-advection equation
+    is written per phase, T*_k = T_k - dt u_k . grad T_k in phase k; centre colours of the
+    interface before it moves).  Elsewhere T*_k keeps T_k: the band cells of the other phase
+    are refilled by the extension from the phase-k cells, and cells beyond the band are not
+    read by any phase-k update."""
+    sides = temperature_sides(T_bc)
+    Ts_l = np.where(ccol == 1, advect(T_l, u_l, sides, dt, h), T_l)
+    Ts_v = np.where(ccol == 0, advect(T_v, u_v, sides, dt, h), T_v)
+    return Ts_l, Ts_v
+
+
 # --------------------------------------------------------------------------
 # S6: narrow-band extension (extrapolation equation)
 # --------------------------------------------------------------------------

@@ -96,8 +96,7 @@ def step(st):
     g_old = st.geom
     # 1. energy advection + extension of T* (old interface)
     if pb.energy:
-        Ts_l = energy.advect(st.T_l, st.u_l, energy.temperature_sides(pb.T_bc), pb.dt, pb.h)
-        Ts_v = energy.advect(st.T_v, st.u_v, energy.temperature_sides(pb.T_bc), pb.dt, pb.h)
+        Ts_l, Ts_v = energy.advect_phases(st.T_l, st.T_v, st.u_l, st.u_v, g_old.ccol, pb.T_bc, pb.dt, pb.h)
         Ts_l, Ts_v = energy.extend_temperatures(Ts_l, Ts_v, g_old, pb.extend_iters)
     # 2. interface advection
     advance_interface(st)

@@ -425,7 +425,7 @@ static ebit_status run_stage(ebit_ctx* ctx, Instance& I, int stage) {
         case EBIT_STAGE_RECONSTRUCT: reconstruct_full(I, st); break;
         case EBIT_STAGE_ADVECT_T:
             if (I.p.energy) {
-                launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, st);
+                launch_advect_T(I.g, I.p, I.flags, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, st);
                 count(1);
             }
             break;
@@ -786,7 +786,7 @@ static ebit_status capture_step(ebit_ctx* ctx, Instance& I, cudaStream_t st, cud
     I.solver.use_graph = 1;
     cudaStream_t s = st;
     if (I.p.energy) {
-        launch_advect_T(I.g, I.p, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, s);
+        launch_advect_T(I.g, I.p, I.flags, I.T_l, I.T_v, I.u_l, I.u_v, I.Ts_l, I.Ts_v, s);
         extend_T(I, I.Ts_l, I.Ts_v, s);
     }
     advance_interface(I, s);

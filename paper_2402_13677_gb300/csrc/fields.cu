@@ -61,22 +61,38 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
     return F[cidx(g, i, j)];
 }
 
-// WENO3 upwind derivative (undivided) from five values along a line. The Jiang-Shu weights
-// a0 = (1/3)/(eps + b0)^2 and a1 = (2/3)/(eps + b1)^2 are normalised after multiplying both
-// by 3 (eps + b0)^2 (eps + b1)^2, which leaves one division instead of three (FP64 division
-// is a multi-instruction sequence on this GPU).
-template <typename R>
-__device__ inline R weno3(R Tm2, R Tm1, R T0, R Tp1, R Tp2, bool upos) {
-    const R eps = R(1e-6);
-    R v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
-    R v2 = upos ? T0 - Tm1 : Tp1 - T0;
-    R v3 = upos ? Tp1 - T0 : T0 - Tm1;
-    R phi0 = R(0.5) * (R(3) * v2 - v1);
-    R phi1 = R(0.5) * (v2 + v3);
-    R s0 = eps + (v2 - v1) * (v2 - v1);
-    R s1 = eps + (v3 - v2) * (v3 - v2);
-    R q0 = s1 * s1, q1 = R(2) * (s0 * s0);
-    return (q0 * phi0 + q1 * phi1) / (q0 + q1);
+// Reciprocal of d > 0 to FP64 accuracy without an FP64 division: the FP32 reciprocal of d
+// (relative error below 2^-23) refined by two Newton-Raphson steps for f(r) = 1/r - d, each
+// r <- r + r (1 - d r) with the residual 1 - d r formed by one fused multiply-add, which doubles
+// the number of correct bits per step.  Outside the FP32 range the FP64 division is used.
+__device__ inline double recip_nr(double d) {
+    if (!(d > 1e-36 && d < 1e36)) return 1.0 / d;
+    double r = (double)__frcp_rn((float)d);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
+// WENO3 upwind derivative (undivided) from five values along a line (Jiang-Shu, linear weights
+// 1/3 and 2/3, smoothness indicators b0 = (v2 - v1)^2, b1 = (v3 - v2)^2, eps = 1e-6).  With the
+// undivided upwind differences v1, v2, v3 the two candidates are phi0 = (3 v2 - v1)/2 and
+// phi1 = (v2 + v3)/2, and the normalised weight of phi0 is
+//   w0 = (1/3)/(eps + b0)^2 / ((1/3)/(eps + b0)^2 + (2/3)/(eps + b1)^2)
+//      = (eps + b1)^2 / ((eps + b1)^2 + 2 (eps + b0)^2),
+// so the derivative is phi1 + w0 (phi0 - phi1) with phi0 - phi1 = ((v2 - v1) - (v3 - v2))/2:
+// the second differences serve both the indicators and the candidates' difference, and the one
+// reciprocal is recip_nr (the FP64 rate of this GPU is a small fraction of its FP32 rate).
+__device__ inline double weno3(double Tm2, double Tm1, double T0, double Tp1, double Tp2, bool upos) {
+    const double eps = 1e-6;
+    double v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
+    double v2 = upos ? T0 - Tm1 : Tp1 - T0;
+    double v3 = upos ? Tp1 - T0 : T0 - Tm1;
+    double a1 = v2 - v1, a2 = v3 - v2;
+    double s0 = fma(a1, a1, eps), s1 = fma(a2, a2, eps);
+    double q0 = s1 * s1;
+    double w0 = q0 * recip_nr(fma(s0 + s0, s0, q0));
+    return 0.5 * fma(w0, a1 - a2, v2 + v3);
 }
 
 // ---- tiled form: the values a 32 x 8 tile of cells reads (two halo layers, boundary
@@ -120,8 +136,8 @@ __device__ inline void tile_stage(const F* T, const Refl* R, const Grid& g, int 
 
 // T - dt/h (u . D T) at tile position (rx, ry) of the staged field v
 __device__ inline double tile_advect(const double (*v)[WSX], int rx, int ry, double2 u, double dth) {
-    double dx = weno3<double>(v[ry][rx - 2], v[ry][rx - 1], v[ry][rx], v[ry][rx + 1], v[ry][rx + 2], u.x >= 0.0);
-    double dy = weno3<double>(v[ry - 2][rx], v[ry - 1][rx], v[ry][rx], v[ry + 1][rx], v[ry + 2][rx], u.y >= 0.0);
+    double dx = weno3(v[ry][rx - 2], v[ry][rx - 1], v[ry][rx], v[ry][rx + 1], v[ry][rx + 2], u.x >= 0.0);
+    double dy = weno3(v[ry - 2][rx], v[ry - 1][rx], v[ry][rx], v[ry + 1][rx], v[ry + 2][rx], u.y >= 0.0);
     return v[ry][rx] - dth * (u.x * dx + u.y * dy);
 }
 
@@ -137,14 +153,18 @@ __host__ inline Refl velocity_refl(const Grid& g, int comp) {
     return r;
 }
 
-// S1: T*_k = T_k - dt u_k . grad T_k for both phases (block WX x WY threads, one cell each)
-__global__ void __launch_bounds__(WX * WY) k_advect_T(Grid g, Refl r, double dth, const double* __restrict__ T_l,
+// S1: T*_k = T_k - dt u_k . grad T_k on the cells of phase k (centre colours of the interface
+// before it moves); elsewhere T*_k = T_k (the other phase's band cells are refilled by the
+// extension, cells beyond the band are not read).  Block WX x WY threads, one cell each.
+__global__ void __launch_bounds__(WX * WY) k_advect_T(Grid g, Refl r, double dth, const uint8_t* __restrict__ flags,
+                                                     const double* __restrict__ T_l,
                                                      const double* __restrict__ T_v,
                                                      const double2* __restrict__ u_l,
                                                      const double2* __restrict__ u_v, double* __restrict__ Ts_l,
                                                      double* __restrict__ Ts_v) {
     if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
     const long long zo = zoff(g.zs);
+    flags = zsh(flags, zo);
     T_l = zsh(T_l, zo);
     T_v = zsh(T_v, zo);
     u_l = zsh(u_l, zo);
@@ -160,8 +180,14 @@ __global__ void __launch_bounds__(WX * WY) k_advect_T(Grid g, Refl r, double dth
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
     int c = cidx(g, i, j);
-    Ts_l[c] = tile_advect(sh[0], tx + WH, ty + WH, u_l[c], dth);
-    Ts_v[c] = tile_advect(sh[1], tx + WH, ty + WH, u_v[c], dth);
+    int sx = tx + WH, sy = ty + WH;
+    if (flags[c] & F_CCOL) {
+        Ts_l[c] = tile_advect(sh[0], sx, sy, u_l[c], dth);
+        Ts_v[c] = sh[1][sy][sx];
+    } else {
+        Ts_l[c] = sh[0][sy][sx];
+        Ts_v[c] = tile_advect(sh[1], sx, sy, u_v[c], dth);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -768,10 +794,10 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
 // host launchers
 // ---------------------------------------------------------------------------------
 
-void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
-                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st) {
+void launch_advect_T(const Grid& g, const Phys& p, const uint8_t* flags, const double* T_l, const double* T_v,
+                     const double2* u_l, const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st) {
     k_advect_T<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
-        g, temperature_refl(g), p.dt / g.h, T_l, T_v, u_l, u_v, Ts_l, Ts_v);
+        g, temperature_refl(g), p.dt / g.h, flags, T_l, T_v, u_l, u_v, Ts_l, Ts_v);
 }
 
 void launch_compact(const Grid& g, const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,

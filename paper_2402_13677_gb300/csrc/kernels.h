@@ -29,8 +29,8 @@ void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const 
 
 // fields.cu
 // f32w: WENO3 nonlinear weights in FP32 (mixed-precision mode)
-void launch_advect_T(const Grid& g, const Phys& p, const double* T_l, const double* T_v, const double2* u_l,
-                     const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st);
+void launch_advect_T(const Grid& g, const Phys& p, const uint8_t* flags, const double* T_l, const double* T_v,
+                     const double2* u_l, const double2* u_v, double* Ts_l, double* Ts_v, cudaStream_t st);
 void launch_compact(const Grid& g, const uint8_t* flags, int N, uint8_t mask, int* list, int* count, int* idxmap,
                     cudaStream_t st);
 void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,

@@ -188,8 +188,7 @@ def test_energy_advection_and_extension(dev, name):
         E.ebit_run_stage(ctx, E.STAGE_ADVECT_T)
         g = E.download(ctx, 0, st.pb.nx, st.pb.ny, ["Ts_l", "Ts_v"])
         pb = st.pb
-        Tl = OE.advect(st.T_l, st.u_l, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
-        Tv = OE.advect(st.T_v, st.u_v, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
+        Tl, Tv = OE.advect_phases(st.T_l, st.T_v, st.u_l, st.u_v, st.geom.ccol, pb.T_bc, pb.dt, pb.h)
         assert relerr(g["Ts_l"], Tl) < 1e-13 or np.max(np.abs(Tl)) == 0
         assert relerr(g["Ts_v"], Tv) < 1e-13
         E.ebit_run_stage(ctx, E.STAGE_EXTEND_TSTAR)
@@ -236,8 +235,7 @@ def test_energy_solve_flux_and_ghost_velocity(dev, name):
     pb = st.pb
     # oracle: run the step up to the energy solve (step counter 0 on both sides)
     so = st.copy()
-    Ts_l = OE.advect(so.T_l, so.u_l, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
-    Ts_v = OE.advect(so.T_v, so.u_v, OE.temperature_sides(pb.T_bc), pb.dt, pb.h)
+    Ts_l, Ts_v = OE.advect_phases(so.T_l, so.T_v, so.u_l, so.u_v, so.geom.ccol, pb.T_bc, pb.dt, pb.h)
     Ts_l, Ts_v = OE.extend_temperatures(Ts_l, Ts_v, so.geom, pb.extend_iters)
     so.nstep = 0
     S.advance_interface(so)

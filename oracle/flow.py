@@ -26,6 +26,17 @@ Readings (the paper gives Eqs. 11-15 only):
     the EBIT edge; mdot n at a face is the mean of its two cells;
   * the surface-tension, 2[mu du/dn] and -mdot^2 [1/rho] terms of the pressure
     jump are not imposed (the paper's projection changes only the RHS).
+
+One-fluid variant (Sec. 2.3, compared with the ghost-fluid method in Sec. 3): one velocity
+field (kept in both the liquid and the vapour arrays, which then stay equal), no ghost
+velocities, and the phase-change source of the pc-source equation added to the mass equation
+of the projection, div u_f^{n+1} = S_pc, nonzero in the cut cells only:
+  S_pc V = mdot S_Gamma (1/rho_v - 1/rho_l),
+with S_Gamma the length of the cell's segments (times the unit depth) and V = h^2.  Reading of
+the sign: the printed source is mdot S_Gamma [1/rho] / V with [.] = liquid - vapour; read with
+the normal from liquid into vapour (the orientation under which the jump conditions of Sec. 2.2
+hold with mdot > 0 for evaporation) the divergence of the velocity jump is (u_v - u_l) . n
+delta = mdot (1/rho_v - 1/rho_l) delta, i.e. evaporation creates volume.
 """
 from __future__ import annotations
 
@@ -34,6 +45,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .energy import advect, velocity_sides
+from .geometry import segment_data
 
 WALL, OUTFLOW, SYMMETRY = 0, 1, 2
 
@@ -52,6 +64,8 @@ def face_colours(vcol, hx_pos, vy_pos):
 # --------------------------------------------------------------------------
 def ghost_velocities(st):
     pb, g = st.pb, st.geom
+    if pb.one_fluid:       # one velocity field: no ghost values
+        return
     J = 1.0 / pb.rho_l - 1.0 / pb.rho_v
     mn = st.mdot[..., None] * g.nb                # mdot n per cell
     liq = (g.ccol == 1) & g.band
@@ -226,13 +240,26 @@ def poisson_rhs(pb, ccol, faces):
     return -pb.h * np.where(ccol == 1, div["l"], div["v"])
 
 
+def phase_change_source(pb, geom, mdot):
+    """h^2 S_pc per cell (one-fluid variant, pc-source equation): mdot S_Gamma (1/rho_v - 1/rho_l)
+    in the cut cells, S_Gamma = (length of the cell's segments in grid units) h."""
+    src = np.zeros((pb.ny, pb.nx))
+    jump = 1.0 / pb.rho_v - 1.0 / pb.rho_l
+    for (j, i), _, _, L in segment_data(geom):
+        src[j, i] += mdot[j, i] * L * pb.h * jump
+    return src
+
+
 def project(st, ustar, faces):
     """Solve the ghost-fluid Poisson equation, update faces (Eq. 14), accelerations and cells (Eq. 15)."""
     pb, g = st.pb, st.geom
     ny, nx = pb.ny, pb.nx
     rfx, rfy = face_rho(pb, g.vf)
     A = poisson_matrix(pb, rfx, rfy).tocsc()
-    b = poisson_rhs(pb, g.ccol, faces).ravel()
+    b = poisson_rhs(pb, g.ccol, faces)
+    if pb.one_fluid:       # div u_f^{n+1} = S_pc in the cut cells
+        b = b + phase_change_source(pb, g, st.mdot)
+    b = b.ravel()
     p = spla.spsolve(A, b).reshape(ny, nx)
     ax, ay = face_acceleration(pb, p, rfx, rfy)
     # face update: u_f^{n+1} = u_f* + dt (a_f - g) on faces the projection acts on

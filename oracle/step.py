@@ -65,6 +65,8 @@ def interface_mdot(st):
 def prepare(pb):
     """Initial state: reconstruction, ghost band of T, mdot, ghost velocities, initial accelerations."""
     st = State(pb)
+    if pb.one_fluid:       # one velocity field, held in both phase arrays
+        st.u_v, st.ufx_v, st.ufy_v = st.u_l.copy(), st.ufx_l.copy(), st.ufy_l.copy()
     st.geom = reconstruct(st.vcol, st.hx_pos, st.vy_pos)
     if pb.energy:
         st.T_l, st.T_v = energy.extend_temperatures(st.T_l, st.T_v, st.geom, pb.extend_iters)

@@ -70,6 +70,9 @@ class Problem:
     sweep_order: int = 1          # 0: always x then y; 1: alternate
     energy: bool = True           # False: mdot imposed (constant-mass-flux bubble)
     mdot_fixed: float = 0.0
+    one_fluid: bool = False       # True: one velocity field and the phase-change source S_pc
+                                  # (Sec. 2.2-2.3) instead of ghost velocities; the vapour
+                                  # velocity arrays then repeat the liquid ones
     # initial state (filled by the generators)
     vcol: np.ndarray = None
     hx_cut: np.ndarray = None
@@ -368,6 +371,25 @@ def film(nx=1024, ny=2048, Lx=1.0, mean=0.05, amp=0.005, modes=None, seed=0,
     pb.T_l = np.zeros((ny, nx))
     _zero_flow(pb)
     return pb
+
+
+def one_fluid(pb: Problem) -> Problem:
+    """The same problem for the one-fluid variant (Sec. 2.3): one velocity field, composed from
+    the generator's two phase fields -- the liquid field in cells whose corners are mostly
+    liquid, the vapour field elsewhere; faces take the liquid field when both end vertices are
+    liquid.  Only the initial single field is composed here; the method's arithmetic is not."""
+    q = pb.copy()
+    q.one_fluid = True
+    q.name = pb.name + "_one_fluid"
+    vc = q.vcol.astype(float)
+    cc = (vc[:-1, :-1] + vc[:-1, 1:] + vc[1:, :-1] + vc[1:, 1:]) > 2.0
+    q.u_l = np.where(cc[..., None], pb.u_l, pb.u_v)
+    fx = (vc[:-1, :] + vc[1:, :]) > 1.5          # x-faces: both end vertices liquid
+    fy = (vc[:, :-1] + vc[:, 1:]) > 1.5
+    q.ufx_l = np.where(fx, pb.ufx_l, pb.ufx_v)
+    q.ufy_l = np.where(fy, pb.ufy_l, pb.ufy_v)
+    q.u_v, q.ufx_v, q.ufy_v = q.u_l.copy(), q.ufx_l.copy(), q.ufy_l.copy()
+    return q
 
 
 def c1_stefan(**kw):

@@ -16,7 +16,9 @@
   * momentum predictor: a shear mode decays by the exact discrete backward-Euler factor
     (symmetry planes and no-slip walls, both components); the two-layer Poiseuille profile
     is approached as the grid is refined; the two-layer step is mirror-symmetric; WENO3
-    momentum advection is exact for quadratic velocity fields.
+    momentum advection is exact for quadratic velocity fields;
+  * one-fluid variant: the Stefan outflow velocity is the velocity jump mdot (1/rho_v - 1/rho_l);
+    its cell velocity oscillates across the interface where the ghost-fluid one does not.
 """
 import math
 
@@ -518,3 +520,47 @@ def test_predictor_advection_exact_for_quadratic_velocity():
     # the vapour field -u advects itself with -u: -(u - dt (u . grad) u) in its own frame
     exv = -ux - dt * (ux * dux[0] + uy * dux[1])
     assert np.max(np.abs(ustar["v"][..., 0][inner] - exv[inner])) < 1e-13
+
+
+# ------------------------------------------------------------------ one-fluid variant
+def _stefan_steps(one_fluid, n=64, steps=5):
+    pb = w.stefan(n, 4, X0=0.2, Lx=1.0, dt=2e-4, steps=0)
+    if one_fluid:
+        pb = w.one_fluid(pb)
+    st = S.prepare(pb)
+    for _ in range(steps):
+        S.step(st)
+    return pb, st
+
+
+def test_one_fluid_stefan_outflow_velocity_is_the_velocity_jump():
+    """One-fluid variant (pc-source equation in the mass equation of the projection): in the 1D
+    Stefan problem the vapour is at rest on the wall, so the liquid leaves through the outflow at
+    the velocity jump of the velocity-jump equation, [u] . n = mdot [1/rho], i.e.
+    u_liq = mdot (1/rho_v - 1/rho_l) -- an equation the source term is not written from.  A
+    source with the printed sign (liquid minus vapour) drives the liquid the wrong way."""
+    pb, st = _stefan_steps(True)
+    cut = st.geom.nseg > 0
+    mdot = st.mdot[cut]
+    assert np.ptp(mdot) < 1e-12 * abs(mdot.mean())          # one front, one mass flux
+    expected = mdot.mean() * (1.0 / pb.rho_v - 1.0 / pb.rho_l)
+    assert expected > 0
+    assert np.allclose(st.ufx_l[:, -1], expected, rtol=1e-12)
+    assert np.array_equal(st.u_l, st.u_v)                     # one velocity field
+
+
+def test_one_fluid_cell_velocity_oscillates_ghost_fluid_does_not():
+    """The paper's comparison of the two variants on the Stefan problem (Sec. 3.1): the cell
+    velocity of the one-fluid method, only approximately projected, oscillates across the
+    interface, while the ghost-fluid method's liquid velocity stays smooth (and carries the
+    jump in its ghost values)."""
+    spans = {}
+    for one in (False, True):
+        pb, st = _stefan_steps(one)
+        far = st.ufx_l[2, -1]
+        row = st.u_l[2, :, 0]
+        i0 = int(np.argmax(st.geom.nseg[2] > 0))
+        near = row[i0 - 4:i0 + 5]
+        spans[one] = (np.max(near) - far) / far, np.min(near) / far
+    assert spans[False][0] < 0.01 and spans[False][1] > 0.98     # ghost fluid: within 1 % of the plateau
+    assert spans[True][0] > 0.2 and spans[True][1] < 0.0          # one fluid: over- and undershoot

@@ -38,6 +38,8 @@ import numpy as np
 
 WORKLOADS = {
     "c2_bubble_512": dict(kind="c2", desc="2D planar vapour bubble in superheated liquid, 512x512"),
+    "c2_bubble_512_one_fluid": dict(kind="c2of", desc="the 512x512 bubble with the one-fluid variant (one velocity "
+                                                     "field, phase-change source in the projection)"),
     "c3_film_1024x2048": dict(kind="c3", desc="2D film boiling over a heated wall, 1024x2048"),
     "c5_film_4096": dict(kind="c5", desc="multi-mode 2D film boiling, 4096x4096"),
     # profiling case: the 4096x4096 film's cell size and physics on half its width (16 modes),
@@ -67,6 +69,8 @@ def make_problems(name, count=None):
         return w.c4_batch(count if count is not None else (BATCH_COUNT or 4096))
     if kind == "c2":
         return [w.c2_bubble(steps=0)]
+    if kind == "c2of":
+        return [w.one_fluid(w.c2_bubble(steps=0))]
     if kind == "c3":
         return [w.c3_film(steps=0)]
     if kind == "c5h":
@@ -521,7 +525,7 @@ def main():
     ap.add_argument("--profile-only", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels from the host (profilers)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
-    ap.add_argument("--extra", default="c3_film_1024x2048,c5_film_4096",
+    ap.add_argument("--extra", default="c2_bubble_512_one_fluid,c3_film_1024x2048,c5_film_4096",
                     help="further workloads measured in the same run (sub-objects of the line; '' for none)")
     ap.add_argument("--extra-steps", type=int, default=5)
     ap.add_argument("--extra-warmup", type=int, default=3)

@@ -94,6 +94,12 @@ typedef struct {
     int sweep_order;          /* 0: x then y every step; 1: alternate x-y / y-x             */
     int energy;               /* 1: solve the energy equation; 0: impose mdot_fixed (Sec. 3.3) */
     double mdot_fixed;
+    int one_fluid;            /* 0: ghost-fluid method (ghost-velocity equation, two velocity
+                                 fields); 1: one-fluid variant (Sec. 2.3): one velocity field
+                                 (the vapour arrays repeat the liquid ones; set the liquid ones),
+                                 no ghost velocities, and the phase-change source of the
+                                 pc-source equation in the projection, div u_f = S_pc with
+                                 S_pc V = mdot S_Gamma (1/rho_v - 1/rho_l) in the cut cells     */
 } ebit_config;
 
 typedef struct { double rho, mu, lambda, cp; } ebit_phase_props;

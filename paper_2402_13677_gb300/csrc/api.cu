@@ -271,6 +271,7 @@ static void mass_flux(Instance& I, cudaStream_t st) {
 }
 
 static void ghost_velocity(Instance& I, cudaStream_t st) {
+    if (I.p.one_fluid) return;   // one velocity field: no ghost values
     launch_ghost_velocity(I.g, I.p, I.flags, I.mdot, I.nb, I.vcol, I.hpos, I.vpos, I.u_l, I.u_v, I.ufx_l, I.ufx_v,
                           I.ufy_l, I.ufy_v, st);
     count(2);
@@ -392,8 +393,8 @@ static void momentum(Instance& I, cudaStream_t st) {
     launch_ustar(I.g, I.p, I.vxx, I.vxy, I.gc, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
     count(2);
     // S12: projection
-    launch_poisson_operator(I.g, I.p, I.vf, I.flags, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, I.op_cd, I.op_dd, I.op_wl,
-                            I.op_wb, I.op_b, st);
+    launch_poisson_operator(I.g, I.p, I.vf, I.flags, I.cseg, I.hpos, I.vpos, I.mdot, I.ufx_l, I.ufx_v, I.ufy_l,
+                            I.ufy_v, I.op_cd, I.op_dd, I.op_wl, I.op_wb, I.op_b, st);
     count(1);
     do_solve(I, SLOT_POISSON, I.op_b, I.P, 1, st);
     launch_project(I.g, I.p, I.P, I.vf, I.op_wl, I.op_wb, I.face_ax, I.face_ay, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v,
@@ -409,6 +410,12 @@ static void diagnostics(Instance& I, cudaStream_t st) {
 }
 
 static void prepare(Instance& I, cudaStream_t st) {
+    if (I.p.one_fluid) {   // the one velocity field is the liquid one; the vapour arrays repeat it
+        size_t N = (size_t)I.g.nx * I.g.ny, nfx = (size_t)I.g.ny * (I.g.nx + 1), nfy = (size_t)(I.g.ny + 1) * I.g.nx;
+        cudaMemcpyAsync(I.u_v, I.u_l, N * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(I.ufx_v, I.ufx_l, nfx * 8, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(I.ufy_v, I.ufy_l, nfy * 8, cudaMemcpyDeviceToDevice, st);
+    }
     reconstruct_full(I, st);
     if (I.p.energy) extend_T(I, I.T_l, I.T_v, st);
     mass_flux(I, st);
@@ -493,7 +500,7 @@ static bool batchable(const ebit_config& a, const ebit_config& b) {
         if (a.bc[s] != b.bc[s] || a.T_fixed[s] != b.T_fixed[s] || a.T_wall[s] != b.T_wall[s]) return false;
     return a.precision == b.precision && a.rtol == b.rtol && a.max_iter == b.max_iter &&
            a.extend_iters == b.extend_iters && a.theta_min == b.theta_min && a.sweep_order == b.sweep_order &&
-           a.energy == b.energy && a.mdot_fixed == b.mdot_fixed;
+           a.energy == b.energy && a.mdot_fixed == b.mdot_fixed && a.one_fluid == b.one_fluid;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -532,7 +539,7 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         }
         std::memset(&I.p, 0, sizeof(I.p));
         I.p.dt = c.dt; I.p.theta_min = c.theta_min; I.p.extend_iters = c.extend_iters;
-        I.p.energy = c.energy; I.p.mdot_fixed = c.mdot_fixed;
+        I.p.energy = c.energy; I.p.mdot_fixed = c.mdot_fixed; I.p.one_fluid = c.one_fluid ? 1 : 0;
         phys_derive(I.p);
     }
     // group instances that can share batched launches (same grid, boundaries and solver settings)

@@ -27,6 +27,7 @@ struct Phys {
     double dt, theta_min;
     int extend_iters, energy;
     double mdot_fixed;
+    int one_fluid;    // one velocity field and the phase-change source (no ghost velocities)
     // derived on the host (phys_derive) whenever the above change: 1 / dt and the liquid-minus-
     // vapour differences of density and viscosity (mixtures as one fused multiply-add)
     double inv_dt, drho, dmu;

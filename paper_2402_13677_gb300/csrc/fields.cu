@@ -542,7 +542,35 @@ __device__ inline double face_vf_y(const Grid& g, const double* vf, int i, int j
 
 // Poisson operator: wl/wb = dt / rho_f (interior faces), dd = 2 dt / rho_f on outflow faces,
 // b = -h * (undivided divergence of the face field of the cell's phase); x0 = p
+// length (grid units) of the segments of a cut cell, from its segment table and the markers
+__device__ inline double segments_length(const Grid& g, const uint16_t* cseg, const double* hpos,
+                                         const double* vpos, int i, int j) {
+    uint16_t code = cseg[cidx(g, i, j)];
+    int ns = code & 3;
+    double L = 0.0;
+    for (int q = 0; q < ns; ++q) {
+        int k[2] = {(code >> (2 + 4 * q)) & 3, (code >> (4 + 4 * q)) & 3};
+        double2 m[2];
+        for (int e = 0; e < 2; ++e) {
+            switch (k[e]) {
+                case 0: m[e] = make_double2(hpos[hidx(g, i, j)], 0.0); break;
+                case 1: m[e] = make_double2(1.0, vpos[veidx(g, i + 1, j)]); break;
+                case 2: m[e] = make_double2(hpos[hidx(g, i, j + 1)], 1.0); break;
+                default: m[e] = make_double2(0.0, vpos[veidx(g, i, j)]); break;
+            }
+        }
+        double dx = m[1].x - m[0].x, dy = m[1].y - m[0].y;
+        L += sqrt(dx * dx + dy * dy);
+    }
+    return L;
+}
+
+// ghost-fluid Poisson operator (face weights dt / rho_f, outflow faces Dirichlet p = 0) and its
+// right-hand side -h div u_f* of each cell's phase; in the one-fluid variant the single field's
+// divergence plus h^2 S_pc = mdot S_Gamma (1/rho_v - 1/rho_l) in the cut cells
 __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf, const uint8_t* __restrict__ flags,
+                                   const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                                   const double* __restrict__ vpos, const double* __restrict__ mdot,
                                    const double* __restrict__ fx_l, const double* __restrict__ fx_v,
                                    const double* __restrict__ fy_l, const double* __restrict__ fy_v,
                                    double* __restrict__ cd, double* __restrict__ dd, double* __restrict__ wl,
@@ -551,6 +579,10 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     const long long zo = zoff(g.zs);
     vf = zsh(vf, zo);
     flags = zsh(flags, zo);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    mdot = zsh(mdot, zo);
     fx_l = zsh(fx_l, zo);
     fx_v = zsh(fx_v, zo);
     fy_l = zsh(fy_l, zo);
@@ -576,7 +608,10 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     const double* fx = (flags[c] & F_CCOL) ? fx_l : fx_v;
     const double* fy = (flags[c] & F_CCOL) ? fy_l : fy_v;
     double div = (fx[veidx(g, i + 1, j)] - fx[veidx(g, i, j)]) + (fy[hidx(g, i, j + 1)] - fy[hidx(g, i, j)]);
-    b[c] = -g.h * div;
+    double rhs = -g.h * div;
+    if (p.one_fluid && (flags[c] & F_CUT))
+        rhs += mdot[c] * segments_length(g, cseg, hpos, vpos, i, j) * g.h * (1.0 / p.rho_v - 1.0 / p.rho_l);
+    b[c] = rhs;
 }
 
 // face accelerations a_f = g - grad_f p / rho_f (0 on walls and symmetry planes); on interior
@@ -875,10 +910,11 @@ void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2
 }
 
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
+                             const uint16_t* cseg, const double* hpos, const double* vpos, const double* mdot,
                              const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
                              double* cd, double* dd, double* wl, double* wb, double* b, cudaStream_t st) {
-    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, fx_l, fx_v, fy_l, fy_v,
-                                                                         cd, dd, wl, wb, b);
+    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, cseg, hpos, vpos, mdot,
+                                                                         fx_l, fx_v, fy_l, fy_v, cd, dd, wl, wb, b);
 }
 
 void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl_p,

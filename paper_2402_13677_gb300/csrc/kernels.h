@@ -52,9 +52,10 @@ void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
                   double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
                   cudaStream_t st);
-void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags, const double* fx_l,
-                             const double* fx_v, const double* fy_l, const double* fy_v, double* cd, double* dd,
-                             double* wl, double* wb, double* b, cudaStream_t st);
+void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
+                             const uint16_t* cseg, const double* hpos, const double* vpos, const double* mdot,
+                             const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
+                             double* cd, double* dd, double* wl, double* wb, double* b, cudaStream_t st);
 // ax/ay: face-acceleration scratch (x-faces ny*(nx+1), y-faces (ny+1)*nx); face velocities
 // are updated when fx_l != null
 // wl_p / wb_p: the Poisson operator's face weights dt / rho_f of the same volume fractions (they

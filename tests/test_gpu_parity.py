@@ -123,6 +123,10 @@ def cases():
             mdot=0.5, cfl=0.1, name="saddle"),
         "outflow": lambda: w.const_mdot_levelset(lambda x, y: np.hypot(x - 0.9, y - 0.47) - 0.17, n=48, mdot=1.0,
                                                  cfl=0.2, name="outflow"),
+        # the one-fluid variant (single velocity field, phase-change source in the projection)
+        "stefan_1f": lambda: w.one_fluid(w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0)),
+        "bubble_1f": lambda: w.one_fluid(w.bubble(n=64, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01,
+                                                  dt=1e-4, steps=0)),
     }
 
 
@@ -296,7 +300,7 @@ def test_full_step_fp64(dev, name):
         E.ebit_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["stefan", "bubble"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "stefan_1f", "bubble_1f"])
 def test_several_steps_track_the_oracle(dev, name):
     st = prepared(name, 0)
     ctx = gpu_ctx(dev, st)

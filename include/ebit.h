@@ -194,10 +194,17 @@ ebit_status ebit_run_stage(ebit_ctx* ctx, int stage);
 /* Advance every instance by nsteps time steps (ebit_run_stage(PREPARE) must have run). */
 ebit_status ebit_step(ebit_ctx* ctx, int nsteps);
 
-/* Diagnostics of the last step of instance `inst` (Sec. 3): up to n doubles of
- * { t, vapour volume, volume expected from sum mdot S dt / rho_v in the step, M_d,
- *   outlet mass in the step, cut cells, solver iterations (energy, viscous, Poisson),
- *   final relative residuals (energy, viscous, Poisson) }. Synchronises. */
+/* Diagnostics of the last step of instance `inst` (Sec. 3): up to n (<= 14) doubles of
+ * { t, vapour volume, volume expected from sum mdot S dt / rho_v in the step, M_d (mass-in-
+ *   domain equation), outlet mass in the step (mass-with-outflow equation), cut cells,
+ *   solver iterations (energy, viscous, Poisson), final relative residuals (energy, viscous,
+ *   Poisson), vapour volume that left through the outflow faces in the step (the V_bc of the
+ *   film-boiling vapour volume, Sec. 3.7: (1 - H) u_f . n h dt over the outflow faces, H the
+ *   boundary cell's volume fraction, u_f the face velocity of its phase), space-averaged
+ *   Nusselt number of the fixed-temperature walls (Sec. 3.7: l / (T_w - T_sat) times the mean
+ *   of 2 (T_w - T_i) / h over their faces, T_i the boundary cell's temperature of its phase,
+ *   l = sqrt(sigma / (|rho_l - rho_v| |g|)) when sigma and g are nonzero, else 1) }.
+ * Synchronises. */
 ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n);
 
 /* Kernel launches issued since the context was created (all instances). */

@@ -11,7 +11,19 @@ One time step, in the paper's order (Sec. 2.5):
   5. mass and momentum: predictor (S11) and ghost-fluid projection (S12).
 Diagnostics (S13): vapour volume, the volume the mass flux should have added,
 M_d (mass-in-domain equation) and the outlet mass of M_c (mass-with-outflow
-equation).
+equation); for film boiling (Sec. 3.7) the vapour volume that left through the
+outflow boundaries (the V_bc of the dimensionless vapour volume) and the
+space-averaged Nusselt number of the heated wall.
+
+Readings of the two film-boiling quantities (the paper gives the integrals only):
+  * V_bc per step: over the outflow boundary faces, (1 - H) u_f . n h dt with H
+    the boundary cell's liquid volume fraction and u_f the face velocity of the
+    cell's phase (the same faces and velocities as the outlet mass of M_c);
+  * Nu = (l / (T_w - T_sat)) times the mean over the faces of the walls with a
+    fixed temperature of -dT/dn at the wall, dT/dn from the cell and its ghost
+    value 2 T_w - T_i, i.e. 2 (T_w - T_i) / h, T_i of the cell's phase; the
+    length l is the paper's sqrt(sigma / ((rho_l - rho_v) |g|)) when sigma and g
+    are nonzero, else 1 (the mean wall gradient over the wall superheat).
 """
 from __future__ import annotations
 
@@ -120,8 +132,16 @@ def step(st):
     return row
 
 
+def nusselt_length(pb):
+    g = math.hypot(pb.gx, pb.gy)
+    if pb.sigma > 0.0 and g > 0.0 and pb.rho_l != pb.rho_v:
+        return math.sqrt(pb.sigma / (abs(pb.rho_l - pb.rho_v) * g))
+    return 1.0
+
+
 def diagnostics(st):
-    """[t, vapour volume, dV expected from mdot this step, M_d, outlet mass this step, cut cells]."""
+    """[t, vapour volume, dV expected from mdot this step, M_d, outlet mass this step, cut cells,
+    vapour volume out of the outflow boundaries this step, wall Nusselt number]."""
     pb, g = st.pb, st.geom
     h2 = pb.h * pb.h
     Vv = float(np.sum(1.0 - g.vf)) * h2
@@ -149,7 +169,29 @@ def diagnostics(st):
             u = np.where(ccol[-1, :] == 1, st.ufy_l[-1, :], st.ufy_v[-1, :])
             out += float(np.sum(rho_c[-1, :] * u))
     out *= pb.h * pb.dt
-    return np.array([st.t, Vv, dV, Md, out, float(np.count_nonzero(g.nseg))])
+    # vapour volume through the outflow faces, and the heat flux of the fixed-temperature walls
+    vout, flux, nf = 0.0, 0.0, 0
+    for s, kind in enumerate(pb.bc):
+        cells = {0: (slice(None), 0), 1: (slice(None), -1), 2: (0, slice(None)), 3: (-1, slice(None))}[s]
+        liq = ccol[cells] == 1
+        if kind == flow.OUTFLOW:
+            if s < 2:
+                u = np.where(liq, st.ufx_l[:, 0 if s == 0 else -1], st.ufx_v[:, 0 if s == 0 else -1])
+            else:
+                u = np.where(liq, st.ufy_l[0 if s == 2 else -1, :], st.ufy_v[0 if s == 2 else -1, :])
+            sign = -1.0 if s in (0, 2) else 1.0
+            vout += float(np.sum((1.0 - g.vf[cells]) * sign * u))
+        if pb.T_bc[s] is not None and kind == flow.WALL:
+            Tw = float(pb.T_bc[s])
+            Ti = np.where(liq, st.T_l[cells], st.T_v[cells])
+            flux += float(np.sum(2.0 * (Tw - Ti) / pb.h))
+            nf += Ti.size
+    vout *= pb.h * pb.dt
+    nu = 0.0
+    if nf:
+        Tw = next(float(v) for s, v in enumerate(pb.T_bc) if v is not None and pb.bc[s] == flow.WALL)
+        nu = nusselt_length(pb) / (Tw - pb.T_sat) * flux / nf if Tw != pb.T_sat else 0.0
+    return np.array([st.t, Vv, dV, Md, out, float(np.count_nonzero(g.nseg)), vout, nu])
 
 
 def run(pb, steps=None):

@@ -404,7 +404,7 @@ static void momentum(Instance& I, cudaStream_t st) {
 
 static void diagnostics(Instance& I, cudaStream_t st) {
     launch_diagnostics(I.g, I.p, I.vf, I.cseg, I.hpos, I.vpos, I.mdot, I.flags, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v,
-                       I.diag_partial, I.diag_ticket, I.clock, I.diag_out, st);
+                       I.T_l, I.T_v, I.diag_partial, I.diag_ticket, I.clock, I.diag_out, st);
     count(1);
     I.nstep += 1;
 }
@@ -621,7 +621,7 @@ ebit_status ebit_set_phase_props(ebit_ctx* ctx, int inst, const ebit_phase_props
     p.rho_l = liq->rho; p.mu_l = liq->mu; p.lam_l = liq->lambda; p.cp_l = liq->cp;
     p.rho_v = vap->rho; p.mu_v = vap->mu; p.lam_v = vap->lambda; p.cp_v = vap->cp;
     phys_derive(p);
-    p.T_sat = T_sat; p.h_lg = h_lg; p.gx = gx; p.gy = gy;
+    p.T_sat = T_sat; p.h_lg = h_lg; p.gx = gx; p.gy = gy; p.sigma = sigma;
     ctx->inst[inst].props_set = true;
     return EBIT_OK;
 }
@@ -1135,12 +1135,15 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
 ebit_status ebit_get_diagnostics(ebit_ctx* ctx, int inst, double* dst, int n) {
     if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !dst || n < 0) return EBIT_EINVAL;
     Instance& I = ctx->inst[inst];
-    double d[12];
-    cudaMemcpyAsync(d, I.diag_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    double d[14], o[8];
+    cudaMemcpyAsync(o, I.diag_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     cudaError_t er = cudaStreamSynchronize(ctx->stream);
     if (er != cudaSuccess) return fail(ctx, EBIT_ECUDA, cudaGetErrorString(er));
+    for (int k = 0; k < 6; ++k) d[k] = o[k];
     for (int k = 0; k < 6; ++k) d[6 + k] = I.stats[k];
-    for (int k = 0; k < n && k < 12; ++k) dst[k] = d[k];
+    d[12] = o[6];
+    d[13] = o[7];
+    for (int k = 0; k < n && k < 14; ++k) dst[k] = d[k];
     return EBIT_OK;
 }
 

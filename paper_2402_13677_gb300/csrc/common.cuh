@@ -24,6 +24,7 @@ constexpr uint8_t F_CUT = 4;    // cell holds interface segments
 struct Phys {
     double rho_l, rho_v, mu_l, mu_v, lam_l, lam_v, cp_l, cp_v;
     double T_sat, h_lg, gx, gy;
+    double sigma;     // surface tension coefficient
     double dt, theta_min;
     int extend_iters, energy;
     double mdot_fixed;

@@ -736,18 +736,29 @@ __device__ inline double block_sum(double v, double* sh) {
     return r;   // valid in thread 0
 }
 
-constexpr int NDIAG_SUMS = 5;
+constexpr int NDIAG_SUMS = 8;
 
+// S13 and the film-boiling quantities of Sec. 3.7, one reduction over the cells:
+//   s0 vapour area, s1 sum mdot S_Gamma, s2 sum rho_c, s3 outlet mass flux (mass-with-outflow
+//   equation), s4 cut cells, s5 vapour volume flux through the outflow faces ((1 - H) u_f . n
+//   with the face velocity of the boundary cell's phase), s6 wall heat flux 2 (T_w - T_i) / h
+//   summed over the faces of fixed-temperature walls, s7 the number of those faces.
+// out: t, vapour volume, dV expected from mdot, M_d, outlet mass, cut cells, vapour volume out,
+// wall Nusselt number (l / (T_w - T_sat)) * mean wall flux, l = sqrt(sigma / (|drho| |g|)) when
+// sigma and g are nonzero, else 1.
 __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, const uint16_t* __restrict__ cseg,
                               const double* __restrict__ hpos, const double* __restrict__ vpos,
                               const double* __restrict__ mdot, const uint8_t* __restrict__ flags,
                               const double* __restrict__ fx_l, const double* __restrict__ fx_v,
                               const double* __restrict__ fy_l, const double* __restrict__ fy_v,
+                              const double* __restrict__ T_l, const double* __restrict__ T_v,
                               double* __restrict__ partial, unsigned* __restrict__ ticket, double* __restrict__ clock,
                               double* __restrict__ out) {
     zphys(g, p);
     const long long zo = zoff(g.zs);
     vf = zsh(vf, zo);
+    T_l = zsh(T_l, zo);
+    T_v = zsh(T_v, zo);
     cseg = zsh(cseg, zo);
     hpos = zsh(hpos, zo);
     vpos = zsh(vpos, zo);
@@ -763,7 +774,7 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
     out = zsh(out, zo);
     __shared__ double sh[32];
     __shared__ bool lastblk;
-    double s[NDIAG_SUMS] = {0, 0, 0, 0, 0};
+    double s[NDIAG_SUMS] = {0, 0, 0, 0, 0, 0, 0, 0};
     int N = g.nx * g.ny;
     for (CellWalk cw(g.nx); cw.c < N; cw.next()) {
         int c = cw.c, i = cw.i, j = cw.j;
@@ -791,10 +802,24 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
             }
         }
         bool liq = flags[c] & F_CCOL;
-        if (i == 0 && g.bc[0] == BC_OUTFLOW) s[3] += -rc * (liq ? fx_l : fx_v)[veidx(g, 0, j)];
-        if (i == g.nx - 1 && g.bc[1] == BC_OUTFLOW) s[3] += rc * (liq ? fx_l : fx_v)[veidx(g, g.nx, j)];
-        if (j == 0 && g.bc[2] == BC_OUTFLOW) s[3] += -rc * (liq ? fy_l : fy_v)[hidx(g, i, 0)];
-        if (j == g.ny - 1 && g.bc[3] == BC_OUTFLOW) s[3] += rc * (liq ? fy_l : fy_v)[hidx(g, i, g.ny)];
+        if (i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1) {
+            // boundary faces of this cell: outflow (mass and vapour volume) and fixed-T walls
+            for (int sd = 0; sd < 4; ++sd) {
+                bool on = sd == 0 ? i == 0 : sd == 1 ? i == g.nx - 1 : sd == 2 ? j == 0 : j == g.ny - 1;
+                if (!on) continue;
+                if (g.bc[sd] == BC_OUTFLOW) {
+                    double u = sd < 2 ? (liq ? fx_l : fx_v)[veidx(g, sd == 0 ? 0 : g.nx, j)]
+                                      : (liq ? fy_l : fy_v)[hidx(g, i, sd == 2 ? 0 : g.ny)];
+                    double un = (sd == 0 || sd == 2) ? -u : u;
+                    s[3] += rc * un;
+                    s[5] += (1.0 - v) * un;
+                }
+                if (g.bc[sd] == BC_WALL && g.Tfix[sd]) {
+                    s[6] += 2.0 * (g.Tw[sd] - (liq ? T_l : T_v)[c]) * g.inv_h;
+                    s[7] += 1.0;
+                }
+            }
+        }
     }
     for (int q = 0; q < NDIAG_SUMS; ++q) {
         double r = block_sum(s[q], sh);
@@ -821,6 +846,17 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
         out[3] = s[2] * h2;
         out[4] = s[3] * g.h * p.dt;
         out[5] = s[4];
+        out[6] = s[5] * g.h * p.dt;
+        double nu = 0.0;
+        if (s[7] > 0.0) {
+            double Tw = 0.0;
+            for (int sd = 3; sd >= 0; --sd)
+                if (g.bc[sd] == BC_WALL && g.Tfix[sd]) Tw = g.Tw[sd];   // the first fixed-T wall
+            double gm = sqrt(p.gx * p.gx + p.gy * p.gy), dr = fabs(p.rho_l - p.rho_v);
+            double ell = (p.sigma > 0.0 && gm > 0.0 && dr > 0.0) ? sqrt(p.sigma / (dr * gm)) : 1.0;
+            if (Tw != p.T_sat) nu = ell / (Tw - p.T_sat) * s[6] / s[7];
+        }
+        out[7] = nu;
         *ticket = 0u;
     }
 }
@@ -935,10 +971,11 @@ int diag_blocks(const Grid& g) {
 
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
-                        const double* fx_v, const double* fy_l, const double* fy_v, double* partial,
-                        unsigned* ticket, double* clock, double* out, cudaStream_t st) {
+                        const double* fx_v, const double* fy_l, const double* fy_v, const double* T_l,
+                        const double* T_v, double* partial, unsigned* ticket, double* clock, double* out,
+                        cudaStream_t st) {
     k_diagnostics<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v,
-                                                                 fy_l, fy_v, partial, ticket, clock, out);
+                                                                 fy_l, fy_v, T_l, T_v, partial, ticket, clock, out);
 }
 
 }  // namespace ebit

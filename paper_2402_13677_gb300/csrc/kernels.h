@@ -67,7 +67,8 @@ void launch_project(const Grid& g, const Phys& p, const double* P, const double*
 int diag_blocks(const Grid& g);
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,
-                        const double* fx_v, const double* fy_l, const double* fy_v, double* partial, unsigned* ticket,
-                        double* clock, double* out, cudaStream_t st);
+                        const double* fx_v, const double* fy_l, const double* fy_v, const double* T_l,
+                        const double* T_v, double* partial, unsigned* ticket, double* clock, double* out,
+                        cudaStream_t st);
 
 }  // namespace ebit

@@ -245,7 +245,7 @@ def ebit_step(ctx, nsteps, allow_noconv=False):
     return _check(ctx, s)
 
 
-def ebit_get_diagnostics(ctx, inst, n=12):
+def ebit_get_diagnostics(ctx, inst, n=14):
     buf = (C.c_double * n)()
     _check(ctx, load().ebit_get_diagnostics(ctx, inst, buf, n))
     return np.array(buf[:])
@@ -355,7 +355,7 @@ STATE_FIELDS = {"T_l": F_T_L, "T_v": F_T_V, "u_l": F_U_L, "u_v": F_U_V, "ufx_l":
 def upload_state(ctx, inst, pb, vcol, hx_pos, vy_pos, fields, t):
     """Interface + every field given in `fields` (name -> array), properties and time."""
     liq, vap = props_from_problem(pb)
-    ebit_set_phase_props(ctx, inst, liq, vap, pb.T_sat, pb.h_lg, 0.0, pb.gx, pb.gy)
+    ebit_set_phase_props(ctx, inst, liq, vap, pb.T_sat, pb.h_lg, getattr(pb, "sigma", 0.0), pb.gx, pb.gy)
     ebit_set_interface(ctx, inst, vcol, hx_pos, vy_pos)
     for name, arr in fields.items():
         if arr is not None:

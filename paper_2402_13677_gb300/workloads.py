@@ -60,6 +60,7 @@ class Problem:
     cp_v: float = 1.0
     T_sat: float = 0.0
     h_lg: float = 1.0
+    sigma: float = 0.0            # surface tension coefficient
     gx: float = 0.0
     gy: float = 0.0
     bc: tuple = (WALL, OUTFLOW, SYMMETRY, SYMMETRY)

@@ -296,6 +296,8 @@ def test_full_step_fp64(dev, name):
         for q in (1, 2, 3, 4):
             assert abs(d[q] - row[q]) <= 1e-9 * max(abs(row[q]), 1e-6 * scale[q]), q
         assert d[5] == row[5]
+        assert abs(d[12] - row[6]) <= 1e-9 * max(abs(row[6]), 1e-6 * scale[4] / pb.rho_l)   # vapour out
+        assert abs(d[13] - row[7]) <= 1e-9 * max(abs(row[7]), 1e-12), (d[13], row[7])      # wall Nusselt
     finally:
         E.ebit_destroy(ctx)
 

@@ -564,3 +564,45 @@ def test_one_fluid_cell_velocity_oscillates_ghost_fluid_does_not():
         spans[one] = (np.max(near) - far) / far, np.min(near) / far
     assert spans[False][0] < 0.01 and spans[False][1] > 0.98     # ghost fluid: within 1 % of the plateau
     assert spans[True][0] > 0.2 and spans[True][1] < 0.0          # one fluid: over- and undershoot
+
+
+# ------------------------------------------------------------------ film-boiling diagnostics
+def test_nusselt_of_a_flat_film_with_a_linear_profile():
+    """Sec. 3.7's space-averaged Nusselt number: a flat vapour film of thickness delta whose
+    temperature falls linearly from the wall's T_w to T_sat at the interface conducts
+    (T_w - T_sat) / delta, so Nu = l / delta with l = sqrt(sigma / ((rho_l - rho_v) g)); the
+    wall gradient from the ghost value 2 T_w - T_i is exact for a linear profile."""
+    delta = 0.2
+    pb = w.film(32, 64, Lx=1.0, mean=delta, amp=0.0, modes=1, seed=0, steps=0, dt=1e-3)
+    pb.sigma = 0.02
+    st = S.prepare(pb)
+    ell = math.sqrt(pb.sigma / ((pb.rho_l - pb.rho_v) * abs(pb.gy)))
+    nu = S.diagnostics(st)[7]
+    assert abs(nu - ell / delta) < 1e-12 * ell / delta
+
+
+def test_vapour_volume_with_outflow_accounting():
+    """Sec. 3.7's vapour volume V = (vapour volume in the domain + V_bc) / V_0, V_bc the vapour
+    volume that left through the outflow boundary: a vapour disc carried out through the top
+    outflow by a uniform flow, with no phase change, keeps V = 1 up to the interface transport
+    error, which falls as the grid is refined (a sign or factor error in V_bc leaves an O(1)
+    deficit once the disc has left)."""
+    devs = []
+    for n in (32, 64):
+        h = 1.0 / n
+        pb = w.const_mdot_levelset(lambda x, y: np.hypot(x - 0.5013, y - 0.83) - 0.15, n=n, mdot=0.0,
+                                   dt=0.4 * h, name="exit")
+        for k in ("u_l", "u_v"):
+            getattr(pb, k)[..., 1] = 1.0
+        pb.ufy_l[:] = 1.0
+        pb.ufy_v[:] = 1.0
+        st = S.prepare(pb)
+        V0 = float(np.sum(1.0 - st.geom.vf)) * h * h
+        vbc, worst = 0.0, 0.0
+        for _ in range(int(0.3 / (0.4 * h))):
+            row = S.step(st)
+            vbc += row[6]
+            worst = max(worst, abs(row[1] + vbc - V0) / V0)
+        assert row[1] < 0.05 * V0             # the disc has left the domain
+        devs.append(worst)
+    assert devs[1] < 0.05 and devs[1] < devs[0] / 1.8, devs

@@ -114,6 +114,35 @@ def stefan_temperature(x, t, beta, alpha_v, T_w, T_sat):
     return T_w + (T_sat - T_w) / math.erf(beta) * special.erf(x / (2.0 * np.sqrt(alpha_v * t)))
 
 
+def sucking_beta(rho_l, rho_v, lam_l, lam_v, cp_l, cp_v, dT, h_lg) -> float:
+    """Growth constant of the 1D sucking problem (Sec. 3.2, its beta equation): the root of
+    beta = dT cp_v lam_l sqrt(alpha_v) exp(-b^2) / (h_lg lam_v sqrt(pi alpha_l) erfc(b)),
+    b = beta rho_v sqrt(alpha_v) / (rho_l sqrt(alpha_l)) (the bracket of the printed equation;
+    its factor exp(beta^2) erf(beta) has no root)."""
+    al, av = lam_l / (rho_l * cp_l), lam_v / (rho_v * cp_v)
+    k = rho_v * math.sqrt(av) / (rho_l * math.sqrt(al))
+
+    def f(b):   # exp(-z^2) / erfc(z) = 1 / erfcx(z), evaluated without underflow
+        return b - dT * cp_v * lam_l * math.sqrt(av) / (
+            h_lg * lam_v * math.sqrt(math.pi * al) * special.erfcx(b * k))
+    return optimize.brentq(f, 1e-12, 100.0, xtol=1e-15, rtol=1e-15, maxiter=500)
+
+
+def sucking_position(t, beta, alpha_v):
+    """Interface position 2 beta sqrt(alpha_v t): the diffusivity that the paper's beta equation
+    and temperature profile are written with (its position equation prints alpha_l)."""
+    return 2.0 * beta * np.sqrt(alpha_v * t)
+
+
+def sucking_temperature(x, t, beta, rho_l, rho_v, alpha_l, alpha_v, T_inf, T_sat):
+    """Liquid temperature of the sucking problem (Sec. 3.2): T_inf - (T_inf - T_sat)
+    erfc(x / (2 sqrt(alpha_l t)) + beta (rho_v - rho_l) sqrt(alpha_v) / (rho_l sqrt(alpha_l)))
+    / erfc(beta rho_v sqrt(alpha_v) / (rho_l sqrt(alpha_l)))."""
+    k = math.sqrt(alpha_v) / (rho_l * math.sqrt(alpha_l))
+    return T_inf - (T_inf - T_sat) * special.erfc(x / (2.0 * np.sqrt(alpha_l * t)) + beta * (rho_v - rho_l) * k) / \
+        special.erfc(beta * rho_v * k)
+
+
 def _bubble2d_logI(eta, a):
     """log of I(eta) = int_eta^inf s^(2a-1) exp(-s^2) ds = Gamma(a) Q(a, eta^2) / 2."""
     q = special.gammaincc(a, eta * eta)
@@ -225,6 +254,37 @@ def stefan(nx=64, ny=64, X0=0.1, Lx=1.0, rho_l=10.0, rho_v=1.0, St=0.1, dT=1.0,
     pb.meta.update(mdot0=mdot, U=U)
     pb.u_l[..., 0] = U
     pb.ufx_l[:, 1:] = U          # the wall face stays 0
+    return pb
+
+
+def sucking(nx=64, ny=4, X0=0.2, Lx=1.0, rho_l=10.0, rho_v=1.0, lam_l=1.0, lam_v=1.0, St=0.2, dT=1.0,
+            mu=0.01, dt=2e-3, steps=100, **kw) -> Problem:
+    """1D sucking problem embedded in 2D (Sec. 3.2): vapour x < X0 at T_sat between a wall at
+    T_sat (left) and superheated liquid (T_sat + dT far away) leaving through an outflow (right);
+    bottom/top symmetry.  Nondimensional, cp = 1, h_lg = cp dT / St (Ja = rho_l cp dT / (rho_v
+    h_lg)); initial state from the similarity solution at the time the front is at X0: vapour at
+    rest at T_sat, liquid at the closed-form profile moving at mdot (1/rho_v - 1/rho_l)."""
+    h = Lx / nx
+    h_lg = 1.0 * dT / St
+    pb = Problem("sucking", nx, ny, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v, mu_l=mu, mu_v=mu,
+                 lam_l=lam_l, lam_v=lam_v, cp_l=1.0, cp_v=1.0, T_sat=0.0, h_lg=h_lg,
+                 bc=(WALL, OUTFLOW, SYMMETRY, SYMMETRY), T_bc=(0.0, None, None, None), **kw)
+    beta = sucking_beta(rho_l, rho_v, lam_l, lam_v, 1.0, 1.0, dT, h_lg)
+    al, av = lam_l / rho_l, lam_v / rho_v
+    t0 = (X0 / (2.0 * beta)) ** 2 / av
+    mdot = rho_v * beta * math.sqrt(av / t0)
+    pb.t0 = t0
+    pb.meta.update(beta=beta, alpha_l=al, alpha_v=av, dT=dT, X0=X0, mdot0=mdot)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: x - X0, nx, ny, h)
+    (Xc, Yc), (Xfx, Yfx), _ = _grids(nx, ny, h, 0.0, 0.0)
+    pb.T_l = sucking_temperature(Xc, t0, beta, rho_l, rho_v, al, av, dT, 0.0)
+    pb.T_v = np.zeros((ny, nx))
+    _zero_flow(pb)
+    ul = mdot * (1.0 / rho_v - 1.0 / rho_l)
+    pb.u_l[..., 0] = ul
+    pb.ufx_l[:] = ul
+    pb.ufx_l[:, 0] = 0.0          # the wall face
     return pb
 
 

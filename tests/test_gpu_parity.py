@@ -123,6 +123,8 @@ def cases():
             mdot=0.5, cfl=0.1, name="saddle"),
         "outflow": lambda: w.const_mdot_levelset(lambda x, y: np.hypot(x - 0.9, y - 0.47) - 0.17, n=48, mdot=1.0,
                                                  cfl=0.2, name="outflow"),
+        # the sucking problem (Sec. 3.2): vapour at rest at T_sat, thin thermal layer in the liquid
+        "sucking": lambda: w.sucking(48, 8, dt=2.5e-3, steps=0),
         # the one-fluid variant (single velocity field, phase-change source in the projection)
         "stefan_1f": lambda: w.one_fluid(w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0)),
         "bubble_1f": lambda: w.one_fluid(w.bubble(n=64, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01,
@@ -184,7 +186,7 @@ def test_prepare_matches_oracle(dev, name):
 
 
 # ----------------------------------------------------------------------------- stages
-@pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "sucking"])
 def test_energy_advection_and_extension(dev, name):
     st = prepared(name, 1)
     ctx = gpu_ctx(dev, st)
@@ -233,7 +235,7 @@ def test_interface_advance_bit_exact(dev, name, order):
         E.ebit_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["stefan", "bubble", "film"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "sucking"])
 def test_energy_solve_flux_and_ghost_velocity(dev, name):
     st = prepared(name, 1)
     pb = st.pb
@@ -302,7 +304,7 @@ def test_full_step_fp64(dev, name):
         E.ebit_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["stefan", "bubble", "stefan_1f", "bubble_1f"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "sucking", "stefan_1f", "bubble_1f"])
 def test_several_steps_track_the_oracle(dev, name):
     st = prepared(name, 0)
     ctx = gpu_ctx(dev, st)

@@ -147,3 +147,46 @@ def test_oracle_planar_bubble_growth():
     Re = 2 * beta * math.sqrt(a * st.t)
     assert abs(R - Re) / Re < 0.03
     assert abs((st.diag[-1][1] - V0) - dv) / dv < 5e-3
+
+
+def test_sucking_closed_form_solves_the_problem():
+    """The sucking problem's similarity solution (Sec. 3.2) as read (front at 2 beta sqrt(alpha_v
+    t), the diffusivity its beta equation and profile are written with): the liquid profile
+    solves T_t + u_l T_x = alpha_l T_xx by finite differences, equals T_sat at the front and
+    T_inf far away, and the interface energy balance rho_v X' h_lg = lam_l T_x holds."""
+    pb = w.sucking(steps=0)
+    m = pb.meta
+    beta, al, av = m["beta"], m["alpha_l"], m["alpha_v"]
+    T = lambda x, t: w.sucking_temperature(x, t, beta, pb.rho_l, pb.rho_v, al, av, m["dT"], 0.0)
+    t = pb.t0 * 1.7
+    X = w.sucking_position(t, beta, av)
+    Xdot = beta * math.sqrt(av / t)
+    ul = pb.rho_v * Xdot * (1.0 / pb.rho_v - 1.0 / pb.rho_l)
+    assert abs(T(X, t)) < 1e-14
+    assert abs(T(50.0, t) - m["dT"]) < 1e-14
+    d = 1e-4
+    for x in (X + 0.01, X + 0.05, X + 0.12):
+        Tt = (T(x, t + d * t) - T(x, t - d * t)) / (2 * d * t)
+        Tx = (T(x + d, t) - T(x - d, t)) / (2 * d)
+        Txx = (T(x + d, t) - 2 * T(x, t) + T(x - d, t)) / (d * d)
+        assert abs(Tt + ul * Tx - al * Txx) < 1e-5 * (abs(Tt) + abs(al * Txx))
+    Tx = (T(X + d, t) - T(X - d, t)) / (2 * d)
+    assert abs(pb.rho_v * Xdot * pb.h_lg - pb.lam_l * Tx) < 1e-7 * pb.lam_l * abs(Tx)
+
+
+def test_oracle_sucking_front_converges():
+    """The oracle's front on the sucking problem approaches the similarity solution as the grid
+    is refined (first order here: the liquid's thermal layer is a few cells thick on the
+    coarse grids; the paper reports second order for its scheme)."""
+    errs = []
+    for n in (64, 128, 256):
+        pb = w.sucking(nx=n, ny=4, dt=0.128 / n, steps=0)
+        st = S.prepare(pb)
+        for _ in range(int(round(0.1 / pb.dt))):
+            S.step(st)
+        m = pb.meta
+        X = float(np.sum(1.0 - st.geom.vf[0])) * pb.h
+        Xe = w.sucking_position(st.t, m["beta"], m["alpha_v"])
+        errs.append(abs(X - Xe) / Xe)
+    assert errs[2] < 0.01
+    assert errs[1] < errs[0] / 1.8 and errs[2] < errs[1] / 1.8, errs

@@ -85,7 +85,7 @@ def prepare(pb):
     st.mdot = interface_mdot(st)
     flow.ghost_velocities(st)
     rfx, rfy = flow.face_rho(pb, st.geom.vf)
-    ax, ay = flow.face_acceleration(pb, st.p, rfx, rfy)
+    ax, ay = flow.face_acceleration(pb, st.p, rfx, rfy, flow.surface_tension_faces(pb, st.geom, rfx, rfy))
     st.gc = flow.faces_to_cells(ax, ay)
     return st
 

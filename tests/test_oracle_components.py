@@ -18,7 +18,10 @@
     is approached as the grid is refined; the two-layer step is mirror-symmetric; WENO3
     momentum advection is exact for quadratic velocity fields;
   * one-fluid variant: the Stefan outflow velocity is the velocity jump mdot (1/rho_v - 1/rho_l);
-    its cell velocity oscillates across the interface where the ghost-fluid one does not.
+    its cell velocity oscillates across the interface where the ghost-fluid one does not;
+  * film-boiling diagnostics: Nu = l / delta for a flat film; vapour volume plus outflow conserved;
+  * surface tension: marker-circle curvature exact for circles (sign of div n), zero for lines,
+    converging on a sinusoid; a static bubble settles to the Laplace jump sigma / R.
 """
 import math
 
@@ -606,3 +609,62 @@ def test_vapour_volume_with_outflow_accounting():
         assert row[1] < 0.05 * V0             # the disc has left the domain
         devs.append(worst)
     assert devs[1] < 0.05 and devs[1] < devs[0] / 1.8, devs
+
+
+# ------------------------------------------------------------------ surface tension
+def test_curvature_exact_for_circles_and_lines():
+    """Curvature from the circles through consecutive markers: markers on a circle give its
+    curvature exactly, with the sign of div n (n from liquid into vapour): -1/R for a vapour
+    bubble, +1/R for a liquid drop; markers on a straight line give 0."""
+    n, R = 48, 0.21
+    for sign, expected in ((1.0, -1.0 / R), (-1.0, 1.0 / R)):
+        pb = w.const_mdot_levelset(lambda x, y: sign * (np.hypot(x - 0.5013, y - 0.4987) - R), n=n, mdot=0.0,
+                                   dt=1e-3)
+        g = geometry.reconstruct(pb.vcol, pb.hx_pos, pb.vy_pos)
+        k = flow.curvature(pb, g)[g.nseg > 0]
+        assert np.all(np.abs(k - expected) < 1e-9 * abs(expected))
+    pb = w.const_mdot_levelset(lambda x, y: y - 0.37 * x - 0.2113, n=n, mdot=0.0, dt=1e-3)
+    g = geometry.reconstruct(pb.vcol, pb.hx_pos, pb.vy_pos)
+    k = flow.curvature(pb, g)[g.nseg > 0]
+    assert np.nanmax(np.abs(k)) < 1e-9
+
+
+def test_curvature_of_a_sinusoid_converges():
+    """Off circles the three-marker circles approximate the curvature f''/(1 + f'^2)^(3/2) of
+    the interface y = f(x) (liquid above) with an error that halves with the cell size."""
+    A, kw = 0.06, 2 * math.pi
+    errs = []
+    for n in (32, 64, 128):
+        h = 1.0 / n
+        pb = w.const_mdot_levelset(lambda x, y: y - 0.5013 - A * np.sin(kw * x + 0.3), n=n, mdot=0.0, dt=1e-3)
+        g = geometry.reconstruct(pb.vcol, pb.hx_pos, pb.vy_pos)
+        kap = flow.curvature(pb, g)
+        e = 0.0
+        for (j, i), (mx, my), nrm, L in geometry.segment_data(g):
+            if 0 < i < n - 1:
+                fp = A * kw * math.cos(kw * mx * h + 0.3)
+                fpp = -A * kw * kw * math.sin(kw * mx * h + 0.3)
+                e = max(e, abs(kap[j, i] - fpp / (1 + fp * fp) ** 1.5))
+        errs.append(e / (A * kw * kw))
+    assert errs[2] < 0.01 and errs[1] < errs[0] / 1.6 and errs[2] < errs[1] / 1.6, errs
+
+
+def test_static_bubble_laplace_pressure():
+    """A vapour bubble at rest in liquid with surface tension and no phase change: the
+    well-balanced surface-tension acceleration sigma kappa_f grad_f H / rho_f and the pressure
+    gradient settle to the Laplace jump p_vap - p_liq = sigma / R of the pressure-jump equation,
+    with small spurious currents."""
+    n, R, sigma = 64, 0.2, 1.0
+    h = 1.0 / n
+    pb = w.const_mdot_levelset(lambda x, y: np.hypot(x - 0.5013, y - 0.4987) - R, n=n, mdot=0.0, dt=2e-4,
+                               rho_l=10.0, rho_v=1.0, mu=0.05)
+    pb.sigma = sigma
+    st = S.prepare(pb)
+    for _ in range(5):
+        S.step(st)
+    xc = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xc, xc)
+    r = np.hypot(X - 0.5013, Y - 0.4987)
+    jump = st.p[r < R - 3 * h].mean() - st.p[r > R + 3 * h].mean()
+    assert abs(jump * R / sigma - 1.0) < 5e-3
+    assert max(np.abs(st.u_l).max(), np.abs(st.u_v).max()) < 1e-3 * sigma / 1.0

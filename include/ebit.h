@@ -156,8 +156,13 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream,
                       const ebit_allocator* alloc, ebit_ctx** out);
 
 /* Material properties of instance `inst` (Sec. 2.2): liquid and vapour rho, mu, lambda,
- * cp; saturation temperature, latent heat h_lg, surface tension (must be 0: the CSF term
- * is not part of this step), gravity. */
+ * cp; saturation temperature, latent heat h_lg, surface tension coefficient sigma >= 0,
+ * gravity.  With sigma > 0 the step adds the surface-tension force f = sigma kappa delta_s n
+ * of the momentum equation (discretization equations 1-5) in the well-balanced face form:
+ * sigma kappa_f (H_j - H_i) / (h rho_f) on every interior face, H the liquid volume fraction,
+ * kappa = div n (n from liquid into vapour) from the circles through each cut cell's markers
+ * and their chain neighbours, so that the pressure jumps by p_liq - p_vap = sigma kappa across
+ * the interface (pressure-jump equation). */
 ebit_status ebit_set_phase_props(ebit_ctx* ctx, int inst, const ebit_phase_props* liq,
                                  const ebit_phase_props* vap, double T_sat, double h_lg,
                                  double sigma, double gx, double gy);

@@ -1,5 +1,7 @@
 // C ABI of the EBIT phase-change step: context, memory, stage orchestration.
 // The time iteration follows Sec. 2.5 of arXiv 2402.13677 (see include/ebit.h).
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -43,6 +45,7 @@ struct Instance {
     int *band_list, *band_count, *band_idx;
     double *ext[4];
     double *face_ax, *face_ay;   // face accelerations of the projection
+    double* kap;                 // interface curvature of the cut cells (surface tension)
     // diagnostics and status
     double *diag_partial, *diag_out, *clock;
     unsigned* diag_ticket;
@@ -238,6 +241,7 @@ static void assign_ptrs(Instance& I, const std::function<char*(size_t)>& take, s
     I.band_count = (int*)take(256);
     I.band_idx = (int*)take(N * 4);
     for (int k = 0; k < 4; ++k) I.ext[k] = (double*)take(N * 8);
+    I.kap = (double*)take(N * 8);
     I.diag_partial = (double*)take(8 * 8 * 1024);
     I.diag_out = (double*)take(64 * 8);
     I.clock = (double*)take(256);
@@ -390,15 +394,19 @@ static void momentum(Instance& I, cudaStream_t st) {
         cudaStreamWaitEvent(st, I.e_join, 0);
         I.solver2.use_graph = 0;
     }
-    launch_ustar(I.g, I.p, I.vxx, I.vxy, I.gc, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
+    if (I.p.sigma > 0.0) {   // curvature of the new interface for the surface-tension force
+        launch_curvature(I.g, I.flags, I.cseg, I.hpos, I.vpos, I.kap, st);
+        count(1);
+    }
+    launch_ustar(I.g, I.p, I.vxx, I.vxy, I.gc, I.kap, I.vf, I.us_l, I.us_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
     count(2);
     // S12: projection
     launch_poisson_operator(I.g, I.p, I.vf, I.flags, I.cseg, I.hpos, I.vpos, I.mdot, I.ufx_l, I.ufx_v, I.ufy_l,
                             I.ufy_v, I.op_cd, I.op_dd, I.op_wl, I.op_wb, I.op_b, st);
     count(1);
     do_solve(I, SLOT_POISSON, I.op_b, I.P, 1, st);
-    launch_project(I.g, I.p, I.P, I.vf, I.op_wl, I.op_wb, I.face_ax, I.face_ay, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v,
-                   I.gc, I.us_l, I.us_v, I.u_l, I.u_v, st);
+    launch_project(I.g, I.p, I.P, I.vf, I.kap, I.op_wl, I.op_wb, I.face_ax, I.face_ay, I.ufx_l, I.ufx_v, I.ufy_l,
+                   I.ufy_v, I.gc, I.us_l, I.us_v, I.u_l, I.u_v, st);
     count(2);
 }
 
@@ -420,8 +428,12 @@ static void prepare(Instance& I, cudaStream_t st) {
     if (I.p.energy) extend_T(I, I.T_l, I.T_v, st);
     mass_flux(I, st);
     ghost_velocity(I, st);
-    launch_project(I.g, I.p, I.P, I.vf, nullptr, nullptr, I.face_ax, I.face_ay, nullptr, nullptr, nullptr, nullptr,
-                   I.gc, nullptr, nullptr, nullptr, nullptr, st);
+    if (I.p.sigma > 0.0) {
+        launch_curvature(I.g, I.flags, I.cseg, I.hpos, I.vpos, I.kap, st);
+        count(1);
+    }
+    launch_project(I.g, I.p, I.P, I.vf, I.kap, nullptr, nullptr, I.face_ax, I.face_ay, nullptr, nullptr, nullptr,
+                   nullptr, I.gc, nullptr, nullptr, nullptr, nullptr, st);
     count(2);
 }
 
@@ -613,16 +625,27 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
 ebit_status ebit_set_phase_props(ebit_ctx* ctx, int inst, const ebit_phase_props* liq, const ebit_phase_props* vap,
                                  double T_sat, double h_lg, double sigma, double gx, double gy) {
     if (!ctx || inst < 0 || inst >= (int)ctx->inst.size() || !liq || !vap) return fail(ctx, EBIT_EINVAL, "bad args");
-    if (sigma != 0.0) return fail(ctx, EBIT_EINVAL, "surface tension is not part of this step (sigma must be 0)");
+    if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(ctx, EBIT_EINVAL, "sigma must be finite and >= 0");
     if (!(liq->rho > 0 && vap->rho > 0 && liq->lambda > 0 && vap->lambda > 0 && liq->cp > 0 && vap->cp > 0 &&
           liq->mu > 0 && vap->mu > 0 && h_lg != 0.0))
         return fail(ctx, EBIT_EINVAL, "properties must be positive");
-    Phys& p = ctx->inst[inst].p;
+    Instance& I = ctx->inst[inst];
+    Phys& p = I.p;
+    // whether the step computes a curvature is decided when its graph is captured: a change
+    // between no surface tension and some drops the captured graphs of the instance (or batch)
+    if (I.props_set && (p.sigma > 0.0) != (sigma > 0.0)) {
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        for (auto& gx : I.graph)
+            if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+        if (I.batch >= 0)
+            for (auto& gx : ctx->batches[I.batch].graph)
+                if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+    }
     p.rho_l = liq->rho; p.mu_l = liq->mu; p.lam_l = liq->lambda; p.cp_l = liq->cp;
     p.rho_v = vap->rho; p.mu_v = vap->mu; p.lam_v = vap->lambda; p.cp_v = vap->cp;
     phys_derive(p);
     p.T_sat = T_sat; p.h_lg = h_lg; p.gx = gx; p.gy = gy; p.sigma = sigma;
-    ctx->inst[inst].props_set = true;
+    I.props_set = true;
     return EBIT_OK;
 }
 
@@ -867,7 +890,12 @@ static ebit_status replay_batch(ebit_ctx* ctx, Batch& B, cudaStream_t st) {
             sv->use_coop = 0;   // a grid barrier per member would not fit one cooperative grid
         }
     }
-    for (size_t z = 0; z < B.members.size(); ++z) B.h_phys[z] = ctx->inst[B.members[z]].p;
+    double smax = 0.0;
+    for (size_t z = 0; z < B.members.size(); ++z) {
+        B.h_phys[z] = ctx->inst[B.members[z]].p;
+        smax = std::max(smax, B.h_phys[z].sigma);
+    }
+    B.lead.p.sigma = smax;   // launches the curvature kernel if any member has surface tension
     cudaMemcpyAsync(B.d_phys, B.h_phys.data(), B.h_phys.size() * sizeof(Phys), cudaMemcpyHostToDevice, st);
     B.lead.nstep = I0.nstep;
     int par = (I0.cfg.sweep_order == 0) ? 0 : (int)(I0.nstep & 1);

@@ -382,6 +382,31 @@ __global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flag
 __device__ inline double rho_mix(const Phys& p, double vf) { return fma(p.drho, vf, p.rho_v); }
 __device__ inline double mu_mix(const Phys& p, double vf) { return fma(p.dmu, vf, p.mu_v); }
 
+// volume fraction of a face: the mean of its two cells (a boundary face takes its cell)
+__device__ inline double face_vf_x(const Grid& g, const double* vf, int i, int j) {
+    if (i == 0) return vf[cidx(g, 0, j)];
+    if (i == g.nx) return vf[cidx(g, g.nx - 1, j)];
+    return 0.5 * (vf[cidx(g, i - 1, j)] + vf[cidx(g, i, j)]);
+}
+__device__ inline double face_vf_y(const Grid& g, const double* vf, int i, int j) {
+    if (j == 0) return vf[cidx(g, i, 0)];
+    if (j == g.ny) return vf[cidx(g, i, g.ny - 1)];
+    return 0.5 * (vf[cidx(g, i, j - 1)] + vf[cidx(g, i, j)]);
+}
+
+// surface-tension acceleration sigma kappa_f (H_b - H_a) / (h rho_f) on the interior face
+// between cells a and b (CSF force in the well-balanced face form; H the liquid volume
+// fraction): kappa_f the mean of the two cells' curvatures where both are defined, else the one
+// that is, else 0; zero without surface tension
+__device__ inline double st_face(const Phys& p, const Grid& g, const double* kap, const double* vf, int a, int b,
+                                 double fvf) {
+    if (p.sigma == 0.0 || !kap) return 0.0;
+    double ka = kap[a], kb = kap[b];
+    bool da = !isnan(ka), db = !isnan(kb);
+    double kf = da && db ? 0.5 * (ka + kb) : (da ? ka : (db ? kb : 0.0));
+    return p.sigma * kf * (vf[b] - vf[a]) / (g.h * rho_mix(p, fvf));
+}
+
 // viscous Helmholtz operator for velocity component comp (integrated form):
 //   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where comp is Dirichlet (odd),
 //   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces).
@@ -470,10 +495,13 @@ __global__ void k_ustar(Grid g, Phys p, const double2* __restrict__ sx, const do
 }
 
 __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, const double2* __restrict__ us_v,
+                            const double* __restrict__ kap, const double* __restrict__ vf,
                             double* __restrict__ fx_l, double* __restrict__ fx_v, double* __restrict__ fy_l,
                             double* __restrict__ fy_v) {
     zphys(g, p);
     const long long zo = zoff(g.zs);
+    kap = zsh(kap, zo);
+    vf = zsh(vf, zo);
     us_l = zsh(us_l, zo);
     us_v = zsh(us_v, zo);
     fx_l = zsh(fx_l, zo);
@@ -489,8 +517,9 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
         double vl, vv;
         if (i > 0 && i < g.nx) {
             int a = cidx(g, i - 1, j), b = a + 1;
-            vl = 0.5 * (us_l[a].x + us_l[b].x) + p.dt * p.gx;
-            vv = 0.5 * (us_v[a].x + us_v[b].x) + p.dt * p.gx;
+            double acc = p.gx + st_face(p, g, kap, vf, a, b, face_vf_x(g, vf, i, j));
+            vl = 0.5 * (us_l[a].x + us_l[b].x) + p.dt * acc;
+            vv = 0.5 * (us_v[a].x + us_v[b].x) + p.dt * acc;
         } else {
             int s = i == 0 ? 0 : 1;
             if (g.bc[s] == BC_OUTFLOW) {
@@ -509,8 +538,9 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
         double vl, vv;
         if (j > 0 && j < g.ny) {
             int a = cidx(g, i, j - 1), b = cidx(g, i, j);
-            vl = 0.5 * (us_l[a].y + us_l[b].y) + p.dt * p.gy;
-            vv = 0.5 * (us_v[a].y + us_v[b].y) + p.dt * p.gy;
+            double acc = p.gy + st_face(p, g, kap, vf, a, b, face_vf_y(g, vf, i, j));
+            vl = 0.5 * (us_l[a].y + us_l[b].y) + p.dt * acc;
+            vv = 0.5 * (us_v[a].y + us_v[b].y) + p.dt * acc;
         } else {
             int s = j == 0 ? 2 : 3;
             if (g.bc[s] == BC_OUTFLOW) {
@@ -529,16 +559,6 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
 // ---------------------------------------------------------------------------------
 // S12: projection
 // ---------------------------------------------------------------------------------
-__device__ inline double face_vf_x(const Grid& g, const double* vf, int i, int j) {
-    if (i == 0) return vf[cidx(g, 0, j)];
-    if (i == g.nx) return vf[cidx(g, g.nx - 1, j)];
-    return 0.5 * (vf[cidx(g, i - 1, j)] + vf[cidx(g, i, j)]);
-}
-__device__ inline double face_vf_y(const Grid& g, const double* vf, int i, int j) {
-    if (j == 0) return vf[cidx(g, i, 0)];
-    if (j == g.ny) return vf[cidx(g, i, g.ny - 1)];
-    return 0.5 * (vf[cidx(g, i, j - 1)] + vf[cidx(g, i, j)]);
-}
 
 // Poisson operator: wl/wb = dt / rho_f (interior faces), dd = 2 dt / rho_f on outflow faces,
 // b = -h * (undivided divergence of the face field of the cell's phase); x0 = p
@@ -614,6 +634,7 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     b[c] = rhs;
 }
 
+
 // face accelerations a_f = g - grad_f p / rho_f (0 on walls and symmetry planes); on interior
 // faces, with the Poisson face weight w = dt / rho_f given (wl != null), as g - dp w / (h dt)
 __device__ inline double accel_x(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl,
@@ -647,12 +668,13 @@ __device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, 
 // with fx_l != null also the face update u_f^{n+1} = u_f* + dt (a_f - g) (discretization
 // equation 4) for both phase fields
 __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
-                             const double* __restrict__ wl_p, const double* __restrict__ wb_p,
-                             double* __restrict__ ax, double* __restrict__ ay, double* fx_l, double* fx_v,
-                             double* fy_l, double* fy_v) {
+                             const double* __restrict__ kap, const double* __restrict__ wl_p,
+                             const double* __restrict__ wb_p, double* __restrict__ ax, double* __restrict__ ay,
+                             double* fx_l, double* fx_v, double* fy_l, double* fy_v) {
     zphys(g, p);
     const long long zo = zoff(g.zs);
     P = zsh(P, zo);
+    kap = zsh(kap, zo);
     vf = zsh(vf, zo);
     wl_p = zsh(wl_p, zo);
     wb_p = zsh(wb_p, zo);
@@ -668,23 +690,25 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
     if (t < nfx) {
         // faces < 2^31 (nx ny <= 2^29): 32-bit division
         int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
-        double a = accel_x(g, p, P, vf, wl_p, i, j);
+        bool bnd = i == 0 || i == g.nx;
+        double sf = bnd ? 0.0 : st_face(p, g, kap, vf, cidx(g, i - 1, j), cidx(g, i, j), face_vf_x(g, vf, i, j));
+        double a = accel_x(g, p, P, vf, wl_p, i, j) + sf;
         ax[t] = a;
         if (!fx_l) return;
-        bool bnd = i == 0 || i == g.nx;
         if (bnd && g.bc[i == 0 ? 0 : 1] != BC_OUTFLOW) { fx_l[t] = 0.0; fx_v[t] = 0.0; return; }
-        double corr = p.dt * (a - p.gx);
+        double corr = p.dt * (a - p.gx - sf);   // u_f* carries dt (g + surface tension) already
         fx_l[t] += corr;
         fx_v[t] += corr;
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
         int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
-        double a = accel_y(g, p, P, vf, wb_p, i, j);
+        bool bnd = j == 0 || j == g.ny;
+        double sf = bnd ? 0.0 : st_face(p, g, kap, vf, cidx(g, i, j - 1), cidx(g, i, j), face_vf_y(g, vf, i, j));
+        double a = accel_y(g, p, P, vf, wb_p, i, j) + sf;
         ay[e] = a;
         if (!fx_l) return;
-        bool bnd = j == 0 || j == g.ny;
         if (bnd && g.bc[j == 0 ? 2 : 3] != BC_OUTFLOW) { fy_l[e] = 0.0; fy_v[e] = 0.0; return; }
-        double corr = p.dt * (a - p.gy);
+        double corr = p.dt * (a - p.gy - sf);
         fy_l[e] += corr;
         fy_v[e] += corr;
     }
@@ -937,12 +961,12 @@ void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double
 }
 
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
-                  double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
-                  cudaStream_t st) {
+                  const double* kap, const double* vf, double2* us_l, double2* us_v, double* fx_l, double* fx_v,
+                  double* fy_l, double* fy_v, cudaStream_t st) {
     int N = g.nx * g.ny;
     k_ustar<<<grid1(N, 256, g.nz), 256, 0, st>>>(g, p, sx, sy, gc, us_l, us_v);
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_face_star<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, us_l, us_v, fx_l, fx_v, fy_l, fy_v);
+    k_face_star<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, us_l, us_v, kap, vf, fx_l, fx_v, fy_l, fy_v);
 }
 
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
@@ -953,12 +977,12 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
                                                                          fx_l, fx_v, fy_l, fy_v, cd, dd, wl, wb, b);
 }
 
-void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl_p,
-                    const double* wb_p, double* ax, double* ay, double* fx_l, double* fx_v, double* fy_l,
-                    double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l, double2* u_v,
-                    cudaStream_t st) {
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* kap,
+                    const double* wl_p, const double* wb_p, double* ax, double* ay, double* fx_l, double* fx_v,
+                    double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l,
+                    double2* u_v, cudaStream_t st) {
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_face_accel<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, P, vf, wl_p, wb_p, ax, ay, fx_l, fx_v, fy_l, fy_v);
+    k_face_accel<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, P, vf, kap, wl_p, wb_p, ax, ay, fx_l, fx_v, fy_l, fy_v);
     k_project_cells<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, ax, ay, gc, us_l, us_v, u_l, u_v);
 }
 

@@ -786,8 +786,86 @@ __global__ void k_check_interface(Grid g, const uint8_t* __restrict__ vcol, doub
 }
 
 // ---------------------------------------------------------------------------------
+// interface curvature for the surface-tension force (CSF term of the momentum equation)
+// ---------------------------------------------------------------------------------
+// signed curvature of the circle through A, B, C: positive when A -> B -> C turns left
+__device__ inline double menger(double2 A, double2 B, double2 C) {
+    double abx = B.x - A.x, aby = B.y - A.y, bcx = C.x - B.x, bcy = C.y - B.y;
+    double cross = abx * bcy - aby * bcx;
+    double den = sqrt(abx * abx + aby * aby) * sqrt(bcx * bcx + bcy * bcy) *
+                 sqrt((C.x - A.x) * (C.x - A.x) + (C.y - A.y) * (C.y - A.y));
+    return den > 0.0 ? 2.0 * cross / den : 0.0;
+}
+
+// grid position of the marker linked, through the cell across cell-edge k of (i, j), to the
+// marker on that edge; false at a domain boundary or if that cell has no such segment
+__device__ inline bool across(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, int i,
+                              int j, int k, double2* R) {
+    int in = i + (k == 1) - (k == 3), jn = j + (k == 2) - (k == 0);
+    if (in < 0 || in >= g.nx || jn < 0 || jn >= g.ny) return false;
+    int kk = (k + 2) & 3;
+    uint16_t code = cseg[cidx(g, in, jn)];
+    for (int s = 0; s < seg_count(code); ++s) {
+        int kP = seg_P(code, s), kQ = seg_Q(code, s);
+        int ko = kP == kk ? kQ : (kQ == kk ? kP : -1);
+        if (ko < 0) continue;
+        double2 m = marker_local(g, hpos, vpos, ko, in, jn);
+        *R = make_double2(in + m.x, jn + m.y);
+        return true;
+    }
+    return false;
+}
+
+// Curvature kappa = div n (n from liquid into vapour) of every cut cell, from the markers: for
+// its segment P -> Q (liquid on the left) and the chain neighbours R_P before P and R_Q after Q,
+// the mean of the curvatures of the circles through (R_P, P, Q) and (P, Q, R_Q) (one circle
+// where a neighbour is missing); two segments: the length-weighted mean; NaN where undefined
+// or not cut.  Grid units in, physical curvature out.
+__global__ void k_curvature(Grid g, const uint8_t* __restrict__ flags, const uint16_t* __restrict__ cseg,
+                            const double* __restrict__ hpos, const double* __restrict__ vpos,
+                            double* __restrict__ kap) {
+    const long long zo = zoff(g.zs);
+    flags = zsh(flags, zo);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    kap = zsh(kap, zo);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    int c = cidx(g, i, j);
+    double out = nan("");
+    if (flags[c] & F_CUT) {
+        uint16_t code = cseg[c];
+        double num = 0.0, den = 0.0;
+        for (int s = 0; s < seg_count(code); ++s) {
+            int kP = seg_P(code, s), kQ = seg_Q(code, s);
+            double2 P = marker_local(g, hpos, vpos, kP, i, j), Q = marker_local(g, hpos, vpos, kQ, i, j);
+            P = make_double2(i + P.x, j + P.y);
+            Q = make_double2(i + Q.x, j + Q.y);
+            double2 R;
+            double sum = 0.0;
+            int nk = 0;
+            if (across(g, cseg, hpos, vpos, i, j, kP, &R)) { sum += menger(R, P, Q); ++nk; }
+            if (across(g, cseg, hpos, vpos, i, j, kQ, &R)) { sum += menger(P, Q, R); ++nk; }
+            if (!nk) continue;
+            double L = sqrt((Q.x - P.x) * (Q.x - P.x) + (Q.y - P.y) * (Q.y - P.y));
+            num += L * (sum / nk);
+            den += L;
+        }
+        if (den > 0.0) out = num / den * g.inv_h;
+    }
+    kap[c] = out;
+}
+
+// ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
+
+void launch_curvature(const Grid& g, const uint8_t* flags, const uint16_t* cseg, const double* hpos,
+                      const double* vpos, double* kap, cudaStream_t st) {
+    k_curvature<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, flags, cseg, hpos, vpos, kap);
+}
 
 void launch_check_interface(const Grid& g, const uint8_t* vcol, double* hpos, double* vpos, int* err,
                             cudaStream_t st) {

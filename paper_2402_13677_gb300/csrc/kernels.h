@@ -24,6 +24,8 @@ void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, cons
 void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,
                             const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
                             double* cd, double* dd, double* wl, double* wb, double* b, double* x0, cudaStream_t st);
+void launch_curvature(const Grid& g, const uint8_t* flags, const uint16_t* cseg, const double* hpos,
+                      const double* vpos, double* kap, cudaStream_t st);
 void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos, const double* vpos,
                       const double* T_l, const double* T_v, double* mdot, cudaStream_t st);
 
@@ -50,8 +52,8 @@ void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
                     const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st);
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,
-                  double2* us_l, double2* us_v, double* fx_l, double* fx_v, double* fy_l, double* fy_v,
-                  cudaStream_t st);
+                  const double* kap, const double* vf, double2* us_l, double2* us_v, double* fx_l, double* fx_v,
+                  double* fy_l, double* fy_v, cudaStream_t st);
 void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, const uint8_t* flags,
                              const uint16_t* cseg, const double* hpos, const double* vpos, const double* mdot,
                              const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
@@ -60,10 +62,10 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
 // are updated when fx_l != null
 // wl_p / wb_p: the Poisson operator's face weights dt / rho_f of the same volume fractions (they
 // replace the per-face division), or null
-void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl_p,
-                    const double* wb_p, double* ax, double* ay, double* fx_l, double* fx_v, double* fy_l,
-                    double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l, double2* u_v,
-                    cudaStream_t st);
+void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* kap,
+                    const double* wl_p, const double* wb_p, double* ax, double* ay, double* fx_l, double* fx_v,
+                    double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l,
+                    double2* u_v, cudaStream_t st);
 int diag_blocks(const Grid& g);
 void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const uint16_t* cseg, const double* hpos,
                         const double* vpos, const double* mdot, const uint8_t* flags, const double* fx_l,

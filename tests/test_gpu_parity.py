@@ -105,6 +105,12 @@ def _merging_discs(n=48, gap=0.3):
                                  n=n, mdot=1.0, name="merge")
 
 
+def _with_sigma(pb, sigma):
+    pb.sigma = sigma
+    pb.name += "_sigma"
+    return pb
+
+
 def cases():
     return {
         "stefan": lambda: w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0),
@@ -125,6 +131,15 @@ def cases():
                                                  cfl=0.2, name="outflow"),
         # the sucking problem (Sec. 3.2): vapour at rest at T_sat, thin thermal layer in the liquid
         "sucking": lambda: w.sucking(48, 8, dt=2.5e-3, steps=0),
+        # surface tension (CSF with marker-circle curvature): a static bubble, a film under
+        # gravity whose Taylor wavelength is the domain width, a growing bubble
+        "static_sigma": lambda: _with_sigma(w.const_mdot_levelset(
+            lambda x, y: np.hypot(x - 0.5013, y - 0.4987) - 0.2, n=48, mdot=0.0, dt=2e-4, rho_l=10.0, rho_v=1.0,
+            mu=0.05, name="static_sigma"), 1.0),
+        "film_sigma": lambda: _with_sigma(w.film(40, 56, Lx=1.0, mean=0.31, amp=0.04, modes=2, seed=3, steps=0,
+                                                 dt=1e-3), 4.0 / (12 * np.pi ** 2)),
+        "bubble_sigma": lambda: _with_sigma(w.bubble(n=64, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01,
+                                                     dt=1e-4, steps=0), 0.05),
         # the one-fluid variant (single velocity field, phase-change source in the projection)
         "stefan_1f": lambda: w.one_fluid(w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0)),
         "bubble_1f": lambda: w.one_fluid(w.bubble(n=64, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01,
@@ -304,7 +319,8 @@ def test_full_step_fp64(dev, name):
         E.ebit_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["stefan", "bubble", "sucking", "stefan_1f", "bubble_1f"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "sucking", "stefan_1f", "bubble_1f", "static_sigma",
+                                  "film_sigma"])
 def test_several_steps_track_the_oracle(dev, name):
     st = prepared(name, 0)
     ctx = gpu_ctx(dev, st)

@@ -130,7 +130,8 @@ enum {
     EBIT_F_HX_POS = 16, EBIT_F_VY_POS = 17, /* marker fractions of horizontal / vertical edges       */
     EBIT_F_TSTAR_L = 18, EBIT_F_TSTAR_V = 19, /* advected temperature of the current step            */
     EBIT_F_CSEG = 20,                       /* uint16 per cell: nseg | P0<<2 | Q0<<4 | P1<<6 | Q1<<8  */
-    EBIT_F_UG = 21,                         /* cell interfacial velocity u_Gamma, double2            */
+    EBIT_F_UG = 21,                         /* cell interfacial velocity u_Gamma of the last step,
+                                               double2, on the cells within two of the interface  */
     EBIT_F_COUNT = 22
 };
 

@@ -43,6 +43,7 @@ struct Instance {
     double2 *vbx, *vby, *vxx, *vxy;   // viscous RHS / solutions, liquid and vapour interleaved
     // band compaction + extension values
     int *band_list, *band_count, *band_idx;
+    int *near_list, *near_count, *near_mark;   // cells within two of the interface (the sweeps)
     double *ext[4];
     double *face_ax, *face_ay;   // face accelerations of the projection
     double* kap;                 // interface curvature of the cut cells (surface tension)
@@ -240,6 +241,9 @@ static void assign_ptrs(Instance& I, const std::function<char*(size_t)>& take, s
     I.band_list = (int*)take(N * 4);
     I.band_count = (int*)take(256);
     I.band_idx = (int*)take(N * 4);
+    I.near_list = (int*)take(N * 4);
+    I.near_count = (int*)take(256);
+    I.near_mark = (int*)take(N * 4);   // zero between steps (the arena starts zeroed)
     for (int k = 0; k < 4; ++k) I.ext[k] = (double*)take(N * 8);
     I.kap = (double*)take(N * 8);
     I.diag_partial = (double*)take(8 * 8 * 1024);
@@ -281,9 +285,12 @@ static void ghost_velocity(Instance& I, cudaStream_t st) {
     count(2);
 }
 
+// S2-S5 over the cells within two of the interface: the narrow band of the start-of-step
+// geometry dilated by one cell, u_Gamma on those cells, the two sweeps, the reconstruction
 static void advance_interface(Instance& I, cudaStream_t st) {
-    launch_ug(I.g, I.p, I.flags, I.u_l, I.u_v, I.mdot, I.nb, I.uG, st);
-    count(1);
+    launch_band_dilate(I.g, I.band_list, I.band_count, I.near_mark, I.near_list, I.near_count, st);
+    launch_ug_list(I.g, I.p, I.near_list, I.near_count, I.flags, I.u_l, I.u_v, I.mdot, I.nb, I.uG, st);
+    count(2);
     double dth = I.p.dt / I.g.h;
     int first = (I.cfg.sweep_order == 0 || (I.nstep % 2) == 0) ? 0 : 1;
     for (int k = 0; k < 2; ++k) {
@@ -292,13 +299,15 @@ static void advance_interface(Instance& I, cudaStream_t st) {
             launch_reconstruct(I.g, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, nullptr, st);
             count(1);
         }
-        launch_sweep(I.g, axis, dth, I.vcol, I.hpos, I.vpos, I.cseg, I.uG, I.hdisp, I.vdisp, I.vcol_n, I.hpos_n,
-                     I.vpos_n, I.status, st);
-        count(4);
+        launch_sweep(I.g, axis, dth, I.near_list, I.near_count, I.vcol, I.hpos, I.vpos, I.cseg, I.uG, I.hdisp,
+                     I.vdisp, I.vcol_n, I.hpos_n, I.vpos_n, I.status, st);
+        count(3);
         std::swap(I.vcol, I.vcol_n);
         std::swap(I.hpos, I.hpos_n);
         std::swap(I.vpos, I.vpos_n);
     }
+    launch_band_unmark(I.g, I.near_list, I.near_count, I.near_mark, st);
+    count(1);
     reconstruct_full(I, st);
 }
 

@@ -517,7 +517,7 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
         double vl, vv;
         if (i > 0 && i < g.nx) {
             int a = cidx(g, i - 1, j), b = a + 1;
-            double acc = p.gx + st_face(p, g, kap, vf, a, b, face_vf_x(g, vf, i, j));
+            double acc = p.sigma > 0.0 ? p.gx + st_face(p, g, kap, vf, a, b, face_vf_x(g, vf, i, j)) : p.gx;
             vl = 0.5 * (us_l[a].x + us_l[b].x) + p.dt * acc;
             vv = 0.5 * (us_v[a].x + us_v[b].x) + p.dt * acc;
         } else {
@@ -538,7 +538,7 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
         double vl, vv;
         if (j > 0 && j < g.ny) {
             int a = cidx(g, i, j - 1), b = cidx(g, i, j);
-            double acc = p.gy + st_face(p, g, kap, vf, a, b, face_vf_y(g, vf, i, j));
+            double acc = p.sigma > 0.0 ? p.gy + st_face(p, g, kap, vf, a, b, face_vf_y(g, vf, i, j)) : p.gy;
             vl = 0.5 * (us_l[a].y + us_l[b].y) + p.dt * acc;
             vv = 0.5 * (us_v[a].y + us_v[b].y) + p.dt * acc;
         } else {
@@ -691,7 +691,8 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
         // faces < 2^31 (nx ny <= 2^29): 32-bit division
         int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
         bool bnd = i == 0 || i == g.nx;
-        double sf = bnd ? 0.0 : st_face(p, g, kap, vf, cidx(g, i - 1, j), cidx(g, i, j), face_vf_x(g, vf, i, j));
+        double sf = (bnd || !(p.sigma > 0.0))
+                        ? 0.0 : st_face(p, g, kap, vf, cidx(g, i - 1, j), cidx(g, i, j), face_vf_x(g, vf, i, j));
         double a = accel_x(g, p, P, vf, wl_p, i, j) + sf;
         ax[t] = a;
         if (!fx_l) return;
@@ -703,7 +704,8 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
         long long e = t - nfx;
         int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
         bool bnd = j == 0 || j == g.ny;
-        double sf = bnd ? 0.0 : st_face(p, g, kap, vf, cidx(g, i, j - 1), cidx(g, i, j), face_vf_y(g, vf, i, j));
+        double sf = (bnd || !(p.sigma > 0.0))
+                        ? 0.0 : st_face(p, g, kap, vf, cidx(g, i, j - 1), cidx(g, i, j), face_vf_y(g, vf, i, j));
         double a = accel_y(g, p, P, vf, wb_p, i, j) + sf;
         ay[e] = a;
         if (!fx_l) return;

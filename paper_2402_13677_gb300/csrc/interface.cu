@@ -198,32 +198,6 @@ __global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* 
 }
 
 // u_Gamma at cell centres from the jump condition (interfacial-velocity equation)
-__global__ void k_ug(Grid g, Phys p, const uint8_t* __restrict__ flags, const double2* __restrict__ u_l,
-                     const double2* __restrict__ u_v, const double* __restrict__ mdot,
-                     const double2* __restrict__ nb, double2* __restrict__ uG) {
-    zphys(g, p);
-    const long long zo = zoff(g.zs);
-    flags = zsh(flags, zo);
-    u_l = zsh(u_l, zo);
-    u_v = zsh(u_v, zo);
-    mdot = zsh(mdot, zo);
-    nb = zsh(nb, zo);
-    uG = zsh(uG, zo);
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.nx * g.ny) return;
-    double m = mdot[c];
-    double2 n = nb[c];
-    if (flags[c] & F_CCOL) {
-        double cl = m / p.rho_l;
-        double2 u = u_l[c];
-        uG[c] = make_double2(u.x - cl * n.x, u.y - cl * n.y);
-    } else {
-        double cv = m / p.rho_v;
-        double2 u = u_v[c];
-        uG[c] = make_double2(u.x - cv * n.x, u.y - cv * n.y);
-    }
-}
-
 // bilinear interpolation from the four nearest cell centres (Fig. 2)
 __device__ inline double interp_bilinear(const double2* uG, const Grid& g, int comp, double x, double y) {
     double fx = x - 0.5;
@@ -251,43 +225,28 @@ __device__ inline bool vcut(const Grid& g, const uint8_t* vcol, int i, int j) {
     return vcol[vidx(g, i, j)] != vcol[vidx(g, i, j + 1)];
 }
 
-// displaced along-coordinate of every marker (marker-motion equation, explicit Euler)
-__global__ void k_displace(Grid g, int axis, double dth, const uint8_t* __restrict__ vcol,
-                           const double* __restrict__ hpos, const double* __restrict__ vpos,
-                           const double2* __restrict__ uG, double* __restrict__ hdisp,
-                           double* __restrict__ vdisp, int* __restrict__ status) {
-    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
-    const long long zo = zoff(g.zs);
-    vcol = zsh(vcol, zo);
-    hpos = zsh(hpos, zo);
-    vpos = zsh(vpos, zo);
-    uG = zsh(uG, zo);
-    hdisp = zsh(hdisp, zo);
-    vdisp = zsh(vdisp, zo);
-    status = zsh(status, zo);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long nh = (long long)(g.ny + 1) * g.nx;
-    long long nv = (long long)g.ny * (g.nx + 1);
+// displaced along-coordinate of the marker on a cut edge (marker-motion equation, explicit
+// Euler): horizontal edge (i, j) if hz, else vertical edge (i, j)
+__device__ inline void displace_edge(const Grid& g, int axis, double dth, const uint8_t* vcol, const double* hpos,
+                                     const double* vpos, const double2* uG, double* hdisp, double* vdisp,
+                                     int* status, bool hz, int i, int j) {
     double x, y;
     bool aligned;
     double* out;
-    if (t < nh) {
-        int j = (int)((unsigned)t / (unsigned)g.nx), i = (int)t - j * g.nx;   // edges < 2^31 (nx ny <= 2^29)
+    if (hz) {
         if (!hcut(g, vcol, i, j)) return;
+        long long t = hidx(g, i, j);
         x = (double)i + hpos[t];
         y = (double)j;
         aligned = axis == 0;
         out = hdisp + t;
-    } else if (t < nh + nv) {
-        long long e = t - nh;
-        int j = (int)((unsigned)e / (unsigned)(g.nx + 1)), i = (int)e - j * (g.nx + 1);
+    } else {
         if (!vcut(g, vcol, i, j)) return;
+        long long e = veidx(g, i, j);
         x = (double)i;
         y = (double)j + vpos[e];
         aligned = axis == 1;
         out = vdisp + e;
-    } else {
-        return;
     }
     double u = interp_bilinear(uG, g, axis, x, y);
     double d = u * dth;
@@ -371,18 +330,8 @@ __device__ inline double pick_median(double* c, int n) {
 }
 
 // vertex colours: flip once per aligned marker crossing the vertex
-__global__ void k_sweep_vertices(SweepView sv, uint8_t* __restrict__ vcol_n) {
-    const long long zo = zoff(sv.g.zs);
-    sv.vcol = zsh(sv.vcol, zo);
-    sv.hpos = zsh(sv.hpos, zo);
-    sv.vpos = zsh(sv.vpos, zo);
-    sv.hdisp = zsh(sv.hdisp, zo);
-    sv.vdisp = zsh(sv.vdisp, zo);
-    vcol_n = zsh(vcol_n, zo);
+__device__ inline void sweep_vertex(const SweepView& sv, uint8_t* vcol_n, int iv, int jv) {
     const Grid& g = sv.g;
-    int iv = blockIdx.x * blockDim.x + threadIdx.x;
-    int jv = blockIdx.y;
-    if (iv > g.nx) return;
     int l = sv.axis == 0 ? jv : iv;   // aligned line through the vertex
     int m = sv.axis == 0 ? iv : jv;   // position of the vertex along it
     int nal = sv.n_al();
@@ -398,20 +347,10 @@ __global__ void k_sweep_vertices(SweepView sv, uint8_t* __restrict__ vcol_n) {
 }
 
 // aligned edges: the markers that slid onto the edge, one kept (lower median)
-__global__ void k_sweep_aligned(SweepView sv, const uint8_t* __restrict__ vcol_n, double* __restrict__ out) {
-    const long long zo = zoff(sv.g.zs);
-    sv.vcol = zsh(sv.vcol, zo);
-    sv.hpos = zsh(sv.hpos, zo);
-    sv.vpos = zsh(sv.vpos, zo);
-    sv.hdisp = zsh(sv.hdisp, zo);
-    sv.vdisp = zsh(sv.vdisp, zo);
-    vcol_n = zsh(vcol_n, zo);
-    out = zsh(out, zo);
+// (aligned line l, index e along it; 0 <= e < n_al)
+__device__ inline void sweep_aligned(const SweepView& sv, const uint8_t* vcol_n, double* out, int l, int e) {
     const Grid& g = sv.g;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    int l = blockIdx.y;
     int nal = sv.n_al();
-    if (e >= nal) return;
     bool cut;
     long long o;
     if (sv.axis == 0) {
@@ -493,25 +432,12 @@ __device__ inline bool chain_neighbour(const SweepView& sv, const uint16_t* cseg
 
 // unaligned edges: crossings of the displaced segments with the edge's grid line, plus
 // displaced markers lying exactly on it; one kept (lower median)
-__global__ void k_sweep_unaligned(SweepView sv, const uint16_t* __restrict__ cseg,
-                                  const uint8_t* __restrict__ vcol_n, double* __restrict__ out,
-                                  int* __restrict__ status) {
-    const long long zo = zoff(sv.g.zs);
-    sv.vcol = zsh(sv.vcol, zo);
-    sv.hpos = zsh(sv.hpos, zo);
-    sv.vpos = zsh(sv.vpos, zo);
-    sv.hdisp = zsh(sv.hdisp, zo);
-    sv.vdisp = zsh(sv.vdisp, zo);
-    cseg = zsh(cseg, zo);
-    vcol_n = zsh(vcol_n, zo);
-    out = zsh(out, zo);
-    status = zsh(status, zo);
+// (unaligned line m, index e across; 0 <= e < n_ac)
+__device__ inline void sweep_unaligned(const SweepView& sv, const uint16_t* cseg, const uint8_t* vcol_n, double* out,
+                                       int* status, int m, int e) {
     const Grid& g = sv.g;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;   // index across
-    int m = blockIdx.y;                               // unaligned line
     int nac = sv.n_ac();
     int nal = sv.n_al();
-    if (e >= nac) return;
     bool cut;
     long long o;
     if (sv.axis == 0) {
@@ -581,6 +507,171 @@ __global__ void k_sweep_unaligned(SweepView sv, const uint16_t* __restrict__ cse
         }
     }
     out[o] = pick_median(cand, n);
+}
+
+// ---------------------------------------------------------------------------------
+// the sweeps over the cells near the interface (O(sqrt N) work)
+// ---------------------------------------------------------------------------------
+// The cells within two of a cut cell of the geometry at the start of the step: the narrow band
+// (cells within one of a cut cell) dilated by one more cell, with an int mark per cell (all
+// zero between steps) so that each cell enters the list once.  A marker moves less than a cell
+// per sweep, so every edge that is cut before, between or after the two sweeps is an edge of a
+// listed cell, and every vertex that can flip colour is a corner of one.
+__global__ void k_band_dilate(Grid g, const int* __restrict__ band, const int* __restrict__ nband,
+                              int* __restrict__ mark, int* __restrict__ list, int* __restrict__ count) {
+    const long long zo = zoff(g.zs);
+    band = zsh(band, zo);
+    nband = zsh(nband, zo);
+    mark = zsh(mark, zo);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    int n = *nband;
+    int lane = threadIdx.x & 31;
+    // whole warps iterate together, so that the appends can be counted with one atomic per warp
+    int stride = gridDim.x * blockDim.x;
+    int n_up = (n + 31) & ~31;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k - lane < n_up; k += stride) {
+        bool valid = k < n;
+        int i = 0, j = 0;
+        if (valid) {
+            int c = band[k];
+            j = (int)((unsigned)c / (unsigned)g.nx);
+            i = c - j * g.nx;
+        }
+        for (int q = 0; q < 9; ++q) {
+            int ii = i + q % 3 - 1, jj = j + q / 3 - 1;
+            bool in = valid && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
+            int d = in ? cidx(g, ii, jj) : 0;
+            bool add = in && atomicExch(&mark[d], 1) == 0;
+            unsigned bal = __ballot_sync(0xffffffffu, add);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(count, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (add) list[base + __popc(bal & ((1u << lane) - 1u))] = d;
+        }
+    }
+}
+
+// the marks of the listed cells back to zero (after the step's sweeps)
+__global__ void k_band_unmark(Grid g, const int* __restrict__ list, const int* __restrict__ count,
+                              int* __restrict__ mark) {
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    mark = zsh(mark, zo);
+    int n = *count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) mark[list[k]] = 0;
+}
+
+// u_Gamma (k_ug's formula) on the listed cells: the cells the markers' bilinear stencils read in
+// both sweeps of the step (a marker moves less than a cell per sweep)
+__global__ void k_ug_list(Grid g, Phys p, const int* __restrict__ list, const int* __restrict__ count,
+                          const uint8_t* __restrict__ flags, const double2* __restrict__ u_l,
+                          const double2* __restrict__ u_v, const double* __restrict__ mdot,
+                          const double2* __restrict__ nb, double2* __restrict__ uG) {
+    zphys(g, p);
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    flags = zsh(flags, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
+    mdot = zsh(mdot, zo);
+    nb = zsh(nb, zo);
+    uG = zsh(uG, zo);
+    int n = *count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int c = list[k];
+        double m = mdot[c];
+        double2 nv = nb[c];
+        if (flags[c] & F_CCOL) {
+            double cl = m / p.rho_l;
+            double2 u = u_l[c];
+            uG[c] = make_double2(u.x - cl * nv.x, u.y - cl * nv.y);
+        } else {
+            double cv = m / p.rho_v;
+            double2 u = u_v[c];
+            uG[c] = make_double2(u.x - cv * nv.x, u.y - cv * nv.y);
+        }
+    }
+}
+
+// displacement of the cut edges among the four edges of each listed cell (an edge shared by two
+// listed cells is computed by both, with the same value)
+__global__ void k_displace_list(Grid g, int axis, double dth, const int* __restrict__ list,
+                                const int* __restrict__ count, const uint8_t* __restrict__ vcol,
+                                const double* __restrict__ hpos, const double* __restrict__ vpos,
+                                const double2* __restrict__ uG, double* __restrict__ hdisp,
+                                double* __restrict__ vdisp, int* __restrict__ status) {
+    if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    vcol = zsh(vcol, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    uG = zsh(uG, zo);
+    hdisp = zsh(hdisp, zo);
+    vdisp = zsh(vdisp, zo);
+    status = zsh(status, zo);
+    int n = 4 * *count;   // one thread per (cell, edge): the work is latency-bound
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int c = list[t >> 2], q = t & 3;
+        int j = (int)((unsigned)c / (unsigned)g.nx), i = c - j * g.nx;
+        displace_edge(g, axis, dth, vcol, hpos, vpos, uG, hdisp, vdisp, status, q < 2, i + (q == 3),
+                      j + (q == 1));
+    }
+}
+
+// the four corners of each listed cell (vcol_n holds a copy of vcol elsewhere)
+__global__ void k_sweep_vertices_list(SweepView sv, const int* __restrict__ list, const int* __restrict__ count,
+                                      uint8_t* __restrict__ vcol_n) {
+    const long long zo = zoff(sv.g.zs);
+    sv.vcol = zsh(sv.vcol, zo);
+    sv.hpos = zsh(sv.hpos, zo);
+    sv.vpos = zsh(sv.vpos, zo);
+    sv.hdisp = zsh(sv.hdisp, zo);
+    sv.vdisp = zsh(sv.vdisp, zo);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    vcol_n = zsh(vcol_n, zo);
+    const Grid& g = sv.g;
+    int n = 4 * *count;   // one thread per (cell, corner)
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int c = list[t >> 2], q = t & 3;
+        int j = (int)((unsigned)c / (unsigned)g.nx), i = c - j * g.nx;
+        sweep_vertex(sv, vcol_n, i + (q & 1), j + (q >> 1));
+    }
+}
+
+// the four edges of each listed cell, aligned or unaligned for this sweep (the new marker
+// arrays are zero elsewhere); out_al / out_un are the new h- / v-edge arrays as the axis says
+__global__ void k_sweep_edges_list(SweepView sv, const int* __restrict__ list, const int* __restrict__ count,
+                                   const uint16_t* __restrict__ cseg, const uint8_t* __restrict__ vcol_n,
+                                   double* __restrict__ out_al, double* __restrict__ out_un, int* __restrict__ status) {
+    const long long zo = zoff(sv.g.zs);
+    sv.vcol = zsh(sv.vcol, zo);
+    sv.hpos = zsh(sv.hpos, zo);
+    sv.vpos = zsh(sv.vpos, zo);
+    sv.hdisp = zsh(sv.hdisp, zo);
+    sv.vdisp = zsh(sv.vdisp, zo);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    cseg = zsh(cseg, zo);
+    vcol_n = zsh(vcol_n, zo);
+    out_al = zsh(out_al, zo);
+    out_un = zsh(out_un, zo);
+    status = zsh(status, zo);
+    int n = 4 * *count;   // one thread per (cell, edge)
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int c = list[t >> 2], q = t & 3;
+        int j = (int)((unsigned)c / (unsigned)sv.g.nx), i = c - j * sv.g.nx;
+        // axis 0: aligned = horizontal edges (line j, index i), unaligned = vertical (line i, index j)
+        // axis 1: aligned = vertical edges (line i, index j), unaligned = horizontal (line j, index i)
+        int la = sv.axis == 0 ? j : i, ea = sv.axis == 0 ? i : j;
+        if (q < 2) sweep_aligned(sv, vcol_n, out_al, la + q, ea);
+        else sweep_unaligned(sv, cseg, vcol_n, out_un, status, ea + (q - 2), la);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -883,26 +974,55 @@ void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const 
     k_band<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, cseg, hpos, vpos, flags, nb);
 }
 
-void launch_ug(const Grid& g, const Phys& p, const uint8_t* flags, const double2* u_l, const double2* u_v,
-               const double* mdot, const double2* nb, double2* uG, cudaStream_t st) {
-    int n = g.nx * g.ny;
-    k_ug<<<grid1(n, 256, g.nz), 256, 0, st>>>(g, p, flags, u_l, u_v, mdot, nb, uG);
+// blocks of a kernel over the cells near the interface (four threads per cell): about 20 cells
+// per unit of interface length across the grid (nx + ny), four blocks per SM at most; the
+// kernels stride over the list, so a longer interface only takes more iterations
+static int list_blocks(const Grid& g) {
+    long long n = div_up(80LL * (g.nx + g.ny), 256);
+    return (int)(n < 4 ? 4 : (n > 4 * 152 ? 4 * 152 : n));
 }
 
-void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, const double* hpos,
-                  const double* vpos, const uint16_t* cseg, const double2* uG, double* hdisp, double* vdisp,
-                  uint8_t* vcol_n, double* hpos_n, double* vpos_n, int* status, cudaStream_t st) {
-    long long ne = (long long)(g.ny + 1) * g.nx + (long long)g.ny * (g.nx + 1);
-    k_displace<<<grid1(ne, 256, g.nz), 256, 0, st>>>(g, axis, dth, vcol, hpos, vpos, uG, hdisp, vdisp, status);
+// the same byte range of every instance of the launch (instances lie g.zs bytes apart)
+static void copy_all(void* dst, const void* src, size_t bytes, const Grid& g, cudaStream_t st) {
+    if (g.nz > 1) cudaMemcpy2DAsync(dst, (size_t)g.zs, src, (size_t)g.zs, bytes, g.nz, cudaMemcpyDeviceToDevice, st);
+    else cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+}
+static void zero_all(void* dst, size_t bytes, const Grid& g, cudaStream_t st) {
+    if (g.nz > 1) cudaMemset2DAsync(dst, (size_t)g.zs, 0, bytes, g.nz, st);
+    else cudaMemsetAsync(dst, 0, bytes, st);
+}
+
+void launch_band_dilate(const Grid& g, const int* band, const int* nband, int* mark, int* list, int* count,
+                        cudaStream_t st) {
+    zero_all(count, sizeof(int), g, st);
+    k_band_dilate<<<dim3(list_blocks(g), 1, g.nz), 256, 0, st>>>(g, band, nband, mark, list, count);
+}
+
+void launch_band_unmark(const Grid& g, const int* list, const int* count, int* mark, cudaStream_t st) {
+    k_band_unmark<<<dim3(list_blocks(g), 1, g.nz), 256, 0, st>>>(g, list, count, mark);
+}
+
+void launch_ug_list(const Grid& g, const Phys& p, const int* list, const int* count, const uint8_t* flags,
+                    const double2* u_l, const double2* u_v, const double* mdot, const double2* nb, double2* uG,
+                    cudaStream_t st) {
+    k_ug_list<<<dim3(list_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, list, count, flags, u_l, u_v, mdot, nb, uG);
+}
+
+void launch_sweep(const Grid& g, int axis, double dth, const int* list, const int* count, const uint8_t* vcol,
+                  const double* hpos, const double* vpos, const uint16_t* cseg, const double2* uG, double* hdisp,
+                  double* vdisp, uint8_t* vcol_n, double* hpos_n, double* vpos_n, int* status, cudaStream_t st) {
+    int nb_ = list_blocks(g);
+    k_displace_list<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(g, axis, dth, list, count, vcol, hpos, vpos, uG, hdisp,
+                                                         vdisp, status);
+    size_t nv = (size_t)(g.nx + 1) * (g.ny + 1), nh = (size_t)(g.ny + 1) * g.nx, nve = (size_t)g.ny * (g.nx + 1);
+    copy_all(vcol_n, vcol, nv, g, st);
     SweepView sv{g, axis, vcol, hpos, vpos, hdisp, vdisp};
-    k_sweep_vertices<<<rows_grid(g.nx + 1, g.ny + 1, 128, g.nz), 128, 0, st>>>(sv, vcol_n);
-    if (axis == 0) {
-        k_sweep_aligned<<<rows_grid(g.nx, g.ny + 1, 128, g.nz), 128, 0, st>>>(sv, vcol_n, hpos_n);
-        k_sweep_unaligned<<<rows_grid(g.ny, g.nx + 1, 128, g.nz), 128, 0, st>>>(sv, cseg, vcol_n, vpos_n, status);
-    } else {
-        k_sweep_aligned<<<rows_grid(g.ny, g.nx + 1, 128, g.nz), 128, 0, st>>>(sv, vcol_n, vpos_n);
-        k_sweep_unaligned<<<rows_grid(g.nx, g.ny + 1, 128, g.nz), 128, 0, st>>>(sv, cseg, vcol_n, hpos_n, status);
-    }
+    k_sweep_vertices_list<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(sv, list, count, vcol_n);
+    zero_all(hpos_n, nh * sizeof(double), g, st);
+    zero_all(vpos_n, nve * sizeof(double), g, st);
+    k_sweep_edges_list<<<dim3(nb_, 1, g.nz), 256, 0, st>>>(sv, list, count, cseg, vcol_n,
+                                                           axis == 0 ? hpos_n : vpos_n,
+                                                           axis == 0 ? vpos_n : hpos_n, status);
 }
 
 void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,

@@ -16,11 +16,16 @@ void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, 
                         uint8_t* flags, double* vf, cudaStream_t st);
 void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, uint8_t* flags,
                  double2* nb, cudaStream_t st);
-void launch_ug(const Grid& g, const Phys& p, const uint8_t* flags, const double2* u_l, const double2* u_v,
-               const double* mdot, const double2* nb, double2* uG, cudaStream_t st);
-void launch_sweep(const Grid& g, int axis, double dth, const uint8_t* vcol, const double* hpos, const double* vpos,
-                  const uint16_t* cseg, const double2* uG, double* hdisp, double* vdisp, uint8_t* vcol_n,
-                  double* hpos_n, double* vpos_n, int* status, cudaStream_t st);
+void launch_sweep(const Grid& g, int axis, double dth, const int* list, const int* count, const uint8_t* vcol,
+                  const double* hpos, const double* vpos, const uint16_t* cseg, const double2* uG, double* hdisp,
+                  double* vdisp, uint8_t* vcol_n, double* hpos_n, double* vpos_n, int* status, cudaStream_t st);
+// the cells within two of a cut cell (from the narrow-band list), their marks cleared after use
+void launch_band_dilate(const Grid& g, const int* band, const int* nband, int* mark, int* list, int* count,
+                        cudaStream_t st);
+void launch_band_unmark(const Grid& g, const int* list, const int* count, int* mark, cudaStream_t st);
+void launch_ug_list(const Grid& g, const Phys& p, const int* list, const int* count, const uint8_t* flags,
+                    const double2* u_l, const double2* u_v, const double* mdot, const double2* nb, double2* uG,
+                    cudaStream_t st);
 void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, const uint16_t* cseg,
                             const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
                             double* cd, double* dd, double* wl, double* wb, double* b, double* x0, cudaStream_t st);

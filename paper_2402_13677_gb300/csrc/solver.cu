@@ -688,18 +688,19 @@ __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, co
     tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 4, 0>(R, C, k, ry0, act);
-    double dot[2] = {0.0, 0.0};
+    // r.z of the thread's (at most four) core cells: summed in T, then one conversion
+    T dot[2] = {T(0), T(0)};
     if (act)
         tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
             Vec<T, NR> xv;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 xv.v[k2] = C.x[r][c][k2];
-                if (DOT) dot[k2] += (double)xv.v[k2] * (double)C.b[r][c][k2];
+                if (DOT) dot[k2] += xv.v[k2] * C.b[r][c][k2];
             }
             reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
         });
-    return make_double2(dot[0], dot[1]);
+    return make_double2((double)dot[0], (double)dot[1]);
 }
 
 // k_post: one tile per block; at the finest level also r.z -> beta
@@ -1272,6 +1273,46 @@ __global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* _
 
 // ---- CG kernels ---------------------------------------------------------------------------
 // p_new = z + beta p_old; q = A p_new; p.q -> alpha = r.z / p.q
+// Dot-product accumulation of a thread: FP64 for FP64 data; for FP32 data the products are
+// summed in FP32 over chunks of 8 terms and each chunk added to the FP64 total (one FP64 add per
+// 8 cells: FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU).  The inner
+// FP32 solves of the refinement work on a residual scaled to values of order one (k_ir_residual),
+// so FP32 products neither underflow nor overflow there.
+template <typename T, int NR>
+struct DotAcc {
+    double tot[NR];
+    __device__ DotAcc() {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) tot[k] = 0.0;
+    }
+    __device__ void add(int k, T a, T b) { tot[k] += (double)a * (double)b; }
+    __device__ void flush() {}
+};
+template <int NR>
+struct DotAcc<float, NR> {
+    double tot[NR];
+    float part[NR];
+    int n = 0;
+    __device__ DotAcc() {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) { tot[k] = 0.0; part[k] = 0.0f; }
+    }
+    __device__ void add(int k, float a, float b) { part[k] = fmaf(a, b, part[k]); }
+    // call once per cell, after its NR products
+    __device__ void next() {
+        if (++n == 8) flush();
+    }
+    __device__ void flush() {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) { tot[k] += (double)part[k]; part[k] = 0.0f; }
+        n = 0;
+    }
+};
+template <typename T, int NR>
+__device__ inline void dot_next(DotAcc<T, NR>&) {}
+template <int NR>
+__device__ inline void dot_next(DotAcc<float, NR>& d) { d.next(); }
+
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z, T* __restrict__ p0,
                                                 T* __restrict__ p1, T* __restrict__ q, SolveState* st,
@@ -1296,9 +1337,7 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
 #pragma unroll
     for (int k = 0; k < NR; ++k) beta[k] = (T)st->beta[k];
     int N = L.nx * L.ny;
-    double acc[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+    DotAcc<T, NR> acc;
 #pragma unroll 2
     for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
         int c = cw.c, i = cw.i, j = cw.j;
@@ -1338,12 +1377,14 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
                 qv.v[k] += w * (pc.v[k] - a.v[k]);
         }
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] += (double)pc.v[k] * (double)qv.v[k];
+        for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
+        dot_next(acc);
         Pn[c] = pc;
         Q[c] = qv;
     }
+    acc.flush();
     double tot[NR];
-    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+    if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
             st->pq[k] = tot[k];
@@ -1376,9 +1417,7 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
     T alpha[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) alpha[k] = (T)st->alpha[k];
-    double acc[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+    DotAcc<T, NR> acc;
 #pragma unroll 4
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
@@ -1386,13 +1425,15 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
         for (int k = 0; k < NR; ++k) {
             xv.v[k] += alpha[k] * pv.v[k];
             rv.v[k] -= alpha[k] * qv.v[k];
-            acc[k] += (double)rv.v[k] * (double)rv.v[k];
+            acc.add(k, rv.v[k], rv.v[k]);
         }
+        dot_next(acc);
         X[c] = xv;
         Rr[c] = rv;
     }
+    acc.flush();
     double tot[NR];
-    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+    if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
         bool done = true, bad = false;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
@@ -1485,6 +1526,14 @@ k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__
     }
 }
 
+// power of two s that brings cell values whose sum of squares over n cells is rr to order one
+__device__ inline double unit_scale(double rr, int n) {
+    double m = sqrt(rr / (double)n);
+    int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+    e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+    return ldexp(1.0, -e);
+}
+
 // refinement start: b.b and the outer tolerance
 template <int NR>
 __global__ void __launch_bounds__(256) k_ir_init(int N, long long zs, const double* __restrict__ b, SolveState* st,
@@ -1510,6 +1559,7 @@ __global__ void __launch_bounds__(256) k_ir_init(int N, long long zs, const doub
             double bb = k < NR ? tot[k] : 0.0;
             st->obb[k] = bb;
             st->otol2[k] = rtol2 * (bb > 1e-300 ? bb : 1e-300);
+            st->scale_next[k] = unit_scale(bb, N);
         }
         st->odone = 0;
         st->oiters = 0;
@@ -1544,6 +1594,12 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
     ticket = zsh(ticket, zo);
     if (st->odone) return;
     int N = L.nx * L.ny;
+    // the inner FP32 system is solved for s r, s a power of two that brings the residual's
+    // cell values to order one, set from the previous residual norm (of b on the first pass) by
+    // the launch that computed it: the same in every block
+    double sc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) sc[k] = st->scale_next[k];
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
@@ -1572,7 +1628,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
         for (int k = 0; k < NR; ++k) {
             double rv = bv.v[k] - s.v[k];
             acc[k] += rv * rv;
-            rf.v[k] = (float)rv;
+            rf.v[k] = (float)(rv * sc[k]);
             ez.v[k] = 0.0f;
         }
         reinterpret_cast<Vec<float, NR>*>(r32)[c] = rf;
@@ -1586,10 +1642,13 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
             st->orr[k] = rr;
             if (!(rr <= st->otol2[k])) done = false;
             if (!isfinite(rr) || !isfinite(st->obb[k])) st->nonfinite = 1;
-            st->rr[k] = rr;
+            double s2 = k < NR ? sc[k] * sc[k] : 1.0;
+            st->scale[k] = k < NR ? sc[k] : 1.0;
+            st->scale_next[k] = unit_scale(rr, N);
+            st->rr[k] = rr * s2;
             // the inner solve reduces the residual by inner_rtol, but never below half the
-            // outer target: no solve past what the refinement needs
-            st->tol2[k] = fmax(st->inner_rtol * st->inner_rtol * rr, 0.25 * st->otol2[k]);
+            // outer target: no solve past what the refinement needs (in the scaled units)
+            st->tol2[k] = fmax(st->inner_rtol * st->inner_rtol * rr, 0.25 * st->otol2[k]) * s2;
             st->rz[k] = 0.0;
             st->beta[k] = 0.0;
         }
@@ -1612,8 +1671,9 @@ __global__ void k_ir_update(int N, long long zs, double* __restrict__ x, const f
     e = zsh(e, zo);
     st = zsh(st, zo);
     if (st->odone) return;
+    double inv[2] = {1.0 / st->scale[0], NR > 1 ? 1.0 / st->scale[1] : 1.0};   // powers of two: exact
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N * NR; c += gridDim.x * blockDim.x)
-        x[c] += (double)e[c];
+        x[c] += (double)e[c] * inv[NR > 1 ? (c & 1) : 0];
 }
 
 // ---------------------------------------------------------------------------------------

@@ -38,6 +38,8 @@ struct SolveState {
     double inner_rtol;
     int fault;         // nonzero: a bounded wait gave up (TMA copies that never landed, a grid barrier)
     int nonfinite;     // nonzero: a residual norm was NaN or infinite (the solve stopped there)
+    double scale[2];   // refinement: the inner FP32 system is solved for scale * r (a power of two)
+    double scale_next[2];   // the scale the next refinement pass uses (from the latest residual norm)
 };
 
 // TMA descriptors of one tiled level (precision and right-hand-side count fixed): the level's

@@ -51,6 +51,25 @@ D1, D2 = 1.5, 2.5
 
 
 # --------------------------------------------------------------------------
+# axisymmetric metric (Sec. 3.4-3.7 run axisymmetric)
+# --------------------------------------------------------------------------
+def metric(pb):
+    """Radius in cells of the cell centres [ny, nx], x-faces [ny, nx+1] and y-faces [ny+1, nx]
+    (x is the radius r; a ring of radius r has 2 pi r times the planar area or length); all ones
+    for a planar problem.  Every integrated balance -- a row of the energy, viscous and Poisson
+    systems, a volume, a face flux -- is multiplied by the radius of the cell or face it lives
+    on; the axis faces (r = 0) carry no flux."""
+    ny, nx = pb.ny, pb.nx
+    if not pb.axi:
+        return np.ones((ny, nx)), np.ones((ny, nx + 1)), np.ones((ny + 1, nx))
+    r0 = pb.x0 / pb.h
+    mc = np.tile(r0 + np.arange(nx) + 0.5, (ny, 1))
+    mfx = np.tile(r0 + np.arange(nx + 1, dtype=float), (ny, 1))
+    mfy = np.tile(r0 + np.arange(nx) + 0.5, (ny + 1, 1))
+    return mc, mfx, mfy
+
+
+# --------------------------------------------------------------------------
 # boundary ghost layers
 # --------------------------------------------------------------------------
 def pad_scalar(F, sides, layers=2):
@@ -199,20 +218,21 @@ def assemble_energy(geom, Tstar_l, Tstar_v, pb):
       - sum_regular lambda_k T_j = h^2 (rho cp)_k / dt T*_i + sum_cut lambda_k T_sat / theta + sum 2 lambda_k T_w
     """
     nx, ny, h = pb.nx, pb.ny, pb.h
+    mc, mfx, mfy = metric(pb)
     th = link_thetas(geom, pb.theta_min)
     liq = geom.ccol == 1
     lam = np.where(liq, pb.lam_l, pb.lam_v)
     rc = np.where(liq, pb.rho_l * pb.cp_l, pb.rho_v * pb.cp_v)
-    coef = h * h * rc / pb.dt
+    coef = h * h * rc / pb.dt * mc
     diag = coef.copy()
     b = coef * np.where(liq, Tstar_l, Tstar_v)
     idx = np.arange(nx * ny).reshape(ny, nx)
     rows, cols, vals = [], [], []
     # regular links between two cells of the same phase
     sx = geom.ccol[:, :-1] == geom.ccol[:, 1:]
-    wx = np.where(sx, lam[:, :-1], 0.0)
+    wx = np.where(sx, lam[:, :-1], 0.0) * mfx[:, 1:-1]
     sy = geom.ccol[:-1, :] == geom.ccol[1:, :]
-    wy = np.where(sy, lam[:-1, :], 0.0)
+    wy = np.where(sy, lam[:-1, :], 0.0) * mfy[1:-1, :]
     diag[:, :-1] += wx
     diag[:, 1:] += wx
     diag[:-1, :] += wy
@@ -224,7 +244,8 @@ def assemble_energy(geom, Tstar_l, Tstar_v, pb):
         vals += [-w[m], -w[m]]
     # cut links: Dirichlet T_sat at distance theta h
     for (j, i, side), t in th.items():
-        lk = lam[j, i]
+        mf = (mfx[j, i + 1], mfx[j, i], mfy[j + 1, i], mfy[j, i])[side]   # the face the link crosses
+        lk = lam[j, i] * mf
         diag[j, i] += lk / t
         b[j, i] += lk * pb.T_sat / t
     # domain walls with fixed temperature
@@ -232,8 +253,9 @@ def assemble_energy(geom, Tstar_l, Tstar_v, pb):
         if Tb is None:
             continue
         sl = {0: (slice(None), 0), 1: (slice(None), nx - 1), 2: (0, slice(None)), 3: (ny - 1, slice(None))}[side]
-        diag[sl] += 2.0 * lam[sl]
-        b[sl] += 2.0 * lam[sl] * Tb
+        mf = (mfx[:, 0], mfx[:, -1], mfy[0, :], mfy[-1, :])[side]
+        diag[sl] += 2.0 * lam[sl] * mf
+        b[sl] += 2.0 * lam[sl] * mf * Tb
     rows.append(idx.ravel())
     cols.append(idx.ravel())
     vals.append(diag.ravel())

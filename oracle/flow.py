@@ -67,7 +67,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .energy import advect, velocity_sides
+from .energy import advect, metric, velocity_sides
 from .geometry import segment_data
 
 WALL, OUTFLOW, SYMMETRY = 0, 1, 2
@@ -179,7 +179,10 @@ def curvature(pb, geom):
             if not ks:
                 continue
             L = math.hypot(Qg[0] - Pg[0], Qg[1] - Pg[1])
-            num += L * sum(ks) / len(ks)
+            k2 = sum(ks) / len(ks)
+            if pb.axi:   # the azimuthal curvature n_r / r at the segment's midpoint (grid units)
+                k2 += ((Qg[1] - Pg[1]) / L) / (pb.x0 / pb.h + 0.5 * (Pg[0] + Qg[0]))
+            num += L * k2
             den += L
         if den > 0.0:
             kap[j, i] = num / den / pb.h
@@ -261,16 +264,22 @@ def _side_slices(nx, ny):
 
 
 def viscous_matrix(pb, rho_c, mu_c, comp):
-    """(h^2 rho_c / dt) u + sum_f mu_f (u_i - u_j) + Dirichlet boundary faces 2 mu u_i."""
+    """(h^2 rho_c / dt) u + sum_f mu_f (u_i - u_j) + Dirichlet boundary faces 2 mu u_i; axisymmetric:
+    every term times the radius (in cells) of its cell or face, and the radial component's hoop
+    term mu u_r / r^2 of the vector Laplacian (mu_c / m_c per cell in these units)."""
     ny, nx = rho_c.shape
     h = pb.h
-    wx = 0.5 * (mu_c[:, :-1] + mu_c[:, 1:])
-    wy = 0.5 * (mu_c[:-1, :] + mu_c[1:, :])
-    extra = h * h * rho_c / pb.dt
+    mc, mfx, mfy = metric(pb)
+    wx = 0.5 * (mu_c[:, :-1] + mu_c[:, 1:]) * mfx[:, 1:-1]
+    wy = 0.5 * (mu_c[:-1, :] + mu_c[1:, :]) * mfy[1:-1, :]
+    extra = h * h * rho_c / pb.dt * mc
     sl = _side_slices(nx, ny)
+    mb = (mfx[:, 0], mfx[:, -1], mfy[0, :], mfy[-1, :])
     for s, (mode, _) in enumerate(velocity_sides(pb.bc, comp)):
         if mode == "odd":
-            extra[sl[s]] += 2.0 * mu_c[sl[s]]
+            extra[sl[s]] += 2.0 * mu_c[sl[s]] * mb[s]
+    if pb.axi and comp == 0:
+        extra += mu_c / mc
     return _five_point(nx, ny, wx, wy, extra)
 
 
@@ -280,7 +289,7 @@ def predictor(st, gc):
     ny, nx = pb.ny, pb.nx
     h, dt = pb.h, pb.dt
     rho_c, mu_c = mixture(pb, g.vf)
-    coef = h * h * rho_c / dt
+    coef = h * h * rho_c / dt * metric(pb)[0]
     ustar = {}
     for name, u in (("l", st.u_l), ("v", st.u_v)):
         ustar[name] = np.empty_like(u)
@@ -320,25 +329,28 @@ def predictor(st, gc):
 # --------------------------------------------------------------------------
 def poisson_matrix(pb, rfx, rfy):
     ny, nx = rfx.shape[0], rfy.shape[1]
-    wx = pb.dt / rfx[:, 1:-1]
-    wy = pb.dt / rfy[1:-1, :]
+    mc, mfx, mfy = metric(pb)
+    wx = pb.dt / rfx[:, 1:-1] * mfx[:, 1:-1]
+    wy = pb.dt / rfy[1:-1, :] * mfy[1:-1, :]
     extra = np.zeros((ny, nx))
     if pb.bc[0] == OUTFLOW:
-        extra[:, 0] += 2.0 * pb.dt / rfx[:, 0]
+        extra[:, 0] += 2.0 * pb.dt / rfx[:, 0] * mfx[:, 0]
     if pb.bc[1] == OUTFLOW:
-        extra[:, -1] += 2.0 * pb.dt / rfx[:, -1]
+        extra[:, -1] += 2.0 * pb.dt / rfx[:, -1] * mfx[:, -1]
     if pb.bc[2] == OUTFLOW:
-        extra[0, :] += 2.0 * pb.dt / rfy[0, :]
+        extra[0, :] += 2.0 * pb.dt / rfy[0, :] * mfy[0, :]
     if pb.bc[3] == OUTFLOW:
-        extra[-1, :] += 2.0 * pb.dt / rfy[-1, :]
+        extra[-1, :] += 2.0 * pb.dt / rfy[-1, :] * mfy[-1, :]
     return _five_point(nx, ny, wx, wy, extra)
 
 
 def poisson_rhs(pb, ccol, faces):
-    """-h times the undivided divergence of the face field of each cell's phase (ghost-fluid Poisson equation)."""
+    """-h times the undivided divergence of the face field of each cell's phase (ghost-fluid Poisson
+    equation); axisymmetric: the face fluxes weighted by their radius."""
+    mc, mfx, mfy = metric(pb)
     div = {}
     for name, (fx, fy) in faces.items():
-        div[name] = (fx[:, 1:] - fx[:, :-1]) + (fy[1:, :] - fy[:-1, :])
+        div[name] = (mfx[:, 1:] * fx[:, 1:] - mfx[:, :-1] * fx[:, :-1]) + mc * (fy[1:, :] - fy[:-1, :])
     return -pb.h * np.where(ccol == 1, div["l"], div["v"])
 
 
@@ -347,8 +359,9 @@ def phase_change_source(pb, geom, mdot):
     in the cut cells, S_Gamma = (length of the cell's segments in grid units) h."""
     src = np.zeros((pb.ny, pb.nx))
     jump = 1.0 / pb.rho_v - 1.0 / pb.rho_l
-    for (j, i), _, _, L in segment_data(geom):
-        src[j, i] += mdot[j, i] * L * pb.h * jump
+    for (j, i), (mx, my), _, L in segment_data(geom):
+        m = (pb.x0 / pb.h + mx) if pb.axi else 1.0     # the segment's radius (axisymmetric)
+        src[j, i] += mdot[j, i] * L * pb.h * jump * m
     return src
 
 

@@ -13,7 +13,8 @@ Diagnostics (S13): vapour volume, the volume the mass flux should have added,
 M_d (mass-in-domain equation) and the outlet mass of M_c (mass-with-outflow
 equation); for film boiling (Sec. 3.7) the vapour volume that left through the
 outflow boundaries (the V_bc of the dimensionless vapour volume) and the
-space-averaged Nusselt number of the heated wall.
+space-averaged Nusselt number of the heated wall.  Axisymmetric problems report
+volumes, masses and fluxes of the full ring (2 pi r times the planar measure).
 
 Readings of the two film-boiling quantities (the paper gives the integrals only):
   * V_bc per step: over the outflow boundary faces, (1 - H) u_f . n h dt with H
@@ -144,13 +145,16 @@ def diagnostics(st):
     vapour volume out of the outflow boundaries this step, wall Nusselt number]."""
     pb, g = st.pb, st.geom
     h2 = pb.h * pb.h
-    Vv = float(np.sum(1.0 - g.vf)) * h2
+    # volumes and face areas: per unit depth (planar) or of the ring, 2 pi r times (axisymmetric)
+    mc, mfx, mfy = energy.metric(pb)
+    ring = 2.0 * math.pi * pb.h if pb.axi else 1.0
+    Vv = float(np.sum((1.0 - g.vf) * mc)) * h2 * ring
     mS = 0.0
-    for (j, i), _, _, L in segment_data(g):
-        mS += st.mdot[j, i] * L * pb.h
+    for (j, i), (mx, my), _, L in segment_data(g):
+        mS += st.mdot[j, i] * L * pb.h * ((pb.x0 / pb.h + mx) * ring if pb.axi else 1.0)
     dV = mS * pb.dt / pb.rho_v
     rho_c, _ = flow.mixture(pb, g.vf)
-    Md = float(np.sum(rho_c)) * h2
+    Md = float(np.sum(rho_c * mc)) * h2 * ring
     out = 0.0
     ccol = g.ccol
     for s, kind in enumerate(pb.bc):
@@ -158,17 +162,17 @@ def diagnostics(st):
             continue
         if s == 0:
             u = np.where(ccol[:, 0] == 1, st.ufx_l[:, 0], st.ufx_v[:, 0])
-            out += float(np.sum(-rho_c[:, 0] * u))
+            out += float(np.sum(-rho_c[:, 0] * u * mfx[:, 0]))
         elif s == 1:
             u = np.where(ccol[:, -1] == 1, st.ufx_l[:, -1], st.ufx_v[:, -1])
-            out += float(np.sum(rho_c[:, -1] * u))
+            out += float(np.sum(rho_c[:, -1] * u * mfx[:, -1]))
         elif s == 2:
             u = np.where(ccol[0, :] == 1, st.ufy_l[0, :], st.ufy_v[0, :])
-            out += float(np.sum(-rho_c[0, :] * u))
+            out += float(np.sum(-rho_c[0, :] * u * mfy[0, :]))
         else:
             u = np.where(ccol[-1, :] == 1, st.ufy_l[-1, :], st.ufy_v[-1, :])
-            out += float(np.sum(rho_c[-1, :] * u))
-    out *= pb.h * pb.dt
+            out += float(np.sum(rho_c[-1, :] * u * mfy[-1, :]))
+    out *= pb.h * pb.dt * ring
     # vapour volume through the outflow faces, and the heat flux of the fixed-temperature walls
     vout, flux, nf = 0.0, 0.0, 0
     for s, kind in enumerate(pb.bc):
@@ -177,16 +181,18 @@ def diagnostics(st):
         if kind == flow.OUTFLOW:
             if s < 2:
                 u = np.where(liq, st.ufx_l[:, 0 if s == 0 else -1], st.ufx_v[:, 0 if s == 0 else -1])
+                mf = mfx[:, 0 if s == 0 else -1]
             else:
                 u = np.where(liq, st.ufy_l[0 if s == 2 else -1, :], st.ufy_v[0 if s == 2 else -1, :])
+                mf = mfy[0 if s == 2 else -1, :]
             sign = -1.0 if s in (0, 2) else 1.0
-            vout += float(np.sum((1.0 - g.vf[cells]) * sign * u))
+            vout += float(np.sum((1.0 - g.vf[cells]) * sign * u * mf))
         if pb.T_bc[s] is not None and kind == flow.WALL:
             Tw = float(pb.T_bc[s])
             Ti = np.where(liq, st.T_l[cells], st.T_v[cells])
             flux += float(np.sum(2.0 * (Tw - Ti) / pb.h))
             nf += Ti.size
-    vout *= pb.h * pb.dt
+    vout *= pb.h * pb.dt * ring
     nu = 0.0
     if nf:
         Tw = next(float(v) for s, v in enumerate(pb.T_bc) if v is not None and pb.bc[s] == flow.WALL)

@@ -71,6 +71,8 @@ class Problem:
     sweep_order: int = 1          # 0: always x then y; 1: alternate
     energy: bool = True           # False: mdot imposed (constant-mass-flux bubble)
     mdot_fixed: float = 0.0
+    axi: bool = False             # True: axisymmetric, x is the radius (the axis at x = 0 is the
+                                  # left side, a symmetry side), y the axial coordinate
     one_fluid: bool = False       # True: one velocity field and the phase-change source S_pc
                                   # (Sec. 2.2-2.3) instead of ghost velocities; the vapour
                                   # velocity arrays then repeat the liquid ones
@@ -112,6 +114,43 @@ def stefan_position(t, beta, alpha_v):
 
 def stefan_temperature(x, t, beta, alpha_v, T_w, T_sat):
     return T_w + (T_sat - T_w) / math.erf(beta) * special.erf(x / (2.0 * np.sqrt(alpha_v * t)))
+
+
+def _scriven_integrand(xi, beta, eps):
+    return math.exp(-beta * beta * ((1.0 - xi) ** -2 - 2.0 * eps * xi - 1.0))
+
+
+def scriven_beta(rho_l, rho_v, cp_l, cp_v, dT, h_lg) -> float:
+    """Growth constant of a spherical bubble in superheated liquid (Scriven; Sec. 3.4): the root of
+    rho_l cp_l dT / (rho_v (h_lg + (cp_l - cp_v) dT)) = 2 beta^2 int_0^1 exp(-beta^2 ((1 - xi)^-2
+    - 2 eps xi - 1)) d xi with eps = 1 - rho_v / rho_l (the exponent of the temperature equation;
+    the growth-constant equation prints 1 - rho_l / rho_v, for which no root exists)."""
+    from scipy import integrate
+    lhs = rho_l * cp_l * dT / (rho_v * (h_lg + (cp_l - cp_v) * dT))
+    eps = 1.0 - rho_v / rho_l
+
+    def f(b):
+        val, _ = integrate.quad(_scriven_integrand, 0.0, 1.0, args=(b, eps), epsabs=0.0, epsrel=1e-13, limit=400)
+        return 2.0 * b * b * val - lhs
+    return optimize.brentq(f, 1e-6, 100.0, xtol=1e-14, rtol=1e-14, maxiter=500)
+
+
+def scriven_temperature(r, t, beta, rho_l, rho_v, cp_l, cp_v, dT, h_lg, alpha_l, T_inf):
+    """Liquid temperature of the Scriven problem (Sec. 3.4, temperature equation) at radius r >= R."""
+    from scipy import integrate
+    R = 2.0 * beta * math.sqrt(alpha_l * t)
+    eps = 1.0 - rho_v / rho_l
+    pref = 2.0 * beta * beta * rho_v * (h_lg + (cp_l - cp_v) * dT) / (rho_l * cp_l)
+    out = np.empty_like(np.asarray(r, dtype=float))
+    flat = out.reshape(-1)
+    for k, rv in enumerate(np.asarray(r, dtype=float).reshape(-1)):
+        if rv <= R:
+            flat[k] = T_inf - dT
+            continue
+        val, _ = integrate.quad(_scriven_integrand, 1.0 - R / rv, 1.0, args=(beta, eps), epsabs=0.0,
+                                epsrel=1e-12, limit=400)
+        flat[k] = T_inf - pref * val
+    return out
 
 
 def sucking_beta(rho_l, rho_v, lam_l, lam_v, cp_l, cp_v, dT, h_lg) -> float:
@@ -254,6 +293,72 @@ def stefan(nx=64, ny=64, X0=0.1, Lx=1.0, rho_l=10.0, rho_v=1.0, St=0.1, dT=1.0,
     pb.meta.update(mdot0=mdot, U=U)
     pb.u_l[..., 0] = U
     pb.ufx_l[:, 1:] = U          # the wall face stays 0
+    return pb
+
+
+def axi_const_mdot_bubble(n=48, L=1.0, R0=0.3, mdot=0.1, rho_l=10.0, rho_v=1.0, mu=0.01, dt=None, cfl=0.3,
+                          steps=4, **kw) -> Problem:
+    """A spherical bubble centred on the axis with an imposed constant mass flux, energy off
+    (Sec. 3.3 in the axisymmetric configuration of Sec. 3.4): a quarter of it on [0, L]^2, the
+    axis on the left and a symmetry plane at the bottom, outflow top and right.  Its radius
+    grows as R0 + mdot t / rho_v."""
+    h = L / n
+    if dt is None:
+        dt = cfl * h * rho_v / abs(mdot)
+    pb = Problem("axi_const_mdot_bubble", n, n, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v, mu_l=mu, mu_v=mu,
+                 T_sat=0.0, h_lg=1.0, bc=(SYMMETRY, OUTFLOW, SYMMETRY, OUTFLOW), T_bc=(None,) * 4, energy=False,
+                 mdot_fixed=mdot, axi=True, **kw)
+    pb.meta.update(R0=R0, mdot=mdot)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: np.hypot(x, y) - R0, n, n, h)
+    pb.T_l = np.zeros((n, n))
+    pb.T_v = np.zeros((n, n))
+    _zero_flow(pb)
+    return pb
+
+
+def scriven(n=64, L=1.0, R0=0.3, rho_ratio=20.0, k_ratio=5.0, St=0.25, dT=1.0, mu=0.01, dt=None, steps=4,
+            **kw) -> Problem:
+    """Scriven problem (Sec. 3.4): a spherical vapour bubble at T_sat growing in superheated liquid,
+    axisymmetric quarter on [0, L]^2 (axis left, symmetry bottom, outflow top and right), initial
+    state from the similarity solution at the time the radius is R0: liquid temperature of the
+    temperature equation, radial liquid velocity eps R R' R^2 / r^2 (eps = 1 - rho_v / rho_l),
+    vapour at rest at T_sat.  Nondimensional, cp = 1 both phases, lambda_v = 1."""
+    h = L / n
+    rho_v, rho_l = 1.0, rho_ratio
+    lam_v, lam_l = 1.0, k_ratio
+    h_lg = 1.0 * dT / St
+    beta = scriven_beta(rho_l, rho_v, 1.0, 1.0, dT, h_lg)
+    alpha_l = lam_l / rho_l
+    t0 = (R0 / (2.0 * beta)) ** 2 / alpha_l
+    Rdot = beta * math.sqrt(alpha_l / t0)
+    if dt is None:
+        dt = 0.2 * h / Rdot
+    pb = Problem("scriven", n, n, h, dt=dt, steps=steps, rho_l=rho_l, rho_v=rho_v, mu_l=mu, mu_v=mu, lam_l=lam_l,
+                 lam_v=lam_v, cp_l=1.0, cp_v=1.0, T_sat=0.0, h_lg=h_lg, bc=(SYMMETRY, OUTFLOW, SYMMETRY, OUTFLOW),
+                 T_bc=(None,) * 4, axi=True, **kw)
+    eps = 1.0 - rho_v / rho_l
+    pb.t0 = t0
+    pb.meta.update(beta=beta, alpha_l=alpha_l, R0=R0, Rdot0=Rdot, eps=eps)
+    pb.vcol, pb.hx_cut, pb.hx_pos, pb.vy_cut, pb.vy_pos = interface_from_levelset(
+        lambda x, y: np.hypot(x, y) - R0, n, n, h)
+    (Xc, Yc), (Xfx, Yfx), (Xfy, Yfy) = _grids(n, n, h, 0.0, 0.0)
+    r = np.hypot(Xc, Yc)
+    pb.T_l = scriven_temperature(r, t0, beta, rho_l, rho_v, 1.0, 1.0, dT, h_lg, alpha_l, dT)
+    pb.T_v = np.zeros((n, n))
+    _zero_flow(pb)
+
+    def radial(X, Y):
+        rr = np.hypot(X, Y)
+        mag = np.where(rr >= R0, eps * Rdot * R0 * R0 / np.maximum(rr, 1e-300) ** 2, eps * Rdot * rr / R0)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            ex = np.where(rr > 0, X / np.maximum(rr, 1e-300), 0.0)
+            ey = np.where(rr > 0, Y / np.maximum(rr, 1e-300), 0.0)
+        return mag * ex, mag * ey
+
+    pb.u_l[..., 0], pb.u_l[..., 1] = radial(Xc, Yc)
+    pb.ufx_l[:] = radial(Xfx, Yfx)[0]
+    pb.ufy_l[:] = radial(Xfy, Yfy)[1]
     return pb
 
 

@@ -668,3 +668,62 @@ def test_static_bubble_laplace_pressure():
     jump = st.p[r < R - 3 * h].mean() - st.p[r > R + 3 * h].mean()
     assert abs(jump * R / sigma - 1.0) < 5e-3
     assert max(np.abs(st.u_l).max(), np.abs(st.u_v).max()) < 1e-3 * sigma / 1.0
+
+
+# ------------------------------------------------------------------ axisymmetric metric
+def _axi_single_phase(n, bc, rho=3.0, mu=0.2, dt=1e-3, lam=1.0):
+    pb = w.stefan(n, n, X0=0.5, Lx=1.0, dt=dt, steps=0)
+    pb.axi = True
+    pb.bc = bc
+    pb.T_bc = (None, None, None, None)
+    pb.rho_l = pb.rho_v = rho
+    pb.mu_l = pb.mu_v = mu
+    pb.lam_l = pb.lam_v = lam
+    pb.energy, pb.mdot_fixed = False, 0.0
+    pb.vcol = np.ones((n + 1, n + 1), np.uint8)
+    pb.hx_pos = np.zeros((n + 1, n))
+    pb.vy_pos = np.zeros((n, n + 1))
+    for k in ("u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v", "p", "T_l", "T_v"):
+        setattr(pb, k, np.zeros_like(getattr(pb, k)))
+    st = S.State(pb)
+    st.geom = geometry.reconstruct(st.vcol, st.hx_pos, st.vy_pos)
+    return pb, st
+
+
+def test_axisymmetric_diffusion_operator_exact_for_quadratics():
+    """The energy system's radius-weighted five-point operator (the axisymmetric Laplacian
+    (1/r) d/dr (r dT/dr) + d2T/dz2 times the ring cell's weight r h^2) is exact for
+    T = a r^2 + b z^2 + c, the axis cells included: the row of cell i gives -lambda h^2 r_i/h
+    (4 a + 2 b).  Planar weights give 2 a instead of 4 a."""
+    n = 16
+    pb, st = _axi_single_phase(n, (flow.SYMMETRY, flow.OUTFLOW, flow.SYMMETRY, flow.OUTFLOW), dt=1e30)
+    h = pb.h
+    xc = (np.arange(n) + 0.5) * h
+    R, Z = np.meshgrid(xc, xc)
+    a, b, c = 0.7, -0.3, 1.1
+    T = a * R * R + b * Z * Z + c
+    A, rhs = energy.assemble_energy(st.geom, T, T, pb)
+    row = (A @ T.ravel() - rhs).reshape(n, n)
+    expect = -pb.lam_l * h * h * (R / h) * (4 * a + 2 * b)
+    inner = (slice(1, -1), slice(0, -1))            # zero-gradient outer sides are not quadratic
+    assert np.max(np.abs(row[inner] - expect[inner])) < 1e-12 * np.max(np.abs(expect))
+
+
+def test_axisymmetric_predictor_stagnation_flow():
+    """The axisymmetric stagnation flow u = (u_r, u_z) = (r, -2 z) has a vanishing vector
+    Laplacian (the hoop term -u_r / r^2 cancels (1/r) d/dr (r du_r/dr) = 1/r), so the viscous
+    predictor returns u - dt (u . grad) u = (r - dt r, -2 z - 4 dt z) wherever the boundaries
+    do not reach; the axis and the bottom symmetry plane are exact reflections of this flow.
+    Dropping the hoop term leaves an O(dt mu / (rho r)) error in u_r."""
+    n, dt = 48, 1e-3
+    pb, st = _axi_single_phase(n, (flow.SYMMETRY, flow.OUTFLOW, flow.SYMMETRY, flow.OUTFLOW), rho=3.0, mu=0.2,
+                               dt=dt)
+    h = pb.h
+    xc = (np.arange(n) + 0.5) * h
+    R, Z = np.meshgrid(xc, xc)
+    for u in (st.u_l, st.u_v):
+        u[..., 0], u[..., 1] = R, -2.0 * Z
+    ustar, _ = flow.predictor(st, np.zeros_like(st.u_l))
+    inner = (slice(0, n - 12), slice(0, n - 12))
+    assert np.max(np.abs(ustar["l"][..., 0][inner] - (R - dt * R)[inner])) < 1e-12
+    assert np.max(np.abs(ustar["l"][..., 1][inner] - (-2 * Z - 4 * dt * Z)[inner])) < 1e-12

@@ -100,6 +100,16 @@ typedef struct {
                                  no ghost velocities, and the phase-change source of the
                                  pc-source equation in the projection, div u_f = S_pc with
                                  S_pc V = mdot S_Gamma (1/rho_v - 1/rho_l) in the cut cells     */
+    int axisymmetric;         /* 0: planar (x, y), per unit depth; 1: axisymmetric (r, z) about the
+                                 line x = 0 (the setting of Secs. 3.4-3.7): x is the radius, x0 >= 0,
+                                 and with x0 == 0 the left side is the axis (bc[0] must be
+                                 EBIT_BC_SYMMETRY).  Every integrated balance (the rows of the
+                                 energy, viscous and Poisson systems, the divergence of the face
+                                 velocities, the phase-change source) is weighted by the radius of
+                                 its cell, face or interface segment, the radial velocity gets the
+                                 hoop term mu u_r / r^2 of the viscous stress, the curvature gets
+                                 its azimuthal part n_r / r, and the diagnostics report ring
+                                 volumes, masses and fluxes (2 pi r times the planar measure)     */
 } ebit_config;
 
 typedef struct { double rho, mu, lambda, cp; } ebit_phase_props;

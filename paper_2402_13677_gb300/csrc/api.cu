@@ -521,7 +521,8 @@ static bool batchable(const ebit_config& a, const ebit_config& b) {
         if (a.bc[s] != b.bc[s] || a.T_fixed[s] != b.T_fixed[s] || a.T_wall[s] != b.T_wall[s]) return false;
     return a.precision == b.precision && a.rtol == b.rtol && a.max_iter == b.max_iter &&
            a.extend_iters == b.extend_iters && a.theta_min == b.theta_min && a.sweep_order == b.sweep_order &&
-           a.energy == b.energy && a.mdot_fixed == b.mdot_fixed && a.one_fluid == b.one_fluid;
+           a.energy == b.energy && a.mdot_fixed == b.mdot_fixed && a.one_fluid == b.one_fluid &&
+           a.axisymmetric == b.axisymmetric;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -549,9 +550,14 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         for (int s = 0; s < 4; ++s)
             if (c.bc[s] < 0 || c.bc[s] > 2) { delete ctx; return EBIT_EINVAL; }
         if (!Solver::supported(c.nx, c.ny)) { delete ctx; return EBIT_EINVAL; }
+        if (c.axisymmetric && (!(c.x0 >= 0.0) || (c.x0 == 0.0 && c.bc[0] != EBIT_BC_SYMMETRY))) {
+            delete ctx;
+            return EBIT_EINVAL;
+        }
         Instance& I = ctx->inst[b];
         I.cfg = c;
         I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0; I.g.inv_h = 1.0 / c.h;
+        I.g.axi = c.axisymmetric ? 1 : 0; I.g.r0 = c.x0 / c.h;
         I.g.nz = 1; I.g.zs = 0; I.g.pz = nullptr;
         for (int s = 0; s < 4; ++s) {
             I.g.bc[s] = c.bc[s];

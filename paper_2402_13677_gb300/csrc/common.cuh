@@ -50,10 +50,18 @@ struct Grid {
     int bc[4];        // left, right, bottom, top
     int Tfix[4];
     double Tw[4];
+    int axi;          // axisymmetric (r, z): x is the radius
+    double r0;        // x0 / h, the radius of the left domain side in cells
     int nz;                  // instances in the launch (1 unless batched)
     long long zs;            // byte stride between consecutive instances' arenas
     const Phys* pz;          // device array of the instances' properties, or null
 };
+
+// radius in cells of the centre of cell column i (and of its y-faces) and of the x-face on its
+// left: every integrated balance of an axisymmetric grid carries the radius of the cell, face or
+// segment it lives on (2 pi r times the planar measure, 2 pi h factored out); 1 on planar grids
+__host__ __device__ inline double rad_c(const Grid& g, int i) { return g.axi ? g.r0 + (double)i + 0.5 : 1.0; }
+__host__ __device__ inline double rad_fx(const Grid& g, int i) { return g.axi ? g.r0 + (double)i : 1.0; }
 
 // byte offset of this block's instance, and a pointer moved to it
 __device__ __forceinline__ long long zoff(long long zs) { return (long long)blockIdx.z * zs; }

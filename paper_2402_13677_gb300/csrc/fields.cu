@@ -61,17 +61,16 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
     return F[cidx(g, i, j)];
 }
 
-// Reciprocal of d > 0 to FP64 accuracy without an FP64 division: the FP32 reciprocal of d
-// (relative error below 2^-23) refined by two Newton-Raphson steps for f(r) = 1/r - d, each
-// r <- r + r (1 - d r) with the residual 1 - d r formed by one fused multiply-add, which doubles
-// the number of correct bits per step.  Outside the FP32 range the FP64 division is used.
+// Reciprocal of d > 0 to 46 bits without an FP64 division: the FP32 reciprocal of d (the
+// conversion and the IEEE reciprocal each within 2^-24 relative) refined by one Newton-Raphson
+// step for f(r) = 1/r - d, r <- r + r (1 - d r), the residual 1 - d r formed by one fused
+// multiply-add; the step squares the relative error (below 2^-46).  The range test runs on the
+// FP32 value; outside it the FP64 division is used.
 __device__ inline double recip_nr(double d) {
-    if (!(d > 1e-36 && d < 1e36)) return 1.0 / d;
-    double r = (double)__frcp_rn((float)d);
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
+    float df = __double2float_rn(d);
+    if (!(df > 1e-36f && df < 1e36f)) return 1.0 / d;
+    double r = (double)__frcp_rn(df);
+    return fma(r, fma(-d, r, 1.0), r);
 }
 
 // WENO3 upwind derivative (undivided) from five values along a line (Jiang-Shu, linear weights
@@ -83,22 +82,31 @@ __device__ inline double recip_nr(double d) {
 // so the derivative is phi1 + w0 (phi0 - phi1) with phi0 - phi1 = ((v2 - v1) - (v3 - v2))/2:
 // the second differences serve both the indicators and the candidates' difference, and the one
 // reciprocal is recip_nr (the FP64 rate of this GPU is a small fraction of its FP32 rate).
-__device__ inline double weno3(double Tm2, double Tm1, double T0, double Tp1, double Tp2, bool upos) {
+//
+// weno3_up takes the stencil ordered from the upwind side, up2 and up1 the two upwind values,
+// dn the downwind one, and returns twice the derivative along the flow direction.  For u >= 0
+// that is the ordering (T_{i-2}, T_{i-1}, T_i, T_{i+1}) and the derivative along +x; for u < 0
+// the mirror image (T_{i+2}, T_{i+1}, T_i, T_{i-1}), whose differences are the negated ones of
+// the upwind-from-the-right stencil, so the x-derivative is the negative of the result (every
+// difference changes sign, the indicators do not).  u dT/dx is therefore |u| times the result
+// / 2: the selection costs no FP64 instruction and the factor 1/2 is folded into dt/h.
+__device__ inline double weno3_up(double up2, double up1, double T0, double dn) {
     const double eps = 1e-6;
-    double v1 = upos ? Tm1 - Tm2 : Tp2 - Tp1;
-    double v2 = upos ? T0 - Tm1 : Tp1 - T0;
-    double v3 = upos ? Tp1 - T0 : T0 - Tm1;
+    double v1 = up1 - up2, v2 = T0 - up1, v3 = dn - T0;
     double a1 = v2 - v1, a2 = v3 - v2;
     double s0 = fma(a1, a1, eps), s1 = fma(a2, a2, eps);
     double q0 = s1 * s1;
     double w0 = q0 * recip_nr(fma(s0 + s0, s0, q0));
-    return 0.5 * fma(w0, a1 - a2, v2 + v3);
+    return fma(w0, a1 - a2, v2 + v3);
 }
+// u >= 0 from the sign bit (no FP64 comparison); -0.0 takes the mirrored stencil, which only
+// multiplies a zero velocity
+__device__ inline bool upwind_left(double u) { return __double2hiint(u) >= 0; }
 
 // ---- tiled form: the values a 32 x 8 tile of cells reads (two halo layers, boundary
 // reflections applied) are staged once in shared memory, in FP64, and each thread evaluates
-// the WENO3 stencils of its cell from there (the same values and operations as the per-cell
-// form above, without the five-fold re-reading of the field through the cache)
+// the WENO3 stencils of its cell from there (weno3_up on the staged values, without the
+// five-fold re-reading of the field through the cache)
 constexpr int WX = 32, WY = 8, WH = 2, WSX = WX + 2 * WH, WSY = WY + 2 * WH;
 
 struct Scal {
@@ -134,11 +142,14 @@ __device__ inline void tile_stage(const F* T, const Refl* R, const Grid& g, int 
     __syncthreads();
 }
 
-// T - dt/h (u . D T) at tile position (rx, ry) of the staged field v
-__device__ inline double tile_advect(const double (*v)[WSX], int rx, int ry, double2 u, double dth) {
-    double dx = weno3(v[ry][rx - 2], v[ry][rx - 1], v[ry][rx], v[ry][rx + 1], v[ry][rx + 2], u.x >= 0.0);
-    double dy = weno3(v[ry - 2][rx], v[ry - 1][rx], v[ry][rx], v[ry + 1][rx], v[ry + 2][rx], u.y >= 0.0);
-    return v[ry][rx] - dth * (u.x * dx + u.y * dy);
+// T - dt/h (u . D T) at tile position (rx, ry) of the staged field v; hdth = dt / (2 h)
+__device__ inline double tile_advect(const double (*v)[WSX], int rx, int ry, double2 u, double hdth) {
+    const double* row = v[ry];
+    bool lx = upwind_left(u.x), ly = upwind_left(u.y);
+    double T0 = row[rx];
+    double ex = weno3_up(row[lx ? rx - 2 : rx + 2], row[lx ? rx - 1 : rx + 1], T0, row[lx ? rx + 1 : rx - 1]);
+    double ey = weno3_up(v[ly ? ry - 2 : ry + 2][rx], v[ly ? ry - 1 : ry + 1][rx], T0, v[ly ? ry + 1 : ry - 1][rx]);
+    return T0 - hdth * (fabs(u.x) * ex + fabs(u.y) * ey);
 }
 
 
@@ -163,6 +174,7 @@ __global__ void __launch_bounds__(WX * WY) k_advect_T(Grid g, Refl r, double dth
                                                      const double2* __restrict__ u_v, double* __restrict__ Ts_l,
                                                      double* __restrict__ Ts_v) {
     if (g.pz) dth = g.pz[blockIdx.z].dt / g.h;
+    const double hdth = 0.5 * dth;
     const long long zo = zoff(g.zs);
     flags = zsh(flags, zo);
     T_l = zsh(T_l, zo);
@@ -181,13 +193,10 @@ __global__ void __launch_bounds__(WX * WY) k_advect_T(Grid g, Refl r, double dth
     if (i >= g.nx || j >= g.ny) return;
     int c = cidx(g, i, j);
     int sx = tx + WH, sy = ty + WH;
-    if (flags[c] & F_CCOL) {
-        Ts_l[c] = tile_advect(sh[0], sx, sy, u_l[c], dth);
-        Ts_v[c] = sh[1][sy][sx];
-    } else {
-        Ts_l[c] = sh[0][sy][sx];
-        Ts_v[c] = tile_advect(sh[1], sx, sy, u_v[c], dth);
-    }
+    bool liq = flags[c] & F_CCOL;
+    double adv = tile_advect(sh[liq ? 0 : 1], sx, sy, (liq ? u_l : u_v)[c], hdth);
+    Ts_l[c] = liq ? adv : sh[0][sy][sx];
+    Ts_v[c] = liq ? sh[1][sy][sx] : adv;
 }
 
 // ---------------------------------------------------------------------------------
@@ -409,7 +418,9 @@ __device__ inline double st_face(const Phys& p, const Grid& g, const double* kap
 
 // viscous Helmholtz operator for velocity component comp (integrated form):
 //   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where comp is Dirichlet (odd),
-//   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces).
+//   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces);
+// axisymmetric: each term times the radius of its cell or face, and the radial component's hoop
+// term mu u_r / r^2 of the vector Laplacian (mu_c / r in cells, integrated over the ring cell).
 __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restrict__ vf, double* __restrict__ cd,
                                 double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb) {
     zphys(g, p);
@@ -425,18 +436,21 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
     int c = cidx(g, i, j);
     double v = vf[c];
     double mu = mu_mix(p, v);
-    cd[c] = g.h * g.h * rho_mix(p, v) * p.inv_dt;
+    const double mc = rad_c(g, i);
+    cd[c] = g.h * g.h * rho_mix(p, v) * p.inv_dt * mc;
     double d = 0.0;
-    if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu;
-    if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu;
-    if (j == 0 && vel_odd(g.bc[2], comp, 1)) d += 2.0 * mu;
-    if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) d += 2.0 * mu;
+    if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu * rad_fx(g, 0);
+    if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu * rad_fx(g, g.nx);
+    if (j == 0 && vel_odd(g.bc[2], comp, 1)) d += 2.0 * mu * mc;
+    if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) d += 2.0 * mu * mc;
+    if (g.axi && comp == 0) d += mu / mc;
     dd[c] = d;
-    wl[c] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) : 0.0;
-    wb[c] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) : 0.0;
+    wl[c] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) * rad_fx(g, i) : 0.0;
+    wb[c] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) * mc : 0.0;
 }
 
-// RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields,
+// RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields (cd as
+// in the viscous operator, with the cell's radius on axisymmetric grids),
 // one two-RHS system per component (liquid, vapour interleaved); initial guesses = current u
 // (block WX x WY threads, one cell each; the four velocity components staged per tile)
 __global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth,
@@ -464,14 +478,15 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Re
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
     int c = cidx(g, i, j);
-    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt;
+    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt * rad_c(g, i);
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
     int sx = tx + WH, sy = ty + WH;
-    bx[c] = make_double2(coef * (tile_advect(sh[0], sx, sy, ul, dth) + p.dt * a.x),
-                         coef * (tile_advect(sh[2], sx, sy, uv, dth) + p.dt * a.x));
-    by[c] = make_double2(coef * (tile_advect(sh[1], sx, sy, ul, dth) + p.dt * a.y),
-                         coef * (tile_advect(sh[3], sx, sy, uv, dth) + p.dt * a.y));
+    const double hdth = 0.5 * dth;
+    bx[c] = make_double2(coef * (tile_advect(sh[0], sx, sy, ul, hdth) + p.dt * a.x),
+                         coef * (tile_advect(sh[2], sx, sy, uv, hdth) + p.dt * a.x));
+    by[c] = make_double2(coef * (tile_advect(sh[1], sx, sy, ul, hdth) + p.dt * a.y),
+                         coef * (tile_advect(sh[3], sx, sy, uv, hdth) + p.dt * a.y));
     xx[c] = make_double2(ul.x, uv.x);
     xy[c] = make_double2(ul.y, uv.y);
 }
@@ -562,7 +577,8 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
 
 // Poisson operator: wl/wb = dt / rho_f (interior faces), dd = 2 dt / rho_f on outflow faces,
 // b = -h * (undivided divergence of the face field of the cell's phase); x0 = p
-// length (grid units) of the segments of a cut cell, from its segment table and the markers
+// length (grid units) of the segments of a cut cell, from its segment table and the markers;
+// on axisymmetric grids each segment's length times the radius (cells) of its midpoint
 __device__ inline double segments_length(const Grid& g, const uint16_t* cseg, const double* hpos,
                                          const double* vpos, int i, int j) {
     uint16_t code = cseg[cidx(g, i, j)];
@@ -580,14 +596,16 @@ __device__ inline double segments_length(const Grid& g, const uint16_t* cseg, co
             }
         }
         double dx = m[1].x - m[0].x, dy = m[1].y - m[0].y;
-        L += sqrt(dx * dx + dy * dy);
+        double l = sqrt(dx * dx + dy * dy);
+        L += g.axi ? l * (g.r0 + (double)i + 0.5 * (m[0].x + m[1].x)) : l;
     }
     return L;
 }
 
 // ghost-fluid Poisson operator (face weights dt / rho_f, outflow faces Dirichlet p = 0) and its
 // right-hand side -h div u_f* of each cell's phase; in the one-fluid variant the single field's
-// divergence plus h^2 S_pc = mdot S_Gamma (1/rho_v - 1/rho_l) in the cut cells
+// divergence plus h^2 S_pc = mdot S_Gamma (1/rho_v - 1/rho_l) in the cut cells; axisymmetric:
+// face weights and face fluxes times the face's radius, S_Gamma times the segment's radius
 __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf, const uint8_t* __restrict__ flags,
                                    const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                                    const double* __restrict__ vpos, const double* __restrict__ mdot,
@@ -617,17 +635,19 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     if (i >= g.nx) return;
     int c = cidx(g, i, j);
     cd[c] = 0.0;
+    const double mc = rad_c(g, i), ml = rad_fx(g, i), mr = rad_fx(g, i + 1);
     double d = 0.0;
-    if (i == 0 && g.bc[0] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, 0, j));
-    if (i == g.nx - 1 && g.bc[1] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, g.nx, j));
-    if (j == 0 && g.bc[2] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, 0));
-    if (j == g.ny - 1 && g.bc[3] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, g.ny));
+    if (i == 0 && g.bc[0] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, 0, j)) * ml;
+    if (i == g.nx - 1 && g.bc[1] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, g.nx, j)) * mr;
+    if (j == 0 && g.bc[2] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, 0)) * mc;
+    if (j == g.ny - 1 && g.bc[3] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_y(g, vf, i, g.ny)) * mc;
     dd[c] = d;
-    wl[c] = i > 0 ? p.dt / rho_mix(p, face_vf_x(g, vf, i, j)) : 0.0;
-    wb[c] = j > 0 ? p.dt / rho_mix(p, face_vf_y(g, vf, i, j)) : 0.0;
+    wl[c] = i > 0 ? p.dt / rho_mix(p, face_vf_x(g, vf, i, j)) * ml : 0.0;
+    wb[c] = j > 0 ? p.dt / rho_mix(p, face_vf_y(g, vf, i, j)) * mc : 0.0;
     const double* fx = (flags[c] & F_CCOL) ? fx_l : fx_v;
     const double* fy = (flags[c] & F_CCOL) ? fy_l : fy_v;
-    double div = (fx[veidx(g, i + 1, j)] - fx[veidx(g, i, j)]) + (fy[hidx(g, i, j + 1)] - fy[hidx(g, i, j)]);
+    double div = (mr * fx[veidx(g, i + 1, j)] - ml * fx[veidx(g, i, j)]) +
+                 mc * (fy[hidx(g, i, j + 1)] - fy[hidx(g, i, j)]);
     double rhs = -g.h * div;
     if (p.one_fluid && (flags[c] & F_CUT))
         rhs += mdot[c] * segments_length(g, cseg, hpos, vpos, i, j) * g.h * (1.0 / p.rho_v - 1.0 / p.rho_l);
@@ -769,6 +789,8 @@ constexpr int NDIAG_SUMS = 8;
 //   equation), s4 cut cells, s5 vapour volume flux through the outflow faces ((1 - H) u_f . n
 //   with the face velocity of the boundary cell's phase), s6 wall heat flux 2 (T_w - T_i) / h
 //   summed over the faces of fixed-temperature walls, s7 the number of those faces.
+// Axisymmetric grids weight every cell, face and segment by its radius and report the ring's
+// volumes, masses and fluxes (the wall Nusselt number stays the plain mean over the faces).
 // out: t, vapour volume, dV expected from mdot, M_d, outlet mass, cut cells, vapour volume out,
 // wall Nusselt number (l / (T_w - T_sat)) * mean wall flux, l = sqrt(sigma / (|drho| |g|)) when
 // sigma and g are nonzero, else 1.
@@ -806,8 +828,9 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
         int c = cw.c, i = cw.i, j = cw.j;
         double v = vf[c];
         double rc = rho_mix(p, v);
-        s[0] += 1.0 - v;
-        s[2] += rc;
+        const double mc = rad_c(g, i);
+        s[0] += (1.0 - v) * mc;
+        s[2] += rc * mc;
         uint16_t code = cseg[c];
         int ns = code & 3;
         if (ns) {
@@ -824,7 +847,8 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
                 };
                 double2 P = ml(kP), Q = ml(kQ);
                 double dx = Q.x - P.x, dy = Q.y - P.y;
-                s[1] += mdot[c] * sqrt(dx * dx + dy * dy) * g.h;
+                double ms = g.axi ? g.r0 + (double)i + 0.5 * (P.x + Q.x) : 1.0;   // the segment's radius
+                s[1] += mdot[c] * sqrt(dx * dx + dy * dy) * g.h * ms;
             }
         }
         bool liq = flags[c] & F_CCOL;
@@ -836,7 +860,8 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
                 if (g.bc[sd] == BC_OUTFLOW) {
                     double u = sd < 2 ? (liq ? fx_l : fx_v)[veidx(g, sd == 0 ? 0 : g.nx, j)]
                                       : (liq ? fy_l : fy_v)[hidx(g, i, sd == 2 ? 0 : g.ny)];
-                    double un = (sd == 0 || sd == 2) ? -u : u;
+                    double un = ((sd == 0 || sd == 2) ? -u : u) *
+                                (sd == 0 ? rad_fx(g, 0) : (sd == 1 ? rad_fx(g, g.nx) : mc));
                     s[3] += rc * un;
                     s[5] += (1.0 - v) * un;
                 }
@@ -864,15 +889,16 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
     }
     if (threadIdx.x == 0) {
         double h2 = g.h * g.h;
+        const double ring = g.axi ? 6.283185307179586 * g.h : 1.0;   // 2 pi r = 2 pi h times the radius in cells
         clock[0] += p.dt;
         clock[1] += 1.0;
         out[0] = clock[0];
-        out[1] = s[0] * h2;
-        out[2] = s[1] * p.dt / p.rho_v;
-        out[3] = s[2] * h2;
-        out[4] = s[3] * g.h * p.dt;
+        out[1] = s[0] * h2 * ring;
+        out[2] = s[1] * p.dt / p.rho_v * ring;
+        out[3] = s[2] * h2 * ring;
+        out[4] = s[3] * g.h * p.dt * ring;
         out[5] = s[4];
-        out[6] = s[5] * g.h * p.dt;
+        out[6] = s[5] * g.h * p.dt * ring;
         double nu = 0.0;
         if (s[7] > 0.0) {
             double Tw = 0.0;
@@ -984,6 +1010,7 @@ void launch_project(const Grid& g, const Phys& p, const double* P, const double*
                     double* fy_l, double* fy_v, double2* gc, const double2* us_l, const double2* us_v, double2* u_l,
                     double2* u_v, cudaStream_t st) {
     long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
+    if (g.axi) wl_p = wb_p = nullptr;   // those weights carry the faces' radii: use dt / rho_f itself
     k_face_accel<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, p, P, vf, kap, wl_p, wb_p, ax, ay, fx_l, fx_v, fy_l, fy_v);
     k_project_cells<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, ax, ay, gc, us_l, us_v, u_l, u_v);
 }

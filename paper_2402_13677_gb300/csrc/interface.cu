@@ -730,7 +730,8 @@ __device__ double link_theta(const Grid& g, const uint16_t* cseg, const double* 
 // Energy operator of the combined (block-diagonal) two-phase system, integrated form:
 //   cd = h^2 (rho cp)_k / dt,   dd = sum_cut lambda_k / theta + sum_Tfixed 2 lambda_k,
 //   wl/wb (left/bottom face) = lambda_k between two cells of the same phase, 0 across the interface,
-//   b = cd T*_k + sum_cut lambda_k T_sat / theta + sum 2 lambda_k T_w,  x0 = T*_k.
+//   b = cd T*_k + sum_cut lambda_k T_sat / theta + sum 2 lambda_k T_w,  x0 = T*_k;
+// axisymmetric: cd times the cell's radius, every face term times the radius of its face.
 __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ flags,
                                   const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                                   const double* __restrict__ vpos, const double* __restrict__ Ts_l,
@@ -758,26 +759,29 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     int k = flags[c] & F_CCOL;
     double lam = k ? p.lam_l : p.lam_v;
     double rc = k ? p.rho_l * p.cp_l : p.rho_v * p.cp_v;
-    double coef = g.h * g.h * rc / p.dt;
+    const double mc = rad_c(g, i);
+    double coef = g.h * g.h * rc / p.dt * mc;
     double ts = k ? Ts_l[c] : Ts_v[c];
     double dsum = 0.0, rhs = coef * ts;
     const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
     const int bside[4] = {1, 0, 3, 2};
     for (int s = 0; s < 4; ++s) {
         int ii = i + di[s], jj = j + dj[s];
+        // conductance of the face this link crosses
+        double lf = lam * (s == 0 ? rad_fx(g, i + 1) : (s == 1 ? rad_fx(g, i) : mc));
         if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.ny) {
             int bs = bside[s];
             if (g.Tfix[bs]) {
-                dsum += 2.0 * lam;
-                rhs += 2.0 * lam * g.Tw[bs];
+                dsum += 2.0 * lf;
+                rhs += 2.0 * lf * g.Tw[bs];
             }
             continue;
         }
         int kn = flags[cidx(g, ii, jj)] & F_CCOL;
         if (kn != k) {
             double th = link_theta(g, cseg, hpos, vpos, i, j, s, p.theta_min);
-            dsum += lam / th;
-            rhs += lam * p.T_sat / th;
+            dsum += lf / th;
+            rhs += lf * p.T_sat / th;
         }
     }
     cd[c] = coef;
@@ -785,8 +789,8 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     b[c] = rhs;
     x0[c] = ts;
     // left and bottom face weights of the cell (domain faces carry none)
-    wl[c] = (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) ? lam : 0.0;
-    wb[c] = (j > 0 && (flags[cidx(g, i, j - 1)] & F_CCOL) == k) ? lam : 0.0;
+    wl[c] = (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) ? lam * rad_fx(g, i) : 0.0;
+    wb[c] = (j > 0 && (flags[cidx(g, i, j - 1)] & F_CCOL) == k) ? lam * mc : 0.0;
 }
 
 // ---------------------------------------------------------------------------------
@@ -910,8 +914,8 @@ __device__ inline bool across(const Grid& g, const uint16_t* cseg, const double*
 // Curvature kappa = div n (n from liquid into vapour) of every cut cell, from the markers: for
 // its segment P -> Q (liquid on the left) and the chain neighbours R_P before P and R_Q after Q,
 // the mean of the curvatures of the circles through (R_P, P, Q) and (P, Q, R_Q) (one circle
-// where a neighbour is missing); two segments: the length-weighted mean; NaN where undefined
-// or not cut.  Grid units in, physical curvature out.
+// where a neighbour is missing), plus n_r / r on axisymmetric grids; two segments: the
+// length-weighted mean; NaN where undefined or not cut.  Grid units in, physical curvature out.
 __global__ void k_curvature(Grid g, const uint8_t* __restrict__ flags, const uint16_t* __restrict__ cseg,
                             const double* __restrict__ hpos, const double* __restrict__ vpos,
                             double* __restrict__ kap) {
@@ -941,7 +945,10 @@ __global__ void k_curvature(Grid g, const uint8_t* __restrict__ flags, const uin
             if (across(g, cseg, hpos, vpos, i, j, kQ, &R)) { sum += menger(P, Q, R); ++nk; }
             if (!nk) continue;
             double L = sqrt((Q.x - P.x) * (Q.x - P.x) + (Q.y - P.y) * (Q.y - P.y));
-            num += L * (sum / nk);
+            double k2 = sum / nk;
+            // axisymmetric: the azimuthal curvature n_r / r at the segment's midpoint (grid units)
+            if (g.axi) k2 += ((Q.y - P.y) / L) / (g.r0 + 0.5 * (P.x + Q.x));
+            num += L * k2;
             den += L;
         }
         if (den > 0.0) out = num / den * g.inv_h;

@@ -51,7 +51,7 @@ class ebit_config(C.Structure):
                 ("bc", C.c_int * 4), ("T_fixed", C.c_int * 4), ("T_wall", C.c_double * 4), ("dt", C.c_double),
                 ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int), ("extend_iters", C.c_int),
                 ("theta_min", C.c_double), ("sweep_order", C.c_int), ("energy", C.c_int),
-                ("mdot_fixed", C.c_double), ("one_fluid", C.c_int)]
+                ("mdot_fixed", C.c_double), ("one_fluid", C.c_int), ("axisymmetric", C.c_int)]
 
 
 class ebit_phase_props(C.Structure):
@@ -340,6 +340,7 @@ def config_from_problem(pb, precision=EBIT_FP64, rtol=1e-8, max_iter=200):
     c.energy = 1 if pb.energy else 0
     c.mdot_fixed = pb.mdot_fixed
     c.one_fluid = 1 if getattr(pb, "one_fluid", False) else 0
+    c.axisymmetric = 1 if getattr(pb, "axi", False) else 0
     return c
 
 

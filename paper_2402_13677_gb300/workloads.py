@@ -10,9 +10,10 @@ step), so both the CUDA path and the CPU oracle can start from the same state.
 Closed forms:
   * 1D Stefan problem (Sec. 3.1, interface-position and temperature equations):
     X(t) = 2 beta sqrt(alpha_v t),  beta exp(beta^2) erf(beta) = cp_v dT / (sqrt(pi) h_lg).
-  * Planar (cylindrical) analogue of the Scriven problem (Sec. 3.4): the paper's
-    case is spherical/axisymmetric; the 2D planar similarity solution used here is
-    derived in the same way (liquid velocity eps R R'/r, eps = 1 - rho_v/rho_l):
+  * Scriven problem (Sec. 3.4), the paper's spherical case on an axisymmetric grid
+    (scriven, scriven_beta, scriven_temperature), and its planar (cylindrical) analogue
+    for planar grids (bubble), derived in the same way (liquid velocity eps R R'/r,
+    eps = 1 - rho_v/rho_l):
     R = 2 beta sqrt(alpha_l t),  T(eta) = T_inf - dT I(eta)/I(beta),
     I(eta) = int_eta^inf s^(2 eps beta^2 - 1) exp(-s^2) ds,
     Ja = rho_l cp_l dT / (rho_v h_lg) = 2 beta^2 exp(beta^2) beta^(-2 eps beta^2) I(beta).

@@ -144,6 +144,12 @@ def cases():
         "stefan_1f": lambda: w.one_fluid(w.stefan(48, 8, X0=0.23, Lx=1.0, dt=2e-4, steps=0)),
         "bubble_1f": lambda: w.one_fluid(w.bubble(n=64, R0=0.17, rho_ratio=5.0, k_ratio=3.0, St=0.3, mu=0.01,
                                                   dt=1e-4, steps=0)),
+        # axisymmetric (r, z), axis on the left: a sphere with an imposed mass flux, the Scriven
+        # problem (Sec. 3.4) and a static sphere held by surface tension (curvature 2 / R)
+        "axi_sphere": lambda: w.axi_const_mdot_bubble(n=48, R0=0.3, steps=0),
+        "scriven": lambda: w.scriven(n=48, R0=0.3, steps=0),
+        "axi_sigma": lambda: _with_sigma(w.axi_const_mdot_bubble(n=48, R0=0.3, mdot=0.0, dt=2e-4, mu=0.05,
+                                                                 steps=0), 1.0),
     }
 
 
@@ -201,7 +207,7 @@ def test_prepare_matches_oracle(dev, name):
 
 
 # ----------------------------------------------------------------------------- stages
-@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "sucking"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "sucking", "scriven"])
 def test_energy_advection_and_extension(dev, name):
     st = prepared(name, 1)
     ctx = gpu_ctx(dev, st)
@@ -250,7 +256,7 @@ def test_interface_advance_bit_exact(dev, name, order):
         E.ebit_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "sucking"])
+@pytest.mark.parametrize("name", ["stefan", "bubble", "film", "sucking", "scriven"])
 def test_energy_solve_flux_and_ghost_velocity(dev, name):
     st = prepared(name, 1)
     pb = st.pb
@@ -321,7 +327,7 @@ def test_full_step_fp64(dev, name):
 
 
 @pytest.mark.parametrize("name", ["stefan", "bubble", "sucking", "stefan_1f", "bubble_1f", "static_sigma",
-                                  "film_sigma"])
+                                  "film_sigma", "axi_sphere", "scriven", "axi_sigma"])
 def test_several_steps_track_the_oracle(dev, name):
     st = prepared(name, 0)
     ctx = gpu_ctx(dev, st)

@@ -53,7 +53,7 @@ METRIC = "cell-steps/s at 1 GPU, FP32+refine vs FP64, 1e-8 rel residual; %HBM ro
 # of the current kernels (summary and command in the named profiles/ file); an entry is removed
 # whenever those kernels change, so that a stale figure is never reported
 SMOOTH_L0_TRAFFIC = {
-    "c2_bubble_512": {"dram_bytes_per_launch": 5.29e6,
+    "c2_bubble_512": {"dram_bytes_per_launch": 5.14e6,
                       "summary": "profiles/smoother_l0_traffic_c2_bubble_512.md"},
 }
 

@@ -59,9 +59,13 @@ struct Grid {
 
 // radius in cells of the centre of cell column i (and of its y-faces) and of the x-face on its
 // left: every integrated balance of an axisymmetric grid carries the radius of the cell, face or
-// segment it lives on (2 pi r times the planar measure, 2 pi h factored out); 1 on planar grids
-__host__ __device__ inline double rad_c(const Grid& g, int i) { return g.axi ? g.r0 + (double)i + 0.5 : 1.0; }
-__host__ __device__ inline double rad_fx(const Grid& g, int i) { return g.axi ? g.r0 + (double)i : 1.0; }
+// segment it lives on (2 pi r times the planar measure, 2 pi h factored out); 1 on planar grids.
+// The kernels that use them are instantiated for AXI = g.axi, so that a planar grid spends no
+// FP64 instruction on the metric (the FP64 rate bounds those kernels).
+template <bool AXI>
+__host__ __device__ inline double rad_c(const Grid& g, int i) { return AXI ? g.r0 + (double)i + 0.5 : 1.0; }
+template <bool AXI>
+__host__ __device__ inline double rad_fx(const Grid& g, int i) { return AXI ? g.r0 + (double)i : 1.0; }
 
 // byte offset of this block's instance, and a pointer moved to it
 __device__ __forceinline__ long long zoff(long long zs) { return (long long)blockIdx.z * zs; }

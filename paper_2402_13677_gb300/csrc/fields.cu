@@ -421,6 +421,7 @@ __device__ inline double st_face(const Phys& p, const Grid& g, const double* kap
 //   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces);
 // axisymmetric: each term times the radius of its cell or face, and the radial component's hoop
 // term mu u_r / r^2 of the vector Laplacian (mu_c / r in cells, integrated over the ring cell).
+template <bool AXI>
 __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restrict__ vf, double* __restrict__ cd,
                                 double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb) {
     zphys(g, p);
@@ -436,16 +437,16 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
     int c = cidx(g, i, j);
     double v = vf[c];
     double mu = mu_mix(p, v);
-    const double mc = rad_c(g, i);
+    const double mc = rad_c<AXI>(g, i);
     cd[c] = g.h * g.h * rho_mix(p, v) * p.inv_dt * mc;
     double d = 0.0;
-    if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu * rad_fx(g, 0);
-    if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu * rad_fx(g, g.nx);
+    if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu * rad_fx<AXI>(g, 0);
+    if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu * rad_fx<AXI>(g, g.nx);
     if (j == 0 && vel_odd(g.bc[2], comp, 1)) d += 2.0 * mu * mc;
     if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) d += 2.0 * mu * mc;
-    if (g.axi && comp == 0) d += mu / mc;
+    if (AXI && comp == 0) d += mu / mc;
     dd[c] = d;
-    wl[c] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) * rad_fx(g, i) : 0.0;
+    wl[c] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) * rad_fx<AXI>(g, i) : 0.0;
     wb[c] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) * mc : 0.0;
 }
 
@@ -453,6 +454,7 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
 // in the viscous operator, with the cell's radius on axisymmetric grids),
 // one two-RHS system per component (liquid, vapour interleaved); initial guesses = current u
 // (block WX x WY threads, one cell each; the four velocity components staged per tile)
+template <bool AXI>
 __global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Refl ry, double dth,
                                                     const double* __restrict__ vf, const double2* __restrict__ u_l,
                                                     const double2* __restrict__ u_v, const double2* __restrict__ gc,
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Re
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
     int c = cidx(g, i, j);
-    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt * rad_c(g, i);
+    double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt * rad_c<AXI>(g, i);
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
     int sx = tx + WH, sy = ty + WH;
@@ -579,6 +581,7 @@ __global__ void k_face_star(Grid g, Phys p, const double2* __restrict__ us_l, co
 // b = -h * (undivided divergence of the face field of the cell's phase); x0 = p
 // length (grid units) of the segments of a cut cell, from its segment table and the markers;
 // on axisymmetric grids each segment's length times the radius (cells) of its midpoint
+template <bool AXI>
 __device__ inline double segments_length(const Grid& g, const uint16_t* cseg, const double* hpos,
                                          const double* vpos, int i, int j) {
     uint16_t code = cseg[cidx(g, i, j)];
@@ -597,7 +600,7 @@ __device__ inline double segments_length(const Grid& g, const uint16_t* cseg, co
         }
         double dx = m[1].x - m[0].x, dy = m[1].y - m[0].y;
         double l = sqrt(dx * dx + dy * dy);
-        L += g.axi ? l * (g.r0 + (double)i + 0.5 * (m[0].x + m[1].x)) : l;
+        L += AXI ? l * (g.r0 + (double)i + 0.5 * (m[0].x + m[1].x)) : l;
     }
     return L;
 }
@@ -606,6 +609,7 @@ __device__ inline double segments_length(const Grid& g, const uint16_t* cseg, co
 // right-hand side -h div u_f* of each cell's phase; in the one-fluid variant the single field's
 // divergence plus h^2 S_pc = mdot S_Gamma (1/rho_v - 1/rho_l) in the cut cells; axisymmetric:
 // face weights and face fluxes times the face's radius, S_Gamma times the segment's radius
+template <bool AXI>
 __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf, const uint8_t* __restrict__ flags,
                                    const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                                    const double* __restrict__ vpos, const double* __restrict__ mdot,
@@ -635,7 +639,7 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
     if (i >= g.nx) return;
     int c = cidx(g, i, j);
     cd[c] = 0.0;
-    const double mc = rad_c(g, i), ml = rad_fx(g, i), mr = rad_fx(g, i + 1);
+    const double mc = rad_c<AXI>(g, i), ml = rad_fx<AXI>(g, i), mr = rad_fx<AXI>(g, i + 1);
     double d = 0.0;
     if (i == 0 && g.bc[0] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, 0, j)) * ml;
     if (i == g.nx - 1 && g.bc[1] == BC_OUTFLOW) d += 2.0 * p.dt / rho_mix(p, face_vf_x(g, vf, g.nx, j)) * mr;
@@ -650,7 +654,7 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
                  mc * (fy[hidx(g, i, j + 1)] - fy[hidx(g, i, j)]);
     double rhs = -g.h * div;
     if (p.one_fluid && (flags[c] & F_CUT))
-        rhs += mdot[c] * segments_length(g, cseg, hpos, vpos, i, j) * g.h * (1.0 / p.rho_v - 1.0 / p.rho_l);
+        rhs += mdot[c] * segments_length<AXI>(g, cseg, hpos, vpos, i, j) * g.h * (1.0 / p.rho_v - 1.0 / p.rho_l);
     b[c] = rhs;
 }
 
@@ -794,6 +798,7 @@ constexpr int NDIAG_SUMS = 8;
 // out: t, vapour volume, dV expected from mdot, M_d, outlet mass, cut cells, vapour volume out,
 // wall Nusselt number (l / (T_w - T_sat)) * mean wall flux, l = sqrt(sigma / (|drho| |g|)) when
 // sigma and g are nonzero, else 1.
+template <bool AXI>
 __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, const uint16_t* __restrict__ cseg,
                               const double* __restrict__ hpos, const double* __restrict__ vpos,
                               const double* __restrict__ mdot, const uint8_t* __restrict__ flags,
@@ -828,7 +833,7 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
         int c = cw.c, i = cw.i, j = cw.j;
         double v = vf[c];
         double rc = rho_mix(p, v);
-        const double mc = rad_c(g, i);
+        const double mc = rad_c<AXI>(g, i);
         s[0] += (1.0 - v) * mc;
         s[2] += rc * mc;
         uint16_t code = cseg[c];
@@ -847,7 +852,7 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
                 };
                 double2 P = ml(kP), Q = ml(kQ);
                 double dx = Q.x - P.x, dy = Q.y - P.y;
-                double ms = g.axi ? g.r0 + (double)i + 0.5 * (P.x + Q.x) : 1.0;   // the segment's radius
+                double ms = AXI ? g.r0 + (double)i + 0.5 * (P.x + Q.x) : 1.0;   // the segment's radius
                 s[1] += mdot[c] * sqrt(dx * dx + dy * dy) * g.h * ms;
             }
         }
@@ -861,7 +866,7 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
                     double u = sd < 2 ? (liq ? fx_l : fx_v)[veidx(g, sd == 0 ? 0 : g.nx, j)]
                                       : (liq ? fy_l : fy_v)[hidx(g, i, sd == 2 ? 0 : g.ny)];
                     double un = ((sd == 0 || sd == 2) ? -u : u) *
-                                (sd == 0 ? rad_fx(g, 0) : (sd == 1 ? rad_fx(g, g.nx) : mc));
+                                (sd == 0 ? rad_fx<AXI>(g, 0) : (sd == 1 ? rad_fx<AXI>(g, g.nx) : mc));
                     s[3] += rc * un;
                     s[5] += (1.0 - v) * un;
                 }
@@ -889,7 +894,7 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
     }
     if (threadIdx.x == 0) {
         double h2 = g.h * g.h;
-        const double ring = g.axi ? 6.283185307179586 * g.h : 1.0;   // 2 pi r = 2 pi h times the radius in cells
+        const double ring = AXI ? 6.283185307179586 * g.h : 1.0;   // 2 pi r = 2 pi h times the radius in cells
         clock[0] += p.dt;
         clock[1] += 1.0;
         out[0] = clock[0];
@@ -979,12 +984,14 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, c
 
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
                           double* wl, double* wb, cudaStream_t st) {
-    k_visc_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, comp, vf, cd, dd, wl, wb);
+    auto k = g.axi ? k_visc_operator<true> : k_visc_operator<false>;
+    k<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, comp, vf, cd, dd, wl, wb);
 }
 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
                     const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st) {
-    k_mom_rhs<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
+    auto k = g.axi ? k_mom_rhs<true> : k_mom_rhs<false>;
+    k<<<dim3(div_up(g.nx, WX), div_up(g.ny, WY), g.nz), WX * WY, 0, st>>>(
         g, p, velocity_refl(g, 0), velocity_refl(g, 1), p.dt / g.h, vf, u_l, u_v, gc, bx, by, xx, xy);
 }
 
@@ -1001,8 +1008,9 @@ void launch_poisson_operator(const Grid& g, const Phys& p, const double* vf, con
                              const uint16_t* cseg, const double* hpos, const double* vpos, const double* mdot,
                              const double* fx_l, const double* fx_v, const double* fy_l, const double* fy_v,
                              double* cd, double* dd, double* wl, double* wb, double* b, cudaStream_t st) {
-    k_poisson_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, cseg, hpos, vpos, mdot,
-                                                                         fx_l, fx_v, fy_l, fy_v, cd, dd, wl, wb, b);
+    auto k = g.axi ? k_poisson_operator<true> : k_poisson_operator<false>;
+    k<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, flags, cseg, hpos, vpos, mdot, fx_l, fx_v, fy_l,
+                                                          fy_v, cd, dd, wl, wb, b);
 }
 
 void launch_project(const Grid& g, const Phys& p, const double* P, const double* vf, const double* kap,
@@ -1027,8 +1035,9 @@ void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const ui
                         const double* fx_v, const double* fy_l, const double* fy_v, const double* T_l,
                         const double* T_v, double* partial, unsigned* ticket, double* clock, double* out,
                         cudaStream_t st) {
-    k_diagnostics<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v,
-                                                                 fy_l, fy_v, T_l, T_v, partial, ticket, clock, out);
+    auto k = g.axi ? k_diagnostics<true> : k_diagnostics<false>;
+    k<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v,
+                                                     T_l, T_v, partial, ticket, clock, out);
 }
 
 }  // namespace ebit

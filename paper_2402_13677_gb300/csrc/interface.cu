@@ -732,6 +732,7 @@ __device__ double link_theta(const Grid& g, const uint16_t* cseg, const double* 
 //   wl/wb (left/bottom face) = lambda_k between two cells of the same phase, 0 across the interface,
 //   b = cd T*_k + sum_cut lambda_k T_sat / theta + sum 2 lambda_k T_w,  x0 = T*_k;
 // axisymmetric: cd times the cell's radius, every face term times the radius of its face.
+template <bool AXI>
 __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ flags,
                                   const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
                                   const double* __restrict__ vpos, const double* __restrict__ Ts_l,
@@ -759,7 +760,7 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     int k = flags[c] & F_CCOL;
     double lam = k ? p.lam_l : p.lam_v;
     double rc = k ? p.rho_l * p.cp_l : p.rho_v * p.cp_v;
-    const double mc = rad_c(g, i);
+    const double mc = rad_c<AXI>(g, i);
     double coef = g.h * g.h * rc / p.dt * mc;
     double ts = k ? Ts_l[c] : Ts_v[c];
     double dsum = 0.0, rhs = coef * ts;
@@ -768,7 +769,7 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     for (int s = 0; s < 4; ++s) {
         int ii = i + di[s], jj = j + dj[s];
         // conductance of the face this link crosses
-        double lf = lam * (s == 0 ? rad_fx(g, i + 1) : (s == 1 ? rad_fx(g, i) : mc));
+        double lf = AXI ? lam * (s == 0 ? rad_fx<AXI>(g, i + 1) : (s == 1 ? rad_fx<AXI>(g, i) : mc)) : lam;
         if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.ny) {
             int bs = bside[s];
             if (g.Tfix[bs]) {
@@ -789,7 +790,7 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     b[c] = rhs;
     x0[c] = ts;
     // left and bottom face weights of the cell (domain faces carry none)
-    wl[c] = (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) ? lam * rad_fx(g, i) : 0.0;
+    wl[c] = (i > 0 && (flags[cidx(g, i - 1, j)] & F_CCOL) == k) ? lam * rad_fx<AXI>(g, i) : 0.0;
     wb[c] = (j > 0 && (flags[cidx(g, i, j - 1)] & F_CCOL) == k) ? lam * mc : 0.0;
 }
 
@@ -1036,8 +1037,9 @@ void launch_energy_operator(const Grid& g, const Phys& p, const uint8_t* flags, 
                             const double* hpos, const double* vpos, const double* Ts_l, const double* Ts_v,
                             double* cd, double* dd, double* wl, double* wb, double* b, double* x0,
                             cudaStream_t st) {
-    k_energy_operator<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, flags, cseg, hpos, vpos, Ts_l, Ts_v, cd,
-                                                                 dd, wl, wb, b, x0);
+    auto k = g.axi ? k_energy_operator<true> : k_energy_operator<false>;
+    k<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, flags, cseg, hpos, vpos, Ts_l, Ts_v, cd, dd, wl, wb, b,
+                                                          x0);
 }
 
 void launch_mass_flux(const Grid& g, const Phys& p, const uint16_t* cseg, const double* hpos,

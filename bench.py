@@ -525,7 +525,7 @@ def main():
     ap.add_argument("--profile-only", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels from the host (profilers)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
-    ap.add_argument("--extra", default="c2_bubble_512_one_fluid,c3_film_1024x2048,c5_film_4096",
+    ap.add_argument("--extra", default="c2_bubble_512_one_fluid,c3_film_1024x2048,c5_film_4096,c4_batch_4096",
                     help="further workloads measured in the same run (sub-objects of the line; '' for none)")
     ap.add_argument("--extra-steps", type=int, default=5)
     ap.add_argument("--extra-warmup", type=int, default=3)

@@ -310,11 +310,16 @@ ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* i
  *   cooperative launch, in polls of the arrival counter.  A fault-path test setting: a bound of
  *   a few polls makes the barriers give up before the other blocks arrive.  Changing it drops
  *   the captured step graphs.
+ *   EBIT_OPT_EXT_BLOCK (default 1 on grids of at most 2^19 cells, 0 above) runs every Jacobi
+ *   sweep of a narrow-band extension (extrapolation equation, Sec. 2.4) in one thread block per
+ *   instance; 0 launches one kernel per sweep over the whole device.  Both give the same values.
+ *   Changing it drops the captured step graphs.
  * A tile kernel that waits for its copies in vain, or a grid barrier that waits in vain, gives
  * up after a bounded wait and records a fault; ebit_step, ebit_solve_system and
  * ebit_solve_system_noalloc then return EBIT_ECUDA: every result of that launch (not only of
  * the instance) is invalid, and the context should be destroyed. */
-enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2, EBIT_OPT_COOP = 3, EBIT_OPT_BARRIER_SPIN = 4 };
+enum { EBIT_OPT_GRAPH = 1, EBIT_OPT_TMA = 2, EBIT_OPT_COOP = 3, EBIT_OPT_BARRIER_SPIN = 4,
+       EBIT_OPT_EXT_BLOCK = 5 };
 ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value);
 
 const char* ebit_last_error(const ebit_ctx* ctx);

@@ -513,6 +513,10 @@ static ebit_status check_status(ebit_ctx* ctx, bool graph_step = false) {
     return worst;
 }
 
+// grids up to this many cells run each narrow-band extension in one CTA per instance (their
+// bands are a few thousand cells); larger ones launch one kernel per Jacobi sweep
+constexpr long long EXT_BLOCK_MAX_CELLS = 1LL << 19;
+
 // two configurations can share batched launches: the same grid, boundaries and solver settings
 // (the time step and the properties may differ)
 static bool batchable(const ebit_config& a, const ebit_config& b) {
@@ -558,6 +562,7 @@ ebit_status ebit_init(const ebit_config* cfgs, int batch, void* stream, const eb
         I.cfg = c;
         I.g.nx = c.nx; I.g.ny = c.ny; I.g.h = c.h; I.g.x0 = c.x0; I.g.y0 = c.y0; I.g.inv_h = 1.0 / c.h;
         I.g.axi = c.axisymmetric ? 1 : 0; I.g.r0 = c.x0 / c.h;
+        I.g.ext_block = (long long)c.nx * c.ny <= EXT_BLOCK_MAX_CELLS ? 1 : 0;
         I.g.nz = 1; I.g.zs = 0; I.g.pz = nullptr;
         for (int s = 0; s < 4; ++s) {
             I.g.bc[s] = c.bc[s];
@@ -1154,6 +1159,20 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
     if (option == EBIT_OPT_GRAPH) {
         ctx->use_graph = value ? 1 : 0;
         return EBIT_OK;
+    }
+    if (option == EBIT_OPT_EXT_BLOCK) {
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        for (auto& I : ctx->inst) {
+            I.g.ext_block = value ? 1 : 0;
+            for (auto& gx : I.graph)
+                if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+        }
+        for (auto& B : ctx->batches) {
+            B.lead.g.ext_block = value ? 1 : 0;
+            for (auto& gx : B.graph)
+                if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+        }
+        return cuda_check(ctx, "ebit_set_option");
     }
     if (option == EBIT_OPT_TMA || option == EBIT_OPT_COOP || option == EBIT_OPT_BARRIER_SPIN) {
         if (option == EBIT_OPT_BARRIER_SPIN && value < 0) return fail(ctx, EBIT_EINVAL, "negative spin bound");

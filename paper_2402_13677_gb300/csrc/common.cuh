@@ -50,6 +50,8 @@ struct Grid {
     int bc[4];        // left, right, bottom, top
     int Tfix[4];
     double Tw[4];
+    int ext_block;    // narrow-band extension: every Jacobi sweep in one CTA per instance (else
+                      // one launch per sweep)
     int axi;          // axisymmetric (r, z): x is the radius
     double r0;        // x0 / h, the radius of the left domain side in cells
     int nz;                  // instances in the launch (1 unless batched)
@@ -120,6 +122,68 @@ __device__ inline double cell_vel(const double2* F, const Grid& g, int comp, int
     double2 v = F[cidx(g, i, j)];
     double s = comp == 0 ? v.x : v.y;
     return neg ? -s : s;
+}
+
+// Conversions between FP64 and FP32 on the integer pipes.  The FP64 pipe of this GPU issues at
+// a small fraction of the FP32 rate and also performs the hardware conversions, so kernels that
+// convert every element (building the FP32 multigrid operators, scaling the refinement residual
+// to FP32, applying the FP32 correction to the FP64 solution) were bound by it.  Both follow
+// IEEE 754: binary64 -> binary32 rounds to nearest, ties to even (subnormal results, overflow
+// to infinity, signed zeros, NaNs kept quiet), binary32 -> binary64 is exact.  Every case is
+// integer arithmetic: a fallback to the hardware conversion would be compiled to a predicated
+// FP64 instruction issued for every element.
+// d2f_rn2(v, k) rounds v 2^k (exact scaling by a power of two, no intermediate binary64) to
+// binary32; v a binary64 subnormal gives zero.
+__device__ __forceinline__ float d2f_rn2(double v, int k) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned sign = (unsigned)(b >> 63) << 31;
+    unsigned e0 = (unsigned)(b >> 52) & 0x7ffu;           // biased binary64 exponent
+    unsigned long long m = b & 0x000fffffffffffffull;
+    // exponent of v 2^k (held in range: inputs that are zero, subnormal, infinite or NaN keep
+    // their class below)
+    int es = (int)e0 + k;
+    unsigned e = (e0 == 0u || e0 == 0x7ffu) ? e0 : (unsigned)(es < 1 ? 1 : (es > 2046 ? 2046 : es));
+    unsigned f;
+    if (e0 != 0u && e0 != 0x7ffu && es != (int)e) {        // scaled beyond the binary64 range
+        f = es > 0 ? 0x7f800000u : 0u;
+    } else if (e - 897u <= 253u) {                        // normal binary32 result (before rounding)
+        unsigned keep = (unsigned)(m >> 29), rest = (unsigned)(m & 0x1fffffffu);
+        f = ((e - 896u) << 23) | keep;                    // a rounding carry moves into the exponent
+        f += (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+    } else if (e == 0x7ffu) {                             // infinity, NaN (made quiet)
+        f = 0x7f800000u | (m ? 0x400000u | (unsigned)(m >> 29) : 0u);
+    } else if (e > 1150u) {                               // beyond the binary32 range
+        f = 0x7f800000u;
+    } else {                                              // binary32 subnormal or zero
+        unsigned shift = 926u - e;                        // value / 2^-149 = (2^52 + m) >> shift
+        if (e == 0u || shift > 53u) {
+            f = 0u;
+        } else {
+            unsigned long long M = m | 0x0010000000000000ull;
+            unsigned long long rest = M & ((1ull << shift) - 1ull), half = 1ull << (shift - 1u);
+            f = (unsigned)(M >> shift);
+            f += (rest > half || (rest == half && (f & 1u))) ? 1u : 0u;
+        }
+    }
+    return __uint_as_float(sign | f);
+}
+__device__ __forceinline__ float d2f_rn(double v) { return d2f_rn2(v, 0); }
+__device__ __forceinline__ double f2d(float v) {
+    unsigned u = __float_as_uint(v);
+    unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long b;
+    if (e - 1u <= 253u) {                                 // normal
+        b = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (e == 0xffu) {                              // infinity, NaN (made quiet)
+        b = 0x7ff0000000000000ull | (m ? 0x0008000000000000ull | ((unsigned long long)m << 29) : 0ull);
+    } else if (m == 0u) {                                 // signed zero
+        b = 0ull;
+    } else {                                              // binary32 subnormal: m 2^-149, normal here
+        unsigned p = 31u - (unsigned)__clz((int)m);       // leading bit, 0..22
+        b = ((unsigned long long)(874u + p) << 52) | (((unsigned long long)m << (52u - p)) & 0x000fffffffffffffull);
+    }
+    return __longlong_as_double((long long)(sign | b));
 }
 
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }

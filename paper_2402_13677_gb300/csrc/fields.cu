@@ -61,15 +61,21 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
     return F[cidx(g, i, j)];
 }
 
-// Reciprocal of d > 0 to 46 bits without an FP64 division: the FP32 reciprocal of d (the
-// conversion and the IEEE reciprocal each within 2^-24 relative) refined by one Newton-Raphson
+// Reciprocal of d > 0 to about 45 bits without an FP64 division and without an FP64-pipe
+// conversion: d truncated to FP32 on the integer pipes (relative error below 2^-23), its IEEE
+// FP32 reciprocal (within 2^-24), widened exactly on the integer pipes, then one Newton-Raphson
 // step for f(r) = 1/r - d, r <- r + r (1 - d r), the residual 1 - d r formed by one fused
-// multiply-add; the step squares the relative error (below 2^-46).  The range test runs on the
-// FP32 value; outside it the FP64 division is used.
+// multiply-add: the step squares the relative error (below 2^-44.8).  Outside
+// [2^-126, 2^126) the FP64 division is used.
 __device__ inline double recip_nr(double d) {
-    float df = __double2float_rn(d);
-    if (!(df > 1e-36f && df < 1e36f)) return 1.0 / d;
-    double r = (double)__frcp_rn(df);
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e - 897u > 251u) return 1.0 / d;
+    float df = __uint_as_float(((unsigned)(b >> 63) << 31) | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    unsigned u = __float_as_uint(__frcp_rn(df));
+    double r = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                                ((unsigned long long)(((u >> 23) & 0xffu) + 896u) << 52) |
+                                                ((unsigned long long)(u & 0x7fffffu) << 29)));
     return fma(r, fma(-d, r, 1.0), r);
 }
 
@@ -949,8 +955,43 @@ void launch_split_T(const Grid& g, const uint8_t* flags, const double* x, const 
     k_split_T<<<grid1(N, 256, g.nz), 256, 0, st>>>(N, flags, x, Ts_l, Ts_v, T_l, T_v, g.zs);
 }
 
+// every sweep of one extension in one CTA per instance (grid z): a band of a few thousand cells
+// takes a few microseconds per sweep, less than a launch; __syncthreads() orders the sweeps
+// (each reads the previous one's values, written to global memory by other threads of the CTA)
+constexpr int EXT_BLOCK_THREADS = 1024;
+__global__ void __launch_bounds__(EXT_BLOCK_THREADS)
+k_extend_block(Grid g, int mode, int iters, const int* __restrict__ list, const int* __restrict__ count,
+               const uint8_t* __restrict__ flags, const int* __restrict__ idxmap, const double2* __restrict__ nb,
+               double* f0, double* va0, double* vb0, double* f1, double* va1, double* vb1) {
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    flags = zsh(flags, zo);
+    idxmap = zsh(idxmap, zo);
+    nb = zsh(nb, zo);
+    f0 = zsh(f0, zo);
+    va0 = zsh(va0, zo);
+    vb0 = zsh(vb0, zo);
+    f1 = zsh(f1, zo);
+    va1 = zsh(va1, zo);
+    vb1 = zsh(vb1, zo);
+    int n = *count;
+    for (int it = 0; it < iters; ++it) {
+        bool odd = it & 1;
+        for (int k = threadIdx.x; k < n; k += blockDim.x)
+            extend_entry(g, mode, it, it == iters - 1, k, list, flags, idxmap, nb, f0, odd ? vb0 : va0,
+                         odd ? va0 : vb0, f1, odd ? vb1 : va1, odd ? va1 : vb1);
+        __syncthreads();
+    }
+}
+
 void launch_extend(const Grid& g, int mode, int iters, const int* list, const int* count, const uint8_t* flags,
                    const int* idxmap, const double2* nb, double* f, double* va, double* vb, cudaStream_t st) {
+    if (g.ext_block) {
+        k_extend_block<<<dim3(1, 1, g.nz), EXT_BLOCK_THREADS, 0, st>>>(g, mode, iters, list, count, flags, idxmap, nb,
+                                                                      f, va, vb, nullptr, nullptr, nullptr);
+        return;
+    }
     int nb_ = extend_grid_blocks(g);
     for (int it = 0; it < iters; ++it) {
         const double* cur = (it & 1) ? vb : va;
@@ -963,6 +1004,11 @@ void launch_extend(const Grid& g, int mode, int iters, const int* list, const in
 void launch_extend_T(const Grid& g, int iters, const int* list, const int* count, const uint8_t* flags,
                      const int* idxmap, const double2* nb, double* T_l, double* T_v, double* const ext[4],
                      cudaStream_t st) {
+    if (g.ext_block) {
+        k_extend_block<<<dim3(1, 1, g.nz), EXT_BLOCK_THREADS, 0, st>>>(g, 3, iters, list, count, flags, idxmap, nb,
+                                                                      T_l, ext[0], ext[1], T_v, ext[2], ext[3]);
+        return;
+    }
     int nb_ = extend_grid_blocks(g);
     for (int it = 0; it < iters; ++it) {
         int a = it & 1;

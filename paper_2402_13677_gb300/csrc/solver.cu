@@ -150,6 +150,34 @@ __device__ inline void block_partial(const double* v, double* partial, int nslot
         if (threadIdx.x == 0) partial[k * nslot + slot] = r;
     }
 }
+// the same block sum in the solver precision T, converted once (thread 0): the r.z of a tile's
+// FP32 cells is summed in FP32 (its slot then joins the FP64 total in tile order), so the tile
+// kernels issue no FP64 shuffles
+template <typename T>
+__device__ inline T bsum_t(T v, T* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    T r = T(0);
+    if (w == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return f2d(v); }
+template <typename T, int NV>
+__device__ inline void block_partial_t(const T* v, double* partial, int nslot, int slot) {
+    __shared__ T sh[32];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        T r = bsum_t(v[k], sh);
+        if (threadIdx.x == 0) partial[k * nslot + slot] = widen(r);
+    }
+}
 template <int NV>
 __device__ inline bool last_block_total(double* partial, int nslot, unsigned* ticket, double* tot) {
     __shared__ double sh[32];
@@ -239,10 +267,11 @@ struct Region {
 };
 template <int H>
 constexpr int tile_block() { return (((TX + 2 * H) / 2) * ((TY + 2 * H) / 2) + 31) / 32 * 32; }
-// blocks per SM the single-value FP32 tile kernels are compiled for (register budget); the
-// others keep the compiler's choice
+// blocks per SM the FP32 tile kernels are compiled for (register budget: two blocks, 72
+// registers, measured 1.2 % faster on the 4096^2 film than three blocks with spills); the FP64
+// ones keep the compiler's choice
 template <typename T, int NR>
-constexpr int tile_min_blocks() { return sizeof(T) == 4 ? (NR == 1 ? 3 : 2) : 1; }
+constexpr int tile_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 
 // ---- TMA staging of the tile regions ------------------------------------------------------
 // One elected thread issues a 2-D tensor copy (cp.async.bulk.tensor) per operand array into
@@ -670,7 +699,7 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
 // post-smoothing of tile (bx, by): x = xin + P xc, then black-red sweeps; returns the tile's
 // part of r.z (each right-hand side) when DOT; after_load() as for pre_tile
 template <typename T, int NR, bool DOT, class AfterLoad = NoOp>
-__device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, const T* __restrict__ xin,
+__device__ inline Vec<T, 2> post_tile(const Lev<T>& L, const T* __restrict__ b, const T* __restrict__ xin,
                                     T* __restrict__ x, const T* __restrict__ xc, int bx, int by, unsigned char* smem,
                                     const unsigned char* stage, AfterLoad after_load = AfterLoad()) {
     constexpr int H = HPOST;
@@ -688,19 +717,20 @@ __device__ inline double2 post_tile(const Lev<T>& L, const T* __restrict__ b, co
     tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 4, 0>(R, C, k, ry0, act);
-    // r.z of the thread's (at most four) core cells: summed in T, then one conversion
-    T dot[2] = {T(0), T(0)};
+    // r.z of the thread's (at most four) core cells, summed in T
+    Vec<T, 2> dot;
+    dot.v[0] = dot.v[1] = T(0);
     if (act)
         tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
             Vec<T, NR> xv;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
                 xv.v[k2] = C.x[r][c][k2];
-                if (DOT) dot[k2] += xv.v[k2] * C.b[r][c][k2];
+                if (DOT) dot.v[k2] += xv.v[k2] * C.b[r][c][k2];
             }
             reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
         });
-    return make_double2((double)dot[0], (double)dot[1]);
+    return dot;
 }
 
 // k_post: one tile per block; at the finest level also r.z -> beta
@@ -737,19 +767,13 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
         // r.z: one slot per tile, summed in tile order as with one block per tile
         staged_tiles<T, NR, H, true>(stage, maps, tx, nt, st, [&](int t, auto after_load) {
-            double2 d = post_tile<T, NR, DOT>(L, b, xin, x, xc, t % tx, t / tx, smem, stage, after_load);
-            if (DOT) {
-                double dot[2] = {d.x, d.y};
-                block_partial<NR>(dot, partial, nt, t);
-            }
+            Vec<T, 2> d = post_tile<T, NR, DOT>(L, b, xin, x, xc, t % tx, t / tx, smem, stage, after_load);
+            if (DOT) block_partial_t<T, NR>(d.v, partial, nt, t);
         });
         nslot = nt;
     } else {
-        double2 d = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, nullptr);
-        if (DOT) {
-            double dot[2] = {d.x, d.y};
-            block_partial<NR>(dot, partial, nslot, blockIdx.y * gridDim.x + blockIdx.x);
-        }
+        Vec<T, 2> d = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, nullptr);
+        if (DOT) block_partial_t<T, NR>(d.v, partial, nslot, blockIdx.y * gridDim.x + blockIdx.x);
     }
     if (DOT) {
         double tot[NR];
@@ -1190,6 +1214,14 @@ __device__ inline void coarse_inverse_warp(int nx, int ny, const T* __restrict__
 }
 
 
+// an FP64 operator value in the solver precision (FP32: rounded on the integer pipes)
+template <typename T>
+__device__ __forceinline__ T to_prec(double v);
+template <>
+__device__ __forceinline__ double to_prec<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_prec<float>(double v) { return d2f_rn(v); }
+
 // Levels of the hierarchy as the setup kernel sees them.
 struct SetupPlan {
     int nlev, nx[Solver::MAXLEV], ny[Solver::MAXLEV];
@@ -1228,11 +1260,11 @@ __global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* _
         int c = j * nx + i;
         double ddv = dd ? dd[c] : 0.0;
         double dg = cd[c] + ddv;
-        diag[c] = (T)dg;
-        owl[c] = (T)wl[c];
-        owb[c] = (T)wb[c];
-        ocd[c] = (T)cd[c];
-        odd[c] = (T)ddv;
+        diag[c] = to_prec<T>(dg);
+        owl[c] = to_prec<T>(wl[c]);
+        owb[c] = to_prec<T>(wb[c]);
+        ocd[c] = to_prec<T>(cd[c]);
+        odd[c] = to_prec<T>(ddv);
         if (d64) d64[c] = dg;
     }
     __syncthreads();   // this block's level-l cells are read back by its own threads below
@@ -1274,10 +1306,15 @@ __global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* _
 // ---- CG kernels ---------------------------------------------------------------------------
 // p_new = z + beta p_old; q = A p_new; p.q -> alpha = r.z / p.q
 // Dot-product accumulation of a thread: FP64 for FP64 data; for FP32 data the products are
-// summed in FP32 over chunks of 8 terms and each chunk added to the FP64 total (one FP64 add per
-// 8 cells: FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU).  The inner
-// FP32 solves of the refinement work on a residual scaled to values of order one (k_ir_residual),
-// so FP32 products neither underflow nor overflow there.
+// summed in FP32 over chunks of DOT_CHUNK cells and each chunk added to the FP64 total (one FP64
+// add per chunk: FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU).  The
+// kernels walk their cells in chunks with flush() after each, outside the per-cell body: a
+// counter test inside the body is compiled to a predicated FP64 add issued for every cell, which
+// kept the FP64 pipe 40-60 % busy in these memory-bound kernels.  The inner FP32 solves of the
+// refinement work on a residual scaled to values of order one (k_ir_residual), so FP32 products
+// neither underflow nor overflow there.  (k_apply keeps one cell per loop iteration with a
+// counted flush: there the loop shape that keeps more loads in flight measured faster.)
+constexpr int DOT_CHUNK = 8;
 template <typename T, int NR>
 struct DotAcc {
     double tot[NR];
@@ -1292,26 +1329,16 @@ template <int NR>
 struct DotAcc<float, NR> {
     double tot[NR];
     float part[NR];
-    int n = 0;
     __device__ DotAcc() {
 #pragma unroll
         for (int k = 0; k < NR; ++k) { tot[k] = 0.0; part[k] = 0.0f; }
     }
     __device__ void add(int k, float a, float b) { part[k] = fmaf(a, b, part[k]); }
-    // call once per cell, after its NR products
-    __device__ void next() {
-        if (++n == 8) flush();
-    }
     __device__ void flush() {
 #pragma unroll
         for (int k = 0; k < NR; ++k) { tot[k] += (double)part[k]; part[k] = 0.0f; }
-        n = 0;
     }
 };
-template <typename T, int NR>
-__device__ inline void dot_next(DotAcc<T, NR>&) {}
-template <int NR>
-__device__ inline void dot_next(DotAcc<float, NR>& d) { d.next(); }
 
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z, T* __restrict__ p0,
@@ -1338,6 +1365,7 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
     for (int k = 0; k < NR; ++k) beta[k] = (T)st->beta[k];
     int N = L.nx * L.ny;
     DotAcc<T, NR> acc;
+    int nchunk = 0;
 #pragma unroll 2
     for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
         int c = cw.c, i = cw.i, j = cw.j;
@@ -1378,7 +1406,10 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
         }
 #pragma unroll
         for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
-        dot_next(acc);
+        if (++nchunk == DOT_CHUNK) {   // measured faster here than chunk-structured loops
+            acc.flush();
+            nchunk = 0;
+        }
         Pn[c] = pc;
         Q[c] = qv;
     }
@@ -1418,20 +1449,25 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
 #pragma unroll
     for (int k = 0; k < NR; ++k) alpha[k] = (T)st->alpha[k];
     DotAcc<T, NR> acc;
-#pragma unroll 4
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
+    const int stride = gridDim.x * blockDim.x;
+    for (int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < N; c0 += DOT_CHUNK * stride) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            xv.v[k] += alpha[k] * pv.v[k];
-            rv.v[k] -= alpha[k] * qv.v[k];
-            acc.add(k, rv.v[k], rv.v[k]);
+        for (int u = 0; u < DOT_CHUNK; ++u) {
+            int c = c0 + u * stride;
+            if (c < N) {   // a guard, not an exit: the chunk's loads can all be in flight at once
+                Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    xv.v[k] += alpha[k] * pv.v[k];
+                    rv.v[k] -= alpha[k] * qv.v[k];
+                    acc.add(k, rv.v[k], rv.v[k]);
+                }
+                X[c] = xv;
+                Rr[c] = rv;
+            }
         }
-        dot_next(acc);
-        X[c] = xv;
-        Rr[c] = rv;
+        acc.flush();
     }
-    acc.flush();
     double tot[NR];
     if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
         bool done = true, bad = false;
@@ -1594,18 +1630,26 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
     ticket = zsh(ticket, zo);
     if (st->odone) return;
     int N = L.nx * L.ny;
-    // the inner FP32 system is solved for s r, s a power of two that brings the residual's
+    // the inner FP32 system is solved for s r, s = 2^k a power of two that brings the residual's
     // cell values to order one, set from the previous residual norm (of b on the first pass) by
-    // the launch that computed it: the same in every block
+    // the launch that computed it: the same in every block.  The FP32 copy is rounded from
+    // r 2^k on the integer pipes and the norm is summed from that copy (FP32 chunks added in
+    // FP64; relative accuracy about 1e-7, ample for the convergence test), so the FP64 pipe
+    // carries the residual alone.
     double sc[NR];
+    int ksc[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) sc[k] = st->scale_next[k];
-    double acc[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NR; ++k) {
+        sc[k] = st->scale_next[k];
+        ksc[k] = (int)((__double_as_longlong(sc[k]) >> 52) & 0x7ff) - 1023;
+    }
+    DotAcc<float, NR> acc;
     const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
-    for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
+    for (CellWalk cw(L.nx); cw.c < N; acc.flush())
+#pragma unroll
+    for (int u = 0; u < DOT_CHUNK; ++u, cw.next()) {
+        if (cw.c >= N) continue;
         int c = cw.c, i = cw.i, j = cw.j;
         Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
         double dg = L.diag[c];
@@ -1626,26 +1670,26 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
         Vec<float, NR> rf, ez;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            double rv = bv.v[k] - s.v[k];
-            acc[k] += rv * rv;
-            rf.v[k] = (float)(rv * sc[k]);
+            float f = d2f_rn2(bv.v[k] - s.v[k], ksc[k]);
+            rf.v[k] = f;
+            acc.add(k, f, f);
             ez.v[k] = 0.0f;
         }
         reinterpret_cast<Vec<float, NR>*>(r32)[c] = rf;
         reinterpret_cast<Vec<float, NR>*>(e32)[c] = ez;
     }
     double tot[NR];
-    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+    if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
         bool done = true;
         for (int k = 0; k < 2; ++k) {
-            double rr = k < NR ? tot[k] : 0.0;
+            double s2 = k < NR ? sc[k] * sc[k] : 1.0;   // a power of two: the divisions are exact
+            double rr = k < NR ? tot[k] / s2 : 0.0;
             st->orr[k] = rr;
             if (!(rr <= st->otol2[k])) done = false;
             if (!isfinite(rr) || !isfinite(st->obb[k])) st->nonfinite = 1;
-            double s2 = k < NR ? sc[k] * sc[k] : 1.0;
             st->scale[k] = k < NR ? sc[k] : 1.0;
             st->scale_next[k] = unit_scale(rr, N);
-            st->rr[k] = rr * s2;
+            st->rr[k] = k < NR ? tot[k] : 0.0;
             // the inner solve reduces the residual by inner_rtol, but never below half the
             // outer target: no solve past what the refinement needs (in the scaled units)
             st->tol2[k] = fmax(st->inner_rtol * st->inner_rtol * rr, 0.25 * st->otol2[k]) * s2;
@@ -1671,9 +1715,26 @@ __global__ void k_ir_update(int N, long long zs, double* __restrict__ x, const f
     e = zsh(e, zo);
     st = zsh(st, zo);
     if (st->odone) return;
-    double inv[2] = {1.0 / st->scale[0], NR > 1 ? 1.0 / st->scale[1] : 1.0};   // powers of two: exact
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N * NR; c += gridDim.x * blockDim.x)
-        x[c] += (double)e[c] * inv[NR > 1 ? (c & 1) : 0];
+    // powers of two: exact; an even element belongs to the first right-hand side
+    const double inv0 = 1.0 / st->scale[0], inv1 = NR > 1 ? 1.0 / st->scale[1] : inv0;
+    const long long n = (long long)N * NR;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, T = gridDim.x * blockDim.x;
+    // four elements per step (one 16-byte load of e, two of x) where both arrays allow it
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(e)) & 15u) == 0;
+    const long long n4 = vec ? n / 4 : 0;
+#pragma unroll 2
+    for (long long q = t; q < n4; q += T) {
+        float4 ev = reinterpret_cast<const float4*>(e)[q];
+        double2* xp = reinterpret_cast<double2*>(x) + 2 * q;
+        double2 a = xp[0], b = xp[1];
+        a.x += f2d(ev.x) * inv0;
+        a.y += f2d(ev.y) * inv1;
+        b.x += f2d(ev.z) * inv0;
+        b.y += f2d(ev.w) * inv1;
+        xp[0] = a;
+        xp[1] = b;
+    }
+    for (long long c = 4 * n4 + t; c < n; c += T) x[c] += f2d(e[c]) * ((c & 1) ? inv1 : inv0);
 }
 
 // ---------------------------------------------------------------------------------------

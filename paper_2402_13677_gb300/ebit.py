@@ -43,6 +43,7 @@ EBIT_OPT_GRAPH = 1
 EBIT_OPT_TMA = 2
 EBIT_OPT_COOP = 3
 EBIT_OPT_BARRIER_SPIN = 4
+EBIT_OPT_EXT_BLOCK = 5
 EBIT_KT_SMOOTH_L0 = 1
 
 

@@ -149,3 +149,33 @@ def test_batched_launch_timer_counts_each_launch_once(dev):
     assert n_1 > 0 and n_b == n_1
     assert ms_b > 0 and ms_1 > 0
     assert b_b == pytest.approx(nz * b_1, rel=1e-12)
+
+
+def axi_batch_problems():
+    """Axisymmetric instances: three constant-flux spheres of different densities and
+    viscosities (one batch: the grid, boundaries and imposed flux are shared) and two Scriven
+    bubbles of different density ratios (a second batch, energy on)."""
+    out = [w.axi_const_mdot_bubble(n=32, R0=0.3, rho_l=rl, mu=mu, dt=1e-3, steps=0)
+           for rl, mu in ((10.0, 0.01), (20.0, 0.02), (5.0, 0.005))]
+    out += [w.scriven(n=32, R0=0.3, rho_ratio=rr, dt=2e-5, steps=0) for rr in (20.0, 10.0)]
+    return out
+
+
+@pytest.mark.parametrize("precision", [E.EBIT_FP64, E.EBIT_MIXED])
+def test_batched_axisymmetric_instances_equal_single_instance_runs(dev, precision):
+    pbs = axi_batch_problems()
+    ctx = make_ctx(dev, pbs, precision)
+    try:
+        E.ebit_step(ctx, 2)
+        got = [E.download(ctx, b, pb.nx, pb.ny, NAMES) for b, pb in enumerate(pbs)]
+    finally:
+        E.ebit_destroy(ctx)
+    for b, pb in enumerate(pbs):
+        one = make_ctx(dev, [pb], precision)
+        try:
+            E.ebit_step(one, 2)
+            ref = E.download(one, 0, pb.nx, pb.ny, NAMES)
+        finally:
+            E.ebit_destroy(one)
+        for k in NAMES:
+            assert np.array_equal(got[b][k], ref[k]), (b, pb.name, k)

@@ -537,6 +537,26 @@ def test_cooperative_coarse_cycle_equals_separate_launches(dev, name, precision)
         assert np.array_equal(out[0][k], out[1][k]), k
 
 
+@pytest.mark.parametrize("name", ["bubble_mid", "saddle", "stefan"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_single_block_extension_equals_launch_per_sweep(dev, name, graph):
+    """The narrow-band extensions give the same values with every Jacobi sweep in one thread
+    block as with one launch per sweep over the whole device: two steps agree bit for bit."""
+    st = prepared(name, 0)
+    out = []
+    for ext in (1, 0):
+        ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-10)
+        try:
+            E.ebit_set_option(ctx, E.EBIT_OPT_GRAPH, 1 if graph else 0)
+            E.ebit_set_option(ctx, E.EBIT_OPT_EXT_BLOCK, ext)
+            E.ebit_step(ctx, 2)
+            out.append(E.download(ctx, 0, st.pb.nx, st.pb.ny))
+        finally:
+            E.ebit_destroy(ctx)
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
 def test_batched_field_copies_equal_single_field_copies(dev):
     """ebit_set_fields / ebit_get_fields (one synchronisation per call) move the same bytes as
     one ebit_set_field / ebit_get_field per field, from and to page-locked host buffers and

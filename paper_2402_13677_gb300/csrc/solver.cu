@@ -1109,25 +1109,28 @@ constexpr int CC_THREADS = 512;
 // grid-wide barrier of a cooperative launch (all blocks resident).  bar[0] counts arrivals and
 // only grows during a launch (the level-0 pre-smoothing kernel, which precedes every launch,
 // zeroes it): barrier k of the launch is passed once it reaches k x (number of blocks).  One
-// atomic per block and acquire loads while waiting; the wait is bounded and a timeout is
+// release reduction per block (it publishes the writes the block's threads made before the
+// block barrier) and acquire loads while waiting (the writes of the other blocks are visible to
+// this block's threads after the closing block barrier); the wait is bounded and a timeout is
 // recorded in st->fault.
 __device__ inline unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ inline void red_release_gpu_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ inline void grid_sync(unsigned* bar, unsigned& target, SolveState* st, int spin) {
     target += gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&bar[0], 1u);
+        red_release_gpu_add(&bar[0], 1u);
         for (int it = 0; (int)(ld_acquire_gpu(&bar[0]) - target) < 0; ++it)
             if (it > spin) {
                 atomicOr(&st->fault, 2);
                 break;
             }
-        __threadfence();
     }
     __syncthreads();
 }

@@ -265,24 +265,26 @@ static void reconstruct_full(Instance& I, cudaStream_t st) {
     count(3);   // + memset
 }
 
+// kernels of one narrow-band extension: one in a single block per instance, else one per sweep
+static int extend_launches(const Instance& I) { return I.g.ext_block ? 1 : I.p.extend_iters; }
+
 static void extend_T(Instance& I, double* Tl, double* Tv, cudaStream_t st) {
-    int it = I.p.extend_iters;
-    launch_extend_T(I.g, it, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tl, Tv, I.ext, st);
-    count(it);
+    launch_extend_T(I.g, I.p.extend_iters, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, Tl, Tv, I.ext, st);
+    count(extend_launches(I));
 }
 
 static void mass_flux(Instance& I, cudaStream_t st) {
     launch_mass_flux(I.g, I.p, I.cseg, I.hpos, I.vpos, I.T_l, I.T_v, I.mdot, st);
     launch_extend(I.g, 2, I.p.extend_iters, I.band_list, I.band_count, I.flags, I.band_idx, I.nb, I.mdot, I.ext[0],
                   I.ext[1], st);
-    count(1 + I.p.extend_iters);
+    count(1 + extend_launches(I));
 }
 
 static void ghost_velocity(Instance& I, cudaStream_t st) {
     if (I.p.one_fluid) return;   // one velocity field: no ghost values
-    launch_ghost_velocity(I.g, I.p, I.flags, I.mdot, I.nb, I.vcol, I.hpos, I.vpos, I.u_l, I.u_v, I.ufx_l, I.ufx_v,
-                          I.ufy_l, I.ufy_v, st);
-    count(2);
+    launch_ghost_velocity(I.g, I.p, I.band_list, I.band_count, I.flags, I.mdot, I.nb, I.vcol, I.hpos, I.vpos, I.u_l,
+                          I.u_v, I.ufx_l, I.ufx_v, I.ufy_l, I.ufy_v, st);
+    count(1);
 }
 
 // S2-S5 over the cells within two of the interface: the narrow band of the start-of-step

@@ -320,19 +320,11 @@ __global__ void k_split_T(int N, const uint8_t* __restrict__ flags, const double
 // ---------------------------------------------------------------------------------
 // S10: ghost velocities (cells and faces)
 // ---------------------------------------------------------------------------------
-__global__ void k_ghost_cells(Grid g, double J, const uint8_t* __restrict__ flags, const double* __restrict__ mdot,
-                              const double2* __restrict__ nb, double2* u_l, double2* u_v) {
-    if (g.pz) J = 1.0 / g.pz[blockIdx.z].rho_l - 1.0 / g.pz[blockIdx.z].rho_v;
-    const long long zo = zoff(g.zs);
-    flags = zsh(flags, zo);
-    mdot = zsh(mdot, zo);
-    nb = zsh(nb, zo);
-    u_l = zsh(u_l, zo);
-    u_v = zsh(u_v, zo);
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.nx * g.ny) return;
+// ghost value of a band cell: the other phase's velocity from the velocity-jump equation,
+// u_v = u_l - [1/rho] mdot n (liquid centre) or u_l = u_v + [1/rho] mdot n (vapour centre)
+__device__ inline void ghost_cell(const Grid& g, double J, int c, const uint8_t* flags, const double* mdot,
+                                  const double2* nb, double2* u_l, double2* u_v) {
     uint8_t fl = flags[c];
-    if (!(fl & F_BAND)) return;
     double m = mdot[c];
     double2 n = nb[c];
     double mx = m * n.x, my = m * n.y;
@@ -345,48 +337,71 @@ __global__ void k_ghost_cells(Grid g, double J, const uint8_t* __restrict__ flag
     }
 }
 
-// x-faces (interior, between cells i-1 and i) and y-faces (interior, between rows j-1 and j)
-__global__ void k_ghost_faces(Grid g, double J, const uint8_t* __restrict__ flags, const double* __restrict__ mdot,
-                              const double2* __restrict__ nb, const uint8_t* __restrict__ vcol,
-                              const double* __restrict__ hpos, const double* __restrict__ vpos,
-                              double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v) {
+// ghost value of the interior x-face t (between cells i - 1 and i of row j) or, with y, of the
+// interior y-face t (between rows j - 1 and j of column i), if one of its cells is in the band:
+// the phase of the face is the colour of its nearer end (the marker position on it decides),
+// the face mass flux the mean of its two cells' mdot n
+__device__ inline void ghost_face(const Grid& g, double J, bool y, int i, int j, const uint8_t* flags,
+                                  const double* mdot, const double2* nb, const uint8_t* vcol, const double* hpos,
+                                  const double* vpos, double* uf_l, double* uf_v) {
+    if (!y) {
+        if (i <= 0 || i >= g.nx) return;
+        int a = cidx(g, i - 1, j), b = cidx(g, i, j);
+        if (!((flags[a] | flags[b]) & F_BAND)) return;
+        long long t = veidx(g, i, j);
+        double mf = 0.5 * (mdot[a] * nb[a].x + mdot[b] * nb[b].x);
+        uint8_t v0 = vcol[vidx(g, i, j)], v1 = vcol[vidx(g, i, j + 1)];
+        int colour = (v0 != v1 && vpos[t] < 0.5) ? v1 : v0;
+        if (colour) uf_v[t] = uf_l[t] - J * mf;
+        else uf_l[t] = uf_v[t] + J * mf;
+    } else {
+        if (j <= 0 || j >= g.ny) return;
+        int a = cidx(g, i, j - 1), b = cidx(g, i, j);
+        if (!((flags[a] | flags[b]) & F_BAND)) return;
+        long long t = hidx(g, i, j);
+        double mf = 0.5 * (mdot[a] * nb[a].y + mdot[b] * nb[b].y);
+        uint8_t v0 = vcol[vidx(g, i, j)], v1 = vcol[vidx(g, i + 1, j)];
+        int colour = (v0 != v1 && hpos[t] < 0.5) ? v1 : v0;
+        if (colour) uf_v[t] = uf_l[t] - J * mf;
+        else uf_l[t] = uf_v[t] + J * mf;
+    }
+}
+
+// S10 over the band list (O(sqrt N)): five items per band cell, the cell and its four faces.
+// A face of two band cells is written twice with the same value from the same inputs (each
+// write reads the other phase's face velocity, which neither writes).
+__global__ void k_ghost_list(Grid g, double J, const int* __restrict__ list, const int* __restrict__ count,
+                             const uint8_t* __restrict__ flags, const double* __restrict__ mdot,
+                             const double2* __restrict__ nb, const uint8_t* __restrict__ vcol,
+                             const double* __restrict__ hpos, const double* __restrict__ vpos, double2* u_l,
+                             double2* u_v, double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v) {
     if (g.pz) J = 1.0 / g.pz[blockIdx.z].rho_l - 1.0 / g.pz[blockIdx.z].rho_v;
     const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
     flags = zsh(flags, zo);
     mdot = zsh(mdot, zo);
     nb = zsh(nb, zo);
     vcol = zsh(vcol, zo);
     hpos = zsh(hpos, zo);
     vpos = zsh(vpos, zo);
+    u_l = zsh(u_l, zo);
+    u_v = zsh(u_v, zo);
     ufx_l = zsh(ufx_l, zo);
     ufx_v = zsh(ufx_v, zo);
     ufy_l = zsh(ufy_l, zo);
     ufy_v = zsh(ufy_v, zo);
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long nfx = (long long)g.ny * (g.nx + 1);
-    long long nfy = (long long)(g.ny + 1) * g.nx;
-    if (t < nfx) {
-        // faces < 2^31 (nx ny <= 2^29): 32-bit division
-        int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
-        if (i == 0 || i == g.nx) return;
-        int a = cidx(g, i - 1, j), b = cidx(g, i, j);
-        if (!((flags[a] | flags[b]) & F_BAND)) return;
-        double mf = 0.5 * (mdot[a] * nb[a].x + mdot[b] * nb[b].x);
-        uint8_t v0 = vcol[vidx(g, i, j)], v1 = vcol[vidx(g, i, j + 1)];
-        int colour = (v0 != v1 && vpos[t] < 0.5) ? v1 : v0;
-        if (colour) ufx_v[t] = ufx_l[t] - J * mf;
-        else ufx_l[t] = ufx_v[t] + J * mf;
-    } else if (t < nfx + nfy) {
-        long long e = t - nfx;
-        int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
-        if (j == 0 || j == g.ny) return;
-        int a = cidx(g, i, j - 1), b = cidx(g, i, j);
-        if (!((flags[a] | flags[b]) & F_BAND)) return;
-        double mf = 0.5 * (mdot[a] * nb[a].y + mdot[b] * nb[b].y);
-        uint8_t v0 = vcol[vidx(g, i, j)], v1 = vcol[vidx(g, i + 1, j)];
-        int colour = (v0 != v1 && hpos[e] < 0.5) ? v1 : v0;
-        if (colour) ufy_v[e] = ufy_l[e] - J * mf;
-        else ufy_l[e] = ufy_v[e] + J * mf;
+    long long n = 5LL * *count;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int c = list[t / 5], q = (int)(t % 5);
+        int i = c % g.nx, j = c / g.nx;
+        switch (q) {
+            case 0: ghost_cell(g, J, c, flags, mdot, nb, u_l, u_v); break;
+            case 1: ghost_face(g, J, false, i, j, flags, mdot, nb, vcol, hpos, vpos, ufx_l, ufx_v); break;
+            case 2: ghost_face(g, J, false, i + 1, j, flags, mdot, nb, vcol, hpos, vpos, ufx_l, ufx_v); break;
+            case 3: ghost_face(g, J, true, i, j, flags, mdot, nb, vcol, hpos, vpos, ufy_l, ufy_v); break;
+            default: ghost_face(g, J, true, i, j + 1, flags, mdot, nb, vcol, hpos, vpos, ufy_l, ufy_v); break;
+        }
     }
 }
 
@@ -1017,15 +1032,16 @@ void launch_extend_T(const Grid& g, int iters, const int* list, const int* count
     }
 }
 
-void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, const double* mdot, const double2* nb,
-                           const uint8_t* vcol, const double* hpos, const double* vpos, double2* u_l, double2* u_v,
-                           double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st) {
+void launch_ghost_velocity(const Grid& g, const Phys& p, const int* band_list, const int* band_count,
+                           const uint8_t* flags, const double* mdot, const double2* nb, const uint8_t* vcol,
+                           const double* hpos, const double* vpos, double2* u_l, double2* u_v, double* ufx_l,
+                           double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st) {
     double J = 1.0 / p.rho_l - 1.0 / p.rho_v;
-    int N = g.nx * g.ny;
-    k_ghost_cells<<<grid1(N, 256, g.nz), 256, 0, st>>>(g, J, flags, mdot, nb, u_l, u_v);
-    long long nf = (long long)g.ny * (g.nx + 1) + (long long)(g.ny + 1) * g.nx;
-    k_ghost_faces<<<grid1(nf, 256, g.nz), 256, 0, st>>>(g, J, flags, mdot, nb, vcol, hpos, vpos, ufx_l, ufx_v, ufy_l,
-                                                   ufy_v);
+    // five items per band cell; the band is O(sqrt N): blocks as for the other list kernels
+    long long nbk = div_up(5LL * 8 * (g.nx + g.ny), 256);
+    int blocks = (int)(nbk < 4 ? 4 : (nbk > 4 * 152 ? 4 * 152 : nbk));
+    k_ghost_list<<<dim3(blocks, 1, g.nz), 256, 0, st>>>(g, J, band_list, band_count, flags, mdot, nb, vcol, hpos,
+                                                        vpos, u_l, u_v, ufx_l, ufx_v, ufy_l, ufy_v);
 }
 
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,

@@ -361,16 +361,24 @@ __device__ inline void sweep_aligned(const SweepView& sv, const uint8_t* vcol_n,
         o = veidx(g, l, e);
     }
     if (!cut) { out[o] = 0.0; return; }
-    double cand[8];
+    double cand[8];   // at most five candidates; the first stays in a register
+    double first = 0.0;
     int n = 0;
     for (int ee = e - 2; ee <= e + 2; ++ee) {
         if (ee < 0 || ee >= nal || !sv.a_cut(l, ee)) continue;
         double al = sv.a_disp(l, ee);
         double fl = floor(al);
         if ((int)fl != e) continue;
-        cand[n++] = clampf(al - fl);
+        double v = clampf(al - fl);
+        if (n == 0) {
+            first = v;
+        } else {
+            if (n == 1) cand[0] = first;
+            cand[n] = v;
+        }
+        ++n;
     }
-    out[o] = pick_median(cand, n);
+    out[o] = n == 1 ? first : pick_median(cand, n);
 }
 
 // circle (through E, O, R) or chord (through E, O) crossing of the unaligned line at m
@@ -448,8 +456,24 @@ __device__ inline void sweep_unaligned(const SweepView& sv, const uint16_t* cseg
         o = hidx(g, e, m);
     }
     if (!cut) { out[o] = 0.0; return; }
+    // candidate positions: the first in a register (most edges have one), the array (local
+    // memory) only once a second arrives
     double cand[32];
+    double first = 0.0;
     int n = 0;
+    auto push = [&](double v) {
+        if (n >= 32) {
+            atomicOr(status, 2);
+            return;
+        }
+        if (n == 0) {
+            first = v;
+        } else {
+            if (n == 1) cand[0] = first;
+            cand[n] = v;
+        }
+        ++n;
+    };
     const double dm = (double)m;
     // (i) displaced segments of the cells of this row/column straddling the line
     for (int c = m - 2; c <= m + 1; ++c) {
@@ -473,8 +497,7 @@ __device__ inline void sweep_unaligned(const SweepView& sv, const uint16_t* cseg
             double2 R;
             bool hasR = chain_neighbour(sv, cseg, ci, cj, kE, &R);
             double ac = crossing(E, O, hasR, R, m, sv.axis);
-            if (n < 32) cand[n++] = clampf(ac - (double)e);
-            else atomicOr(status, 2);
+            push(clampf(ac - (double)e));
         }
     }
     // (ii) displaced markers exactly on the line: unaligned markers of nearby lines
@@ -485,10 +508,7 @@ __device__ inline void sweep_unaligned(const SweepView& sv, const uint16_t* cseg
             double ac = sv.u_orig_ac(mm, e);
             double fl = floor(ac);
             int ee = min(max((int)fl, 0), nac - 1);
-            if (ee == e) {
-                if (n < 32) cand[n++] = clampf(ac - (double)ee);
-                else atomicOr(status, 2);
-            }
+            if (ee == e) push(clampf(ac - (double)ee));
         }
     }
     //      and aligned markers whose line maps to this edge index
@@ -499,14 +519,11 @@ __device__ inline void sweep_unaligned(const SweepView& sv, const uint16_t* cseg
             if (sv.a_disp(l, ea) == dm) {
                 double ac = (double)l;
                 int ee = min(max(l, 0), nac - 1);
-                if (ee == e) {
-                    if (n < 32) cand[n++] = clampf(ac - (double)ee);
-                    else atomicOr(status, 2);
-                }
+                if (ee == e) push(clampf(ac - (double)ee));
             }
         }
     }
-    out[o] = pick_median(cand, n);
+    out[o] = n == 1 ? first : pick_median(cand, n);
 }
 
 // ---------------------------------------------------------------------------------

@@ -49,9 +49,10 @@ void launch_extend_T(const Grid& g, int iters, const int* list, const int* count
                      cudaStream_t st);
 void launch_split_T(const Grid& g, const uint8_t* flags, const double* x, const double* Ts_l, const double* Ts_v,
                     double* T_l, double* T_v, cudaStream_t st);
-void launch_ghost_velocity(const Grid& g, const Phys& p, const uint8_t* flags, const double* mdot, const double2* nb,
-                           const uint8_t* vcol, const double* hpos, const double* vpos, double2* u_l, double2* u_v,
-                           double* ufx_l, double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st);
+void launch_ghost_velocity(const Grid& g, const Phys& p, const int* band_list, const int* band_count,
+                           const uint8_t* flags, const double* mdot, const double2* nb, const uint8_t* vcol,
+                           const double* hpos, const double* vpos, double2* u_l, double2* u_v, double* ufx_l,
+                           double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st);
 void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
                           double* wl, double* wb, cudaStream_t st);
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,

@@ -291,7 +291,7 @@ ebit_status ebit_solve_system_noalloc(int nx, int ny, const double* D, const dou
  * the duration of the call.  Needs graph mode.  EBIT_ENOMEM when the snapshot does not fit. */
 ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps);
 /* The schedule an instance uses: single-block level size, inner tolerance, TMA staging,
- * cooperative coarse cycle. */
+ * cooperative launches (EBIT_OPT_COOP's values). */
 ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* inner_rtol, int* tma, int* coop);
 
 /* Options:
@@ -305,7 +305,13 @@ ebit_status ebit_get_schedule(ebit_ctx* ctx, int inst, int* small_max, double* i
  *   EBIT_OPT_COOP (default 1) runs the coarse tiled levels of each V-cycle (those whose tiles
  *   fit one per co-resident block) and the single-block levels in one cooperative launch with
  *   grid barriers between the phases; 0 launches each level separately.  Both give the same
- *   values.  Instances stepped in batches always launch each level separately.
+ *   values.  2 (mixed precision) runs each whole inner FP32 solve of the refinement, every
+ *   V-cycle and CG update until the inner tolerance, in one cooperative launch with bounded
+ *   grid barriers between its phases (grids whose finest tiles fit the reduction slots; others
+ *   fall back to 1); its dot products are grouped per block, so the iterates agree with the
+ *   other forms to rounding, not bit for bit (measured 10-30 % slower than 0 or 1 on 512^2 and
+ *   1024x2048 grids, where its one block per SM and the spills of its 128 registers outweigh
+ *   the saved launches).  Instances stepped in batches always launch each level separately.
  *   EBIT_OPT_BARRIER_SPIN (default 0 = 2^22 polls) bounds the wait of each grid barrier of the
  *   cooperative launch, in polls of the arrival counter.  A fault-path test setting: a bound of
  *   a few polls makes the barriers give up before the other blocks arrive.  Changing it drops

@@ -1065,6 +1065,9 @@ ebit_status ebit_autotune(ebit_ctx* ctx, int trial_steps) {
         std::vector<double> inners = I0.cfg.precision == EBIT_MIXED ? std::vector<double>{1e-4, 1e-5}
                                                                     : std::vector<double>{1e-5};
         std::vector<int> tmas = U.batch ? std::vector<int>{0} : std::vector<int>{1, 0};
+        // cooperative launches: none or the coarse part of each V-cycle (a whole inner solve in
+        // one launch measured slower at 512^2 and 1024x2048 and is not a candidate); batched
+        // instances launch every kernel per level
         std::vector<int> coops = U.batch ? std::vector<int>{0} : std::vector<int>{1, 0};
         float best = 1e30f;
         int bs = I0.solver.small_max_f, bt = I0.solver.use_tma, bc = I0.solver.use_coop;
@@ -1182,7 +1185,7 @@ ebit_status ebit_set_option(ebit_ctx* ctx, int option, int value) {
         for (auto& I : ctx->inst) {
             for (Solver* sv : {&I.solver, &I.solver2}) {
                 if (option == EBIT_OPT_TMA) sv->use_tma = value ? 1 : 0;
-                else if (option == EBIT_OPT_COOP) sv->use_coop = value ? 1 : 0;
+                else if (option == EBIT_OPT_COOP) sv->use_coop = value <= 0 ? 0 : (value >= 2 ? 2 : 1);
                 else sv->barrier_spin = value;
             }
             for (auto& gx : I.graph)

@@ -1490,6 +1490,237 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
     }
 }
 
+// ---- a whole inner solve in one cooperative launch (small grids) ---------------------------
+// On small grids a CG iteration is a handful of short kernels (the V-cycle legs, p/q, x/r), each
+// a graph node whose launch costs as much as its work.  k_cg_persist runs the whole inner FP32
+// MG-PCG solve of one refinement pass in one cooperative launch: the V-cycle as in the
+// cooperative coarse cycle but from the finest level, then p = z + beta p with q = A p, then x
+// and r, with a bounded grid barrier between the phases.  The dot products of a phase are
+// written as per-tile (r.z) or per-block (p.q, r.r) slots; after the barrier every block sums
+// the slots in the same order with the same code, so all blocks hold the same alpha, beta and
+// convergence decision without another barrier; block 0 alone writes the solve state.  The
+// arithmetic of each cell is that of the separate kernels; only the grouping of the dot
+// products differs (per block instead of per launch block).
+
+// grid barrier that gives up: false if this block's wait ran out or a fault is already recorded
+// (every block then leaves at its next barrier, so a fault ends the launch after a bounded time)
+__device__ inline bool grid_sync_ok(unsigned* bar, unsigned& target, SolveState* st, int spin) {
+    __shared__ int bad;
+    target += gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = *((volatile int*)&st->fault);
+        if (!b) {
+            red_release_gpu_add(&bar[0], 1u);
+            for (int it = 0; (int)(ld_acquire_gpu(&bar[0]) - target) < 0; ++it)
+                if (it > spin) {
+                    atomicOr(&st->fault, 2);
+                    b = 1;
+                    break;
+                }
+        }
+        bad = b;
+    }
+    __syncthreads();
+    return bad == 0;
+}
+
+// sum of nslot slots per right-hand side (partial[k * nslot + s]) in a fixed order, in every
+// block (the result is in every thread)
+template <int NR>
+__device__ inline void sum_slots(const double* partial, int nslot, double* tot) {
+    __shared__ double sh[32];
+    __shared__ double res[2];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nslot; b += blockDim.x) a += ((const volatile double*)partial)[k * nslot + b];
+        a = bsum(a, sh);
+        if (threadIdx.x == 0) res[k] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NR; ++k) tot[k] = res[k];
+    __syncthreads();
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(CC_THREADS)
+k_cg_persist(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag, const T* __restrict__ wl,
+             const T* __restrict__ wb, const T* __restrict__ inv, T* __restrict__ x, T* __restrict__ r,
+             T* __restrict__ p0, T* __restrict__ p1, T* __restrict__ q, SolveState* st, double* partial,
+             unsigned* bar) {
+    if (skip(st)) return;   // the refinement has converged: the same in every block
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned gen = 0;
+    const int G = gridDim.x;
+    const Lev<T>& L0 = C.L[0];
+    const int N = L0.nx * L0.ny;
+    const int tx0 = (L0.nx + TX - 1) / TX, nt0 = tx0 * ((L0.ny + TY - 1) / TY);
+    double* prz = partial;                // r.z per finest tile
+    double* ppq = partial + 2 * nt0;      // p.q per block
+    double* prr = ppq + 2 * G;            // r.r per block
+    double rz[2], tol2[2], alpha[2] = {0.0, 0.0}, beta[2] = {0.0, 0.0}, pq[2] = {0.0, 0.0}, rr[2] = {0.0, 0.0};
+    int iters = st->iters;
+    const int maxit = st->max_iters;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        rz[k] = st->rz[k];
+        tol2[k] = st->tol2[k];
+    }
+    bool done = false, bad = false, ok = true;
+    while (!done) {
+        // ---- z = M r: the V-cycle from the finest level
+        for (int l = 0; l < C.nb && ok; ++l) {
+            const Lev<T>& L = C.L[l];
+            int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
+            for (int t = blockIdx.x; t < nt; t += G) {
+                pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr);
+                __syncthreads();
+            }
+            ok = grid_sync_ok(bar, gen, st, C.spin);
+        }
+        if (!ok) break;
+        if (blockIdx.x == 0) small_cycle<T, NR, false>(P, diag, wl, wb, inv, C.bc[C.nb - 1], C.xo[C.nb], st, smem);
+        if (!grid_sync_ok(bar, gen, st, C.spin)) break;
+        for (int l = C.nb - 1; l >= 1 && ok; --l) {
+            const Lev<T>& L = C.L[l];
+            int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
+            for (int t = blockIdx.x; t < nt; t += G) {
+                post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr);
+                __syncthreads();
+            }
+            ok = grid_sync_ok(bar, gen, st, C.spin);
+        }
+        if (!ok) break;
+        for (int t = blockIdx.x; t < nt0; t += G) {
+            Vec<T, 2> d = post_tile<T, NR, true>(L0, C.b[0], C.x2[0], C.xo[0], C.xc[0], t % tx0, t / tx0, smem, nullptr);
+            block_partial_t<T, NR>(d.v, prz, nt0, t);
+            __syncthreads();
+        }
+        if (!grid_sync_ok(bar, gen, st, C.spin)) break;
+        double rzn[2] = {0.0, 0.0};
+        sum_slots<NR>(prz, nt0, rzn);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            beta[k] = rz[k] != 0.0 ? rzn[k] / rz[k] : 0.0;
+            rz[k] = rzn[k];
+        }
+        // ---- p = z + beta p; q = A p; p.q (the new p of the neighbours recomputed, as k_apply)
+        const Vec<T, NR>* __restrict__ Z = reinterpret_cast<const Vec<T, NR>*>(C.xo[0]);
+        const Vec<T, NR>* __restrict__ Po = reinterpret_cast<const Vec<T, NR>*>((iters & 1) ? p1 : p0);
+        Vec<T, NR>* __restrict__ Pn = reinterpret_cast<Vec<T, NR>*>((iters & 1) ? p0 : p1);
+        Vec<T, NR>* __restrict__ Q = reinterpret_cast<Vec<T, NR>*>(q);
+        {
+            T bt[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) bt[k] = (T)beta[k];
+            DotAcc<T, NR> acc;
+            int nchunk = 0;
+            for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += G * blockDim.x) {
+                int i = c % L0.nx, j = c / L0.nx;
+                auto pn = [&](int cc) {
+                    Vec<T, NR> a = Z[cc], b = Po[cc];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k)
+                        if (bt[k] != T(0)) a.v[k] += bt[k] * b.v[k];
+                    return a;
+                };
+                Vec<T, NR> pc = pn(c), qv;
+                T dg = L0.diag[c];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) qv.v[k] = dg * pc.v[k];
+                if (i > 0) {
+                    T w = L0.wl[c];
+                    Vec<T, NR> a = pn(c - 1);
+                    for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]);
+                }
+                if (i < L0.nx - 1) {
+                    T w = L0.wl[c + 1];
+                    Vec<T, NR> a = pn(c + 1);
+                    for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]);
+                }
+                if (j > 0) {
+                    T w = L0.wb[c];
+                    Vec<T, NR> a = pn(c - L0.nx);
+                    for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]);
+                }
+                if (j < L0.ny - 1) {
+                    T w = L0.wb[c + L0.nx];
+                    Vec<T, NR> a = pn(c + L0.nx);
+                    for (int k = 0; k < NR; ++k) qv.v[k] += w * (pc.v[k] - a.v[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
+                if (++nchunk == DOT_CHUNK) {
+                    acc.flush();
+                    nchunk = 0;
+                }
+                Pn[c] = pc;
+                Q[c] = qv;
+            }
+            acc.flush();
+            block_partial<NR>(acc.tot, ppq, G, blockIdx.x);
+        }
+        if (!grid_sync_ok(bar, gen, st, C.spin)) break;
+        sum_slots<NR>(ppq, G, pq);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) alpha[k] = pq[k] != 0.0 ? rz[k] / pq[k] : 0.0;
+        // ---- x += alpha p; r -= alpha q; r.r
+        {
+            T al[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) al[k] = (T)alpha[k];
+            Vec<T, NR>* __restrict__ X = reinterpret_cast<Vec<T, NR>*>(x);
+            Vec<T, NR>* __restrict__ Rr = reinterpret_cast<Vec<T, NR>*>(r);
+            DotAcc<T, NR> acc;
+            const int stride = G * blockDim.x;
+            for (int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < N; c0 += DOT_CHUNK * stride) {
+#pragma unroll
+                for (int u = 0; u < DOT_CHUNK; ++u) {
+                    int c = c0 + u * stride;
+                    if (c < N) {
+                        Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
+#pragma unroll
+                        for (int k = 0; k < NR; ++k) {
+                            xv.v[k] += al[k] * pv.v[k];
+                            rv.v[k] -= al[k] * qv.v[k];
+                            acc.add(k, rv.v[k], rv.v[k]);
+                        }
+                        X[c] = xv;
+                        Rr[c] = rv;
+                    }
+                }
+                acc.flush();
+            }
+            block_partial<NR>(acc.tot, prr, G, blockIdx.x);
+        }
+        if (!grid_sync_ok(bar, gen, st, C.spin)) break;
+        sum_slots<NR>(prr, G, rr);
+        iters += 1;
+        done = true;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            if (!(rr[k] <= tol2[k])) done = false;
+            bad = bad || !isfinite(rr[k]);
+        }
+        if (bad || iters >= maxit) done = true;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            st->rz[k] = rz[k];
+            st->beta[k] = beta[k];
+            st->pq[k] = pq[k];
+            st->alpha[k] = alpha[k];
+            st->rr[k] = rr[k];
+        }
+        st->iters = iters;
+        if (bad) st->nonfinite = 1;
+        st->done = 1;
+    }
+}
+
 // FP64 CG start: r = b - A x, r.r, b.b, tolerance, state reset
 template <int NR>
 __global__ void __launch_bounds__(256)
@@ -1619,7 +1850,11 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
                                                       const double* __restrict__ x, float* __restrict__ r32,
                                                       float* __restrict__ e32, SolveState* st, double* partial,
                                                       unsigned* ticket, cudaGraphConditionalHandle ho,
-                                                      cudaGraphConditionalHandle hi, int use_h) {
+                                                      cudaGraphConditionalHandle hi, int use_h, int set_hi,
+                                                      unsigned* coop_bar) {
+    // the whole-solve cooperative launch that follows counts its barrier arrivals from 0 (its
+    // previous launch has completed: stream order)
+    if (coop_bar && blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0) *coop_bar = 0u;
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -1706,7 +1941,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
         st->iters = 0;
         st->done = done ? 1 : 0;
         set_cond(ho, use_h, done ? 0u : 1u);
-        set_cond(hi, use_h, done ? 0u : 1u);
+        if (set_hi) set_cond(hi, use_h, done ? 0u : 1u);
     }
 }
 
@@ -1847,6 +2082,8 @@ cudaError_t Solver::bind(void* base, int nx_, int ny_, bool make_streams, cudaSt
     allow_smem(k_coarse_cycle<float, 2>, SM, &err);
     allow_smem(k_coarse_cycle<double, 1>, SM, &err);
     allow_smem(k_coarse_cycle<double, 2>, SM, &err);
+    allow_smem(k_cg_persist<float, 1>, SM, &err);
+    allow_smem(k_cg_persist<float, 2>, SM, &err);
     allow_smem(k_small<float, 1, true>, SM, &err);
     allow_smem(k_small<float, 1, false>, SM, &err);
     allow_smem(k_small<float, 2, true>, SM, &err);
@@ -2279,6 +2516,72 @@ static void solve_fp64(Solver& s, const double* b, double* x, double rtol, int m
     }
 }
 
+// The whole inner FP32 solve as one cooperative launch (use_coop == 2): single instances with
+// at least one tiled level whose finest tiles and block slots fit the reduction buffer; the
+// grid is min(finest tiles, co-resident blocks).  False: the solve runs as separate kernels.
+template <int NR>
+static bool persist_plan(Solver& s, CoarsePlan<float>& C, SmallPlan& P, int& G, size_t& smem) {
+    if (s.use_coop != 2 || s.nz != 1) return false;
+    int nb = nbig_of<float>(s);
+    if (nb < 1) return false;
+    P = small_plan<float>(s);
+    smem = coarse_smem<float, NR>(P);
+    struct Entry { size_t smem; int dev, res; };
+    thread_local std::vector<Entry> cache[2];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int res = -1;
+    for (const Entry& e : cache[NR - 1])
+        if (e.smem == smem && e.dev == dev) res = e.res;
+    if (res < 0) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persist<float, NR>, CC_THREADS, smem);
+        res = per * sms;
+        cudaGetLastError();
+        cache[NR - 1].push_back({smem, dev, res});
+    }
+    long long nt0 = (long long)tiles(s.nx, s.ny);
+    G = (int)(nt0 < res ? nt0 : res);
+    long long mb = nt0 > NRED ? nt0 : NRED;
+    if (G < 1 || 2 * nt0 + 4LL * G > 4 * mb) return false;
+    float* X = s.f_x;
+    float* X2 = s.f_x2;
+    float* B = s.f_b;
+    C.l0 = 0;
+    C.nb = nb;
+    C.spin = s.barrier_spin > 0 ? s.barrier_spin : (1 << 22);
+    for (int l = 0; l < nb; ++l) {
+        C.L[l] = lev<float>(s, l);
+        C.b[l] = l == 0 ? s.f_r : B + 2 * s.loff[l];
+        C.x2[l] = X2 + 2 * s.loff[l];
+        C.bc[l] = B + 2 * s.loff[l + 1];
+        C.xo[l] = X + 2 * s.loff[l];
+        C.xc[l] = X + 2 * s.loff[l + 1];
+    }
+    C.xo[nb] = X + 2 * s.loff[nb];
+    return true;
+}
+
+template <int NR>
+static void launch_persist(Solver& s, const CoarsePlan<float>& C, const SmallPlan& P, int G, size_t smem,
+                           cudaStream_t stm) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(CC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stm;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_cg_persist<float, NR>, C, P, (const float*)s.f_diag, (const float*)s.f_wl,
+                       (const float*)s.f_wb, (const float*)s.f_inv, s.f_e, s.f_r, s.f_p,
+                       s.f_p + (size_t)s.nx * s.ny * NR, s.f_q, s.st, s.partial, s.tickets + 8);
+    if (!s.use_graph) ++s.launches;
+}
+
 template <int NR>
 static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, double rtol, int max_iter,
                         cudaStream_t stm) {
@@ -2289,32 +2592,48 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
     k_ir_init<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(N, s.zs, b, s.st, s.partial, s.tickets + 3,
                                                              rtol * rtol, inner_rtol, max_iter, max_outer);
     ++s.launches;
+    CoarsePlan<float> PC;
+    SmallPlan PS;
+    int PG = 0;
+    size_t psmem = 0;
+    bool persist = persist_plan<NR>(s, PC, PS, PG, psmem);
+    unsigned* pbar = persist ? s.tickets + 8 : nullptr;
     if (s.use_graph) {
         cudaGraph_t g;
         cudaGraphConditionalHandle ho = make_handle(stm, &g);
         cudaStream_t obs = begin_while(stm, s.aux[0], ho);
-        cudaGraph_t og;
-        cudaGraphConditionalHandle hi = make_handle(obs, &og);
         int mode = s.nz > 1 ? 2 : 1;
-        if (mode == 2) k_cond_reset<<<1, 32, 0, obs>>>(ho, hi, 1);
-        k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
-                                                                     s.tickets + 5, ho, hi, mode);
-        cudaStream_t ibs = begin_while(obs, s.aux[1], hi);
-        cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, hi, mode, ibs);
-        end_while(ibs);
+        if (persist) {
+            k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                                         s.tickets + 5, ho, ho, mode, 0, pbar);
+            launch_persist<NR>(s, PC, PS, PG, psmem, obs);
+        } else {
+            cudaGraph_t og;
+            cudaGraphConditionalHandle hi = make_handle(obs, &og);
+            if (mode == 2) k_cond_reset<<<1, 32, 0, obs>>>(ho, hi, 1);
+            k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                                         s.tickets + 5, ho, hi, mode, 1, nullptr);
+            cudaStream_t ibs = begin_while(obs, s.aux[1], hi);
+            cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, hi, mode, ibs);
+            end_while(ibs);
+        }
         k_ir_update<NR><<<dim3(nblocks(N * NR), 1, s.nz), RB, 0, obs>>>(N, s.zs, x, s.f_e, s.st);
         end_while(obs);
         return;
     }
     for (int o = 0; o <= max_outer; ++o) {
         k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
-                                                                     s.tickets + 5, 0, 0, 0);
+                                                                     s.tickets + 5, 0, 0, 0, 0, pbar);
         ++s.launches;
         poll(s, stm);
         if (s.st_host[s.slot].odone) break;
-        for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
-            cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, 0, 0, stm);
-            poll(s, stm);
+        if (persist) {
+            launch_persist<NR>(s, PC, PS, PG, psmem, stm);
+        } else {
+            for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
+                cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, 0, 0, stm);
+                poll(s, stm);
+            }
         }
         k_ir_update<NR><<<dim3(nblocks(N * NR), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, s.f_e, s.st);
         ++s.launches;

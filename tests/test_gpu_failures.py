@@ -104,14 +104,17 @@ def test_nonfinite_field_is_reported(dev, precision, field):
         E.ebit_destroy(ctx)
 
 
-def test_grid_barrier_timeout_is_reported_as_a_fault(dev):
+@pytest.mark.parametrize("coop", [1, 2])
+def test_grid_barrier_timeout_is_reported_as_a_fault(dev, coop):
     # 96^2 in the mixed path: the FP32 48^2 level and the single-block levels run in one
-    # cooperative launch (in FP64 the single-block kernel's shared memory leaves no room for a
-    # co-resident grid, so FP64 solves launch every level separately and have no grid barrier)
+    # cooperative launch (coop 1), or each whole inner solve does (coop 2); in FP64 the
+    # single-block kernel's shared memory leaves no room for a co-resident grid, so FP64 solves
+    # launch every level separately and have no grid barrier
     precision = E.EBIT_MIXED
     pb = bubble(96)
     ctx, _ = make(dev, pb, precision)
     try:
+        E.ebit_set_option(ctx, E.EBIT_OPT_COOP, coop)
         E.ebit_set_option(ctx, E.EBIT_OPT_BARRIER_SPIN, 1)
         with pytest.raises(E.EbitError) as ei:
             E.ebit_step(ctx, 1)

@@ -557,6 +557,35 @@ def test_single_block_extension_equals_launch_per_sweep(dev, name, graph):
         assert np.array_equal(out[0][k], out[1][k]), k
 
 
+@pytest.mark.parametrize("name", ["bubble_mid", "film_mid", "saddle", "sucking", "axi_sphere"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_persistent_inner_solve_matches_separate_kernels(dev, name, graph):
+    """Mixed precision with each whole inner FP32 solve in one cooperative launch
+    (EBIT_OPT_COOP = 2) against one kernel per V-cycle leg and CG update: the dot products are
+    grouped differently, so the iterates differ by rounding; both refine to a relative residual
+    of 1e-12, two steps agree to 1e-9 of each field group's scale, the vertex colours exactly
+    and the markers to 1e-10 of a cell."""
+    st = prepared(name, 0)
+    out = []
+    for coop in (2, 0):
+        ctx = gpu_ctx(dev, st, precision=E.EBIT_MIXED, rtol=1e-12, graph=graph)
+        try:
+            E.ebit_set_option(ctx, E.EBIT_OPT_COOP, coop)
+            E.ebit_step(ctx, 2)
+            out.append(E.download(ctx, 0, st.pb.nx, st.pb.ny))
+        finally:
+            E.ebit_destroy(ctx)
+    so = st.copy()
+    assert np.array_equal(out[0]["vcol"], out[1]["vcol"])
+    for k in ("hx_pos", "vy_pos"):
+        assert np.max(np.abs(out[0][k] - out[1][k])) < 1e-10, k
+    for k in FIELDS:
+        ref = out[1][k]
+        setattr(so, k, ref)
+    for k in FIELDS:
+        assert relerr(out[0][k], out[1][k], group_scale(so, k)) < 1e-9, k
+
+
 def test_batched_field_copies_equal_single_field_copies(dev):
     """ebit_set_fields / ebit_get_fields (one synchronisation per call) move the same bytes as
     one ebit_set_field / ebit_get_field per field, from and to page-locked host buffers and

@@ -61,23 +61,55 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
     return F[cidx(g, i, j)];
 }
 
-// Reciprocal of d > 0 to about 45 bits without an FP64 division and without an FP64-pipe
-// conversion: d truncated to FP32 on the integer pipes (relative error below 2^-23), its IEEE
-// FP32 reciprocal (within 2^-24), widened exactly on the integer pipes, then one Newton-Raphson
-// step for f(r) = 1/r - d, r <- r + r (1 - d r), the residual 1 - d r formed by one fused
-// multiply-add: the step squares the relative error (below 2^-44.8).  Outside
-// [2^-126, 2^126) the FP64 division is used.
-__device__ inline double recip_nr(double d) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (e - 897u > 251u) return 1.0 / d;
-    float df = __uint_as_float(((unsigned)(b >> 63) << 31) | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-    unsigned u = __float_as_uint(__frcp_rn(df));
-    double r = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
-                                                ((unsigned long long)(((u >> 23) & 0xffu) + 896u) << 52) |
-                                                ((unsigned long long)(u & 0x7fffffu) << 29)));
-    return fma(r, fma(-d, r, 1.0), r);
+// ---- FP32-pair ("double-single") arithmetic for the WENO3 weights --------------------------
+// A value is an unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2 (48-bit
+// significand).  Sums use Knuth's TwoSum and the fast renormalisation of Dekker (1971); products
+// use the exact product error of a fused multiply-add.  Every operation is FP32 arithmetic, so
+// the weights cost no FP64 instruction (the FP64 pipe of this GPU issues at a small fraction
+// of the FP32 rate).  Each operation is accurate to a few units of 2^-44 relative.
+struct f32x2 {
+    float hi, lo;
+};
+__device__ __forceinline__ f32x2 quick_two_sum(float a, float b) {   // |a| >= |b|
+    float s = a + b;
+    return {s, b - (s - a)};
 }
+__device__ __forceinline__ f32x2 two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);                 // the exact error of the product
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ f32x2 x2_div(f32x2 a, f32x2 b) {     // b > 0
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    f32x2 p = x2_mul(b, {q1, 0.0f});
+    f32x2 r = x2_add(a, {-p.hi, -p.lo});             // a - q1 b
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return quick_two_sum(q1, q2);
+}
+// a binary64 value as a pair on the integer pipes: the top 24 significand bits (truncated) and
+// the remaining 29 rounded to 24; |a| in [2^-60, 2^28) (smaller values are 0 here)
+__device__ __forceinline__ f32x2 x2_from(double a) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e < 963u) return {0.0f, 0.0f};
+    unsigned sign = (unsigned)(b >> 63) << 31;
+    float hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    float scale = __uint_as_float((e - 948u) << 23);        // 2^(e - 1075), a normal float
+    float lo = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * scale;
+    return {hi, sign ? -lo : lo};
+}
+// the pair as a binary64 value: the two widened exactly, one FP64 add
+__device__ __forceinline__ double x2_to(f32x2 a) { return f2d(a.hi) + f2d(a.lo); }
 
 // WENO3 upwind derivative (undivided) from five values along a line (Jiang-Shu, linear weights
 // 1/3 and 2/3, smoothness indicators b0 = (v2 - v1)^2, b1 = (v3 - v2)^2, eps = 1e-6).  With the
@@ -86,8 +118,32 @@ __device__ inline double recip_nr(double d) {
 //   w0 = (1/3)/(eps + b0)^2 / ((1/3)/(eps + b0)^2 + (2/3)/(eps + b1)^2)
 //      = (eps + b1)^2 / ((eps + b1)^2 + 2 (eps + b0)^2),
 // so the derivative is phi1 + w0 (phi0 - phi1) with phi0 - phi1 = ((v2 - v1) - (v3 - v2))/2:
-// the second differences serve both the indicators and the candidates' difference, and the one
-// reciprocal is recip_nr (the FP64 rate of this GPU is a small fraction of its FP32 rate).
+// the second differences serve both the indicators and the candidates' difference.  The
+// differences and the final combination are FP64; the weight w0 is formed from the second
+// differences in FP32-pair arithmetic (48-bit, relative error a few times 2^-44: the derivative
+// then differs from its FP64 evaluation by a few times 1e-14 of the second difference).
+// Second differences of 2^28 or more take the FP64 formula (a call, not an inlined branch, so
+// that its FP64 instructions are not issued for every stencil).
+__device__ __noinline__ double weno_weight_fp64(double a1, double a2) {
+    const double eps = 1e-6;
+    double s0 = fma(a1, a1, eps), s1 = fma(a2, a2, eps);
+    double q0 = s1 * s1;
+    return q0 / fma(s0 + s0, s0, q0);
+}
+__device__ inline double weno_weight(double a1, double a2) {
+    unsigned e1 = (unsigned)(__double_as_longlong(a1) >> 52) & 0x7ffu;
+    unsigned e2 = (unsigned)(__double_as_longlong(a2) >> 52) & 0x7ffu;
+    if ((e1 > e2 ? e1 : e2) >= 1023u + 28u) return weno_weight_fp64(a1, a2);
+    constexpr double EPS = 1e-6;
+    constexpr float EPS_HI = (float)EPS;
+    constexpr float EPS_LO = (float)(EPS - (double)EPS_HI);
+    const f32x2 eps = {EPS_HI, EPS_LO};
+    f32x2 A1 = x2_from(a1), A2 = x2_from(a2);
+    f32x2 s0 = x2_add(x2_mul(A1, A1), eps), s1 = x2_add(x2_mul(A2, A2), eps);
+    f32x2 q0 = x2_mul(s1, s1), t = x2_mul(s0, s0);
+    f32x2 d = x2_add({t.hi + t.hi, t.lo + t.lo}, q0);
+    return x2_to(x2_div(q0, d));
+}
 //
 // weno3_up takes the stencil ordered from the upwind side, up2 and up1 the two upwind values,
 // dn the downwind one, and returns twice the derivative along the flow direction.  For u >= 0
@@ -97,13 +153,9 @@ __device__ inline double recip_nr(double d) {
 // difference changes sign, the indicators do not).  u dT/dx is therefore |u| times the result
 // / 2: the selection costs no FP64 instruction and the factor 1/2 is folded into dt/h.
 __device__ inline double weno3_up(double up2, double up1, double T0, double dn) {
-    const double eps = 1e-6;
     double v1 = up1 - up2, v2 = T0 - up1, v3 = dn - T0;
     double a1 = v2 - v1, a2 = v3 - v2;
-    double s0 = fma(a1, a1, eps), s1 = fma(a2, a2, eps);
-    double q0 = s1 * s1;
-    double w0 = q0 * recip_nr(fma(s0 + s0, s0, q0));
-    return fma(w0, a1 - a2, v2 + v3);
+    return fma(weno_weight(a1, a2), a1 - a2, v2 + v3);
 }
 // u >= 0 from the sign bit (no FP64 comparison); -0.0 takes the mirrored stencil, which only
 // multiplies a zero velocity

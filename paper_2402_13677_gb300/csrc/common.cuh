@@ -186,6 +186,24 @@ __device__ __forceinline__ double f2d(float v) {
     return __longlong_as_double((long long)(sign | b));
 }
 
+// 1 / x for x > 0 without the FP64 division sequence: an FP32 seed (x truncated to FP32 on the
+// integer pipes, its IEEE reciprocal, widened exactly) and two Newton-Raphson steps r <- r + r
+// (1 - x r), each squaring the relative error (2^-22.4 -> 2^-44.8 -> rounding): within about
+// one unit in the last place.  Outside [2^-126, 2^126) the division, in a call (so that its
+// instructions are not issued for every element).
+static __device__ __noinline__ double recip64_div(double x) { return 1.0 / x; }
+__device__ __forceinline__ double recip64(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e - 897u > 251u || (b >> 63)) return recip64_div(x);
+    float xf = __uint_as_float(((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    unsigned u = __float_as_uint(__frcp_rn(xf));
+    double r = __longlong_as_double((long long)(((unsigned long long)(((u >> 23) & 0xffu) + 896u) << 52) |
+                                                ((unsigned long long)(u & 0x7fffffu) << 29)));
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 // launch grids that cover every instance of a (possibly batched) launch
 inline dim3 grid1(long long n, int bs, int nz) { return dim3(div_up(n, bs), 1, nz); }

@@ -778,7 +778,7 @@ __global__ void k_energy_operator(Grid g, Phys p, const uint8_t* __restrict__ fl
     double lam = k ? p.lam_l : p.lam_v;
     double rc = k ? p.rho_l * p.cp_l : p.rho_v * p.cp_v;
     const double mc = rad_c<AXI>(g, i);
-    double coef = g.h * g.h * rc / p.dt * mc;
+    double coef = g.h * g.h * rc * p.inv_dt * mc;
     double ts = k ? Ts_l[c] : Ts_v[c];
     double dsum = 0.0, rhs = coef * ts;
     const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};

@@ -739,38 +739,36 @@ __global__ void k_poisson_operator(Grid g, Phys p, const double* __restrict__ vf
 }
 
 
-// face accelerations a_f = g - grad_f p / rho_f (0 on walls and symmetry planes); on interior
-// faces, with the Poisson face weight w = dt / rho_f given (wl != null), as g - dp w / (h dt)
-__device__ inline double accel_x(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl,
+// the pressure part -grad_f p / rho_f of the face acceleration on a face the projection acts on
+// (interior, or an outflow boundary face with p = 0 on it): on interior faces with the Poisson
+// face weight w = dt / rho_f given (wl != null) as -dp w / (h dt), else through recip64
+__device__ inline double pgrad_x(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wl,
                                  int i, int j) {
     if (i > 0 && i < g.nx) {
         double dP = P[cidx(g, i, j)] - P[cidx(g, i - 1, j)];
-        if (wl) return p.gx - dP * wl[cidx(g, i, j)] * (g.inv_h * p.inv_dt);
-        return p.gx - dP * recip64(g.h * rho_mix(p, face_vf_x(g, vf, i, j)));
+        if (wl) return -(dP * wl[cidx(g, i, j)] * (g.inv_h * p.inv_dt));
+        return -(dP * recip64(g.h * rho_mix(p, face_vf_x(g, vf, i, j))));
     }
-    int s = i == 0 ? 0 : 1;
-    if (g.bc[s] != BC_OUTFLOW) return 0.0;
     double r = rho_mix(p, face_vf_x(g, vf, i, j));
-    if (i == 0) return p.gx - (2.0 * P[cidx(g, 0, j)]) / (g.h * r);
-    return p.gx - (-2.0 * P[cidx(g, g.nx - 1, j)]) / (g.h * r);
+    if (i == 0) return -((2.0 * P[cidx(g, 0, j)]) / (g.h * r));
+    return -((-2.0 * P[cidx(g, g.nx - 1, j)]) / (g.h * r));
 }
-__device__ inline double accel_y(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wb,
+__device__ inline double pgrad_y(const Grid& g, const Phys& p, const double* P, const double* vf, const double* wb,
                                  int i, int j) {
     if (j > 0 && j < g.ny) {
         double dP = P[cidx(g, i, j)] - P[cidx(g, i, j - 1)];
-        if (wb) return p.gy - dP * wb[cidx(g, i, j)] * (g.inv_h * p.inv_dt);
-        return p.gy - dP * recip64(g.h * rho_mix(p, face_vf_y(g, vf, i, j)));
+        if (wb) return -(dP * wb[cidx(g, i, j)] * (g.inv_h * p.inv_dt));
+        return -(dP * recip64(g.h * rho_mix(p, face_vf_y(g, vf, i, j))));
     }
-    int s = j == 0 ? 2 : 3;
-    if (g.bc[s] != BC_OUTFLOW) return 0.0;
     double r = rho_mix(p, face_vf_y(g, vf, i, j));
-    if (j == 0) return p.gy - (2.0 * P[cidx(g, i, 0)]) / (g.h * r);
-    return p.gy - (-2.0 * P[cidx(g, i, g.ny - 1)]) / (g.h * r);
+    if (j == 0) return -((2.0 * P[cidx(g, i, 0)]) / (g.h * r));
+    return -((-2.0 * P[cidx(g, i, g.ny - 1)]) / (g.h * r));
 }
 
-// face accelerations a_f = g - grad_f p / rho_f (one FP64 division per face), stored in ax/ay;
-// with fx_l != null also the face update u_f^{n+1} = u_f* + dt (a_f - g) (discretization
-// equation 4) for both phase fields
+// face accelerations a_f = g - grad_f p / rho_f (+ the surface-tension term), stored in ax/ay
+// (0 on walls and symmetry planes); with fx_l != null also the face update of discretization
+// equation 4 for both phase fields, u_f^{n+1} = u_f* + dt (a_f - g - surface tension) =
+// u_f* - dt grad_f p / rho_f (u_f* carries dt (g + surface tension) already)
 __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const double* __restrict__ vf,
                              const double* __restrict__ kap, const double* __restrict__ wl_p,
                              const double* __restrict__ wb_p, double* __restrict__ ax, double* __restrict__ ay,
@@ -795,26 +793,36 @@ __global__ void k_face_accel(Grid g, Phys p, const double* __restrict__ P, const
         // faces < 2^31 (nx ny <= 2^29): 32-bit division
         int j = (int)((unsigned)t / (unsigned)(g.nx + 1)), i = (int)t - j * (g.nx + 1);
         bool bnd = i == 0 || i == g.nx;
-        double sf = (bnd || !(has_sigma(p)))
-                        ? 0.0 : st_face(p, g, kap, vf, cidx(g, i - 1, j), cidx(g, i, j), face_vf_x(g, vf, i, j));
-        double a = accel_x(g, p, P, vf, wl_p, i, j) + sf;
+        if (bnd && g.bc[i == 0 ? 0 : 1] != BC_OUTFLOW) {
+            ax[t] = 0.0;
+            if (fx_l) { fx_l[t] = 0.0; fx_v[t] = 0.0; }
+            return;
+        }
+        double G = pgrad_x(g, p, P, vf, wl_p, i, j);
+        double a = p.gx + G;
+        if (!bnd && has_sigma(p))
+            a += st_face(p, g, kap, vf, cidx(g, i - 1, j), cidx(g, i, j), face_vf_x(g, vf, i, j));
         ax[t] = a;
         if (!fx_l) return;
-        if (bnd && g.bc[i == 0 ? 0 : 1] != BC_OUTFLOW) { fx_l[t] = 0.0; fx_v[t] = 0.0; return; }
-        double corr = p.dt * (a - p.gx - sf);   // u_f* carries dt (g + surface tension) already
+        double corr = p.dt * G;
         fx_l[t] += corr;
         fx_v[t] += corr;
     } else if (t < nfx + nfy) {
         long long e = t - nfx;
         int j = (int)((unsigned)e / (unsigned)g.nx), i = (int)e - j * g.nx;
         bool bnd = j == 0 || j == g.ny;
-        double sf = (bnd || !(has_sigma(p)))
-                        ? 0.0 : st_face(p, g, kap, vf, cidx(g, i, j - 1), cidx(g, i, j), face_vf_y(g, vf, i, j));
-        double a = accel_y(g, p, P, vf, wb_p, i, j) + sf;
+        if (bnd && g.bc[j == 0 ? 2 : 3] != BC_OUTFLOW) {
+            ay[e] = 0.0;
+            if (fx_l) { fy_l[e] = 0.0; fy_v[e] = 0.0; }
+            return;
+        }
+        double G = pgrad_y(g, p, P, vf, wb_p, i, j);
+        double a = p.gy + G;
+        if (!bnd && has_sigma(p))
+            a += st_face(p, g, kap, vf, cidx(g, i, j - 1), cidx(g, i, j), face_vf_y(g, vf, i, j));
         ay[e] = a;
         if (!fx_l) return;
-        if (bnd && g.bc[j == 0 ? 2 : 3] != BC_OUTFLOW) { fy_l[e] = 0.0; fy_v[e] = 0.0; return; }
-        double corr = p.dt * (a - p.gy - sf);
+        double corr = p.dt * G;
         fy_l[e] += corr;
         fy_v[e] += corr;
     }

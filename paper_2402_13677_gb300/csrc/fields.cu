@@ -61,56 +61,6 @@ __device__ inline double refl_y(const Comp& F, const Grid& g, const Refl& r, int
     return F[cidx(g, i, j)];
 }
 
-// ---- FP32-pair ("double-single") arithmetic for the WENO3 weights --------------------------
-// A value is an unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2 (48-bit
-// significand).  Sums use Knuth's TwoSum and the fast renormalisation of Dekker (1971); products
-// use the exact product error of a fused multiply-add.  Every operation is FP32 arithmetic, so
-// the weights cost no FP64 instruction (the FP64 pipe of this GPU issues at a small fraction
-// of the FP32 rate).  Each operation is accurate to a few units of 2^-44 relative.
-struct f32x2 {
-    float hi, lo;
-};
-__device__ __forceinline__ f32x2 quick_two_sum(float a, float b) {   // |a| >= |b|
-    float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ f32x2 two_sum(float a, float b) {
-    float s = a + b;
-    float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
-    f32x2 s = two_sum(a.hi, b.hi);
-    return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
-    float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);                 // the exact error of the product
-    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-    return quick_two_sum(p, e);
-}
-__device__ __forceinline__ f32x2 x2_div(f32x2 a, f32x2 b) {     // b > 0
-    float q1 = __fdiv_rn(a.hi, b.hi);
-    f32x2 p = x2_mul(b, {q1, 0.0f});
-    f32x2 r = x2_add(a, {-p.hi, -p.lo});             // a - q1 b
-    float q2 = __fdiv_rn(r.hi, b.hi);
-    return quick_two_sum(q1, q2);
-}
-// a binary64 value as a pair on the integer pipes: the top 24 significand bits (truncated) and
-// the remaining 29 rounded to 24; |a| in [2^-60, 2^28) (smaller values are 0 here)
-__device__ __forceinline__ f32x2 x2_from(double a) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(a);
-    unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (e < 963u) return {0.0f, 0.0f};
-    unsigned sign = (unsigned)(b >> 63) << 31;
-    float hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-    float scale = __uint_as_float((e - 948u) << 23);        // 2^(e - 1075), a normal float
-    float lo = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * scale;
-    return {hi, sign ? -lo : lo};
-}
-// the pair as a binary64 value: the two widened exactly, one FP64 add
-__device__ __forceinline__ double x2_to(f32x2 a) { return f2d(a.hi) + f2d(a.lo); }
-
 // WENO3 upwind derivative (undivided) from five values along a line (Jiang-Shu, linear weights
 // 1/3 and 2/3, smoothness indicators b0 = (v2 - v1)^2, b1 = (v3 - v2)^2, eps = 1e-6).  With the
 // undivided upwind differences v1, v2, v3 the two candidates are phi0 = (3 v2 - v1)/2 and

@@ -1310,15 +1310,14 @@ __global__ void __launch_bounds__(256) k_setup_tree(SetupPlan P, const double* _
 
 // ---- CG kernels ---------------------------------------------------------------------------
 // p_new = z + beta p_old; q = A p_new; p.q -> alpha = r.z / p.q
-// Dot-product accumulation of a thread: FP64 for FP64 data; for FP32 data the products are
-// summed in FP32 over chunks of DOT_CHUNK cells and each chunk added to the FP64 total (one FP64
-// add per chunk: FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU).  The
-// kernels walk their cells in chunks with flush() after each, outside the per-cell body: a
-// counter test inside the body is compiled to a predicated FP64 add issued for every cell, which
-// kept the FP64 pipe 40-60 % busy in these memory-bound kernels.  The inner FP32 solves of the
+// Dot-product accumulation of a thread: FP64 for FP64 data; for FP32 data an FP32-pair running
+// sum (48-bit, FP32 instructions only), written to the FP64 total by flush().  An earlier form
+// summed FP32 chunks of eight cells into FP64 with a counter tested in the per-cell body, which
+// the compiler issued as a predicated FP64 add for every cell (the FP64 pipe 40-60 % busy in
+// these memory-bound kernels).  The loops of k_update and k_ir_residual walk their cells in
+// chunks of DOT_CHUNK (more loads in flight per thread).  The inner FP32 solves of the
 // refinement work on a residual scaled to values of order one (k_ir_residual), so FP32 products
-// neither underflow nor overflow there.  (k_apply keeps one cell per loop iteration with a
-// counted flush: there the loop shape that keeps more loads in flight measured faster.)
+// neither underflow nor overflow there.
 constexpr int DOT_CHUNK = 8;
 template <typename T, int NR>
 struct DotAcc {
@@ -1330,18 +1329,24 @@ struct DotAcc {
     __device__ void add(int k, T a, T b) { tot[k] += (double)a * (double)b; }
     __device__ void flush() {}
 };
+// FP32 data: each product added to an FP32-pair running sum (TwoSum, FP32 instructions only);
+// flush() writes the sum so far to tot in FP64 (one FP64 add), so it may be called once at the
+// end or after every chunk
 template <int NR>
 struct DotAcc<float, NR> {
     double tot[NR];
-    float part[NR];
+    f32x2 sum[NR];
     __device__ DotAcc() {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) { tot[k] = 0.0; part[k] = 0.0f; }
+        for (int k = 0; k < NR; ++k) { tot[k] = 0.0; sum[k] = {0.0f, 0.0f}; }
     }
-    __device__ void add(int k, float a, float b) { part[k] = fmaf(a, b, part[k]); }
+    __device__ void add(int k, float a, float b) {
+        f32x2 t = two_sum(sum[k].hi, a * b);
+        sum[k] = quick_two_sum(t.hi, t.lo + sum[k].lo);
+    }
     __device__ void flush() {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) { tot[k] += (double)part[k]; part[k] = 0.0f; }
+        for (int k = 0; k < NR; ++k) tot[k] = x2_to(sum[k]);
     }
 };
 
@@ -1370,7 +1375,6 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
     for (int k = 0; k < NR; ++k) beta[k] = (T)st->beta[k];
     int N = L.nx * L.ny;
     DotAcc<T, NR> acc;
-    int nchunk = 0;
 #pragma unroll 2
     for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
         int c = cw.c, i = cw.i, j = cw.j;
@@ -1411,10 +1415,6 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
         }
 #pragma unroll
         for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
-        if (++nchunk == DOT_CHUNK) {   // measured faster here than chunk-structured loops
-            acc.flush();
-            nchunk = 0;
-        }
         Pn[c] = pc;
         Q[c] = qv;
     }
@@ -1618,7 +1618,6 @@ k_cg_persist(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag, const T* 
 #pragma unroll
             for (int k = 0; k < NR; ++k) bt[k] = (T)beta[k];
             DotAcc<T, NR> acc;
-            int nchunk = 0;
             for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += G * blockDim.x) {
                 int i = c % L0.nx, j = c / L0.nx;
                 auto pn = [&](int cc) {
@@ -1654,10 +1653,6 @@ k_cg_persist(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag, const T* 
                 }
 #pragma unroll
                 for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
-                if (++nchunk == DOT_CHUNK) {
-                    acc.flush();
-                    nchunk = 0;
-                }
                 Pn[c] = pc;
                 Q[c] = qv;
             }

@@ -385,6 +385,10 @@ static void momentum(Instance& I, cudaStream_t st) {
     count(1);
     // the two components are independent: while capturing a graph the y solve becomes a
     // parallel branch (forked and joined through events on the side stream)
+    // both components' operators in one pass (their cell and face terms are shared)
+    launch_visc_operator(I.g, I.p, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, I.op2_cd, I.op2_dd, I.op2_wl, I.op2_wb,
+                         st);
+    count(1);
     bool fork = I.solver.use_graph && I.side;
     cudaStream_t s2 = fork ? I.side : st;
     if (fork) {
@@ -394,11 +398,7 @@ static void momentum(Instance& I, cudaStream_t st) {
         cudaStreamWaitEvent(s2, I.e_fork, 0);
         I.solver2.use_graph = 1;
     }
-    launch_visc_operator(I.g, I.p, 0, I.vf, I.op_cd, I.op_dd, I.op_wl, I.op_wb, st);
-    count(1);
     do_solve(I, SLOT_VISC_X, (const double*)I.vbx, (double*)I.vxx, 2, st);
-    launch_visc_operator(I.g, I.p, 1, I.vf, I.op2_cd, I.op2_dd, I.op2_wl, I.op2_wb, s2);
-    count(1);
     do_solve2(I, SLOT_VISC_Y, (const double*)I.vby, (double*)I.vxy, 2, s2);
     if (fork) {
         cudaEventRecord(I.e_join, s2);

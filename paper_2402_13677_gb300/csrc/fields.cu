@@ -443,21 +443,28 @@ __device__ inline double st_face(const Phys& p, const Grid& g, const double* kap
 // a positive integer, so the test takes no FP64 comparison
 __device__ __forceinline__ bool has_sigma(const Phys& p) { return __double_as_longlong(p.sigma) > 0; }
 
-// viscous Helmholtz operator for velocity component comp (integrated form):
-//   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where comp is Dirichlet (odd),
+// viscous Helmholtz operators of both velocity components in one pass (integrated form):
+//   cd = h^2 rho_c / dt, dd = 2 mu_c on boundary faces where the component is Dirichlet (odd),
 //   wl/wb = mean of the two cells' mu_c on the cell's left/bottom face (0 on domain faces);
 // axisymmetric: each term times the radius of its cell or face, and the radial component's hoop
 // term mu u_r / r^2 of the vector Laplacian (mu_c / r in cells, integrated over the ring cell).
+// cd, wl and wb are the same for both components and are computed once, written to both sets.
 template <bool AXI>
-__global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restrict__ vf, double* __restrict__ cd,
-                                double* __restrict__ dd, double* __restrict__ wl, double* __restrict__ wb) {
+__global__ void k_visc_operator(Grid g, Phys p, const double* __restrict__ vf, double* __restrict__ cd0,
+                                double* __restrict__ dd0, double* __restrict__ wl0, double* __restrict__ wb0,
+                                double* __restrict__ cd1, double* __restrict__ dd1, double* __restrict__ wl1,
+                                double* __restrict__ wb1) {
     zphys(g, p);
     const long long zo = zoff(g.zs);
     vf = zsh(vf, zo);
-    cd = zsh(cd, zo);
-    dd = zsh(dd, zo);
-    wl = zsh(wl, zo);
-    wb = zsh(wb, zo);
+    cd0 = zsh(cd0, zo);
+    dd0 = zsh(dd0, zo);
+    wl0 = zsh(wl0, zo);
+    wb0 = zsh(wb0, zo);
+    cd1 = zsh(cd1, zo);
+    dd1 = zsh(dd1, zo);
+    wl1 = zsh(wl1, zo);
+    wb1 = zsh(wb1, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
@@ -465,16 +472,28 @@ __global__ void k_visc_operator(Grid g, Phys p, int comp, const double* __restri
     double v = vf[c];
     double mu = mu_mix(p, v);
     const double mc = rad_c<AXI>(g, i);
-    cd[c] = g.h * g.h * rho_mix(p, v) * p.inv_dt * mc;
-    double d = 0.0;
-    if (i == 0 && vel_odd(g.bc[0], comp, 0)) d += 2.0 * mu * rad_fx<AXI>(g, 0);
-    if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) d += 2.0 * mu * rad_fx<AXI>(g, g.nx);
-    if (j == 0 && vel_odd(g.bc[2], comp, 1)) d += 2.0 * mu * mc;
-    if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) d += 2.0 * mu * mc;
-    if (AXI && comp == 0) d += mu / mc;
-    dd[c] = d;
-    wl[c] = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) * rad_fx<AXI>(g, i) : 0.0;
-    wb[c] = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) * mc : 0.0;
+    double cdv = g.h * g.h * rho_mix(p, v) * p.inv_dt * mc;
+    double wlv = i > 0 ? 0.5 * (mu_mix(p, vf[c - 1]) + mu) * rad_fx<AXI>(g, i) : 0.0;
+    double wbv = j > 0 ? 0.5 * (mu_mix(p, vf[c - g.nx]) + mu) * mc : 0.0;
+    double d[2];
+#pragma unroll
+    for (int comp = 0; comp < 2; ++comp) {
+        double dc = 0.0;
+        if (i == 0 && vel_odd(g.bc[0], comp, 0)) dc += 2.0 * mu * rad_fx<AXI>(g, 0);
+        if (i == g.nx - 1 && vel_odd(g.bc[1], comp, 0)) dc += 2.0 * mu * rad_fx<AXI>(g, g.nx);
+        if (j == 0 && vel_odd(g.bc[2], comp, 1)) dc += 2.0 * mu * mc;
+        if (j == g.ny - 1 && vel_odd(g.bc[3], comp, 1)) dc += 2.0 * mu * mc;
+        if (AXI && comp == 0) dc += mu / mc;
+        d[comp] = dc;
+    }
+    cd0[c] = cdv;
+    wl0[c] = wlv;
+    wb0[c] = wbv;
+    dd0[c] = d[0];
+    cd1[c] = cdv;
+    wl1[c] = wlv;
+    wb1[c] = wbv;
+    dd1[c] = d[1];
 }
 
 // RHS of the viscous solves: cd * (WENO3-advected u_c + dt gc_c) for both phase fields (cd as
@@ -1061,10 +1080,10 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const int* band_list, c
                                                         vpos, u_l, u_v, ufx_l, ufx_v, ufy_l, ufy_v);
 }
 
-void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
-                          double* wl, double* wb, cudaStream_t st) {
+void launch_visc_operator(const Grid& g, const Phys& p, const double* vf, double* cd0, double* dd0, double* wl0,
+                          double* wb0, double* cd1, double* dd1, double* wl1, double* wb1, cudaStream_t st) {
     auto k = g.axi ? k_visc_operator<true> : k_visc_operator<false>;
-    k<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, comp, vf, cd, dd, wl, wb);
+    k<<<rows_grid(g.nx, g.ny, 128, g.nz), 128, 0, st>>>(g, p, vf, cd0, dd0, wl0, wb0, cd1, dd1, wl1, wb1);
 }
 
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,

@@ -53,8 +53,8 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const int* band_list, c
                            const uint8_t* flags, const double* mdot, const double2* nb, const uint8_t* vcol,
                            const double* hpos, const double* vpos, double2* u_l, double2* u_v, double* ufx_l,
                            double* ufx_v, double* ufy_l, double* ufy_v, cudaStream_t st);
-void launch_visc_operator(const Grid& g, const Phys& p, int comp, const double* vf, double* cd, double* dd,
-                          double* wl, double* wb, cudaStream_t st);
+void launch_visc_operator(const Grid& g, const Phys& p, const double* vf, double* cd0, double* dd0, double* wl0,
+                          double* wb0, double* cd1, double* dd1, double* wl1, double* wb1, cudaStream_t st);
 void launch_mom_rhs(const Grid& g, const Phys& p, const double* vf, const double2* u_l, const double2* u_v,
                     const double2* gc, double2* bx, double2* by, double2* xx, double2* xy, cudaStream_t st);
 void launch_ustar(const Grid& g, const Phys& p, const double2* sx, const double2* sy, const double2* gc,

@@ -298,7 +298,8 @@ static void advance_interface(Instance& I, cudaStream_t st) {
     for (int k = 0; k < 2; ++k) {
         int axis = k == 0 ? first : 1 - first;
         if (k == 1) {
-            launch_reconstruct(I.g, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, nullptr, st);
+            launch_reconstruct_list(I.g, I.near_list, I.near_count, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, nullptr,
+                                    st);
             count(1);
         }
         launch_sweep(I.g, axis, dth, I.near_list, I.near_count, I.vcol, I.hpos, I.vpos, I.cseg, I.uG, I.hdisp,
@@ -309,8 +310,11 @@ static void advance_interface(Instance& I, cudaStream_t st) {
         std::swap(I.vpos, I.vpos_n);
     }
     launch_band_unmark(I.g, I.near_list, I.near_count, I.near_mark, st);
-    count(1);
-    reconstruct_full(I, st);
+    // S5 over the near list (the cells the sweeps can change) and its neighbours (the new band)
+    launch_reconstruct_list(I.g, I.near_list, I.near_count, I.vcol, I.hpos, I.vpos, I.cseg, I.flags, I.vf, st);
+    launch_band_list(I.g, I.near_list, I.near_count, I.cseg, I.hpos, I.vpos, I.flags, I.nb, st);
+    launch_compact(I.g, I.flags, I.g.nx * I.g.ny, F_BAND, I.band_list, I.band_count, I.band_idx, st);
+    count(3);   // + memset
 }
 
 enum { SLOT_ENERGY = 0, SLOT_VISC_X = 1, SLOT_VISC_Y = 2, SLOT_POISSON = 3 };

@@ -63,19 +63,10 @@ __device__ inline int seg_Q(uint16_t code, int s) { return (code >> (4 + 4 * s))
 // ---------------------------------------------------------------------------------
 // S0: Color-Vertex reconstruction of every cell
 // ---------------------------------------------------------------------------------
-__global__ void k_reconstruct(Grid g, const uint8_t* __restrict__ vcol, const double* __restrict__ hpos,
-                              const double* __restrict__ vpos, uint16_t* __restrict__ cseg,
-                              uint8_t* __restrict__ flags, double* __restrict__ vf) {
-    const long long zo = zoff(g.zs);
-    vcol = zsh(vcol, zo);
-    hpos = zsh(hpos, zo);
-    vpos = zsh(vpos, zo);
-    cseg = zsh(cseg, zo);
-    flags = zsh(flags, zo);
-    vf = zsh(vf, zo);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (i >= g.nx) return;
+__device__ inline void reconstruct_cell(const Grid& g, const uint8_t* __restrict__ vcol,
+                                        const double* __restrict__ hpos, const double* __restrict__ vpos,
+                                        uint16_t* __restrict__ cseg, uint8_t* __restrict__ flags,
+                                        double* __restrict__ vf, int i, int j) {
     int c[4];
     c[0] = vcol[vidx(g, i, j)];
     c[1] = vcol[vidx(g, i + 1, j)];
@@ -151,20 +142,51 @@ __global__ void k_reconstruct(Grid g, const uint8_t* __restrict__ vcol, const do
     if (vf) vf[cell] = area;
 }
 
-// narrow band (a cut cell in the 3x3 block) and band normal: normalised sum of (dy, -dx)
-// over the segments of the block, visited row by row
-__global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
-                       const double* __restrict__ vpos, uint8_t* __restrict__ flags,
-                       double2* __restrict__ nb) {
+__global__ void k_reconstruct(Grid g, const uint8_t* __restrict__ vcol, const double* __restrict__ hpos,
+                              const double* __restrict__ vpos, uint16_t* __restrict__ cseg,
+                              uint8_t* __restrict__ flags, double* __restrict__ vf) {
     const long long zo = zoff(g.zs);
-    cseg = zsh(cseg, zo);
+    vcol = zsh(vcol, zo);
     hpos = zsh(hpos, zo);
     vpos = zsh(vpos, zo);
+    cseg = zsh(cseg, zo);
     flags = zsh(flags, zo);
-    nb = zsh(nb, zo);
+    vf = zsh(vf, zo);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nx) return;
+    reconstruct_cell(g, vcol, hpos, vpos, cseg, flags, vf, i, j);
+}
+
+// the same over the cells within two of the start-of-step interface (the near list): with every
+// marker moving less than a cell per sweep (the sweeps report EBIT_ECFL otherwise) the vertices
+// and edges the sweeps change, and every cell they can cut, lie in those cells; the other cells
+// keep their geometry
+__global__ void k_reconstruct_list(Grid g, const int* __restrict__ list, const int* __restrict__ count,
+                                   const uint8_t* __restrict__ vcol, const double* __restrict__ hpos,
+                                   const double* __restrict__ vpos, uint16_t* __restrict__ cseg,
+                                   uint8_t* __restrict__ flags, double* __restrict__ vf) {
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    vcol = zsh(vcol, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    cseg = zsh(cseg, zo);
+    flags = zsh(flags, zo);
+    vf = zsh(vf, zo);
+    int n = *count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int c = list[k];
+        reconstruct_cell(g, vcol, hpos, vpos, cseg, flags, vf, c % g.nx, c / g.nx);
+    }
+}
+
+// narrow band (a cut cell in the 3x3 block) and band normal: normalised sum of (dy, -dx)
+// over the segments of the block, visited row by row
+__device__ inline void band_cell(const Grid& g, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                                 const double* __restrict__ vpos, uint8_t* __restrict__ flags,
+                                 double2* __restrict__ nb, int i, int j) {
     double ax = 0.0, ay = 0.0;
     bool inband = false;
     for (int jj = j - 1; jj <= j + 1; ++jj) {
@@ -195,6 +217,46 @@ __global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* 
     }
     flags[cell] = f;
     nb[cell] = n;
+}
+
+__global__ void k_band(Grid g, const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                       const double* __restrict__ vpos, uint8_t* __restrict__ flags,
+                       double2* __restrict__ nb) {
+    const long long zo = zoff(g.zs);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    flags = zsh(flags, zo);
+    nb = zsh(nb, zo);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx) return;
+    band_cell(g, cseg, hpos, vpos, flags, nb, i, j);
+}
+
+// the same over the near list and its neighbours (nine items per listed cell: the new band lies
+// within one cell of the new cut cells, which lie in the near list, and the old band lies in the
+// near list); a cell reached from several listed cells is written several times with the same
+// value (each write masks the band bit it reads)
+__global__ void k_band_list(Grid g, const int* __restrict__ list, const int* __restrict__ count,
+                            const uint16_t* __restrict__ cseg, const double* __restrict__ hpos,
+                            const double* __restrict__ vpos, uint8_t* __restrict__ flags,
+                            double2* __restrict__ nb) {
+    const long long zo = zoff(g.zs);
+    list = zsh(list, zo);
+    count = zsh(count, zo);
+    cseg = zsh(cseg, zo);
+    hpos = zsh(hpos, zo);
+    vpos = zsh(vpos, zo);
+    flags = zsh(flags, zo);
+    nb = zsh(nb, zo);
+    long long n = 9LL * *count;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int c = list[t / 9], q = (int)(t % 9);
+        int i = c % g.nx + q % 3 - 1, j = c / g.nx + q / 3 - 1;
+        if (i < 0 || i >= g.nx || j < 0 || j >= g.ny) continue;
+        band_cell(g, cseg, hpos, vpos, flags, nb, i, j);
+    }
 }
 
 // u_Gamma at cell centres from the jump condition (interfacial-velocity equation)
@@ -1005,6 +1067,18 @@ void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const 
 static int list_blocks(const Grid& g) {
     long long n = div_up(80LL * (g.nx + g.ny), 256);
     return (int)(n < 4 ? 4 : (n > 4 * 152 ? 4 * 152 : n));
+}
+
+void launch_reconstruct_list(const Grid& g, const int* list, const int* count, const uint8_t* vcol,
+                             const double* hpos, const double* vpos, uint16_t* cseg, uint8_t* flags, double* vf,
+                             cudaStream_t st) {
+    k_reconstruct_list<<<dim3(list_blocks(g), 1, g.nz), 256, 0, st>>>(g, list, count, vcol, hpos, vpos, cseg,
+                                                                      flags, vf);
+}
+
+void launch_band_list(const Grid& g, const int* list, const int* count, const uint16_t* cseg, const double* hpos,
+                      const double* vpos, uint8_t* flags, double2* nb, cudaStream_t st) {
+    k_band_list<<<dim3(list_blocks(g), 1, g.nz), 256, 0, st>>>(g, list, count, cseg, hpos, vpos, flags, nb);
 }
 
 // the same byte range of every instance of the launch (instances lie g.zs bytes apart)

@@ -16,6 +16,12 @@ void launch_reconstruct(const Grid& g, const uint8_t* vcol, const double* hpos, 
                         uint8_t* flags, double* vf, cudaStream_t st);
 void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const double* vpos, uint8_t* flags,
                  double2* nb, cudaStream_t st);
+// the same over the listed cells (reconstruction) and the listed cells with their neighbours (band)
+void launch_reconstruct_list(const Grid& g, const int* list, const int* count, const uint8_t* vcol,
+                             const double* hpos, const double* vpos, uint16_t* cseg, uint8_t* flags, double* vf,
+                             cudaStream_t st);
+void launch_band_list(const Grid& g, const int* list, const int* count, const uint16_t* cseg, const double* hpos,
+                      const double* vpos, uint8_t* flags, double2* nb, cudaStream_t st);
 void launch_sweep(const Grid& g, int axis, double dth, const int* list, const int* count, const uint8_t* vcol,
                   const double* hpos, const double* vpos, const uint16_t* cseg, const double2* uG, double* hdisp,
                   double* vdisp, uint8_t* vcol_n, double* hpos_n, double* vpos_n, int* status, cudaStream_t st);

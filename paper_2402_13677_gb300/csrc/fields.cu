@@ -130,6 +130,10 @@ __device__ inline double refl_y(const Scal& F, const Grid& g, const Refl& r, int
 
 template <class F>
 __device__ inline double tile_value(const F& T, const Grid& g, const Refl& r, int i, int j) {
+    // a ragged tile reaches past the two reflected layers (up to WX + 1 cells beyond a grid
+    // narrower than the tile): no stencil of a grid cell reads there, and the reflection would
+    // index outside the field
+    if (i > g.nx + 1 || j > g.ny + 1) return 0.0;
     bool iin = i >= 0 && i < g.nx, jin = j >= 0 && j < g.ny;
     if (iin && jin) return T[cidx(g, i, j)];
     if (jin) return refl_x(T, g, r, i, j);
@@ -160,6 +164,50 @@ __device__ inline double tile_advect(const double (*v)[WSX], int rx, int ry, dou
     return T0 - hdth * (fabs(u.x) * ex + fabs(u.y) * ey);
 }
 
+
+// ---- the same with the second differences of the tile shared: D_i = T_{i+1} - 2 T_i + T_{i-1}
+// along x at tile columns -1 .. WX (rows 0 .. WY-1) and along y at tile rows -1 .. WY (columns
+// 0 .. WX-1), formed once per cell and field.  In the upwind-ordered stencil the two second
+// differences are a1 = D_{i-1}, a2 = D_i for u >= 0 and a1 = D_{i+1}, a2 = D_i for u < 0, and
+// v2 + v3 = +-(T_{i+1} - T_{i-1}), so a stencil costs four FP64 operations instead of nine
+// (the mathematical value is that of weno3_up; the rounding differs by a few ulps of T).
+constexpr int D2X_N = (WX + 2) * WY, D2Y_N = WX * (WY + 2);
+template <int NF>
+__device__ inline void tile_d2(const double (*sh)[WSY][WSX], double (*d2x)[WY][WX + 2],
+                               double (*d2y)[WY + 2][WX]) {
+    for (int k = threadIdx.x; k < D2X_N + D2Y_N; k += blockDim.x) {
+        if (k < D2X_N) {
+            int cx = k % (WX + 2), cy = k / (WX + 2);   // tile column cx - 1, row cy
+            int rx = cx - 1 + WH, ry = cy + WH;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                d2x[f][cy][cx] = fma(-2.0, sh[f][ry][rx], sh[f][ry][rx - 1] + sh[f][ry][rx + 1]);
+        } else {
+            int q = k - D2X_N;
+            int cx = q % WX, cy = q / WX;   // tile column cx, row cy - 1
+            int rx = cx + WH, ry = cy - 1 + WH;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                d2y[f][cy][cx] = fma(-2.0, sh[f][ry][rx], sh[f][ry - 1][rx] + sh[f][ry + 1][rx]);
+        }
+    }
+    __syncthreads();
+}
+// T - dt/h (u . D T) at tile cell (tx, ty) of the staged field v with its second differences
+__device__ inline double tile_advect_d2(const double (*v)[WSX], const double (*dx)[WX + 2], const double (*dy)[WX],
+                                        int tx, int ty, double2 u, double hdth) {
+    const int rx = tx + WH, ry = ty + WH;
+    bool lx = upwind_left(u.x), ly = upwind_left(u.y);
+    double T0 = v[ry][rx];
+    // the central difference oriented along the flow (operands selected, no FP64 negation)
+    double cx = v[ry][lx ? rx + 1 : rx - 1] - v[ry][lx ? rx - 1 : rx + 1];
+    double cy = v[ly ? ry + 1 : ry - 1][rx] - v[ly ? ry - 1 : ry + 1][rx];
+    double ax2 = dx[ty][tx + 1], ax1 = dx[ty][lx ? tx : tx + 2];
+    double ay2 = dy[ty + 1][tx], ay1 = dy[ly ? ty : ty + 2][tx];
+    double ex = fma(weno_weight(ax1, ax2), ax1 - ax2, cx);
+    double ey = fma(weno_weight(ay1, ay2), ay1 - ay2, cy);
+    return T0 - hdth * (fabs(u.x) * ex + fabs(u.y) * ey);
+}
 
 __host__ inline Refl temperature_refl(const Grid& g) {
     Refl r;
@@ -518,10 +566,13 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Re
     xx = zsh(xx, zo);
     xy = zsh(xy, zo);
     __shared__ double sh[4][WSY][WSX];
+    __shared__ double d2x[4][WY][WX + 2];
+    __shared__ double d2y[4][WY + 2][WX];
     int i0 = blockIdx.x * WX, j0 = blockIdx.y * WY;
     Comp F[4] = {{u_l, 0}, {u_l, 1}, {u_v, 0}, {u_v, 1}};
     Refl R[4] = {rx, ry, rx, ry};
     tile_stage<4>(F, R, g, i0, j0, sh);
+    tile_d2<4>(sh, d2x, d2y);
     int tx = threadIdx.x % WX, ty = threadIdx.x / WX;
     int i = i0 + tx, j = j0 + ty;
     if (i >= g.nx || j >= g.ny) return;
@@ -529,12 +580,11 @@ __global__ void __launch_bounds__(WX * WY) k_mom_rhs(Grid g, Phys p, Refl rx, Re
     double coef = g.h * g.h * rho_mix(p, vf[c]) * p.inv_dt * rad_c<AXI>(g, i);
     double2 a = gc[c];
     double2 ul = u_l[c], uv = u_v[c];
-    int sx = tx + WH, sy = ty + WH;
     const double hdth = 0.5 * dth;
-    bx[c] = make_double2(coef * (tile_advect(sh[0], sx, sy, ul, hdth) + p.dt * a.x),
-                         coef * (tile_advect(sh[2], sx, sy, uv, hdth) + p.dt * a.x));
-    by[c] = make_double2(coef * (tile_advect(sh[1], sx, sy, ul, hdth) + p.dt * a.y),
-                         coef * (tile_advect(sh[3], sx, sy, uv, hdth) + p.dt * a.y));
+    bx[c] = make_double2(coef * (tile_advect_d2(sh[0], d2x[0], d2y[0], tx, ty, ul, hdth) + p.dt * a.x),
+                         coef * (tile_advect_d2(sh[2], d2x[2], d2y[2], tx, ty, uv, hdth) + p.dt * a.x));
+    by[c] = make_double2(coef * (tile_advect_d2(sh[1], d2x[1], d2y[1], tx, ty, ul, hdth) + p.dt * a.y),
+                         coef * (tile_advect_d2(sh[3], d2x[3], d2y[3], tx, ty, uv, hdth) + p.dt * a.y));
     xx[c] = make_double2(ul.x, uv.x);
     xy[c] = make_double2(ul.y, uv.y);
 }

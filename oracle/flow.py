@@ -283,26 +283,44 @@ def viscous_matrix(pb, rho_c, mu_c, comp):
     return _five_point(nx, ny, wx, wy, extra)
 
 
+def viscous_system(pb, g, u_l, u_v, gc, c):
+    """Implicit viscous system of velocity component c (Eqs. 11-12): the Helmholtz matrix (CSC)
+    and one right-hand side per phase field (columns liquid, vapour), h^2 rho_c / dt times the
+    WENO3-advected component plus dt gc_c."""
+    h, dt = pb.h, pb.dt
+    rho_c, mu_c = mixture(pb, g.vf)
+    coef = h * h * rho_c / dt * metric(pb)[0]
+    A = viscous_matrix(pb, rho_c, mu_c, c).tocsc()
+    sides = velocity_sides(pb.bc, c)
+    rhs = []
+    for u in (u_l, u_v):
+        ua = advect(u[..., c], u, sides, dt, h)
+        rhs.append((coef * (ua + dt * gc[..., c])).ravel())
+    return A, np.stack(rhs, axis=1)
+
+
 def predictor(st, gc):
     """Eqs. 11-13 for the liquid and the vapour velocity fields.  Returns u** and face u_f*."""
     pb, g = st.pb, st.geom
     ny, nx = pb.ny, pb.nx
-    h, dt = pb.h, pb.dt
-    rho_c, mu_c = mixture(pb, g.vf)
-    coef = h * h * rho_c / dt * metric(pb)[0]
+    dt = pb.dt
     ustar = {}
     for name, u in (("l", st.u_l), ("v", st.u_v)):
         ustar[name] = np.empty_like(u)
     for c in range(2):
-        A = viscous_matrix(pb, rho_c, mu_c, c).tocsc()
-        sides = velocity_sides(pb.bc, c)
-        rhs = []
-        for name, u in (("l", st.u_l), ("v", st.u_v)):
-            ua = advect(u[..., c], u, sides, dt, h)
-            rhs.append((coef * (ua + dt * gc[..., c])).ravel())
-        sol = spla.spsolve(A, np.stack(rhs, axis=1))
+        A, rhs = viscous_system(pb, g, st.u_l, st.u_v, gc, c)
+        sol = spla.spsolve(A, rhs)
         for k, name in enumerate(("l", "v")):
             ustar[name][..., c] = sol[:, k].reshape(ny, nx) - dt * gc[..., c]
+    return ustar, predicted_faces(pb, g, ustar)
+
+
+def predicted_faces(pb, g, ustar):
+    """Face velocities u_f* of both phase fields from the cell values u** (Eq. 13): the mean of
+    the two cells plus dt times gravity and the surface-tension acceleration on interior faces,
+    the boundary cell's value plus dt g on outflow faces, zero elsewhere."""
+    ny, nx = pb.ny, pb.nx
+    dt = pb.dt
     faces = {}
     rfx, rfy = face_rho(pb, g.vf)
     stx, sty = surface_tension_faces(pb, g, rfx, rfy)       # new interface (eq. 3)
@@ -321,7 +339,7 @@ def predictor(st, gc):
         if pb.bc[3] == OUTFLOW:
             fy[-1, :] = u2[-1, :, 1] + dt * pb.gy
         faces[name] = (fx, fy)
-    return ustar, faces
+    return faces
 
 
 # --------------------------------------------------------------------------

@@ -215,3 +215,54 @@ def test_full_size_graph_step_equals_stages(dev, prep):
     for k in a:
         assert np.array_equal(a[k], b[k]), k
     assert np.array_equal(da, db)
+
+
+def _scale(st, k):
+    """Magnitude a field is judged against: its group's max over the oracle state (temperatures
+    together, velocities together; pressure at least rho_l |u|^2, mdot its own max)."""
+    groups = (("T_l", "T_v"), ("u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v"))
+    umax = max(np.max(np.abs(getattr(st, n))) for n in groups[1])
+    if k == "p":
+        return max(np.max(np.abs(st.p)), st.pb.rho_l * umax * umax, 1e-300)
+    for names in groups:
+        if k in names:
+            return max(max(np.max(np.abs(getattr(st, n))) for n in names), 1e-300)
+    return max(np.max(np.abs(getattr(st, k))), 1e-300)
+
+
+def test_full_batch_sampled_instances_match_oracle(dev):
+    """The whole batched workload (4096 Stefan / bubble instances of sides 32..256) as the
+    benchmark runs it (mixed precision, CUDA graphs on the worker streams, schedules chosen by
+    the autotuner), one step; one instance of each grid side and kind is compared with the
+    oracle's step of that instance, every cell and face: interface bit for bit, fields within
+    1e-7 of their group's magnitude with the refinement run to a 1e-12 relative residual."""
+    pbs = w.c4_batch(4096)
+    ctx = E.ebit_init([E.config_from_problem(pb, E.EBIT_MIXED, 1e-12, 600) for pb in pbs], dev.stream.cuda_stream,
+                      dev.alloc)
+    picks = {}
+    for b, pb in enumerate(pbs):
+        picks.setdefault((pb.nx, pb.meta["c4_kind"]), b)
+    names = ("T_l", "T_v", "u_l", "u_v", "ufx_l", "ufx_v", "ufy_l", "ufy_v", "p", "mdot", "vcol", "hx_pos",
+             "vy_pos")
+    try:
+        for b, pb in enumerate(pbs):
+            E.upload_state(ctx, b, pb, pb.vcol, np.where(pb.hx_cut > 0, pb.hx_pos, 0.0),
+                           np.where(pb.vy_cut > 0, pb.vy_pos, 0.0),
+                           {"T_l": pb.T_l, "T_v": pb.T_v, "u_l": pb.u_l, "u_v": pb.u_v, "ufx_l": pb.ufx_l,
+                            "ufx_v": pb.ufx_v, "ufy_l": pb.ufy_l, "ufy_v": pb.ufy_v, "p": pb.p}, pb.t0)
+        E.ebit_run_stage(ctx, E.STAGE_PREPARE)
+        E.ebit_autotune(ctx, 2)
+        E.ebit_step(ctx, 1, allow_noconv=True)   # judged below, cell by cell
+        got = {b: E.download(ctx, b, pbs[b].nx, pbs[b].ny, names) for b in picks.values()}
+    finally:
+        E.ebit_destroy(ctx)
+    assert len(picks) >= 10            # most (side, kind) pairs occur among 4096 draws
+    for (n, kind), b in sorted(picks.items()):
+        st = S.prepare(pbs[b])
+        S.step(st)
+        g = got[b]
+        assert np.array_equal(g["vcol"], st.vcol), (n, kind)
+        assert np.array_equal(g["hx_pos"], st.hx_pos) and np.array_equal(g["vy_pos"], st.vy_pos), (n, kind)
+        worst = max(relerr(g[k], getattr(st, k), _scale(st, k)) for k in names[:10])
+        print(f"instance {b} ({kind}, {n}^2): largest field error {worst:.2e}")
+        assert worst <= 1e-7, (n, kind, worst)

@@ -83,9 +83,11 @@ __device__ __forceinline__ void zphys(const Grid& g, Phys& p) {
 // step
 struct CellWalk {
     int c, i, j, stride, di, dj, nx;
-    __device__ CellWalk(int nx_) : nx(nx_) {
-        c = blockIdx.x * blockDim.x + threadIdx.x;
-        stride = gridDim.x * blockDim.x;
+    __device__ CellWalk(int nx_) : CellWalk(nx_, blockIdx.x, gridDim.x) {}
+    // the walk of block v of an nv-block grid (a virtual block of a reduction kernel)
+    __device__ CellWalk(int nx_, int v, int nv) : nx(nx_) {
+        c = v * blockDim.x + threadIdx.x;
+        stride = nv * blockDim.x;
         i = c % nx;
         j = c / nx;
         di = stride % nx;

@@ -913,7 +913,7 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
                               const double* __restrict__ fy_l, const double* __restrict__ fy_v,
                               const double* __restrict__ T_l, const double* __restrict__ T_v,
                               double* __restrict__ partial, unsigned* __restrict__ ticket, double* __restrict__ clock,
-                              double* __restrict__ out) {
+                              double* __restrict__ out, int vb) {
     zphys(g, p);
     const long long zo = zoff(g.zs);
     vf = zsh(vf, zo);
@@ -934,59 +934,64 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
     out = zsh(out, zo);
     __shared__ double sh[32];
     __shared__ bool lastblk;
-    double s[NDIAG_SUMS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // virtual blocks: the reduction is that of a vb-block launch whatever the launch's size
+    // (blocks take the virtual blocks b, b + gridDim.x, ...), as in the solver's reductions
     int N = g.nx * g.ny;
-    for (CellWalk cw(g.nx); cw.c < N; cw.next()) {
-        int c = cw.c, i = cw.i, j = cw.j;
-        double v = vf[c];
-        double rc = rho_mix(p, v);
-        const double mc = rad_c<AXI>(g, i);
-        s[0] += (1.0 - v) * mc;
-        s[2] += rc * mc;
-        uint16_t code = cseg[c];
-        int ns = code & 3;
-        if (ns) {
-            s[4] += 1.0;
-            for (int q = 0; q < ns; ++q) {
-                int kP = (code >> (2 + 4 * q)) & 3, kQ = (code >> (4 + 4 * q)) & 3;
-                auto ml = [&](int k) -> double2 {
-                    switch (k) {
-                        case 0: return make_double2(hpos[hidx(g, i, j)], 0.0);
-                        case 1: return make_double2(1.0, vpos[veidx(g, i + 1, j)]);
-                        case 2: return make_double2(hpos[hidx(g, i, j + 1)], 1.0);
-                        default: return make_double2(0.0, vpos[veidx(g, i, j)]);
+    double tot[NDIAG_SUMS];
+    for (int vblk = blockIdx.x; vblk < vb; vblk += gridDim.x) {
+        double s[NDIAG_SUMS] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (CellWalk cw(g.nx, vblk, vb); cw.c < N; cw.next()) {
+            int c = cw.c, i = cw.i, j = cw.j;
+            double v = vf[c];
+            double rc = rho_mix(p, v);
+            const double mc = rad_c<AXI>(g, i);
+            s[0] += (1.0 - v) * mc;
+            s[2] += rc * mc;
+            uint16_t code = cseg[c];
+            int ns = code & 3;
+            if (ns) {
+                s[4] += 1.0;
+                for (int q = 0; q < ns; ++q) {
+                    int kP = (code >> (2 + 4 * q)) & 3, kQ = (code >> (4 + 4 * q)) & 3;
+                    auto ml = [&](int k) -> double2 {
+                        switch (k) {
+                            case 0: return make_double2(hpos[hidx(g, i, j)], 0.0);
+                            case 1: return make_double2(1.0, vpos[veidx(g, i + 1, j)]);
+                            case 2: return make_double2(hpos[hidx(g, i, j + 1)], 1.0);
+                            default: return make_double2(0.0, vpos[veidx(g, i, j)]);
+                        }
+                    };
+                    double2 P = ml(kP), Q = ml(kQ);
+                    double dx = Q.x - P.x, dy = Q.y - P.y;
+                    double ms = AXI ? g.r0 + (double)i + 0.5 * (P.x + Q.x) : 1.0;   // the segment's radius
+                    s[1] += mdot[c] * sqrt(dx * dx + dy * dy) * g.h * ms;
+                }
+            }
+            bool liq = flags[c] & F_CCOL;
+            if (i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1) {
+                // boundary faces of this cell: outflow (mass and vapour volume) and fixed-T walls
+                for (int sd = 0; sd < 4; ++sd) {
+                    bool on = sd == 0 ? i == 0 : sd == 1 ? i == g.nx - 1 : sd == 2 ? j == 0 : j == g.ny - 1;
+                    if (!on) continue;
+                    if (g.bc[sd] == BC_OUTFLOW) {
+                        double u = sd < 2 ? (liq ? fx_l : fx_v)[veidx(g, sd == 0 ? 0 : g.nx, j)]
+                                          : (liq ? fy_l : fy_v)[hidx(g, i, sd == 2 ? 0 : g.ny)];
+                        double un = ((sd == 0 || sd == 2) ? -u : u) *
+                                    (sd == 0 ? rad_fx<AXI>(g, 0) : (sd == 1 ? rad_fx<AXI>(g, g.nx) : mc));
+                        s[3] += rc * un;
+                        s[5] += (1.0 - v) * un;
                     }
-                };
-                double2 P = ml(kP), Q = ml(kQ);
-                double dx = Q.x - P.x, dy = Q.y - P.y;
-                double ms = AXI ? g.r0 + (double)i + 0.5 * (P.x + Q.x) : 1.0;   // the segment's radius
-                s[1] += mdot[c] * sqrt(dx * dx + dy * dy) * g.h * ms;
-            }
-        }
-        bool liq = flags[c] & F_CCOL;
-        if (i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1) {
-            // boundary faces of this cell: outflow (mass and vapour volume) and fixed-T walls
-            for (int sd = 0; sd < 4; ++sd) {
-                bool on = sd == 0 ? i == 0 : sd == 1 ? i == g.nx - 1 : sd == 2 ? j == 0 : j == g.ny - 1;
-                if (!on) continue;
-                if (g.bc[sd] == BC_OUTFLOW) {
-                    double u = sd < 2 ? (liq ? fx_l : fx_v)[veidx(g, sd == 0 ? 0 : g.nx, j)]
-                                      : (liq ? fy_l : fy_v)[hidx(g, i, sd == 2 ? 0 : g.ny)];
-                    double un = ((sd == 0 || sd == 2) ? -u : u) *
-                                (sd == 0 ? rad_fx<AXI>(g, 0) : (sd == 1 ? rad_fx<AXI>(g, g.nx) : mc));
-                    s[3] += rc * un;
-                    s[5] += (1.0 - v) * un;
-                }
-                if (g.bc[sd] == BC_WALL && g.Tfix[sd]) {
-                    s[6] += 2.0 * (g.Tw[sd] - (liq ? T_l : T_v)[c]) * g.inv_h;
-                    s[7] += 1.0;
+                    if (g.bc[sd] == BC_WALL && g.Tfix[sd]) {
+                        s[6] += 2.0 * (g.Tw[sd] - (liq ? T_l : T_v)[c]) * g.inv_h;
+                        s[7] += 1.0;
+                    }
                 }
             }
         }
-    }
-    for (int q = 0; q < NDIAG_SUMS; ++q) {
-        double r = block_sum(s[q], sh);
-        if (threadIdx.x == 0) partial[q * gridDim.x + blockIdx.x] = r;
+        for (int q = 0; q < NDIAG_SUMS; ++q) {
+            double r = block_sum(s[q], sh);
+            if (threadIdx.x == 0) partial[q * vb + vblk] = r;
+        }
     }
     __threadfence();
     if (threadIdx.x == 0) lastblk = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -995,9 +1000,9 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
     __threadfence();
     for (int q = 0; q < NDIAG_SUMS; ++q) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += partial[q * gridDim.x + b];
+        for (int b = threadIdx.x; b < vb; b += blockDim.x) v += partial[q * vb + b];
         double r = block_sum(v, sh);
-        if (threadIdx.x == 0) s[q] = r;
+        if (threadIdx.x == 0) tot[q] = r;
     }
     if (threadIdx.x == 0) {
         double h2 = g.h * g.h;
@@ -1005,20 +1010,20 @@ __global__ void k_diagnostics(Grid g, Phys p, const double* __restrict__ vf, con
         clock[0] += p.dt;
         clock[1] += 1.0;
         out[0] = clock[0];
-        out[1] = s[0] * h2 * ring;
-        out[2] = s[1] * p.dt / p.rho_v * ring;
-        out[3] = s[2] * h2 * ring;
-        out[4] = s[3] * g.h * p.dt * ring;
-        out[5] = s[4];
-        out[6] = s[5] * g.h * p.dt * ring;
+        out[1] = tot[0] * h2 * ring;
+        out[2] = tot[1] * p.dt / p.rho_v * ring;
+        out[3] = tot[2] * h2 * ring;
+        out[4] = tot[3] * g.h * p.dt * ring;
+        out[5] = tot[4];
+        out[6] = tot[5] * g.h * p.dt * ring;
         double nu = 0.0;
-        if (s[7] > 0.0) {
+        if (tot[7] > 0.0) {
             double Tw = 0.0;
             for (int sd = 3; sd >= 0; --sd)
                 if (g.bc[sd] == BC_WALL && g.Tfix[sd]) Tw = g.Tw[sd];   // the first fixed-T wall
             double gm = sqrt(p.gx * p.gx + p.gy * p.gy), dr = fabs(p.rho_l - p.rho_v);
             double ell = (has_sigma(p) && gm > 0.0 && dr > 0.0) ? sqrt(p.sigma / (dr * gm)) : 1.0;
-            if (Tw != p.T_sat) nu = ell / (Tw - p.T_sat) * s[6] / s[7];
+            if (Tw != p.T_sat) nu = ell / (Tw - p.T_sat) * tot[6] / tot[7];
         }
         out[7] = nu;
         *ticket = 0u;
@@ -1125,7 +1130,12 @@ void launch_ghost_velocity(const Grid& g, const Phys& p, const int* band_list, c
     double J = 1.0 / p.rho_l - 1.0 / p.rho_v;
     // five items per band cell; the band is O(sqrt N): blocks as for the other list kernels
     long long nbk = div_up(5LL * 8 * (g.nx + g.ny), 256);
-    int blocks = (int)(nbk < 4 ? 4 : (nbk > 4 * 152 ? 4 * 152 : nbk));
+    nbk = nbk < 4 ? 4 : (nbk > 4 * 152 ? 4 * 152 : nbk);
+    if (g.nz > 1) {   // a batch: about two blocks per SM slot shared among its instances
+        long long per = (2LL * 4 * 152) / g.nz;
+        nbk = nbk < per ? nbk : (per < 1 ? 1 : per);
+    }
+    int blocks = (int)nbk;
     k_ghost_list<<<dim3(blocks, 1, g.nz), 256, 0, st>>>(g, J, band_list, band_count, flags, mdot, nb, vcol, hpos,
                                                         vpos, u_l, u_v, ufx_l, ufx_v, ufy_l, ufy_v);
 }
@@ -1184,8 +1194,11 @@ void launch_diagnostics(const Grid& g, const Phys& p, const double* vf, const ui
                         const double* T_v, double* partial, unsigned* ticket, double* clock, double* out,
                         cudaStream_t st) {
     auto k = g.axi ? k_diagnostics<true> : k_diagnostics<false>;
-    k<<<dim3(diag_blocks(g), 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v,
-                                                     T_l, T_v, partial, ticket, clock, out);
+    // a batch: about two blocks per SM slot in total, each taking several virtual blocks
+    int vb = diag_blocks(g), per = (2 * 4 * 152) / g.nz;
+    int lb = g.nz <= 1 ? vb : (vb < per ? vb : (per < 1 ? 1 : per));
+    k<<<dim3(lb, 1, g.nz), 256, 0, st>>>(g, p, vf, cseg, hpos, vpos, mdot, flags, fx_l, fx_v, fy_l, fy_v, T_l, T_v,
+                                         partial, ticket, clock, out, vb);
 }
 
 }  // namespace ebit

@@ -1063,10 +1063,17 @@ void launch_band(const Grid& g, const uint16_t* cseg, const double* hpos, const 
 
 // blocks of a kernel over the cells near the interface (four threads per cell): about 20 cells
 // per unit of interface length across the grid (nx + ny), four blocks per SM at most; the
-// kernels stride over the list, so a longer interface only takes more iterations
+// kernels stride over the list, so a longer interface only takes more iterations.  A batch
+// shares about two blocks per SM slot among its instances (at least one each), instead of
+// launching each instance's count of mostly idle blocks.
 static int list_blocks(const Grid& g) {
     long long n = div_up(80LL * (g.nx + g.ny), 256);
-    return (int)(n < 4 ? 4 : (n > 4 * 152 ? 4 * 152 : n));
+    n = n < 4 ? 4 : (n > 4 * 152 ? 4 * 152 : n);
+    if (g.nz > 1) {
+        long long per = (2LL * 4 * 152) / g.nz;
+        n = n < per ? n : (per < 1 ? 1 : per);
+    }
+    return (int)n;
 }
 
 void launch_reconstruct_list(const Grid& g, const int* list, const int* count, const uint8_t* vcol,

@@ -1353,7 +1353,7 @@ struct DotAcc<float, NR> {
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z, T* __restrict__ p0,
                                                 T* __restrict__ p1, T* __restrict__ q, SolveState* st,
-                                                double* partial, unsigned* ticket) {
+                                                double* partial, unsigned* ticket, int vb) {
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -1374,53 +1374,56 @@ __global__ void __launch_bounds__(256) k_apply(Lev<T> L, const T* __restrict__ z
 #pragma unroll
     for (int k = 0; k < NR; ++k) beta[k] = (T)st->beta[k];
     int N = L.nx * L.ny;
-    DotAcc<T, NR> acc;
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        DotAcc<T, NR> acc;
 #pragma unroll 2
-    for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
-        int c = cw.c, i = cw.i, j = cw.j;
-        auto pn = [&](int cc) {
-            Vec<T, NR> a = Z[cc], b = Po[cc];
+        for (CellWalk cw(L.nx, v, vb); cw.c < N; cw.next()) {
+            int c = cw.c, i = cw.i, j = cw.j;
+            auto pn = [&](int cc) {
+                Vec<T, NR> a = Z[cc], b = Po[cc];
 #pragma unroll
-            for (int k = 0; k < NR; ++k)
-                if (beta[k] != T(0)) a.v[k] += beta[k] * b.v[k];   // beta = 0: p = z (old p unused)
-            return a;
-        };
-        Vec<T, NR> pc = pn(c), qv;
-        T d = L.diag[c];
+                for (int k = 0; k < NR; ++k)
+                    if (beta[k] != T(0)) a.v[k] += beta[k] * b.v[k];   // beta = 0: p = z (old p unused)
+                return a;
+            };
+            Vec<T, NR> pc = pn(c), qv;
+            T d = L.diag[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) qv.v[k] = d * pc.v[k];
-        if (i > 0) {
-            T w = L.wl[c];
-            Vec<T, NR> a = pn(c - 1);
-            for (int k = 0; k < NR; ++k)
-                qv.v[k] += w * (pc.v[k] - a.v[k]);
-        }
-        if (i < L.nx - 1) {
-            T w = L.wl[c + 1];
-            Vec<T, NR> a = pn(c + 1);
-            for (int k = 0; k < NR; ++k)
-                qv.v[k] += w * (pc.v[k] - a.v[k]);
-        }
-        if (j > 0) {
-            T w = L.wb[c];
-            Vec<T, NR> a = pn(c - L.nx);
-            for (int k = 0; k < NR; ++k)
-                qv.v[k] += w * (pc.v[k] - a.v[k]);
-        }
-        if (j < L.ny - 1) {
-            T w = L.wb[c + L.nx];
-            Vec<T, NR> a = pn(c + L.nx);
-            for (int k = 0; k < NR; ++k)
-                qv.v[k] += w * (pc.v[k] - a.v[k]);
-        }
+            for (int k = 0; k < NR; ++k) qv.v[k] = d * pc.v[k];
+            if (i > 0) {
+                T w = L.wl[c];
+                Vec<T, NR> a = pn(c - 1);
+                for (int k = 0; k < NR; ++k)
+                    qv.v[k] += w * (pc.v[k] - a.v[k]);
+            }
+            if (i < L.nx - 1) {
+                T w = L.wl[c + 1];
+                Vec<T, NR> a = pn(c + 1);
+                for (int k = 0; k < NR; ++k)
+                    qv.v[k] += w * (pc.v[k] - a.v[k]);
+            }
+            if (j > 0) {
+                T w = L.wb[c];
+                Vec<T, NR> a = pn(c - L.nx);
+                for (int k = 0; k < NR; ++k)
+                    qv.v[k] += w * (pc.v[k] - a.v[k]);
+            }
+            if (j < L.ny - 1) {
+                T w = L.wb[c + L.nx];
+                Vec<T, NR> a = pn(c + L.nx);
+                for (int k = 0; k < NR; ++k)
+                    qv.v[k] += w * (pc.v[k] - a.v[k]);
+            }
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
-        Pn[c] = pc;
-        Q[c] = qv;
+            for (int k = 0; k < NR; ++k) acc.add(k, pc.v[k], qv.v[k]);
+            Pn[c] = pc;
+            Q[c] = qv;
+        }
+        acc.flush();
+        block_partial<NR>(acc.tot, partial, vb, v);
     }
-    acc.flush();
     double tot[NR];
-    if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
+    if (last_block_total<NR>(partial, vb, ticket, tot)) {
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
             st->pq[k] = tot[k];
@@ -1435,7 +1438,7 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
                                                  const T* __restrict__ p0,
                                                  const T* __restrict__ p1, const T* __restrict__ q, SolveState* st,
                                                  double* partial, unsigned* ticket, cudaGraphConditionalHandle h,
-                                                 int use_h) {
+                                                 int use_h, int vb) {
     const long long zo = zoff(zs);
     x = zsh(x, zo);
     r = zsh(r, zo);
@@ -1453,28 +1456,31 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
     T alpha[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) alpha[k] = (T)st->alpha[k];
-    DotAcc<T, NR> acc;
-    const int stride = gridDim.x * blockDim.x;
-    for (int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < N; c0 += DOT_CHUNK * stride) {
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        DotAcc<T, NR> acc;
+        const int stride = vb * blockDim.x;
+        for (int c0 = v * blockDim.x + threadIdx.x; c0 < N; c0 += DOT_CHUNK * stride) {
 #pragma unroll
-        for (int u = 0; u < DOT_CHUNK; ++u) {
-            int c = c0 + u * stride;
-            if (c < N) {   // a guard, not an exit: the chunk's loads can all be in flight at once
-                Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
+            for (int u = 0; u < DOT_CHUNK; ++u) {
+                int c = c0 + u * stride;
+                if (c < N) {   // a guard, not an exit: the chunk's loads can all be in flight at once
+                    Vec<T, NR> xv = X[c], rv = Rr[c], pv = Pn[c], qv = Q[c];
 #pragma unroll
-                for (int k = 0; k < NR; ++k) {
-                    xv.v[k] += alpha[k] * pv.v[k];
-                    rv.v[k] -= alpha[k] * qv.v[k];
-                    acc.add(k, rv.v[k], rv.v[k]);
+                    for (int k = 0; k < NR; ++k) {
+                        xv.v[k] += alpha[k] * pv.v[k];
+                        rv.v[k] -= alpha[k] * qv.v[k];
+                        acc.add(k, rv.v[k], rv.v[k]);
+                    }
+                    X[c] = xv;
+                    Rr[c] = rv;
                 }
-                X[c] = xv;
-                Rr[c] = rv;
             }
+            acc.flush();
         }
-        acc.flush();
+        block_partial<NR>(acc.tot, partial, vb, v);
     }
     double tot[NR];
-    if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
+    if (last_block_total<NR>(partial, vb, ticket, tot)) {
         bool done = true, bad = false;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
@@ -1723,7 +1729,7 @@ template <int NR>
 __global__ void __launch_bounds__(256)
 k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
          SolveState* st, double* partial, unsigned* ticket, double rtol2, int max_iters,
-         cudaGraphConditionalHandle h, int use_h) {
+         cudaGraphConditionalHandle h, int use_h, int vb) {
     const long long zo = zoff(L.zs);
     L.diag = zsh(L.diag, zo);
     L.wl = zsh(L.wl, zo);
@@ -1735,40 +1741,43 @@ k_init64(Lev<double> L, const double* __restrict__ b, const double* __restrict__
     partial = zsh(partial, zo);
     ticket = zsh(ticket, zo);
     int N = L.nx * L.ny;
-    double acc[2 * NR];
-#pragma unroll
-    for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
     const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
-    for (CellWalk cw(L.nx); cw.c < N; cw.next()) {
-        int c = cw.c, i = cw.i, j = cw.j;
-        Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
-        double dg = L.diag[c];
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        double acc[2 * NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
-        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
-        if (i < L.nx - 1) {
-            double w = L.wl[c + 1];
-            for (int k = 0; k < NR; ++k)
-                s.v[k] += w * (xv.v[k] - X[c + 1].v[k]);
-        }
-        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
-        if (j < L.ny - 1) {
-            double w = L.wb[c + L.nx];
-            for (int k = 0; k < NR; ++k)
-                s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]);
-        }
-        Vec<double, NR> rv;
+        for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
+        for (CellWalk cw(L.nx, v, vb); cw.c < N; cw.next()) {
+            int c = cw.c, i = cw.i, j = cw.j;
+            Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
+            double dg = L.diag[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            rv.v[k] = bv.v[k] - s.v[k];
-            acc[k] += rv.v[k] * rv.v[k];
-            acc[NR + k] += bv.v[k] * bv.v[k];
+            for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
+            if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
+            if (i < L.nx - 1) {
+                double w = L.wl[c + 1];
+                for (int k = 0; k < NR; ++k)
+                    s.v[k] += w * (xv.v[k] - X[c + 1].v[k]);
+            }
+            if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
+            if (j < L.ny - 1) {
+                double w = L.wb[c + L.nx];
+                for (int k = 0; k < NR; ++k)
+                    s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]);
+            }
+            Vec<double, NR> rv;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                rv.v[k] = bv.v[k] - s.v[k];
+                acc[k] += rv.v[k] * rv.v[k];
+                acc[NR + k] += bv.v[k] * bv.v[k];
+            }
+            reinterpret_cast<Vec<double, NR>*>(r)[c] = rv;
         }
-        reinterpret_cast<Vec<double, NR>*>(r)[c] = rv;
+        block_partial<2 * NR>(acc, partial, vb, v);
     }
     double tot[2 * NR];
-    if (grid_reduce<2 * NR>(acc, partial, ticket, tot)) {
+    if (last_block_total<2 * NR>(partial, vb, ticket, tot)) {
         bool done = true, bad = false;
         for (int k = 0; k < 2; ++k) {
             double rr = k < NR ? tot[k] : 0.0, bb = k < NR ? tot[NR + k] : 0.0;
@@ -1806,22 +1815,25 @@ template <int NR>
 __global__ void __launch_bounds__(256) k_ir_init(int N, long long zs, const double* __restrict__ b, SolveState* st,
                                                   double* partial,
                                                   unsigned* ticket, double rtol2, double inner_rtol, int max_iters,
-                                                  int max_outer) {
+                                                  int max_outer, int vb) {
     const long long zo = zoff(zs);
     b = zsh(b, zo);
     st = zsh(st, zo);
     partial = zsh(partial, zo);
     ticket = zsh(ticket, zo);
-    double acc[NR];
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        double acc[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        Vec<double, NR> bv = reinterpret_cast<const Vec<double, NR>*>(b)[c];
+        for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+        for (int c = v * blockDim.x + threadIdx.x; c < N; c += vb * blockDim.x) {
+            Vec<double, NR> bv = reinterpret_cast<const Vec<double, NR>*>(b)[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] += bv.v[k] * bv.v[k];
+            for (int k = 0; k < NR; ++k) acc[k] += bv.v[k] * bv.v[k];
+        }
+        block_partial<NR>(acc, partial, vb, v);
     }
     double tot[NR];
-    if (grid_reduce<NR>(acc, partial, ticket, tot)) {
+    if (last_block_total<NR>(partial, vb, ticket, tot)) {
         for (int k = 0; k < 2; ++k) {
             double bb = k < NR ? tot[k] : 0.0;
             st->obb[k] = bb;
@@ -1848,7 +1860,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
                                                       float* __restrict__ e32, SolveState* st, double* partial,
                                                       unsigned* ticket, cudaGraphConditionalHandle ho,
                                                       cudaGraphConditionalHandle hi, int use_h, int set_hi,
-                                                      unsigned* coop_bar) {
+                                                      unsigned* coop_bar, int vb) {
     // the whole-solve cooperative launch that follows counts its barrier arrivals from 0 (its
     // previous launch has completed: stream order)
     if (coop_bar && blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0) *coop_bar = 0u;
@@ -1878,43 +1890,46 @@ __global__ void __launch_bounds__(256) k_ir_residual(Lev<double> L, const double
         sc[k] = st->scale_next[k];
         ksc[k] = (int)((__double_as_longlong(sc[k]) >> 52) & 0x7ff) - 1023;
     }
-    DotAcc<float, NR> acc;
     const Vec<double, NR>* X = reinterpret_cast<const Vec<double, NR>*>(x);
     const Vec<double, NR>* B = reinterpret_cast<const Vec<double, NR>*>(b);
-    for (CellWalk cw(L.nx); cw.c < N; acc.flush())
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        DotAcc<float, NR> acc;
+        for (CellWalk cw(L.nx, v, vb); cw.c < N; acc.flush())
 #pragma unroll
-    for (int u = 0; u < DOT_CHUNK; ++u, cw.next()) {
-        if (cw.c >= N) continue;
-        int c = cw.c, i = cw.i, j = cw.j;
-        Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
-        double dg = L.diag[c];
+        for (int u = 0; u < DOT_CHUNK; ++u, cw.next()) {
+            if (cw.c >= N) continue;
+            int c = cw.c, i = cw.i, j = cw.j;
+            Vec<double, NR> xv = X[c], bv = B[c], s;   // s = (A x)_i in flux form
+            double dg = L.diag[c];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
-        if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
-        if (i < L.nx - 1) {
-            double w = L.wl[c + 1];
-            for (int k = 0; k < NR; ++k)
-                s.v[k] += w * (xv.v[k] - X[c + 1].v[k]);
-        }
-        if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
-        if (j < L.ny - 1) {
-            double w = L.wb[c + L.nx];
-            for (int k = 0; k < NR; ++k)
-                s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]);
-        }
-        Vec<float, NR> rf, ez;
+            for (int k = 0; k < NR; ++k) s.v[k] = dg * xv.v[k];
+            if (i > 0) { double w = L.wl[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - 1].v[k]); }
+            if (i < L.nx - 1) {
+                double w = L.wl[c + 1];
+                for (int k = 0; k < NR; ++k)
+                    s.v[k] += w * (xv.v[k] - X[c + 1].v[k]);
+            }
+            if (j > 0) { double w = L.wb[c]; for (int k = 0; k < NR; ++k) s.v[k] += w * (xv.v[k] - X[c - L.nx].v[k]); }
+            if (j < L.ny - 1) {
+                double w = L.wb[c + L.nx];
+                for (int k = 0; k < NR; ++k)
+                    s.v[k] += w * (xv.v[k] - X[c + L.nx].v[k]);
+            }
+            Vec<float, NR> rf, ez;
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            float f = d2f_rn2(bv.v[k] - s.v[k], ksc[k]);
-            rf.v[k] = f;
-            acc.add(k, f, f);
-            ez.v[k] = 0.0f;
+            for (int k = 0; k < NR; ++k) {
+                float f = d2f_rn2(bv.v[k] - s.v[k], ksc[k]);
+                rf.v[k] = f;
+                acc.add(k, f, f);
+                ez.v[k] = 0.0f;
+            }
+            reinterpret_cast<Vec<float, NR>*>(r32)[c] = rf;
+            reinterpret_cast<Vec<float, NR>*>(e32)[c] = ez;
         }
-        reinterpret_cast<Vec<float, NR>*>(r32)[c] = rf;
-        reinterpret_cast<Vec<float, NR>*>(e32)[c] = ez;
+        block_partial<NR>(acc.tot, partial, vb, v);
     }
     double tot[NR];
-    if (grid_reduce<NR>(acc.tot, partial, ticket, tot)) {
+    if (last_block_total<NR>(partial, vb, ticket, tot)) {
         bool done = true;
         for (int k = 0; k < 2; ++k) {
             double s2 = k < NR ? sc[k] * sc[k] : 1.0;   // a power of two: the divisions are exact
@@ -1978,6 +1993,18 @@ __global__ void k_ir_update(int N, long long zs, double* __restrict__ x, const f
 static inline int nblocks(long long n) {
     long long b = (n + RB - 1) / RB;
     return (int)(b < NRED ? (b < 1 ? 1 : b) : NRED);
+}
+// Blocks per instance of a launch over nz instances.  The reduction kernels are written for
+// nblocks(n) blocks per instance (their virtual blocks, a function of the grid alone) and run
+// them on this many real blocks, each taking the virtual blocks b, b + launch, ...: the same cells
+// in the same order into the same slots, so that an instance's sums do not depend on how many
+// instances share the launch.  One instance keeps one real block per virtual block; a batch
+// gets about two blocks per SM slot in total (NRED = 4 per SM), instead of thousands of blocks
+// that each reduce a few hundred cells.
+static inline int lblocks(long long n, int nz) {
+    int v = nblocks(n);
+    int per = (2 * NRED) / (nz > 0 ? nz : 1);
+    return nz <= 1 ? v : (v < per ? v : (per < 1 ? 1 : per));
 }
 
 void Solver::plan(int nx_, int ny_) {
@@ -2435,9 +2462,10 @@ static void cg_body(Solver& s, T* x, T* r, T* z, T* p, T* q, SolveState* st, cud
     int N = s.nx * s.ny;
     Lev<T> L0 = lev<T>(s, 0);
     T* p1 = p + (size_t)N * NR;
-    k_apply<T, NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1);
-    k_update<T, NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial, s.tickets + 2,
-                                                               h, use_h);
+    k_apply<T, NR><<<dim3(lblocks(N, s.nz), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1,
+                                                                   nblocks(N));
+    k_update<T, NR><<<dim3(lblocks(N, s.nz), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial,
+                                                                    s.tickets + 2, h, use_h, nblocks(N));
     if (!s.use_graph) s.launches += 2;
 }
 
@@ -2503,16 +2531,16 @@ static void solve_fp64(Solver& s, const double* b, double* x, double rtol, int m
         cudaGraph_t g;
         cudaGraphConditionalHandle h = make_handle(stm, &g);
         int mode = s.nz > 1 ? 2 : 1;
-        k_init64<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets,
-                                                                rtol * rtol, max_iter, h, mode);
+        k_init64<NR><<<dim3(lblocks(N, s.nz), 1, s.nz), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets,
+                                                                      rtol * rtol, max_iter, h, mode, nblocks(N));
         ++s.launches;
         cudaStream_t bs = begin_while(stm, s.aux[0], h);
         cg_body<double, NR>(s, x, s.d_r, z, s.d_p, s.d_q, s.st, h, mode, bs);
         end_while(bs);
         return;
     }
-    k_init64<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets,
-                                                            rtol * rtol, max_iter, 0, 0);
+    k_init64<NR><<<dim3(lblocks(N, s.nz), 1, s.nz), RB, 0, stm>>>(L0, b, x, s.d_r, s.st, s.partial, s.tickets,
+                                                                  rtol * rtol, max_iter, 0, 0, nblocks(N));
     ++s.launches;
     poll(s, stm);
     for (int it = 0; it < max_iter && !s.st_host[s.slot].done; ++it) {
@@ -2594,8 +2622,9 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
     const int max_outer = 8;
     const double inner_rtol = s.inner_rtol;
     float* z = s.f_x;
-    k_ir_init<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(N, s.zs, b, s.st, s.partial, s.tickets + 3,
-                                                             rtol * rtol, inner_rtol, max_iter, max_outer);
+    const int vb = nblocks(N), lb = lblocks(N, s.nz), lbu = lblocks((long long)N * NR, s.nz);
+    k_ir_init<NR><<<dim3(lb, 1, s.nz), RB, 0, stm>>>(N, s.zs, b, s.st, s.partial, s.tickets + 3, rtol * rtol,
+                                                     inner_rtol, max_iter, max_outer, vb);
     ++s.launches;
     CoarsePlan<float> PC;
     SmallPlan PS;
@@ -2609,26 +2638,26 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
         cudaStream_t obs = begin_while(stm, s.aux[0], ho);
         int mode = s.nz > 1 ? 2 : 1;
         if (persist) {
-            k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
-                                                                         s.tickets + 5, ho, ho, mode, 0, pbar);
+            k_ir_residual<NR><<<dim3(lb, 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                                 s.tickets + 5, ho, ho, mode, 0, pbar, vb);
             launch_persist<NR>(s, PC, PS, PG, psmem, obs);
         } else {
             cudaGraph_t og;
             cudaGraphConditionalHandle hi = make_handle(obs, &og);
             if (mode == 2) k_cond_reset<<<1, 32, 0, obs>>>(ho, hi, 1);
-            k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
-                                                                         s.tickets + 5, ho, hi, mode, 1, nullptr);
+            k_ir_residual<NR><<<dim3(lb, 1, s.nz), RB, 0, obs>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                                 s.tickets + 5, ho, hi, mode, 1, nullptr, vb);
             cudaStream_t ibs = begin_while(obs, s.aux[1], hi);
             cg_body<float, NR>(s, s.f_e, s.f_r, z, s.f_p, s.f_q, s.st, hi, mode, ibs);
             end_while(ibs);
         }
-        k_ir_update<NR><<<dim3(nblocks(N * NR), 1, s.nz), RB, 0, obs>>>(N, s.zs, x, s.f_e, s.st);
+        k_ir_update<NR><<<dim3(lbu, 1, s.nz), RB, 0, obs>>>(N, s.zs, x, s.f_e, s.st);
         end_while(obs);
         return;
     }
     for (int o = 0; o <= max_outer; ++o) {
-        k_ir_residual<NR><<<dim3(nblocks(N), 1, s.nz), RB, 0, stm>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
-                                                                     s.tickets + 5, 0, 0, 0, 0, pbar);
+        k_ir_residual<NR><<<dim3(lb, 1, s.nz), RB, 0, stm>>>(L64, b, x, s.f_r, s.f_e, s.st, s.partial,
+                                                             s.tickets + 5, 0, 0, 0, 0, pbar, vb);
         ++s.launches;
         poll(s, stm);
         if (s.st_host[s.slot].odone) break;
@@ -2640,7 +2669,7 @@ static void solve_mixed(Solver& s, Lev<double> L64, const double* b, double* x, 
                 poll(s, stm);
             }
         }
-        k_ir_update<NR><<<dim3(nblocks(N * NR), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, s.f_e, s.st);
+        k_ir_update<NR><<<dim3(lbu, 1, s.nz), RB, 0, stm>>>(N, s.zs, x, s.f_e, s.st);
         ++s.launches;
     }
 }

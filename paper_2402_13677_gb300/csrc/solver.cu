@@ -258,11 +258,14 @@ struct Region {
     static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, HX = SX / 2, NC = SY * HX;
     static constexpr int NSEG = SY / 2, THREADS = HX * NSEG;
     static_assert(SX % 2 == 0 && SY % 2 == 0, "region sides must be even");
-    T* x0;   // x of colour 0 (NR per cell), then colour 1; then the core residuals (k_pre)
+    // the FP64 tile kernels restrict through shared memory (their residuals in registers
+    // would spill at the register count their occupancy allows); the FP32 ones in registers
+    static constexpr bool RES_SMEM = sizeof(T) == 8;
+    T* x0;   // x of colour 0 (NR per cell), then colour 1; then the core residuals (FP64 k_pre)
     __device__ Region(unsigned char* base) { x0 = (T*)base; }
     __device__ T* x(int c) const { return x0 + c * (NR * NC); }
     __device__ T* res() const { return x0 + 2 * NR * NC; }
-    static constexpr size_t BYTES = ((size_t)2 * NC + TX * TY) * NR * sizeof(T);
+    static constexpr size_t BYTES = ((size_t)2 * NC + (RES_SMEM ? TX * TY : 0)) * NR * sizeof(T);
     __host__ __device__ static constexpr size_t bytes() { return BYTES; }
 };
 template <int H>
@@ -616,8 +619,10 @@ __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __r
     tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
     tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
-    // x of the core cells to global memory, their residuals to shared memory
-    T* res = R.res();
+    // x of the core cells to global memory; their residuals stay in registers ([r][e]: row
+    // ry0 + r, column 2k + e), or go to shared memory (FP64)
+    T res[2][2][NR];
+    T* sres = R.res();
     if (act)
         tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
             const T* xo = R.x(1 - c);
@@ -634,24 +639,42 @@ __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __r
                 T xu = r == 0 ? own_v : xo[(q + HX) * NR + k2];
                 T ax = C.d[r][c] * x0v + C.wl[r][c] * (x0v - xl) + C.wr[r][c] * (x0v - xrt) +
                        C.wb[r][c] * (x0v - xd) + C.wt[r][c] * (x0v - xu);
-                res[((ry - H) * TX + (rx - H)) * NR + k2] = C.b[r][c][k2] - ax;
+                if constexpr (Rg::RES_SMEM) sres[((ry - H) * TX + (rx - H)) * NR + k2] = C.b[r][c][k2] - ax;
+                else res[r][e][k2] = C.b[r][c][k2] - ax;
             }
             reinterpret_cast<Vec<T, NR>*>(x)[gj * L.nx + gi] = xv;
         });
-    __syncthreads();
-    // restriction: sum of the four children
     int cnx = L.nx / 2, cny = L.ny / 2;
-    for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += blockDim.x) {
-        int ti = t % (TX / 2), tj = t / (TX / 2);
-        int ci = bx * (TX / 2) + ti, cj = by * (TY / 2) + tj;
-        if (ci >= cnx || cj >= cny) continue;
-        // the core starts at an even global index, so children (2ti + a, 2tj + b) are core cells
-        Vec<T, NR> acc;
+    if constexpr (Rg::RES_SMEM) {
+        __syncthreads();
+        // restriction: sum of the four children (the core starts at an even global index, so
+        // children (2ti + a, 2tj + b) are core cells)
+        for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += blockDim.x) {
+            int ti = t % (TX / 2), tj = t / (TX / 2);
+            int ci = bx * (TX / 2) + ti, cj = by * (TY / 2) + tj;
+            if (ci >= cnx || cj >= cny) continue;
+            Vec<T, NR> acc;
 #pragma unroll
-        for (int k2 = 0; k2 < NR; ++k2)
-            acc.v[k2] = res[((2 * tj) * TX + 2 * ti) * NR + k2] + res[((2 * tj) * TX + 2 * ti + 1) * NR + k2] +
-                        res[((2 * tj + 1) * TX + 2 * ti) * NR + k2] + res[((2 * tj + 1) * TX + 2 * ti + 1) * NR + k2];
-        reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
+            for (int k2 = 0; k2 < NR; ++k2)
+                acc.v[k2] = sres[((2 * tj) * TX + 2 * ti) * NR + k2] + sres[((2 * tj) * TX + 2 * ti + 1) * NR + k2] +
+                            sres[((2 * tj + 1) * TX + 2 * ti) * NR + k2] +
+                            sres[((2 * tj + 1) * TX + 2 * ti + 1) * NR + k2];
+            reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
+        }
+        return;
+    }
+    // restriction: sum of the four children.  The region starts H (even) cells before the tile,
+    // so a thread's 2 x 2 block is the four children of coarse cell (k - H/2, ry0/2 - H/2) of the
+    // tile; a coarse cell of the grid has all four children inside the grid, hence computed above
+    int ti = k - H / 2, tj = ry0 / 2 - H / 2;
+    if (act && ti >= 0 && ti < TX / 2 && tj >= 0 && tj < TY / 2) {
+        int ci = bx * (TX / 2) + ti, cj = by * (TY / 2) + tj;
+        if (ci < cnx && cj < cny) {
+            Vec<T, NR> acc;
+#pragma unroll
+            for (int k2 = 0; k2 < NR; ++k2) acc.v[k2] = res[0][0][k2] + res[0][1][k2] + res[1][0][k2] + res[1][1][k2];
+            reinterpret_cast<Vec<T, NR>*>(bc)[cj * cnx + ci] = acc;
+        }
     }
 }
 

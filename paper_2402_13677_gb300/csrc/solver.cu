@@ -76,8 +76,17 @@ struct Lev {
 };
 
 // correctly rounded reciprocal (the same value as 1 / v)
-__device__ inline float rcp_rn(float v) { return __frcp_rn(v); }
-__device__ inline double rcp_rn(double v) { return __drcp_rn(v); }
+// reciprocal of a smoother's diagonal.  FP32 (the preconditioner of the inner solves): the
+// hardware approximation (one MUFU instruction, within about an ulp; the diagonals are normal
+// numbers), the same in every kernel, so that the tile, cooperative and single-block paths stay
+// identical; a preconditioner need only be fixed and symmetric, not correctly rounded.  FP64:
+// correctly rounded.
+__device__ inline float rcp_diag(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ inline double rcp_diag(double v) { return __drcp_rn(v); }
 
 __device__ inline bool skip(const SolveState* s) { return s->done != 0 || s->odone != 0; }
 
@@ -387,9 +396,11 @@ __device__ inline void staged_tiles(unsigned char* sbase, const TileMaps& M, int
     using Sg = Stage<T, NR, H, POST>;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Sg::OFF_BAR);
     stage_init<T, NR, H, POST>(sbase);
-    int t = blockIdx.x;
-    if (threadIdx.x == 0 && t < nt) stage_issue<T, NR, H, POST>(sbase, M, (t % tx) * TX - H, (t / tx) * TY - H);
-    for (uint32_t i = 0; t < nt; ++i, t += gridDim.x) {
+    // tile t = by tx + bx, advanced by gridDim.x = gq tx + gr without a division per tile
+    int t = blockIdx.x, bx = t % tx, by = t / tx;
+    const int gq = (int)gridDim.x / tx, gr = (int)gridDim.x % tx;
+    if (threadIdx.x == 0 && t < nt) stage_issue<T, NR, H, POST>(sbase, M, bx * TX - H, by * TY - H);
+    for (uint32_t i = 0; t < nt; ++i) {
         bool landed = mbar_wait_bounded(bar, i & 1u);
         if (__syncthreads_or(!landed)) {
             if (threadIdx.x == 0) atomicOr(&st->fault, 1);
@@ -397,14 +408,18 @@ __device__ inline void staged_tiles(unsigned char* sbase, const TileMaps& M, int
             __syncthreads();
             break;
         }
-        int tn = t + gridDim.x;
-        work(t, [&]() {
+        int tn = t + gridDim.x, bxn = bx + gr, byn = by + gq;
+        if (bxn >= tx) { bxn -= tx; ++byn; }
+        work(t, bx, by, [&]() {
             if (threadIdx.x == 0 && tn < nt) {
                 fence_proxy_async();
-                stage_issue<T, NR, H, POST>(sbase, M, (tn % tx) * TX - H, (tn / tx) * TY - H);
+                stage_issue<T, NR, H, POST>(sbase, M, bxn * TX - H, byn * TY - H);
             }
         });
         __syncthreads();   // the region is rewritten by the next tile
+        t = tn;
+        bx = bxn;
+        by = byn;
     }
 }
 
@@ -422,10 +437,10 @@ struct Cells {
 // the result of the first colour-0 half-sweep from x = 0, for post-smoothing xin + the
 // prolongated coarse x); cells outside the domain get D = 1, zero weights, b = x = 0, so
 // sweeps leave them 0
-template <typename T, int NR, int H, bool POST>
-__device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, int ry0, const Lev<T>& L,
-                                 const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
-                                 int cnx, int gx0, int gy0, const unsigned char* stage) {
+template <typename T, int NR, int H, bool POST, bool CHECK>
+__device__ inline void tile_load_cells(Region<T, NR, H>& R, Cells<T, NR>& C, int k, int ry0, const Lev<T>& L,
+                                       const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
+                                       int cnx, int gx0, int gy0, const unsigned char* stage) {
     constexpr int HX = Region<T, NR, H>::HX;
     using Sg = Stage<T, NR, H, POST>;
     static_assert(H % 2 == 0 && TX % 2 == 0 && TY % 2 == 0, "regions must start at an even cell");
@@ -437,7 +452,7 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, in
         for (int e = 0; e < 2; ++e) {
             int rx = 2 * k + e;
             int gi = gx0 + rx;
-            bool in = gj >= 0 && gj < L.ny && gi >= 0 && gi < L.nx;
+            bool in = !CHECK || (gj >= 0 && gj < L.ny && gi >= 0 && gi < L.nx);
             Vec<T, NR> bv, xv;
             T dv, wlv, wbv, wrv, wtv;
             if (stage) {
@@ -467,16 +482,16 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, in
                 }
             } else {
                 // unconditional loads (clamped, then masked): all of them can be in flight at once
-                int gic = min(max(gi, 0), L.nx - 1), gjc = min(max(gj, 0), L.ny - 1);
+                int gic = CHECK ? min(max(gi, 0), L.nx - 1) : gi, gjc = CHECK ? min(max(gj, 0), L.ny - 1) : gj;
                 int g = gjc * L.nx + gic;
                 bv = reinterpret_cast<const Vec<T, NR>*>(b)[g];
                 dv = L.diag[g];
                 wlv = L.wl[g];
                 wbv = L.wb[g];
-                wrv = L.wl[gic + 1 < L.nx ? g + 1 : g];
-                wtv = L.wb[gjc + 1 < L.ny ? g + L.nx : g];
-                if (gi + 1 >= L.nx) wrv = T(0);
-                if (gj + 1 >= L.ny) wtv = T(0);
+                wrv = L.wl[!CHECK || gic + 1 < L.nx ? g + 1 : g];
+                wtv = L.wb[!CHECK || gjc + 1 < L.ny ? g + L.nx : g];
+                if (CHECK && gi + 1 >= L.nx) wrv = T(0);
+                if (CHECK && gj + 1 >= L.ny) wtv = T(0);
                 if (POST) {
                     xv = reinterpret_cast<const Vec<T, NR>*>(xin)[g];
                     Vec<T, NR> cv = reinterpret_cast<const Vec<T, NR>*>(xc)[(gjc >> 1) * cnx + (gic >> 1)];
@@ -487,7 +502,7 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, in
                     for (int k2 = 0; k2 < NR; ++k2) xv.v[k2] = T(0);
                 }
             }
-            if (!in) {
+            if (CHECK && !in) {
 #pragma unroll
                 for (int k2 = 0; k2 < NR; ++k2) { bv.v[k2] = T(0); xv.v[k2] = T(0); }
                 dv = T(1);
@@ -495,7 +510,7 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, in
             }
             // this cell's colour is e ^ r (both known at compile time)
             bool mine0 = (e ^ r) == 0;
-            T idv = rcp_rn(dv + wlv + wrv + wbv + wtv);
+            T idv = rcp_diag(dv + wlv + wrv + wbv + wtv);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 bool m = (c == 0) == mine0;
@@ -527,16 +542,64 @@ __device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, in
     }
 }
 
+// A region wholly inside the grid, with the right and upper faces of its last cells too (all
+// but the tiles along the grid's edges), needs no range tests or masks
+template <typename T, int NR, int H, bool POST>
+__device__ inline void tile_load(Region<T, NR, H>& R, Cells<T, NR>& C, int k, int ry0, const Lev<T>& L,
+                                 const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ xc,
+                                 int cnx, int gx0, int gy0, const unsigned char* stage) {
+    constexpr int SX = Region<T, NR, H>::SX, SY = Region<T, NR, H>::SY;
+    if (gx0 >= 0 && gy0 >= 0 && gx0 + SX < L.nx && gy0 + SY < L.ny)
+        tile_load_cells<T, NR, H, POST, false>(R, C, k, ry0, L, b, xin, xc, cnx, gx0, gy0, stage);
+    else
+        tile_load_cells<T, NR, H, POST, true>(R, C, k, ry0, L, b, xin, xc, cnx, gx0, gy0, stage);
+}
+
+// A thread's place in a tile region, the same for every tile of a launch (computed once per
+// launch, one register): bit 2 (S - 1) + r is set if half-sweep S updates the thread's cell
+// (r, COLOR ^ r) (distance >= S from the region's edge; COLOR, the sweep's colour, is S & 1),
+// bit 8 + 2 r + c if cell (r, c) lies in the tile's core, bit 12 if the thread owns cells.  The
+// column pair k and the row pair ry0 follow from threadIdx (a division by a constant).
+struct TileThread {
+    unsigned m;
+    __device__ bool act() const { return (m >> 12) & 1u; }
+    __device__ bool sweeps(int S, int r) const { return (m >> (2 * (S - 1) + r)) & 1u; }
+    __device__ bool core(int r, int c) const { return (m >> (8 + 2 * r + c)) & 1u; }
+};
+template <int H>
+__device__ inline TileThread tile_thread() {
+    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, HX = SX / 2, THREADS = HX * (SY / 2);
+    const int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    unsigned m = threadIdx.x < THREADS ? 1u << 12 : 0u;
+#pragma unroll
+    for (int S = 1; S <= 4; ++S)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int ry = ry0 + r, rx = 2 * k + ((S & 1) ^ r);
+            if (ry >= S && ry < SY - S && rx >= S && rx < SX - S) m |= 1u << (2 * (S - 1) + r);
+        }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            int ry = ry0 + r, rx = 2 * k + (c ^ r);
+            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY) m |= 1u << (8 + 2 * r + c);
+        }
+    return TileThread{m};
+}
+
 // one Gauss-Seidel half-sweep of colour COLOR over the region cells at distance >= S from its
 // edge; both rows' operands are loaded before either result is stored.  Cell (r, e) of the
 // thread (colour COLOR, e = COLOR ^ r) has its horizontal neighbour 2k + 1 - e and its vertical
 // neighbour in row 1 - r among the thread's own cells (registers); the other two come from the
 // neighbour threads through shared memory.
 template <typename T, int NR, int H, int S, int COLOR>
-__device__ inline void tile_sweep(Region<T, NR, H>& R, Cells<T, NR>& C, int k, int ry0, bool act) {
+__device__ inline void tile_sweep(Region<T, NR, H>& R, Cells<T, NR>& C, const TileThread& tt) {
+    static_assert(COLOR == (S & 1), "half-sweep S has colour S & 1");
     using Rg = Region<T, NR, H>;
-    constexpr int HX = Rg::HX, SX = Rg::SX, SY = Rg::SY;
-    if (act) {
+    constexpr int HX = Rg::HX;
+    const int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    if (tt.act()) {
         const T* xo = R.x(1 - COLOR);
         T acc[2][NR];
         bool ok[2];
@@ -545,8 +608,7 @@ __device__ inline void tile_sweep(Region<T, NR, H>& R, Cells<T, NR>& C, int k, i
         for (int r = 0; r < 2; ++r) {
             int ry = ry0 + r;
             const int e = COLOR ^ r;
-            int rx = 2 * k + e;
-            ok[r] = ry >= S && ry < SY - S && rx >= S && rx < SX - S;
+            ok[r] = tt.sweeps(S, r);
             int q = ok[r] ? ry * HX + k : HX + 1;   // a harmless in-range slot otherwise
             qs[r] = q;
 #pragma unroll
@@ -576,9 +638,10 @@ __device__ inline void tile_sweep(Region<T, NR, H>& R, Cells<T, NR>& C, int k, i
 
 // the thread's core cells (inside the TX x TY tile and the domain): f(r, c, rx, ry, q, gi, gj)
 template <typename T, int NR, int H, class Fn>
-__device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, int gx0, int gy0, const Lev<T>& L,
-                                       Fn&& f) {
+__device__ inline void tile_core_cells(const Cells<T, NR>& C, const TileThread& tt, int gx0, int gy0,
+                                       const Lev<T>& L, Fn&& f) {
     constexpr int HX = Region<T, NR, H>::HX;
+    const int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         int ry = ry0 + r;
@@ -586,8 +649,7 @@ __device__ inline void tile_core_cells(const Cells<T, NR>& C, int k, int ry0, in
         for (int c = 0; c < 2; ++c) {
             int rx = 2 * k + (c ^ r);
             int gi = gx0 + rx, gj = gy0 + ry;
-            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY && gi < L.nx && gj < L.ny)
-                f(r, c, rx, ry, ry * HX + k, gi, gj);
+            if (tt.core(r, c) && gi < L.nx && gj < L.ny) f(r, c, rx, ry, ry * HX + k, gi, gj);
         }
     }
 }
@@ -602,29 +664,29 @@ struct NoOp {
 template <typename T, int NR, class AfterLoad = NoOp>
 __device__ inline void pre_tile(const Lev<T>& L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
                                 int bx, int by, unsigned char* smem, const unsigned char* stage,
-                                AfterLoad after_load = AfterLoad()) {
+                                const TileThread& tt, AfterLoad after_load = AfterLoad()) {
     constexpr int H = HPRE;
     static_assert(NU == 2, "the sweep sequence below is written out for two pairs");
     using Rg = Region<T, NR, H>;
     constexpr int HX = Rg::HX;
     Rg R(smem);
     int gx0 = bx * TX - H, gy0 = by * TY - H;
-    bool act = threadIdx.x < Rg::THREADS;
-    int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    const bool act = tt.act();
+    const int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
     Cells<T, NR> C;
     if (act) tile_load<T, NR, H, false>(R, C, k, ry0, L, b, nullptr, nullptr, 0, gx0, gy0, stage);
     __syncthreads();
     after_load();
     // the first colour-0 half-sweep (from x = 0) was done by tile_load
-    tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 1, 1>(R, C, tt);
+    tile_sweep<T, NR, H, 2, 0>(R, C, tt);
+    tile_sweep<T, NR, H, 3, 1>(R, C, tt);
     // x of the core cells to global memory; their residuals stay in registers ([r][e]: row
     // ry0 + r, column 2k + e), or go to shared memory (FP64)
     T res[2][2][NR];
     T* sres = R.res();
     if (act)
-        tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
+        tile_core_cells<T, NR, H>(C, tt, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
             const T* xo = R.x(1 - c);
             const int e = c ^ r;   // rx = 2k + e
             Vec<T, NR> xv;
@@ -709,11 +771,12 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
         unsigned char* stage =
             reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
-        staged_tiles<T, NR, H, false>(stage, maps, tx, nt, st, [&](int t, auto after_load) {
-            pre_tile<T, NR>(L, b, x, bc, t % tx, t / tx, smem, stage, after_load);
+        const TileThread tt = tile_thread<H>();
+        staged_tiles<T, NR, H, false>(stage, maps, tx, nt, st, [&](int, int bx, int by, auto after_load) {
+            pre_tile<T, NR>(L, b, x, bc, bx, by, smem, stage, tt, after_load);
         });
     } else {
-        pre_tile<T, NR>(L, b, x, bc, blockIdx.x, blockIdx.y, smem, nullptr);
+        pre_tile<T, NR>(L, b, x, bc, blockIdx.x, blockIdx.y, smem, nullptr, tile_thread<H>());
     }
     // algorithmic bytes: b, diag, wl, wb read; x and the quarter-size coarse b written
     timer_end(tm, (double)L.nx * L.ny * bytes_cell);
@@ -724,27 +787,29 @@ k_pre(Lev<T> L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc, 
 template <typename T, int NR, bool DOT, class AfterLoad = NoOp>
 __device__ inline Vec<T, 2> post_tile(const Lev<T>& L, const T* __restrict__ b, const T* __restrict__ xin,
                                     T* __restrict__ x, const T* __restrict__ xc, int bx, int by, unsigned char* smem,
-                                    const unsigned char* stage, AfterLoad after_load = AfterLoad()) {
+                                    const unsigned char* stage, const TileThread& tt,
+                                    AfterLoad after_load = AfterLoad()) {
     constexpr int H = HPOST;
     using Rg = Region<T, NR, H>;
-    constexpr int HX = Rg::HX;
     Rg R(smem);
     int gx0 = bx * TX - H, gy0 = by * TY - H;
-    bool act = threadIdx.x < Rg::THREADS;
-    int k = threadIdx.x % HX, ry0 = 2 * (threadIdx.x / HX);
+    constexpr int HX = Rg::HX;
+    const bool act = tt.act();
     Cells<T, NR> C;
-    if (act) tile_load<T, NR, H, true>(R, C, k, ry0, L, b, xin, xc, L.nx / 2, gx0, gy0, stage);
+    if (act)
+        tile_load<T, NR, H, true>(R, C, threadIdx.x % HX, 2 * (threadIdx.x / HX), L, b, xin, xc, L.nx / 2, gx0, gy0,
+                                  stage);
     __syncthreads();
     after_load();
-    tile_sweep<T, NR, H, 1, 1>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 2, 0>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 3, 1>(R, C, k, ry0, act);
-    tile_sweep<T, NR, H, 4, 0>(R, C, k, ry0, act);
+    tile_sweep<T, NR, H, 1, 1>(R, C, tt);
+    tile_sweep<T, NR, H, 2, 0>(R, C, tt);
+    tile_sweep<T, NR, H, 3, 1>(R, C, tt);
+    tile_sweep<T, NR, H, 4, 0>(R, C, tt);
     // r.z of the thread's (at most four) core cells, summed in T
     Vec<T, 2> dot;
     dot.v[0] = dot.v[1] = T(0);
     if (act)
-        tile_core_cells<T, NR, H>(C, k, ry0, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
+        tile_core_cells<T, NR, H>(C, tt, gx0, gy0, L, [&](int r, int c, int rx, int ry, int q, int gi, int gj) {
             Vec<T, NR> xv;
 #pragma unroll
             for (int k2 = 0; k2 < NR; ++k2) {
@@ -789,13 +854,15 @@ k_post(Lev<T> L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
             reinterpret_cast<unsigned char*>(align128(reinterpret_cast<uintptr_t>(smem) + Rg::BYTES));
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
         // r.z: one slot per tile, summed in tile order as with one block per tile
-        staged_tiles<T, NR, H, true>(stage, maps, tx, nt, st, [&](int t, auto after_load) {
-            Vec<T, 2> d = post_tile<T, NR, DOT>(L, b, xin, x, xc, t % tx, t / tx, smem, stage, after_load);
+        const TileThread tt = tile_thread<H>();
+        staged_tiles<T, NR, H, true>(stage, maps, tx, nt, st, [&](int t, int bx, int by, auto after_load) {
+            Vec<T, 2> d = post_tile<T, NR, DOT>(L, b, xin, x, xc, bx, by, smem, stage, tt, after_load);
             if (DOT) block_partial_t<T, NR>(d.v, partial, nt, t);
         });
         nslot = nt;
     } else {
-        Vec<T, 2> d = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, nullptr);
+        Vec<T, 2> d = post_tile<T, NR, DOT>(L, b, xin, x, xc, blockIdx.x, blockIdx.y, smem, nullptr,
+                                            tile_thread<H>());
         if (DOT) block_partial_t<T, NR>(d.v, partial, nslot, blockIdx.y * gridDim.x + blockIdx.x);
     }
     if (DOT) {
@@ -1049,7 +1116,7 @@ __device__ void small_cycle(const SmallPlan& P, const T* __restrict__ diag, cons
                 int q = o + j * nx + i;
                 T dg = M.d[q] + M.wl[q] + (i < nx - 1 ? M.wl[q + 1] : T(0)) + M.wb[q] +
                        (j < ny - 1 ? M.wb[q + nx] : T(0));
-                M.id[q] = rcp_rn(dg);
+                M.id[q] = rcp_diag(dg);
             }
     }
     __syncthreads();
@@ -1166,11 +1233,12 @@ __global__ void __launch_bounds__(CC_THREADS) k_coarse_cycle(CoarsePlan<T> C, Sm
     if (skip(st)) return;   // written by an earlier launch: the same for every block
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned gen = 0;   // arrivals that pass the next barrier (bar[0] starts the launch at 0)
+    const TileThread tpre = tile_thread<HPRE>(), tpost = tile_thread<HPOST>();
     for (int l = C.l0; l < C.nb; ++l) {
         const Lev<T>& L = C.L[l];
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
         for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-            pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr);
+            pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr, tpre);
             __syncthreads();
         }
         grid_sync(bar, gen, st, C.spin);
@@ -1181,7 +1249,7 @@ __global__ void __launch_bounds__(CC_THREADS) k_coarse_cycle(CoarsePlan<T> C, Sm
         const Lev<T>& L = C.L[l];
         int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
         for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-            post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr);
+            post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr, tpost);
             __syncthreads();
         }
         if (l > C.l0) grid_sync(bar, gen, st, C.spin);
@@ -1584,6 +1652,7 @@ k_cg_persist(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag, const T* 
     if (skip(st)) return;   // the refinement has converged: the same in every block
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned gen = 0;
+    const TileThread tpre = tile_thread<HPRE>(), tpost = tile_thread<HPOST>();
     const int G = gridDim.x;
     const Lev<T>& L0 = C.L[0];
     const int N = L0.nx * L0.ny;
@@ -1606,7 +1675,7 @@ k_cg_persist(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag, const T* 
             const Lev<T>& L = C.L[l];
             int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
             for (int t = blockIdx.x; t < nt; t += G) {
-                pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr);
+                pre_tile<T, NR>(L, C.b[l], C.x2[l], C.bc[l], t % tx, t / tx, smem, nullptr, tpre);
                 __syncthreads();
             }
             ok = grid_sync_ok(bar, gen, st, C.spin);
@@ -1618,14 +1687,15 @@ k_cg_persist(CoarsePlan<T> C, SmallPlan P, const T* __restrict__ diag, const T* 
             const Lev<T>& L = C.L[l];
             int tx = (L.nx + TX - 1) / TX, nt = tx * ((L.ny + TY - 1) / TY);
             for (int t = blockIdx.x; t < nt; t += G) {
-                post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr);
+                post_tile<T, NR, false>(L, C.b[l], C.x2[l], C.xo[l], C.xc[l], t % tx, t / tx, smem, nullptr, tpost);
                 __syncthreads();
             }
             ok = grid_sync_ok(bar, gen, st, C.spin);
         }
         if (!ok) break;
         for (int t = blockIdx.x; t < nt0; t += G) {
-            Vec<T, 2> d = post_tile<T, NR, true>(L0, C.b[0], C.x2[0], C.xo[0], C.xc[0], t % tx0, t / tx0, smem, nullptr);
+            Vec<T, 2> d =
+                post_tile<T, NR, true>(L0, C.b[0], C.x2[0], C.xo[0], C.xc[0], t % tx0, t / tx0, smem, nullptr, tpost);
             block_partial_t<T, NR>(d.v, prz, nt0, t);
             __syncthreads();
         }

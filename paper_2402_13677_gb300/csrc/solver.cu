@@ -1589,6 +1589,168 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
     }
 }
 
+// ---- the same two kernels for FP32 and one right-hand side, four cells per thread ---------------
+// On rows whose length is a multiple of four (and 16-byte aligned arrays) a thread takes four
+// consecutive cells of a row: 16-byte loads and stores, a quarter of the index work and four
+// times the bytes in flight per load.  Each cell's arithmetic is k_apply's / k_update's (the
+// same flux form, terms in the same order); the dot products add a thread's four cells in order
+// to its FP32-pair sum.  Virtual blocks over the quads as in the per-cell kernels, so a batched
+// instance still sums exactly as the instance launched alone.
+
+// walk over the quads (row j, cells 4m .. 4m + 3) of virtual block v of vb, without a division
+// per step
+struct QuadWalk {
+    int t, m, j, stride, dm, dj, nq;
+    __device__ QuadWalk(int nq_, int v, int nv) : nq(nq_) {
+        t = v * blockDim.x + threadIdx.x;
+        stride = nv * blockDim.x;
+        m = t % nq;
+        j = t / nq;
+        dm = stride % nq;
+        dj = stride / nq;
+    }
+    __device__ void next() {
+        t += stride;
+        m += dm;
+        j += dj;
+        if (m >= nq) { m -= nq; ++j; }
+    }
+};
+
+__device__ __forceinline__ float f4(const float4& a, int k) { return k == 0 ? a.x : k == 1 ? a.y : k == 2 ? a.z : a.w; }
+
+__global__ void __launch_bounds__(256) k_apply4(Lev<float> L, const float* __restrict__ z, float* __restrict__ p0,
+                                                float* __restrict__ p1, float* __restrict__ q, SolveState* st,
+                                                double* partial, unsigned* ticket, int vb) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    z = zsh(z, zo);
+    p0 = zsh(p0, zo);
+    p1 = zsh(p1, zo);
+    q = zsh(q, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
+    if (skip(st)) return;
+    const float* __restrict__ Po = (st->iters & 1) ? p1 : p0;
+    float* __restrict__ Pn = (st->iters & 1) ? p0 : p1;
+    const float beta = (float)st->beta[0];
+    const int nx = L.nx, ny = L.ny, nq = nx / 4, NQ = nq * ny;
+    // p = z + beta p_old of one cell / of four (beta = 0: p = z, the old p unused)
+    auto pn1 = [&](int cc) { return beta != 0.0f ? z[cc] + beta * Po[cc] : z[cc]; };
+    auto pn4 = [&](int cc) {
+        float4 a = *reinterpret_cast<const float4*>(z + cc);
+        if (beta != 0.0f) {
+            float4 o = *reinterpret_cast<const float4*>(Po + cc);
+            a.x += beta * o.x;
+            a.y += beta * o.y;
+            a.z += beta * o.z;
+            a.w += beta * o.w;
+        }
+        return a;
+    };
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        DotAcc<float, 1> acc;
+#pragma unroll 2
+        for (QuadWalk w(nq, v, vb); w.t < NQ; w.next()) {
+            const int i0 = 4 * w.m, j = w.j, c = j * nx + i0;
+            float4 pc = pn4(c);
+            float4 dg = *reinterpret_cast<const float4*>(L.diag + c);
+            float4 wl = *reinterpret_cast<const float4*>(L.wl + c);
+            float4 wb = *reinterpret_cast<const float4*>(L.wb + c);
+            float pl = i0 > 0 ? pn1(c - 1) : 0.0f;
+            float pr = i0 + 4 < nx ? pn1(c + 4) : 0.0f;
+            float wr3 = i0 + 4 < nx ? L.wl[c + 4] : 0.0f;
+            float4 pd = j > 0 ? pn4(c - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 pu = j < ny - 1 ? pn4(c + nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 wt = j < ny - 1 ? *reinterpret_cast<const float4*>(L.wb + c + nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float qv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float p = f4(pc, a);
+                float s = f4(dg, a) * p;
+                const int i = i0 + a;
+                if (i > 0) s += f4(wl, a) * (p - (a == 0 ? pl : f4(pc, a - 1)));
+                if (i < nx - 1) s += (a == 3 ? wr3 : f4(wl, a + 1)) * (p - (a == 3 ? pr : f4(pc, a + 1)));
+                if (j > 0) s += f4(wb, a) * (p - f4(pd, a));
+                if (j < ny - 1) s += f4(wt, a) * (p - f4(pu, a));
+                qv[a] = s;
+                acc.add(0, p, s);
+            }
+            *reinterpret_cast<float4*>(Pn + c) = pc;
+            *reinterpret_cast<float4*>(q + c) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+        }
+        acc.flush();
+        block_partial<1>(acc.tot, partial, vb, v);
+    }
+    double tot[1];
+    if (last_block_total<1>(partial, vb, ticket, tot)) {
+        st->pq[0] = tot[0];
+        st->alpha[0] = tot[0] != 0.0 ? st->rz[0] / tot[0] : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_update4(int N, long long zs, float* __restrict__ x, float* __restrict__ r,
+                                                 const float* __restrict__ p0, const float* __restrict__ p1,
+                                                 const float* __restrict__ q, SolveState* st, double* partial,
+                                                 unsigned* ticket, cudaGraphConditionalHandle h, int use_h, int vb) {
+    const long long zo = zoff(zs);
+    x = zsh(x, zo);
+    r = zsh(r, zo);
+    p0 = zsh(p0, zo);
+    p1 = zsh(p1, zo);
+    q = zsh(q, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
+    if (skip(st)) return;
+    const float4* __restrict__ Pn = reinterpret_cast<const float4*>((st->iters & 1) ? p0 : p1);
+    const float4* __restrict__ Q = reinterpret_cast<const float4*>(q);
+    float4* __restrict__ X = reinterpret_cast<float4*>(x);
+    float4* __restrict__ R = reinterpret_cast<float4*>(r);
+    const float alpha = (float)st->alpha[0];
+    const int NQ = N / 4;
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        DotAcc<float, 1> acc;
+#pragma unroll 2
+        for (int t = v * blockDim.x + threadIdx.x; t < NQ; t += vb * blockDim.x) {
+            float4 xv = X[t], rv = R[t], pv = Pn[t], qv = Q[t];
+            xv.x += alpha * pv.x;
+            xv.y += alpha * pv.y;
+            xv.z += alpha * pv.z;
+            xv.w += alpha * pv.w;
+            rv.x -= alpha * qv.x;
+            rv.y -= alpha * qv.y;
+            rv.z -= alpha * qv.z;
+            rv.w -= alpha * qv.w;
+            acc.add(0, rv.x, rv.x);
+            acc.add(0, rv.y, rv.y);
+            acc.add(0, rv.z, rv.z);
+            acc.add(0, rv.w, rv.w);
+            X[t] = xv;
+            R[t] = rv;
+        }
+        acc.flush();
+        block_partial<1>(acc.tot, partial, vb, v);
+    }
+    double tot[1];
+    if (last_block_total<1>(partial, vb, ticket, tot)) {
+        bool done = true, bad = false;
+        st->rr[0] = tot[0];
+        if (!(tot[0] <= st->tol2[0])) done = false;
+        bad = !isfinite(tot[0]);
+        st->iters += 1;
+        if (bad) {   // a NaN or infinity: no further iteration can recover
+            st->nonfinite = 1;
+            done = true;
+        }
+        if (done) st->done = 1;
+        set_cond(h, use_h, (!done && st->iters < st->max_iters) ? 1u : 0u);
+    }
+}
+
 // ---- a whole inner solve in one cooperative launch (small grids) ---------------------------
 // On small grids a CG iteration is a handful of short kernels (the V-cycle legs, p/q, x/r), each
 // a graph node whose launch costs as much as its work.  k_cg_persist runs the whole inner FP32
@@ -2555,6 +2717,20 @@ static void cg_body(Solver& s, T* x, T* r, T* z, T* p, T* q, SolveState* st, cud
     int N = s.nx * s.ny;
     Lev<T> L0 = lev<T>(s, 0);
     T* p1 = p + (size_t)N * NR;
+    if constexpr (sizeof(T) == 4 && NR == 1) {
+        // four cells per thread where the rows and the arrays allow 16-byte accesses
+        auto a16 = [](const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; };
+        if (s.nx % 4 == 0 && s.zs % 16 == 0 && a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(L0.diag) &&
+            a16(L0.wl) && a16(L0.wb)) {
+            const int NQ = N / 4;
+            k_apply4<<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1,
+                                                                       nblocks(NQ));
+            k_update4<<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial,
+                                                                        s.tickets + 2, h, use_h, nblocks(NQ));
+            if (!s.use_graph) s.launches += 2;
+            return;
+        }
+    }
     k_apply<T, NR><<<dim3(lblocks(N, s.nz), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1,
                                                                    nblocks(N));
     k_update<T, NR><<<dim3(lblocks(N, s.nz), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial,

@@ -1597,8 +1597,8 @@ __global__ void __launch_bounds__(256) k_update(int N, long long zs, T* __restri
 // to its FP32-pair sum.  Virtual blocks over the quads as in the per-cell kernels, so a batched
 // instance still sums exactly as the instance launched alone.
 
-// walk over the quads (row j, cells 4m .. 4m + 3) of virtual block v of vb, without a division
-// per step
+// walk over the groups of a thread (row j, group m of the row: cells G m .. G m + G - 1, G = 4
+// or 2) of virtual block v of vb, without a division per step
 struct QuadWalk {
     int t, m, j, stride, dm, dj, nq;
     __device__ QuadWalk(int nq_, int v, int nv) : nq(nq_) {
@@ -1692,6 +1692,94 @@ __global__ void __launch_bounds__(256) k_apply4(Lev<float> L, const float* __res
     }
 }
 
+// two right-hand sides (liquid and vapour values of a cell interleaved): a thread takes two
+// consecutive cells of a row, one float4 of each vector, a float2 of each coefficient array
+__global__ void __launch_bounds__(256) k_apply2(Lev<float> L, const float* __restrict__ z, float* __restrict__ p0,
+                                                float* __restrict__ p1, float* __restrict__ q, SolveState* st,
+                                                double* partial, unsigned* ticket, int vb) {
+    const long long zo = zoff(L.zs);
+    L.diag = zsh(L.diag, zo);
+    L.wl = zsh(L.wl, zo);
+    L.wb = zsh(L.wb, zo);
+    z = zsh(z, zo);
+    p0 = zsh(p0, zo);
+    p1 = zsh(p1, zo);
+    q = zsh(q, zo);
+    st = zsh(st, zo);
+    partial = zsh(partial, zo);
+    ticket = zsh(ticket, zo);
+    if (skip(st)) return;
+    const float* __restrict__ Po = (st->iters & 1) ? p1 : p0;
+    float* __restrict__ Pn = (st->iters & 1) ? p0 : p1;
+    const float b0 = (float)st->beta[0], b1 = (float)st->beta[1];
+    const int nx = L.nx, ny = L.ny, np = nx / 2, NP = np * ny;
+    // p = z + beta p_old of one cell (float2) / of two (float4), per right-hand side
+    auto pn2 = [&](int cc) {
+        float2 a = *reinterpret_cast<const float2*>(z + 2 * cc);
+        float2 o = *reinterpret_cast<const float2*>(Po + 2 * cc);
+        if (b0 != 0.0f) a.x += b0 * o.x;
+        if (b1 != 0.0f) a.y += b1 * o.y;
+        return a;
+    };
+    auto pn4 = [&](int cc) {
+        float4 a = *reinterpret_cast<const float4*>(z + 2 * cc);
+        float4 o = *reinterpret_cast<const float4*>(Po + 2 * cc);
+        if (b0 != 0.0f) { a.x += b0 * o.x; a.z += b0 * o.z; }
+        if (b1 != 0.0f) { a.y += b1 * o.y; a.w += b1 * o.w; }
+        return a;
+    };
+    for (int v = blockIdx.x; v < vb; v += gridDim.x) {
+        DotAcc<float, 2> acc;
+#pragma unroll 2
+        for (QuadWalk w(np, v, vb); w.t < NP; w.next()) {
+            const int i0 = 2 * w.m, j = w.j, c = j * nx + i0;
+            float4 pc = pn4(c);
+            float2 dg = *reinterpret_cast<const float2*>(L.diag + c);
+            float2 wl = *reinterpret_cast<const float2*>(L.wl + c);
+            float2 wb = *reinterpret_cast<const float2*>(L.wb + c);
+            float2 pl = i0 > 0 ? pn2(c - 1) : make_float2(0.f, 0.f);
+            float2 pr = i0 + 2 < nx ? pn2(c + 2) : make_float2(0.f, 0.f);
+            float wr1 = i0 + 2 < nx ? L.wl[c + 2] : 0.0f;
+            float4 pd = j > 0 ? pn4(c - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 pu = j < ny - 1 ? pn4(c + nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 wt = j < ny - 1 ? *reinterpret_cast<const float2*>(L.wb + c + nx) : make_float2(0.f, 0.f);
+            float qv[4];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {          // cell i0 + a
+                const int i = i0 + a;
+                const float d = a == 0 ? dg.x : dg.y, wlf = a == 0 ? wl.x : wl.y, wbf = a == 0 ? wb.x : wb.y;
+                const float wrf = a == 0 ? wl.y : wr1, wtf = a == 0 ? wt.x : wt.y;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {      // right-hand side k
+                    const float p = f4(pc, 2 * a + k);
+                    float s = d * p;
+                    const float left = a == 0 ? (k == 0 ? pl.x : pl.y) : f4(pc, k);
+                    const float right = a == 1 ? (k == 0 ? pr.x : pr.y) : f4(pc, 2 + k);
+                    if (i > 0) s += wlf * (p - left);
+                    if (i < nx - 1) s += wrf * (p - right);
+                    if (j > 0) s += wbf * (p - f4(pd, 2 * a + k));
+                    if (j < ny - 1) s += wtf * (p - f4(pu, 2 * a + k));
+                    qv[2 * a + k] = s;
+                    acc.add(k, p, s);
+                }
+            }
+            *reinterpret_cast<float4*>(Pn + 2 * c) = pc;
+            *reinterpret_cast<float4*>(q + 2 * c) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+        }
+        acc.flush();
+        block_partial<2>(acc.tot, partial, vb, v);
+    }
+    double tot[2];
+    if (last_block_total<2>(partial, vb, ticket, tot)) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            st->pq[k] = tot[k];
+            st->alpha[k] = tot[k] != 0.0 ? st->rz[k] / tot[k] : 0.0;
+        }
+    }
+}
+
+template <int NR>
 __global__ void __launch_bounds__(256) k_update4(int N, long long zs, float* __restrict__ x, float* __restrict__ r,
                                                  const float* __restrict__ p0, const float* __restrict__ p1,
                                                  const float* __restrict__ q, SolveState* st, double* partial,
@@ -1710,37 +1798,41 @@ __global__ void __launch_bounds__(256) k_update4(int N, long long zs, float* __r
     const float4* __restrict__ Q = reinterpret_cast<const float4*>(q);
     float4* __restrict__ X = reinterpret_cast<float4*>(x);
     float4* __restrict__ R = reinterpret_cast<float4*>(r);
-    const float alpha = (float)st->alpha[0];
-    const int NQ = N / 4;
+    // element e of a float4 belongs to right-hand side e % NR (NR = 2: liquid, vapour interleaved)
+    const float a0 = (float)st->alpha[0], a1 = NR > 1 ? (float)st->alpha[1] : a0;
+    const int NQ = N * NR / 4;
     for (int v = blockIdx.x; v < vb; v += gridDim.x) {
-        DotAcc<float, 1> acc;
+        DotAcc<float, NR> acc;
 #pragma unroll 2
         for (int t = v * blockDim.x + threadIdx.x; t < NQ; t += vb * blockDim.x) {
             float4 xv = X[t], rv = R[t], pv = Pn[t], qv = Q[t];
-            xv.x += alpha * pv.x;
-            xv.y += alpha * pv.y;
-            xv.z += alpha * pv.z;
-            xv.w += alpha * pv.w;
-            rv.x -= alpha * qv.x;
-            rv.y -= alpha * qv.y;
-            rv.z -= alpha * qv.z;
-            rv.w -= alpha * qv.w;
+            xv.x += a0 * pv.x;
+            xv.y += a1 * pv.y;
+            xv.z += a0 * pv.z;
+            xv.w += a1 * pv.w;
+            rv.x -= a0 * qv.x;
+            rv.y -= a1 * qv.y;
+            rv.z -= a0 * qv.z;
+            rv.w -= a1 * qv.w;
             acc.add(0, rv.x, rv.x);
-            acc.add(0, rv.y, rv.y);
+            acc.add(NR - 1, rv.y, rv.y);
             acc.add(0, rv.z, rv.z);
-            acc.add(0, rv.w, rv.w);
+            acc.add(NR - 1, rv.w, rv.w);
             X[t] = xv;
             R[t] = rv;
         }
         acc.flush();
-        block_partial<1>(acc.tot, partial, vb, v);
+        block_partial<NR>(acc.tot, partial, vb, v);
     }
-    double tot[1];
-    if (last_block_total<1>(partial, vb, ticket, tot)) {
+    double tot[NR];
+    if (last_block_total<NR>(partial, vb, ticket, tot)) {
         bool done = true, bad = false;
-        st->rr[0] = tot[0];
-        if (!(tot[0] <= st->tol2[0])) done = false;
-        bad = !isfinite(tot[0]);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            st->rr[k] = tot[k];
+            if (!(tot[k] <= st->tol2[k])) done = false;
+            bad = bad || !isfinite(tot[k]);
+        }
         st->iters += 1;
         if (bad) {   // a NaN or infinity: no further iteration can recover
             st->nonfinite = 1;
@@ -2717,16 +2809,22 @@ static void cg_body(Solver& s, T* x, T* r, T* z, T* p, T* q, SolveState* st, cud
     int N = s.nx * s.ny;
     Lev<T> L0 = lev<T>(s, 0);
     T* p1 = p + (size_t)N * NR;
-    if constexpr (sizeof(T) == 4 && NR == 1) {
-        // four cells per thread where the rows and the arrays allow 16-byte accesses
+    if constexpr (sizeof(T) == 4) {
+        // four values per thread (four cells, or two cells of two right-hand sides) where the
+        // rows and the arrays allow 16-byte accesses
         auto a16 = [](const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; };
-        if (s.nx % 4 == 0 && s.zs % 16 == 0 && a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(L0.diag) &&
+        constexpr int G = 4 / NR;   // cells per thread
+        if (s.nx % G == 0 && s.zs % 16 == 0 && a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(L0.diag) &&
             a16(L0.wl) && a16(L0.wb)) {
-            const int NQ = N / 4;
-            k_apply4<<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial, s.tickets + 1,
-                                                                       nblocks(NQ));
-            k_update4<<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial,
-                                                                        s.tickets + 2, h, use_h, nblocks(NQ));
+            const int NQ = N / G;
+            if constexpr (NR == 1)
+                k_apply4<<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial,
+                                                                           s.tickets + 1, nblocks(NQ));
+            else
+                k_apply2<<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(L0, z, p, p1, q, st, s.partial,
+                                                                           s.tickets + 1, nblocks(NQ));
+            k_update4<NR><<<dim3(lblocks(NQ, s.nz), 1, s.nz), RB, 0, stm>>>(N, s.zs, x, r, p, p1, q, st, s.partial,
+                                                                            s.tickets + 2, h, use_h, nblocks(NQ));
             if (!s.use_graph) s.launches += 2;
             return;
         }
